@@ -1,0 +1,469 @@
+#!/usr/bin/env python
+"""Benchmark of the FLA hot path on one GB300.
+
+Workload (the 512^2 planar-jet configuration): a 512 x 512 mesh on [0,1]^2, a
+Gaussian jet (centre speed 1, width 0.05) with 8 Lamb-Oseen vortices carried
+by it, 256 releases of 1,024 FLA seeds at the inlet over 1,000 RK4 steps of
+dt = 1e-3, St0 ~ U[0.2, 2] per release, d^2-law evaporation (delta = -0.2),
+the carrier re-sampled and the kernel-regression sources deposited every 10
+steps (100 deposits onto 262,144 cells), FP32 with FP64 det J.
+
+One step = one whole run of the path over that input: 100 windows of
+{carrier sample, fused 10-step advance, cell keys, radix sort, bin starts,
+records, kernel-regression gather}.  The run is captured once in a CUDA graph
+and replayed; the cloud is reset to its seeds (device-to-device copy) and L2 is
+flushed (a 256 MB write) before each timed step, outside the step's events.
+
+Reported: source-term cells/s (cells x deposits / step time) as the headline,
+droplet-steps/s from the device's own counter, the PSI-CELL reference run
+(2^24 parcels, same flow) as a separately timed leg, per-phase CUDA-event
+times from an instrumented eager run, the roofline of the dominant kernel, the
+end-to-end number with host buffers, and the FP64 CPU oracle on a bounded
+sample as the CPU baseline.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "source-term cells/s (kernel-regression deposit, with droplet-steps/s) at rel-L2 <= 1e-4 vs FP64 oracle"
+UNIT = "cells/s"
+WORKLOAD = "jet_vortex_2d: 512^2 cells, 262,144 FLA seeds (256 releases x 1,024), 1,000 RK4 steps, 100 deposits"
+
+# FP32 operations per droplet step of the fused advance, counted from the kernel's
+# operation list (FMA = 2): four stages of bilinear interpolation of 6 node values
+# (58) and the right-hand side (28), the RK4 combinations (156), St(t) (13) and the
+# window sums (20).
+FLOPS_PER_STEP_FLA2D = 533
+# FP32 operations per kernel pair inside the truncation (2D spherical kernel):
+# 2 differences, r^2 (3), exponent scale (1), weight scale (1), 4 FMA sums (8); plus one ex2.
+FLOPS_PER_PAIR_ISO2D = 15
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-psicell", action="store_true", help="skip the PSI-CELL reference leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="run warm-up and timed steps only (for external profilers)")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        sm = [r[0] for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(r[1] for r in rows)),
+                "samples": len(rows), "reasons": reasons}
+
+
+# --------------------------------------------------------------------------- GPU path
+
+class JetPath:
+    """Device buffers and the issue order of one whole run of the jet workload."""
+
+    def __init__(self, ctx, wl, fla, with_fla=True, with_lpt=False):
+        import torch
+        self.fla, self.ctx, self.wl = fla, ctx, wl
+        self.m = fla.mesh(wl.dim, wl.n_cells_axis)
+        self.desc = fla.carrier_desc(wl.carrier)
+        self.nodes = fla.nodes_buffer(self.m, fla.F32)
+        self.cfg = fla.deposit_cfg(wl.kernel, wl.h_min, wl.h_max, wl.window * wl.dt, wl.p)
+        self.cloud = fla.DeviceCloud.from_seeds(wl.fla, 2, wl.delta, wl.dt, fla.F32) if with_fla else None
+        self.lpt = fla.DeviceCloud.from_seeds(wl.lpt, 2, wl.delta, wl.dt, fla.F32) if with_lpt else None
+        n = max(c.n for c in (self.cloud, self.lpt) if c is not None)
+        self.ws = fla.aligned_ws(fla.workspace(self.m, fla.F32, wl.kernel, n))
+        self.out = fla.SourceFields(self.m, fla.F32) if with_fla else None
+        self.psi = fla.PsicellFields(self.m, fla.F32) if with_lpt else None
+        self.pristine = [(c.state.clone(), c.meta.clone()) for c in (self.cloud, self.lpt) if c is not None]
+
+    def clouds(self):
+        return [c for c in (self.cloud, self.lpt) if c is not None]
+
+    def reset(self):
+        for c, (s, m) in zip(self.clouds(), self.pristine):
+            c.state.copy_(s)
+            c.meta.copy_(m)
+
+    def issue(self):
+        """Enqueue the whole run on the current stream (capturable)."""
+        fla, wl, m = self.fla, self.wl, self.m
+        for s in range(0, wl.nsteps, wl.window):
+            fla.carrier_sample(self.ctx, self.desc, m, s * wl.dt, fla.F32, self.nodes)
+            for c in self.clouds():
+                fla.advance(self.ctx, c, m, self.nodes, s, wl.window, wl.dt, reset_acc=True)
+            if self.cloud is not None:
+                fla.deposit_sources(self.ctx, self.cloud, m, self.cfg, self.out, self.ws)
+            if self.lpt is not None:
+                fla.psicell(self.ctx, self.lpt, m, wl.window * wl.dt, self.psi, self.ws)
+
+
+def capture(path):
+    import torch
+    path.reset()
+    path.issue()                     # eager warm-up (sets kernel attributes once)
+    torch.cuda.synchronize()
+    path.reset()
+    torch.cuda.synchronize()
+    path.ctx.profile(False, reset=True)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        path.issue()
+    torch.cuda.synchronize()
+    launches = sum(v["launches"] for v in path.ctx.profile_read().values())
+    return g, launches
+
+
+def timed_replays(path, g, steps, flush, events=True):
+    import torch
+    times = []
+    for _ in range(steps):
+        path.reset()
+        flush.add_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.replay()
+        b.record()
+        times.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in times]
+
+
+def roofline_entry(phase_name, prof, peaks, clocks, status_pairs, droplet_steps_per_run, runs):
+    """Roofline of the dominant phase from the instrumented run's CUDA-event times."""
+    p = prof[phase_name]
+    launches = max(p["launches"], 1)
+    ms_per_launch = p["ms"] / launches
+    sm_max = 2070.0
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s at the maximum SM clock
+    mufu_peak_pairs = 152 * 16 * sm_max * 1e6                # ex2 per second
+    if phase_name == "advance":
+        flops = droplet_steps_per_run * FLOPS_PER_STEP_FLA2D / max(prof["advance"]["calls"] / runs, 1)
+        ach = flops / (ms_per_launch * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                "traffic": None, "kernel": "k_advance<float,2,FLA>",
+                "peak_basis": "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived, max clock)"}
+    if phase_name == "gather":
+        pairs = status_pairs / max(prof["gather"]["calls"], 1)
+        flops = pairs * FLOPS_PER_PAIR_ISO2D
+        ach = flops / (ms_per_launch * 1e-3) / 1e12
+        peak = min(fp32_peak, mufu_peak_pairs * FLOPS_PER_PAIR_ISO2D / 1e12)
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": "k_nw_gather<float,2,ISO>",
+                "peak_basis": "min(FP32 152x128x2, MUFU ex2 152x16 per pair x 15 flops) at 2070 MHz (derived)"}
+    # HBM-bound phases: algorithmic bytes
+    return {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s", "frac": None,
+            "traffic": None, "kernel": phase_name}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2512_20829_gb300 import fla, inputs as I
+
+    rank, local, world = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    ctx = fla.Context(local)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    wl = I.jet_vortex_2d(lpt_per_batch=0 if args.no_psicell else 65_536)
+    cells = wl.n_cells
+    deposits = wl.nsteps // wl.window
+
+    path = JetPath(ctx, wl, fla, with_fla=True)
+    g, launches_per_run = capture(path)
+    flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        path.reset()
+        g.replay()
+    torch.cuda.synchronize()
+
+    # ---------------- timed region (graph replays)
+    ctx.sync_status(reset=True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times = timed_replays(path, g, args.steps, flush)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    st = ctx.sync_status(reset=True)
+    total_ms = float(sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    if args.profile_only:
+        if rank == 0:
+            print(json.dumps({"profile_only": True, "ms": total_ms / args.steps}))
+        return
+    ms_per_step = total_ms / args.steps
+    droplet_steps_per_run = st.droplet_steps / args.steps
+    value = world * cells * deposits * args.steps / (total_ms * 1e-3)
+
+    # ---------------- instrumented eager run: per-phase CUDA-event times
+    path.reset()
+    ctx.sync_status(reset=True)
+    ctx.profile(True, reset=True)
+    path.issue()
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False, reset=True)
+    stp = ctx.sync_status(reset=True)
+    dominant = max(prof, key=lambda k: prof[k]["ms"])
+    roof = roofline_entry(dominant, prof, peaks, clocks, stp.pairs, droplet_steps_per_run, 1)
+    phases = {k: {"ms_per_run": round(v["ms"], 4), "launches_per_run": v["launches"]} for k, v in prof.items()
+              if v["calls"]}
+
+    # ---------------- end to end: pinned host seeds in, final source fields out
+    host_state = path.pristine[0][0].cpu().pin_memory()
+    host_meta = path.pristine[0][1].cpu().pin_memory()
+    out_host = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in (path.out.s_mass, path.out.s_mom,
+                                                                              path.out.dsum)]
+    h2d = host_state.numel() * host_state.element_size() + host_meta.numel() * host_meta.element_size()
+    d2h = sum(t.numel() * t.element_size() for t in out_host)
+    e2e = []
+    for k in range(max(2, args.steps // 2)):
+        flush.add_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        path.cloud.state.copy_(host_state, non_blocking=True)
+        path.cloud.meta.copy_(host_meta, non_blocking=True)
+        g.replay()
+        for dst, src in zip(out_host, (path.out.s_mass, path.out.s_mom, path.out.dsum)):
+            dst.copy_(src, non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        e2e.append(a.elapsed_time(b))
+    e2e_ms = float(np.mean(e2e))
+
+    # ---------------- PSI-CELL reference leg (2^24 parcels, same flow, same windows)
+    psi = None
+    if not args.no_psicell and rank == 0:
+        del g
+        ppath = JetPath(ctx, wl, fla, with_fla=False, with_lpt=True)
+        pg, plaunch = capture(ppath)
+        pg.replay()
+        torch.cuda.synchronize()
+        ctx.sync_status(reset=True)
+        pt = timed_replays(ppath, pg, 2, flush)
+        pst = ctx.sync_status(reset=True)
+        pms = float(np.mean(pt))
+        psi = {"parcels": wl.lpt.n, "ms_per_run": round(pms, 3),
+               "cells_per_s": cells * deposits / (pms * 1e-3),
+               "parcel_steps_per_s": pst.droplet_steps / 2 / (pms * 1e-3),
+               "gpu_launches_per_run": plaunch,
+               "fla_speedup_vs_psicell": round(pms / ms_per_step, 2)}
+        del pg, ppath
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(wl)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (f64 det J)", "data": "synthetic (seeded jet + vortices)",
+            "config": {"workload": WORKLOAD, "global_batch": world * wl.fla.n, "cells": cells,
+                       "deposits_per_step": deposits, "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"replicas x{world} (independent clouds, no collective)"},
+            "droplet_steps_per_s": world * droplet_steps_per_run * args.steps / (total_ms * 1e-3),
+            "gpu_launches": launches_per_run * args.steps,
+            "clocks": clocks,
+            "roofline": roof,
+            "phases": phases,
+            "e2e": {"value": world * cells * deposits / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
+            "psicell_reference": psi,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------- CPU oracle
+
+def cpu_baseline(wl, seeds=8192, cells_a=256, cells_b=4096, track=256):
+    """The FP64 oracle, single-threaded, on a bounded sample of the same workload,
+    scaled to the whole run from separately timed parts:
+      carrier  one node re-sample, times the number of carrier steps;
+      advance  cost per droplet step from `seeds` seeds of the first release over
+               two windows (their two re-samples subtracted), times the run's active
+               droplet steps, counted from `track` random seeds integrated through the
+               whole run with the analytic carrier;
+      deposit  cell-list deposit of a cloud state of the workload's size and shape at
+               cells_a and cells_b cells: fixed part (cell list and records) plus the
+               per-cell slope times all cells, times the number of deposits."""
+    from oracle import oracle as O
+    from paper_2512_20829_gb300 import inputs as I
+    rng = np.random.default_rng(0)
+    n, nsteps, win = wl.fla.n, wl.nsteps, wl.window
+    deposits = nsteps // win
+    wall0 = time.perf_counter()
+    # carrier
+    t0 = time.perf_counter()
+    O.carrier_nodes(wl.carrier, 0.0, wl.n_cells_axis)
+    t_node = time.perf_counter() - t0
+    t_car = t_node * (1 if wl.carrier.steady else deposits)
+    # advance cost per droplet step
+    first = np.nonzero(wl.fla.batch == 0)[0][:seeds]
+    sub = I.Cloud(kind=wl.fla.kind, x0=wl.fla.x0[first], batch=wl.fla.batch[first], step_start=wl.fla.step_start,
+                  St0=wl.fla.St0, n0=wl.fla.n0, h0=wl.fla.h0)
+    adv = O.Advancer(wl, sub)
+    st = O.initial_state(sub, wl.dim)
+    t0 = time.perf_counter()
+    adv.advance(st, 0, win, reset_acc=True)
+    adv.advance(st, win, win, reset_acc=True)
+    t_two = time.perf_counter() - t0
+    per_step = max(t_two - 2 * t_node, 1e-9) / (len(first) * 2 * win)
+    # active droplet steps of the whole run (fraction from tracked seeds, analytic carrier)
+    idx = np.sort(rng.choice(n, track, replace=False))
+    tr = I.Cloud(kind=wl.fla.kind, x0=wl.fla.x0[idx], batch=wl.fla.batch[idx], step_start=wl.fla.step_start,
+                 St0=wl.fla.St0, n0=wl.fla.n0, h0=wl.fla.h0)
+    adv2 = O.Advancer(wl, tr, use_mesh=False)
+    st2 = O.initial_state(tr, wl.dim)
+    active_steps = 0
+    for s in range(0, nsteps, win):
+        adv2.advance(st2, s, win, reset_acc=True)
+        active_steps += win * int((st2.status == O.ACTIVE).sum())
+    droplet_steps = active_steps * n / track
+    # deposit: fixed + per-cell
+    s_ = I.synthetic_state(2, n, wl.n_cells_axis, seed=31, band=(0.4, 0.6), h0_cells=2.0, jac_spread=0.3)
+    D = O.dep_struct(wl)
+    band = np.arange(int(0.4 * wl.n_cells_axis), int(0.6 * wl.n_cells_axis))
+    times = []
+    for c in (cells_a, cells_b):
+        cells = rng.choice(band, c) * wl.n_cells_axis + rng.integers(0, wl.n_cells_axis, c)
+        t0 = time.perf_counter()
+        O.nw_deposit_celllist(D, s_.x, s_.J, s_.acc, s_.status, s_.batch, s_.n0, s_.h0, cells=cells)
+        times.append(time.perf_counter() - t0)
+    per_cell = max(times[1] - times[0], 1e-9) / (cells_b - cells_a)
+    fixed = max(times[0] - per_cell * cells_a, 0.0)
+    t_dep = fixed + per_cell * wl.n_cells
+    t_run = t_car + per_step * droplet_steps + deposits * t_dep
+    return {"value": wl.n_cells * deposits / t_run, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"carrier re-sample x{1 if wl.carrier.steady else deposits}; {len(first)} seeds x {2 * win} "
+                       f"steps ({per_step * 1e6:.2f} us per droplet step) x {droplet_steps:.3g} active droplet "
+                       f"steps (from {track} tracked seeds); cell-list deposit at {cells_a}/{cells_b} cells of a "
+                       f"{n}-droplet state ({per_cell * 1e6:.1f} us per cell + {fixed:.2f} s fixed) x {deposits}"),
+            "est_seconds_per_run": round(t_run, 1), "sample_seconds": round(time.perf_counter() - wall0, 2),
+            "cpu": platform_cpu()}
+
+
+def platform_cpu():
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                return ln.split(":", 1)[1].strip() + f" x{os.cpu_count()}"
+    except Exception:
+        pass
+    return f"{os.uname().machine} x{os.cpu_count()}"
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    from paper_2512_20829_gb300 import inputs as I
+    wl = I.jet_vortex_2d(lpt_per_batch=0)
+    per_step = []
+    last = None
+    for k in range(args.warmup + args.steps):
+        last = cpu_baseline(wl, seeds=256, cells_a=32, cells_b=96, track=32)
+        if k >= args.warmup:
+            per_step.append(wl.n_cells * (wl.nsteps // wl.window) / last["value"])
+    ms = 1e3 * float(np.mean(per_step))
+    value = wl.n_cells * (wl.nsteps // wl.window) / (ms * 1e-3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded jet + vortices)",
+            "config": {"workload": WORKLOAD, "cells": wl.n_cells},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "per step: " + last["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,287 @@
+/*
+ * fla.h -- C interface of the GB300 (sm_103a) library for the fully Lagrangian
+ * approach (FLA) advance and the interphase source-term deposits of
+ * Stafford & Rybdylova, "Interphase coupling for gas-droplet flows using the
+ * fully Lagrangian approach".  Equation numbers below are the paper's.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Domain [0,1]^dim (dim = 2 or 3) with a uniform mesh of n^dim cells, cell
+ *    size dx = 1/n, cell centres (i + 1/2) dx.  Cells and mesh nodes are
+ *    numbered with x fastest, then y, then z.
+ *  - Every pointer named *_dev is device memory that the CALLER owns and keeps
+ *    alive until the work enqueued on the stream has finished.  The library
+ *    never allocates device memory in these calls; temporary storage comes from
+ *    the caller's workspace (see fla_workspace_size).  Only fla_create
+ *    allocates (a small status block) and fla_destroy frees it.
+ *  - All GPU work is enqueued asynchronously on the caller's stream; a NULL
+ *    stream is the legacy default stream.  A return of FLA_OK means that the
+ *    arguments were valid and the kernels were enqueued.  Problems found on
+ *    the device (non-finite values) are counted in a status block that only
+ *    fla_sync_status reads back.  Device code never traps or asserts.
+ *  - Host-detectable errors return a negative fla_status and enqueue nothing.
+ *  - There is no CPU fallback: without a usable CUDA device fla_create returns
+ *    FLA_ERR_CUDA.
+ */
+#ifndef FLA_H
+#define FLA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FLA_ABI_VERSION 1
+
+/* cudaStream_t without including the CUDA headers. */
+typedef struct CUstream_st* fla_stream_t;
+
+typedef enum {
+    FLA_OK = 0,
+    FLA_ERR_ARG = -1,          /* invalid argument: null pointer, bad size or mode */
+    FLA_ERR_CUDA = -2,         /* a CUDA runtime call or kernel launch failed */
+    FLA_ERR_WORKSPACE = -3,    /* workspace pointer missing, misaligned or too small */
+    FLA_ERR_NONFINITE = -4,    /* reported by fla_sync_status: non-finite records seen */
+    FLA_ERR_TIMEOUT = -5,      /* reserved for bounded device-side waits */
+    FLA_ERR_UNSUPPORTED = -6   /* valid but not implemented combination */
+} fla_status;
+
+enum { FLA_F32 = 0, FLA_F64 = 1 };                    /* arithmetic and storage type */
+enum { FLA_CLOUD_FLA = 0, FLA_CLOUD_LPT = 1 };        /* FLA seeds (with J) or plain parcels */
+enum { FLA_KERNEL_ISO = 0, FLA_KERNEL_ANISO = 1 };    /* deposit kernel shape */
+
+/* Analytic carriers sampled onto the mesh nodes (stand-ins for the paper's
+ * Navier-Stokes carrier of Eq. 1). */
+enum {
+    FLA_CARRIER_UNIFORM = 0,   /* u = U */
+    FLA_CARRIER_LINEAR = 1,    /* u = U + A (x - xref) */
+    FLA_CARRIER_TG2 = 2,       /* (sin pi x cos pi y, -cos pi x sin pi y) */
+    FLA_CARRIER_JETVORT2 = 3,  /* planar jet exp(-((y-1/2)/w)^2) e_x + Lamb-Oseen vortices */
+    FLA_CARRIER_ABCJET3 = 4    /* ABC flow at wavenumber 2 pi + round jet along z */
+};
+
+/* Per-droplet meta word: release index in bits 0..23 plus two state bits.
+ * A seed with neither bit set is pending (not yet released). */
+#define FLA_META_BATCH_MASK 0x00FFFFFFu
+#define FLA_META_DEAD 0x40000000u
+#define FLA_META_ACTIVE 0x80000000u
+
+#define FLA_MAX_VORTICES 16
+#define FLA_NO_DEADLINE 2147483647
+
+/* Opaque context: the device it was created on, its SM count and a small
+ * device status block. */
+typedef struct fla_ctx fla_ctx;
+
+typedef struct {
+    int32_t dim;               /* 2 or 3 */
+    int32_t n;                 /* cells per axis, >= 1; n^dim < 2^31 */
+} fla_mesh;
+
+typedef struct {
+    int32_t kind, dim;
+    double U[3];
+    double A[9];               /* row-major: u_i += A[3 i + j] (x_j - xref_j) */
+    double xref[3];
+    int32_t n_vortex;          /* <= FLA_MAX_VORTICES */
+    double vortex[FLA_MAX_VORTICES][5]; /* x0, yc, Gamma, rc, Uadv: centre x = frac(x0 + Uadv t) */
+    double jet_width;          /* planar jet width w */
+    double abc[3];             /* ABC amplitudes A, B, C */
+    double jet_amp, jet_radius;/* round jet u_z += amp exp(-(rho/radius)^2) */
+} fla_carrier_desc;
+
+/* One release ("batch") of seeds.  32 bytes, device array. */
+typedef struct {
+    double St0;                /* Stokes number at release (Eq. 5 with r = r0) */
+    double n0;                 /* FLA: number density at release (Eq. 6, App. A);
+                                  LPT: real droplets represented by one parcel */
+    double h0;                 /* FLA: smoothing length at release (Eq. 15) */
+    int32_t step_start;        /* step index at which the seeds are released */
+    int32_t step_dead;         /* step index from which they are inactive (evaporated) */
+} fla_batch;
+
+/* A cloud of droplets stored as structure-of-arrays "planes" of 4 values:
+ * state_dev holds n_planes * n * 4 values of the cloud's dtype; value c of
+ * droplet i in plane p is at index (p * n + i) * 4 + c.  The flattened value
+ * vector of one droplet is
+ *   FLA: x[dim], v[dim], J[dim*dim], W[dim*dim], acc[1+dim], zero padding
+ *   LPT: x[dim], v[dim], acc[1+dim], zero padding
+ * (J = dx/dx0 row-major, W = dJ/dt, acc = window sums of mdot and F + mdot v).
+ * Use fla_state_layout for n_planes and the offsets.  Pending seeds hold
+ * their release position in x. */
+typedef struct {
+    int32_t kind;              /* FLA_CLOUD_FLA or FLA_CLOUD_LPT */
+    int32_t dim;
+    int32_t dtype;             /* FLA_F32 or FLA_F64 */
+    int32_t n_batches;
+    int64_t n;                 /* droplets, < 2^31 */
+    void* state_dev;
+    uint32_t* meta_dev;        /* n meta words */
+    const fla_batch* batches_dev; /* n_batches entries */
+    double delta;              /* d^2-law rate: r^2 = r0^2 + delta (t - t0), r0 = 1 (Eq. 4) */
+} fla_cloud;
+
+/* Kernel-regression deposit settings. */
+typedef struct {
+    int32_t kernel;            /* FLA_KERNEL_ISO: Eq. 14 with h of Eq. 15;
+                                  FLA_KERNEL_ANISO: covariance f h0^2 J J^T + h_min^2 I */
+    int32_t per_cell;          /* 0: sources per unit volume; 1: multiplied by the cell volume */
+    double h_min, h_max;       /* smoothing-length clamps (absolute lengths), 0 < h_min <= h_max */
+    double p;                  /* h = h0 |det J|^p; the paper's Eq. 15 is p = 1 */
+    double window_dt;          /* time covered by the window sums acc (> 0) */
+} fla_deposit_cfg;
+
+/* Deposit outputs, device arrays of the cloud's dtype, n_cells entries each
+ * (s_mom: dim consecutive planes of n_cells).  dsum_dev (the kernel-estimator
+ * denominator) may be NULL. */
+typedef struct {
+    void* s_mass_dev;
+    void* s_mom_dev;
+    void* dsum_dev;
+} fla_sources;
+
+typedef struct {
+    uint32_t* counts_dev;      /* parcels per cell, n_cells entries */
+    void* s_mass_dev;          /* n_cells of the cloud dtype */
+    void* s_mom_dev;           /* dim planes of n_cells */
+} fla_psicell_out;
+
+typedef struct {
+    uint64_t nonfinite;        /* records with a non-finite n, h or source value */
+    uint64_t deposited;        /* droplets that entered a kernel-regression deposit */
+    uint64_t droplet_steps;    /* droplet steps integrated by fla_advance (active droplet x step) */
+    uint64_t pairs;            /* (cell, droplet) pairs inside the truncated kernels, summed over deposits */
+    uint32_t flags;            /* reserved, 0 */
+    uint32_t pad;
+} fla_device_status;
+
+/* Phases of the path, for fla_profile_read. */
+enum {
+    FLA_PHASE_CARRIER = 0,     /* carrier sampling */
+    FLA_PHASE_ADVANCE = 1,     /* fused RK4 advance */
+    FLA_PHASE_KEYS = 2,        /* cell keys */
+    FLA_PHASE_SORT = 3,        /* radix sort passes */
+    FLA_PHASE_BINS = 4,        /* bin starts */
+    FLA_PHASE_RECORDS = 5,     /* kernel-regression records */
+    FLA_PHASE_GATHER = 6,      /* kernel-regression gather */
+    FLA_PHASE_PSICELL = 7,     /* PSI-CELL records and per-cell sums */
+    FLA_PHASE_COUNT = 8
+};
+
+/* ------------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device` (it also becomes the current
+ * device of the calling thread).  Allocates a 64-byte status block.
+ * Returns FLA_ERR_CUDA when no usable device exists. */
+int fla_create(fla_ctx** out, int device);
+void fla_destroy(fla_ctx* ctx);
+const char* fla_status_string(int code);
+int fla_abi_version(void);
+
+/* Number of value planes of a cloud and the offsets (in values) of x, v, J,
+ * W and acc in the flattened per-droplet vector (J and W are -1 for LPT). */
+int fla_state_layout(int32_t kind, int32_t dim, int32_t* n_planes, int32_t* off_x, int32_t* off_v,
+                     int32_t* off_J, int32_t* off_W, int32_t* off_acc);
+
+/* Bytes of a node array for fla_carrier_sample: (n+1)^dim nodes, each holding
+ * u (dim values) then grad u (dim*dim, row-major, G_ij = du_i/dx_j), padded
+ * to 8 values (2D) or 12 values (3D). */
+size_t fla_carrier_nodes_bytes(const fla_mesh* mesh, int32_t dtype);
+
+/* Sample the analytic carrier and its gradient at time t on the mesh nodes
+ * (Eq. 3 needs u at the droplet, Eq. 8 grad u; both are interpolated from
+ * these nodes by fla_advance).  nodes_dev: fla_carrier_nodes_bytes bytes,
+ * 16-byte aligned. */
+int fla_carrier_sample(fla_ctx* ctx, const fla_carrier_desc* carrier, const fla_mesh* mesh, double t,
+                       int32_t dtype, void* nodes_dev, fla_stream_t stream);
+
+/* Host helper: the step from which a release is inactive because it has nearly
+ * evaporated: the first s >= step_start with 1 + delta (s - step_start) dt below
+ * max(0.01, 4 dt / St0) (Eq. 4 with r0 = 1); FLA_NO_DEADLINE if delta >= 0. */
+int fla_batch_deadline(double St0, double delta, double dt, int32_t step_start, int32_t* step_dead);
+
+#define FLA_ADVANCE_RESET_ACC 1u
+
+/* Advance every droplet through steps [step0, step0 + nsteps) of size dt with
+ * the carrier frozen at the given node values (re-sample between calls for an
+ * unsteady carrier).  Per step s and droplet:
+ *   - a pending seed with step_start == s is released: v = u(x0), and for FLA
+ *     J = I and W = grad u(x0) (initial data of Eq. 8);
+ *   - an active droplet with s >= step_dead becomes inactive;
+ *   - an active droplet adds dt * (mdot, F + mdot v) at the step's first RK
+ *     stage to acc (App. B, parcel level a-b; F = m x'' below Eq. 9, m = r^3,
+ *     mdot = 1.5 delta r), then takes one classical RK4 step of
+ *     x' = v, v' = (u - v)/St (Eq. 3) and, for FLA, J' = W,
+ *     W' = (grad u . J - W)/St (Eq. 8), with St = St0 (1 + delta (t - t0)) (Eqs. 4-5);
+ *   - a droplet that leaves [0,1]^dim becomes inactive.
+ * Carrier values are bi/trilinear interpolations of nodes_dev (cell index
+ * clamped to the mesh).  FLA_ADVANCE_RESET_ACC zeroes acc before the first step.
+ * The cloud and nodes must share the dtype; nodes_dev 16-byte aligned. */
+int fla_advance(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, const void* nodes_dev,
+                int32_t step0, int32_t nsteps, double dt, uint32_t flags, fla_stream_t stream);
+
+/* Workspace bytes needed by fla_cell_bins, fla_deposit_sources and
+ * psicell_deposit for a cloud of n_droplets on this mesh (the maximum over the
+ * three, for the given dtype and kernel).  The workspace must be 256-byte
+ * aligned. */
+int fla_workspace_size(const fla_mesh* mesh, int32_t dtype, int32_t kernel, int64_t n_droplets, size_t* bytes);
+
+/* Cell binning of a cloud: key_i = linear index of the cell holding x_i
+ * (floor(x N) per axis in the cloud's precision, clamped to N-1 so x = 1 is in
+ * the last cell), droplets that are not active or lie outside [0,1]^dim get
+ * the key n_cells.  Outputs (device, caller-owned): keys_sorted_dev[n] (the
+ * keys in stable ascending order, inactive last, with n_cells as key),
+ * perm_dev[n] (droplet index at each sorted position; ties keep index order)
+ * and bin_start_dev[n_cells + 1] (first sorted position of each cell;
+ * bin_start[n_cells] = number of binned droplets).  Bit-exact, deterministic. */
+int fla_cell_bins(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, uint32_t* keys_sorted_dev,
+                  uint32_t* perm_dev, uint32_t* bin_start_dev, void* workspace_dev, size_t workspace_bytes,
+                  fla_stream_t stream);
+
+/* Kernel-regression (Nadaraya-Watson) source terms of an FLA cloud at every
+ * cell centre x_c (Eqs. 13 and 16, signs of Eq. 9, App. B cloud level):
+ *   n_i = n0/max(|det J_i|, 1e-12) (Eq. 6),  a_i = n_i acc_i / window_dt,
+ *   K_i(x_c) = pref_i exp(-q/2) if q <= 9 else 0 (Eq. 14, truncated at 3 sigma),
+ *     ISO:   q = |x_c - x_i|^2 / h_i^2, h_i = clamp(h0 |det J_i|^p, h_min, h_max), pref = 1/h_i
+ *     ANISO: q = d^T Sigma_i^-1 d, Sigma_i = f h0^2 J J^T + h_min^2 I with
+ *            f = min(1, (h_max^2 - dim h_min^2)/tr(h0^2 J J^T)), pref = det(Sigma_i)^-1/2
+ *   D_c = sum_i K_i(x_c),  S_mass = -sum K_i a_mass,i / D_c,  S_mom = -sum K_i a_mom,i / D_c,
+ *   S = 0 where D_c = 0; times the cell volume when cfg->per_cell.
+ * Sums run in a fixed order with compensated (Neumaier) accumulation; the
+ * result does not depend on launch timing.  Single precision decides the
+ * truncation test on single-precision operands. */
+int fla_deposit_sources(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, const fla_deposit_cfg* cfg,
+                        const fla_sources* out, void* workspace_dev, size_t workspace_bytes,
+                        fla_stream_t stream);
+
+/* PSI-CELL box-count sources of a parcel cloud (Eqs. 10-11): for each cell,
+ * counts = number of active parcels inside, and
+ *   S_mass = -(1/V) sum w_b acc_mass,i / window_dt,  S_mom = -(1/V) sum w_b acc_mom,i / window_dt
+ * over those parcels, w_b = batches[b].n0 the real droplets per parcel,
+ * V the cell volume (dropped when per_cell).  Counts are exact; sums are in a
+ * fixed order. */
+int psicell_deposit(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, double window_dt,
+                    int32_t per_cell, const fla_psicell_out* out, void* workspace_dev, size_t workspace_bytes,
+                    fla_stream_t stream);
+
+/* Read the device status block (synchronises `stream`); reset != 0 zeroes it
+ * afterwards.  Returns FLA_ERR_NONFINITE when nonfinite > 0, else FLA_OK. */
+int fla_sync_status(fla_ctx* ctx, fla_stream_t stream, fla_device_status* out, int reset);
+
+/* Per-phase profiling.  The context always counts the kernels it launches per
+ * phase (also while a stream is being captured into a CUDA graph).  With
+ * timing enabled it also brackets every phase of every call with CUDA events
+ * on the call's stream; fla_profile_read waits for those events and returns,
+ * per phase, the summed milliseconds, kernel launches and calls since the last
+ * reset.  Timing must stay disabled while a stream is being captured.
+ * enable: 0 off, 1 on; reset != 0 zeroes the counters and drops pending events. */
+int fla_profile_enable(fla_ctx* ctx, int enable, int reset);
+int fla_profile_read(fla_ctx* ctx, int32_t n_phases, double* ms, int64_t* launches, int64_t* calls);
+const char* fla_phase_name(int32_t phase);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLA_H */

@@ -619,9 +619,23 @@ static int cmp_int(const void* a, const void* b)
  * cells (every droplet whose truncated kernel can reach the centre), sorts the
  * candidates by index and sums in that order.  Gives bit-identical results to
  * ora_nw_deposit. */
+int ora_nw_deposit_celllist_cells(const ora_dep* D, int n, const double* x, const double* J, const double* acc,
+                                  const int* status, const int* batch, const double* n0, const double* h0,
+                                  long n_out, const long* cells, double* S_mass, double* S_mom, double* Dsum);
+
 int ora_nw_deposit_celllist(const ora_dep* D, int n, const double* x, const double* J, const double* acc,
                             const int* status, const int* batch, const double* n0, const double* h0,
                             double* S_mass, double* S_mom, double* Dsum)
+{
+    int d = D->dim, N = D->N;
+    long nc = (d == 2) ? (long)N * N : (long)N * N * N;
+    return ora_nw_deposit_celllist_cells(D, n, x, J, acc, status, batch, n0, h0, nc, NULL, S_mass, S_mom, Dsum);
+}
+
+/* Cell-list deposit at the listed cells (NULL: every cell in order). */
+int ora_nw_deposit_celllist_cells(const ora_dep* D, int n, const double* x, const double* J, const double* acc,
+                                  const int* status, const int* batch, const double* n0, const double* h0,
+                                  long n_out, const long* cells, double* S_mass, double* S_mom, double* Dsum)
 {
     int d = D->dim, N = D->N;
     long nc = (d == 2) ? (long)N * N : (long)N * N * N;
@@ -636,13 +650,14 @@ int ora_nw_deposit_celllist(const ora_dep* D, int n, const double* x, const doub
     for (int i = 0; i < n; ++i) if (keys[i] != 0xFFFFFFFFu) list[fill[keys[i]]++] = i;
     ora_rec* rec = (ora_rec*)malloc(sizeof(ora_rec) * (n > 0 ? n : 1));
     for (int i = 0; i < n; ++i)
-        if (status[i] == ORA_ACTIVE)
+        if (keys[i] != 0xFFFFFFFFu)
             ora_record(D, x + (long)i * d, J + (long)i * d * d, acc + (long)i * (1 + d),
                        n0[batch[i]], h0[batch[i]], &rec[i]);
     int R = (int)floor(3.0 * D->h_max * N + 0.5) + 1;
     int* cand = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
     double V = cell_volume(D);
-    for (long c = 0; c < nc; ++c) {
+    for (long o = 0; o < n_out; ++o) {
+        long c = cells ? cells[o] : o;
         int ci[3] = {0, 0, 0};
         long r = c;
         for (int a = 0; a < d; ++a) { ci[a] = (int)(r % N); r /= N; }
@@ -672,9 +687,9 @@ int ora_nw_deposit_celllist(const ora_dep* D, int n, const double* x, const doub
             for (int a = 0; a < 1 + d; ++a) num[a] += w * rec[i].a[a];
         }
         double scale = D->per_cell ? V : 1.0;
-        S_mass[c] = den > 0.0 ? -num[0] / den * scale : 0.0;
-        for (int a = 0; a < d; ++a) S_mom[c * d + a] = den > 0.0 ? -num[1 + a] / den * scale : 0.0;
-        Dsum[c] = den;
+        S_mass[o] = den > 0.0 ? -num[0] / den * scale : 0.0;
+        for (int a = 0; a < d; ++a) S_mom[o * d + a] = den > 0.0 ? -num[1 + a] / den * scale : 0.0;
+        Dsum[o] = den;
     }
     free(keys); free(start); free(list); free(fill); free(rec); free(cand);
     return 0;

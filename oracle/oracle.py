@@ -74,6 +74,8 @@ def lib():
         _lib.ora_cell_keys.argtypes = [i, i, i, v, v, i, v]
         _lib.ora_nw_deposit.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, v, v, C.c_long, v, v, v, v]
         _lib.ora_nw_deposit_celllist.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, v, v, v, v, v]
+        _lib.ora_nw_deposit_celllist_cells.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, v, v, C.c_long, v,
+                                                       v, v, v]
         _lib.ora_kernel_on_cells.argtypes = [C.POINTER(_Dep), v, v, d, d, i, v]
         _lib.ora_records.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, v, v]
         _lib.ora_psicell.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, i, v, v, v]
@@ -249,16 +251,21 @@ def nw_deposit(D: _Dep, x, J, acc, status, batch, n0, h0, cells=None):
     return Sm, Sv, Ds
 
 
-def nw_deposit_celllist(D: _Dep, x, J, acc, status, batch, n0, h0):
+def nw_deposit_celllist(D: _Dep, x, J, acc, status, batch, n0, h0, cells=None):
+    """Cell-list deposit (bit-identical to the brute force); cells limits it to a list."""
     d = D.dim
     x, J, acc = _f64(x).reshape(-1, d), _f64(J).reshape(-1, d * d), _f64(acc).reshape(-1, 1 + d)
     status, batch = _i32(status), _i32(batch)
-    nc = D.N ** d
-    Sm = np.zeros(nc)
-    Sv = np.zeros((nc, d))
-    Ds = np.zeros(nc)
-    lib().ora_nw_deposit_celllist(C.byref(D), x.shape[0], _p(x), _p(J), _p(acc), _p(status), _p(batch),
-                                  _p(_f64(n0)), _p(_f64(h0)), _p(Sm), _p(Sv), _p(Ds))
+    if cells is None:
+        n_out, cptr = D.N ** d, None
+    else:
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        n_out, cptr = cells.shape[0], _p(cells)
+    Sm = np.zeros(n_out)
+    Sv = np.zeros((n_out, d))
+    Ds = np.zeros(n_out)
+    lib().ora_nw_deposit_celllist_cells(C.byref(D), x.shape[0], _p(x), _p(J), _p(acc), _p(status), _p(batch),
+                                        _p(_f64(n0)), _p(_f64(h0)), n_out, cptr, _p(Sm), _p(Sv), _p(Ds))
     return Sm, Sv, Ds
 
 

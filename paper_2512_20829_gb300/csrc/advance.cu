@@ -1,0 +1,284 @@
+// FLA / LPT advance: k fused RK4 steps per launch, one thread per droplet.
+//
+// Per droplet and step (Eqs. 3-5 and 8; App. B parcel level a-b):
+//   x' = v,  v' = (u(x) - v)/St(t),  J' = W,  W' = (grad u(x) . J - W)/St(t),
+//   St(t) = St0 (1 + delta (t - t0))  (d^2 law with r0 = 1),
+// with window sums of mdot = 1.5 delta r and F + mdot v = m (u - v)/St + mdot v
+// taken at the first RK stage.  The state stays in registers across the fused
+// steps, so HBM is touched once per launch; the carrier node array (a few MB
+// in 2D) is read through the L1/L2 caches by the interpolation gathers.
+#include "fla_internal.cuh"
+
+namespace fla {
+namespace {
+
+struct AdvArgs {
+    void* state;
+    uint32_t* meta;
+    const fla_batch* batches;
+    const void* nodes;
+    int64_t n;
+    int N;
+    int step0, nsteps;
+    double dt, delta;
+    int reset;
+    DevStatus* status;
+};
+
+// Cell index of coordinate s = x N: floor clamped to [0, N-1]; positions past
+// the edge are extrapolated from the edge cell (RK stages may step outside).
+template <typename T>
+__device__ __forceinline__ int cell_of(T s, int N, T& frac)
+{
+    int i;
+    if (s >= T(N - 1)) i = N - 1;
+    else if (s > T(0)) i = (int)s;
+    else i = 0;
+    frac = s - T(i);
+    return i;
+}
+
+// Bi/trilinear interpolation of the node values (u then grad u) at x.
+template <typename T, int D>
+__device__ __forceinline__ void interp(const T* __restrict__ nodes, int N, T fN, const T* x, T* u, T* G)
+{
+    constexpr int S4 = node_stride(D) / 4;
+    T f[D];
+    int ic[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) ic[a] = cell_of<T>(x[a] * fN, N, f[a]);
+    const int64_t nn = N + 1;
+    int64_t base = ic[0];
+    if (D == 2) base += nn * ic[1];
+    else base += nn * (ic[1] + nn * (int64_t)ic[2]);
+    T acc[D + D * D];
+#pragma unroll
+    for (int q = 0; q < D + D * D; ++q) acc[q] = T(0);
+#pragma unroll
+    for (int cnr = 0; cnr < (1 << D); ++cnr) {
+        T w = T(1);
+        int64_t idx = base;
+        int64_t mul = 1;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const int bit = (cnr >> a) & 1;
+            w *= bit ? f[a] : T(1) - f[a];
+            idx += bit * mul;
+            mul *= nn;
+        }
+        T v[node_stride(D)];
+#pragma unroll
+        for (int c = 0; c < S4; ++c) load4<T>(nodes, idx * S4 + c, v + 4 * c);
+#pragma unroll
+        for (int q = 0; q < D + D * D; ++q) acc[q] = fma(w, v[q], acc[q]);
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) u[a] = acc[a];
+#pragma unroll
+    for (int q = 0; q < D * D; ++q) G[q] = acc[D + q];
+}
+
+// Right-hand side of the droplet system given u, G at the stage position.
+template <typename T, int D, bool FLA>
+__device__ __forceinline__ void rhs(const T* y, const T* u, const T* G, T invSt, T* f)
+{
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        f[a] = y[D + a];
+        f[D + a] = (u[a] - y[D + a]) * invSt;
+    }
+    if (FLA) {
+        const T* J = y + 2 * D;
+        const T* W = y + 2 * D + D * D;
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                T gj = T(0);
+#pragma unroll
+                for (int j = 0; j < D; ++j) gj = fma(G[i * D + j], J[j * D + k], gj);
+                f[2 * D + i * D + k] = W[i * D + k];
+                f[2 * D + D * D + i * D + k] = (gj - W[i * D + k]) * invSt;
+            }
+    }
+}
+
+template <typename T, int D, bool FLA>
+__device__ __forceinline__ int advance_one(const AdvArgs& a, int64_t i)
+{
+    constexpr int kind = FLA ? FLA_CLOUD_FLA : FLA_CLOUD_LPT;
+    constexpr int NP = state_planes(kind, D);
+    constexpr int NY = FLA ? 2 * D + 2 * D * D : 2 * D;
+    constexpr int OA = acc_offset(kind, D);
+    uint32_t meta = a.meta[i];
+    if (meta & FLA_META_DEAD) return 0;
+    const fla_batch* B = a.batches + (meta & FLA_META_BATCH_MASK);
+    const int ss = __ldg(&B->step_start);
+    const int sd = __ldg(&B->step_dead);
+    bool active = (meta & FLA_META_ACTIVE) != 0;
+    if (!active && (ss < a.step0 || ss >= a.step0 + a.nsteps)) return 0;
+
+    T* state = (T*)a.state;
+    const T* nodes = (const T*)a.nodes;
+    T sv[NP * 4];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) load4<T>(state, p * a.n + i, sv + 4 * p);
+    T y[NY], acc[1 + D];
+#pragma unroll
+    for (int q = 0; q < NY; ++q) y[q] = sv[q];
+#pragma unroll
+    for (int q = 0; q <= D; ++q) acc[q] = a.reset ? T(0) : sv[OA + q];
+
+    const T St0 = T(__ldg(&B->St0));
+    const T delta = T(a.delta);
+    const T h = T(a.dt);
+    const T half = T(0.5) * h;
+    const T sixth = h / T(6);
+    const T fN = T(a.N);
+    T u[D], G[D * D];
+    int integrated = 0;
+
+    for (int s = a.step0; s < a.step0 + a.nsteps; ++s) {
+        if (!active) {
+            if (s != ss) continue;
+            // release: v0 = u(x0); J = I, W = dv0/dx0 = grad u(x0) (initial data of Eq. 8)
+            interp<T, D>(nodes, a.N, fN, y, u, G);
+#pragma unroll
+            for (int q = 0; q < D; ++q) y[D + q] = u[q];
+            if (FLA) {
+#pragma unroll
+                for (int q = 0; q < D * D; ++q) {
+                    y[2 * D + q] = (q % (D + 1) == 0) ? T(1) : T(0);
+                    y[2 * D + D * D + q] = G[q];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q <= D; ++q) acc[q] = T(0);
+            active = true;
+            meta |= FLA_META_ACTIVE;
+        }
+        if (s >= sd) {   // evaporated (deadline decided on the host in double precision)
+            active = false;
+            meta = (meta & ~FLA_META_ACTIVE) | FLA_META_DEAD;
+            break;
+        }
+        ++integrated;
+        const T tau = T(s - ss) * h;                       // t - t0
+        const T r2a = T(1) + delta * tau;                  // (r/r0)^2, Eq. 4
+        const T r2b = T(1) + delta * (tau + half);
+        const T r2c = T(1) + delta * (tau + h);
+        const T iSa = T(1) / (St0 * r2a), iSb = T(1) / (St0 * r2b), iSc = T(1) / (St0 * r2c);
+
+        T k[NY], ks[NY], ys[NY];
+        // stage 1; the window sums use its u and v (left rectangle over substeps)
+        interp<T, D>(nodes, a.N, fN, y, u, G);
+        {
+            const T r = sqrt(r2a);
+            const T m = r2a * r;                 // m = r^3
+            const T mdot = T(1.5) * delta * r;   // dm/dt with r r' = delta/2
+            acc[0] = fma(h, mdot, acc[0]);
+#pragma unroll
+            for (int q = 0; q < D; ++q)
+                acc[1 + q] = fma(h, m * (u[q] - y[D + q]) * iSa + mdot * y[D + q], acc[1 + q]);
+        }
+        rhs<T, D, FLA>(y, u, G, iSa, k);
+#pragma unroll
+        for (int q = 0; q < NY; ++q) {
+            ks[q] = k[q];
+            ys[q] = fma(half, k[q], y[q]);
+        }
+        // stage 2
+        interp<T, D>(nodes, a.N, fN, ys, u, G);
+        rhs<T, D, FLA>(ys, u, G, iSb, k);
+#pragma unroll
+        for (int q = 0; q < NY; ++q) {
+            ks[q] = fma(T(2), k[q], ks[q]);
+            ys[q] = fma(half, k[q], y[q]);
+        }
+        // stage 3
+        interp<T, D>(nodes, a.N, fN, ys, u, G);
+        rhs<T, D, FLA>(ys, u, G, iSb, k);
+#pragma unroll
+        for (int q = 0; q < NY; ++q) {
+            ks[q] = fma(T(2), k[q], ks[q]);
+            ys[q] = fma(h, k[q], y[q]);
+        }
+        // stage 4
+        interp<T, D>(nodes, a.N, fN, ys, u, G);
+        rhs<T, D, FLA>(ys, u, G, iSc, k);
+#pragma unroll
+        for (int q = 0; q < NY; ++q) y[q] = fma(sixth, ks[q] + k[q], y[q]);
+        // outflow: leaving [0,1]^dim ends the trajectory
+        bool out = false;
+#pragma unroll
+        for (int q = 0; q < D; ++q) out |= !(y[q] >= T(0) && y[q] <= T(1));
+        if (out) {
+            active = false;
+            meta = (meta & ~FLA_META_ACTIVE) | FLA_META_DEAD;
+            break;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NY; ++q) sv[q] = y[q];
+#pragma unroll
+    for (int q = 0; q <= D; ++q) sv[OA + q] = acc[q];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) store4<T>(state, p * a.n + i, sv + 4 * p);
+    a.meta[i] = meta;
+    return integrated;
+}
+
+template <typename T, int D, bool FLA>
+__global__ void __launch_bounds__(128) k_advance(AdvArgs a)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int n = i < a.n ? advance_one<T, D, FLA>(a, i) : 0;
+    // integrated droplet steps: one atomic per block
+    __shared__ int s_sum[4];
+    const int w = __reduce_add_sync(0xffffffffu, n);
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const long long t = (long long)s_sum[0] + s_sum[1] + s_sum[2] + s_sum[3];
+        if (t) atomicAdd(&a.status->droplet_steps, (unsigned long long)t);
+    }
+}
+
+template <typename T, int D, bool FLA>
+cudaError_t launch_t(const AdvArgs& a, cudaStream_t s)
+{
+    const int threads = 128;
+    const unsigned blocks = (unsigned)((a.n + threads - 1) / threads);
+    k_advance<T, D, FLA><<<blocks, threads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_advance(const fla_cloud& cl, const fla_mesh& m, const void* nodes, int step0, int nsteps,
+                           double dt, bool reset, DevStatus* st, cudaStream_t s)
+{
+    AdvArgs a{};
+    a.status = st;
+    a.state = cl.state_dev;
+    a.meta = cl.meta_dev;
+    a.batches = cl.batches_dev;
+    a.nodes = nodes;
+    a.n = cl.n;
+    a.N = m.n;
+    a.step0 = step0;
+    a.nsteps = nsteps;
+    a.dt = dt;
+    a.delta = cl.delta;
+    a.reset = reset ? 1 : 0;
+    if (a.n == 0) return cudaSuccess;
+    const bool fla = cl.kind == FLA_CLOUD_FLA;
+    if (cl.dtype == FLA_F32) {
+        if (cl.dim == 2) return fla ? launch_t<float, 2, true>(a, s) : launch_t<float, 2, false>(a, s);
+        return fla ? launch_t<float, 3, true>(a, s) : launch_t<float, 3, false>(a, s);
+    }
+    if (cl.dim == 2) return fla ? launch_t<double, 2, true>(a, s) : launch_t<double, 2, false>(a, s);
+    return fla ? launch_t<double, 3, true>(a, s) : launch_t<double, 3, false>(a, s);
+}
+
+}  // namespace fla

@@ -1,0 +1,241 @@
+// Cell binning: integer cell keys, a stable LSD radix sort of (key, index)
+// and the per-cell bin starts.  All integer work: bit-exact and deterministic.
+//
+// The sort processes tiles of 4,096 keys (256 threads x 16).  Per pass of a
+// digit of up to 8 bits: (1) per-tile digit histograms, (2) per-digit
+// exclusive scans over tiles, (3) a stable scatter in which each warp ranks
+// its keys with __match_any_sync and per-warp running digit counters, so a
+// key's destination depends only on the input order.
+#include "fla_internal.cuh"
+
+namespace fla {
+namespace {
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+constexpr int RS_WARPS = RS_THREADS / 32;
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_cell_keys(const T* __restrict__ state, const uint32_t* __restrict__ meta,
+                                                   int64_t n, int N, uint32_t sentinel, uint32_t* __restrict__ keys)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T x[4];
+    load4<T>(state, i, x);   // plane 0 starts with the position
+    bool ok = (meta[i] & FLA_META_ACTIVE) != 0;
+    uint32_t key = 0, mul = 1;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        ok &= (x[a] >= T(0) && x[a] <= T(1));
+        const T s = x[a] * T(N);            // formed in the cloud's precision
+        int c = ok ? (int)floor(s) : 0;
+        c = c > N - 1 ? N - 1 : c;
+        key += (uint32_t)c * mul;
+        mul *= (uint32_t)N;
+    }
+    keys[i] = ok ? key : sentinel;
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                                                           int width, uint32_t* __restrict__ counts, int tiles)
+{
+    __shared__ uint32_t h[256];
+    const int nd = 1 << width;
+    for (int t = threadIdx.x; t < 256; t += RS_THREADS) h[t] = 0;
+    __syncthreads();
+    const int64_t base = blockIdx.x * (int64_t)RS_TILE;
+    const int lane = threadIdx.x & 31;
+#pragma unroll 4
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        const int64_t j = base + k * RS_THREADS + threadIdx.x;
+        const bool valid = j < n;
+        const uint32_t dg = valid ? (keys[j] >> shift) & (uint32_t)(nd - 1) : 0x100u;
+        const unsigned peers = __match_any_sync(0xffffffffu, dg);
+        if (valid && (__ffs(peers) - 1) == lane) atomicAdd(&h[dg], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < nd; d += RS_THREADS) counts[(int64_t)d * tiles + blockIdx.x] = h[d];
+}
+
+// Block-wide exclusive scan of one value per thread (256 threads).
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s_warp, uint32_t& total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t = lane < RS_WARPS ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < RS_WARPS) s_warp[lane] = t;
+    }
+    __syncthreads();
+    total = s_warp[RS_WARPS - 1];
+    const uint32_t before = w > 0 ? s_warp[w - 1] : 0;
+    __syncthreads();
+    return before + x - v;
+}
+
+// One block per digit: exclusive scan of the digit's per-tile counts, and the digit total.
+__global__ void __launch_bounds__(RS_THREADS) k_radix_scan(uint32_t* __restrict__ counts, int tiles,
+                                                           uint32_t* __restrict__ totals)
+{
+    __shared__ uint32_t s_warp[RS_WARPS];
+    uint32_t* row = counts + (int64_t)blockIdx.x * tiles;
+    uint32_t running = 0;
+    for (int base = 0; base < tiles; base += RS_THREADS) {
+        const int t = base + threadIdx.x;
+        const uint32_t v = t < tiles ? row[t] : 0;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(v, s_warp, tot);
+        if (t < tiles) row[t] = running + ex;
+        running += tot;
+    }
+    if (threadIdx.x == 0) totals[blockIdx.x] = running;
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint32_t* __restrict__ kin,
+                                                              const uint32_t* __restrict__ vin,
+                                                              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                              int64_t n, int shift, int width,
+                                                              const uint32_t* __restrict__ counts,
+                                                              const uint32_t* __restrict__ totals, int tiles)
+{
+    __shared__ uint32_t s_base[256];
+    __shared__ uint32_t s_cnt[RS_WARPS][256];
+    __shared__ uint32_t s_warp[RS_WARPS];
+    const int nd = 1 << width;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    {
+        const uint32_t t = tid < nd ? totals[tid] : 0;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(t, s_warp, tot);
+        s_base[tid] = ex + (tid < nd ? counts[(int64_t)tid * tiles + blockIdx.x] : 0);
+    }
+    for (int q = tid; q < RS_WARPS * 256; q += RS_THREADS) (&s_cnt[0][0])[q] = 0;
+    __syncthreads();
+
+    const int64_t wbase = blockIdx.x * (int64_t)RS_TILE + w * (RS_ITEMS * 32);
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t key[RS_ITEMS], val[RS_ITEMS], rank[RS_ITEMS];
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        const int64_t j = wbase + k * 32 + lane;
+        const bool valid = j < n;
+        const uint32_t kk = valid ? kin[j] : 0u;
+        const uint32_t vv = valid ? (vin ? vin[j] : (uint32_t)j) : 0u;
+        const uint32_t dg = valid ? (kk >> shift) & (uint32_t)(nd - 1) : 0x100u;
+        const unsigned peers = __match_any_sync(0xffffffffu, dg);
+        const uint32_t before = valid ? s_cnt[w][dg] : 0u;
+        __syncwarp();
+        if (valid && (peers & lt) == 0) s_cnt[w][dg] = before + (uint32_t)__popc(peers);
+        __syncwarp();
+        key[k] = kk;
+        val[k] = vv;
+        rank[k] = valid ? before + (uint32_t)__popc(peers & lt) : 0xffffffffu;
+    }
+    __syncthreads();
+    if (tid < nd) {   // exclusive scan across warps, per digit (warp order = input order)
+        uint32_t run = 0;
+#pragma unroll
+        for (int ww = 0; ww < RS_WARPS; ++ww) {
+            const uint32_t c = s_cnt[ww][tid];
+            s_cnt[ww][tid] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        if (rank[k] == 0xffffffffu) continue;
+        const uint32_t dg = (key[k] >> shift) & (uint32_t)(nd - 1);
+        const uint32_t pos = s_base[dg] + s_cnt[w][dg] + rank[k];
+        kout[pos] = key[k];
+        vout[pos] = val[k];
+    }
+}
+
+// bin_start[c] = first sorted position whose key is >= c, for c in [0, n_cells].
+__global__ void __launch_bounds__(256) k_bin_start(const uint32_t* __restrict__ keys, int64_t n, int64_t n_cells,
+                                                   uint32_t* __restrict__ bin_start)
+{
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c > n_cells) return;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)__ldg(keys + mid) < c) lo = mid + 1;
+        else hi = mid;
+    }
+    bin_start[c] = (uint32_t)lo;
+}
+
+}  // namespace
+
+int sort_bits(uint32_t max_key)
+{
+    int b = 0;
+    while (b < 32 && (max_key >> b) != 0) ++b;
+    return b < 1 ? 1 : b;
+}
+
+int radix_tiles(int64_t n) { return (int)((n + RS_TILE - 1) / RS_TILE); }
+
+int sort_passes(int bits) { return (bits + 7) / 8; }
+
+cudaError_t launch_cell_keys(const fla_cloud& cl, const fla_mesh& m, uint32_t* keys, cudaStream_t s)
+{
+    if (cl.n == 0) return cudaSuccess;
+    const int64_t nc = m.dim == 2 ? (int64_t)m.n * m.n : (int64_t)m.n * m.n * m.n;
+    const unsigned blocks = (unsigned)((cl.n + 255) / 256);
+    if (cl.dtype == FLA_F32) {
+        if (m.dim == 2) k_cell_keys<float, 2><<<blocks, 256, 0, s>>>((const float*)cl.state_dev, cl.meta_dev, cl.n, m.n, (uint32_t)nc, keys);
+        else k_cell_keys<float, 3><<<blocks, 256, 0, s>>>((const float*)cl.state_dev, cl.meta_dev, cl.n, m.n, (uint32_t)nc, keys);
+    } else {
+        if (m.dim == 2) k_cell_keys<double, 2><<<blocks, 256, 0, s>>>((const double*)cl.state_dev, cl.meta_dev, cl.n, m.n, (uint32_t)nc, keys);
+        else k_cell_keys<double, 3><<<blocks, 256, 0, s>>>((const double*)cl.state_dev, cl.meta_dev, cl.n, m.n, (uint32_t)nc, keys);
+    }
+    return cudaGetLastError();
+}
+
+// Sorts keys[first] (values: the identity) into buffer first ^ (passes & 1).
+cudaError_t launch_radix_sort(SortWork w, int64_t n, int bits, int first, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const int passes = sort_passes(bits);
+    const int width = (bits + passes - 1) / passes;
+    const int tiles = radix_tiles(n);
+    int cur = first;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = p * width;
+        const int wp = (bits - shift) < width ? (bits - shift) : width;
+        const int nd = 1 << wp;
+        k_radix_hist<<<tiles, RS_THREADS, 0, s>>>(w.keys[cur], n, shift, wp, w.counts, tiles);
+        k_radix_scan<<<nd, RS_THREADS, 0, s>>>(w.counts, tiles, w.totals);
+        k_radix_scatter<<<tiles, RS_THREADS, 0, s>>>(w.keys[cur], p == 0 ? nullptr : w.vals[cur], w.keys[cur ^ 1],
+                                                     w.vals[cur ^ 1], n, shift, wp, w.counts, w.totals, tiles);
+        cur ^= 1;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_start(const uint32_t* keys_sorted, int64_t n, int64_t n_cells, uint32_t* bin_start,
+                             cudaStream_t s)
+{
+    const unsigned blocks = (unsigned)((n_cells + 1 + 255) / 256);
+    k_bin_start<<<blocks, 256, 0, s>>>(keys_sorted, n, n_cells, bin_start);
+    return cudaGetLastError();
+}
+
+}  // namespace fla

@@ -1,0 +1,207 @@
+// Analytic carrier velocity and gradient sampled on the mesh nodes.
+//
+// The paper's carrier is an incompressible Navier-Stokes solution (Eq. 1);
+// the droplet equations need u and grad u at the droplet position (Eqs. 3
+// and 8).  Here synthetic analytic carriers stand in for it: they are sampled
+// once per carrier step on the (n+1)^dim mesh nodes and the advance kernel
+// interpolates the node values, as a mesh-based solver would.
+#include "fla_internal.cuh"
+
+namespace fla {
+namespace {
+
+struct CarrierArgs {
+    int kind, dim, N, n_vortex;
+    double U[3], A[9], xref[3];
+    double vort[FLA_MAX_VORTICES][4];  // centre x at the sampling time (wrapped), yc, Gamma, rc
+    double jet_width, abc[3], jet_amp, jet_radius;
+};
+
+__device__ __forceinline__ float m_exp(float x) { return expf(x); }
+__device__ __forceinline__ double m_exp(double x) { return exp(x); }
+__device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double m_expm1(double x) { return expm1(x); }
+__device__ __forceinline__ float m_sinpi(float x) { return sinpif(x); }
+__device__ __forceinline__ double m_sinpi(double x) { return sinpi(x); }
+__device__ __forceinline__ float m_cospi(float x) { return cospif(x); }
+__device__ __forceinline__ double m_cospi(double x) { return cospi(x); }
+
+// Lamb-Oseen vortex, azimuthal speed Gam/(2 pi rho) (1 - exp(-rho^2/rc^2)),
+// written u = f(s) (-dy, dx) with s = rho^2.  f = (c/a) h(X), f' = (c/a^2) g(X),
+// X = s/a, a = rc^2, c = Gam/(2 pi); h(X) = (1 - e^-X)/X and
+// g(X) = (X e^-X - (1 - e^-X))/X^2 use their Taylor series near X = 0.
+template <typename T>
+__device__ __forceinline__ void lamb_oseen(T gam, T rc, T xc, T yc, T x, T y, T* u, T* G)
+{
+    const T dx = x - xc, dy = y - yc;
+    const T s = dx * dx + dy * dy;
+    const T a = rc * rc;
+    const T c = gam * T(0.15915494309189533577);  // 1/(2 pi)
+    const T X = s / a;
+    T h, g;
+    const T small = sizeof(T) == 4 ? T(1e-2) : T(1e-3);
+    if (X < small) {
+        h = T(1) + X * (T(-0.5) + X * (T(1.0 / 6.0) + X * T(-1.0 / 24.0)));
+        g = T(-0.5) + X * (T(1.0 / 3.0) + X * (T(-0.125) + X * T(1.0 / 30.0)));
+    } else {
+        const T em = m_expm1(-X);
+        h = -em / X;
+        g = (X * m_exp(-X) + em) / (X * X);
+    }
+    const T f = c / a * h;
+    const T fp = c / (a * a) * g;
+    u[0] -= dy * f;
+    u[1] += dx * f;
+    G[0] -= T(2) * fp * dx * dy;
+    G[1] -= f + T(2) * fp * dy * dy;
+    G[2] += f + T(2) * fp * dx * dx;
+    G[3] += T(2) * fp * dx * dy;
+}
+
+template <typename T, int D>
+__device__ void eval_carrier(const CarrierArgs& p, const T* x, T* u, T* G)
+{
+#pragma unroll
+    for (int i = 0; i < D; ++i) u[i] = T(0);
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) G[i] = T(0);
+    switch (p.kind) {
+    case FLA_CARRIER_UNIFORM:
+        for (int i = 0; i < D; ++i) u[i] = T(p.U[i]);
+        break;
+    case FLA_CARRIER_LINEAR:
+        for (int i = 0; i < D; ++i) {
+            T s = T(p.U[i]);
+            for (int j = 0; j < D; ++j) {
+                s += T(p.A[3 * i + j]) * (x[j] - T(p.xref[j]));
+                G[i * D + j] = T(p.A[3 * i + j]);
+            }
+            u[i] = s;
+        }
+        break;
+    case FLA_CARRIER_TG2:
+        if (D == 2) {
+            const T sx = m_sinpi(x[0]), cx = m_cospi(x[0]);
+            const T sy = m_sinpi(x[1]), cy = m_cospi(x[1]);
+            const T pi = T(3.14159265358979323846);
+            u[0] = sx * cy;
+            u[1] = -cx * sy;
+            G[0] = pi * cx * cy;
+            G[1] = -pi * sx * sy;
+            G[2] = pi * sx * sy;
+            G[3] = -pi * cx * cy;
+        }
+        break;
+    case FLA_CARRIER_JETVORT2:
+        if (D == 2) {
+            const T w = T(p.jet_width);
+            const T eta = (x[1] - T(0.5)) / w;
+            const T uj = m_exp(-eta * eta);
+            u[0] = uj;
+            G[1] = T(-2) * eta / w * uj;
+            for (int k = 0; k < p.n_vortex; ++k) {
+                const T xc = T(p.vort[k][0]), yc = T(p.vort[k][1]);
+                const T gam = T(p.vort[k][2]), rc = T(p.vort[k][3]);
+                for (int img = -1; img <= 1; ++img)   // periodic images along x
+                    lamb_oseen<T>(gam, rc, xc + T(img), yc, x[0], x[1], u, G);
+            }
+        }
+        break;
+    case FLA_CARRIER_ABCJET3:
+        if (D == 3) {
+            const T A = T(p.abc[0]), B = T(p.abc[1]), C = T(p.abc[2]);
+            const T k = T(6.28318530717958647692);
+            const T sxv = m_sinpi(T(2) * x[0]), cxv = m_cospi(T(2) * x[0]);
+            const T syv = m_sinpi(T(2) * x[1]), cyv = m_cospi(T(2) * x[1]);
+            const T szv = m_sinpi(T(2) * x[2]), czv = m_cospi(T(2) * x[2]);
+            u[0] = A * szv + C * cyv;
+            u[1] = B * sxv + A * czv;
+            u[2] = C * syv + B * cxv;
+            G[1] = -k * C * syv;
+            G[2] = k * A * czv;
+            G[3] = k * B * cxv;
+            G[5] = -k * A * szv;
+            G[6] = -k * B * sxv;
+            G[7] = k * C * cyv;
+            const T rx = x[0] - T(0.5), ry = x[1] - T(0.5);
+            const T r2j = T(p.jet_radius) * T(p.jet_radius);
+            const T e = T(p.jet_amp) * m_exp(-(rx * rx + ry * ry) / r2j);
+            u[2] += e;
+            G[6] += T(-2) * rx / r2j * e;
+            G[7] += T(-2) * ry / r2j * e;
+        }
+        break;
+    default:
+        break;
+    }
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_carrier_sample(CarrierArgs p, T* __restrict__ nodes, int64_t total)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= total) return;
+    const int nn = p.N + 1;
+    T x[3];
+    int64_t r = k;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        x[a] = T(double(r % nn) / double(p.N));
+        r /= nn;
+    }
+    T u[3], G[9];
+    eval_carrier<T, D>(p, x, u, G);
+    constexpr int S = node_stride(D);
+    T out[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) out[q] = T(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) out[a] = u[a];
+#pragma unroll
+    for (int q = 0; q < D * D; ++q) out[D + q] = G[q];
+#pragma unroll
+    for (int v = 0; v < S / 4; ++v) store4<T>(nodes, k * (S / 4) + v, out + 4 * v);
+}
+
+}  // namespace
+
+cudaError_t launch_carrier_sample(const fla_carrier_desc& c, const fla_mesh& m, double t, int dtype, void* nodes,
+                                  cudaStream_t s)
+{
+    CarrierArgs p{};
+    p.kind = c.kind;
+    p.dim = c.dim;
+    p.N = m.n;
+    p.n_vortex = c.n_vortex;
+    for (int i = 0; i < 3; ++i) {
+        p.U[i] = c.U[i];
+        p.xref[i] = c.xref[i];
+        p.abc[i] = c.abc[i];
+    }
+    for (int i = 0; i < 9; ++i) p.A[i] = c.A[i];
+    for (int k = 0; k < c.n_vortex; ++k) {
+        double xc = c.vortex[k][0] + c.vortex[k][4] * t;   // carried with the jet
+        xc -= floor(xc);                                   // wrapped into [0, 1)
+        p.vort[k][0] = xc;
+        p.vort[k][1] = c.vortex[k][1];
+        p.vort[k][2] = c.vortex[k][2];
+        p.vort[k][3] = c.vortex[k][3];
+    }
+    p.jet_width = c.jet_width;
+    p.jet_amp = c.jet_amp;
+    p.jet_radius = c.jet_radius;
+    const int64_t nn = m.n + 1;
+    const int64_t total = m.dim == 2 ? nn * nn : nn * nn * nn;
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((total + threads - 1) / threads);
+    if (dtype == FLA_F32) {
+        if (m.dim == 2) k_carrier_sample<float, 2><<<blocks, threads, 0, s>>>(p, (float*)nodes, total);
+        else k_carrier_sample<float, 3><<<blocks, threads, 0, s>>>(p, (float*)nodes, total);
+    } else {
+        if (m.dim == 2) k_carrier_sample<double, 2><<<blocks, threads, 0, s>>>(p, (double*)nodes, total);
+        else k_carrier_sample<double, 3><<<blocks, threads, 0, s>>>(p, (double*)nodes, total);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace fla

@@ -1,0 +1,440 @@
+// Kernel-regression gather (Eqs. 13 and 16) and PSI-CELL box counting (Eqs. 10-11).
+//
+// Gather: one CTA per tile of cells (16x16 in 2D, 8x8x4 in 3D), one cell per
+// thread.  Droplet records are sorted by cell key, so the records of the
+// cells in one mesh row of the tile's neighbourhood are contiguous.  The CTA
+// walks those rows, each thread loads one record, records whose support cannot
+// reach the tile are culled, and the survivors are compacted (order kept)
+// into shared memory.  Every cell then evaluates the staged records in the
+// same order: truncation test, Gaussian weight with a single MUFU ex2 in
+// single precision, and FMA accumulation.  Each staged chunk is summed
+// plainly and chunk sums are added with Neumaier compensation.  No atomics
+// touch the outputs, so results are deterministic.
+#include "fla_internal.cuh"
+
+namespace fla {
+namespace {
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Neumaier-compensated add of a chunk sum v into (s, c).
+template <typename T>
+__device__ __forceinline__ void neumaier(T& s, T& c, T v)
+{
+    const T t = s + v;
+    if (fabs(s) >= fabs(v)) c += (s - t) + v;
+    else c += (v - t) + s;
+    s = t;
+}
+
+struct GatherArgs {
+    const void* rec;
+    const uint32_t* bin_start;
+    const unsigned int* ext_max;
+    int N;
+    int per_cell;
+    void* s_mass;
+    void* s_mom;
+    void* dsum;
+    DevStatus* status;
+};
+
+template <int D> struct Tile;
+template <> struct Tile<2> { static constexpr int X = 16, Y = 16, Z = 1; };
+template <> struct Tile<3> { static constexpr int X = 8, Y = 8, Z = 4; };
+
+constexpr int GT = 256;            // threads per CTA = cells per tile
+constexpr int CAP = 2 * GT;        // staged records
+
+template <typename T, int D, int KER>
+__global__ void __launch_bounds__(GT) k_nw_gather(GatherArgs a)
+{
+    constexpr int RV = record_values(D, KER);
+    constexpr int R4 = RV / 4;
+    constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* srec = reinterpret_cast<T*>(smem_raw);
+    __shared__ int s_wcount[GT / 32];
+    __shared__ int s_count;
+
+    const int N = a.N;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int t0[3] = {(int)blockIdx.x * TX, (int)blockIdx.y * TY, (int)blockIdx.z * TZ};
+    const int cc[3] = {t0[0] + tid % TX, t0[1] + (tid / TX) % TY, t0[2] + tid / (TX * TY)};
+    bool in_mesh = cc[0] < N && cc[1] < N;
+    if (D == 3) in_mesh = in_mesh && cc[2] < N;
+    T xc[3];
+    float xcf[3];
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+        const double v = ((double)cc[q] + 0.5) / (double)N;
+        xc[q] = T(v);
+        xcf[q] = (float)v;
+    }
+    // bounding box of the tile's cell centres (for culling)
+    T lo[3], hi[3];
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+        const int tq = q == 0 ? TX : (q == 1 ? TY : TZ);
+        const int last = (t0[q] + tq < N ? t0[q] + tq : N) - 1;
+        lo[q] = T(((double)t0[q] + 0.5) / (double)N);
+        hi[q] = T(((double)last + 0.5) / (double)N);
+    }
+    const float ext2max = __uint_as_float(__ldg(a.ext_max));
+    const int R = (int)floorf(sqrtf(ext2max) * (float)N + 0.5f) + 1;
+
+    T sD = T(0), cD = T(0);
+    T sN[4] = {T(0), T(0), T(0), T(0)}, cN[4] = {T(0), T(0), T(0), T(0)};
+    int npairs = 0;
+    if (tid == 0) s_count = 0;
+
+    const int xlo = t0[0] - R < 0 ? 0 : t0[0] - R;
+    const int xhi = t0[0] + TX - 1 + R > N - 1 ? N - 1 : t0[0] + TX - 1 + R;
+    const int ylo = t0[1] - R < 0 ? 0 : t0[1] - R;
+    const int yhi = t0[1] + TY - 1 + R > N - 1 ? N - 1 : t0[1] + TY - 1 + R;
+    int zlo = 0, zhi = 0;
+    if (D == 3) {
+        zlo = t0[2] - R < 0 ? 0 : t0[2] - R;
+        zhi = t0[2] + TZ - 1 + R > N - 1 ? N - 1 : t0[2] + TZ - 1 + R;
+    }
+    __syncthreads();
+
+    auto flush = [&](int count) {
+        T pD = T(0), pN[4] = {T(0), T(0), T(0), T(0)};
+        for (int k = 0; k < count; ++k) {
+            const T* r = srec + k * RV;
+            T w;
+            bool inside;
+            if (KER == FLA_KERNEL_ISO) {
+                if (sizeof(T) == 4) {
+                    // single-precision decision in a fixed operation order
+                    float dx = __fsub_rn(xcf[0], (float)r[0]);
+                    float dy = __fsub_rn(xcf[1], (float)r[1]);
+                    float r2 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
+                    float r2max, c, ih;
+                    if (D == 3) {
+                        const float dz = __fsub_rn(xcf[2], (float)r[2]);
+                        r2 = __fmaf_rn(dz, dz, r2);
+                        r2max = (float)r[3]; c = (float)r[4]; ih = (float)r[5];
+                    } else {
+                        r2max = (float)r[7]; c = (float)r[2]; ih = (float)r[3];
+                    }
+                    inside = r2 <= r2max;
+                    w = T(ih * ex2_approx(r2 * c));
+                } else {
+                    const T dx = xc[0] - r[0], dy = xc[1] - r[1];
+                    T r2 = dx * dx + dy * dy;
+                    T c, ih;
+                    if (D == 3) {
+                        const T dz = xc[2] - r[2];
+                        r2 += dz * dz;
+                        c = r[4]; ih = r[5];
+                    } else {
+                        c = r[2]; ih = r[3];
+                    }
+                    const T e = r2 * c;        // = -q/2
+                    inside = e >= T(-4.5);
+                    w = ih * exp(e);
+                }
+            } else {
+                T P[9];
+                T pref;
+                if (D == 2) {
+                    P[0] = r[4]; P[1] = r[5]; P[2] = r[5]; P[3] = r[6];
+                    pref = r[2];
+                } else {
+                    P[0] = r[4]; P[1] = r[5]; P[2] = r[6];
+                    P[3] = r[5]; P[4] = r[7]; P[5] = r[8];
+                    P[6] = r[6]; P[7] = r[8]; P[8] = r[9];
+                    pref = r[3];
+                }
+                T q;
+                if (sizeof(T) == 4) {
+                    float df[3], pd[3];
+#pragma unroll
+                    for (int i = 0; i < D; ++i) df[i] = __fsub_rn(xcf[i], (float)r[i]);
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        float s = __fmul_rn((float)P[i * D], df[0]);
+#pragma unroll
+                        for (int k2 = 1; k2 < D; ++k2) s = __fmaf_rn((float)P[i * D + k2], df[k2], s);
+                        pd[i] = s;
+                    }
+                    float qf = __fmul_rn(pd[0], df[0]);
+#pragma unroll
+                    for (int i = 1; i < D; ++i) qf = __fmaf_rn(pd[i], df[i], qf);
+                    inside = qf <= 9.0f;
+                    w = T((float)pref * ex2_approx(qf * -0.72134752044448170368f));
+                    q = T(qf);
+                } else {
+                    T df[3];
+#pragma unroll
+                    for (int i = 0; i < D; ++i) df[i] = xc[i] - r[i];
+                    q = T(0);
+#pragma unroll
+                    for (int i = 0; i < D; ++i)
+#pragma unroll
+                        for (int k2 = 0; k2 < D; ++k2) q += df[i] * P[i * D + k2] * df[k2];
+                    inside = q <= T(9);
+                    w = pref * exp(T(-0.5) * q);
+                }
+                (void)q;
+            }
+            if (inside) {
+                const T* am = r + (RV - 4);
+                ++npairs;
+                pD += w;
+#pragma unroll
+                for (int q2 = 0; q2 <= D; ++q2) pN[q2] = fma(w, am[q2], pN[q2]);
+            }
+        }
+        neumaier(sD, cD, pD);
+#pragma unroll
+        for (int q2 = 0; q2 <= D; ++q2) neumaier(sN[q2], cN[q2], pN[q2]);
+    };
+
+    // walk the neighbourhood rows; each row's records are contiguous
+    for (int z = zlo; z <= zhi; ++z) {
+        for (int y = ylo; y <= yhi; ++y) {
+            const int64_t rowbase = ((int64_t)z * N + y) * N;
+            const uint32_t beg = __ldg(a.bin_start + rowbase + xlo);
+            const uint32_t end = __ldg(a.bin_start + rowbase + xhi + 1);
+            for (uint32_t j0 = beg; j0 < end; j0 += GT) {
+                const uint32_t j = j0 + tid;
+                T rv[16];
+                bool keep = false;
+                if (j < end) {
+#pragma unroll
+                    for (int v = 0; v < R4; ++v) load4<T>((const T*)a.rec, (int64_t)j * R4 + v, rv + 4 * v);
+                    T e2;
+                    if (KER == FLA_KERNEL_ISO) e2 = D == 2 ? rv[7] : rv[3];
+                    else e2 = D == 2 ? rv[3] : rv[10];
+                    T d2 = T(0);
+#pragma unroll
+                    for (int q = 0; q < D; ++q) {
+                        const T dl = lo[q] - rv[q], dh = rv[q] - hi[q];
+                        const T dd = dl > T(0) ? dl : (dh > T(0) ? dh : T(0));
+                        d2 += dd * dd;
+                    }
+                    keep = d2 <= e2 * T(1.0009765625);   // small margin over rounding of the test
+                }
+                const unsigned ballot = __ballot_sync(0xffffffffu, keep);
+                if (lane == 0) s_wcount[warp] = __popc(ballot);
+                __syncthreads();
+                int off = s_count;
+                for (int w2 = 0; w2 < warp; ++w2) off += s_wcount[w2];
+                int total = s_count;
+                for (int w2 = 0; w2 < GT / 32; ++w2) total += s_wcount[w2];
+                if (keep) {
+                    const int pos = off + __popc(ballot & ((1u << lane) - 1u));
+#pragma unroll
+                    for (int v = 0; v < RV; ++v) srec[pos * RV + v] = rv[v];
+                }
+                __syncthreads();
+                if (total > CAP - GT) {
+                    flush(total);
+                    total = 0;
+                }
+                __syncthreads();
+                if (tid == 0) s_count = total;
+                __syncthreads();
+            }
+        }
+    }
+    const int rem = s_count;
+    if (rem > 0) flush(rem);
+
+    // pairs inside the truncation (cells of the mesh only): one atomic per CTA
+    {
+        const int w = __reduce_add_sync(0xffffffffu, in_mesh ? npairs : 0);
+        __syncthreads();
+        if (lane == 0) s_wcount[warp] = w;
+        __syncthreads();
+        if (tid == 0) {
+            long long t = 0;
+            for (int q = 0; q < GT / 32; ++q) t += s_wcount[q];
+            if (t) atomicAdd(&a.status->pairs, (unsigned long long)t);
+        }
+    }
+
+    if (in_mesh) {
+        const int64_t cell = cc[0] + (int64_t)N * (cc[1] + (D == 3 ? (int64_t)N * cc[2] : 0));
+        const int64_t nc = D == 2 ? (int64_t)N * N : (int64_t)N * N * N;
+        const T Dt = sD + cD;
+        T scale = T(1);
+        if (a.per_cell) {
+            const double dx = 1.0 / N;
+            scale = T(D == 2 ? dx * dx : dx * dx * dx);
+        }
+        const bool cov = Dt > T(0);
+        ((T*)a.s_mass)[cell] = cov ? -(sN[0] + cN[0]) / Dt * scale : T(0);
+#pragma unroll
+        for (int q = 0; q < D; ++q) ((T*)a.s_mom)[q * nc + cell] = cov ? -(sN[1 + q] + cN[1 + q]) / Dt * scale : T(0);
+        if (a.dsum) ((T*)a.dsum)[cell] = Dt;
+    }
+}
+
+template <typename T, int D, int KER>
+cudaError_t launch_gather_t(const GatherArgs& a, cudaStream_t s)
+{
+    constexpr int RV = record_values(D, KER);
+    const size_t smem = (size_t)CAP * RV * sizeof(T);
+    auto fn = k_nw_gather<T, D, KER>;
+    static bool attr_set = false;   // set once, before any stream capture that uses it
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int N = a.N;
+    dim3 grid((N + Tile<D>::X - 1) / Tile<D>::X, (N + Tile<D>::Y - 1) / Tile<D>::Y,
+              D == 3 ? (N + Tile<D>::Z - 1) / Tile<D>::Z : 1);
+    fn<<<grid, GT, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- PSI-CELL
+
+struct PsiArgs {
+    const void* state;
+    const uint32_t* meta;
+    const fla_batch* batches;
+    const uint32_t* perm;
+    const uint32_t* bin_start;
+    int64_t n, n_cells;
+    double inv_window;
+    void* rec;
+    DevStatus* status;
+};
+
+// Gather w * acc / T_window of each binned parcel into sorted order (4 values).
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_psi_records(PsiArgs a)
+{
+    constexpr int OA = acc_offset(FLA_CLOUD_LPT, D);
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nvalid = a.bin_start[a.n_cells];
+    if (j >= nvalid) return;
+    const uint32_t i = a.perm[j];
+    const double w = __ldg(&a.batches[a.meta[i] & FLA_META_BATCH_MASK].n0);
+    T v0[4], v1[4], out[4];
+    load4<T>((const T*)a.state, (OA / 4) * a.n + i, v0);
+    if (OA % 4 + D + 1 > 4) load4<T>((const T*)a.state, (OA / 4 + 1) * a.n + i, v1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[q] = T(0);
+#pragma unroll
+    for (int q = 0; q <= D; ++q) {
+        const int o = OA % 4 + q;
+        const T v = o < 4 ? v0[o] : v1[o - 4];
+        out[q] = T(w * (double)v * a.inv_window);
+    }
+    store4<T>((T*)a.rec, j, out);
+}
+
+// One warp per cell: fixed lane assignment and a butterfly reduction.
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_psi_cells(const T* __restrict__ rec, const uint32_t* __restrict__ bin_start,
+                                                   int64_t n_cells, T scale, uint32_t* __restrict__ counts,
+                                                   T* __restrict__ s_mass, T* __restrict__ s_mom)
+{
+    const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= n_cells) return;
+    const uint32_t beg = bin_start[c], end = bin_start[c + 1];
+    T s[4] = {T(0), T(0), T(0), T(0)};
+    for (uint32_t j = beg + lane; j < end; j += 32) {
+        T v[4];
+        load4<T>(rec, j, v);
+#pragma unroll
+        for (int q = 0; q <= D; ++q) s[q] += v[q];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q <= D; ++q) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
+    if (lane == 0) {
+        counts[c] = end - beg;
+        s_mass[c] = -scale * s[0];
+#pragma unroll
+        for (int q = 0; q < D; ++q) s_mom[q * n_cells + c] = -scale * s[1 + q];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_nw_gather(const fla_cloud& cl, const fla_mesh& m, const fla_deposit_cfg& cfg, const void* rec,
+                             const uint32_t* bin_start, const unsigned int* ext_max, const fla_sources& out,
+                             DevStatus* st, cudaStream_t s)
+{
+    GatherArgs a{};
+    a.status = st;
+    a.rec = rec;
+    a.bin_start = bin_start;
+    a.ext_max = ext_max;
+    a.N = m.n;
+    a.per_cell = cfg.per_cell;
+    a.s_mass = out.s_mass_dev;
+    a.s_mom = out.s_mom_dev;
+    a.dsum = out.dsum_dev;
+    const bool iso = cfg.kernel == FLA_KERNEL_ISO;
+    if (cl.dtype == FLA_F32) {
+        if (m.dim == 2) return iso ? launch_gather_t<float, 2, 0>(a, s) : launch_gather_t<float, 2, 1>(a, s);
+        return iso ? launch_gather_t<float, 3, 0>(a, s) : launch_gather_t<float, 3, 1>(a, s);
+    }
+    if (m.dim == 2) return iso ? launch_gather_t<double, 2, 0>(a, s) : launch_gather_t<double, 2, 1>(a, s);
+    return iso ? launch_gather_t<double, 3, 0>(a, s) : launch_gather_t<double, 3, 1>(a, s);
+}
+
+cudaError_t launch_psicell(const fla_cloud& cl, const fla_mesh& m, double window_dt, int per_cell,
+                           const uint32_t* perm, const uint32_t* bin_start, void* rec, const fla_psicell_out& out,
+                           DevStatus* st, cudaStream_t s)
+{
+    const int64_t nc = m.dim == 2 ? (int64_t)m.n * m.n : (int64_t)m.n * m.n * m.n;
+    PsiArgs a{};
+    a.state = cl.state_dev;
+    a.meta = cl.meta_dev;
+    a.batches = cl.batches_dev;
+    a.perm = perm;
+    a.bin_start = bin_start;
+    a.n = cl.n;
+    a.n_cells = nc;
+    a.inv_window = 1.0 / window_dt;
+    a.rec = rec;
+    a.status = st;
+    const double dx = 1.0 / m.n;
+    const double V = m.dim == 2 ? dx * dx : dx * dx * dx;
+    const double scale = per_cell ? 1.0 : 1.0 / V;
+    const unsigned rb = (unsigned)((cl.n + 255) / 256);
+    const unsigned cb = (unsigned)((nc * 32 + 255) / 256);
+    if (cl.dtype == FLA_F32) {
+        if (cl.n > 0) {
+            if (m.dim == 2) k_psi_records<float, 2><<<rb, 256, 0, s>>>(a);
+            else k_psi_records<float, 3><<<rb, 256, 0, s>>>(a);
+        }
+        if (m.dim == 2)
+            k_psi_cells<float, 2><<<cb, 256, 0, s>>>((const float*)rec, bin_start, nc, (float)scale, out.counts_dev,
+                                                     (float*)out.s_mass_dev, (float*)out.s_mom_dev);
+        else
+            k_psi_cells<float, 3><<<cb, 256, 0, s>>>((const float*)rec, bin_start, nc, (float)scale, out.counts_dev,
+                                                     (float*)out.s_mass_dev, (float*)out.s_mom_dev);
+    } else {
+        if (cl.n > 0) {
+            if (m.dim == 2) k_psi_records<double, 2><<<rb, 256, 0, s>>>(a);
+            else k_psi_records<double, 3><<<rb, 256, 0, s>>>(a);
+        }
+        if (m.dim == 2)
+            k_psi_cells<double, 2><<<cb, 256, 0, s>>>((const double*)rec, bin_start, nc, scale, out.counts_dev,
+                                                      (double*)out.s_mass_dev, (double*)out.s_mom_dev);
+        else
+            k_psi_cells<double, 3><<<cb, 256, 0, s>>>((const double*)rec, bin_start, nc, scale, out.counts_dev,
+                                                      (double*)out.s_mass_dev, (double*)out.s_mom_dev);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace fla

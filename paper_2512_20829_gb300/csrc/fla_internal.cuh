@@ -1,0 +1,130 @@
+// Internal declarations shared by the translation units of libfla.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/fla.h"
+
+struct fla_ctx {
+    int device;
+    int num_sms;
+    fla_device_status* status_dev;   // 64-byte block, zeroed at creation
+    // profiling: launch/call counters (always) and CUDA-event phase timing (optional)
+    int timing;
+    double ms[FLA_PHASE_COUNT];
+    long long launches[FLA_PHASE_COUNT];
+    long long calls[FLA_PHASE_COUNT];
+    struct Pending {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+};
+
+namespace fla {
+
+constexpr int kMaxPlanes = 7;
+
+// vec4 of the storage type: float4 or a 32-byte pair of double2.
+template <typename T> struct V4;
+template <> struct V4<float> {
+    float4 v;
+};
+template <> struct V4<double> {
+    double2 a, b;
+};
+
+template <typename T>
+__device__ __forceinline__ void load4(const T* base, int64_t idx4, T out[4]);
+template <>
+__device__ __forceinline__ void load4<float>(const float* base, int64_t idx4, float out[4])
+{
+    float4 v = __ldg(reinterpret_cast<const float4*>(base) + idx4);
+    out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void load4<double>(const double* base, int64_t idx4, double out[4])
+{
+    const double2* p = reinterpret_cast<const double2*>(base) + 2 * idx4;
+    double2 a = __ldg(p), b = __ldg(p + 1);
+    out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+}
+template <typename T>
+__device__ __forceinline__ void store4(T* base, int64_t idx4, const T in[4]);
+template <>
+__device__ __forceinline__ void store4<float>(float* base, int64_t idx4, const float in[4])
+{
+    reinterpret_cast<float4*>(base)[idx4] = make_float4(in[0], in[1], in[2], in[3]);
+}
+template <>
+__device__ __forceinline__ void store4<double>(double* base, int64_t idx4, const double in[4])
+{
+    double2* p = reinterpret_cast<double2*>(base) + 2 * idx4;
+    p[0] = make_double2(in[0], in[1]);
+    p[1] = make_double2(in[2], in[3]);
+}
+
+// Values per droplet (before padding) and planes of 4.
+__host__ __device__ constexpr int state_values(int kind, int dim)
+{
+    return kind == FLA_CLOUD_FLA ? 2 * dim + 2 * dim * dim + 1 + dim : 2 * dim + 1 + dim;
+}
+__host__ __device__ constexpr int state_planes(int kind, int dim) { return (state_values(kind, dim) + 3) / 4; }
+__host__ __device__ constexpr int acc_offset(int kind, int dim)
+{
+    return kind == FLA_CLOUD_FLA ? 2 * dim + 2 * dim * dim : 2 * dim;
+}
+__host__ __device__ constexpr int node_stride(int dim) { return dim == 2 ? 8 : 12; }
+
+// Record of one binned droplet for the kernel-regression gather, in sorted order.
+//   2D iso   (8 values):  x, y, c, inv_h | a_m, a_x, a_y, r2max
+//   3D iso   (12 values): x, y, z, r2max | c, inv_h, 0, 0 | a_m, a_x, a_y, a_z
+//   2D aniso (12 values): x, y, pref, ext2 | P00, P01, P11, 0 | a_m, a_x, a_y, 0
+//   3D aniso (16 values): x, y, z, pref | P00, P01, P02, P11 | P12, P22, ext2, 0 | a_m, a_x, a_y, a_z
+// c = -log2(e)/(2 h^2) in single precision (the weight is inv_h * 2^(c r^2)),
+// c = -1/(2 h^2) in double precision; ext2 = 9 tr(Sigma) bounds the squared
+// support radius; r2max = 9 h^2 rounded to the storage type.
+__host__ __device__ constexpr int record_values(int dim, int kernel)
+{
+    return (dim == 2 && kernel == FLA_KERNEL_ISO) ? 8 : ((dim == 3 && kernel == FLA_KERNEL_ANISO) ? 16 : 12);
+}
+
+// Device status block layout (matches fla_device_status).
+struct DevStatus {
+    unsigned long long nonfinite, deposited, droplet_steps, pairs;
+    unsigned int flags, pad;
+};
+
+struct SortWork {
+    uint32_t* keys[2];
+    uint32_t* vals[2];
+    uint32_t* counts;     // 256 * tiles
+    uint32_t* totals;     // 256
+};
+
+// ---------------------------------------------------------------- launches
+cudaError_t launch_carrier_sample(const fla_carrier_desc& c, const fla_mesh& m, double t, int dtype, void* nodes,
+                                  cudaStream_t s);
+cudaError_t launch_advance(const fla_cloud& cl, const fla_mesh& m, const void* nodes, int step0, int nsteps,
+                           double dt, bool reset, DevStatus* st, cudaStream_t s);
+int sort_passes(int bits);
+cudaError_t launch_cell_keys(const fla_cloud& cl, const fla_mesh& m, uint32_t* keys, cudaStream_t s);
+int sort_bits(uint32_t max_key);
+int radix_tiles(int64_t n);
+cudaError_t launch_radix_sort(SortWork w, int64_t n, int bits, int first_buf, cudaStream_t s);
+cudaError_t launch_bin_start(const uint32_t* keys_sorted, int64_t n, int64_t n_cells, uint32_t* bin_start,
+                             cudaStream_t s);
+cudaError_t launch_records(const fla_cloud& cl, const fla_mesh& m, const fla_deposit_cfg& cfg,
+                           const uint32_t* perm, const uint32_t* bin_start, int64_t n_cells, void* rec,
+                           unsigned int* ext_max, DevStatus* st, cudaStream_t s);
+cudaError_t launch_nw_gather(const fla_cloud& cl, const fla_mesh& m, const fla_deposit_cfg& cfg, const void* rec,
+                             const uint32_t* bin_start, const unsigned int* ext_max, const fla_sources& out,
+                             DevStatus* st, cudaStream_t s);
+cudaError_t launch_psicell(const fla_cloud& cl, const fla_mesh& m, double window_dt, int per_cell,
+                           const uint32_t* perm, const uint32_t* bin_start, void* rec, const fla_psicell_out& out,
+                           DevStatus* st, cudaStream_t s);
+
+}  // namespace fla

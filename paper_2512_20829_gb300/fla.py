@@ -1,0 +1,477 @@
+"""Thin Python binding of libfla (``include/fla.h``).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  PyTorch supplies device memory and streams; NumPy packs host
+arrays into the library's plane layout.  The binding refuses to work without
+the compiled library: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import inputs as I
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfla.so")
+
+F32, F64 = 0, 1
+CLOUD_FLA, CLOUD_LPT = 0, 1
+KERNEL_ISO, KERNEL_ANISO = 0, 1
+META_BATCH_MASK = 0x00FFFFFF
+META_DEAD = 0x40000000
+META_ACTIVE = 0x80000000
+ADVANCE_RESET_ACC = 1
+MAX_VORTICES = 16
+
+EXPORTED = ["fla_abi_version", "fla_status_string", "fla_create", "fla_destroy", "fla_state_layout",
+            "fla_carrier_nodes_bytes", "fla_carrier_sample", "fla_batch_deadline", "fla_advance",
+            "fla_workspace_size", "fla_cell_bins", "fla_deposit_sources", "psicell_deposit", "fla_sync_status",
+            "fla_profile_enable", "fla_profile_read", "fla_phase_name"]
+PHASES = ["carrier", "advance", "keys", "sort", "bins", "records", "gather", "psicell"]
+
+
+class FlaError(RuntimeError):
+    pass
+
+
+class Mesh(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n", C.c_int32)]
+
+
+class CarrierDesc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("dim", C.c_int32), ("U", C.c_double * 3), ("A", C.c_double * 9),
+                ("xref", C.c_double * 3), ("n_vortex", C.c_int32), ("vortex", (C.c_double * 5) * MAX_VORTICES),
+                ("jet_width", C.c_double), ("abc", C.c_double * 3), ("jet_amp", C.c_double),
+                ("jet_radius", C.c_double)]
+
+
+class Cloud(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("dim", C.c_int32), ("dtype", C.c_int32), ("n_batches", C.c_int32),
+                ("n", C.c_int64), ("state_dev", C.c_void_p), ("meta_dev", C.c_void_p),
+                ("batches_dev", C.c_void_p), ("delta", C.c_double)]
+
+
+class DepositCfg(C.Structure):
+    _fields_ = [("kernel", C.c_int32), ("per_cell", C.c_int32), ("h_min", C.c_double), ("h_max", C.c_double),
+                ("p", C.c_double), ("window_dt", C.c_double)]
+
+
+class Sources(C.Structure):
+    _fields_ = [("s_mass_dev", C.c_void_p), ("s_mom_dev", C.c_void_p), ("dsum_dev", C.c_void_p)]
+
+
+class PsicellOut(C.Structure):
+    _fields_ = [("counts_dev", C.c_void_p), ("s_mass_dev", C.c_void_p), ("s_mom_dev", C.c_void_p)]
+
+
+class DeviceStatus(C.Structure):
+    _fields_ = [("nonfinite", C.c_uint64), ("deposited", C.c_uint64), ("droplet_steps", C.c_uint64),
+                ("pairs", C.c_uint64), ("flags", C.c_uint32), ("pad", C.c_uint32)]
+
+
+BATCH_DTYPE = np.dtype([("St0", "<f8"), ("n0", "<f8"), ("h0", "<f8"), ("step_start", "<i4"),
+                        ("step_dead", "<i4")])
+assert BATCH_DTYPE.itemsize == 32
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libfla.so; raise if it has not been built (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise FlaError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                           "(the CUDA library is required; there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        v, i32, i64, u32, d = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_double
+        P = C.POINTER
+        L.fla_abi_version.restype = C.c_int
+        L.fla_status_string.restype = C.c_char_p
+        L.fla_status_string.argtypes = [C.c_int]
+        L.fla_create.argtypes = [P(v), C.c_int]
+        L.fla_destroy.argtypes = [v]
+        L.fla_destroy.restype = None
+        L.fla_state_layout.argtypes = [i32, i32] + [P(i32)] * 6
+        L.fla_carrier_nodes_bytes.argtypes = [P(Mesh), i32]
+        L.fla_carrier_nodes_bytes.restype = C.c_size_t
+        L.fla_carrier_sample.argtypes = [v, P(CarrierDesc), P(Mesh), d, i32, v, v]
+        L.fla_batch_deadline.argtypes = [d, d, d, i32, P(i32)]
+        L.fla_advance.argtypes = [v, P(Cloud), P(Mesh), v, i32, i32, d, u32, v]
+        L.fla_workspace_size.argtypes = [P(Mesh), i32, i32, i64, P(C.c_size_t)]
+        L.fla_cell_bins.argtypes = [v, P(Cloud), P(Mesh), v, v, v, v, C.c_size_t, v]
+        L.fla_deposit_sources.argtypes = [v, P(Cloud), P(Mesh), P(DepositCfg), P(Sources), v, C.c_size_t, v]
+        L.psicell_deposit.argtypes = [v, P(Cloud), P(Mesh), d, i32, P(PsicellOut), v, C.c_size_t, v]
+        L.fla_sync_status.argtypes = [v, v, P(DeviceStatus), C.c_int]
+        L.fla_profile_enable.argtypes = [v, C.c_int, C.c_int]
+        L.fla_profile_read.argtypes = [v, i32, P(C.c_double), P(i64), P(i64)]
+        L.fla_phase_name.argtypes = [i32]
+        L.fla_phase_name.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def check(code: int, what: str) -> None:
+    if code != 0:
+        msg = lib().fla_status_string(code).decode()
+        raise FlaError(f"{what} failed: {msg} ({code})")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+class Context:
+    """Owns an fla_ctx (device handle, SM count, status block)."""
+
+    def __init__(self, device: int = 0):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise FlaError("no CUDA device: the FLA library has no CPU path")
+        torch.cuda.set_device(device)
+        h = C.c_void_p()
+        check(lib().fla_create(C.byref(h), device), "fla_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            lib().fla_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def profile(self, enable: bool, reset: bool = True) -> None:
+        """Per-phase launch counting is always on; enable adds CUDA-event timing
+        (eager launches only, not while capturing a graph)."""
+        check(lib().fla_profile_enable(self.handle, 1 if enable else 0, 1 if reset else 0), "fla_profile_enable")
+
+    def profile_read(self) -> dict:
+        n = len(PHASES)
+        ms = (C.c_double * n)()
+        la = (C.c_int64 * n)()
+        ca = (C.c_int64 * n)()
+        check(lib().fla_profile_read(self.handle, n, ms, la, ca), "fla_profile_read")
+        return {PHASES[i]: {"ms": ms[i], "launches": la[i], "calls": ca[i]} for i in range(n)}
+
+    def sync_status(self, stream=None, reset: bool = False) -> DeviceStatus:
+        st = DeviceStatus()
+        code = lib().fla_sync_status(self.handle, _stream_ptr(stream), C.byref(st), 1 if reset else 0)
+        if code not in (0, -4):
+            check(code, "fla_sync_status")
+        return st
+
+
+def mesh(dim: int, n: int) -> Mesh:
+    return Mesh(dim, n)
+
+
+def state_layout(kind: int, dim: int) -> dict:
+    vals = [C.c_int32() for _ in range(6)]
+    check(lib().fla_state_layout(kind, dim, *[C.byref(x) for x in vals]), "fla_state_layout")
+    keys = ["n_planes", "x", "v", "J", "W", "acc"]
+    return {k: x.value for k, x in zip(keys, vals)}
+
+
+def carrier_desc(car: I.Carrier) -> CarrierDesc:
+    c = CarrierDesc()
+    c.kind, c.dim = int(car.kind), int(car.dim)
+    U = np.zeros(3); U[:np.asarray(car.U).size] = np.asarray(car.U, float).ravel()[:3]
+    xr = np.zeros(3); xr[:np.asarray(car.xref).size] = np.asarray(car.xref, float).ravel()[:3]
+    A = np.zeros((3, 3)); Ai = np.asarray(car.A, float); A[:Ai.shape[0], :Ai.shape[1]] = Ai
+    for k in range(3):
+        c.U[k], c.xref[k], c.abc[k] = U[k], xr[k], float(car.abc[k])
+    for k in range(9):
+        c.A[k] = A.ravel()[k]
+    vt = np.asarray(car.vortices, float).reshape(-1, 5)
+    if vt.shape[0] > MAX_VORTICES:
+        raise FlaError("too many vortices")
+    c.n_vortex = vt.shape[0]
+    for k in range(vt.shape[0]):
+        for q in range(5):
+            c.vortex[k][q] = vt[k, q]
+    c.jet_width, c.jet_amp, c.jet_radius = float(car.jet_width), float(car.jet_amp), float(car.jet_radius)
+    return c
+
+
+def batch_deadline(St0: float, delta: float, dt: float, step_start: int) -> int:
+    out = C.c_int32()
+    check(lib().fla_batch_deadline(float(St0), float(delta), float(dt), int(step_start), C.byref(out)),
+          "fla_batch_deadline")
+    return out.value
+
+
+def batch_table(cloud: I.Cloud, delta: float, dt: float) -> np.ndarray:
+    nb = len(cloud.St0)
+    t = np.zeros(nb, BATCH_DTYPE)
+    t["St0"], t["n0"], t["h0"] = cloud.St0, cloud.n0, cloud.h0
+    t["step_start"] = cloud.step_start
+    t["step_dead"] = [batch_deadline(s, delta, dt, ss) for s, ss in zip(cloud.St0, cloud.step_start)]
+    return t
+
+
+def meta_words(status: np.ndarray, batch: np.ndarray) -> np.ndarray:
+    m = np.asarray(batch, np.uint32) & META_BATCH_MASK
+    m = np.where(np.asarray(status) == 1, m | META_ACTIVE, m)
+    m = np.where(np.asarray(status) == 2, m | META_DEAD, m)
+    return m.astype(np.uint32)
+
+
+def status_of(meta: np.ndarray) -> np.ndarray:
+    meta = np.asarray(meta, np.uint32)
+    st = np.zeros(meta.shape, np.int32)
+    st[(meta & META_ACTIVE) != 0] = 1
+    st[(meta & META_DEAD) != 0] = 2
+    return st
+
+
+def pack_state(kind: int, dim: int, n: int, np_dtype, x=None, v=None, J=None, W=None, acc=None) -> np.ndarray:
+    """Host array (n_planes, n, 4) in the library's plane layout."""
+    L = state_layout(kind, dim)
+    flat = np.zeros((n, L["n_planes"] * 4), dtype=np_dtype)
+    for name, arr, width in (("x", x, dim), ("v", v, dim), ("J", J, dim * dim), ("W", W, dim * dim),
+                             ("acc", acc, 1 + dim)):
+        if arr is not None:
+            flat[:, L[name]:L[name] + width] = np.asarray(arr).reshape(n, width)
+    return np.ascontiguousarray(flat.reshape(n, L["n_planes"], 4).transpose(1, 0, 2))
+
+
+def unpack_state(kind: int, dim: int, planes: np.ndarray) -> dict:
+    L = state_layout(kind, dim)
+    n = planes.shape[1]
+    flat = planes.transpose(1, 0, 2).reshape(n, -1)
+    out = {"x": flat[:, 0:dim], "v": flat[:, dim:2 * dim], "acc": flat[:, L["acc"]:L["acc"] + 1 + dim]}
+    if kind == CLOUD_FLA:
+        out["J"] = flat[:, L["J"]:L["J"] + dim * dim].reshape(n, dim, dim)
+        out["W"] = flat[:, L["W"]:L["W"] + dim * dim].reshape(n, dim, dim)
+    return out
+
+
+class DeviceCloud:
+    """A cloud resident on the GPU: state planes, meta words and release table."""
+
+    def __init__(self, kind: int, dim: int, dtype: int, planes: np.ndarray, meta: np.ndarray,
+                 batches: np.ndarray, delta: float, device="cuda"):
+        torch = _torch()
+        self.kind, self.dim, self.dtype, self.delta = kind, dim, dtype, float(delta)
+        self.n = int(planes.shape[1])
+        self.state = torch.from_numpy(np.ascontiguousarray(planes)).to(device)
+        self.meta = torch.from_numpy(np.ascontiguousarray(meta).view(np.int32)).to(device)
+        self.batches = torch.from_numpy(np.ascontiguousarray(batches).view(np.uint8)).to(device)
+        self.n_batches = int(len(batches))
+
+    @classmethod
+    def from_seeds(cls, cloud: I.Cloud, dim: int, delta: float, dt: float, dtype: int = F32, device="cuda"):
+        npd = np.float32 if dtype == F32 else np.float64
+        planes = pack_state(cloud.kind, dim, cloud.n, npd, x=cloud.x0)
+        meta = meta_words(np.zeros(cloud.n, np.int32), cloud.batch)
+        return cls(cloud.kind, dim, dtype, planes, meta, batch_table(cloud, delta, dt), delta, device)
+
+    @classmethod
+    def from_state(cls, kind: int, dim: int, dtype: int, *, x, status, batch, batches: np.ndarray, delta=0.0,
+                   v=None, J=None, W=None, acc=None, device="cuda"):
+        npd = np.float32 if dtype == F32 else np.float64
+        n = np.asarray(x).shape[0]
+        planes = pack_state(kind, dim, n, npd, x=x, v=v, J=J, W=W, acc=acc)
+        return cls(kind, dim, dtype, planes, meta_words(status, batch), batches, delta, device)
+
+    def struct(self) -> Cloud:
+        c = Cloud()
+        c.kind, c.dim, c.dtype, c.n_batches = self.kind, self.dim, self.dtype, self.n_batches
+        c.n = self.n
+        c.state_dev = self.state.data_ptr()
+        c.meta_dev = self.meta.data_ptr()
+        c.batches_dev = self.batches.data_ptr()
+        c.delta = self.delta
+        return c
+
+    def to_host(self) -> dict:
+        d = unpack_state(self.kind, self.dim, self.state.cpu().numpy())
+        meta = self.meta.cpu().numpy().view(np.uint32)
+        d["status"] = status_of(meta)
+        d["batch"] = (meta & META_BATCH_MASK).astype(np.int32)
+        return d
+
+
+def torch_dtype(dtype: int):
+    torch = _torch()
+    return torch.float32 if dtype == F32 else torch.float64
+
+
+def nodes_buffer(m: Mesh, dtype: int, device="cuda"):
+    torch = _torch()
+    nbytes = lib().fla_carrier_nodes_bytes(C.byref(m), dtype)
+    return torch.empty(nbytes // (4 if dtype == F32 else 8), dtype=torch_dtype(dtype), device=device)
+
+
+def carrier_sample(ctx: Context, desc: CarrierDesc, m: Mesh, t: float, dtype: int, nodes, stream=None):
+    check(lib().fla_carrier_sample(ctx.handle, C.byref(desc), C.byref(m), float(t), dtype, _ptr(nodes),
+                                   _stream_ptr(stream)), "fla_carrier_sample")
+
+
+def advance(ctx: Context, cloud: DeviceCloud, m: Mesh, nodes, step0: int, nsteps: int, dt: float,
+            reset_acc: bool = False, stream=None):
+    cs = cloud.struct()
+    check(lib().fla_advance(ctx.handle, C.byref(cs), C.byref(m), _ptr(nodes), int(step0), int(nsteps), float(dt),
+                            ADVANCE_RESET_ACC if reset_acc else 0, _stream_ptr(stream)), "fla_advance")
+
+
+def workspace_size(m: Mesh, dtype: int, kernel: int, n: int) -> int:
+    out = C.c_size_t()
+    check(lib().fla_workspace_size(C.byref(m), dtype, kernel, int(n), C.byref(out)), "fla_workspace_size")
+    return out.value
+
+
+def workspace(m: Mesh, dtype: int, kernel: int, n: int, device="cuda"):
+    torch = _torch()
+    nb = workspace_size(m, dtype, kernel, n)
+    return torch.empty(nb + 256, dtype=torch.uint8, device=device)   # caching allocator blocks are 512-aligned
+
+
+def n_cells(m: Mesh) -> int:
+    return m.n ** m.dim
+
+
+def cell_bins(ctx: Context, cloud: DeviceCloud, m: Mesh, ws, stream=None):
+    torch = _torch()
+    nc = n_cells(m)
+    keys = torch.empty(max(cloud.n, 1), dtype=torch.int32, device=cloud.state.device)
+    perm = torch.empty(max(cloud.n, 1), dtype=torch.int32, device=cloud.state.device)
+    bins = torch.empty(nc + 1, dtype=torch.int32, device=cloud.state.device)
+    cs = cloud.struct()
+    check(lib().fla_cell_bins(ctx.handle, C.byref(cs), C.byref(m), _ptr(keys), _ptr(perm), _ptr(bins), _ptr(ws),
+                              ws.numel(), _stream_ptr(stream)), "fla_cell_bins")
+    return keys[:cloud.n], perm[:cloud.n], bins
+
+
+def deposit_cfg(kernel: int, h_min: float, h_max: float, window_dt: float, p: float = 1.0,
+                per_cell: bool = False) -> DepositCfg:
+    return DepositCfg(int(kernel), 1 if per_cell else 0, float(h_min), float(h_max), float(p), float(window_dt))
+
+
+class SourceFields:
+    def __init__(self, m: Mesh, dtype: int, device="cuda", with_dsum: bool = True):
+        torch = _torch()
+        nc = n_cells(m)
+        td = torch_dtype(dtype)
+        self.s_mass = torch.empty(nc, dtype=td, device=device)
+        self.s_mom = torch.empty(m.dim, nc, dtype=td, device=device)
+        self.dsum = torch.empty(nc, dtype=td, device=device) if with_dsum else None
+
+    def struct(self) -> Sources:
+        return Sources(self.s_mass.data_ptr(), self.s_mom.data_ptr(), self.dsum.data_ptr() if self.dsum is not None else None)
+
+
+def deposit_sources(ctx: Context, cloud: DeviceCloud, m: Mesh, cfg: DepositCfg, out: SourceFields, ws, stream=None):
+    cs = cloud.struct()
+    so = out.struct()
+    check(lib().fla_deposit_sources(ctx.handle, C.byref(cs), C.byref(m), C.byref(cfg), C.byref(so), _ptr(ws),
+                                    ws.numel(), _stream_ptr(stream)), "fla_deposit_sources")
+
+
+class PsicellFields:
+    def __init__(self, m: Mesh, dtype: int, device="cuda"):
+        torch = _torch()
+        nc = n_cells(m)
+        td = torch_dtype(dtype)
+        self.counts = torch.empty(nc, dtype=torch.int32, device=device)
+        self.s_mass = torch.empty(nc, dtype=td, device=device)
+        self.s_mom = torch.empty(m.dim, nc, dtype=td, device=device)
+
+    def struct(self) -> PsicellOut:
+        return PsicellOut(self.counts.data_ptr(), self.s_mass.data_ptr(), self.s_mom.data_ptr())
+
+
+def psicell(ctx: Context, cloud: DeviceCloud, m: Mesh, window_dt: float, out: PsicellFields, ws,
+            per_cell: bool = False, stream=None):
+    cs = cloud.struct()
+    po = out.struct()
+    check(lib().psicell_deposit(ctx.handle, C.byref(cs), C.byref(m), float(window_dt), 1 if per_cell else 0,
+                                C.byref(po), _ptr(ws), ws.numel(), _stream_ptr(stream)), "psicell_deposit")
+
+
+def aligned_ws(ws):
+    """View of a workspace tensor starting on a 256-byte boundary."""
+    off = (-ws.data_ptr()) % 256
+    return ws[off:]
+
+
+@dataclass
+class RunConfig:
+    dtype: int = F32
+    deposit: bool = True
+    psicell: bool = False
+
+
+class Simulation:
+    """Runs a workload's FLA cloud (and optionally its PSI-CELL parcels) window by
+    window on one GPU: carrier sample -> advance (fused window) -> deposit."""
+
+    def __init__(self, ctx: Context, wl: I.Workload, dtype: int = F32, with_psicell: bool = False,
+                 device="cuda"):
+        self.ctx, self.wl, self.dtype = ctx, wl, dtype
+        self.m = mesh(wl.dim, wl.n_cells_axis)
+        self.desc = carrier_desc(wl.carrier)
+        self.nodes = nodes_buffer(self.m, dtype, device)
+        self.fla = DeviceCloud.from_seeds(wl.fla, wl.dim, wl.delta, wl.dt, dtype, device)
+        self.cfg = deposit_cfg(wl.kernel, wl.h_min, wl.h_max, wl.window * wl.dt, wl.p)
+        self.out = SourceFields(self.m, dtype, device)
+        n_ws = self.fla.n
+        self.lpt = None
+        if with_psicell and wl.lpt is not None:
+            self.lpt = DeviceCloud.from_seeds(wl.lpt, wl.dim, wl.delta, wl.dt, dtype, device)
+            self.psi = PsicellFields(self.m, dtype, device)
+            n_ws = max(n_ws, self.lpt.n)
+        self.ws = aligned_ws(workspace(self.m, dtype, wl.kernel, n_ws, device))
+        self.step = 0
+        self._sampled_t = None
+
+    def reset(self):
+        """Back to the seeds (device-side copies only re-upload the initial planes)."""
+        wl = self.wl
+        self.fla = DeviceCloud.from_seeds(wl.fla, wl.dim, wl.delta, wl.dt, self.dtype, self.fla.state.device)
+        if self.lpt is not None:
+            self.lpt = DeviceCloud.from_seeds(wl.lpt, wl.dim, wl.delta, wl.dt, self.dtype, self.lpt.state.device)
+        self.step = 0
+        self._sampled_t = None
+
+    def window(self, deposit: bool = True, with_psicell: bool = True, stream=None):
+        wl = self.wl
+        k = min(wl.window, wl.nsteps - self.step) if wl.nsteps > self.step else wl.window
+        t_c = self.step * wl.dt if not wl.carrier.steady else 0.0
+        if self._sampled_t != t_c:
+            carrier_sample(self.ctx, self.desc, self.m, t_c, self.dtype, self.nodes, stream)
+            self._sampled_t = t_c
+        advance(self.ctx, self.fla, self.m, self.nodes, self.step, k, wl.dt, reset_acc=True, stream=stream)
+        if self.lpt is not None:
+            advance(self.ctx, self.lpt, self.m, self.nodes, self.step, k, wl.dt, reset_acc=True, stream=stream)
+        self.step += k
+        if deposit:
+            deposit_sources(self.ctx, self.fla, self.m, self.cfg, self.out, self.ws, stream)
+        if with_psicell and self.lpt is not None:
+            psicell(self.ctx, self.lpt, self.m, wl.window * wl.dt, self.psi, self.ws, stream=stream)
+
+    def run(self, nsteps: int | None = None, deposit_every: bool = True, stream=None):
+        total = self.wl.nsteps if nsteps is None else nsteps
+        while self.step < total:
+            last = self.step + self.wl.window >= total
+            self.window(deposit=deposit_every or last, with_psicell=deposit_every or last, stream=stream)

@@ -1,0 +1,153 @@
+"""Whole path (carrier -> advance -> records -> cell list -> deposits) on the GPU
+against the FP64 oracle, at the workload sizes the benchmark uses.
+
+* 64^2 Taylor-Green (4,096 FLA seeds, 200 steps, 262,144 PSI-CELL parcels):
+  complete end-to-end comparison, FP64 (tight) and FP32 (rel-L2 <= 1e-4).
+* 512^2 jet + vortices (262,144 FLA seeds, 1,000 steps): the benchmark's launch
+  configuration.  The oracle integrates a random sample of the seeds through
+  all 1,000 steps and compares them one by one; the deposit is compared at
+  sampled cells on a cloud state of the same shape and size.
+* 128^3 ABC + jet, anisotropic kernel: deposit at sampled cells on a 2^21-droplet
+  state; a reduced 32^3 run end to end.
+"""
+import numpy as np
+import pytest
+import torch
+
+from helpers import gpu_cloud_from_state, oracle_deposit, oracle_scale, rel_l2
+from oracle import oracle as O
+from paper_2512_20829_gb300 import fla
+from paper_2512_20829_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = fla.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def tg_oracle():
+    wl = I.taylor_green_2d()
+    st = O.run(wl)
+    D = O.dep_struct(wl)
+    src = O.nw_deposit_celllist(D, st.x, st.J, st.acc, st.status, st.batch, wl.fla.n0, wl.fla.h0)
+    lst = O.run(wl, wl.lpt)
+    return wl, st, src, lst
+
+
+def test_taylor_green_fp64_end_to_end(ctx, tg_oracle):
+    wl, st, (Sm, Sv, Ds), lst = tg_oracle
+    sim = fla.Simulation(ctx, wl, dtype=fla.F64, with_psicell=True)
+    sim.run(deposit_every=True)
+    torch.cuda.synchronize()
+    g = sim.fla.to_host()
+    assert np.array_equal(g["status"], st.status)
+    assert np.abs(g["x"] - st.x).max() < 1e-12 and np.abs(g["J"] - st.J).max() < 1e-10
+    assert rel_l2(sim.out.s_mass.cpu().numpy(), Sm) < 1e-10
+    assert rel_l2(sim.out.s_mom.cpu().numpy().T, Sv) < 1e-10
+    assert rel_l2(sim.out.dsum.cpu().numpy(), Ds) < 1e-10
+    # PSI-CELL reference with 262,144 parcels
+    D = O.dep_struct(wl)
+    counts, pm, pv = O.psicell(D, lst.x, lst.acc, lst.status, lst.batch, wl.lpt.n0, fp32_keys=False)
+    assert np.array_equal(sim.psi.counts.cpu().numpy().astype(np.uint32), counts)
+    assert rel_l2(sim.psi.s_mass.cpu().numpy(), pm) < 1e-12
+    assert rel_l2(sim.psi.s_mom.cpu().numpy().T, pv) < 1e-12
+
+
+def test_taylor_green_fp32_end_to_end(ctx, tg_oracle):
+    """FP32 trajectories + FP32 deposit vs the FP64 oracle: rel-L2 <= 1e-4 per field."""
+    wl, st, (Sm, Sv, Ds), lst = tg_oracle
+    sim = fla.Simulation(ctx, wl, dtype=fla.F32, with_psicell=True)
+    sim.run(deposit_every=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(sim.fla.to_host()["status"], st.status)
+    assert rel_l2(sim.out.s_mass.double().cpu().numpy(), Sm) <= 1e-4
+    assert rel_l2(sim.out.s_mom.double().cpu().numpy().T, Sv) <= 1e-4
+    D = O.dep_struct(wl)
+    counts, pm, pv = O.psicell(D, lst.x, lst.acc, lst.status, lst.batch, wl.lpt.n0, fp32_keys=False)
+    gc = sim.psi.counts.cpu().numpy().astype(np.int64)
+    # parcels within FP32 rounding of a cell face may land in the neighbour cell
+    assert np.abs(gc - counts).sum() <= 1e-4 * counts.sum()
+    assert rel_l2(sim.psi.s_mass.double().cpu().numpy(), pm) <= 1e-2
+
+
+def test_jet_vortex_full_size_sampled_trajectories(ctx):
+    """512^2 / 262,144 seeds / 1,000 steps in the benchmark's configuration; a
+    random sample of 192 seeds is integrated by the oracle and compared one by
+    one.  The rounding error of FP32 is carried forward by the flow map, whose
+    amplification the seed's own |J| bounds: |dx| <= 1e-4 (1 + max_t |J|)."""
+    wl = I.jet_vortex_2d(lpt_per_batch=0)
+    sim = fla.Simulation(ctx, wl, dtype=fla.F32)
+    sim.run(deposit_every=True)
+    torch.cuda.synchronize()
+    g = sim.fla.to_host()
+    rng = np.random.default_rng(17)
+    idx = np.sort(rng.choice(wl.fla.n, 192, replace=False))
+    sub = I.Cloud(kind=wl.fla.kind, x0=wl.fla.x0[idx], batch=wl.fla.batch[idx], step_start=wl.fla.step_start,
+                  St0=wl.fla.St0, n0=wl.fla.n0, h0=wl.fla.h0)
+    adv = O.Advancer(wl, sub)
+    st = O.initial_state(sub, 2)
+    jmax = np.zeros(len(idx))
+    for s in range(0, wl.nsteps, wl.window):
+        adv.advance(st, s, wl.window, reset_acc=True)
+        act = st.status == 1
+        jmax[act] = np.maximum(jmax[act], np.linalg.norm(st.J[act], axis=(1, 2)))
+    # the status agrees except where the trajectory ends within rounding of the boundary
+    same = g["status"][idx] == st.status
+    assert same.mean() >= 0.97
+    both = same & (st.status == 1)
+    assert both.sum() > 50
+    dx = np.abs(g["x"][idx][both] - st.x[both]).max(axis=1)
+    bound = 1e-4 * (1 + jmax[both])
+    assert np.all(dx <= bound), (dx / bound).max()
+
+
+def _synthetic_like(dim, n, N, seed, band, h0_cells):
+    return I.synthetic_state(dim, n, N, seed=seed, band=band, h0_cells=h0_cells, jac_spread=0.3)
+
+
+@pytest.mark.parametrize("dim,N,n,kernel,hmax,h0,ncheck", [
+    (2, 512, 262_144, I.KERNEL_ISO, 4.0, 2.0, 1024),
+    (3, 128, 2_097_152, I.KERNEL_ANISO, 2.0, 0.45, 96),
+])
+def test_full_size_deposit_at_sampled_cells(ctx, dim, N, n, kernel, hmax, h0, ncheck):
+    """Deposit of a full-size cloud state (the benchmark's sizes); the oracle
+    evaluates sampled cells one by one by brute force over every droplet."""
+    s = _synthetic_like(dim, n, N, seed=31 + dim, band=(0.4, 0.6), h0_cells=h0)
+    m = fla.mesh(dim, N)
+    cl = gpu_cloud_from_state(s, fla.F32)
+    ws = fla.aligned_ws(fla.workspace(m, fla.F32, kernel, n))
+    out = fla.SourceFields(m, fla.F32)
+    cfg = fla.deposit_cfg(kernel, 0.5 / N, hmax / N, 0.01)
+    fla.deposit_sources(ctx, cl, m, cfg, out, ws)
+    torch.cuda.synchronize()
+    gd = out.dsum.double().cpu().numpy()
+    rng = np.random.default_rng(5)
+    covered = np.nonzero(gd > 0)[0]
+    cells = np.sort(np.concatenate([rng.choice(covered, ncheck - 16, replace=False),
+                                    rng.choice(gd.size, 16, replace=False)]))
+    om, ov, od = oracle_deposit(s, N, kernel, 0.5 / N, hmax / N, 0.01, fp32=True, cells=cells)
+    sm, sv = oracle_scale(s, N, kernel, 0.5 / N, hmax / N, 0.01, fp32=True, cells=cells)
+    gm = out.s_mass.double().cpu().numpy()[cells]
+    gv = out.s_mom.double().cpu().numpy().T[cells]
+    assert np.array_equal(gd[cells] > 0, od > 0)
+    assert np.all(np.abs(gm - om) <= 1e-4 * sm + 1e-30)
+    assert np.all(np.abs(gv - ov) <= 1e-4 * sv + 1e-30)
+    assert rel_l2(gm, om) <= 1e-4 and rel_l2(gv, ov) <= 1e-4
+
+
+def test_abc_jet_reduced_end_to_end(ctx):
+    """32^3 mesh, 32,768 seeds, 100 steps, anisotropic kernel; FP32 GPU path vs FP64 oracle."""
+    wl = I.abc_jet_3d(scale=4, nsteps=100)
+    sim = fla.Simulation(ctx, wl, dtype=fla.F32)
+    sim.run(deposit_every=True)
+    torch.cuda.synchronize()
+    st = O.run(wl)
+    D = O.dep_struct(wl)
+    Sm, Sv, Ds = O.nw_deposit_celllist(D, st.x, st.J, st.acc, st.status, st.batch, wl.fla.n0, wl.fla.h0)
+    assert rel_l2(sim.out.s_mass.double().cpu().numpy(), Sm) <= 1e-4
+    assert rel_l2(sim.out.s_mom.double().cpu().numpy().T, Sv) <= 1e-4
