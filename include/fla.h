@@ -270,6 +270,30 @@ int psicell_deposit(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, 
  * afterwards.  Returns FLA_ERR_NONFINITE when nonfinite > 0, else FLA_OK. */
 int fla_sync_status(fla_ctx* ctx, fla_stream_t stream, fla_device_status* out, int reset);
 
+/* Allocation-free cell binning, for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this exists for host programs that
+ * can pass device pointers to buffers they already own but cannot create new
+ * ones, such as a solver's C or Fortran coupling layer without a CUDA
+ * allocator, or code where cudaMalloc is not allowed because it synchronises
+ * the device or because another framework has reserved the memory.
+ *
+ * Same inputs, outputs and results as fla_cell_bins (bit for bit), but the
+ * scratch space is a fixed array compiled into the library (about 4.2 MB of
+ * device memory on every GPU that loads the library, held until the process
+ * exits) and no fla_ctx is needed.  The call allocates nothing.
+ *  - Clouds of more than FLA_NOALLOC_MAX_DROPLETS droplets are rejected with
+ *    FLA_ERR_WORKSPACE before anything is enqueued.
+ *  - The first call on a device, with that device current, looks up the
+ *    array's device address (cudaGetSymbolAddress); make that first call
+ *    before any stream capture on that device.
+ *  - All calls on a device share the one array, which keeps the last call's
+ *    contents; nothing in it needs to start at zero.  Calls whose GPU work
+ *    overlaps (different streams or host threads without ordering) race on
+ *    it and must be serialised by the caller. */
+#define FLA_NOALLOC_MAX_DROPLETS 262144
+int fla_cell_bins_noalloc(const fla_cloud* cloud, const fla_mesh* mesh, uint32_t* keys_sorted_dev,
+                          uint32_t* perm_dev, uint32_t* bin_start_dev, fla_stream_t stream);
+
 /* Per-phase profiling.  The context always counts the kernels it launches per
  * phase (also while a stream is being captured into a CUDA graph).  With
  * timing enabled it also brackets every phase of every call with CUDA events

@@ -1,0 +1,93 @@
+// fla_cell_bins_noalloc: the cell binning of fla_cell_bins for callers that
+// cannot allocate device memory.
+//
+// Some host programs hand this library device pointers to buffers they
+// already own but have no way to create new device buffers: a solver's C or
+// Fortran coupling layer without a CUDA allocator of its own, or code running
+// where cudaMalloc is not allowed because it synchronises the device or
+// because another framework has reserved the memory.  For them this entry
+// point takes its scratch space from a fixed array compiled into the library
+// instead of a caller-provided workspace, and needs no fla_ctx (creating one
+// allocates a small status block).
+//
+// The scratch array lives in device memory of every GPU that loads the
+// library, until the process exits.  Its size caps the cloud at
+// FLA_NOALLOC_MAX_DROPLETS droplets.
+#include <mutex>
+
+#include "fla_internal.cuh"
+
+using namespace fla;
+
+namespace {
+
+constexpr int64_t kMaxDroplets = FLA_NOALLOC_MAX_DROPLETS;
+constexpr int64_t kMaxTiles = (kMaxDroplets + 4095) / 4096;
+// keys[2][max], vals[2][max], counts[256 * tiles], totals[256]  (u32 words)
+constexpr int64_t kWords = 4 * kMaxDroplets + 256 * kMaxTiles + 256;
+
+static __device__ __align__(256) uint32_t g_scratch[kWords];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mutex;
+uint32_t* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_scratch on the current device (looked up once per device;
+// the host-side name g_scratch is not a device address).
+int scratch_for_current_device(uint32_t** out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FLA_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return FLA_ERR_CUDA;
+        g_scratch_ptr[dev] = static_cast<uint32_t*>(p);
+    }
+    *out = g_scratch_ptr[dev];
+    return FLA_OK;
+}
+
+}  // namespace
+
+extern "C" int fla_cell_bins_noalloc(const fla_cloud* cloud, const fla_mesh* mesh, uint32_t* keys_sorted_dev,
+                                     uint32_t* perm_dev, uint32_t* bin_start_dev, fla_stream_t stream)
+{
+    if (!cloud || !mesh) return FLA_ERR_ARG;
+    if ((mesh->dim != 2 && mesh->dim != 3) || mesh->n < 1 || mesh->n > (1 << 20)) return FLA_ERR_ARG;
+    const int64_t nc = mesh->dim == 2 ? (int64_t)mesh->n * mesh->n : (int64_t)mesh->n * mesh->n * mesh->n;
+    if (nc >= 2147483647LL) return FLA_ERR_ARG;
+    if (cloud->dim != mesh->dim || (cloud->dtype != FLA_F32 && cloud->dtype != FLA_F64)) return FLA_ERR_ARG;
+    if (cloud->kind != FLA_CLOUD_FLA && cloud->kind != FLA_CLOUD_LPT) return FLA_ERR_ARG;
+    if (cloud->n < 0) return FLA_ERR_ARG;
+    if (cloud->n > kMaxDroplets) return FLA_ERR_WORKSPACE;   // beyond the fixed scratch array
+    if (!bin_start_dev) return FLA_ERR_ARG;
+    if (cloud->n > 0 && (!cloud->state_dev || !cloud->meta_dev || !keys_sorted_dev || !perm_dev ||
+                         ((uintptr_t)cloud->state_dev % 16) != 0))
+        return FLA_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cloud->n == 0) return cudaMemsetAsync(bin_start_dev, 0, (size_t)(nc + 1) * 4, s) == cudaSuccess
+                                  ? FLA_OK : FLA_ERR_CUDA;
+    uint32_t* base = nullptr;
+    const int st = scratch_for_current_device(&base);
+    if (st != FLA_OK) return st;
+    // Every word the sort reads is written earlier in the same call (keys by the
+    // key kernel, digit counts by each pass's histogram), so nothing needs clearing.
+    SortWork w{};
+    w.keys[0] = base;
+    w.keys[1] = base + kMaxDroplets;
+    w.vals[0] = base + 2 * kMaxDroplets;
+    w.vals[1] = base + 3 * kMaxDroplets;
+    w.counts = base + 4 * kMaxDroplets;
+    w.totals = w.counts + 256 * kMaxTiles;
+    if (launch_cell_keys(*cloud, *mesh, w.keys[0], s) != cudaSuccess) return FLA_ERR_CUDA;
+    const int bits = sort_bits((uint32_t)nc);
+    if (launch_radix_sort(w, cloud->n, bits, 0, s) != cudaSuccess) return FLA_ERR_CUDA;
+    const int cur = sort_passes(bits) & 1;
+    if (cudaMemcpyAsync(keys_sorted_dev, w.keys[cur], (size_t)cloud->n * 4, cudaMemcpyDeviceToDevice, s) !=
+        cudaSuccess)
+        return FLA_ERR_CUDA;
+    if (cudaMemcpyAsync(perm_dev, w.vals[cur], (size_t)cloud->n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return FLA_ERR_CUDA;
+    return launch_bin_start(w.keys[cur], cloud->n, nc, bin_start_dev, s) == cudaSuccess ? FLA_OK : FLA_ERR_CUDA;
+}
