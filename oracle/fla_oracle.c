@@ -458,6 +458,69 @@ static void inv_sym(int d, const double* S, double det, double* P)
     P[6] = P[2];      P[7] = P[5];      P[8] = c22 / det;
 }
 
+/* Single-precision operands of the truncation decision, formed as a
+ * single-precision kernel forms them (reading: a floating-point comparison
+ * that decides an integer is taken in the kernel's precision on both sides).
+ *  - |det J|: in double from the single-precision entries (2D, products exact);
+ *    in 3D the cofactor expansion in single precision unless |det| < 1e-2 times
+ *    the product of the rows' L1 norms (near a fold), then in double;
+ *  - spherical kernel: h = clamp(h0 |det J|^p, h_min, h_max) in double, rounded,
+ *    and r2max = 9 h^2 formed in double from the rounded h and rounded;
+ *  - J-scaled kernel: Sigma and its inverse in single precision, one rounding
+ *    per operation, in the order written below. */
+static double det_decision(int d, const double* J)
+{
+    if (d == 2) return J[0] * J[3] - J[1] * J[2];
+    float j[9];
+    for (int q = 0; q < 9; ++q) j[q] = (float)J[q];
+    float detf = j[0] * (j[4] * j[8] - j[5] * j[7]) - j[1] * (j[3] * j[8] - j[5] * j[6])
+               + j[2] * (j[3] * j[7] - j[4] * j[6]);
+    float H = (fabsf(j[0]) + fabsf(j[1]) + fabsf(j[2])) * (fabsf(j[3]) + fabsf(j[4]) + fabsf(j[5]))
+            * (fabsf(j[6]) + fabsf(j[7]) + fabsf(j[8]));
+    if (fabsf(detf) < 0.01f * H) return det_d(3, J);
+    return (double)detf;
+}
+
+static void aniso_decision(const ora_dep* D, const double* J, double h0, float* Pf)
+{
+    int d = D->dim;
+    float j[9], S[9];
+    for (int q = 0; q < d * d; ++q) j[q] = (float)J[q];
+    float h02 = (float)h0 * (float)h0;
+    float room = (float)(D->h_max * D->h_max - d * D->h_min * D->h_min);
+    float hmin2 = (float)(D->h_min * D->h_min);
+    float tr0 = 0.0f;
+    for (int i = 0; i < d; ++i)
+        for (int k = 0; k < d; ++k) {
+            float sum = 0.0f;
+            for (int q = 0; q < d; ++q) sum = sum + j[i * d + q] * j[k * d + q];
+            S[i * d + k] = h02 * sum;
+            if (i == k) tr0 = tr0 + S[i * d + k];
+        }
+    if (tr0 > room) {
+        float f = room / tr0;
+        for (int q = 0; q < d * d; ++q) S[q] = S[q] * f;
+    }
+    for (int i = 0; i < d; ++i) S[i * d + i] = S[i * d + i] + hmin2;
+    if (d == 2) {
+        float dS = S[0] * S[3] - S[1] * S[2];
+        float inv = 1.0f / dS;
+        Pf[0] = S[3] * inv; Pf[3] = S[0] * inv; Pf[1] = -S[1] * inv; Pf[2] = Pf[1];
+        return;
+    }
+    float c00 = S[4] * S[8] - S[5] * S[7];
+    float c01 = S[5] * S[6] - S[3] * S[8];
+    float c02 = S[3] * S[7] - S[4] * S[6];
+    float c11 = S[0] * S[8] - S[2] * S[6];
+    float c12 = S[2] * S[3] - S[0] * S[5];
+    float c22 = S[0] * S[4] - S[1] * S[3];
+    float dS = S[0] * c00 + S[1] * c01 + S[2] * c02;
+    float inv = 1.0f / dS;
+    Pf[0] = c00 * inv; Pf[1] = c01 * inv; Pf[2] = c02 * inv;
+    Pf[3] = Pf[1];     Pf[4] = c11 * inv; Pf[5] = c12 * inv;
+    Pf[6] = Pf[2];     Pf[7] = Pf[5];     Pf[8] = c22 * inv;
+}
+
 /* Record of one active droplet: Eq. 6 number density, Eq. 15 smoothing length
  * or the J-scaled covariance Sigma = f h0^2 J J^T + h_min^2 I (reading: the
  * push-forward of the spherical kernel by J, kept positive definite at folds by
@@ -480,7 +543,11 @@ void ora_record(const ora_dep* D, const double* x, const double* J, const double
         if (h > D->h_max) h = D->h_max;
         r->h = h;
         r->pref = 1.0 / h;                                 /* Eq. 14 prefactor */
-        r->r2max_f = (float)(9.0 * (double)(float)h * (double)(float)h);
+        double ad = fabs(det_decision(d, J));
+        double hd = (D->p == 1.0) ? h0 * ad : h0 * pow(ad, D->p);
+        if (hd < D->h_min) hd = D->h_min;
+        if (hd > D->h_max) hd = D->h_max;
+        r->r2max_f = (float)(9.0 * (double)(float)hd * (double)(float)hd);
     } else {
         double Sg[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         double tr0 = 0.0;
@@ -503,7 +570,7 @@ void ora_record(const ora_dep* D, const double* x, const double* J, const double
         inv_sym(d, Sg, dS, r->P);
         r->pref = 1.0 / sqrt(dS);
         r->h = sqrt(tr);
-        for (int q = 0; q < d * d; ++q) r->Pf[q] = (float)r->P[q];
+        aniso_decision(D, J, h0, r->Pf);
     }
 }
 

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libfla.so")
 
-SOURCES = ["api.cu", "carrier.cu", "advance.cu", "binning.cu", "records.cu", "deposit.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "carrier.cu", "advance.cu", "binning.cu", "records.cu", "deposit.cu", "gather2d.cu", "noalloc.cu"]
 NO_FMA = {"records.cu"}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -41,8 +41,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     cc = nvcc()
-    common = ["-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-I", INCLUDE,
-              "--expt-relaxed-constexpr"]
+    # host code: no FMA contraction either (host-side double values such as the
+    # evaporation deadline must round as the expressions are written)
+    common = ["-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+              "-I", INCLUDE, "--expt-relaxed-constexpr"]
     procs = []
     objs = []
     for src in SOURCES:

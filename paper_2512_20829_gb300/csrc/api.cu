@@ -43,8 +43,14 @@ int cloud_ok(const fla_cloud* c, const fla_mesh* m)
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct WsLayout {
-    size_t keys[2], vals[2], counts, totals, bin_start, misc, rec, total;
+    size_t keys[2], vals[2], counts, totals, bin_start, misc, rec, tiles, temp, total;
 };
+
+// The load-balanced gather serves single-precision 2D clouds with the spherical kernel.
+bool use_gather2d(const fla_mesh& m, int dtype, int kernel)
+{
+    return m.dim == 2 && dtype == FLA_F32 && kernel == FLA_KERNEL_ISO;
+}
 
 WsLayout layout(const fla_mesh& m, int dtype, int kernel, int64_t n)
 {
@@ -62,6 +68,13 @@ WsLayout layout(const fla_mesh& m, int dtype, int kernel, int64_t n)
     L.bin_start = o; o += up256(((size_t)cells_of(m) + 1) * 4);
     L.misc = o; o += 256;
     L.rec = o; o += up256(rec_bytes);
+    L.tiles = o;
+    L.temp = o;
+    if (use_gather2d(m, dtype, kernel)) {
+        o += up256((size_t)(2 * gather2d_tiles(m.n) + 1) * 4);
+        L.temp = o;
+        o += up256(gather2d_temp_bytes(m.n, n));
+    }
     L.total = o;
     return L;
 }
@@ -134,10 +147,13 @@ int bin_cloud(fla_ctx* ctx, const fla_cloud& c, const fla_mesh& m, void* ws, con
     return FLA_OK;
 }
 
-int ws_ok(const fla_mesh& m, int dtype, int kernel, int64_t n, void* ws, size_t bytes)
+// Workspace check: `need` bytes from the start of the layout (each entry point
+// uses a prefix of it: binning up to the records, PSI-CELL 4 values per record,
+// the kernel-regression deposit all of it).
+int ws_ok(void* ws, size_t bytes, size_t need)
 {
     if (!ws || !aligned(ws, 256)) return FLA_ERR_WORKSPACE;
-    if (bytes < layout(m, dtype, kernel, n).total) return FLA_ERR_WORKSPACE;
+    if (bytes < need) return FLA_ERR_WORKSPACE;
     return FLA_OK;
 }
 
@@ -348,9 +364,9 @@ int fla_cell_bins(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, ui
     int st = cloud_ok(cloud, mesh);
     if (st != FLA_OK) return st;
     if (!bin_start_dev || (cloud->n > 0 && (!keys_sorted_dev || !perm_dev))) return FLA_ERR_ARG;
-    st = ws_ok(*mesh, cloud->dtype, FLA_KERNEL_ISO, cloud->n, ws, ws_bytes);
-    if (st != FLA_OK) return st;
     const WsLayout L = layout(*mesh, cloud->dtype, FLA_KERNEL_ISO, cloud->n);
+    st = ws_ok(ws, ws_bytes, L.rec);
+    if (st != FLA_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t nc = cells_of(*mesh);
     if (cloud->n == 0) {
@@ -386,9 +402,9 @@ int fla_deposit_sources(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* me
     const size_t T = cloud->dtype == FLA_F64 ? 8 : 4;
     if (!aligned(out->s_mass_dev, T) || !aligned(out->s_mom_dev, T) || (out->dsum_dev && !aligned(out->dsum_dev, T)))
         return FLA_ERR_ARG;
-    st = ws_ok(*mesh, cloud->dtype, cfg->kernel, cloud->n, ws, ws_bytes);
-    if (st != FLA_OK) return st;
     const WsLayout L = layout(*mesh, cloud->dtype, cfg->kernel, cloud->n);
+    st = ws_ok(ws, ws_bytes, L.total);
+    if (st != FLA_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t nc = cells_of(*mesh);
     uint32_t* bins = at<uint32_t>(ws, L.bin_start);
@@ -412,6 +428,14 @@ int fla_deposit_sources(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* me
                 return FLA_ERR_CUDA;
         }
     }
+    if (use_gather2d(*mesh, cloud->dtype, cfg->kernel)) {
+        PhaseScope ps(ctx, FLA_PHASE_GATHER, s, 4);
+        const int nt = gather2d_tiles(mesh->n);
+        uint32_t* tiles = at<uint32_t>(ws, L.tiles);
+        return cuda_status(launch_gather2d(*mesh, *cfg, at<void>(ws, L.rec), bins, ext, tiles, tiles + nt,
+                                           ext + 1, at<void>(ws, L.temp), gather2d_item_budget(mesh->n, cloud->n),
+                                           *out, (DevStatus*)ctx->status_dev, ctx->num_sms, s));
+    }
     PhaseScope ps(ctx, FLA_PHASE_GATHER, s, 1);
     return cuda_status(launch_nw_gather(*cloud, *mesh, *cfg, at<void>(ws, L.rec), bins, ext, *out,
                                         (DevStatus*)ctx->status_dev, s));
@@ -426,9 +450,10 @@ int psicell_deposit(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, 
     if (cloud->kind != FLA_CLOUD_LPT) return FLA_ERR_ARG;
     if (!(window_dt > 0) || !isfinite(window_dt) || (per_cell != 0 && per_cell != 1)) return FLA_ERR_ARG;
     if (!out->counts_dev || !out->s_mass_dev || !out->s_mom_dev) return FLA_ERR_ARG;
-    st = ws_ok(*mesh, cloud->dtype, FLA_KERNEL_ISO, cloud->n, ws, ws_bytes);
-    if (st != FLA_OK) return st;
     const WsLayout L = layout(*mesh, cloud->dtype, FLA_KERNEL_ISO, cloud->n);
+    const size_t psi_rec = up256((size_t)(cloud->n > 0 ? cloud->n : 1) * 4 * (cloud->dtype == FLA_F64 ? 8 : 4));
+    st = ws_ok(ws, ws_bytes, L.rec + psi_rec);
+    if (st != FLA_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t nc = cells_of(*mesh);
     uint32_t* bins = at<uint32_t>(ws, L.bin_start);

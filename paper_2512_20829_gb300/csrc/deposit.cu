@@ -1,15 +1,17 @@
 // Kernel-regression gather (Eqs. 13 and 16) and PSI-CELL box counting (Eqs. 10-11).
 //
 // Gather: one CTA per tile of cells (16x16 in 2D, 8x8x4 in 3D), one cell per
-// thread.  Droplet records are sorted by cell key, so the records of the
-// cells in one mesh row of the tile's neighbourhood are contiguous.  The CTA
-// walks those rows, each thread loads one record, records whose support cannot
-// reach the tile are culled, and the survivors are compacted (order kept)
-// into shared memory.  Every cell then evaluates the staged records in the
-// same order: truncation test, Gaussian weight with a single MUFU ex2 in
-// single precision, and FMA accumulation.  Each staged chunk is summed
-// plainly and chunk sums are added with Neumaier compensation.  No atomics
-// touch the outputs, so results are deterministic.
+// thread, each warp owning a 32-cell sub-tile.  Droplet records are sorted by
+// cell key, so the records of the cells in one mesh row of the tile's
+// neighbourhood are contiguous.  The CTA walks those rows, each thread loads
+// one record, records whose support cannot reach the tile are culled, and the
+// survivors are compacted (order kept) into shared memory.  Each warp then
+// tests 32 staged records at a time against its own sub-tile with one ballot
+// and evaluates only the records that can reach it: truncation test (as a
+// predicate), Gaussian weight 2^(c r^2 + log2(1/h)) with one MUFU ex2 in single
+// precision, FMA accumulation.  Each staged chunk is summed plainly and chunk
+// sums are added with Neumaier compensation.  Every cell sums its records in
+// staging order and no atomics touch the outputs, so results are deterministic.
 #include "fla_internal.cuh"
 
 namespace fla {
@@ -44,12 +46,104 @@ struct GatherArgs {
     DevStatus* status;
 };
 
+// CTA tile of cells and the per-warp sub-tile (32 cells, one per lane).
 template <int D> struct Tile;
-template <> struct Tile<2> { static constexpr int X = 16, Y = 16, Z = 1; };
-template <> struct Tile<3> { static constexpr int X = 8, Y = 8, Z = 4; };
+template <> struct Tile<2> {
+    static constexpr int X = 16, Y = 16, Z = 1;      // 8 warps of 8 x 4 cells
+    static constexpr int SX = 8, SY = 4, SZ = 1;
+};
+template <> struct Tile<3> {
+    static constexpr int X = 8, Y = 8, Z = 4;        // 8 warps of 4 x 4 x 2 cells
+    static constexpr int SX = 4, SY = 4, SZ = 2;
+};
 
 constexpr int GT = 256;            // threads per CTA = cells per tile
 constexpr int CAP = 2 * GT;        // staged records
+
+// position of the squared support radius inside a record
+template <int D, int KER> struct ExtSlot { static constexpr int v = (KER == FLA_KERNEL_ISO) ? (D == 2 ? 7 : 3) : (D == 2 ? 3 : 10); };
+
+// Weight of one record at this lane's cell centre; inside = truncation test.
+template <typename T, int D, int KER>
+__device__ __forceinline__ T weight_of(const T* r, const float* xcf, const T* xc, bool& inside)
+{
+    if (sizeof(T) == 4) {
+        const float* rf = reinterpret_cast<const float*>(r);
+        float df[3];
+#pragma unroll
+        for (int i = 0; i < D; ++i) df[i] = __fsub_rn(xcf[i], rf[i]);
+        if (KER == FLA_KERNEL_ISO) {
+            // single-precision decision in a fixed operation order
+            float r2 = __fmul_rn(df[0], df[0]);
+            r2 = __fmaf_rn(df[1], df[1], r2);
+            if (D == 3) r2 = __fmaf_rn(df[2], df[2], r2);
+            const float r2max = D == 2 ? rf[7] : rf[3];
+            const float c = D == 2 ? rf[2] : rf[4];
+            const float lih = D == 2 ? rf[3] : rf[5];
+            inside = r2 <= r2max;
+            const float w = ex2_approx(fmaf(r2, c, lih));
+            return T(inside ? w : 0.0f);
+        } else {
+            float P[9];
+            float lpref;
+            if (D == 2) {
+                P[0] = rf[4]; P[1] = rf[5]; P[2] = rf[5]; P[3] = rf[6];
+                lpref = rf[2];
+            } else {
+                P[0] = rf[4]; P[1] = rf[5]; P[2] = rf[6];
+                P[3] = rf[5]; P[4] = rf[7]; P[5] = rf[8];
+                P[6] = rf[6]; P[7] = rf[8]; P[8] = rf[9];
+                lpref = rf[3];
+            }
+            float pd[3];
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                float acc = __fmul_rn(P[i * D], df[0]);
+#pragma unroll
+                for (int k = 1; k < D; ++k) acc = __fmaf_rn(P[i * D + k], df[k], acc);
+                pd[i] = acc;
+            }
+            float q = __fmul_rn(pd[0], df[0]);
+#pragma unroll
+            for (int i = 1; i < D; ++i) q = __fmaf_rn(pd[i], df[i], q);
+            inside = q <= 9.0f;
+            const float w = ex2_approx(fmaf(q, -0.72134752044448170368f, lpref));
+            return T(inside ? w : 0.0f);
+        }
+    } else {
+        T df[3];
+#pragma unroll
+        for (int i = 0; i < D; ++i) df[i] = xc[i] - r[i];
+        if (KER == FLA_KERNEL_ISO) {
+            T r2 = df[0] * df[0] + df[1] * df[1];
+            if (D == 3) r2 += df[2] * df[2];
+            const T c = D == 2 ? r[2] : r[4];
+            const T ih = D == 2 ? r[3] : r[5];
+            const T e = r2 * c;                       // = -q/2
+            inside = e >= T(-4.5);
+            return inside ? ih * exp(e) : T(0);
+        } else {
+            T P[9];
+            T pref;
+            if (D == 2) {
+                P[0] = r[4]; P[1] = r[5]; P[2] = r[5]; P[3] = r[6];
+                pref = r[2];
+            } else {
+                P[0] = r[4]; P[1] = r[5]; P[2] = r[6];
+                P[3] = r[5]; P[4] = r[7]; P[5] = r[8];
+                P[6] = r[6]; P[7] = r[8]; P[8] = r[9];
+                pref = r[3];
+            }
+            T q = T(0);
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) q += df[i] * P[i * D + k] * df[k];
+            inside = q <= T(9);
+            return inside ? pref * exp(T(-0.5) * q) : T(0);
+        }
+    }
+}
 
 template <typename T, int D, int KER>
 __global__ void __launch_bounds__(GT) k_nw_gather(GatherArgs a)
@@ -57,6 +151,8 @@ __global__ void __launch_bounds__(GT) k_nw_gather(GatherArgs a)
     constexpr int RV = record_values(D, KER);
     constexpr int R4 = RV / 4;
     constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
+    constexpr int SX = Tile<D>::SX, SY = Tile<D>::SY, SZ = Tile<D>::SZ;
+    constexpr int EXT = ExtSlot<D, KER>::v;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* srec = reinterpret_cast<T*>(smem_raw);
     __shared__ int s_wcount[GT / 32];
@@ -65,25 +161,37 @@ __global__ void __launch_bounds__(GT) k_nw_gather(GatherArgs a)
     const int N = a.N;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int t0[3] = {(int)blockIdx.x * TX, (int)blockIdx.y * TY, (int)blockIdx.z * TZ};
-    const int cc[3] = {t0[0] + tid % TX, t0[1] + (tid / TX) % TY, t0[2] + tid / (TX * TY)};
-    bool in_mesh = cc[0] < N && cc[1] < N;
-    if (D == 3) in_mesh = in_mesh && cc[2] < N;
+    // warp sub-tile origin and this lane's cell
+    int w0[3], cc[3];
+    if (D == 2) {
+        w0[0] = t0[0] + (warp & 1) * SX; w0[1] = t0[1] + (warp >> 1) * SY; w0[2] = 0;
+        cc[0] = w0[0] + (lane & 7); cc[1] = w0[1] + (lane >> 3); cc[2] = 0;
+    } else {
+        w0[0] = t0[0] + (warp & 1) * SX; w0[1] = t0[1] + ((warp >> 1) & 1) * SY; w0[2] = t0[2] + (warp >> 2) * SZ;
+        cc[0] = w0[0] + (lane & 3); cc[1] = w0[1] + ((lane >> 2) & 3); cc[2] = w0[2] + (lane >> 4);
+    }
+    bool in_mesh = cc[0] < N && cc[1] < N && (D == 2 || cc[2] < N);
+    bool warp_live = w0[0] < N && w0[1] < N && (D == 2 || w0[2] < N);
     T xc[3];
     float xcf[3];
 #pragma unroll
     for (int q = 0; q < D; ++q) {
-        const double v = ((double)cc[q] + 0.5) / (double)N;
-        xc[q] = T(v);
-        xcf[q] = (float)v;
+        const float v = ((float)cc[q] + 0.5f) / (float)N;
+        xc[q] = T(((double)cc[q] + 0.5) / (double)N);
+        xcf[q] = sizeof(T) == 4 ? v : (float)xc[q];
     }
-    // bounding box of the tile's cell centres (for culling)
-    T lo[3], hi[3];
+    // boxes of cell centres: the CTA tile (staging cull) and the warp sub-tile (flush cull)
+    T lo[3], hi[3], wlo[3], whi[3];
 #pragma unroll
     for (int q = 0; q < D; ++q) {
         const int tq = q == 0 ? TX : (q == 1 ? TY : TZ);
+        const int sq = q == 0 ? SX : (q == 1 ? SY : SZ);
         const int last = (t0[q] + tq < N ? t0[q] + tq : N) - 1;
+        const int wlast = (w0[q] + sq < N ? w0[q] + sq : N) - 1;
         lo[q] = T(((double)t0[q] + 0.5) / (double)N);
         hi[q] = T(((double)last + 0.5) / (double)N);
+        wlo[q] = T(((double)w0[q] + 0.5) / (double)N);
+        whi[q] = T(((double)wlast + 0.5) / (double)N);
     }
     const float ext2max = __uint_as_float(__ldg(a.ext_max));
     const int R = (int)floorf(sqrtf(ext2max) * (float)N + 0.5f) + 1;
@@ -104,93 +212,52 @@ __global__ void __launch_bounds__(GT) k_nw_gather(GatherArgs a)
     }
     __syncthreads();
 
+    // Evaluate the staged records for this warp's cells in staging order: 32 records
+    // at a time are tested against the warp's sub-tile (one per lane, one ballot),
+    // and only those that can reach it are evaluated by every lane.
     auto flush = [&](int count) {
+        if (!warp_live) return;
         T pD = T(0), pN[4] = {T(0), T(0), T(0), T(0)};
-        for (int k = 0; k < count; ++k) {
-            const T* r = srec + k * RV;
-            T w;
-            bool inside;
-            if (KER == FLA_KERNEL_ISO) {
-                if (sizeof(T) == 4) {
-                    // single-precision decision in a fixed operation order
-                    float dx = __fsub_rn(xcf[0], (float)r[0]);
-                    float dy = __fsub_rn(xcf[1], (float)r[1]);
-                    float r2 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
-                    float r2max, c, ih;
-                    if (D == 3) {
-                        const float dz = __fsub_rn(xcf[2], (float)r[2]);
-                        r2 = __fmaf_rn(dz, dz, r2);
-                        r2max = (float)r[3]; c = (float)r[4]; ih = (float)r[5];
-                    } else {
-                        r2max = (float)r[7]; c = (float)r[2]; ih = (float)r[3];
-                    }
-                    inside = r2 <= r2max;
-                    w = T(ih * ex2_approx(r2 * c));
-                } else {
-                    const T dx = xc[0] - r[0], dy = xc[1] - r[1];
-                    T r2 = dx * dx + dy * dy;
-                    T c, ih;
-                    if (D == 3) {
-                        const T dz = xc[2] - r[2];
-                        r2 += dz * dz;
-                        c = r[4]; ih = r[5];
-                    } else {
-                        c = r[2]; ih = r[3];
-                    }
-                    const T e = r2 * c;        // = -q/2
-                    inside = e >= T(-4.5);
-                    w = ih * exp(e);
+        for (int k0 = 0; k0 < count; k0 += 32) {
+            const int k = k0 + lane;
+            bool ov = false;
+            if (k < count) {
+                const T* r = srec + k * RV;
+                T d2 = T(0);
+#pragma unroll
+                for (int q = 0; q < D; ++q) {
+                    const T dl = wlo[q] - r[q], dh = r[q] - whi[q];
+                    const T dd = dl > T(0) ? dl : (dh > T(0) ? dh : T(0));
+                    d2 += dd * dd;
                 }
-            } else {
-                T P[9];
-                T pref;
-                if (D == 2) {
-                    P[0] = r[4]; P[1] = r[5]; P[2] = r[5]; P[3] = r[6];
-                    pref = r[2];
-                } else {
-                    P[0] = r[4]; P[1] = r[5]; P[2] = r[6];
-                    P[3] = r[5]; P[4] = r[7]; P[5] = r[8];
-                    P[6] = r[6]; P[7] = r[8]; P[8] = r[9];
-                    pref = r[3];
-                }
-                T q;
-                if (sizeof(T) == 4) {
-                    float df[3], pd[3];
-#pragma unroll
-                    for (int i = 0; i < D; ++i) df[i] = __fsub_rn(xcf[i], (float)r[i]);
-#pragma unroll
-                    for (int i = 0; i < D; ++i) {
-                        float s = __fmul_rn((float)P[i * D], df[0]);
-#pragma unroll
-                        for (int k2 = 1; k2 < D; ++k2) s = __fmaf_rn((float)P[i * D + k2], df[k2], s);
-                        pd[i] = s;
-                    }
-                    float qf = __fmul_rn(pd[0], df[0]);
-#pragma unroll
-                    for (int i = 1; i < D; ++i) qf = __fmaf_rn(pd[i], df[i], qf);
-                    inside = qf <= 9.0f;
-                    w = T((float)pref * ex2_approx(qf * -0.72134752044448170368f));
-                    q = T(qf);
-                } else {
-                    T df[3];
-#pragma unroll
-                    for (int i = 0; i < D; ++i) df[i] = xc[i] - r[i];
-                    q = T(0);
-#pragma unroll
-                    for (int i = 0; i < D; ++i)
-#pragma unroll
-                        for (int k2 = 0; k2 < D; ++k2) q += df[i] * P[i * D + k2] * df[k2];
-                    inside = q <= T(9);
-                    w = pref * exp(T(-0.5) * q);
-                }
-                (void)q;
+                ov = d2 <= r[EXT] * T(1.0009765625);
             }
-            if (inside) {
-                const T* am = r + (RV - 4);
-                ++npairs;
-                pD += w;
+            unsigned m = __ballot_sync(0xffffffffu, ov);
+            while (m) {
+                const int j1 = __ffs(m) - 1;
+                m &= m - 1;
+                bool in1;
+                const T w1 = weight_of<T, D, KER>(srec + (k0 + j1) * RV, xcf, xc, in1);
+                const T* am1 = srec + (k0 + j1) * RV + (RV - 4);
+                if (m) {
+                    const int j2 = __ffs(m) - 1;
+                    m &= m - 1;
+                    bool in2;
+                    const T w2 = weight_of<T, D, KER>(srec + (k0 + j2) * RV, xcf, xc, in2);
+                    const T* am2 = srec + (k0 + j2) * RV + (RV - 4);
+                    pD += w1;
 #pragma unroll
-                for (int q2 = 0; q2 <= D; ++q2) pN[q2] = fma(w, am[q2], pN[q2]);
+                    for (int q2 = 0; q2 <= D; ++q2) pN[q2] = fma(w1, am1[q2], pN[q2]);
+                    pD += w2;
+#pragma unroll
+                    for (int q2 = 0; q2 <= D; ++q2) pN[q2] = fma(w2, am2[q2], pN[q2]);
+                    npairs += (int)in1 + (int)in2;
+                } else {
+                    pD += w1;
+#pragma unroll
+                    for (int q2 = 0; q2 <= D; ++q2) pN[q2] = fma(w1, am1[q2], pN[q2]);
+                    npairs += (int)in1;
+                }
             }
         }
         neumaier(sD, cD, pD);
@@ -211,9 +278,6 @@ __global__ void __launch_bounds__(GT) k_nw_gather(GatherArgs a)
                 if (j < end) {
 #pragma unroll
                     for (int v = 0; v < R4; ++v) load4<T>((const T*)a.rec, (int64_t)j * R4 + v, rv + 4 * v);
-                    T e2;
-                    if (KER == FLA_KERNEL_ISO) e2 = D == 2 ? rv[7] : rv[3];
-                    else e2 = D == 2 ? rv[3] : rv[10];
                     T d2 = T(0);
 #pragma unroll
                     for (int q = 0; q < D; ++q) {
@@ -221,7 +285,7 @@ __global__ void __launch_bounds__(GT) k_nw_gather(GatherArgs a)
                         const T dd = dl > T(0) ? dl : (dh > T(0) ? dh : T(0));
                         d2 += dd * dd;
                     }
-                    keep = d2 <= e2 * T(1.0009765625);   // small margin over rounding of the test
+                    keep = d2 <= rv[EXT] * T(1.0009765625);   // small margin over rounding of the test
                 }
                 const unsigned ballot = __ballot_sync(0xffffffffu, keep);
                 if (lane == 0) s_wcount[warp] = __popc(ballot);
@@ -233,7 +297,7 @@ __global__ void __launch_bounds__(GT) k_nw_gather(GatherArgs a)
                 if (keep) {
                     const int pos = off + __popc(ballot & ((1u << lane) - 1u));
 #pragma unroll
-                    for (int v = 0; v < RV; ++v) srec[pos * RV + v] = rv[v];
+                    for (int v = 0; v < R4; ++v) store4<T>(srec, (int64_t)pos * R4 + v, rv + 4 * v);
                 }
                 __syncthreads();
                 if (total > CAP - GT) {

@@ -80,13 +80,15 @@ __host__ __device__ constexpr int acc_offset(int kind, int dim)
 __host__ __device__ constexpr int node_stride(int dim) { return dim == 2 ? 8 : 12; }
 
 // Record of one binned droplet for the kernel-regression gather, in sorted order.
-//   2D iso   (8 values):  x, y, c, inv_h | a_m, a_x, a_y, r2max
-//   3D iso   (12 values): x, y, z, r2max | c, inv_h, 0, 0 | a_m, a_x, a_y, a_z
-//   2D aniso (12 values): x, y, pref, ext2 | P00, P01, P11, 0 | a_m, a_x, a_y, 0
-//   3D aniso (16 values): x, y, z, pref | P00, P01, P02, P11 | P12, P22, ext2, 0 | a_m, a_x, a_y, a_z
-// c = -log2(e)/(2 h^2) in single precision (the weight is inv_h * 2^(c r^2)),
-// c = -1/(2 h^2) in double precision; ext2 = 9 tr(Sigma) bounds the squared
-// support radius; r2max = 9 h^2 rounded to the storage type.
+// Single precision (the weight is 2^(c r^2 + lih), resp. 2^(-q log2(e)/2 + lpref)):
+//   2D iso   (8 values):  x, y, c, lih | a_m, a_x, a_y, r2max
+//   3D iso   (12 values): x, y, z, r2max | c, lih, 0, 0 | a_m, a_x, a_y, a_z
+//   2D aniso (12 values): x, y, lpref, ext2 | P00, P01, P11, 0 | a_m, a_x, a_y, 0
+//   3D aniso (16 values): x, y, z, lpref | P00, P01, P02, P11 | P12, P22, ext2, 0 | a_m, a_x, a_y, a_z
+// with c = -log2(e)/(2 h^2), lih = log2(1/h), lpref = log2(det(Sigma)^-1/2),
+// r2max = 9 h^2 and ext2 = 9 tr(Sigma) (squared support radius bounds).
+// Double precision keeps the same slots with c = -1/(2 h^2), 1/h in place of lih
+// and det(Sigma)^-1/2 in place of lpref (the weight is (1/h) e^(c r^2)).
 __host__ __device__ constexpr int record_values(int dim, int kernel)
 {
     return (dim == 2 && kernel == FLA_KERNEL_ISO) ? 8 : ((dim == 3 && kernel == FLA_KERNEL_ANISO) ? 16 : 12);
@@ -123,6 +125,13 @@ cudaError_t launch_records(const fla_cloud& cl, const fla_mesh& m, const fla_dep
 cudaError_t launch_nw_gather(const fla_cloud& cl, const fla_mesh& m, const fla_deposit_cfg& cfg, const void* rec,
                              const uint32_t* bin_start, const unsigned int* ext_max, const fla_sources& out,
                              DevStatus* st, cudaStream_t s);
+int gather2d_tiles(int N);
+uint32_t gather2d_item_budget(int N, int64_t n);
+size_t gather2d_temp_bytes(int N, int64_t n);
+cudaError_t launch_gather2d(const fla_mesh& m, const fla_deposit_cfg& cfg, const void* rec, const uint32_t* bin_start,
+                            const unsigned int* ext_max, uint32_t* tile_cand, uint32_t* tile_items,
+                            unsigned int* counter, void* temp, uint32_t budget, const fla_sources& out,
+                            DevStatus* st, int num_sms, cudaStream_t s);
 cudaError_t launch_psicell(const fla_cloud& cl, const fla_mesh& m, double window_dt, int per_cell,
                            const uint32_t* perm, const uint32_t* bin_start, void* rec, const fla_psicell_out& out,
                            DevStatus* st, cudaStream_t s);

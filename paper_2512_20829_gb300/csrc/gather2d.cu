@@ -1,0 +1,392 @@
+// Kernel-regression gather for 2D clouds with the spherical kernel in single
+// precision (Eqs. 13-16): the load-balanced, lane-per-record form.
+//
+// Work decomposition.  The mesh is cut into 16x16-cell tiles.  The candidate
+// records of a tile are the records of the cells within R of it (R from the
+// largest support in the cloud); because records are sorted by cell, they are
+// the concatenation of one contiguous segment per neighbourhood row.  A plan
+// kernel counts each tile's candidates and cuts the list into work items of
+// at most kChunk candidates, so that a dense cluster of droplets (a caustic)
+// is spread over many CTAs instead of stalling one.
+//
+// Evaluation.  A persistent CTA of 16 warps takes work items from a counter.
+// Each warp owns a 4x4 block of the tile's cells; it streams the item's
+// candidates from the row segments that can reach its block, keeps (by ballot)
+// the records whose support reaches the block, queues them in a shared-memory
+// ring and, 32 at a time, lets each lane evaluate one record against all 16
+// cells of the block.  The Gaussian is separable, so a lane needs 4 + 4 ex2
+// per record instead of one per cell: w = 2^(c dx^2) * 2^(c dy^2 + log2(1/h)).
+// The truncation test keeps the single-precision form r^2 = fma(dy, dy, dx*dx)
+// <= 9 h^2.  Each lane accumulates its own records; the 32 lane partials of a
+// cell are then combined with Neumaier compensation in lane order, written per
+// work item, and a combine kernel adds the items of a tile in item order
+// (again compensated) and divides.  Every step has a fixed order: the result
+// does not depend on timing.
+#include "fla_internal.cuh"
+
+namespace fla {
+namespace {
+
+constexpr int kTile = 16;          // tile edge in cells
+constexpr int kWarps = 16;         // 4 x 4 blocks of 4 x 4 cells
+constexpr int kThreads = kWarps * 32;
+constexpr int kChunk = 4096;       // candidates per work item
+constexpr int kRing = 64;          // queued records per warp
+constexpr int kScratchFloats = 32 * 33;  // per-warp reduction scratch (padded rows)
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ int support_cells(const unsigned int* ext_max, int N)
+{
+    const float ext2max = __uint_as_float(__ldg(ext_max));
+    return (int)floorf(sqrtf(ext2max) * (float)N + 0.5f) + 1;
+}
+
+struct PlanArgs {
+    const uint32_t* bin_start;
+    const unsigned int* ext_max;
+    uint32_t* tile_cand;
+    uint32_t* tile_items;      // n_tiles + 1
+    int N, tiles_x, n_tiles;
+    uint32_t budget;           // maximum number of work items (temp buffer size)
+};
+
+// Candidates of each tile and the number of work items it needs.
+__global__ void __launch_bounds__(256) k_plan2d(PlanArgs a)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.n_tiles) return;
+    const int N = a.N, R = support_cells(a.ext_max, N);
+    const int tx0 = (t % a.tiles_x) * kTile, ty0 = (t / a.tiles_x) * kTile;
+    const int xlo = max(tx0 - R, 0), xhi = min(tx0 + kTile - 1 + R, N - 1);
+    const int ylo = max(ty0 - R, 0), yhi = min(ty0 + kTile - 1 + R, N - 1);
+    uint32_t cand = 0;
+    for (int y = ylo; y <= yhi; ++y) {
+        const int64_t rb = (int64_t)y * N;
+        cand += __ldg(a.bin_start + rb + xhi + 1) - __ldg(a.bin_start + rb + xlo);
+    }
+    a.tile_cand[t] = cand;
+    a.tile_items[t] = cand ? (cand + kChunk - 1) / kChunk : 0;
+}
+
+// Exclusive scan of the per-tile item counts (one block); if the total exceeds
+// the budget, every non-empty tile gets a single item instead.
+__global__ void __launch_bounds__(1024) k_scan_items(PlanArgs a)
+{
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_total;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int pass = 0; pass < 2; ++pass) {
+        uint32_t running = 0;
+        for (int base = 0; base < a.n_tiles; base += 1024) {
+            const int t = base + tid;
+            uint32_t v = 0;
+            if (t < a.n_tiles) v = pass == 0 ? a.tile_items[t] : (a.tile_cand[t] ? 1u : 0u);
+            uint32_t x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) s_warp[w] = x;
+            __syncthreads();
+            if (w == 0) {
+                uint32_t s = s_warp[lane];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+                    if (lane >= o) s += y;
+                }
+                s_warp[lane] = s;
+            }
+            __syncthreads();
+            const uint32_t excl = running + (w > 0 ? s_warp[w - 1] : 0) + x - v;
+            if (t < a.n_tiles) a.tile_items[t] = excl;
+            running += s_warp[31];
+            __syncthreads();
+        }
+        if (tid == 0) {
+            a.tile_items[a.n_tiles] = running;
+            s_total = running;
+        }
+        __syncthreads();
+        if (pass == 0 && s_total <= a.budget) break;
+    }
+}
+
+struct G2Args {
+    const float4* rec;          // 2 float4 per record: x, y, c, lih | a_m, a_x, a_y, r2max
+    const uint32_t* bin_start;
+    const unsigned int* ext_max;
+    const uint32_t* tile_cand;
+    const uint32_t* tile_items;
+    unsigned int* counter;
+    float4* temp;               // [item][256 cells] of (D, N_m, N_x, N_y)
+    unsigned long long* pairs;
+    int N, tiles_x, n_tiles;
+};
+
+__global__ void __launch_bounds__(kThreads, 1) k_gather2d_items(G2Args a)
+{
+    extern __shared__ __align__(16) float4 smem4[];
+    __shared__ int s_item;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float4* ring = smem4 + warp * (kScratchFloats / 4 + 8);   // per-warp region (ring, then scratch)
+    const int N = a.N;
+    const int R = support_cells(a.ext_max, N);
+    const uint32_t total = __ldg(a.tile_items + a.n_tiles);
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned long long npairs = 0;
+
+    for (;;) {
+        if (tid == 0) s_item = (int)atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const uint32_t item = (uint32_t)s_item;
+        __syncthreads();
+        if (item >= total) break;
+        // tile of this item: last t with tile_items[t] <= item
+        int lo = 0, hi = a.n_tiles - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(a.tile_items + mid) <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const int t = lo;
+        const uint32_t i0 = __ldg(a.tile_items + t), ni = __ldg(a.tile_items + t + 1) - i0;
+        const uint32_t cand = __ldg(a.tile_cand + t);
+        const uint32_t csize = (cand + ni - 1) / ni;
+        const uint32_t c0 = (item - i0) * csize, c1 = min(c0 + csize, cand);
+        const int tx0 = (t % a.tiles_x) * kTile, ty0 = (t / a.tiles_x) * kTile;
+        const int xlo = max(tx0 - R, 0), xhi = min(tx0 + kTile - 1 + R, N - 1);
+        const int ylo = max(ty0 - R, 0), yhi = min(ty0 + kTile - 1 + R, N - 1);
+        // this warp's 4x4 block of cells
+        const int bx0 = tx0 + 4 * (warp & 3), by0 = ty0 + 4 * (warp >> 2);
+        const bool live = bx0 < N && by0 < N;
+        const int bx1 = min(bx0 + 3, N - 1), by1 = min(by0 + 3, N - 1);
+        const float fN = (float)N;
+        float xc[4], yc[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            xc[i] = ((float)(bx0 + i) + 0.5f) / fN;
+            yc[i] = ((float)(by0 + i) + 0.5f) / fN;
+        }
+        const float bxl = ((float)bx0 + 0.5f) / fN, bxh = ((float)bx1 + 0.5f) / fN;
+        const float byl = ((float)by0 + 0.5f) / fN, byh = ((float)by1 + 0.5f) / fN;
+        const int wxlo = max(bx0 - R, xlo), wxhi = min(bx1 + R, xhi);
+        const int wylo = by0 - R, wyhi = by1 + R;
+
+        float acc[16][4];
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[k][q] = 0.0f;
+
+        auto eval = [&](const float4 ra, const float4 rb) {
+            float dxx[4], ex[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float dx = __fsub_rn(xc[i], ra.x);
+                dxx[i] = __fmul_rn(dx, dx);
+                ex[i] = ex2_approx(dxx[i] * ra.z);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float dy = __fsub_rn(yc[j], ra.y);
+                const float ey = ex2_approx(fmaf(dy * dy, ra.z, ra.w));
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float r2 = __fmaf_rn(dy, dy, dxx[i]);   // single-precision decision
+                    const bool in = r2 <= rb.w;
+                    const float w = in ? ex[i] * ey : 0.0f;
+                    float* c = acc[4 * j + i];
+                    c[0] += w;
+                    c[1] = fmaf(w, rb.x, c[1]);
+                    c[2] = fmaf(w, rb.y, c[2]);
+                    c[3] = fmaf(w, rb.z, c[3]);
+                    npairs += in && (bx0 + i < N) && (by0 + j < N);
+                }
+            }
+        };
+
+        uint32_t wr = 0, rd = 0, offset = 0;
+        for (int y = ylo; y <= yhi && offset < c1; ++y) {
+            const int64_t rowb = (int64_t)y * N;
+            const uint32_t beg = __ldg(a.bin_start + rowb + xlo);
+            const uint32_t len = __ldg(a.bin_start + rowb + xhi + 1) - beg;
+            if (live && y >= wylo && y <= wyhi && offset + len > c0 && wxlo <= wxhi) {
+                const uint32_t wb = __ldg(a.bin_start + rowb + wxlo);
+                const uint32_t we = __ldg(a.bin_start + rowb + wxhi + 1);
+                const uint32_t s = max(beg + (c0 > offset ? c0 - offset : 0u), wb);
+                const uint32_t e = min(beg + min(c1 - offset, len), we);
+                for (uint32_t j0 = s; j0 < e; j0 += 32) {
+                    const uint32_t j = j0 + lane;
+                    bool ov = false;
+                    float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra;
+                    if (j < e) {
+                        ra = __ldg(a.rec + 2 * (int64_t)j);
+                        rb = __ldg(a.rec + 2 * (int64_t)j + 1);
+                        const float dl = fmaxf(fmaxf(bxl - ra.x, ra.x - bxh), 0.0f);
+                        const float dm = fmaxf(fmaxf(byl - ra.y, ra.y - byh), 0.0f);
+                        ov = dl * dl + dm * dm <= rb.w * 1.0009765625f;
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, ov);
+                    if (ov) {
+                        const uint32_t slot = (wr + __popc(m & lt)) & (kRing - 1);
+                        ring[2 * slot] = ra;
+                        ring[2 * slot + 1] = rb;
+                    }
+                    wr += __popc(m);
+                    __syncwarp();
+                    if (wr - rd >= 32) {
+                        const uint32_t slot = (rd + lane) & (kRing - 1);
+                        eval(ring[2 * slot], ring[2 * slot + 1]);
+                        rd += 32;
+                        __syncwarp();
+                    }
+                }
+            }
+            offset += len;
+        }
+        if (live && lane < wr - rd) {
+            const uint32_t slot = (rd + lane) & (kRing - 1);
+            eval(ring[2 * slot], ring[2 * slot + 1]);
+        }
+        __syncwarp();
+
+        // combine the 32 lane partials of each value with Neumaier compensation,
+        // 32 values at a time through the warp's scratch (rows padded to 33)
+        float* scr = reinterpret_cast<float*>(ring);
+        float4* out = a.temp + (int64_t)item * (kTile * kTile);
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+#pragma unroll
+            for (int v = 0; v < 32; ++v) scr[lane * 33 + v] = acc[(32 * half + v) >> 2][v & 3];
+            __syncwarp();
+            float sum = 0.0f, comp = 0.0f;
+#pragma unroll 8
+            for (int l = 0; l < 32; ++l) {
+                const float v = scr[l * 33 + lane];
+                const float tt = sum + v;
+                if (fabsf(sum) >= fabsf(v)) comp += (sum - tt) + v;
+                else comp += (v - tt) + sum;
+                sum = tt;
+            }
+            __syncwarp();
+            const int f = 32 * half + lane;      // value f of the block: cell f/4, component f%4
+            const int k = f >> 2;
+            const int local = (4 * (warp & 3) + (k & 3)) + kTile * (4 * (warp >> 2) + (k >> 2));
+            reinterpret_cast<float*>(out + local)[f & 3] = sum + comp;
+        }
+        __syncwarp();
+    }
+    // pairs inside the truncation: one atomic per warp
+    const unsigned long long wsum = __reduce_add_sync(0xffffffffu, (unsigned)npairs);
+    if (lane == 0 && wsum) atomicAdd(a.pairs, wsum);
+}
+
+struct CombineArgs {
+    const float4* temp;
+    const uint32_t* tile_items;
+    int N, tiles_x;
+    float scale;
+    float* s_mass;
+    float* s_mom;
+    float* dsum;
+};
+
+// Sum a cell's work-item partials in item order (compensated) and divide.
+__global__ void __launch_bounds__(256) k_combine2d(CombineArgs a)
+{
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int N = a.N;
+    const int64_t nc = (int64_t)N * N;
+    if (c >= nc) return;
+    const int cx = (int)(c % N), cy = (int)(c / N);
+    const int t = (cy / kTile) * a.tiles_x + cx / kTile;
+    const int local = (cx % kTile) + kTile * (cy % kTile);
+    const uint32_t i0 = __ldg(a.tile_items + t), i1 = __ldg(a.tile_items + t + 1);
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, cmp[4] = {0.f, 0.f, 0.f, 0.f};
+    for (uint32_t it = i0; it < i1; ++it) {
+        const float4 v = __ldg(a.temp + (int64_t)it * (kTile * kTile) + local);
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float tt = s[q] + vv[q];
+            if (fabsf(s[q]) >= fabsf(vv[q])) cmp[q] += (s[q] - tt) + vv[q];
+            else cmp[q] += (vv[q] - tt) + s[q];
+            s[q] = tt;
+        }
+    }
+    const float D = s[0] + cmp[0];
+    const bool cov = D > 0.0f;
+    a.s_mass[c] = cov ? -(s[1] + cmp[1]) / D * a.scale : 0.0f;
+    a.s_mom[c] = cov ? -(s[2] + cmp[2]) / D * a.scale : 0.0f;
+    a.s_mom[nc + c] = cov ? -(s[3] + cmp[3]) / D * a.scale : 0.0f;
+    if (a.dsum) a.dsum[c] = D;
+}
+
+}  // namespace
+
+int gather2d_tiles(int N) { return ((N + kTile - 1) / kTile) * ((N + kTile - 1) / kTile); }
+
+uint32_t gather2d_item_budget(int N, int64_t n)
+{
+    return (uint32_t)(gather2d_tiles(N) + (16 * (n > 0 ? n : 1) + kChunk - 1) / kChunk + 1);
+}
+
+size_t gather2d_temp_bytes(int N, int64_t n) { return (size_t)gather2d_item_budget(N, n) * kTile * kTile * 16; }
+
+cudaError_t launch_gather2d(const fla_mesh& m, const fla_deposit_cfg& cfg, const void* rec, const uint32_t* bin_start,
+                            const unsigned int* ext_max, uint32_t* tile_cand, uint32_t* tile_items,
+                            unsigned int* counter, void* temp, uint32_t budget, const fla_sources& out,
+                            DevStatus* st, int num_sms, cudaStream_t s)
+{
+    const int N = m.n;
+    const int tiles_x = (N + kTile - 1) / kTile;
+    const int n_tiles = tiles_x * tiles_x;
+    PlanArgs p{bin_start, ext_max, tile_cand, tile_items, N, tiles_x, n_tiles, budget};
+    k_plan2d<<<(n_tiles + 255) / 256, 256, 0, s>>>(p);
+    k_scan_items<<<1, 1024, 0, s>>>(p);
+    cudaError_t e = cudaMemsetAsync(counter, 0, 4, s);
+    if (e != cudaSuccess) return e;
+    G2Args g{};
+    g.rec = (const float4*)rec;
+    g.bin_start = bin_start;
+    g.ext_max = ext_max;
+    g.tile_cand = tile_cand;
+    g.tile_items = tile_items;
+    g.counter = counter;
+    g.temp = (float4*)temp;
+    g.pairs = &st->pairs;
+    g.N = N;
+    g.tiles_x = tiles_x;
+    g.n_tiles = n_tiles;
+    const size_t smem = (size_t)kWarps * (kScratchFloats / 4 + 8) * sizeof(float4);
+    static bool attr_set = false;   // set once, before any stream capture that uses it
+    if (!attr_set) {
+        e = cudaFuncSetAttribute(k_gather2d_items, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_gather2d_items<<<num_sms, kThreads, smem, s>>>(g);
+    CombineArgs c{};
+    c.temp = (const float4*)temp;
+    c.tile_items = tile_items;
+    c.N = N;
+    c.tiles_x = tiles_x;
+    const double dx = 1.0 / N;
+    c.scale = cfg.per_cell ? (float)(dx * dx) : 1.0f;
+    c.s_mass = (float*)out.s_mass_dev;
+    c.s_mom = (float*)out.s_mom_dev;
+    c.dsum = (float*)out.dsum_dev;
+    const int64_t nc = (int64_t)N * N;
+    k_combine2d<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(c);
+    return cudaGetLastError();
+}
+
+}  // namespace fla

@@ -1,14 +1,20 @@
 // Droplet records for the kernel-regression gather, written in sorted order.
 //
 // Per binned droplet (Eq. 6, Eq. 15, Eq. 14 and App. B parcel level c):
-//   det J in double precision from the stored J,
 //   n = n0 / max(|det J|, 1e-12),  a = n * acc / T_window,
 //   ISO:   h = clamp(h0 |det J|^p, h_min, h_max), weight (1/h) exp(-r^2/(2 h^2)),
 //   ANISO: Sigma = f h0^2 J J^T + h_min^2 I, f = min(1, (h_max^2 - d h_min^2)/tr(h0^2 J J^T)),
 //          weight det(Sigma)^-1/2 exp(-d^T Sigma^-1 d / 2).
-// This file is compiled without FMA contraction: the double-precision values
-// that decide the truncation test (h, Sigma^-1) are formed with one rounding
-// per operation in a fixed order, so the decision is reproducible.
+//
+// Precision (single-precision path): det J is formed in double where it can
+// cancel -- always in 2D (the products of single-precision entries are exact
+// in double), and in 3D when the single-precision cofactor expansion is below
+// 1e-2 of the product of the rows' L1 norms (near a fold caustic, where det J
+// nearly vanishes).  Everything else is single precision; double-precision
+// division and square root, which are slow on this GPU, are not used.
+// The values that decide the truncation test (h and 9 h^2; Sigma^-1) are
+// formed one rounding per operation in a fixed order: this file is compiled
+// without FMA contraction so that the decision is reproducible.
 #include "fla_internal.cuh"
 
 namespace fla {
@@ -22,27 +28,227 @@ struct RecArgs {
     const uint32_t* bin_start;
     int64_t n;
     int64_t n_cells;
-    int kernel;
     double h_min, h_max, p, window_dt;
+    float inv_window;           // 1 / window_dt
+    float room;                 // (float)(h_max^2 - d h_min^2)
+    float hmin2;                // (float)(h_min^2)
     void* rec;
     unsigned int* ext_max;      // max over droplets of the squared support radius (float bits)
     DevStatus* status;
 };
 
 template <typename T, int D>
-__device__ __forceinline__ double det_of(const T* J)
+__device__ __forceinline__ double det_double(const T* J)
 {
     if (D == 2) return (double)J[0] * (double)J[3] - (double)J[1] * (double)J[2];
     const double j0 = J[0], j1 = J[1], j2 = J[2], j3 = J[3], j4 = J[4], j5 = J[5], j6 = J[6], j7 = J[7], j8 = J[8];
     return j0 * (j4 * j8 - j5 * j7) - j1 * (j3 * j8 - j5 * j6) + j2 * (j3 * j7 - j4 * j6);
 }
 
+// det J for the single-precision path: double where it can cancel.
+template <int D>
+__device__ __forceinline__ double det_mixed(const float* j)
+{
+    if (D == 2) return det_double<float, 2>(j);
+    const float detf = j[0] * (j[4] * j[8] - j[5] * j[7]) - j[1] * (j[3] * j[8] - j[5] * j[6]) +
+                       j[2] * (j[3] * j[7] - j[4] * j[6]);
+    const float H = (fabsf(j[0]) + fabsf(j[1]) + fabsf(j[2])) * (fabsf(j[3]) + fabsf(j[4]) + fabsf(j[5])) *
+                    (fabsf(j[6]) + fabsf(j[7]) + fabsf(j[8]));
+    if (fabsf(detf) < 0.01f * H) return det_double<float, 3>(j);   // near a fold: FP64
+    return (double)detf;
+}
+
+// Sigma and its inverse in single precision, in a fixed order (see file header).
+template <int D>
+__device__ __forceinline__ void sigma_inverse_f32(const float* j, float h0f, float room, float hmin2, float* P,
+                                                  float& dS, float& tr)
+{
+    float S[D * D];
+    const float h02 = h0f * h0f;
+    float tr0 = 0.0f;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            float sum = 0.0f;
+#pragma unroll
+            for (int q = 0; q < D; ++q) sum = sum + j[i * D + q] * j[k * D + q];
+            S[i * D + k] = h02 * sum;
+            if (i == k) tr0 = tr0 + S[i * D + k];
+        }
+    if (tr0 > room) {
+        const float f = room / tr0;
+#pragma unroll
+        for (int q = 0; q < D * D; ++q) S[q] = S[q] * f;
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) S[i * D + i] = S[i * D + i] + hmin2;
+    tr = 0.0f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) tr = tr + S[i * D + i];
+    if (D == 2) {
+        dS = S[0] * S[3] - S[1] * S[2];
+        const float inv = 1.0f / dS;
+        P[0] = S[3] * inv; P[3] = S[0] * inv; P[1] = -S[1] * inv; P[2] = P[1];
+    } else {
+        const float c00 = S[4] * S[8] - S[5] * S[7];
+        const float c01 = S[5] * S[6] - S[3] * S[8];
+        const float c02 = S[3] * S[7] - S[4] * S[6];
+        const float c11 = S[0] * S[8] - S[2] * S[6];
+        const float c12 = S[2] * S[3] - S[0] * S[5];
+        const float c22 = S[0] * S[4] - S[1] * S[3];
+        dS = S[0] * c00 + S[1] * c01 + S[2] * c02;
+        const float inv = 1.0f / dS;
+        P[0] = c00 * inv; P[1] = c01 * inv; P[2] = c02 * inv;
+        P[3] = P[1];      P[4] = c11 * inv; P[5] = c12 * inv;
+        P[6] = P[2];      P[7] = P[5];      P[8] = c22 * inv;
+    }
+}
+
+// Single-precision record.  Layouts: see fla_internal.cuh (c = -log2(e)/(2 h^2),
+// lih = log2(1/h), lpref = log2(det(Sigma)^-1/2): the weight is 2^(c r^2 + lih)).
+template <int D, int KER>
+__device__ __forceinline__ void record_f32(const RecArgs& a, const float* sv, double n0, double h0, float* r,
+                                           float& ext2, bool& bad)
+{
+    constexpr int OA = acc_offset(FLA_CLOUD_FLA, D);
+    const float* J = sv + 2 * D;
+    const double adet = fabs(det_mixed<D>(J));
+    const float n = (float)n0 / fmaxf((float)adet, 1e-12f);
+    float am[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int q = 0; q <= D; ++q) am[q] = n * sv[OA + q] * a.inv_window;
+    if (KER == FLA_KERNEL_ISO) {
+        double h = (a.p == 1.0) ? h0 * adet : h0 * pow(adet, a.p);
+        h = h < a.h_min ? a.h_min : h;
+        h = h > a.h_max ? a.h_max : h;
+        const float hf = (float)h;
+        const float r2max = (float)(9.0 * (double)hf * (double)hf);
+        const float c = -0.72134752044448170368f / (hf * hf);
+        const float lih = -log2f(hf);
+        if (D == 2) {
+            r[0] = sv[0]; r[1] = sv[1]; r[2] = c; r[3] = lih;
+            r[4] = am[0]; r[5] = am[1]; r[6] = am[2]; r[7] = r2max;
+        } else {
+            r[0] = sv[0]; r[1] = sv[1]; r[2] = sv[2]; r[3] = r2max;
+            r[4] = c; r[5] = lih;
+            r[8] = am[0]; r[9] = am[1]; r[10] = am[2]; r[11] = am[3];
+        }
+        ext2 = r2max;
+        bad = !isfinite(n) || !isfinite(hf);
+    } else {
+        float P[9], dS, tr;
+        sigma_inverse_f32<D>(J, (float)h0, a.room, a.hmin2, P, dS, tr);
+        const float lpref = -0.5f * log2f(dS);
+        const float e2 = 9.0f * tr;
+        if (D == 2) {
+            r[0] = sv[0]; r[1] = sv[1]; r[2] = lpref; r[3] = e2;
+            r[4] = P[0]; r[5] = P[1]; r[6] = P[3];
+            r[8] = am[0]; r[9] = am[1]; r[10] = am[2];
+        } else {
+            r[0] = sv[0]; r[1] = sv[1]; r[2] = sv[2]; r[3] = lpref;
+            r[4] = P[0]; r[5] = P[1]; r[6] = P[2]; r[7] = P[4];
+            r[8] = P[5]; r[9] = P[8]; r[10] = e2;
+            r[12] = am[0]; r[13] = am[1]; r[14] = am[2]; r[15] = am[3];
+        }
+        ext2 = e2;
+        bad = !isfinite(n) || !(dS > 0.0f) || !isfinite(dS);
+    }
+#pragma unroll
+    for (int q = 0; q <= D; ++q) bad |= !isfinite(am[q]);
+}
+
+// Double-precision record (the FP64 path): c = -1/(2 h^2), ih = 1/h, pref = det(Sigma)^-1/2.
+template <int D, int KER>
+__device__ __forceinline__ void record_f64(const RecArgs& a, const double* sv, double n0, double h0, double* r,
+                                           float& ext2, bool& bad)
+{
+    constexpr int OA = acc_offset(FLA_CLOUD_FLA, D);
+    const double* J = sv + 2 * D;
+    const double adet = fabs(det_double<double, D>(J));
+    const double nd = n0 / (adet > 1e-12 ? adet : 1e-12);
+    double am[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int q = 0; q <= D; ++q) am[q] = nd * sv[OA + q] / a.window_dt;
+    if (KER == FLA_KERNEL_ISO) {
+        double h = (a.p == 1.0) ? h0 * adet : h0 * pow(adet, a.p);
+        h = h < a.h_min ? a.h_min : h;
+        h = h > a.h_max ? a.h_max : h;
+        const double r2max = 9.0 * h * h;
+        const double c = -0.5 / (h * h);
+        const double ih = 1.0 / h;
+        if (D == 2) {
+            r[0] = sv[0]; r[1] = sv[1]; r[2] = c; r[3] = ih;
+            r[4] = am[0]; r[5] = am[1]; r[6] = am[2]; r[7] = r2max;
+        } else {
+            r[0] = sv[0]; r[1] = sv[1]; r[2] = sv[2]; r[3] = r2max;
+            r[4] = c; r[5] = ih;
+            r[8] = am[0]; r[9] = am[1]; r[10] = am[2]; r[11] = am[3];
+        }
+        ext2 = (float)r2max;
+        bad = !isfinite(nd) || !isfinite(h);
+    } else {
+        double Sg[9];
+        double tr0 = 0.0;
+#pragma unroll
+        for (int ii = 0; ii < D; ++ii)
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                double s = 0.0;
+#pragma unroll
+                for (int jj = 0; jj < D; ++jj) s += J[ii * D + jj] * J[k * D + jj];
+                Sg[ii * D + k] = h0 * h0 * s;
+                if (ii == k) tr0 += Sg[ii * D + k];
+            }
+        const double room = a.h_max * a.h_max - (double)D * a.h_min * a.h_min;
+        if (tr0 > room) {
+            const double f = room / tr0;
+#pragma unroll
+            for (int q = 0; q < D * D; ++q) Sg[q] *= f;
+        }
+#pragma unroll
+        for (int ii = 0; ii < D; ++ii) Sg[ii * D + ii] += a.h_min * a.h_min;
+        double tr = 0.0;
+#pragma unroll
+        for (int ii = 0; ii < D; ++ii) tr += Sg[ii * D + ii];
+        double P[9], dS;
+        if (D == 2) {
+            dS = Sg[0] * Sg[3] - Sg[1] * Sg[2];
+            P[0] = Sg[3] / dS; P[3] = Sg[0] / dS; P[1] = -Sg[1] / dS;
+        } else {
+            const double c00 = Sg[4] * Sg[8] - Sg[5] * Sg[7];
+            const double c01 = Sg[5] * Sg[6] - Sg[3] * Sg[8];
+            const double c02 = Sg[3] * Sg[7] - Sg[4] * Sg[6];
+            const double c11 = Sg[0] * Sg[8] - Sg[2] * Sg[6];
+            const double c12 = Sg[2] * Sg[3] - Sg[0] * Sg[5];
+            const double c22 = Sg[0] * Sg[4] - Sg[1] * Sg[3];
+            dS = Sg[0] * c00 + Sg[1] * c01 + Sg[2] * c02;
+            P[0] = c00 / dS; P[1] = c01 / dS; P[2] = c02 / dS;
+            P[4] = c11 / dS; P[5] = c12 / dS; P[8] = c22 / dS;
+        }
+        const double pref = 1.0 / sqrt(dS);
+        const double e2 = 9.0 * tr;
+        if (D == 2) {
+            r[0] = sv[0]; r[1] = sv[1]; r[2] = pref; r[3] = e2;
+            r[4] = P[0]; r[5] = P[1]; r[6] = P[3];
+            r[8] = am[0]; r[9] = am[1]; r[10] = am[2];
+        } else {
+            r[0] = sv[0]; r[1] = sv[1]; r[2] = sv[2]; r[3] = pref;
+            r[4] = P[0]; r[5] = P[1]; r[6] = P[2]; r[7] = P[4];
+            r[8] = P[5]; r[9] = P[8]; r[10] = e2;
+            r[12] = am[0]; r[13] = am[1]; r[14] = am[2]; r[15] = am[3];
+        }
+        ext2 = (float)e2;
+        bad = !isfinite(nd) || !(dS > 0.0) || !isfinite(dS);
+    }
+#pragma unroll
+    for (int q = 0; q <= D; ++q) bad |= !isfinite(am[q]);
+}
+
 template <typename T, int D, int KER>
 __global__ void __launch_bounds__(256) k_records(RecArgs a)
 {
     constexpr int NP = state_planes(FLA_CLOUD_FLA, D);
-    constexpr int OJ = 2 * D;
-    constexpr int OA = acc_offset(FLA_CLOUD_FLA, D);
     constexpr int RV = record_values(D, KER);
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nvalid = a.bin_start[a.n_cells];
@@ -55,97 +261,16 @@ __global__ void __launch_bounds__(256) k_records(RecArgs a)
         for (int p = 0; p < NP; ++p) load4<T>((const T*)a.state, p * a.n + i, sv + 4 * p);
         const fla_batch* B = a.batches + (a.meta[i] & FLA_META_BATCH_MASK);
         const double n0 = __ldg(&B->n0), h0 = __ldg(&B->h0);
-        const T* J = sv + OJ;
-        const double det = det_of<T, D>(J);
-        const double adet = fabs(det);
-        const double nd = n0 / (adet > 1e-12 ? adet : 1e-12);
         T r[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) r[q] = T(0);
-        T am[4];
-#pragma unroll
-        for (int q = 0; q <= D; ++q) am[q] = T(nd * (double)sv[OA + q] / a.window_dt);
-        if (KER == FLA_KERNEL_ISO) {
-            double h = (a.p == 1.0) ? h0 * adet : h0 * pow(adet, a.p);
-            h = h < a.h_min ? a.h_min : h;
-            h = h > a.h_max ? a.h_max : h;
-            const T hT = T(h);
-            const T r2max = T(9.0 * (double)hT * (double)hT);
-            const T c = sizeof(T) == 4 ? T(-0.72134752044448170368 / (h * h)) : T(-0.5 / (h * h));
-            const T inv_h = T(1.0 / h);
-            if (D == 2) {
-                r[0] = sv[0]; r[1] = sv[1]; r[2] = c; r[3] = inv_h;
-                r[4] = am[0]; r[5] = am[1]; r[6] = am[2]; r[7] = r2max;
-            } else {
-                r[0] = sv[0]; r[1] = sv[1]; r[2] = sv[2]; r[3] = r2max;
-                r[4] = c; r[5] = inv_h;
-                r[8] = am[0]; r[9] = am[1]; r[10] = am[2]; r[11] = am[3];
-            }
-            ext2 = (float)r2max;
-            bad = !isfinite(nd) || !isfinite(h);
-        } else {
-            double Sg[9];
-            double tr0 = 0.0;
-#pragma unroll
-            for (int ii = 0; ii < D; ++ii)
-#pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    double s = 0.0;
-#pragma unroll
-                    for (int jj = 0; jj < D; ++jj) s += (double)J[ii * D + jj] * (double)J[k * D + jj];
-                    Sg[ii * D + k] = h0 * h0 * s;
-                    if (ii == k) tr0 += Sg[ii * D + k];
-                }
-            const double room = a.h_max * a.h_max - (double)D * a.h_min * a.h_min;
-            if (tr0 > room) {
-                const double f = room / tr0;
-#pragma unroll
-                for (int q = 0; q < D * D; ++q) Sg[q] *= f;
-            }
-#pragma unroll
-            for (int ii = 0; ii < D; ++ii) Sg[ii * D + ii] += a.h_min * a.h_min;
-            double tr = 0.0;
-#pragma unroll
-            for (int ii = 0; ii < D; ++ii) tr += Sg[ii * D + ii];
-            double P[9];
-            double dS;
-            if (D == 2) {
-                dS = Sg[0] * Sg[3] - Sg[1] * Sg[2];
-                P[0] = Sg[3] / dS; P[3] = Sg[0] / dS; P[1] = -Sg[1] / dS; P[2] = P[1];
-            } else {
-                dS = Sg[0] * (Sg[4] * Sg[8] - Sg[5] * Sg[7]) - Sg[1] * (Sg[3] * Sg[8] - Sg[5] * Sg[6]) +
-                     Sg[2] * (Sg[3] * Sg[7] - Sg[4] * Sg[6]);
-                const double c00 = Sg[4] * Sg[8] - Sg[5] * Sg[7];
-                const double c01 = Sg[5] * Sg[6] - Sg[3] * Sg[8];
-                const double c02 = Sg[3] * Sg[7] - Sg[4] * Sg[6];
-                const double c11 = Sg[0] * Sg[8] - Sg[2] * Sg[6];
-                const double c12 = Sg[2] * Sg[3] - Sg[0] * Sg[5];
-                const double c22 = Sg[0] * Sg[4] - Sg[1] * Sg[3];
-                P[0] = c00 / dS; P[1] = c01 / dS; P[2] = c02 / dS;
-                P[4] = c11 / dS; P[5] = c12 / dS; P[8] = c22 / dS;
-            }
-            const T pref = T(1.0 / sqrt(dS));
-            const T e2 = T(9.0 * tr);
-            if (D == 2) {
-                r[0] = sv[0]; r[1] = sv[1]; r[2] = pref; r[3] = e2;
-                r[4] = T(P[0]); r[5] = T(P[1]); r[6] = T(P[3]);
-                r[8] = am[0]; r[9] = am[1]; r[10] = am[2];
-            } else {
-                r[0] = sv[0]; r[1] = sv[1]; r[2] = sv[2]; r[3] = pref;
-                r[4] = T(P[0]); r[5] = T(P[1]); r[6] = T(P[2]); r[7] = T(P[4]);
-                r[8] = T(P[5]); r[9] = T(P[8]); r[10] = e2;
-                r[12] = am[0]; r[13] = am[1]; r[14] = am[2]; r[15] = am[3];
-            }
-            ext2 = (float)e2;
-            bad = !isfinite(nd) || !(dS > 0.0) || !isfinite(dS);
-        }
-#pragma unroll
-        for (int q = 0; q <= D; ++q) bad |= !isfinite((double)am[q]);
+        if (sizeof(T) == 4) record_f32<D, KER>(a, (const float*)sv, n0, h0, (float*)r, ext2, bad);
+        else record_f64<D, KER>(a, (const double*)sv, n0, h0, (double*)r, ext2, bad);
 #pragma unroll
         for (int v = 0; v < RV / 4; ++v) store4<T>((T*)a.rec, j * (RV / 4) + v, r + 4 * v);
         if (!(ext2 >= 0.0f) || !isfinite(ext2)) ext2 = 0.0f;
     }
-    // block maximum of the support extent, one atomic per block
+    // block maximum of the support extent and the counters: one atomic each per block
     __shared__ float s_ext[8];
     __shared__ unsigned s_bad[8];
     float e = ext2;
@@ -161,10 +286,9 @@ __global__ void __launch_bounds__(256) k_records(RecArgs a)
     if (threadIdx.x == 0) {
         float m = 0.0f;
         unsigned nb = 0;
-        int cnt = 0;
         for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { m = fmaxf(m, s_ext[q]); nb += s_bad[q]; }
         const int64_t lo = blockIdx.x * (int64_t)blockDim.x;
-        cnt = (int)(nvalid > lo ? ((nvalid - lo) < (int64_t)blockDim.x ? (nvalid - lo) : (int64_t)blockDim.x) : 0);
+        const int64_t cnt = nvalid > lo ? ((nvalid - lo) < (int64_t)blockDim.x ? (nvalid - lo) : (int64_t)blockDim.x) : 0;
         if (m > 0.0f) atomicMax(a.ext_max, __float_as_uint(m));
         if (nb) atomicAdd(&a.status->nonfinite, (unsigned long long)nb);
         if (cnt) atomicAdd(&a.status->deposited, (unsigned long long)cnt);
@@ -193,11 +317,13 @@ cudaError_t launch_records(const fla_cloud& cl, const fla_mesh& m, const fla_dep
     a.bin_start = bin_start;
     a.n = cl.n;
     a.n_cells = n_cells;
-    a.kernel = cfg.kernel;
     a.h_min = cfg.h_min;
     a.h_max = cfg.h_max;
     a.p = cfg.p;
     a.window_dt = cfg.window_dt;
+    a.inv_window = (float)(1.0 / cfg.window_dt);
+    a.room = (float)(cfg.h_max * cfg.h_max - (double)m.dim * cfg.h_min * cfg.h_min);
+    a.hmin2 = (float)(cfg.h_min * cfg.h_min);
     a.rec = rec;
     a.ext_max = ext_max;
     a.status = st;
