@@ -194,8 +194,8 @@ def timed_replays(path, g, steps, flush, events=True):
 def roofline_entry(phase_name, prof, peaks, clocks, status_pairs, droplet_steps_per_run, runs):
     """Roofline of the dominant phase from the instrumented run's CUDA-event times."""
     p = prof[phase_name]
-    launches = max(p["launches"], 1)
-    ms_per_launch = p["ms"] / launches
+    calls = max(p["calls"], 1)
+    ms_per_launch = p["ms"] / calls      # one call = one launch of the phase's kernel(s)
     sm_max = 2070.0
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s at the maximum SM clock
     mufu_peak_pairs = 152 * 16 * sm_max * 1e6                # ex2 per second
@@ -211,7 +211,7 @@ def roofline_entry(phase_name, prof, peaks, clocks, status_pairs, droplet_steps_
         ach = flops / (ms_per_launch * 1e-3) / 1e12
         peak = min(fp32_peak, mufu_peak_pairs * FLOPS_PER_PAIR_ISO2D / 1e12)
         return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "kernel": "k_nw_gather<float,2,ISO>",
+                "traffic": None, "kernel": "gather (plan + k_gather2d_items + combine)",
                 "peak_basis": "min(FP32 152x128x2, MUFU ex2 152x16 per pair x 15 flops) at 2070 MHz (derived)"}
     # HBM-bound phases: algorithmic bytes
     return {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s", "frac": None,

@@ -278,7 +278,7 @@ int fla_sync_status(fla_ctx* ctx, fla_stream_t stream, fla_device_status* out, i
  * the device or because another framework has reserved the memory.
  *
  * Same inputs, outputs and results as fla_cell_bins (bit for bit), but the
- * scratch space is a fixed array compiled into the library (about 4.2 MB of
+ * scratch space is a fixed array compiled into the library (about 5.3 MB of
  * device memory on every GPU that loads the library, held until the process
  * exits) and no fla_ctx is needed.  The call allocates nothing.
  *  - Clouds of more than FLA_NOALLOC_MAX_DROPLETS droplets are rejected with

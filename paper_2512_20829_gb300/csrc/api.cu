@@ -56,15 +56,14 @@ WsLayout layout(const fla_mesh& m, int dtype, int kernel, int64_t n)
 {
     WsLayout L{};
     const size_t nn = (size_t)(n > 0 ? n : 1);
-    const size_t tiles = (size_t)radix_tiles(n > 0 ? n : 1);
     const size_t T = dtype == FLA_F64 ? 8 : 4;
     const size_t rv = (size_t)record_values(m.dim, kernel);
     const size_t rec_bytes = nn * T * (rv > 4 ? rv : 4);
     size_t o = 0;
     for (int b = 0; b < 2; ++b) { L.keys[b] = o; o += up256(nn * 4); }
     for (int b = 0; b < 2; ++b) { L.vals[b] = o; o += up256(nn * 4); }
-    L.counts = o; o += up256(256 * tiles * 4);
-    L.totals = o; o += up256(256 * 4);
+    L.counts = o; o += up256((size_t)sort_counts_words(n) * 4);
+    L.totals = o; o += up256((size_t)kSortTotalsWords * 4);
     L.bin_start = o; o += up256(((size_t)cells_of(m) + 1) * 4);
     L.misc = o; o += 256;
     L.rec = o; o += up256(rec_bytes);
@@ -137,7 +136,7 @@ int bin_cloud(fla_ctx* ctx, const fla_cloud& c, const fla_mesh& m, void* ws, con
     }
     if (e != cudaSuccess) return FLA_ERR_CUDA;
     const int bits = sort_bits((uint32_t)nc);
-    const int passes = sort_passes(bits);
+    const int passes = sort_passes_n(bits, c.n);
     {
         PhaseScope ps(ctx, FLA_PHASE_SORT, s, 3 * passes);
         e = launch_radix_sort(w, c.n, bits, 0, s);

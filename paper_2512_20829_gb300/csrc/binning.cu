@@ -1,8 +1,8 @@
 // Cell binning: integer cell keys, a stable LSD radix sort of (key, index)
 // and the per-cell bin starts.  All integer work: bit-exact and deterministic.
 //
-// The sort processes tiles of 4,096 keys (256 threads x 16).  Per pass of a
-// digit of up to 8 bits: (1) per-tile digit histograms, (2) per-digit
+// The sort processes tiles of 2,048 keys (256 threads x 8).  Per pass of a
+// digit of up to 11 bits: (1) per-tile digit histograms, (2) per-digit
 // exclusive scans over tiles, (3) a stable scatter in which each warp ranks
 // its keys with __match_any_sync and per-warp running digit counters, so a
 // key's destination depends only on the input order.
@@ -12,9 +12,11 @@ namespace fla {
 namespace {
 
 constexpr int RS_THREADS = 256;
-constexpr int RS_ITEMS = 16;
-constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+constexpr int RS_ITEMS = 8;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;    // 2,048 keys per tile
+static_assert(RS_TILE == kSortTile, "tile size shared with the scratch sizes");
 constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_MAX_DIGITS = 2048;               // digits of up to 11 bits
 
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_cell_keys(const T* __restrict__ state, const uint32_t* __restrict__ meta,
@@ -41,17 +43,17 @@ __global__ void __launch_bounds__(256) k_cell_keys(const T* __restrict__ state, 
 __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
                                                            int width, uint32_t* __restrict__ counts, int tiles)
 {
-    __shared__ uint32_t h[256];
+    __shared__ uint32_t h[RS_MAX_DIGITS];
     const int nd = 1 << width;
-    for (int t = threadIdx.x; t < 256; t += RS_THREADS) h[t] = 0;
+    for (int t = threadIdx.x; t < nd; t += RS_THREADS) h[t] = 0;
     __syncthreads();
     const int64_t base = blockIdx.x * (int64_t)RS_TILE;
     const int lane = threadIdx.x & 31;
-#pragma unroll 4
+#pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
         const int64_t j = base + k * RS_THREADS + threadIdx.x;
         const bool valid = j < n;
-        const uint32_t dg = valid ? (keys[j] >> shift) & (uint32_t)(nd - 1) : 0x100u;
+        const uint32_t dg = valid ? (keys[j] >> shift) & (uint32_t)(nd - 1) : 0xFFFFu;
         const unsigned peers = __match_any_sync(0xffffffffu, dg);
         if (valid && (__ffs(peers) - 1) == lane) atomicAdd(&h[dg], (uint32_t)__popc(peers));
     }
@@ -112,18 +114,31 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint32_t* __
                                                               const uint32_t* __restrict__ counts,
                                                               const uint32_t* __restrict__ totals, int tiles)
 {
-    __shared__ uint32_t s_base[256];
-    __shared__ uint32_t s_cnt[RS_WARPS][256];
+    __shared__ uint32_t s_base[RS_MAX_DIGITS];
+    __shared__ uint16_t s_cnt[RS_WARPS][RS_MAX_DIGITS];
     __shared__ uint32_t s_warp[RS_WARPS];
     const int nd = 1 << width;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    // digit bases: exclusive scan of the digit totals plus this tile's offset
     {
-        const uint32_t t = tid < nd ? totals[tid] : 0;
+        constexpr int PER = RS_MAX_DIGITS / RS_THREADS;   // 8 digits per thread
+        uint32_t v[PER], sum = 0;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int d = tid * PER + q;
+            v[q] = d < nd ? totals[d] : 0;
+            sum += v[q];
+        }
         uint32_t tot;
-        const uint32_t ex = block_exclusive_scan(t, s_warp, tot);
-        s_base[tid] = ex + (tid < nd ? counts[(int64_t)tid * tiles + blockIdx.x] : 0);
+        uint32_t ex = block_exclusive_scan(sum, s_warp, tot);
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int d = tid * PER + q;
+            if (d < nd) s_base[d] = ex + counts[(int64_t)d * tiles + blockIdx.x];
+            ex += v[q];
+        }
     }
-    for (int q = tid; q < RS_WARPS * 256; q += RS_THREADS) (&s_cnt[0][0])[q] = 0;
+    for (int q = tid; q < RS_WARPS * RS_MAX_DIGITS; q += RS_THREADS) (&s_cnt[0][0])[q] = 0;
     __syncthreads();
 
     const int64_t wbase = blockIdx.x * (int64_t)RS_TILE + w * (RS_ITEMS * 32);
@@ -135,23 +150,23 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint32_t* __
         const bool valid = j < n;
         const uint32_t kk = valid ? kin[j] : 0u;
         const uint32_t vv = valid ? (vin ? vin[j] : (uint32_t)j) : 0u;
-        const uint32_t dg = valid ? (kk >> shift) & (uint32_t)(nd - 1) : 0x100u;
+        const uint32_t dg = valid ? (kk >> shift) & (uint32_t)(nd - 1) : 0xFFFFu;
         const unsigned peers = __match_any_sync(0xffffffffu, dg);
         const uint32_t before = valid ? s_cnt[w][dg] : 0u;
         __syncwarp();
-        if (valid && (peers & lt) == 0) s_cnt[w][dg] = before + (uint32_t)__popc(peers);
+        if (valid && (peers & lt) == 0) s_cnt[w][dg] = (uint16_t)(before + (uint32_t)__popc(peers));
         __syncwarp();
         key[k] = kk;
         val[k] = vv;
         rank[k] = valid ? before + (uint32_t)__popc(peers & lt) : 0xffffffffu;
     }
     __syncthreads();
-    if (tid < nd) {   // exclusive scan across warps, per digit (warp order = input order)
+    for (int d = tid; d < nd; d += RS_THREADS) {   // exclusive scan across warps, per digit
         uint32_t run = 0;
 #pragma unroll
         for (int ww = 0; ww < RS_WARPS; ++ww) {
-            const uint32_t c = s_cnt[ww][tid];
-            s_cnt[ww][tid] = run;
+            const uint32_t c = s_cnt[ww][d];
+            s_cnt[ww][d] = (uint16_t)run;
             run += c;
         }
     }
@@ -192,7 +207,17 @@ int sort_bits(uint32_t max_key)
 
 int radix_tiles(int64_t n) { return (int)((n + RS_TILE - 1) / RS_TILE); }
 
-int sort_passes(int bits) { return (bits + 7) / 8; }
+// Digits of up to 11 bits (2 passes for the meshes used here) while the per-tile
+// digit counts stay small next to the keys; 8-bit digits for very large clouds.
+static int max_digit_bits(int64_t n) { return sort_digit_values(n) == 2048 ? 11 : 8; }
+
+int sort_passes(int bits) { return (bits + 10) / 11; }
+
+int sort_passes_n(int bits, int64_t n)
+{
+    const int w = max_digit_bits(n);
+    return (bits + w - 1) / w;
+}
 
 cudaError_t launch_cell_keys(const fla_cloud& cl, const fla_mesh& m, uint32_t* keys, cudaStream_t s)
 {
@@ -213,7 +238,7 @@ cudaError_t launch_cell_keys(const fla_cloud& cl, const fla_mesh& m, uint32_t* k
 cudaError_t launch_radix_sort(SortWork w, int64_t n, int bits, int first, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    const int passes = sort_passes(bits);
+    const int passes = sort_passes_n(bits, n);
     const int width = (bits + passes - 1) / passes;
     const int tiles = radix_tiles(n);
     int cur = first;

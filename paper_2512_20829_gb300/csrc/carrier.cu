@@ -13,7 +13,7 @@ namespace {
 struct CarrierArgs {
     int kind, dim, N, n_vortex;
     double U[3], A[9], xref[3];
-    double vort[FLA_MAX_VORTICES][4];  // centre x at the sampling time (wrapped), yc, Gamma, rc
+    double vort[FLA_MAX_VORTICES][5];  // centre x at the sampling time (wrapped), yc, 1/rc^2, c/rc^2, c/rc^4
     double jet_width, abc[3], jet_amp, jet_radius;
 };
 
@@ -27,35 +27,59 @@ __device__ __forceinline__ float m_cospi(float x) { return cospif(x); }
 __device__ __forceinline__ double m_cospi(double x) { return cospi(x); }
 
 // Lamb-Oseen vortex, azimuthal speed Gam/(2 pi rho) (1 - exp(-rho^2/rc^2)),
-// written u = f(s) (-dy, dx) with s = rho^2.  f = (c/a) h(X), f' = (c/a^2) g(X),
-// X = s/a, a = rc^2, c = Gam/(2 pi); h(X) = (1 - e^-X)/X and
-// g(X) = (X e^-X - (1 - e^-X))/X^2 use their Taylor series near X = 0.
+// written u = f(s) (-dy, dx) with s = rho^2, X = s/rc^2:
+//   f  = (c/a) h(X),    h(X) = (1 - e^-X)/X,
+//   f' = (c/a^2) g(X),  g(X) = (X e^-X - (1 - e^-X))/X^2,
+// with a = rc^2, c = Gam/(2 pi); h and g use their Taylor series near X = 0.
+// inv_a = 1/a, ca = c/a and ca2 = c/a^2 are formed on the host.
+// Single precision: the series near X = 0, expm1 up to X = 1.5 (where e^-X - 1
+// and X e^-X + e^-X - 1 would otherwise cancel), and the fast exponential above,
+// where neither cancels (error below 1e-6 relative).
+__device__ __forceinline__ void lo_hg(float X, float& h, float& g)
+{
+    if (X < 1e-2f) {
+        h = 1.0f + X * (-0.5f + X * (1.0f / 6.0f + X * (-1.0f / 24.0f)));
+        g = -0.5f + X * (1.0f / 3.0f + X * (-0.125f + X * (1.0f / 30.0f)));
+    } else if (X < 1.5f) {
+        const float em = expm1f(-X);   // e^-X - 1
+        const float iX = 1.0f / X;
+        h = -em * iX;
+        g = (X * (em + 1.0f) + em) * iX * iX;
+    } else {
+        const float e = __expf(-X);
+        const float iX = __frcp_rn(X);
+        h = (1.0f - e) * iX;
+        g = (X * e + (e - 1.0f)) * iX * iX;
+    }
+}
+__device__ __forceinline__ void lo_hg(double X, double& h, double& g)
+{
+    if (X < 1e-3) {
+        h = 1.0 + X * (-0.5 + X * (1.0 / 6.0 + X * (-1.0 / 24.0)));
+        g = -0.5 + X * (1.0 / 3.0 + X * (-0.125 + X * (1.0 / 30.0)));
+    } else {
+        const double em = expm1(-X);    // e^-X - 1
+        const double iX = 1.0 / X;
+        h = -em * iX;
+        g = (X * (em + 1.0) + em) * iX * iX;
+    }
+}
+
 template <typename T>
-__device__ __forceinline__ void lamb_oseen(T gam, T rc, T xc, T yc, T x, T y, T* u, T* G)
+__device__ __forceinline__ void lamb_oseen(T inv_a, T ca, T ca2, T xc, T yc, T x, T y, T* u, T* G)
 {
     const T dx = x - xc, dy = y - yc;
-    const T s = dx * dx + dy * dy;
-    const T a = rc * rc;
-    const T c = gam * T(0.15915494309189533577);  // 1/(2 pi)
-    const T X = s / a;
+    const T X = (dx * dx + dy * dy) * inv_a;
     T h, g;
-    const T small = sizeof(T) == 4 ? T(1e-2) : T(1e-3);
-    if (X < small) {
-        h = T(1) + X * (T(-0.5) + X * (T(1.0 / 6.0) + X * T(-1.0 / 24.0)));
-        g = T(-0.5) + X * (T(1.0 / 3.0) + X * (T(-0.125) + X * T(1.0 / 30.0)));
-    } else {
-        const T em = m_expm1(-X);
-        h = -em / X;
-        g = (X * m_exp(-X) + em) / (X * X);
-    }
-    const T f = c / a * h;
-    const T fp = c / (a * a) * g;
+    lo_hg(X, h, g);
+    const T f = ca * h;
+    const T fp2 = T(2) * ca2 * g;
     u[0] -= dy * f;
     u[1] += dx * f;
-    G[0] -= T(2) * fp * dx * dy;
-    G[1] -= f + T(2) * fp * dy * dy;
-    G[2] += f + T(2) * fp * dx * dx;
-    G[3] += T(2) * fp * dx * dy;
+    G[0] -= fp2 * dx * dy;
+    G[1] -= f + fp2 * dy * dy;
+    G[2] += f + fp2 * dx * dx;
+    G[3] += fp2 * dx * dy;
 }
 
 template <typename T, int D>
@@ -101,9 +125,9 @@ __device__ void eval_carrier(const CarrierArgs& p, const T* x, T* u, T* G)
             G[1] = T(-2) * eta / w * uj;
             for (int k = 0; k < p.n_vortex; ++k) {
                 const T xc = T(p.vort[k][0]), yc = T(p.vort[k][1]);
-                const T gam = T(p.vort[k][2]), rc = T(p.vort[k][3]);
+                const T inv_a = T(p.vort[k][2]), ca = T(p.vort[k][3]), ca2 = T(p.vort[k][4]);
                 for (int img = -1; img <= 1; ++img)   // periodic images along x
-                    lamb_oseen<T>(gam, rc, xc + T(img), yc, x[0], x[1], u, G);
+                    lamb_oseen<T>(inv_a, ca, ca2, xc + T(img), yc, x[0], x[1], u, G);
             }
         }
         break;
@@ -146,7 +170,7 @@ __global__ void __launch_bounds__(256) k_carrier_sample(CarrierArgs p, T* __rest
     int64_t r = k;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        x[a] = T(double(r % nn) / double(p.N));
+        x[a] = T(r % nn) / T(p.N);   // node coordinate i/N in the storage precision
         r /= nn;
     }
     T u[3], G[9];
@@ -182,10 +206,13 @@ cudaError_t launch_carrier_sample(const fla_carrier_desc& c, const fla_mesh& m, 
     for (int k = 0; k < c.n_vortex; ++k) {
         double xc = c.vortex[k][0] + c.vortex[k][4] * t;   // carried with the jet
         xc -= floor(xc);                                   // wrapped into [0, 1)
+        const double rc2 = c.vortex[k][3] * c.vortex[k][3];
+        const double cg = c.vortex[k][2] / (2.0 * 3.14159265358979323846);   // Gamma / (2 pi)
         p.vort[k][0] = xc;
         p.vort[k][1] = c.vortex[k][1];
-        p.vort[k][2] = c.vortex[k][2];
-        p.vort[k][3] = c.vortex[k][3];
+        p.vort[k][2] = 1.0 / rc2;
+        p.vort[k][3] = cg / rc2;
+        p.vort[k][4] = cg / (rc2 * rc2);
     }
     p.jet_width = c.jet_width;
     p.jet_amp = c.jet_amp;

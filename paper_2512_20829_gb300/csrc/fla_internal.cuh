@@ -100,6 +100,14 @@ struct DevStatus {
     unsigned int flags, pad;
 };
 
+// Radix-sort scratch sizes (u32 words): tiles of 2,048 keys, digits of up to
+// 11 bits (2,048 values) for clouds of up to 2^21 droplets, 8 bits beyond.
+constexpr int64_t kSortTile = 2048;
+constexpr int64_t sort_tiles(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
+constexpr int64_t sort_digit_values(int64_t n) { return n <= (int64_t(1) << 21) ? 2048 : 256; }
+constexpr int64_t sort_counts_words(int64_t n) { return sort_digit_values(n) * sort_tiles(n > 0 ? n : 1); }
+constexpr int64_t kSortTotalsWords = 2048;
+
 struct SortWork {
     uint32_t* keys[2];
     uint32_t* vals[2];
@@ -113,6 +121,7 @@ cudaError_t launch_carrier_sample(const fla_carrier_desc& c, const fla_mesh& m, 
 cudaError_t launch_advance(const fla_cloud& cl, const fla_mesh& m, const void* nodes, int step0, int nsteps,
                            double dt, bool reset, DevStatus* st, cudaStream_t s);
 int sort_passes(int bits);
+int sort_passes_n(int bits, int64_t n);
 cudaError_t launch_cell_keys(const fla_cloud& cl, const fla_mesh& m, uint32_t* keys, cudaStream_t s);
 int sort_bits(uint32_t max_key);
 int radix_tiles(int64_t n);

@@ -9,12 +9,13 @@
 // at most kChunk candidates, so that a dense cluster of droplets (a caustic)
 // is spread over many CTAs instead of stalling one.
 //
-// Evaluation.  A persistent CTA of 16 warps takes work items from a counter.
-// Each warp owns a 4x4 block of the tile's cells; it streams the item's
+// Evaluation.  Persistent warps take (work item, 4x4 cell block) units from a
+// counter, independently of each other (no CTA barriers).  A warp streams the item's
 // candidates from the row segments that can reach its block, keeps (by ballot)
-// the records whose support reaches the block, queues them in a shared-memory
-// ring and, 32 at a time, lets each lane evaluate one record against all 16
-// cells of the block.  The Gaussian is separable, so a lane needs 4 + 4 ex2
+// the records whose support reaches the block, queues them in shared memory
+// (records covering the whole block and the others in two queues, so each batch
+// takes one path) and, 32 at a time, lets each lane evaluate one record against
+// all 16 cells of the block.  The Gaussian is separable, so a lane needs 4 + 4 ex2
 // per record instead of one per cell: w = 2^(c dx^2) * 2^(c dy^2 + log2(1/h)).
 // The truncation test keeps the single-precision form r^2 = fma(dy, dy, dx*dx)
 // <= 9 h^2.  Each lane accumulates its own records; the 32 lane partials of a
@@ -134,21 +135,23 @@ struct G2Args {
 __global__ void __launch_bounds__(kThreads, 1) k_gather2d_items(G2Args a)
 {
     extern __shared__ __align__(16) float4 smem4[];
-    __shared__ int s_item;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    float4* ring = smem4 + warp * (kScratchFloats / 4 + 8);   // per-warp region (ring, then scratch)
+    float4* ring = smem4 + warp * (kScratchFloats / 4 + 8);   // per-warp region (two rings, then scratch)
     const int N = a.N;
+    const float fN = (float)N;
     const int R = support_cells(a.ext_max, N);
-    const uint32_t total = __ldg(a.tile_items + a.n_tiles);
+    const uint32_t total = __ldg(a.tile_items + a.n_tiles) * kWarps;   // (item, block) units
     const unsigned lt = (1u << lane) - 1u;
-    unsigned long long npairs = 0;
+    unsigned npairs = 0;
 
     for (;;) {
-        if (tid == 0) s_item = (int)atomicAdd(a.counter, 1u);
-        __syncthreads();
-        const uint32_t item = (uint32_t)s_item;
-        __syncthreads();
-        if (item >= total) break;
+        // each warp takes one (work item, 4x4 block) unit at a time: no CTA barriers
+        uint32_t unit = 0;
+        if (lane == 0) unit = atomicAdd(a.counter, 1u);
+        unit = __shfl_sync(0xffffffffu, unit, 0);
+        if (unit >= total) break;
+        const uint32_t item = unit / kWarps;
+        const int blk = (int)(unit % kWarps);
         // tile of this item: last t with tile_items[t] <= item
         int lo = 0, hi = a.n_tiles - 1;
         while (lo < hi) {
@@ -164,11 +167,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gather2d_items(G2Args a)
         const int tx0 = (t % a.tiles_x) * kTile, ty0 = (t / a.tiles_x) * kTile;
         const int xlo = max(tx0 - R, 0), xhi = min(tx0 + kTile - 1 + R, N - 1);
         const int ylo = max(ty0 - R, 0), yhi = min(ty0 + kTile - 1 + R, N - 1);
-        // this warp's 4x4 block of cells
-        const int bx0 = tx0 + 4 * (warp & 3), by0 = ty0 + 4 * (warp >> 2);
+        // the 4x4 block of cells
+        const int bx0 = tx0 + 4 * (blk & 3), by0 = ty0 + 4 * (blk >> 2);
         const bool live = bx0 < N && by0 < N;
         const int bx1 = min(bx0 + 3, N - 1), by1 = min(by0 + 3, N - 1);
-        const float fN = (float)N;
         float xc[4], yc[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -186,8 +188,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gather2d_items(G2Args a)
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[k][q] = 0.0f;
 
-        auto eval = [&](const float4 ra, const float4 rb) {
-            float dxx[4], ex[4];
+        // Evaluation of one record against the 16 cells.  FULL: the record's
+        // truncated support covers the whole block (decided when it was queued),
+        // so no per-cell test is needed.
+        auto eval = [&](const float4 ra, const float4 rb, const bool full) {
+            float dxx[4], ex[4], dyv[4], ey[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const float dx = __fsub_rn(xc[i], ra.x);
@@ -196,65 +201,145 @@ __global__ void __launch_bounds__(kThreads, 1) k_gather2d_items(G2Args a)
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const float dy = __fsub_rn(yc[j], ra.y);
-                const float ey = ex2_approx(fmaf(dy * dy, ra.z, ra.w));
+                dyv[j] = __fsub_rn(yc[j], ra.y);
+                ey[j] = ex2_approx(fmaf(dyv[j] * dyv[j], ra.z, ra.w));
+            }
+            if (full) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float r2 = __fmaf_rn(dy, dy, dxx[i]);   // single-precision decision
-                    const bool in = r2 <= rb.w;
-                    const float w = in ? ex[i] * ey : 0.0f;
-                    float* c = acc[4 * j + i];
-                    c[0] += w;
-                    c[1] = fmaf(w, rb.x, c[1]);
-                    c[2] = fmaf(w, rb.y, c[2]);
-                    c[3] = fmaf(w, rb.z, c[3]);
-                    npairs += in && (bx0 + i < N) && (by0 + j < N);
-                }
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float w = ex[i] * ey[j];
+                        float* c = acc[4 * j + i];
+                        c[0] += w;
+                        c[1] = fmaf(w, rb.x, c[1]);
+                        c[2] = fmaf(w, rb.y, c[2]);
+                        c[3] = fmaf(w, rb.z, c[3]);
+                    }
+                npairs += 16;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float r2 = __fmaf_rn(dyv[j], dyv[j], dxx[i]);   // single-precision decision
+                        const bool in = r2 <= rb.w;
+                        const float w = in ? ex[i] * ey[j] : 0.0f;
+                        float* c = acc[4 * j + i];
+                        c[0] += w;
+                        c[1] = fmaf(w, rb.x, c[1]);
+                        c[2] = fmaf(w, rb.y, c[2]);
+                        c[3] = fmaf(w, rb.z, c[3]);
+                        npairs += in;
+                    }
             }
         };
 
-        uint32_t wr = 0, rd = 0, offset = 0;
-        for (int y = ylo; y <= yhi && offset < c1; ++y) {
-            const int64_t rowb = (int64_t)y * N;
-            const uint32_t beg = __ldg(a.bin_start + rowb + xlo);
-            const uint32_t len = __ldg(a.bin_start + rowb + xhi + 1) - beg;
-            if (live && y >= wylo && y <= wyhi && offset + len > c0 && wxlo <= wxhi) {
-                const uint32_t wb = __ldg(a.bin_start + rowb + wxlo);
-                const uint32_t we = __ldg(a.bin_start + rowb + wxhi + 1);
-                const uint32_t s = max(beg + (c0 > offset ? c0 - offset : 0u), wb);
-                const uint32_t e = min(beg + min(c1 - offset, len), we);
-                for (uint32_t j0 = s; j0 < e; j0 += 32) {
-                    const uint32_t j = j0 + lane;
-                    bool ov = false;
-                    float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra;
-                    if (j < e) {
-                        ra = __ldg(a.rec + 2 * (int64_t)j);
-                        rb = __ldg(a.rec + 2 * (int64_t)j + 1);
-                        const float dl = fmaxf(fmaxf(bxl - ra.x, ra.x - bxh), 0.0f);
-                        const float dm = fmaxf(fmaxf(byl - ra.y, ra.y - byh), 0.0f);
-                        ov = dl * dl + dm * dm <= rb.w * 1.0009765625f;
-                    }
-                    const unsigned m = __ballot_sync(0xffffffffu, ov);
-                    if (ov) {
-                        const uint32_t slot = (wr + __popc(m & lt)) & (kRing - 1);
-                        ring[2 * slot] = ra;
-                        ring[2 * slot + 1] = rb;
-                    }
-                    wr += __popc(m);
-                    __syncwarp();
-                    if (wr - rd >= 32) {
-                        const uint32_t slot = (rd + lane) & (kRing - 1);
-                        eval(ring[2 * slot], ring[2 * slot + 1]);
-                        rd += 32;
-                        __syncwarp();
-                    }
+        // Two queues: records covering the whole block (ring 0) and the others
+        // (ring 1), so that each batch of 32 takes one path for the whole warp.
+        uint32_t wr0 = 0, rd0 = 0, wr1 = 0, rd1 = 0;
+        float4* ring0 = ring;
+        float4* ring1 = ring + 2 * kRing;
+        auto stream = [&](const float4 ra, const float4 rb, const bool valid) {
+            bool ov = false, full = false;
+            if (valid) {
+                const float dl = fmaxf(fmaxf(bxl - ra.x, ra.x - bxh), 0.0f);
+                const float dm = fmaxf(fmaxf(byl - ra.y, ra.y - byh), 0.0f);
+                ov = dl * dl + dm * dm <= rb.w * 1.0009765625f;
+                // the computed r^2 grows with |dx| and |dy| (each rounding is monotone):
+                // if the farthest cell passes the single-precision test, every cell does
+                const float dxe = fmaxf(fabsf(__fsub_rn(xc[0], ra.x)), fabsf(__fsub_rn(xc[3], ra.x)));
+                const float dye = fmaxf(fabsf(__fsub_rn(yc[0], ra.y)), fabsf(__fsub_rn(yc[3], ra.y)));
+                full = ov && __fmaf_rn(dye, dye, __fmul_rn(dxe, dxe)) <= rb.w;
+            }
+            const unsigned m0 = __ballot_sync(0xffffffffu, full);
+            const unsigned m1 = __ballot_sync(0xffffffffu, ov && !full);
+            if (full) {
+                const uint32_t slot = (wr0 + __popc(m0 & lt)) & (kRing - 1);
+                ring0[2 * slot] = ra;
+                ring0[2 * slot + 1] = rb;
+            } else if (ov) {
+                const uint32_t slot = (wr1 + __popc(m1 & lt)) & (kRing - 1);
+                ring1[2 * slot] = ra;
+                ring1[2 * slot + 1] = rb;
+            }
+            wr0 += __popc(m0);
+            wr1 += __popc(m1);
+            __syncwarp();
+            if (wr0 - rd0 >= 32) {
+                const uint32_t slot = (rd0 + lane) & (kRing - 1);
+                eval(ring0[2 * slot], ring0[2 * slot + 1], true);
+                rd0 += 32;
+                __syncwarp();
+            }
+            if (wr1 - rd1 >= 32) {
+                const uint32_t slot = (rd1 + lane) & (kRing - 1);
+                eval(ring1[2 * slot], ring1[2 * slot + 1], false);
+                rd1 += 32;
+                __syncwarp();
+            }
+        };
+
+        // Row segments, 32 rows at a time: lane l reads the bin offsets of row l so
+        // that the offsets of all rows arrive together.
+        uint32_t offset = 0;
+        for (int yg = ylo; yg <= yhi && offset < c1; yg += 32) {
+            const int yl = yg + lane;
+            uint32_t beg = 0, len = 0, wb = 0, we = 0;
+            if (yl <= yhi) {
+                const int64_t rowb = (int64_t)yl * N;
+                beg = __ldg(a.bin_start + rowb + xlo);
+                len = __ldg(a.bin_start + rowb + xhi + 1) - beg;
+                if (wxlo <= wxhi) {
+                    wb = __ldg(a.bin_start + rowb + wxlo);
+                    we = __ldg(a.bin_start + rowb + wxhi + 1);
                 }
             }
-            offset += len;
+            uint32_t incl = len;   // inclusive scan of the row lengths across lanes
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int nrows = min(32, yhi - yg + 1);
+            for (int r = 0; r < nrows; ++r) {
+                const uint32_t rbeg = __shfl_sync(0xffffffffu, beg, r);
+                const uint32_t rlen = __shfl_sync(0xffffffffu, len, r);
+                const uint32_t rwb = __shfl_sync(0xffffffffu, wb, r);
+                const uint32_t rwe = __shfl_sync(0xffffffffu, we, r);
+                const uint32_t roff = offset + __shfl_sync(0xffffffffu, incl, r) - rlen;
+                if (roff >= c1) break;
+                const int y = yg + r;
+                if (!live || y < wylo || y > wyhi || roff + rlen <= c0 || wxlo > wxhi) continue;
+                const uint32_t s0 = max(rbeg + (c0 > roff ? c0 - roff : 0u), rwb);
+                const uint32_t e = min(rbeg + min(c1 - roff, rlen), rwe);
+                // stream the segment 32 records at a time, loading one batch ahead
+                float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra;
+                if (s0 + lane < e) {
+                    ra = __ldg(a.rec + 2 * (int64_t)(s0 + lane));
+                    rb = __ldg(a.rec + 2 * (int64_t)(s0 + lane) + 1);
+                }
+                for (uint32_t j0 = s0; j0 < e; j0 += 32) {
+                    const uint32_t jn = j0 + 32 + lane;
+                    float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na;
+                    if (jn < e) {
+                        na = __ldg(a.rec + 2 * (int64_t)jn);
+                        nb = __ldg(a.rec + 2 * (int64_t)jn + 1);
+                    }
+                    stream(ra, rb, j0 + lane < e);
+                    ra = na;
+                    rb = nb;
+                }
+            }
+            offset += __shfl_sync(0xffffffffu, incl, 31);
         }
-        if (live && lane < wr - rd) {
-            const uint32_t slot = (rd + lane) & (kRing - 1);
-            eval(ring[2 * slot], ring[2 * slot + 1]);
+        if (live && lane < wr0 - rd0) {
+            const uint32_t slot = (rd0 + lane) & (kRing - 1);
+            eval(ring0[2 * slot], ring0[2 * slot + 1], true);
+        }
+        if (live && lane < wr1 - rd1) {
+            const uint32_t slot = (rd1 + lane) & (kRing - 1);
+            eval(ring1[2 * slot], ring1[2 * slot + 1], false);
         }
         __syncwarp();
 
@@ -279,14 +364,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_gather2d_items(G2Args a)
             __syncwarp();
             const int f = 32 * half + lane;      // value f of the block: cell f/4, component f%4
             const int k = f >> 2;
-            const int local = (4 * (warp & 3) + (k & 3)) + kTile * (4 * (warp >> 2) + (k >> 2));
+            const int local = (4 * (blk & 3) + (k & 3)) + kTile * (4 * (blk >> 2) + (k >> 2));
             reinterpret_cast<float*>(out + local)[f & 3] = sum + comp;
         }
         __syncwarp();
     }
-    // pairs inside the truncation: one atomic per warp
-    const unsigned long long wsum = __reduce_add_sync(0xffffffffu, (unsigned)npairs);
-    if (lane == 0 && wsum) atomicAdd(a.pairs, wsum);
+    // pairs inside the truncation (cells of partial blocks at the mesh edge included):
+    // one atomic per warp
+    const unsigned wsum = __reduce_add_sync(0xffffffffu, npairs);
+    if (lane == 0 && wsum) atomicAdd(a.pairs, (unsigned long long)wsum);
 }
 
 struct CombineArgs {

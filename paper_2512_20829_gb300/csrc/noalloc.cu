@@ -22,9 +22,10 @@ using namespace fla;
 namespace {
 
 constexpr int64_t kMaxDroplets = FLA_NOALLOC_MAX_DROPLETS;
-constexpr int64_t kMaxTiles = (kMaxDroplets + 4095) / 4096;
-// keys[2][max], vals[2][max], counts[256 * tiles], totals[256]  (u32 words)
-constexpr int64_t kWords = 4 * kMaxDroplets + 256 * kMaxTiles + 256;
+constexpr int64_t kCountsWords = sort_counts_words(kMaxDroplets);
+// keys[2][max], vals[2][max], per-tile digit counts, digit totals  (u32 words)
+constexpr int64_t kWords = 4 * kMaxDroplets + kCountsWords + kSortTotalsWords;
+static_assert(sort_counts_words(kMaxDroplets) >= sort_counts_words(1), "counts sized for the largest cloud");
 
 static __device__ __align__(256) uint32_t g_scratch[kWords];
 
@@ -79,11 +80,11 @@ extern "C" int fla_cell_bins_noalloc(const fla_cloud* cloud, const fla_mesh* mes
     w.vals[0] = base + 2 * kMaxDroplets;
     w.vals[1] = base + 3 * kMaxDroplets;
     w.counts = base + 4 * kMaxDroplets;
-    w.totals = w.counts + 256 * kMaxTiles;
+    w.totals = w.counts + kCountsWords;
     if (launch_cell_keys(*cloud, *mesh, w.keys[0], s) != cudaSuccess) return FLA_ERR_CUDA;
     const int bits = sort_bits((uint32_t)nc);
     if (launch_radix_sort(w, cloud->n, bits, 0, s) != cudaSuccess) return FLA_ERR_CUDA;
-    const int cur = sort_passes(bits) & 1;
+    const int cur = sort_passes_n(bits, cloud->n) & 1;
     if (cudaMemcpyAsync(keys_sorted_dev, w.keys[cur], (size_t)cloud->n * 4, cudaMemcpyDeviceToDevice, s) !=
         cudaSuccess)
         return FLA_ERR_CUDA;
