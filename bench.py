@@ -38,16 +38,46 @@ sys.path.insert(0, ROOT)
 
 METRIC = "source-term cells/s (kernel-regression deposit, with droplet-steps/s) at rel-L2 <= 1e-4 vs FP64 oracle"
 UNIT = "cells/s"
-WORKLOAD = "jet_vortex_2d: 512^2 cells, 262,144 FLA seeds (256 releases x 1,024), 1,000 RK4 steps, 100 deposits"
+WORKLOADS = {
+    # name: (description, dtype name, has PSI-CELL reference)
+    "jet_vortex_2d": ("jet_vortex_2d: 512^2 cells, 262,144 FLA seeds (256 releases x 1,024), 1,000 RK4 steps, "
+                      "100 deposits", "F32", True),
+    "taylor_green_2d": ("taylor_green_2d: 64^2 cells, 4,096 FLA seeds, 200 RK4 steps, 20 deposits, FP64", "F64", True),
+    "abc_jet_3d": ("abc_jet_3d: 128^3 cells, 2,097,152 FLA seeds in a cone, 500 RK4 steps, 50 deposits, "
+                   "J-scaled anisotropic kernel", "F32", False),
+}
+WORKLOAD = WORKLOADS["jet_vortex_2d"][0]
 
-# FP32 operations per droplet step of the fused advance, counted from the kernel's
-# operation list (FMA = 2): four stages of bilinear interpolation of 6 node values
-# (58) and the right-hand side (28), the RK4 combinations (156), St(t) (13) and the
-# window sums (20).
-FLOPS_PER_STEP_FLA2D = 533
-# FP32 operations per kernel pair inside the truncation (2D spherical kernel):
-# 2 differences, r^2 (3), exponent scale (1), weight scale (1), 4 FMA sums (8); plus one ex2.
-FLOPS_PER_PAIR_ISO2D = 15
+
+def make_workload(name, with_lpt):
+    from paper_2512_20829_gb300 import inputs as I
+    if name == "jet_vortex_2d":
+        return I.jet_vortex_2d(lpt_per_batch=65_536 if with_lpt else 0)
+    if name == "taylor_green_2d":
+        wl = I.taylor_green_2d()
+        if not with_lpt:
+            wl.lpt = None
+        return wl
+    return I.abc_jet_3d()
+
+# Floating-point operations per droplet step of the fused advance, counted from the
+# kernel's operation list (FMA = 2).  2D: four stages of bilinear interpolation of 6
+# node values (58) and the right-hand side (28), the RK4 combinations (156), St(t)
+# (13) and the window sums (20).  3D: trilinear interpolation of 12 values (217) and
+# the right-hand side (78) per stage, combinations (312), St(t) and sums (40).
+FLOPS_PER_STEP = {2: 533, 3: 1532}
+# Operations per (cell, droplet) pair inside the truncated kernel, the paper's
+# form of the weight (one ex2 per pair besides these).  2D spherical: 2 differences,
+# r^2 (3), exponent (1), prefactor (1), 4 FMA sums (8).  3D spherical: 3 differences,
+# r^2 (5), exponent and prefactor (2), sums (9).  3D J-scaled: 3 differences,
+# P d (15), d.(P d) (5), exponent (2), sums (9).
+FLOPS_PER_PAIR = {(2, 0): 15, (3, 0): 19, (2, 1): 24, (3, 1): 34}
+FP64_PEAK_TFLOPS = 1.25   # GB300 FP64, per the hardware description
+# DRAM bytes (read + write) of one k_gather2d_items launch from an ncu capture
+# (profiles/gather2d_jet512_window81.md); None once the kernel changes.
+GATHER_TRAFFIC = {
+    (2, 0, False): (6246144, "ncu dram__bytes_read+write of k_gather2d_items, jet 512^2 deposit 81"),
+}
 
 
 def parse():
@@ -56,6 +86,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="jet_vortex_2d",
+                    help="configuration to run (the headline metric is quoted on jet_vortex_2d)")
     ap.add_argument("--no-psicell", action="store_true", help="skip the PSI-CELL reference leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--profile-only", action="store_true",
@@ -121,21 +153,22 @@ class ClockSampler:
 # --------------------------------------------------------------------------- GPU path
 
 class JetPath:
-    """Device buffers and the issue order of one whole run of the jet workload."""
+    """Device buffers and the issue order of one whole run of a workload."""
 
-    def __init__(self, ctx, wl, fla, with_fla=True, with_lpt=False):
+    def __init__(self, ctx, wl, fla, with_fla=True, with_lpt=False, dtype=None):
         import torch
         self.fla, self.ctx, self.wl = fla, ctx, wl
+        self.dtype = fla.F32 if dtype is None else dtype
         self.m = fla.mesh(wl.dim, wl.n_cells_axis)
         self.desc = fla.carrier_desc(wl.carrier)
-        self.nodes = fla.nodes_buffer(self.m, fla.F32)
+        self.nodes = fla.nodes_buffer(self.m, self.dtype)
         self.cfg = fla.deposit_cfg(wl.kernel, wl.h_min, wl.h_max, wl.window * wl.dt, wl.p)
-        self.cloud = fla.DeviceCloud.from_seeds(wl.fla, 2, wl.delta, wl.dt, fla.F32) if with_fla else None
-        self.lpt = fla.DeviceCloud.from_seeds(wl.lpt, 2, wl.delta, wl.dt, fla.F32) if with_lpt else None
+        self.cloud = fla.DeviceCloud.from_seeds(wl.fla, wl.dim, wl.delta, wl.dt, self.dtype) if with_fla else None
+        self.lpt = fla.DeviceCloud.from_seeds(wl.lpt, wl.dim, wl.delta, wl.dt, self.dtype) if with_lpt else None
         n = max(c.n for c in (self.cloud, self.lpt) if c is not None)
-        self.ws = fla.aligned_ws(fla.workspace(self.m, fla.F32, wl.kernel, n))
-        self.out = fla.SourceFields(self.m, fla.F32) if with_fla else None
-        self.psi = fla.PsicellFields(self.m, fla.F32) if with_lpt else None
+        self.ws = fla.aligned_ws(fla.workspace(self.m, self.dtype, wl.kernel, n))
+        self.out = fla.SourceFields(self.m, self.dtype) if with_fla else None
+        self.psi = fla.PsicellFields(self.m, self.dtype) if with_lpt else None
         self.pristine = [(c.state.clone(), c.meta.clone()) for c in (self.cloud, self.lpt) if c is not None]
 
     def clouds(self):
@@ -150,7 +183,9 @@ class JetPath:
         """Enqueue the whole run on the current stream (capturable)."""
         fla, wl, m = self.fla, self.wl, self.m
         for s in range(0, wl.nsteps, wl.window):
-            fla.carrier_sample(self.ctx, self.desc, m, s * wl.dt, fla.F32, self.nodes)
+            if s == 0 or not wl.carrier.steady:   # a steady carrier is sampled once per run
+                fla.carrier_sample(self.ctx, self.desc, m, 0.0 if wl.carrier.steady else s * wl.dt, self.dtype,
+                                   self.nodes)
             for c in self.clouds():
                 fla.advance(self.ctx, c, m, self.nodes, s, wl.window, wl.dt, reset_acc=True)
             if self.cloud is not None:
@@ -191,28 +226,35 @@ def timed_replays(path, g, steps, flush, events=True):
     return [a.elapsed_time(b) for a, b in times]
 
 
-def roofline_entry(phase_name, prof, peaks, clocks, status_pairs, droplet_steps_per_run, runs):
-    """Roofline of the dominant phase from the instrumented run's CUDA-event times."""
+def roofline_entry(phase_name, prof, peaks, status_pairs, droplet_steps_per_run, dim, kernel, f64):
+    """Roofline of the dominant phase from the instrumented run's CUDA-event times
+    (one call = the phase's kernel launches for one window)."""
     p = prof[phase_name]
     calls = max(p["calls"], 1)
-    ms_per_launch = p["ms"] / calls      # one call = one launch of the phase's kernel(s)
+    ms_per_call = p["ms"] / calls
     sm_max = 2070.0
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s at the maximum SM clock
-    mufu_peak_pairs = 152 * 16 * sm_max * 1e6                # ex2 per second
+    mufu_pairs = 152 * 16 * sm_max * 1e6                     # ex2 per second
     if phase_name == "advance":
-        flops = droplet_steps_per_run * FLOPS_PER_STEP_FLA2D / max(prof["advance"]["calls"] / runs, 1)
-        ach = flops / (ms_per_launch * 1e-3) / 1e12
-        return {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
-                "traffic": None, "kernel": "k_advance<float,2,FLA>",
-                "peak_basis": "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived, max clock)"}
-    if phase_name == "gather":
-        pairs = status_pairs / max(prof["gather"]["calls"], 1)
-        flops = pairs * FLOPS_PER_PAIR_ISO2D
-        ach = flops / (ms_per_launch * 1e-3) / 1e12
-        peak = min(fp32_peak, mufu_peak_pairs * FLOPS_PER_PAIR_ISO2D / 1e12)
+        flops = droplet_steps_per_run * FLOPS_PER_STEP[dim] / calls
+        ach = flops / (ms_per_call * 1e-3) / 1e12
+        peak = FP64_PEAK_TFLOPS if f64 else fp32_peak
         return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "kernel": "gather (plan + k_gather2d_items + combine)",
-                "peak_basis": "min(FP32 152x128x2, MUFU ex2 152x16 per pair x 15 flops) at 2070 MHz (derived)"}
+                "traffic": None, "kernel": "k_advance",
+                "peak_basis": ("GB300 FP64 rate (derived)" if f64 else
+                               "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived, max clock)")}
+    if phase_name == "gather":
+        fpp = FLOPS_PER_PAIR[(dim, kernel)]
+        flops = status_pairs / calls * fpp
+        ach = flops / (ms_per_call * 1e-3) / 1e12
+        peak = FP64_PEAK_TFLOPS if f64 else min(fp32_peak, mufu_pairs * fpp / 1e12)
+        traffic = GATHER_TRAFFIC.get((dim, kernel, f64))
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": traffic[0] if traffic else None,
+                "traffic_basis": traffic[1] if traffic else None,
+                "kernel": "kernel-regression gather (all launches of one deposit)",
+                "peak_basis": ("GB300 FP64 rate (derived)" if f64 else
+                               f"min(FP32 152x128x2, MUFU ex2 152x16 per pair x {fpp} flops) at 2070 MHz (derived)")}
     # HBM-bound phases: algorithmic bytes
     return {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s", "frac": None,
             "traffic": None, "kernel": phase_name}
@@ -233,18 +275,20 @@ def run_ours(args):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    wl = I.jet_vortex_2d(lpt_per_batch=0 if args.no_psicell else 65_536)
+    desc, dname, has_psi = WORKLOADS[args.workload]
+    dtype = getattr(fla, dname)
+    wl = make_workload(args.workload, has_psi and not args.no_psicell)
     cells = wl.n_cells
     deposits = wl.nsteps // wl.window
 
-    path = JetPath(ctx, wl, fla, with_fla=True)
+    path = JetPath(ctx, wl, fla, with_fla=True, dtype=dtype)
     if args.profile_only:
         # one eager run of the whole path (no graph), for external profilers
         path.reset()
         path.issue()
         torch.cuda.synchronize()
         if rank == 0:
-            print(json.dumps({"profile_only": True, "workload": WORKLOAD}))
+            print(json.dumps({"profile_only": True, "workload": desc}))
         return
     g, launches_per_run = capture(path)
     flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device="cuda")
@@ -285,7 +329,8 @@ def run_ours(args):
     ctx.profile(False, reset=True)
     stp = ctx.sync_status(reset=True)
     dominant = max(prof, key=lambda k: prof[k]["ms"])
-    roof = roofline_entry(dominant, prof, peaks, clocks, stp.pairs, droplet_steps_per_run, 1)
+    roof = roofline_entry(dominant, prof, peaks, stp.pairs, droplet_steps_per_run, wl.dim, wl.kernel,
+                          dtype == fla.F64)
     phases = {k: {"ms_per_run": round(v["ms"], 4), "launches_per_run": v["launches"]} for k, v in prof.items()
               if v["calls"]}
 
@@ -314,9 +359,9 @@ def run_ours(args):
 
     # ---------------- PSI-CELL reference leg (2^24 parcels, same flow, same windows)
     psi = None
-    if not args.no_psicell and rank == 0:
+    if not args.no_psicell and wl.lpt is not None and rank == 0:
         del g
-        ppath = JetPath(ctx, wl, fla, with_fla=False, with_lpt=True)
+        ppath = JetPath(ctx, wl, fla, with_fla=False, with_lpt=True, dtype=dtype)
         pg, plaunch = capture(ppath)
         pg.replay()
         torch.cuda.synchronize()
@@ -332,15 +377,16 @@ def run_ours(args):
         del pg, ppath
 
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and not args.no_cpu and args.workload == "jet_vortex_2d":
         cpu = cpu_baseline(wl)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 (f64 det J)", "data": "synthetic (seeded jet + vortices)",
-            "config": {"workload": WORKLOAD, "global_batch": world * wl.fla.n, "cells": cells,
+            "vs_baseline": None, "dtype": "f32 (f64 det J)" if dtype == fla.F32 else "f64",
+            "data": "synthetic (seeded, " + args.workload + ")",
+            "config": {"workload": desc, "global_batch": world * wl.fla.n, "cells": cells,
                        "deposits_per_step": deposits, "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"replicas x{world} (independent clouds, no collective)"},
             "droplet_steps_per_s": world * droplet_steps_per_run * args.steps / (total_ms * 1e-3),
