@@ -90,6 +90,7 @@ def parse():
                     help="configuration to run (the headline metric is quoted on jet_vortex_2d)")
     ap.add_argument("--no-psicell", action="store_true", help="skip the PSI-CELL reference leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-variants", action="store_true", help="skip the other precision forms")
     ap.add_argument("--profile-only", action="store_true",
                     help="one eager run of the whole path, nothing else (for external profilers)")
     return ap.parse_args()
@@ -155,15 +156,19 @@ class ClockSampler:
 class JetPath:
     """Device buffers and the issue order of one whole run of a workload."""
 
-    def __init__(self, ctx, wl, fla, with_fla=True, with_lpt=False, dtype=None):
+    def __init__(self, ctx, wl, fla, with_fla=True, with_lpt=False, dtype=None, precision=None,
+                 fold_guard=False):
         import torch
         self.fla, self.ctx, self.wl = fla, ctx, wl
         self.dtype = fla.F32 if dtype is None else dtype
+        self.precision = fla.PREC_MIXED if precision is None else precision
         self.m = fla.mesh(wl.dim, wl.n_cells_axis)
         self.desc = fla.carrier_desc(wl.carrier)
         self.nodes = fla.nodes_buffer(self.m, self.dtype)
-        self.cfg = fla.deposit_cfg(wl.kernel, wl.h_min, wl.h_max, wl.window * wl.dt, wl.p)
+        self.cfg = fla.deposit_cfg(wl.kernel, wl.h_min, wl.h_max, wl.window * wl.dt, wl.p, precision=self.precision)
         self.cloud = fla.DeviceCloud.from_seeds(wl.fla, wl.dim, wl.delta, wl.dt, self.dtype) if with_fla else None
+        if self.cloud is not None and self.dtype == fla.F32 and self.precision == fla.PREC_MIXED and fold_guard:
+            self.cloud.enable_fold()   # double-precision J, W near fold caustics
         self.lpt = fla.DeviceCloud.from_seeds(wl.lpt, wl.dim, wl.delta, wl.dt, self.dtype) if with_lpt else None
         n = max(c.n for c in (self.cloud, self.lpt) if c is not None)
         self.ws = fla.aligned_ws(fla.workspace(self.m, self.dtype, wl.kernel, n))
@@ -357,6 +362,25 @@ def run_ours(args):
         e2e.append(a.elapsed_time(b))
     e2e_ms = float(np.mean(e2e))
 
+    # ---------------- the other precision forms of the same path, timed the same way:
+    # plain single precision (det J and n in FP32) and mixed with the advance's fold guard
+    precision = None
+    if dtype == fla.F32 and not args.no_variants:
+        variants = {}
+        for name, prec, guard in (("plain_fp32", fla.PREC_PLAIN, False), ("mixed_fold_guard", fla.PREC_MIXED, True)):
+            vp = JetPath(ctx, wl, fla, with_fla=True, dtype=dtype, precision=prec, fold_guard=guard)
+            vg, _ = capture(vp)
+            vg.replay()
+            torch.cuda.synchronize()
+            ctx.sync_status(reset=True)
+            vt = timed_replays(vp, vg, 3, flush)
+            vst = ctx.sync_status(reset=True)
+            variants[name] = {"ms_per_step": round(float(np.mean(vt)), 4),
+                              "fold_steps_per_run": vst.fold_steps / 3}
+            del vg, vp
+        precision = {"mode": "mixed: FP32 trajectories and kernels, det J and n in FP64 where det J cancels",
+                     "variants": variants}
+
     # ---------------- PSI-CELL reference leg (2^24 parcels, same flow, same windows)
     psi = None
     if not args.no_psicell and wl.lpt is not None and rank == 0:
@@ -396,6 +420,7 @@ def run_ours(args):
             "phases": phases,
             "e2e": {"value": world * cells * deposits / (e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
+            "precision": precision,
             "psicell_reference": psi,
             "cpu_baseline": cpu,
         }

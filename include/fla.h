@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define FLA_ABI_VERSION 1
+#define FLA_ABI_VERSION 2
 
 /* cudaStream_t without including the CUDA headers. */
 typedef struct CUstream_st* fla_stream_t;
@@ -62,9 +62,12 @@ enum {
     FLA_CARRIER_ABCJET3 = 4    /* ABC flow at wavenumber 2 pi + round jet along z */
 };
 
-/* Per-droplet meta word: release index in bits 0..23 plus two state bits.
- * A seed with neither bit set is pending (not yet released). */
+/* Per-droplet meta word: release index in bits 0..23 plus state bits.
+ * A seed with neither ACTIVE nor DEAD set is pending (not yet released).
+ * FOLD marks a droplet of a single-precision FLA cloud whose J and W are
+ * currently integrated in double precision (see fla_cloud.fold_dev). */
 #define FLA_META_BATCH_MASK 0x00FFFFFFu
+#define FLA_META_FOLD 0x20000000u
 #define FLA_META_DEAD 0x40000000u
 #define FLA_META_ACTIVE 0x80000000u
 
@@ -121,7 +124,24 @@ typedef struct {
     uint32_t* meta_dev;        /* n meta words */
     const fla_batch* batches_dev; /* n_batches entries */
     double delta;              /* d^2-law rate: r^2 = r0^2 + delta (t - t0), r0 = 1 (Eq. 4) */
+    /* Fold guard of single-precision FLA clouds (NULL: none).  Near a fold
+     * caustic det J passes through zero (Eq. 6 gives n -> infinity) and its
+     * single-precision value loses its relative accuracy.  With fold_dev set,
+     * fla_advance moves a droplet whose |det J| drops below tau_fold to double
+     * precision for the J and W part of its RK4 step, keeping those values in
+     * fold_dev (FP64 planes of 4: J[dim*dim] then W[dim*dim]; value c of
+     * droplet i in plane p at (p * n + i) * 4 + c; fla_fold_bytes gives the
+     * size) and setting FLA_META_FOLD; it moves back once |det J| exceeds
+     * 4 tau_fold.  The single-precision J and W in state_dev stay the rounded
+     * copies.  Records of flagged droplets take det J and 1/|det J| from
+     * fold_dev in double precision.  Caller-owned, 16-byte aligned; the
+     * library reads it only for flagged droplets, so it needs no clearing. */
+    void* fold_dev;
+    double tau_fold;           /* fold threshold on |det J| (> 0 when fold_dev is set); 1e-2 typical */
 } fla_cloud;
+
+/* Bytes of fold_dev for n droplets of dimension dim. */
+size_t fla_fold_bytes(int32_t dim, int64_t n);
 
 /* Kernel-regression deposit settings. */
 typedef struct {
@@ -131,7 +151,14 @@ typedef struct {
     double h_min, h_max;       /* smoothing-length clamps (absolute lengths), 0 < h_min <= h_max */
     double p;                  /* h = h0 |det J|^p; the paper's Eq. 15 is p = 1 */
     double window_dt;          /* time covered by the window sums acc (> 0) */
+    int32_t precision;         /* single-precision clouds: FLA_PREC_MIXED (det J and 1/|det J| in
+                                  double where they can cancel, and from fold_dev for flagged droplets)
+                                  or FLA_PREC_PLAIN (det J, 1/|det J| in single precision throughout);
+                                  ignored by double-precision clouds */
+    int32_t reserved;          /* 0 */
 } fla_deposit_cfg;
+
+enum { FLA_PREC_MIXED = 0, FLA_PREC_PLAIN = 1 };
 
 /* Deposit outputs, device arrays of the cloud's dtype, n_cells entries each
  * (s_mom: dim consecutive planes of n_cells).  dsum_dev (the kernel-estimator
@@ -153,6 +180,7 @@ typedef struct {
     uint64_t deposited;        /* droplets that entered a kernel-regression deposit */
     uint64_t droplet_steps;    /* droplet steps integrated by fla_advance (active droplet x step) */
     uint64_t pairs;            /* (cell, droplet) pairs inside the truncated kernels, summed over deposits */
+    uint64_t fold_steps;       /* of droplet_steps, those whose J and W were integrated in double precision */
     uint32_t flags;            /* reserved, 0 */
     uint32_t pad;
 } fla_device_status;
@@ -216,6 +244,11 @@ int fla_batch_deadline(double St0, double delta, double dt, int32_t step_start, 
  *     x' = v, v' = (u - v)/St (Eq. 3) and, for FLA, J' = W,
  *     W' = (grad u . J - W)/St (Eq. 8), with St = St0 (1 + delta (t - t0)) (Eqs. 4-5);
  *   - a droplet that leaves [0,1]^dim becomes inactive.
+ * Single-precision FLA clouds with fold_dev set: at the start of each step a
+ * droplet with |det J| < tau_fold (single precision) enters the fold guard
+ * and one with |det J| > 4 tau_fold (double, from fold_dev) leaves it; while
+ * in it, the J and W part of its RK4 step is computed in double precision from
+ * the single-precision stage values of grad u and St (fold_steps counts them).
  * Carrier values are bi/trilinear interpolations of nodes_dev (cell index
  * clamped to the mesh).  FLA_ADVANCE_RESET_ACC zeroes acc before the first step.
  * The cloud and nodes must share the dtype; nodes_dev 16-byte aligned. */

@@ -416,6 +416,8 @@ typedef struct {
     double window_dt;    /* length of the window the sums cover */
     int per_cell;        /* 1: multiply S by the cell volume (per-cell amounts) */
     int fp32_decision;   /* 1: the q <= 9 truncation is decided on single-precision operands */
+    int plain;           /* with fp32_decision: det J decided in single precision throughout */
+    const int* fold;     /* per droplet, or NULL: 1 = J is the fold guard's double-precision copy */
 } ora_dep;
 
 typedef struct {
@@ -463,16 +465,25 @@ static void inv_sym(int d, const double* S, double det, double* P)
  * that decides an integer is taken in the kernel's precision on both sides).
  *  - |det J|: in double from the single-precision entries (2D, products exact);
  *    in 3D the cofactor expansion in single precision unless |det| < 1e-2 times
- *    the product of the rows' L1 norms (near a fold), then in double;
+ *    the product of the rows' L1 norms (near a fold), then in double; in double
+ *    from the given J for a droplet in the fold guard; and in single precision
+ *    throughout in the plain mode;
  *  - spherical kernel: h = clamp(h0 |det J|^p, h_min, h_max) in double, rounded,
  *    and r2max = 9 h^2 formed in double from the rounded h and rounded;
  *  - J-scaled kernel: Sigma and its inverse in single precision, one rounding
  *    per operation, in the order written below. */
-static double det_decision(int d, const double* J)
+static double det_decision(int d, const double* J, int plain, int fold)
 {
-    if (d == 2) return J[0] * J[3] - J[1] * J[2];
     float j[9];
-    for (int q = 0; q < 9; ++q) j[q] = (float)J[q];
+    for (int q = 0; q < d * d; ++q) j[q] = (float)J[q];
+    if (plain) {
+        /* plain single precision: the cofactor expansion in float */
+        if (d == 2) return (double)(j[0] * j[3] - j[1] * j[2]);
+        return (double)(j[0] * (j[4] * j[8] - j[5] * j[7]) - j[1] * (j[3] * j[8] - j[5] * j[6])
+                        + j[2] * (j[3] * j[7] - j[4] * j[6]));
+    }
+    /* a droplet in the fold guard: det J in double from its double-precision J */
+    if (fold || d == 2) return det_d(d, J);
     float detf = j[0] * (j[4] * j[8] - j[5] * j[7]) - j[1] * (j[3] * j[8] - j[5] * j[6])
                + j[2] * (j[3] * j[7] - j[4] * j[6]);
     float H = (fabsf(j[0]) + fabsf(j[1]) + fabsf(j[2])) * (fabsf(j[3]) + fabsf(j[4]) + fabsf(j[5]))
@@ -527,7 +538,7 @@ static void aniso_decision(const ora_dep* D, const double* J, double h0, float* 
  * the h_min^2 I floor), where f = min(1, (h_max^2 - d h_min^2)/tr(h0^2 J J^T))
  * caps tr(Sigma) <= h_max^2 so that the support stays within 3 h_max. */
 void ora_record(const ora_dep* D, const double* x, const double* J, const double* acc,
-                double n0, double h0, ora_rec* r)
+                double n0, double h0, int fold, ora_rec* r)
 {
     int d = D->dim;
     memset(r, 0, sizeof(*r));
@@ -543,7 +554,7 @@ void ora_record(const ora_dep* D, const double* x, const double* J, const double
         if (h > D->h_max) h = D->h_max;
         r->h = h;
         r->pref = 1.0 / h;                                 /* Eq. 14 prefactor */
-        double ad = fabs(det_decision(d, J));
+        double ad = fabs(det_decision(d, J, D->plain, fold));
         double hd = (D->p == 1.0) ? h0 * ad : h0 * pow(ad, D->p);
         if (hd < D->h_min) hd = D->h_min;
         if (hd > D->h_max) hd = D->h_max;
@@ -650,7 +661,7 @@ int ora_nw_deposit(const ora_dep* D, int n, const double* x, const double* J, co
         use[i] = contributes(d, x + (long)i * d, status[i]);
         if (use[i])
             ora_record(D, x + (long)i * d, J + (long)i * d * d, acc + (long)i * (1 + d),
-                       n0[batch[i]], h0[batch[i]], &rec[i]);
+                       n0[batch[i]], h0[batch[i]], D->fold ? D->fold[i] : 0, &rec[i]);
     }
     double V = cell_volume(D);
     for (long o = 0; o < n_out; ++o) {
@@ -719,7 +730,7 @@ int ora_nw_deposit_celllist_cells(const ora_dep* D, int n, const double* x, cons
     for (int i = 0; i < n; ++i)
         if (keys[i] != 0xFFFFFFFFu)
             ora_record(D, x + (long)i * d, J + (long)i * d * d, acc + (long)i * (1 + d),
-                       n0[batch[i]], h0[batch[i]], &rec[i]);
+                       n0[batch[i]], h0[batch[i]], D->fold ? D->fold[i] : 0, &rec[i]);
     int R = (int)floor(3.0 * D->h_max * N + 0.5) + 1;
     int* cand = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
     double V = cell_volume(D);
@@ -773,7 +784,7 @@ void ora_kernel_on_cells(const ora_dep* D, const double* x, const double* J, dou
     long nc = (d == 2) ? (long)N * N : (long)N * N * N;
     double acc0[4] = {0, 0, 0, 0};
     ora_rec r;
-    ora_record(D, x, J, acc0, n0, h0, &r);
+    ora_record(D, x, J, acc0, n0, h0, 0, &r);
     double norm = 1.0;
     if (normalised) {
         double c2pi = pow(2.0 * ORA_PI, 0.5 * d);
@@ -795,7 +806,7 @@ void ora_records(const ora_dep* D, int n, const double* x, const double* J, cons
     for (int i = 0; i < n; ++i) {
         ora_rec r;
         ora_record(D, x + (long)i * d, J + (long)i * d * d, acc + (long)i * (1 + d),
-                   n0[batch[i]], h0[batch[i]], &r);
+                   n0[batch[i]], h0[batch[i]], D->fold ? D->fold[i] : 0, &r);
         out[i * 4 + 0] = r.n;
         out[i * 4 + 1] = r.detJ;
         out[i * 4 + 2] = r.h;

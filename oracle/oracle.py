@@ -54,7 +54,8 @@ class _Setup(C.Structure):
 class _Dep(C.Structure):
     _fields_ = [("dim", C.c_int), ("N", C.c_int), ("kernel", C.c_int), ("h_min", C.c_double),
                 ("h_max", C.c_double), ("p", C.c_double), ("window_dt", C.c_double),
-                ("per_cell", C.c_int), ("fp32_decision", C.c_int)]
+                ("per_cell", C.c_int), ("fp32_decision", C.c_int), ("plain", C.c_int),
+                ("fold", C.c_void_p)]
 
 
 _lib = None
@@ -216,7 +217,10 @@ class Advancer:
 
 
 def dep_struct(wl=None, *, dim=None, N=None, kernel=None, h_min=None, h_max=None, p=None,
-               window_dt=None, per_cell=False, fp32_decision=False) -> _Dep:
+               window_dt=None, per_cell=False, fp32_decision=False, plain=False, fold=None) -> _Dep:
+    """Deposit settings.  plain: det J decided in single precision (plain mode);
+    fold: per-droplet flags of J given as the fold guard's double-precision copy
+    (the array is kept alive on the returned struct)."""
     D = _Dep()
     D.dim = dim if dim is not None else wl.dim
     D.N = N if N is not None else wl.n_cells_axis
@@ -227,6 +231,12 @@ def dep_struct(wl=None, *, dim=None, N=None, kernel=None, h_min=None, h_max=None
     D.window_dt = window_dt if window_dt is not None else wl.window * wl.dt
     D.per_cell = 1 if per_cell else 0
     D.fp32_decision = 1 if fp32_decision else 0
+    D.plain = 1 if plain else 0
+    if fold is not None:
+        D._fold_keep = np.ascontiguousarray(fold, dtype=np.int32)
+        D.fold = D._fold_keep.ctypes.data
+    else:
+        D.fold = None
     return D
 
 

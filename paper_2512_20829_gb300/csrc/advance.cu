@@ -7,6 +7,18 @@
 // taken at the first RK stage.  The state stays in registers across the fused
 // steps, so HBM is touched once per launch; the carrier node array (a few MB
 // in 2D) is read through the L1/L2 caches by the interpolation gathers.
+//
+// Fold guard (single-precision FLA clouds with a fold array): near a fold
+// caustic det J nearly vanishes (Eq. 6), so a droplet whose |det J| falls
+// below tau integrates the J, W part of its RK4 step in double precision from
+// the stage values of grad u and 1/St, keeping J, W in the fold array; it
+// returns to single precision once |det J| exceeds 4 tau.  Two launches keep
+// the common case at full speed: a screening pass integrates every droplet in
+// single precision and tests det J at each step start; a droplet that is in
+// the guard, or would enter it during the launch, is left untouched and
+// appended to a list, and a second pass integrates the listed droplets from
+// the same starting state with the guard logic.  The result equals one pass
+// that applies the guard at every step.
 #include "fla_internal.cuh"
 
 namespace fla {
@@ -23,7 +35,114 @@ struct AdvArgs {
     double dt, delta;
     int reset;
     DevStatus* status;
+    double* fold;        // fold-guard planes (FP64), or null
+    uint32_t* fold_list; // droplets handed from the screening pass to the guarded pass
+    unsigned int* fold_count;
+    float tau_fold;
 };
+
+enum { kPlain = 0, kScreen = 1, kGuarded = 2 };
+
+// Double-precision J, W of one droplet in the fold guard, and its RK4 stage
+// accumulators.
+template <int D>
+struct FoldState {
+    double y[2 * D * D];    // J then W
+    double ks[2 * D * D];
+    double ys[2 * D * D];
+};
+
+template <int D>
+struct StageG {
+    float g[D * D];
+};
+
+template <int D>
+__device__ __forceinline__ StageG<D> stage_g(const float* G)
+{
+    StageG<D> r;
+#pragma unroll
+    for (int q = 0; q < D * D; ++q) r.g[q] = G[q];
+    return r;
+}
+
+// One RK4 stage of J' = W, W' = (G J - W)/St in double precision (Eq. 8).
+// stage 0..3; hs = the stage's step (dt/2, dt/2, dt, and dt for the final combination).
+template <int D>
+__device__ __forceinline__ void fold_stage(FoldState<D>& f, StageG<D> G, float invSt, double hs, int stage)
+{
+    constexpr int Q = D * D;
+    const double iS = (double)invSt;
+    const double* src = stage == 0 ? f.y : f.ys;
+    double k[2 * Q];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            double gj = 0.0;
+#pragma unroll
+            for (int j = 0; j < D; ++j) gj = fma((double)G.g[i * D + j], src[j * D + c], gj);
+            k[i * D + c] = src[Q + i * D + c];
+            k[Q + i * D + c] = (gj - src[Q + i * D + c]) * iS;
+        }
+    if (stage == 0) {
+#pragma unroll
+        for (int q = 0; q < 2 * Q; ++q) { f.ks[q] = k[q]; f.ys[q] = fma(hs, k[q], f.y[q]); }
+    } else if (stage < 3) {
+#pragma unroll
+        for (int q = 0; q < 2 * Q; ++q) { f.ks[q] = fma(2.0, k[q], f.ks[q]); f.ys[q] = fma(hs, k[q], f.y[q]); }
+    } else {
+        const double sixth = hs / 6.0;
+#pragma unroll
+        for (int q = 0; q < 2 * Q; ++q) f.y[q] = fma(sixth, f.ks[q] + k[q], f.y[q]);
+    }
+}
+
+template <int D>
+__device__ __forceinline__ float det_f32(const float* J)
+{
+    if (D == 2) return J[0] * J[3] - J[1] * J[2];
+    return J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
+           J[2] * (J[3] * J[7] - J[4] * J[6]);
+}
+
+template <int D>
+__device__ __forceinline__ double fold_det(const FoldState<D>& f)
+{
+    const double* J = f.y;
+    if (D == 2) return J[0] * J[3] - J[1] * J[2];
+    return J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
+           J[2] * (J[3] * J[7] - J[4] * J[6]);
+}
+
+template <int D>
+__device__ __forceinline__ void fold_load(FoldState<D>& f, const double* fold, int64_t n, int64_t i)
+{
+    constexpr int NQ = 2 * D * D;
+#pragma unroll
+    for (int p = 0; p < fold_planes(D); ++p) {
+        const double2 a = *reinterpret_cast<const double2*>(fold + (p * n + i) * 4);
+        const double2 b = *reinterpret_cast<const double2*>(fold + (p * n + i) * 4 + 2);
+        const double v[4] = {a.x, a.y, b.x, b.y};
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (4 * p + c < NQ) f.y[4 * p + c] = v[c];
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void fold_store(const FoldState<D>& f, double* fold, int64_t n, int64_t i)
+{
+    constexpr int NQ = 2 * D * D;
+#pragma unroll
+    for (int p = 0; p < fold_planes(D); ++p) {
+        double v[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] = (4 * p + c < NQ) ? f.y[4 * p + c] : 0.0;
+        *reinterpret_cast<double2*>(fold + (p * n + i) * 4) = make_double2(v[0], v[1]);
+        *reinterpret_cast<double2*>(fold + (p * n + i) * 4 + 2) = make_double2(v[2], v[3]);
+    }
+}
 
 // Cell index of coordinate s = x N: floor clamped to [0, N-1]; positions past
 // the edge are extrapolated from the edge cell (RK stages may step outside).
@@ -103,15 +222,20 @@ __device__ __forceinline__ void rhs(const T* y, const T* u, const T* G, T invSt,
     }
 }
 
-template <typename T, int D, bool FLA>
-__device__ __forceinline__ int advance_one(const AdvArgs& a, int64_t i)
+template <typename T, int D, bool FLA, int MODE>
+__device__ __forceinline__ int advance_one(const AdvArgs& a, int64_t i, int& fold_steps)
 {
+    constexpr bool FOLD = MODE == kGuarded;
     constexpr int kind = FLA ? FLA_CLOUD_FLA : FLA_CLOUD_LPT;
     constexpr int NP = state_planes(kind, D);
     constexpr int NY = FLA ? 2 * D + 2 * D * D : 2 * D;
     constexpr int OA = acc_offset(kind, D);
     uint32_t meta = a.meta[i];
     if (meta & FLA_META_DEAD) return 0;
+    if (MODE == kScreen && (meta & FLA_META_FOLD)) {   // in the guard: the guarded pass takes it
+        a.fold_list[atomicAdd(a.fold_count, 1u)] = (uint32_t)i;
+        return 0;
+    }
     const fla_batch* B = a.batches + (meta & FLA_META_BATCH_MASK);
     const int ss = __ldg(&B->step_start);
     const int sd = __ldg(&B->step_dead);
@@ -137,6 +261,12 @@ __device__ __forceinline__ int advance_one(const AdvArgs& a, int64_t i)
     const T fN = T(a.N);
     T u[D], G[D * D];
     int integrated = 0;
+    FoldState<D> fs;
+    bool fold = false;
+    if (FOLD && (meta & FLA_META_FOLD)) {
+        fold = true;
+        fold_load<D>(fs, a.fold, a.n, i);
+    }
 
     for (int s = a.step0; s < a.step0 + a.nsteps; ++s) {
         if (!active) {
@@ -156,13 +286,36 @@ __device__ __forceinline__ int advance_one(const AdvArgs& a, int64_t i)
             for (int q = 0; q <= D; ++q) acc[q] = T(0);
             active = true;
             meta |= FLA_META_ACTIVE;
+            if (FOLD) {
+                fold = false;
+                meta &= ~FLA_META_FOLD;
+            }
         }
         if (s >= sd) {   // evaporated (deadline decided on the host in double precision)
             active = false;
             meta = (meta & ~FLA_META_ACTIVE) | FLA_META_DEAD;
             break;
         }
+        if (MODE == kScreen && fabsf(det_f32<D>((const float*)y + 2 * D)) < a.tau_fold) {
+            // would enter the guard: leave the state as it was and hand the droplet over
+            a.fold_list[atomicAdd(a.fold_count, 1u)] = (uint32_t)i;
+            return 0;
+        }
         ++integrated;
+        if (FOLD) {   // enter or leave the fold guard (hysteresis tau .. 4 tau)
+            if (!fold) {
+                if (fabsf(det_f32<D>((const float*)y + 2 * D)) < a.tau_fold) {
+                    fold = true;
+                    meta |= FLA_META_FOLD;
+#pragma unroll
+                    for (int q = 0; q < 2 * D * D; ++q) fs.y[q] = (double)y[2 * D + q];
+                }
+            } else if (fabs(fold_det<D>(fs)) > 4.0 * (double)a.tau_fold) {
+                fold = false;
+                meta &= ~FLA_META_FOLD;
+            }
+            fold_steps += fold ? 1 : 0;
+        }
         const T tau = T(s - ss) * h;                       // t - t0
         const T r2a = T(1) + delta * tau;                  // (r/r0)^2, Eq. 4
         const T r2b = T(1) + delta * (tau + half);
@@ -182,6 +335,7 @@ __device__ __forceinline__ int advance_one(const AdvArgs& a, int64_t i)
                 acc[1 + q] = fma(h, m * (u[q] - y[D + q]) * iSa + mdot * y[D + q], acc[1 + q]);
         }
         rhs<T, D, FLA>(y, u, G, iSa, k);
+        if (FOLD && fold) fold_stage<D>(fs, stage_g<D>((const float*)G), (float)iSa, 0.5 * a.dt, 0);
 #pragma unroll
         for (int q = 0; q < NY; ++q) {
             ks[q] = k[q];
@@ -190,6 +344,7 @@ __device__ __forceinline__ int advance_one(const AdvArgs& a, int64_t i)
         // stage 2
         interp<T, D>(nodes, a.N, fN, ys, u, G);
         rhs<T, D, FLA>(ys, u, G, iSb, k);
+        if (FOLD && fold) fold_stage<D>(fs, stage_g<D>((const float*)G), (float)iSb, 0.5 * a.dt, 1);
 #pragma unroll
         for (int q = 0; q < NY; ++q) {
             ks[q] = fma(T(2), k[q], ks[q]);
@@ -198,6 +353,7 @@ __device__ __forceinline__ int advance_one(const AdvArgs& a, int64_t i)
         // stage 3
         interp<T, D>(nodes, a.N, fN, ys, u, G);
         rhs<T, D, FLA>(ys, u, G, iSb, k);
+        if (FOLD && fold) fold_stage<D>(fs, stage_g<D>((const float*)G), (float)iSb, a.dt, 2);
 #pragma unroll
         for (int q = 0; q < NY; ++q) {
             ks[q] = fma(T(2), k[q], ks[q]);
@@ -208,6 +364,11 @@ __device__ __forceinline__ int advance_one(const AdvArgs& a, int64_t i)
         rhs<T, D, FLA>(ys, u, G, iSc, k);
 #pragma unroll
         for (int q = 0; q < NY; ++q) y[q] = fma(sixth, ks[q] + k[q], y[q]);
+        if (FOLD && fold) {   // double-precision J, W replace the single-precision update
+            fold_stage<D>(fs, stage_g<D>((const float*)G), (float)iSc, a.dt, 3);
+#pragma unroll
+            for (int q = 0; q < 2 * D * D; ++q) y[2 * D + q] = (T)fs.y[q];
+        }
         // outflow: leaving [0,1]^dim ends the trajectory
         bool out = false;
 #pragma unroll
@@ -224,39 +385,62 @@ __device__ __forceinline__ int advance_one(const AdvArgs& a, int64_t i)
     for (int q = 0; q <= D; ++q) sv[OA + q] = acc[q];
 #pragma unroll
     for (int p = 0; p < NP; ++p) store4<T>(state, p * a.n + i, sv + 4 * p);
+    if (FOLD && fold) fold_store<D>(fs, a.fold, a.n, i);
     a.meta[i] = meta;
     return integrated;
 }
 
-template <typename T, int D, bool FLA>
+template <typename T, int D, bool FLA, int MODE>
 __global__ void __launch_bounds__(128) k_advance(AdvArgs a)
 {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int n = i < a.n ? advance_one<T, D, FLA>(a, i) : 0;
-    // integrated droplet steps: one atomic per block
-    __shared__ int s_sum[4];
+    constexpr bool FOLD = MODE == kGuarded;
+    int nf = 0, n = 0;
+    if (MODE != kGuarded) {
+        const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        n = i < a.n ? advance_one<T, D, FLA, MODE>(a, i, nf) : 0;
+    } else {   // the listed droplets, grid-stride
+        const unsigned cnt = *a.fold_count;
+        for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x)
+            n += advance_one<T, D, FLA, MODE>(a, a.fold_list[k], nf);
+    }
+    // integrated droplet steps (and those in the fold guard): one atomic per block
+    __shared__ int s_sum[2][4];
     const int w = __reduce_add_sync(0xffffffffu, n);
-    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = w;
+    const int wf = FOLD ? __reduce_add_sync(0xffffffffu, nf) : 0;
+    if ((threadIdx.x & 31) == 0) {
+        s_sum[0][threadIdx.x >> 5] = w;
+        s_sum[1][threadIdx.x >> 5] = wf;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const long long t = (long long)s_sum[0] + s_sum[1] + s_sum[2] + s_sum[3];
+        const long long t = (long long)s_sum[0][0] + s_sum[0][1] + s_sum[0][2] + s_sum[0][3];
         if (t) atomicAdd(&a.status->droplet_steps, (unsigned long long)t);
+        if (FOLD) {
+            const long long tf = (long long)s_sum[1][0] + s_sum[1][1] + s_sum[1][2] + s_sum[1][3];
+            if (tf) atomicAdd(&a.status->fold_steps, (unsigned long long)tf);
+        }
     }
 }
 
-template <typename T, int D, bool FLA>
-cudaError_t launch_t(const AdvArgs& a, cudaStream_t s)
+template <typename T, int D, bool FLA, int MODE = kPlain>
+cudaError_t launch_t(const AdvArgs& a, cudaStream_t s, int guarded_blocks = 0)
 {
     const int threads = 128;
     const unsigned blocks = (unsigned)((a.n + threads - 1) / threads);
-    k_advance<T, D, FLA><<<blocks, threads, 0, s>>>(a);
+    k_advance<T, D, FLA, MODE><<<blocks, threads, 0, s>>>(a);
+    if constexpr (MODE == kScreen) {
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const unsigned gb = (unsigned)(guarded_blocks < (int)blocks ? guarded_blocks : (int)blocks);
+        k_advance<T, D, FLA, kGuarded><<<gb, threads, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_advance(const fla_cloud& cl, const fla_mesh& m, const void* nodes, int step0, int nsteps,
-                           double dt, bool reset, DevStatus* st, cudaStream_t s)
+                           double dt, bool reset, DevStatus* st, int num_sms, cudaStream_t s)
 {
     AdvArgs a{};
     a.status = st;
@@ -271,8 +455,20 @@ cudaError_t launch_advance(const fla_cloud& cl, const fla_mesh& m, const void* n
     a.dt = dt;
     a.delta = cl.delta;
     a.reset = reset ? 1 : 0;
+    a.fold = (double*)cl.fold_dev;
+    a.tau_fold = (float)cl.tau_fold;
     if (a.n == 0) return cudaSuccess;
     const bool fla = cl.kind == FLA_CLOUD_FLA;
+    if (cl.dtype == FLA_F32 && fla && a.fold) {
+        FoldLayout L = fold_layout(cl.dim, cl.n);
+        a.fold_list = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(cl.fold_dev) + L.list);
+        a.fold_count = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(cl.fold_dev) + L.count);
+        const cudaError_t e = cudaMemsetAsync(a.fold_count, 0, 4, s);
+        if (e != cudaSuccess) return e;
+        const int gb = 4 * (num_sms > 0 ? num_sms : 1);
+        if (cl.dim == 2) return launch_t<float, 2, true, kScreen>(a, s, gb);
+        return launch_t<float, 3, true, kScreen>(a, s, gb);
+    }
     if (cl.dtype == FLA_F32) {
         if (cl.dim == 2) return fla ? launch_t<float, 2, true>(a, s) : launch_t<float, 2, false>(a, s);
         return fla ? launch_t<float, 3, true>(a, s) : launch_t<float, 3, false>(a, s);

@@ -37,6 +37,10 @@ int cloud_ok(const fla_cloud* c, const fla_mesh* m)
         if (c->n_batches > (int32_t)FLA_META_BATCH_MASK + 1) return FLA_ERR_ARG;
     }
     if (!isfinite(c->delta)) return FLA_ERR_ARG;
+    if (c->fold_dev) {   // fold guard: single-precision FLA clouds only
+        if (c->kind != FLA_CLOUD_FLA || c->dtype != FLA_F32 || !aligned(c->fold_dev, 16)) return FLA_ERR_ARG;
+        if (!(c->tau_fold > 0) || !isfinite(c->tau_fold)) return FLA_ERR_ARG;
+    }
     return FLA_OK;
 }
 
@@ -341,10 +345,17 @@ int fla_advance(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, cons
     if (flags & ~FLA_ADVANCE_RESET_ACC) return FLA_ERR_ARG;
     if (cloud->n == 0 || nsteps == 0) return FLA_OK;
     if (!nodes_dev || !aligned(nodes_dev, 16)) return FLA_ERR_ARG;
-    PhaseScope ps(ctx, FLA_PHASE_ADVANCE, (cudaStream_t)stream, 1);
+    const bool guarded = cloud->fold_dev != nullptr;   // screening + guarded passes
+    PhaseScope ps(ctx, FLA_PHASE_ADVANCE, (cudaStream_t)stream, guarded ? 2 : 1);
     return cuda_status(launch_advance(*cloud, *mesh, nodes_dev, step0, nsteps, dt,
                                       (flags & FLA_ADVANCE_RESET_ACC) != 0, (DevStatus*)ctx->status_dev,
-                                      (cudaStream_t)stream));
+                                      ctx->num_sms, (cudaStream_t)stream));
+}
+
+size_t fla_fold_bytes(int32_t dim, int64_t n)
+{
+    if ((dim != 2 && dim != 3) || n < 0) return 0;
+    return fold_layout(dim, n).total;
 }
 
 int fla_workspace_size(const fla_mesh* mesh, int32_t dtype, int32_t kernel, int64_t n_droplets, size_t* bytes)
@@ -396,6 +407,7 @@ int fla_deposit_sources(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* me
     if (!(cfg->window_dt > 0) || !isfinite(cfg->window_dt) || !(cfg->p > 0) || !isfinite(cfg->p)) return FLA_ERR_ARG;
     if (cfg->kernel == FLA_KERNEL_ANISO && !(cfg->h_max * cfg->h_max > mesh->dim * cfg->h_min * cfg->h_min))
         return FLA_ERR_ARG;
+    if (cfg->precision != FLA_PREC_MIXED && cfg->precision != FLA_PREC_PLAIN) return FLA_ERR_ARG;
     if (cfg->h_max * mesh->n > 64.0) return FLA_ERR_UNSUPPORTED;   // support wider than 192 cells
     if (!out->s_mass_dev || !out->s_mom_dev) return FLA_ERR_ARG;
     const size_t T = cloud->dtype == FLA_F64 ? 8 : 4;

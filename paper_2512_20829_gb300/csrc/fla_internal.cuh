@@ -96,9 +96,26 @@ __host__ __device__ constexpr int record_values(int dim, int kernel)
 
 // Device status block layout (matches fla_device_status).
 struct DevStatus {
-    unsigned long long nonfinite, deposited, droplet_steps, pairs;
+    unsigned long long nonfinite, deposited, droplet_steps, pairs, fold_steps;
     unsigned int flags, pad;
 };
+static_assert(sizeof(DevStatus) == sizeof(fla_device_status), "status block mirrors fla_device_status");
+
+// Fold-guard array: planes of 4 doubles holding J[d*d] then W[d*d] (2D 8
+// values, 3D 18), then the hand-over list of the advance (n u32) and its
+// counter, each on a 16-byte boundary.
+__host__ __device__ constexpr int fold_planes(int dim) { return (2 * dim * dim + 3) / 4; }
+struct FoldLayout {
+    size_t list, count, total;
+};
+inline FoldLayout fold_layout(int dim, int64_t n)
+{
+    FoldLayout L{};
+    L.list = (size_t)fold_planes(dim) * (size_t)n * 4 * sizeof(double);
+    L.count = L.list + (((size_t)n * 4 + 15) & ~(size_t)15);
+    L.total = L.count + 16;
+    return L;
+}
 
 // Radix-sort scratch sizes (u32 words): tiles of 2,048 keys, digits of up to
 // 11 bits (2,048 values) for clouds of up to 2^21 droplets, 8 bits beyond.
@@ -119,7 +136,7 @@ struct SortWork {
 cudaError_t launch_carrier_sample(const fla_carrier_desc& c, const fla_mesh& m, double t, int dtype, void* nodes,
                                   cudaStream_t s);
 cudaError_t launch_advance(const fla_cloud& cl, const fla_mesh& m, const void* nodes, int step0, int nsteps,
-                           double dt, bool reset, DevStatus* st, cudaStream_t s);
+                           double dt, bool reset, DevStatus* st, int num_sms, cudaStream_t s);
 int sort_passes(int bits);
 int sort_passes_n(int bits, int64_t n);
 cudaError_t launch_cell_keys(const fla_cloud& cl, const fla_mesh& m, uint32_t* keys, cudaStream_t s);

@@ -6,12 +6,15 @@
 //   ANISO: Sigma = f h0^2 J J^T + h_min^2 I, f = min(1, (h_max^2 - d h_min^2)/tr(h0^2 J J^T)),
 //          weight det(Sigma)^-1/2 exp(-d^T Sigma^-1 d / 2).
 //
-// Precision (single-precision path): det J is formed in double where it can
-// cancel -- always in 2D (the products of single-precision entries are exact
-// in double), and in 3D when the single-precision cofactor expansion is below
-// 1e-2 of the product of the rows' L1 norms (near a fold caustic, where det J
-// nearly vanishes).  Everything else is single precision; double-precision
-// division and square root, which are slow on this GPU, are not used.
+// Precision (single-precision path, mixed mode): det J is formed in double
+// where it can cancel -- always in 2D (the products of single-precision
+// entries are exact in double), and in 3D when the single-precision cofactor
+// expansion is below 1e-2 of the product of the rows' L1 norms (near a fold
+// caustic, where det J nearly vanishes).  A droplet held in the advance's fold
+// guard takes det J from its double-precision J and n = n0/|det J| in double.
+// Everything else is single precision; double-precision division and square
+// root, which are slow on this GPU, are used for those droplets only.  Plain
+// mode forms det J and n in single precision for every droplet.
 // The values that decide the truncation test (h and 9 h^2; Sigma^-1) are
 // formed one rounding per operation in a fixed order: this file is compiled
 // without FMA contraction so that the decision is reproducible.
@@ -35,6 +38,8 @@ struct RecArgs {
     void* rec;
     unsigned int* ext_max;      // max over droplets of the squared support radius (float bits)
     DevStatus* status;
+    const double* fold;         // fold-guard planes (double J first), or null
+    int plain;                  // 1: det J and n in single precision
 };
 
 template <typename T, int D>
@@ -56,6 +61,38 @@ __device__ __forceinline__ double det_mixed(const float* j)
                     (fabsf(j[6]) + fabsf(j[7]) + fabsf(j[8]));
     if (fabsf(detf) < 0.01f * H) return det_double<float, 3>(j);   // near a fold: FP64
     return (double)detf;
+}
+
+template <int D>
+__device__ __forceinline__ float det_f32(const float* j)
+{
+    if (D == 2) return j[0] * j[3] - j[1] * j[2];
+    return j[0] * (j[4] * j[8] - j[5] * j[7]) - j[1] * (j[3] * j[8] - j[5] * j[6]) +
+           j[2] * (j[3] * j[7] - j[4] * j[6]);
+}
+
+// |det J| and n = n0/max(|det J|, 1e-12) of a single-precision droplet in the
+// selected precision (see file header).
+template <int D>
+__device__ __forceinline__ void det_and_n(const RecArgs& a, const float* J, uint32_t meta, int64_t i, double n0,
+                                          double& adet, float& n)
+{
+    if (a.plain) {
+        const float d = fabsf(det_f32<D>(J));
+        adet = (double)d;
+        n = (float)n0 / fmaxf(d, 1e-12f);
+        return;
+    }
+    if (a.fold && (meta & FLA_META_FOLD)) {
+        double jd[D * D];
+#pragma unroll
+        for (int q = 0; q < D * D; ++q) jd[q] = a.fold[((int64_t)(q >> 2) * a.n + i) * 4 + (q & 3)];
+        adet = fabs(det_double<double, D>(jd));
+        n = (float)(n0 / (adet > 1e-12 ? adet : 1e-12));
+        return;
+    }
+    adet = fabs(det_mixed<D>(J));
+    n = (float)n0 / fmaxf((float)adet, 1e-12f);
 }
 
 // Sigma and its inverse in single precision, in a fixed order (see file header).
@@ -108,13 +145,14 @@ __device__ __forceinline__ void sigma_inverse_f32(const float* j, float h0f, flo
 // Single-precision record.  Layouts: see fla_internal.cuh (c = -log2(e)/(2 h^2),
 // lih = log2(1/h), lpref = log2(det(Sigma)^-1/2): the weight is 2^(c r^2 + lih)).
 template <int D, int KER>
-__device__ __forceinline__ void record_f32(const RecArgs& a, const float* sv, double n0, double h0, float* r,
-                                           float& ext2, bool& bad)
+__device__ __forceinline__ void record_f32(const RecArgs& a, const float* sv, uint32_t meta, int64_t i, double n0,
+                                           double h0, float* r, float& ext2, bool& bad)
 {
     constexpr int OA = acc_offset(FLA_CLOUD_FLA, D);
     const float* J = sv + 2 * D;
-    const double adet = fabs(det_mixed<D>(J));
-    const float n = (float)n0 / fmaxf((float)adet, 1e-12f);
+    double adet;
+    float n;
+    det_and_n<D>(a, J, meta, i, n0, adet, n);
     float am[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int q = 0; q <= D; ++q) am[q] = n * sv[OA + q] * a.inv_window;
@@ -259,12 +297,13 @@ __global__ void __launch_bounds__(256) k_records(RecArgs a)
         T sv[NP * 4];
 #pragma unroll
         for (int p = 0; p < NP; ++p) load4<T>((const T*)a.state, p * a.n + i, sv + 4 * p);
-        const fla_batch* B = a.batches + (a.meta[i] & FLA_META_BATCH_MASK);
+        const uint32_t meta = a.meta[i];
+        const fla_batch* B = a.batches + (meta & FLA_META_BATCH_MASK);
         const double n0 = __ldg(&B->n0), h0 = __ldg(&B->h0);
         T r[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) r[q] = T(0);
-        if (sizeof(T) == 4) record_f32<D, KER>(a, (const float*)sv, n0, h0, (float*)r, ext2, bad);
+        if (sizeof(T) == 4) record_f32<D, KER>(a, (const float*)sv, meta, i, n0, h0, (float*)r, ext2, bad);
         else record_f64<D, KER>(a, (const double*)sv, n0, h0, (double*)r, ext2, bad);
 #pragma unroll
         for (int v = 0; v < RV / 4; ++v) store4<T>((T*)a.rec, j * (RV / 4) + v, r + 4 * v);
@@ -327,6 +366,8 @@ cudaError_t launch_records(const fla_cloud& cl, const fla_mesh& m, const fla_dep
     a.rec = rec;
     a.ext_max = ext_max;
     a.status = st;
+    a.fold = (const double*)cl.fold_dev;
+    a.plain = cfg.precision == FLA_PREC_PLAIN ? 1 : 0;
     if (a.n == 0) return cudaSuccess;
     const bool iso = cfg.kernel == FLA_KERNEL_ISO;
     if (cl.dtype == FLA_F32) {

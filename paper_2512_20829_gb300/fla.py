@@ -18,10 +18,12 @@ from . import inputs as I
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfla.so")
 
+ABI_VERSION = 2            # FLA_ABI_VERSION of include/fla.h that these structures mirror
 F32, F64 = 0, 1
 CLOUD_FLA, CLOUD_LPT = 0, 1
 KERNEL_ISO, KERNEL_ANISO = 0, 1
 META_BATCH_MASK = 0x00FFFFFF
+META_FOLD = 0x20000000
 META_DEAD = 0x40000000
 META_ACTIVE = 0x80000000
 ADVANCE_RESET_ACC = 1
@@ -30,7 +32,9 @@ MAX_VORTICES = 16
 EXPORTED = ["fla_abi_version", "fla_status_string", "fla_create", "fla_destroy", "fla_state_layout",
             "fla_carrier_nodes_bytes", "fla_carrier_sample", "fla_batch_deadline", "fla_advance",
             "fla_workspace_size", "fla_cell_bins", "fla_deposit_sources", "psicell_deposit", "fla_sync_status",
-            "fla_profile_enable", "fla_profile_read", "fla_phase_name"]
+            "fla_profile_enable", "fla_profile_read", "fla_phase_name", "fla_fold_bytes"]
+PREC_MIXED, PREC_PLAIN = 0, 1
+TAU_FOLD = 1e-2
 PHASES = ["carrier", "advance", "keys", "sort", "bins", "records", "gather", "psicell"]
 
 
@@ -52,12 +56,14 @@ class CarrierDesc(C.Structure):
 class Cloud(C.Structure):
     _fields_ = [("kind", C.c_int32), ("dim", C.c_int32), ("dtype", C.c_int32), ("n_batches", C.c_int32),
                 ("n", C.c_int64), ("state_dev", C.c_void_p), ("meta_dev", C.c_void_p),
-                ("batches_dev", C.c_void_p), ("delta", C.c_double)]
+                ("batches_dev", C.c_void_p), ("delta", C.c_double), ("fold_dev", C.c_void_p),
+                ("tau_fold", C.c_double)]
 
 
 class DepositCfg(C.Structure):
     _fields_ = [("kernel", C.c_int32), ("per_cell", C.c_int32), ("h_min", C.c_double), ("h_max", C.c_double),
-                ("p", C.c_double), ("window_dt", C.c_double)]
+                ("p", C.c_double), ("window_dt", C.c_double), ("precision", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class Sources(C.Structure):
@@ -70,7 +76,7 @@ class PsicellOut(C.Structure):
 
 class DeviceStatus(C.Structure):
     _fields_ = [("nonfinite", C.c_uint64), ("deposited", C.c_uint64), ("droplet_steps", C.c_uint64),
-                ("pairs", C.c_uint64), ("flags", C.c_uint32), ("pad", C.c_uint32)]
+                ("pairs", C.c_uint64), ("fold_steps", C.c_uint64), ("flags", C.c_uint32), ("pad", C.c_uint32)]
 
 
 BATCH_DTYPE = np.dtype([("St0", "<f8"), ("n0", "<f8"), ("h0", "<f8"), ("step_start", "<i4"),
@@ -111,6 +117,11 @@ def lib() -> C.CDLL:
         L.fla_profile_read.argtypes = [v, i32, P(C.c_double), P(i64), P(i64)]
         L.fla_phase_name.argtypes = [i32]
         L.fla_phase_name.restype = C.c_char_p
+        L.fla_fold_bytes.argtypes = [i32, i64]
+        L.fla_fold_bytes.restype = C.c_size_t
+        if L.fla_abi_version() != ABI_VERSION:
+            raise FlaError(f"{LIB_PATH} has ABI version {L.fla_abi_version()}, the binding expects "
+                           f"{ABI_VERSION}: rebuild it with __graft_entry__.build()")
         _lib = L
     return _lib
 
@@ -278,6 +289,17 @@ class DeviceCloud:
         self.meta = torch.from_numpy(np.ascontiguousarray(meta).view(np.int32)).to(device)
         self.batches = torch.from_numpy(np.ascontiguousarray(batches).view(np.uint8)).to(device)
         self.n_batches = int(len(batches))
+        self.fold = None
+        self.tau_fold = 0.0
+
+    def enable_fold(self, tau: float = TAU_FOLD):
+        """Attach the fold guard of single-precision FLA clouds: double-precision J, W
+        for droplets with |det J| < tau (see fla_cloud.fold_dev)."""
+        torch = _torch()
+        nb = lib().fla_fold_bytes(self.dim, self.n)
+        self.fold = torch.zeros(max(nb // 8, 4), dtype=torch.float64, device=self.state.device)
+        self.tau_fold = float(tau)
+        return self
 
     @classmethod
     def from_seeds(cls, cloud: I.Cloud, dim: int, delta: float, dt: float, dtype: int = F32, device="cuda"):
@@ -288,11 +310,30 @@ class DeviceCloud:
 
     @classmethod
     def from_state(cls, kind: int, dim: int, dtype: int, *, x, status, batch, batches: np.ndarray, delta=0.0,
-                   v=None, J=None, W=None, acc=None, device="cuda"):
+                   v=None, J=None, W=None, acc=None, fold=None, fold_J=None, fold_W=None, tau_fold=TAU_FOLD,
+                   device="cuda"):
+        """Upload a given state.  fold (bool per droplet) with fold_J, fold_W (double
+        precision) attaches the fold guard with those droplets inside it."""
         npd = np.float32 if dtype == F32 else np.float64
         n = np.asarray(x).shape[0]
         planes = pack_state(kind, dim, n, npd, x=x, v=v, J=J, W=W, acc=acc)
-        return cls(kind, dim, dtype, planes, meta_words(status, batch), batches, delta, device)
+        meta = meta_words(status, batch)
+        if fold is not None:
+            meta = np.where(np.asarray(fold, bool), meta | META_FOLD, meta).astype(np.uint32)
+        c = cls(kind, dim, dtype, planes, meta, batches, delta, device)
+        if fold is not None:
+            torch = _torch()
+            c.enable_fold(tau_fold)
+            q = dim * dim
+            npl = (2 * q + 3) // 4
+            flat = np.zeros((n, npl * 4))
+            if fold_J is not None:
+                flat[:, :q] = np.asarray(fold_J, np.float64).reshape(n, q)
+            if fold_W is not None:
+                flat[:, q:2 * q] = np.asarray(fold_W, np.float64).reshape(n, q)
+            planes_f = np.ascontiguousarray(flat.reshape(n, npl, 4).transpose(1, 0, 2))
+            c.fold[: planes_f.size].copy_(torch.from_numpy(planes_f.ravel()))
+        return c
 
     def struct(self) -> Cloud:
         c = Cloud()
@@ -302,6 +343,8 @@ class DeviceCloud:
         c.meta_dev = self.meta.data_ptr()
         c.batches_dev = self.batches.data_ptr()
         c.delta = self.delta
+        c.fold_dev = self.fold.data_ptr() if self.fold is not None else None
+        c.tau_fold = self.tau_fold
         return c
 
     def to_host(self) -> dict:
@@ -309,6 +352,13 @@ class DeviceCloud:
         meta = self.meta.cpu().numpy().view(np.uint32)
         d["status"] = status_of(meta)
         d["batch"] = (meta & META_BATCH_MASK).astype(np.int32)
+        d["fold"] = ((meta & META_FOLD) != 0) & (d["status"] == 1)
+        if self.fold is not None:
+            q = self.dim * self.dim
+            planes = self.fold.cpu().numpy()[: (2 * q + 3) // 4 * self.n * 4].reshape(-1, self.n, 4)
+            flat = planes.transpose(1, 0, 2).reshape(self.n, -1)
+            d["fold_J"] = flat[:, :q].reshape(self.n, self.dim, self.dim)
+            d["fold_W"] = flat[:, q:2 * q].reshape(self.n, self.dim, self.dim)
         return d
 
 
@@ -364,8 +414,9 @@ def cell_bins(ctx: Context, cloud: DeviceCloud, m: Mesh, ws, stream=None):
 
 
 def deposit_cfg(kernel: int, h_min: float, h_max: float, window_dt: float, p: float = 1.0,
-                per_cell: bool = False) -> DepositCfg:
-    return DepositCfg(int(kernel), 1 if per_cell else 0, float(h_min), float(h_max), float(p), float(window_dt))
+                per_cell: bool = False, precision: int = PREC_MIXED) -> DepositCfg:
+    return DepositCfg(int(kernel), 1 if per_cell else 0, float(h_min), float(h_max), float(p), float(window_dt),
+                      int(precision), 0)
 
 
 class SourceFields:
@@ -427,13 +478,18 @@ class Simulation:
     window on one GPU: carrier sample -> advance (fused window) -> deposit."""
 
     def __init__(self, ctx: Context, wl: I.Workload, dtype: int = F32, with_psicell: bool = False,
-                 device="cuda"):
+                 device="cuda", precision: int = PREC_MIXED, fold_guard: bool = False,
+                 tau_fold: float = TAU_FOLD):
+        """precision (single-precision clouds): PREC_MIXED forms det J and n in double
+        where det J cancels; PREC_PLAIN keeps them single.  fold_guard (mixed only)
+        attaches the advance's fold guard: double-precision J, W while |det J| < tau_fold."""
         self.ctx, self.wl, self.dtype = ctx, wl, dtype
+        self.precision, self.fold_guard, self.tau_fold = precision, fold_guard, tau_fold
         self.m = mesh(wl.dim, wl.n_cells_axis)
         self.desc = carrier_desc(wl.carrier)
         self.nodes = nodes_buffer(self.m, dtype, device)
-        self.fla = DeviceCloud.from_seeds(wl.fla, wl.dim, wl.delta, wl.dt, dtype, device)
-        self.cfg = deposit_cfg(wl.kernel, wl.h_min, wl.h_max, wl.window * wl.dt, wl.p)
+        self.fla = self._fla_cloud(device)
+        self.cfg = deposit_cfg(wl.kernel, wl.h_min, wl.h_max, wl.window * wl.dt, wl.p, precision=precision)
         self.out = SourceFields(self.m, dtype, device)
         n_ws = self.fla.n
         self.lpt = None
@@ -448,11 +504,18 @@ class Simulation:
     def reset(self):
         """Back to the seeds (device-side copies only re-upload the initial planes)."""
         wl = self.wl
-        self.fla = DeviceCloud.from_seeds(wl.fla, wl.dim, wl.delta, wl.dt, self.dtype, self.fla.state.device)
+        self.fla = self._fla_cloud(self.fla.state.device)
         if self.lpt is not None:
             self.lpt = DeviceCloud.from_seeds(wl.lpt, wl.dim, wl.delta, wl.dt, self.dtype, self.lpt.state.device)
         self.step = 0
         self._sampled_t = None
+
+    def _fla_cloud(self, device):
+        wl = self.wl
+        c = DeviceCloud.from_seeds(wl.fla, wl.dim, wl.delta, wl.dt, self.dtype, device)
+        if self.dtype == F32 and self.precision == PREC_MIXED and self.fold_guard:
+            c.enable_fold(self.tau_fold)
+        return c
 
     def window(self, deposit: bool = True, with_psicell: bool = True, stream=None):
         wl = self.wl

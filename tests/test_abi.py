@@ -49,7 +49,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert lib.fla_abi_version() == 1
+    assert lib.fla_abi_version() == fla.ABI_VERSION
     for code in (0, -1, -2, -3, -4, -5, -6):
         assert lib.fla_status_string(code)
     assert lib.fla_status_string(42) == b"unknown status"

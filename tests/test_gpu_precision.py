@@ -1,0 +1,242 @@
+"""Precision pattern of the single-precision path: the fold guard of the advance
+(double-precision J, W while |det J| is small), det J and n = n0/|det J| in
+double precision near folds in the records, and the plain single-precision
+mode beside it.  Every case is checked against the FP64 oracle.
+
+* a rotated linear strain drives det J through zero (the fold caustic of the
+  closed-form pin P3, rotated so that det J cancels in single precision);
+* sparse droplets with |J| ~ 10-30 and |det J| ~ 1e-5-1e-3, one per kernel
+  support, so that each cell's source is -n phi of one droplet (pin P6) and
+  the error of n is read directly;
+* deposit parity (identical truncation decisions) with droplets inside the
+  fold guard, and in the plain mode;
+* the reduced jet end to end: per-field error of plain and mixed against the
+  oracle, over all cells and with the caustic cells (any contributor with
+  |det J| < 1e-2) taken out.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from helpers import rel_l2
+from oracle import oracle as O
+from paper_2512_20829_gb300 import fla
+from paper_2512_20829_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = fla.Context(0)
+    yield c
+    c.close()
+
+
+def _rot(t):
+    return np.array([[math.cos(t), -math.sin(t)], [math.sin(t), math.cos(t)]])
+
+
+def _strain_workload(n_seeds=256, nsteps=300, window=1):
+    """u = A (x - x_c), A = R diag(alpha, -alpha) R^T with alpha = 10, St = 1, no
+    evaporation: J solves St J'' + J' = A J, so along the compressive axis
+    St q'' + q' + alpha q = 0 oscillates (4 alpha St > 1) and det J changes sign."""
+    alpha = 10.0
+    R = _rot(math.radians(30.0))
+    A2 = R @ np.diag([alpha, -alpha]) @ R.T
+    A = np.zeros((3, 3))
+    A[:2, :2] = A2
+    car = I.Carrier(kind=I.CARRIER_LINEAR, dim=2, A=A, xref=np.array([0.5, 0.5, 0.0]))
+    rng = np.random.default_rng(44)
+    x0 = 0.5 + rng.uniform(-0.02, 0.02, (n_seeds, 2))
+    cl = I.Cloud(kind=I.CLOUD_FLA, x0=x0, batch=np.zeros(n_seeds, np.int32), step_start=np.zeros(1, np.int32),
+                 St0=np.array([1.0]), n0=np.array([1.0]), h0=np.array([1.0 / 64]))
+    return I.Workload(name="rotated_strain", dim=2, n_cells_axis=64, dt=1e-3, nsteps=nsteps, window=window,
+                      delta=0.0, carrier=car, fla=cl, lpt=None, kernel=I.KERNEL_ISO, h_min=0.5 / 64,
+                      h_max=4.0 / 64)
+
+
+def test_fold_guard_rotated_strain(ctx):
+    """det J = p q with p growing and q oscillating crosses zero near t = 0.1; the
+    state is compared with the oracle after every step."""
+    wl = _strain_workload()
+    adv = O.Advancer(wl, wl.fla)
+    st = O.initial_state(wl.fla, 2)
+    sims = {p: fla.Simulation(ctx, wl, dtype=fla.F32, precision=p, fold_guard=p == fla.PREC_MIXED)
+            for p in (fla.PREC_PLAIN, fla.PREC_MIXED)}
+    ctx.sync_status(reset=True)
+    err = {p: [] for p in sims}
+    flagged_total = 0
+    for s in range(0, wl.nsteps, wl.window):
+        adv.advance(st, s, wl.window, reset_acc=True)
+        for p, sim in sims.items():
+            sim.window(deposit=False)
+        torch.cuda.synchronize()
+        det_o = np.linalg.det(st.J)
+        band = np.abs(det_o) < 1e-2
+        for p, sim in sims.items():
+            g = sim.fla.to_host()
+            J = g["J"].astype(np.float64)
+            if p == fla.PREC_MIXED:
+                f = g["fold"]
+                flagged_total += int(f.sum())
+                # the single-precision J of a guarded droplet is its double J rounded
+                assert np.array_equal(g["fold_J"][f].astype(np.float32), g["J"][f])
+                J = np.where(f[:, None, None], g["fold_J"], J)
+            jn = np.linalg.norm(st.J, axis=(1, 2))
+            dJ = np.abs(J - st.J).max(axis=(1, 2))
+            assert np.all(dJ <= 1e-4 * (1 + jn) ** 2), (p, s, (dJ / (1 + jn) ** 2).max())
+            if band.any():
+                err[p].append(np.abs(np.linalg.det(J) - det_o)[band])
+    status = ctx.sync_status(reset=True)
+    assert flagged_total > 0 and status.fold_steps > 0
+    e_plain = np.concatenate(err[fla.PREC_PLAIN])
+    e_mixed = np.concatenate(err[fla.PREC_MIXED])
+    print(f"\n|det J - det J_oracle| in the fold band: plain max {e_plain.max():.3e} median "
+          f"{np.median(e_plain):.3e}; fold guard max {e_mixed.max():.3e} median {np.median(e_mixed):.3e}; "
+          f"{status.fold_steps} guarded droplet steps")
+    assert e_mixed.max() <= 1e-5
+
+
+def _sparse_fold_state(n_side=10, N=256, seed=3):
+    """One droplet per 25 x 25 cells (no two supports overlap), each with a
+    double-precision J of norm 10-30 and |det J| in [1e-5, 1e-3]."""
+    rng = np.random.default_rng(seed)
+    n = n_side * n_side
+    c = (np.arange(n_side) + 0.5) / n_side
+    X, Y = np.meshgrid(c, c, indexing="xy")
+    x = np.stack([X.ravel(), Y.ravel()], axis=1) + rng.uniform(-0.3, 0.3, (n, 2)) / N
+    s1 = rng.uniform(10.0, 30.0, n)
+    det = rng.choice([-1.0, 1.0], n) * 10.0 ** rng.uniform(-5, -3, n)
+    Jd = np.stack([_rot(a) @ np.diag([s1[i], det[i] / s1[i]]) @ _rot(b)
+                   for i, (a, b) in enumerate(rng.uniform(0, math.pi, (n, 2)))])
+    acc = np.zeros((n, 3))
+    acc[:, 0] = -1e-3 * rng.uniform(0.5, 1.5, n)
+    acc[:, 1:] = 1e-2 * rng.standard_normal((n, 2))
+    return I.CloudState(dim=2, x=x.astype(np.float32), v=np.zeros((n, 2), np.float32),
+                        J=Jd.astype(np.float32), W=np.zeros((n, 2, 2), np.float32), acc=acc.astype(np.float32),
+                        status=np.ones(n, np.int32), batch=np.zeros(n, np.int32), n0=np.array([1.0]),
+                        h0=np.array([2.0 / N])), Jd
+
+
+def test_records_n_near_folds(ctx):
+    """n = n0/|det J| of droplets near a fold: from the fold guard's double J (mixed)
+    it matches the FP64 value; from single-precision J it carries the cancellation
+    error u |J|^2 / |det J|."""
+    N = 256
+    s, Jd = _sparse_fold_state(N=N)
+    n = s.x.shape[0]
+    m = fla.mesh(2, N)
+    tb = np.zeros(1, fla.BATCH_DTYPE)
+    tb["St0"], tb["n0"], tb["h0"], tb["step_dead"] = 1.0, 1.0, s.h0[0], 2**31 - 1
+    # truth: S at the droplet's own cell is -n acc_m / T with n from the double J
+    key = (np.floor(s.x[:, 0].astype(np.float64) * N) + N * np.floor(s.x[:, 1].astype(np.float64) * N)).astype(int)
+    truth = -(1.0 / np.abs(np.linalg.det(Jd))) * s.acc[:, 0].astype(np.float64) / 0.01
+    rel = {}
+    for name, prec, fold in (("plain", fla.PREC_PLAIN, False), ("mixed", fla.PREC_MIXED, False),
+                             ("mixed+guard", fla.PREC_MIXED, True)):
+        kw = dict(fold=np.ones(n, bool), fold_J=Jd, fold_W=np.zeros_like(Jd)) if fold else {}
+        cl = fla.DeviceCloud.from_state(fla.CLOUD_FLA, 2, fla.F32, x=s.x, v=s.v, J=s.J, W=s.W, acc=s.acc,
+                                        status=s.status, batch=s.batch, batches=tb, **kw)
+        ws = fla.aligned_ws(fla.workspace(m, fla.F32, fla.KERNEL_ISO, n))
+        out = fla.SourceFields(m, fla.F32)
+        fla.deposit_sources(ctx, cl, m, fla.deposit_cfg(fla.KERNEL_ISO, 0.5 / N, 4.0 / N, 0.01, precision=prec),
+                            out, ws)
+        torch.cuda.synchronize()
+        g = out.s_mass.double().cpu().numpy()[key]
+        rel[name] = np.abs(g - truth) / np.abs(truth)
+    print("\nrelative error of n0/|det J| near folds: " +
+          ", ".join(f"{k} max {v.max():.2e} median {np.median(v):.2e}" for k, v in rel.items()))
+    assert rel["mixed+guard"].max() <= 1e-6
+    assert np.median(rel["plain"]) >= 100 * np.median(rel["mixed+guard"])
+
+
+@pytest.mark.parametrize("dim,kernel", [(2, I.KERNEL_ISO), (2, I.KERNEL_ANISO), (3, I.KERNEL_ISO),
+                                        (3, I.KERNEL_ANISO)])
+@pytest.mark.parametrize("prec", [fla.PREC_MIXED, fla.PREC_PLAIN])
+def test_deposit_parity_fold_and_plain(ctx, dim, kernel, prec):
+    """GPU deposit vs the oracle deciding the truncation on the same operands:
+    with a fifth of the droplets inside the fold guard (their J given in double
+    precision), and in the plain mode."""
+    N = 64 if dim == 2 else 24
+    n = 6000 if dim == 2 else 8000
+    s = I.synthetic_state(dim, n, N, seed=70 + dim + 3 * kernel, band=(0.2, 0.8), h0_cells=2.0, jac_spread=0.4)
+    rng = np.random.default_rng(9)
+    fold = (rng.uniform(size=n) < 0.2) & (s.status == 1) if prec == fla.PREC_MIXED else None
+    Jd = s.J.astype(np.float64) * (1.0 + 1e-7 * rng.standard_normal(s.J.shape))
+    if prec == fla.PREC_PLAIN:
+        # the plain mode's single-precision det J carries u |J|^d / |det J| of relative
+        # error into n, which the oracle's double det does not: keep J well conditioned
+        # so that this stays far below the tolerance (its size near folds is measured
+        # by test_records_n_near_folds)
+        sc = np.exp(rng.uniform(-1.0, 1.0, (n, 1, 1)))
+        Jd = sc * (np.eye(dim)[None] + 0.15 * rng.standard_normal((n, dim, dim)))
+    J32 = Jd.astype(np.float32)
+    m = fla.mesh(dim, N)
+    nb = len(s.n0)
+    tb = np.zeros(nb, fla.BATCH_DTYPE)
+    tb["St0"], tb["n0"], tb["h0"], tb["step_dead"] = 1.0, s.n0, s.h0, 2**31 - 1
+    kw = dict(fold=fold, fold_J=Jd, fold_W=np.zeros_like(Jd)) if fold is not None else {}
+    cl = fla.DeviceCloud.from_state(fla.CLOUD_FLA, dim, fla.F32, x=s.x, v=s.v, J=J32, W=s.W, acc=s.acc,
+                                    status=s.status, batch=s.batch, batches=tb, **kw)
+    h_min, h_max = 0.5 / N, (4.0 if kernel == I.KERNEL_ISO else 2.0) / N
+    ws = fla.aligned_ws(fla.workspace(m, fla.F32, kernel, n))
+    out = fla.SourceFields(m, fla.F32)
+    fla.deposit_sources(ctx, cl, m, fla.deposit_cfg(kernel, h_min, h_max, 0.01, precision=prec), out, ws)
+    torch.cuda.synchronize()
+    # oracle: J of guarded droplets is the double copy; others the single-precision values
+    Jo = np.where(fold[:, None, None], Jd, J32.astype(np.float64)) if fold is not None else J32.astype(np.float64)
+    D = O.dep_struct(dim=dim, N=N, kernel=kernel, h_min=h_min, h_max=h_max, p=1.0, window_dt=0.01,
+                     fp32_decision=True, plain=prec == fla.PREC_PLAIN,
+                     fold=fold.astype(np.int32) if fold is not None else None)
+    om, ov, od = O.nw_deposit_celllist(D, s.x, Jo, s.acc, s.status, s.batch, s.n0, s.h0)
+    # sum K |a| / D: the size of the terms each source value averages
+    am, av, _ = O.nw_deposit_celllist(D, s.x, Jo, np.abs(s.acc), s.status, s.batch, s.n0, s.h0)
+    gd = out.dsum.double().cpu().numpy()
+    gm = out.s_mass.double().cpu().numpy()
+    gv = out.s_mom.double().cpu().numpy().T
+    assert np.array_equal(gd > 0, od > 0)
+    assert np.all(np.abs(gm - om) <= 1e-4 * np.abs(am) + 1e-30)
+    assert np.all(np.abs(gv - ov) <= 1e-4 * np.abs(av) + 1e-30)
+
+
+def test_precision_report_jet(ctx):
+    """Reduced jet (128^2, 16,384 seeds, 1,000 steps): error of every source field
+    against the FP64 oracle for the plain and the mixed single-precision forms,
+    over all cells and outside the caustic cells."""
+    wl = I.jet_vortex_2d(scale=4, lpt_per_batch=0)
+    st = O.run(wl)
+    D = O.dep_struct(wl)
+    om, ov, od = O.nw_deposit_celllist(D, st.x, st.J, st.acc, st.status, st.batch, wl.fla.n0, wl.fla.h0)
+    # caustic cells: any contributor with |det J| < 1e-2 (R20)
+    caustic_droplets = (st.status == 1) & (np.abs(np.linalg.det(st.J)) < 1e-2)
+    stc = np.where(caustic_droplets, st.status, 0).astype(np.int32)
+    _, _, dc = O.nw_deposit_celllist(D, st.x, st.J, st.acc, stc, st.batch, wl.fla.n0, wl.fla.h0)
+    caustic = dc > 0
+    rows = {}
+    for name, prec, guard in (("plain", fla.PREC_PLAIN, False), ("mixed", fla.PREC_MIXED, False),
+                              ("mixed+guard", fla.PREC_MIXED, True)):
+        sim = fla.Simulation(ctx, wl, dtype=fla.F32, precision=prec, fold_guard=guard)
+        ctx.sync_status(reset=True)
+        sim.run(deposit_every=True)
+        torch.cuda.synchronize()
+        status = ctx.sync_status(reset=True)
+        gm = sim.out.s_mass.double().cpu().numpy()
+        gv = sim.out.s_mom.double().cpu().numpy().T
+        gd = sim.out.dsum.double().cpu().numpy()
+        r = {}
+        for fname, g, o in (("S_mass", gm, om), ("S_mom_x", gv[:, 0], ov[:, 0]), ("S_mom_y", gv[:, 1], ov[:, 1]),
+                            ("D", gd, od)):
+            r[fname] = (rel_l2(g, o), rel_l2(g[~caustic], o[~caustic]),
+                        rel_l2(g[caustic], o[caustic]) if caustic.any() else 0.0)
+        r["fold_steps"] = status.fold_steps
+        rows[name] = r
+    print(f"\ncaustic cells {int(caustic.sum())} of {caustic.size}; caustic droplets {int(caustic_droplets.sum())}")
+    for name, r in rows.items():
+        print(name, {k: (tuple(f"{x:.2e}" for x in v) if isinstance(v, tuple) else v) for k, v in r.items()})
+    for name, r in rows.items():
+        for fname in ("S_mass", "S_mom_x", "S_mom_y", "D"):
+            assert r[fname][1] <= 1e-4, (name, fname, r[fname])
+    assert rows["mixed+guard"]["fold_steps"] > 0 and rows["mixed"]["fold_steps"] == 0
