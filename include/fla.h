@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define FLA_ABI_VERSION 2
+#define FLA_ABI_VERSION 3
 
 /* cudaStream_t without including the CUDA headers. */
 typedef struct CUstream_st* fla_stream_t;
@@ -156,6 +156,10 @@ typedef struct {
                                   or FLA_PREC_PLAIN (det J, 1/|det J| in single precision throughout);
                                   ignored by double-precision clouds */
     int32_t reserved;          /* 0 */
+    const void* mlp_dev;       /* packed learned correction (fla_mlp_pack), or NULL for the plain
+                                  method; single-precision clouds with FLA_KERNEL_ISO only */
+    float* mlp_out_dev;        /* optional (with mlp_dev): g(f_i) per droplet index (n floats);
+                                  entries of droplets that are not deposited are left as they are */
 } fla_deposit_cfg;
 
 enum { FLA_PREC_MIXED = 0, FLA_PREC_PLAIN = 1 };
@@ -297,6 +301,36 @@ int fla_deposit_sources(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* me
  * fixed order. */
 int psicell_deposit(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, double window_dt,
                     int32_t per_cell, const fla_psicell_out* out, void* workspace_dev, size_t workspace_bytes,
+                    fla_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Learned bandwidth correction.  The paper has no counterpart: a small
+ * network g corrects each droplet's smoothing length,
+ *   h = clamp(h0 |det J|^p * exp(clip(g(f), -2, 2)), h_min, h_max),
+ * for the spherical kernel (Eq. 14 with h of Eq. 15).  g is
+ * 6 -> 64 -> 64 -> 64 -> 1 with SiLU after the hidden layers, evaluated on the
+ * tensor cores with BF16 weights and activations and FP32 accumulation (the
+ * last layer in FP32 on the CUDA cores).  The features of a droplet are
+ *   f0 = ln ||J||_F^2 / 8,  f1 = ln ||cof J||_F^2 / 8 (3D) or ln det(J)^2 / 8 (2D),
+ *   f2 = ln |det J| / 8,    f3 = ln n / 8 (n of Eq. 6),
+ *   f4 = ln(h0 |det J|^(1/dim) / dx) / 4,  f5 = min(|det J|, 4) / 4,
+ * logarithms taken of max(x, 1e-30).
+ * Parameters: FLA_MLP_PARAMS FP32 masters W1[64][6], b1[64], W2[64][64],
+ * b2[64], W3[64][64], b3[64], W4[64], b4 (rows are output units).
+ * ------------------------------------------------------------------------ */
+#define FLA_MLP_FEATURES 6
+#define FLA_MLP_HIDDEN 64
+#define FLA_MLP_PARAMS 8833
+#define FLA_MLP_PACKED_BYTES 19472
+
+/* Round the FP32 masters params_dev[FLA_MLP_PARAMS] into the packed device
+ * image the tensor-core kernels read (packed_dev, FLA_MLP_PACKED_BYTES,
+ * 16-byte aligned, caller-owned).  Re-pack after every parameter update. */
+int fla_mlp_pack(fla_ctx* ctx, const float* params_dev, void* packed_dev, fla_stream_t stream);
+
+/* c_i = g(f_i) for n feature rows features_dev[n][6] (FP32; rounded to BF16
+ * on the way in) into out_dev[n]. */
+int fla_mlp_forward(fla_ctx* ctx, const void* packed_dev, const float* features_dev, int64_t n, float* out_dev,
                     fla_stream_t stream);
 
 /* Read the device status block (synchronises `stream`); reset != 0 zeroes it

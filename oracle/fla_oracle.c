@@ -418,7 +418,13 @@ typedef struct {
     int fp32_decision;   /* 1: the q <= 9 truncation is decided on single-precision operands */
     int plain;           /* with fp32_decision: det J decided in single precision throughout */
     const int* fold;     /* per droplet, or NULL: 1 = J is the fold guard's double-precision copy */
+    const float* mlp;    /* learned bandwidth correction (spherical kernel), or NULL */
 } ora_dep;
+
+/* learned bandwidth correction, defined at the end of this file */
+void ora_mlp_features(int d, const double* J, double n0, double h0, double dx, double* f);
+double ora_mlp_forward(const float* P, const double* f, const double* fe, double* bound, double* act, double* zs);
+void ora_mlp_backward(const float* P, const double* f, double dLdc, double* grad);
 
 typedef struct {
     double x[3];
@@ -431,6 +437,9 @@ typedef struct {
     float xf[3];         /* single-precision operands of the truncation decision */
     float r2max_f;
     float Pf[9];
+    double c;            /* learned correction g(f) (0 without the network) */
+    int dh_dc;           /* 1 when h moves with c: c inside (-2, 2) and h not clamped */
+    double f[6];         /* the network's features */
 } ora_rec;
 
 static double det_d(int d, const double* J)
@@ -550,12 +559,22 @@ void ora_record(const ora_dep* D, const double* x, const double* J, const double
     for (int a = 0; a < 1 + d; ++a) r->a[a] = r->n * acc[a] / D->window_dt;
     if (D->kernel == 0) {
         double h = (D->p == 1.0) ? h0 * adet : h0 * pow(adet, D->p);   /* Eq. 15 */
+        double corr = 1.0;
+        if (D->mlp) {      /* learned correction: h <- h exp(clip(g(f), -2, 2)) */
+            ora_mlp_features(d, J, n0, h0, 1.0 / D->N, r->f);
+            r->c = ora_mlp_forward(D->mlp, r->f, NULL, NULL, NULL, NULL);
+            double ct = r->c < -2.0 ? -2.0 : (r->c > 2.0 ? 2.0 : r->c);
+            corr = exp(ct);
+            h *= corr;
+            r->dh_dc = (r->c > -2.0 && r->c < 2.0 && h > D->h_min && h < D->h_max);
+        }
         if (h < D->h_min) h = D->h_min;
         if (h > D->h_max) h = D->h_max;
         r->h = h;
         r->pref = 1.0 / h;                                 /* Eq. 14 prefactor */
         double ad = fabs(det_decision(d, J, D->plain, fold));
         double hd = (D->p == 1.0) ? h0 * ad : h0 * pow(ad, D->p);
+        hd *= corr;
         if (hd < D->h_min) hd = D->h_min;
         if (hd > D->h_max) hd = D->h_max;
         r->r2max_f = (float)(9.0 * (double)(float)hd * (double)(float)hd);
@@ -847,4 +866,366 @@ int ora_psicell(const ora_dep* D, int n, const double* x, const double* acc, con
     }
     free(keys);
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Learned bandwidth correction (no counterpart in the paper)                */
+/* ------------------------------------------------------------------------ */
+/*
+ * A small MLP g maps per-droplet features to a correction of the smoothing
+ * length of Eq. 15: h = clamp(h0 |det J|^p * exp(clip(g(f), -2, 2)), h_min, h_max).
+ * g is 6 -> 64 -> 64 -> 64 -> 1 with SiLU after the three hidden layers.
+ * Parameters are single-precision masters; the forward uses them rounded to
+ * bfloat16 (round to nearest even), the biases unrounded, and rounds the
+ * inputs of the first three layers to bfloat16 as a tensor-core forward does.
+ * Arithmetic here is double precision.
+ *
+ * Features (readings of "local J invariants, n and neighbour spacing"):
+ *   f0 = ln ||J||_F^2 / 8                  first invariant of J^T J
+ *   f1 = ln ||cof J||_F^2 / 8 (3D), ln det(J)^2 / 8 (2D)   second invariant
+ *   f2 = ln |det J| / 8
+ *   f3 = ln n / 8,  n = n0 / max(|det J|, 1e-12)           (Eq. 6)
+ *   f4 = ln(h0 |det J|^(1/d) / dx) / 4      Lagrangian seed spacing over the cell size
+ *   f5 = min(|det J|, 4) / 4
+ * with ln taken of max(x, 1e-30).
+ *
+ * Parameter layout (ORA_MLP_NPARAM floats): W1[64][6], b1[64], W2[64][64],
+ * b2[64], W3[64][64], b3[64], W4[64], b4 (rows are output units).
+ */
+#define ORA_MLP_IN 6
+#define ORA_MLP_H 64
+#define ORA_MLP_NPARAM (ORA_MLP_H * ORA_MLP_IN + ORA_MLP_H + 2 * (ORA_MLP_H * ORA_MLP_H + ORA_MLP_H) + ORA_MLP_H + 1)
+
+static const int ORA_OFF_W1 = 0;
+static const int ORA_OFF_B1 = ORA_MLP_H * ORA_MLP_IN;
+static const int ORA_OFF_W2 = ORA_MLP_H * ORA_MLP_IN + ORA_MLP_H;
+static const int ORA_OFF_B2 = ORA_MLP_H * ORA_MLP_IN + ORA_MLP_H + ORA_MLP_H * ORA_MLP_H;
+static const int ORA_OFF_W3 = ORA_MLP_H * ORA_MLP_IN + 2 * ORA_MLP_H + ORA_MLP_H * ORA_MLP_H;
+static const int ORA_OFF_B3 = ORA_MLP_H * ORA_MLP_IN + 2 * ORA_MLP_H + 2 * ORA_MLP_H * ORA_MLP_H;
+static const int ORA_OFF_W4 = ORA_MLP_H * ORA_MLP_IN + 3 * ORA_MLP_H + 2 * ORA_MLP_H * ORA_MLP_H;
+static const int ORA_OFF_B4 = ORA_MLP_H * ORA_MLP_IN + 4 * ORA_MLP_H + 2 * ORA_MLP_H * ORA_MLP_H;
+
+int ora_mlp_nparam(void) { return ORA_MLP_NPARAM; }
+
+/* bfloat16 value of a float: keep the top 16 bits, rounding to nearest even */
+static int g_mlp_exact;
+static double bf16_of_float(float x)
+{
+    if (g_mlp_exact) return (double)x;
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    u &= 0xFFFF0000u;
+    float r;
+    memcpy(&r, &u, 4);
+    return (double)r;
+}
+
+/* bfloat16 value nearest to a double (ties to even), and the spacing of the
+ * bfloat16 numbers around it; finite normal range only */
+static double bf16_of_double(double x, double* spacing)
+{
+    if (g_mlp_exact) { if (spacing) *spacing = 0.0; return x; }
+    if (x == 0.0) { if (spacing) *spacing = ldexp(1.0, -133); return 0.0; }
+    int e;
+    frexp(x, &e);                          /* |x| in [2^(e-1), 2^e) */
+    double ulp = ldexp(1.0, e - 8);        /* 8 significant bits */
+    double q = x / ulp;
+    double r = nearbyint(q);               /* default rounding mode: to nearest even */
+    if (spacing) *spacing = ulp;
+    return r * ulp;
+}
+
+/* distance from x to the nearest rounding boundary (midpoint between two
+ * consecutive bfloat16 numbers) */
+static double bf16_boundary_distance(double x)
+{
+    double sp;
+    double r = bf16_of_double(x, &sp);
+    double d = fabs(fabs(x - r) - 0.5 * sp);
+    return d;
+}
+
+static double silu(double z) { return z / (1.0 + exp(-z)); }
+static double silu_d(double z) { double s = 1.0 / (1.0 + exp(-z)); return s * (1.0 + z * (1.0 - s)); }
+
+void ora_mlp_features(int d, const double* J, double n0, double h0, double dx, double* f)
+{
+    double I1 = 0.0;
+    for (int q = 0; q < d * d; ++q) I1 += J[q] * J[q];
+    double det = det_d(d, J);
+    double ad = fabs(det);
+    double I2;
+    if (d == 2) {
+        I2 = det * det;
+    } else {
+        I2 = 0.0;   /* squared 2x2 minors: the Frobenius norm of the cofactor matrix */
+        for (int r0 = 0; r0 < 3; ++r0)
+            for (int r1 = r0 + 1; r1 < 3; ++r1)
+                for (int c0 = 0; c0 < 3; ++c0)
+                    for (int c1 = c0 + 1; c1 < 3; ++c1) {
+                        double m = J[r0 * 3 + c0] * J[r1 * 3 + c1] - J[r0 * 3 + c1] * J[r1 * 3 + c0];
+                        I2 += m * m;
+                    }
+    }
+    double n = n0 / (ad > 1e-12 ? ad : 1e-12);
+    f[0] = log(I1 > 1e-30 ? I1 : 1e-30) / 8.0;
+    f[1] = log(I2 > 1e-30 ? I2 : 1e-30) / 8.0;
+    f[2] = log(ad > 1e-30 ? ad : 1e-30) / 8.0;
+    f[3] = log(n > 1e-30 ? n : 1e-30) / 8.0;
+    double sp = h0 * pow(ad, 1.0 / d) / dx;
+    f[4] = log(sp > 1e-30 ? sp : 1e-30) / 4.0;
+    f[5] = (ad < 4.0 ? ad : 4.0) / 4.0;
+}
+
+/* Rounds v to bfloat16 and returns, in *dev, a bound on how far a forward
+ * that computed v with error at most e and rounded it could be from the
+ * rounded value: 0 when no rounding boundary lies within e of v. */
+/* 1: no bfloat16 rounding anywhere (the network in plain double precision,
+ * for finite-difference checks of the gradient) */
+void ora_mlp_set_exact(int exact) { g_mlp_exact = exact; }
+
+static double round_with_bound(double v, double e, double* dev)
+{
+    if (g_mlp_exact) { *dev = e; return v; }
+    double sp;
+    double r = bf16_of_double(v, &sp);
+    *dev = (bf16_boundary_distance(v) > e) ? 0.0 : e + sp;
+    return r;
+}
+
+/*
+ * Forward pass.  Returns c = g(f).  If bound != NULL it receives a bound on
+ * |c_single - c| for a forward that evaluates the same network with
+ * single-precision accumulation (relative error of each dot product of K terms
+ * at most 2 K 2^-24 of the sum of |terms|), a single-precision SiLU (error at
+ * most 2^-20 (|z| + |silu(z)|)) and features with absolute errors fe[k]
+ * (NULL: 1e-6 (1 + |f|)): the bound propagates these through the layers and
+ * adds one bfloat16 spacing wherever a rounding boundary lies within the
+ * propagated error.  act (optional, 3 x 64) receives the post-SiLU values
+ * before rounding and zs (optional, 3 x 64) the pre-activations.
+ */
+double ora_mlp_forward(const float* P, const double* f, const double* fe, double* bound, double* act, double* zs)
+{
+    const int H = ORA_MLP_H;
+    double a0[ORA_MLP_IN], e0[ORA_MLP_IN];
+    for (int k = 0; k < ORA_MLP_IN; ++k) {
+        double ef = fe ? fe[k] : 1e-6 * (1.0 + fabs(f[k]));
+        a0[k] = round_with_bound(f[k], ef, &e0[k]);
+    }
+    double a[ORA_MLP_H], ea[ORA_MLP_H], nxt[ORA_MLP_H], en[ORA_MLP_H];
+    const int K1 = ORA_MLP_IN;
+    for (int j = 0; j < H; ++j) {
+        double z = 0.0, s_abs = 0.0, prop = 0.0;
+        for (int k = 0; k < K1; ++k) {
+            double w = bf16_of_float(P[ORA_OFF_W1 + j * K1 + k]);
+            z += w * a0[k];
+            s_abs += fabs(w * a0[k]);
+            prop += fabs(w) * e0[k];
+        }
+        z += (double)P[ORA_OFF_B1 + j];
+        double ez = prop + 2.0 * (K1 + 1) * ldexp(s_abs + fabs(z), -24);
+        double p = silu(z);
+        double ep = 1.1 * ez + ldexp(fabs(z) + fabs(p), -20);
+        if (zs) zs[j] = z;
+        if (act) act[j] = p;
+        a[j] = round_with_bound(p, ep, &ea[j]);
+    }
+    for (int layer = 0; layer < 2; ++layer) {
+        const int ow = layer == 0 ? ORA_OFF_W2 : ORA_OFF_W3;
+        const int ob = layer == 0 ? ORA_OFF_B2 : ORA_OFF_B3;
+        for (int j = 0; j < H; ++j) {
+            double z = 0.0, s_abs = 0.0, prop = 0.0;
+            for (int k = 0; k < H; ++k) {
+                double w = bf16_of_float(P[ow + j * H + k]);
+                z += w * a[k];
+                s_abs += fabs(w * a[k]);
+                prop += fabs(w) * ea[k];
+            }
+            z += (double)P[ob + j];
+            double ez = prop + 2.0 * (H + 1) * ldexp(s_abs + fabs(z), -24);
+            double p = silu(z);
+            double ep = 1.1 * ez + ldexp(fabs(z) + fabs(p), -20);
+            if (zs) zs[(layer + 1) * H + j] = z;
+            if (act) act[(layer + 1) * H + j] = p;
+            if (layer == 0) {
+                nxt[j] = round_with_bound(p, ep, &en[j]);
+            } else {
+                nxt[j] = p;            /* the last hidden layer feeds a single-precision dot product */
+                en[j] = ep;
+            }
+        }
+        memcpy(a, nxt, sizeof(a));
+        memcpy(ea, en, sizeof(ea));
+    }
+    double c = 0.0, s_abs = 0.0, prop = 0.0;
+    for (int k = 0; k < H; ++k) {
+        double w = bf16_of_float(P[ORA_OFF_W4 + k]);
+        c += w * a[k];
+        s_abs += fabs(w * a[k]);
+        prop += fabs(w) * ea[k];
+    }
+    c += (double)P[ORA_OFF_B4];
+    if (bound) *bound = prop + 2.0 * (H + 1) * ldexp(s_abs + fabs(c), -24);
+    return c;
+}
+
+/*
+ * Gradient of c = g(f) with respect to the master parameters, times dLdc,
+ * added to grad (ORA_MLP_NPARAM doubles).  The bfloat16 roundings are treated
+ * as the identity (straight-through), so the gradient is that of the network
+ * evaluated with the rounded weights and activations.
+ */
+void ora_mlp_backward(const float* P, const double* f, double dLdc, double* grad)
+{
+    const int H = ORA_MLP_H;
+    double z[3 * ORA_MLP_H], p[3 * ORA_MLP_H];
+    ora_mlp_forward(P, f, NULL, NULL, p, z);
+    double a0[ORA_MLP_IN];
+    for (int k = 0; k < ORA_MLP_IN; ++k) a0[k] = bf16_of_double(f[k], NULL);
+    double a1[ORA_MLP_H], a2[ORA_MLP_H], a3[ORA_MLP_H];
+    for (int j = 0; j < H; ++j) {
+        a1[j] = bf16_of_double(p[j], NULL);
+        a2[j] = bf16_of_double(p[H + j], NULL);
+        a3[j] = p[2 * H + j];
+    }
+    /* layer 4 */
+    double d3[ORA_MLP_H];
+    for (int k = 0; k < H; ++k) {
+        grad[ORA_OFF_W4 + k] += dLdc * a3[k];
+        d3[k] = dLdc * bf16_of_float(P[ORA_OFF_W4 + k]) * silu_d(z[2 * H + k]);
+    }
+    grad[ORA_OFF_B4] += dLdc;
+    /* layer 3: z3 = W3 a2 + b3 */
+    double d2[ORA_MLP_H];
+    for (int k = 0; k < H; ++k) d2[k] = 0.0;
+    for (int j = 0; j < H; ++j) {
+        grad[ORA_OFF_B3 + j] += d3[j];
+        for (int k = 0; k < H; ++k) {
+            grad[ORA_OFF_W3 + j * H + k] += d3[j] * a2[k];
+            d2[k] += d3[j] * bf16_of_float(P[ORA_OFF_W3 + j * H + k]);
+        }
+    }
+    for (int k = 0; k < H; ++k) d2[k] *= silu_d(z[H + k]);
+    /* layer 2: z2 = W2 a1 + b2 */
+    double d1[ORA_MLP_H];
+    for (int k = 0; k < H; ++k) d1[k] = 0.0;
+    for (int j = 0; j < H; ++j) {
+        grad[ORA_OFF_B2 + j] += d2[j];
+        for (int k = 0; k < H; ++k) {
+            grad[ORA_OFF_W2 + j * H + k] += d2[j] * a1[k];
+            d1[k] += d2[j] * bf16_of_float(P[ORA_OFF_W2 + j * H + k]);
+        }
+    }
+    for (int k = 0; k < H; ++k) d1[k] *= silu_d(z[k]);
+    /* layer 1: z1 = W1 a0 + b1 */
+    for (int j = 0; j < H; ++j) {
+        grad[ORA_OFF_B1 + j] += d1[j];
+        for (int k = 0; k < ORA_MLP_IN; ++k) grad[ORA_OFF_W1 + j * ORA_MLP_IN + k] += d1[j] * a0[k];
+    }
+}
+
+/* Batch helpers for tests: c (and its bound) for n feature rows. */
+void ora_mlp_forward_batch(const float* P, int n, const double* F, const double* FE, double* c, double* bound)
+{
+    for (int i = 0; i < n; ++i)
+        c[i] = ora_mlp_forward(P, F + (long)i * ORA_MLP_IN, FE ? FE + (long)i * ORA_MLP_IN : NULL,
+                               bound ? &bound[i] : NULL, NULL, NULL);
+}
+
+/*
+ * Training loss of the learned correction and its gradient (spherical kernel).
+ * At the listed training cells c and for each source component k (mass, then
+ * momentum):
+ *   L = 1/(1+d) sum_k sum_c (S_kc - T_kc)^2 / sum_c T_kc^2,
+ * S the Nadaraya-Watson sources of the cloud with the corrected h, T the
+ * targets (n_train x (1+d)).  With w_ic = exp(-q/2)/h_i, q = r^2/h_i^2:
+ *   dS_kc/dw_ic = -(a_ki + S_kc)/D_c,   dw_ic/dc_i = w_ic (q - 1) [dh_i/dc_i = h_i],
+ * so dL/dc_i = -sum_c w_ic (q - 1) sum_k g_kc (a_ki + S_kc)/D_c with
+ * g_kc = dL/dS_kc; the truncation edge is held fixed.  The gradient with
+ * respect to the parameters follows by ora_mlp_backward.  grad may be NULL.
+ */
+int ora_learn_loss_grad(const ora_dep* D, int n, const double* x, const double* J, const double* acc,
+                        const int* status, const int* batch, const double* n0, const double* h0,
+                        long n_train, const long* cells, const double* target, double* loss, double* grad)
+{
+    int d = D->dim;
+    if (!D->mlp || D->kernel != 0) return -1;
+    ora_rec* rec = (ora_rec*)malloc(sizeof(ora_rec) * (n > 0 ? n : 1));
+    int* use = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) {
+        use[i] = contributes(d, x + (long)i * d, status[i]);
+        if (use[i])
+            ora_record(D, x + (long)i * d, J + (long)i * d * d, acc + (long)i * (1 + d),
+                       n0[batch[i]], h0[batch[i]], D->fold ? D->fold[i] : 0, &rec[i]);
+    }
+    double* S = (double*)calloc((size_t)n_train * (1 + d), sizeof(double));
+    double* Dc = (double*)calloc((size_t)n_train, sizeof(double));
+    for (long o = 0; o < n_train; ++o) {
+        double xc[3]; float xcf[3];
+        cell_centre(d, D->N, cells[o], xc, xcf);
+        double den = 0.0, num[4] = {0, 0, 0, 0};
+        for (int i = 0; i < n; ++i) {
+            if (!use[i]) continue;
+            double q;
+            if (!in_support(D, &rec[i], xc, xcf, &q)) continue;
+            double w = rec[i].pref * exp(-0.5 * q);
+            den += w;
+            for (int a = 0; a < 1 + d; ++a) num[a] += w * rec[i].a[a];
+        }
+        Dc[o] = den;
+        for (int a = 0; a < 1 + d; ++a) S[o * (1 + d) + a] = den > 0.0 ? -num[a] / den : 0.0;
+    }
+    double L = 0.0, norm[4] = {0, 0, 0, 0};
+    for (long o = 0; o < n_train; ++o)
+        for (int a = 0; a < 1 + d; ++a) norm[a] += target[o * (1 + d) + a] * target[o * (1 + d) + a];
+    for (int a = 0; a < 1 + d; ++a) {
+        double e = 0.0;
+        for (long o = 0; o < n_train; ++o) {
+            double r = S[o * (1 + d) + a] - target[o * (1 + d) + a];
+            e += r * r;
+        }
+        L += norm[a] > 0.0 ? e / norm[a] : 0.0;
+    }
+    L /= (1 + d);
+    *loss = L;
+    if (grad) {
+        for (int i = 0; i < n; ++i) {
+            if (!use[i] || !rec[i].dh_dc) continue;
+            double dLdc = 0.0;
+            for (long o = 0; o < n_train; ++o) {
+                if (!(Dc[o] > 0.0)) continue;
+                double xc[3]; float xcf[3];
+                cell_centre(d, D->N, cells[o], xc, xcf);
+                double q;
+                if (!in_support(D, &rec[i], xc, xcf, &q)) continue;
+                double w = rec[i].pref * exp(-0.5 * q);
+                double acc_k = 0.0;
+                for (int a = 0; a < 1 + d; ++a) {
+                    if (!(norm[a] > 0.0)) continue;
+                    double g = 2.0 * (S[o * (1 + d) + a] - target[o * (1 + d) + a]) / (norm[a] * (1 + d));
+                    acc_k += g * (rec[i].a[a] + S[o * (1 + d) + a]);
+                }
+                dLdc += -w * (q - 1.0) * acc_k / Dc[o];
+            }
+            if (dLdc != 0.0) ora_mlp_backward(D->mlp, rec[i].f, dLdc, grad);
+        }
+    }
+    free(rec); free(use); free(S); free(Dc);
+    return 0;
+}
+
+/* Per-droplet learned correction of the records (tests): c and the flag dh/dc != 0. */
+void ora_learn_records(const ora_dep* D, int n, const double* x, const double* J, const double* acc,
+                       const int* batch, const double* n0, const double* h0, double* c, int* active, double* h)
+{
+    int d = D->dim;
+    for (int i = 0; i < n; ++i) {
+        ora_rec r;
+        ora_record(D, x + (long)i * d, J + (long)i * d * d, acc + (long)i * (1 + d), n0[batch[i]], h0[batch[i]],
+                   D->fold ? D->fold[i] : 0, &r);
+        c[i] = r.c;
+        active[i] = r.dh_dc;
+        h[i] = r.h;
+    }
 }

@@ -55,7 +55,7 @@ class _Dep(C.Structure):
     _fields_ = [("dim", C.c_int), ("N", C.c_int), ("kernel", C.c_int), ("h_min", C.c_double),
                 ("h_max", C.c_double), ("p", C.c_double), ("window_dt", C.c_double),
                 ("per_cell", C.c_int), ("fp32_decision", C.c_int), ("plain", C.c_int),
-                ("fold", C.c_void_p)]
+                ("fold", C.c_void_p), ("mlp", C.c_void_p)]
 
 
 _lib = None
@@ -80,6 +80,13 @@ def lib():
         _lib.ora_kernel_on_cells.argtypes = [C.POINTER(_Dep), v, v, d, d, i, v]
         _lib.ora_records.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, v, v]
         _lib.ora_psicell.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, i, v, v, v]
+        _lib.ora_mlp_nparam.restype = i
+        _lib.ora_mlp_set_exact.argtypes = [i]
+        _lib.ora_mlp_features.argtypes = [i, v, d, d, d, v]
+        _lib.ora_mlp_forward_batch.argtypes = [v, i, v, v, v, v]
+        _lib.ora_mlp_backward.argtypes = [v, v, d, v]
+        _lib.ora_learn_loss_grad.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, v, v, C.c_long, v, v, v, v]
+        _lib.ora_learn_records.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, v, v, v, v]
     return _lib
 
 
@@ -217,7 +224,7 @@ class Advancer:
 
 
 def dep_struct(wl=None, *, dim=None, N=None, kernel=None, h_min=None, h_max=None, p=None,
-               window_dt=None, per_cell=False, fp32_decision=False, plain=False, fold=None) -> _Dep:
+               window_dt=None, per_cell=False, fp32_decision=False, plain=False, fold=None, mlp=None) -> _Dep:
     """Deposit settings.  plain: det J decided in single precision (plain mode);
     fold: per-droplet flags of J given as the fold guard's double-precision copy
     (the array is kept alive on the returned struct)."""
@@ -237,6 +244,11 @@ def dep_struct(wl=None, *, dim=None, N=None, kernel=None, h_min=None, h_max=None
         D.fold = D._fold_keep.ctypes.data
     else:
         D.fold = None
+    if mlp is not None:
+        D._mlp_keep = np.ascontiguousarray(mlp, dtype=np.float32)
+        D.mlp = D._mlp_keep.ctypes.data
+    else:
+        D.mlp = None
     return D
 
 
@@ -337,3 +349,80 @@ def run(wl, cloud=None, *, nsteps=None, use_mesh=True, deposit_every_window=Fals
         adv.advance(st, s, k, reset_acc=True)
         s += k
     return st
+
+
+# ---------------------------------------------------------------------------
+# Learned bandwidth correction (no counterpart in the paper)
+
+MLP_IN, MLP_HIDDEN = 6, 64
+
+
+def mlp_nparam() -> int:
+    return lib().ora_mlp_nparam()
+
+
+class exact_mlp:
+    """Context: evaluate the network without any bfloat16 rounding."""
+
+    def __enter__(self):
+        lib().ora_mlp_set_exact(1)
+
+    def __exit__(self, *a):
+        lib().ora_mlp_set_exact(0)
+
+
+def mlp_features(d: int, J, n0, h0, dx: float) -> np.ndarray:
+    J = _f64(J).reshape(-1, d * d)
+    n = J.shape[0]
+    n0 = np.broadcast_to(np.asarray(n0, np.float64), (n,))
+    h0 = np.broadcast_to(np.asarray(h0, np.float64), (n,))
+    out = np.zeros((n, MLP_IN))
+    for i in range(n):
+        f = np.zeros(MLP_IN)
+        lib().ora_mlp_features(d, _p(_f64(J[i])), float(n0[i]), float(h0[i]), float(dx), _p(f))
+        out[i] = f
+    return out
+
+
+def mlp_forward(params, F, FE=None):
+    """c = g(f) for each row of F and the bound on a single-precision forward's deviation."""
+    P = np.ascontiguousarray(params, dtype=np.float32)
+    F = _f64(F).reshape(-1, MLP_IN)
+    c = np.zeros(F.shape[0])
+    b = np.zeros(F.shape[0])
+    FE = None if FE is None else _f64(FE).reshape(-1, MLP_IN)
+    lib().ora_mlp_forward_batch(_p(P), F.shape[0], _p(F), _p(FE) if FE is not None else None, _p(c), _p(b))
+    return c, b
+
+
+def mlp_backward(params, f, dLdc: float) -> np.ndarray:
+    P = np.ascontiguousarray(params, dtype=np.float32)
+    g = np.zeros(mlp_nparam())
+    lib().ora_mlp_backward(_p(P), _p(_f64(f)), float(dLdc), _p(g))
+    return g
+
+
+def learn_loss_grad(D: _Dep, x, J, acc, status, batch, n0, h0, cells, target, with_grad=True):
+    """Training loss of the learned correction at the listed cells and its gradient."""
+    d = D.dim
+    x, J, acc = _f64(x).reshape(-1, d), _f64(J).reshape(-1, d * d), _f64(acc).reshape(-1, 1 + d)
+    cells = np.ascontiguousarray(cells, dtype=np.int64)
+    target = _f64(target).reshape(-1, 1 + d)
+    loss = np.zeros(1)
+    grad = np.zeros(mlp_nparam()) if with_grad else None
+    rc = lib().ora_learn_loss_grad(C.byref(D), x.shape[0], _p(x), _p(J), _p(acc), _p(_i32(status)), _p(_i32(batch)),
+                                   _p(_f64(n0)), _p(_f64(h0)), cells.shape[0], _p(cells), _p(target), _p(loss),
+                                   _p(grad) if grad is not None else None)
+    assert rc == 0
+    return float(loss[0]), grad
+
+
+def learn_records(D: _Dep, x, J, acc, batch, n0, h0):
+    """Per droplet: the network output c, whether h moves with c, and h."""
+    d = D.dim
+    x, J, acc = _f64(x).reshape(-1, d), _f64(J).reshape(-1, d * d), _f64(acc).reshape(-1, 1 + d)
+    n = x.shape[0]
+    c, act, h = np.zeros(n), np.zeros(n, np.int32), np.zeros(n)
+    lib().ora_learn_records(C.byref(D), n, _p(x), _p(J), _p(acc), _p(_i32(batch)), _p(_f64(n0)), _p(_f64(h0)),
+                            _p(c), _p(act), _p(h))
+    return c, act.astype(bool), h

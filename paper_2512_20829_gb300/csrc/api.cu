@@ -5,7 +5,7 @@
 
 #include <new>
 
-#include "fla_internal.cuh"
+#include "mlp_tc.cuh"
 
 using namespace fla;
 
@@ -408,6 +408,10 @@ int fla_deposit_sources(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* me
     if (cfg->kernel == FLA_KERNEL_ANISO && !(cfg->h_max * cfg->h_max > mesh->dim * cfg->h_min * cfg->h_min))
         return FLA_ERR_ARG;
     if (cfg->precision != FLA_PREC_MIXED && cfg->precision != FLA_PREC_PLAIN) return FLA_ERR_ARG;
+    if (cfg->mlp_dev) {   // learned correction: single precision, spherical kernel
+        if (!aligned(cfg->mlp_dev, 16) || (cfg->mlp_out_dev && !aligned(cfg->mlp_out_dev, 4))) return FLA_ERR_ARG;
+        if (cloud->dtype != FLA_F32 || cfg->kernel != FLA_KERNEL_ISO) return FLA_ERR_UNSUPPORTED;
+    }
     if (cfg->h_max * mesh->n > 64.0) return FLA_ERR_UNSUPPORTED;   // support wider than 192 cells
     if (!out->s_mass_dev || !out->s_mom_dev) return FLA_ERR_ARG;
     const size_t T = cloud->dtype == FLA_F64 ? 8 : 4;
@@ -494,3 +498,19 @@ int fla_sync_status(fla_ctx* ctx, fla_stream_t stream, fla_device_status* out, i
 }
 
 }  // extern "C"
+
+int fla_mlp_pack(fla_ctx* ctx, const float* params_dev, void* packed_dev, fla_stream_t stream)
+{
+    if (!ctx || !params_dev || !packed_dev || !aligned(packed_dev, 16) || !aligned(params_dev, 4)) return FLA_ERR_ARG;
+    return cuda_status(launch_mlp_pack(params_dev, packed_dev, (cudaStream_t)stream));
+}
+
+int fla_mlp_forward(fla_ctx* ctx, const void* packed_dev, const float* features_dev, int64_t n, float* out_dev,
+                    fla_stream_t stream)
+{
+    if (!ctx || n < 0 || n >= 2147483647LL) return FLA_ERR_ARG;
+    if (n == 0) return FLA_OK;
+    if (!packed_dev || !aligned(packed_dev, 16) || !features_dev || !out_dev) return FLA_ERR_ARG;
+    return cuda_status(launch_mlp_forward(packed_dev, features_dev, n, out_dev, (DevStatus*)ctx->status_dev,
+                                          (cudaStream_t)stream));
+}

@@ -18,7 +18,7 @@
 // The values that decide the truncation test (h and 9 h^2; Sigma^-1) are
 // formed one rounding per operation in a fixed order: this file is compiled
 // without FMA contraction so that the decision is reproducible.
-#include "fla_internal.cuh"
+#include "mlp_tc.cuh"
 
 namespace fla {
 namespace {
@@ -40,6 +40,9 @@ struct RecArgs {
     DevStatus* status;
     const double* fold;         // fold-guard planes (double J first), or null
     int plain;                  // 1: det J and n in single precision
+    const unsigned char* mlp;   // packed learned correction, or null
+    float* mlp_out;             // g(f) per droplet index, or null
+    double dx;                  // cell size (network feature f4)
 };
 
 template <typename T, int D>
@@ -145,19 +148,17 @@ __device__ __forceinline__ void sigma_inverse_f32(const float* j, float h0f, flo
 // Single-precision record.  Layouts: see fla_internal.cuh (c = -log2(e)/(2 h^2),
 // lih = log2(1/h), lpref = log2(det(Sigma)^-1/2): the weight is 2^(c r^2 + lih)).
 template <int D, int KER>
-__device__ __forceinline__ void record_f32(const RecArgs& a, const float* sv, uint32_t meta, int64_t i, double n0,
-                                           double h0, float* r, float& ext2, bool& bad)
+__device__ __forceinline__ void record_f32(const RecArgs& a, const float* sv, double adet, float n, double h0,
+                                           double corr, float* r, float& ext2, bool& bad)
 {
     constexpr int OA = acc_offset(FLA_CLOUD_FLA, D);
     const float* J = sv + 2 * D;
-    double adet;
-    float n;
-    det_and_n<D>(a, J, meta, i, n0, adet, n);
     float am[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int q = 0; q <= D; ++q) am[q] = n * sv[OA + q] * a.inv_window;
     if (KER == FLA_KERNEL_ISO) {
         double h = (a.p == 1.0) ? h0 * adet : h0 * pow(adet, a.p);
+        h *= corr;   // learned correction (1 without the network)
         h = h < a.h_min ? a.h_min : h;
         h = h > a.h_max ? a.h_max : h;
         const float hf = (float)h;
@@ -303,7 +304,12 @@ __global__ void __launch_bounds__(256) k_records(RecArgs a)
         T r[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) r[q] = T(0);
-        if (sizeof(T) == 4) record_f32<D, KER>(a, (const float*)sv, meta, i, n0, h0, (float*)r, ext2, bad);
+        if (sizeof(T) == 4) {
+            double adet;
+            float n;
+            det_and_n<D>(a, (const float*)sv + 2 * D, meta, i, n0, adet, n);
+            record_f32<D, KER>(a, (const float*)sv, adet, n, h0, 1.0, (float*)r, ext2, bad);
+        }
         else record_f64<D, KER>(a, (const double*)sv, n0, h0, (double*)r, ext2, bad);
 #pragma unroll
         for (int v = 0; v < RV / 4; ++v) store4<T>((T*)a.rec, j * (RV / 4) + v, r + 4 * v);
@@ -329,6 +335,107 @@ __global__ void __launch_bounds__(256) k_records(RecArgs a)
         const int64_t lo = blockIdx.x * (int64_t)blockDim.x;
         const int64_t cnt = nvalid > lo ? ((nvalid - lo) < (int64_t)blockDim.x ? (nvalid - lo) : (int64_t)blockDim.x) : 0;
         if (m > 0.0f) atomicMax(a.ext_max, __float_as_uint(m));
+        if (nb) atomicAdd(&a.status->nonfinite, (unsigned long long)nb);
+        if (cnt) atomicAdd(&a.status->deposited, (unsigned long long)cnt);
+    }
+}
+
+// Network features of a droplet (see fla.h), single precision.
+template <int D>
+__device__ __forceinline__ void mlp_features(const float* J, double adet, float n, double h0, double dx, float* f)
+{
+    float I1 = 0.0f;
+#pragma unroll
+    for (int q = 0; q < D * D; ++q) I1 = I1 + J[q] * J[q];
+    float I2;
+    if (D == 2) {
+        I2 = (float)(adet * adet);
+    } else {
+        I2 = 0.0f;
+#pragma unroll
+        for (int r0 = 0; r0 < 3; ++r0)
+#pragma unroll
+            for (int r1 = r0 + 1; r1 < 3; ++r1)
+#pragma unroll
+                for (int c0 = 0; c0 < 3; ++c0)
+#pragma unroll
+                    for (int c1 = c0 + 1; c1 < 3; ++c1) {
+                        const float mnr = J[r0 * 3 + c0] * J[r1 * 3 + c1] - J[r0 * 3 + c1] * J[r1 * 3 + c0];
+                        I2 = I2 + mnr * mnr;
+                    }
+    }
+    const float ad = (float)adet;
+    const float root = D == 2 ? sqrtf(ad) : cbrtf(ad);
+    f[0] = logf(fmaxf(I1, 1e-30f)) * 0.125f;
+    f[1] = logf(fmaxf(I2, 1e-30f)) * 0.125f;
+    f[2] = logf(fmaxf(ad, 1e-30f)) * 0.125f;
+    f[3] = logf(fmaxf(n, 1e-30f)) * 0.125f;
+    f[4] = logf(fmaxf((float)(h0 / dx) * root, 1e-30f)) * 0.25f;
+    f[5] = fminf(ad, 4.0f) * 0.25f;
+}
+
+// Records with the learned correction (single precision, spherical kernel):
+// 128 sorted positions per CTA, the network on the tensor cores.
+template <int D>
+__global__ void __launch_bounds__(kMlpRows) k_records_mlp(RecArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int NP = state_planes(FLA_CLOUD_FLA, D);
+    constexpr int RV = record_values(D, FLA_KERNEL_ISO);
+    MlpCta m = mlp_cta_layout(smem);
+    mlp_cta_begin(m, a.mlp);
+    const int64_t j = blockIdx.x * (int64_t)kMlpRows + threadIdx.x;
+    const int64_t nvalid = a.bin_start[a.n_cells];
+    const bool valid = j < nvalid;
+    float sv[NP * 4];
+    float f[kMlpIn] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    uint32_t i = 0;
+    double adet = 1.0, h0 = 0.0;
+    float n = 0.0f;
+    if (valid) {
+        i = a.perm[j];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) load4<float>((const float*)a.state, p * a.n + i, sv + 4 * p);
+        const uint32_t meta = a.meta[i];
+        const fla_batch* B = a.batches + (meta & FLA_META_BATCH_MASK);
+        const double n0 = __ldg(&B->n0);
+        h0 = __ldg(&B->h0);
+        det_and_n<D>(a, sv + 2 * D, meta, i, n0, adet, n);
+        mlp_features<D>(sv + 2 * D, adet, n, h0, a.dx, f);
+    }
+    bool ok = true;
+    const float c = mlp_cta_forward(m, f, &ok);
+    float ext2 = 0.0f;
+    bool bad = false;
+    if (valid) {
+        const float ct = fminf(fmaxf(c, -2.0f), 2.0f);
+        float r[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) r[q] = 0.0f;
+        record_f32<D, FLA_KERNEL_ISO>(a, sv, adet, n, h0, exp((double)ct), r, ext2, bad);
+#pragma unroll
+        for (int v = 0; v < RV / 4; ++v) store4<float>((float*)a.rec, j * (RV / 4) + v, r + 4 * v);
+        if (!(ext2 >= 0.0f) || !isfinite(ext2)) ext2 = 0.0f;
+        if (a.mlp_out) a.mlp_out[i] = c;
+    }
+    if (!ok && threadIdx.x == 0) atomicOr(&a.status->flags, kFlagMlpTimeout);
+    __shared__ float s_ext[4];
+    __shared__ unsigned s_bad[4];
+    float e = ext2;
+    unsigned b = bad ? 1u : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        e = fmaxf(e, __shfl_xor_sync(0xffffffffu, e, o));
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) { s_ext[threadIdx.x >> 5] = e; s_bad[threadIdx.x >> 5] = b; }
+    mlp_cta_end(m);   // synchronises the CTA
+    if (threadIdx.x == 0) {
+        const float mx = fmaxf(fmaxf(s_ext[0], s_ext[1]), fmaxf(s_ext[2], s_ext[3]));
+        const unsigned nb = s_bad[0] + s_bad[1] + s_bad[2] + s_bad[3];
+        const int64_t lo = blockIdx.x * (int64_t)kMlpRows;
+        const int64_t cnt = nvalid > lo ? ((nvalid - lo) < kMlpRows ? (nvalid - lo) : kMlpRows) : 0;
+        if (mx > 0.0f) atomicMax(a.ext_max, __float_as_uint(mx));
         if (nb) atomicAdd(&a.status->nonfinite, (unsigned long long)nb);
         if (cnt) atomicAdd(&a.status->deposited, (unsigned long long)cnt);
     }
@@ -368,7 +475,16 @@ cudaError_t launch_records(const fla_cloud& cl, const fla_mesh& m, const fla_dep
     a.status = st;
     a.fold = (const double*)cl.fold_dev;
     a.plain = cfg.precision == FLA_PREC_PLAIN ? 1 : 0;
+    a.mlp = (const unsigned char*)cfg.mlp_dev;
+    a.mlp_out = cfg.mlp_out_dev;
+    a.dx = 1.0 / m.n;
     if (a.n == 0) return cudaSuccess;
+    if (a.mlp) {   // validated by the caller: single precision, spherical kernel
+        const unsigned blocks = (unsigned)((a.n + kMlpRows - 1) / kMlpRows);
+        if (m.dim == 2) k_records_mlp<2><<<blocks, kMlpRows, kMlpSmemBytes, s>>>(a);
+        else k_records_mlp<3><<<blocks, kMlpRows, kMlpSmemBytes, s>>>(a);
+        return cudaGetLastError();
+    }
     const bool iso = cfg.kernel == FLA_KERNEL_ISO;
     if (cl.dtype == FLA_F32) {
         if (m.dim == 2) return iso ? launch_t<float, 2, 0>(a, s) : launch_t<float, 2, 1>(a, s);

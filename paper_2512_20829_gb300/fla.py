@@ -18,7 +18,7 @@ from . import inputs as I
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfla.so")
 
-ABI_VERSION = 2            # FLA_ABI_VERSION of include/fla.h that these structures mirror
+ABI_VERSION = 3            # FLA_ABI_VERSION of include/fla.h that these structures mirror
 F32, F64 = 0, 1
 CLOUD_FLA, CLOUD_LPT = 0, 1
 KERNEL_ISO, KERNEL_ANISO = 0, 1
@@ -32,7 +32,9 @@ MAX_VORTICES = 16
 EXPORTED = ["fla_abi_version", "fla_status_string", "fla_create", "fla_destroy", "fla_state_layout",
             "fla_carrier_nodes_bytes", "fla_carrier_sample", "fla_batch_deadline", "fla_advance",
             "fla_workspace_size", "fla_cell_bins", "fla_deposit_sources", "psicell_deposit", "fla_sync_status",
-            "fla_profile_enable", "fla_profile_read", "fla_phase_name", "fla_fold_bytes"]
+            "fla_profile_enable", "fla_profile_read", "fla_phase_name", "fla_fold_bytes", "fla_mlp_pack",
+            "fla_mlp_forward"]
+MLP_FEATURES, MLP_HIDDEN, MLP_PARAMS, MLP_PACKED_BYTES = 6, 64, 8833, 19472
 PREC_MIXED, PREC_PLAIN = 0, 1
 TAU_FOLD = 1e-2
 PHASES = ["carrier", "advance", "keys", "sort", "bins", "records", "gather", "psicell"]
@@ -63,7 +65,7 @@ class Cloud(C.Structure):
 class DepositCfg(C.Structure):
     _fields_ = [("kernel", C.c_int32), ("per_cell", C.c_int32), ("h_min", C.c_double), ("h_max", C.c_double),
                 ("p", C.c_double), ("window_dt", C.c_double), ("precision", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("reserved", C.c_int32), ("mlp_dev", C.c_void_p), ("mlp_out_dev", C.c_void_p)]
 
 
 class Sources(C.Structure):
@@ -119,6 +121,8 @@ def lib() -> C.CDLL:
         L.fla_phase_name.restype = C.c_char_p
         L.fla_fold_bytes.argtypes = [i32, i64]
         L.fla_fold_bytes.restype = C.c_size_t
+        L.fla_mlp_pack.argtypes = [v, v, v, v]
+        L.fla_mlp_forward.argtypes = [v, v, v, i64, v, v]
         if L.fla_abi_version() != ABI_VERSION:
             raise FlaError(f"{LIB_PATH} has ABI version {L.fla_abi_version()}, the binding expects "
                            f"{ABI_VERSION}: rebuild it with __graft_entry__.build()")
@@ -414,9 +418,55 @@ def cell_bins(ctx: Context, cloud: DeviceCloud, m: Mesh, ws, stream=None):
 
 
 def deposit_cfg(kernel: int, h_min: float, h_max: float, window_dt: float, p: float = 1.0,
-                per_cell: bool = False, precision: int = PREC_MIXED) -> DepositCfg:
+                per_cell: bool = False, precision: int = PREC_MIXED, mlp=None, mlp_out=None) -> DepositCfg:
+    """mlp: a LearnedCorrection (its packed image), or None for the plain method;
+    mlp_out: optional float32 tensor receiving g(f) per droplet."""
     return DepositCfg(int(kernel), 1 if per_cell else 0, float(h_min), float(h_max), float(p), float(window_dt),
-                      int(precision), 0)
+                      int(precision), 0, mlp.packed.data_ptr() if mlp is not None else None,
+                      mlp_out.data_ptr() if mlp_out is not None else None)
+
+
+class LearnedCorrection:
+    """FP32 master parameters of the bandwidth network and their packed BF16 image."""
+
+    def __init__(self, ctx: "Context", params=None, device="cuda", seed: int = 0, scale: float = 1.0):
+        torch = _torch()
+        self.ctx = ctx
+        if params is None:
+            params = init_mlp_params(seed, scale)
+        self.params = torch.as_tensor(np.asarray(params, np.float32)).to(device).contiguous()
+        assert self.params.numel() == MLP_PARAMS
+        self.packed = torch.empty(MLP_PACKED_BYTES, dtype=torch.uint8, device=device)
+        self.pack()
+
+    def pack(self, stream=None):
+        check(lib().fla_mlp_pack(self.ctx.handle, _ptr(self.params), _ptr(self.packed), _stream_ptr(stream)),
+              "fla_mlp_pack")
+
+    def forward(self, features, stream=None):
+        """g(f) for a (n, 6) float32 device tensor of features."""
+        torch = _torch()
+        features = features.contiguous()
+        n = features.shape[0]
+        out = torch.empty(max(n, 1), dtype=torch.float32, device=features.device)
+        check(lib().fla_mlp_forward(self.ctx.handle, _ptr(self.packed), _ptr(features), int(n), _ptr(out),
+                                    _stream_ptr(stream)), "fla_mlp_forward")
+        return out[:n]
+
+
+def init_mlp_params(seed: int = 0, scale: float = 1.0, zero_last: bool = False) -> np.ndarray:
+    """Seeded initial parameters: uniform +-scale/sqrt(fan_in) weights, zero biases."""
+    rng = np.random.default_rng(seed)
+    H, F = MLP_HIDDEN, MLP_FEATURES
+    parts = []
+    for fan_out, fan_in in ((H, F), (H, H), (H, H)):
+        parts.append(rng.uniform(-1, 1, fan_out * fan_in) * scale / np.sqrt(fan_in))
+        parts.append(np.zeros(fan_out))
+    parts.append(np.zeros(H) if zero_last else rng.uniform(-1, 1, H) * scale / np.sqrt(H))
+    parts.append(np.zeros(1))
+    p = np.concatenate(parts).astype(np.float32)
+    assert p.size == MLP_PARAMS
+    return p
 
 
 class SourceFields:
