@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define FLA_ABI_VERSION 3
+#define FLA_ABI_VERSION 4
 
 /* cudaStream_t without including the CUDA headers. */
 typedef struct CUstream_st* fla_stream_t;
@@ -332,6 +332,31 @@ int fla_mlp_pack(fla_ctx* ctx, const float* params_dev, void* packed_dev, fla_st
  * on the way in) into out_dev[n]. */
 int fla_mlp_forward(fla_ctx* ctx, const void* packed_dev, const float* features_dev, int64_t n, float* out_dev,
                     fla_stream_t stream);
+
+/* Training of the learned correction.  For a cloud state and targets T at
+ * n_train distinct training cells (T: n_train x (1+dim) FP32, mass then
+ * momentum, e.g. the sources of a densely seeded cloud of the same flow), the
+ * loss of the learned deposit is
+ *   L = 1/(1+dim) sum_k sum_c (S_kc - T_kc)^2 / sum_c T_kc^2,
+ * S the sources of fla_deposit_sources with cfg (mlp_dev required).
+ * fla_learn_grad runs that deposit into out (dsum_dev required), then adds L
+ * to *loss_dev and dL/dtheta (the gradient with respect to the FP32 master
+ * parameters, BF16 roundings treated as the identity, the truncation edge held
+ * fixed) to grad_dev[FLA_MLP_PARAMS]; callers zero both to start a batch.
+ * Single-precision clouds, FLA_KERNEL_ISO.  workspace: as for
+ * fla_deposit_sources; learn_ws: fla_learn_workspace_size bytes, 256-byte
+ * aligned.  The sums run in a fixed order: the result is deterministic. */
+int fla_learn_workspace_size(fla_ctx* ctx, const fla_mesh* mesh, int64_t n_droplets, size_t* bytes);
+int fla_learn_grad(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, const fla_deposit_cfg* cfg,
+                   const uint32_t* cells_dev, int64_t n_train, const float* targets_dev, const fla_sources* out,
+                   float* grad_dev, float* loss_dev, void* workspace_dev, size_t workspace_bytes, void* learn_ws_dev,
+                   size_t learn_ws_bytes, fla_stream_t stream);
+
+/* One Adam step (bias-corrected, step >= 1) on n FP32 parameters:
+ *   m = b1 m + (1-b1) g,  v = b2 v + (1-b2) g^2,
+ *   p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps). */
+int fla_adam_step(fla_ctx* ctx, float* params_dev, const float* grad_dev, float* m_dev, float* v_dev, int64_t n,
+                  float lr, float beta1, float beta2, float eps, int32_t step, fla_stream_t stream);
 
 /* Read the device status block (synchronises `stream`); reset != 0 zeroes it
  * afterwards.  Returns FLA_ERR_NONFINITE when nonfinite > 0, else FLA_OK. */

@@ -395,8 +395,12 @@ int fla_cell_bins(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, ui
     return cuda_status(launch_bin_start(ks, cloud->n, nc, bin_start_dev, s));
 }
 
-int fla_deposit_sources(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, const fla_deposit_cfg* cfg,
-                        const fla_sources* out, void* ws, size_t ws_bytes, fla_stream_t stream)
+namespace {
+
+// The kernel-regression deposit; aux (learned correction only) receives per
+// sorted record g(f) and whether h moves with it.
+int deposit_impl(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, const fla_deposit_cfg* cfg,
+                 const fla_sources* out, void* ws, size_t ws_bytes, fla_stream_t stream, float* aux)
 {
     if (!ctx || !cfg || !out) return FLA_ERR_ARG;
     int st = cloud_ok(cloud, mesh);
@@ -439,7 +443,7 @@ int fla_deposit_sources(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* me
         {
             PhaseScope ps(ctx, FLA_PHASE_RECORDS, s, 1);
             if (launch_records(*cloud, *mesh, *cfg, at<uint32_t>(ws, L.vals[cur]), bins, nc, at<void>(ws, L.rec),
-                               ext, (DevStatus*)ctx->status_dev, s) != cudaSuccess)
+                               ext, (DevStatus*)ctx->status_dev, s, aux) != cudaSuccess)
                 return FLA_ERR_CUDA;
         }
     }
@@ -454,6 +458,103 @@ int fla_deposit_sources(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* me
     PhaseScope ps(ctx, FLA_PHASE_GATHER, s, 1);
     return cuda_status(launch_nw_gather(*cloud, *mesh, *cfg, at<void>(ws, L.rec), bins, ext, *out,
                                         (DevStatus*)ctx->status_dev, s));
+}
+
+// Which of the sort's ping-pong buffers holds the sorted order of a cloud of n.
+int sorted_buffer(const fla_mesh& m, int64_t n) { return sort_passes_n(sort_bits((uint32_t)cells_of(m)), n) & 1; }
+
+struct LearnLayout {
+    size_t q, aux, dldc, partial, scal, total;
+};
+
+LearnLayout learn_layout(const fla_mesh& m, int64_t n, int num_sms)
+{
+    LearnLayout L{};
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    size_t o = 0;
+    L.q = o; o += up256((size_t)cells_of(m) * (m.dim == 2 ? 4 : 8) * 4);
+    L.aux = o; o += up256(nn * 8);
+    L.dldc = o; o += up256(nn * 4);
+    L.partial = o; o += up256((size_t)(num_sms > 0 ? num_sms : 1) * kMlpParams * 4);
+    L.scal = o; o += 256;
+    L.total = o;
+    return L;
+}
+
+int backward_parts(fla_ctx* ctx, int64_t n)
+{
+    const int64_t tiles = (n + kMlpRows - 1) / kMlpRows;
+    const int64_t p = tiles < ctx->num_sms ? tiles : ctx->num_sms;
+    return (int)(p > 0 ? p : 1);
+}
+
+}  // namespace
+
+int fla_deposit_sources(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, const fla_deposit_cfg* cfg,
+                        const fla_sources* out, void* ws, size_t ws_bytes, fla_stream_t stream)
+{
+    return deposit_impl(ctx, cloud, mesh, cfg, out, ws, ws_bytes, stream, nullptr);
+}
+
+int fla_learn_workspace_size(fla_ctx* ctx, const fla_mesh* mesh, int64_t n_droplets, size_t* bytes)
+{
+    if (!ctx || !bytes || !mesh_ok(mesh) || n_droplets < 0 || n_droplets >= 2147483647LL) return FLA_ERR_ARG;
+    *bytes = learn_layout(*mesh, n_droplets, ctx->num_sms).total;
+    return FLA_OK;
+}
+
+int fla_learn_grad(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, const fla_deposit_cfg* cfg,
+                   const uint32_t* cells_dev, int64_t n_train, const float* targets_dev, const fla_sources* out,
+                   float* grad_dev, float* loss_dev, void* ws, size_t ws_bytes, void* lws, size_t lws_bytes,
+                   fla_stream_t stream)
+{
+    if (!ctx || !cfg || !out || !cloud || !mesh) return FLA_ERR_ARG;
+    if (!cfg->mlp_dev || !out->dsum_dev || !grad_dev || !loss_dev) return FLA_ERR_ARG;
+    if (cloud->dtype != FLA_F32 || cfg->kernel != FLA_KERNEL_ISO) return FLA_ERR_UNSUPPORTED;
+    if (n_train < 1 || n_train > 2147483647LL || !cells_dev || !targets_dev) return FLA_ERR_ARG;
+    const LearnLayout LL = learn_layout(*mesh, cloud->n, ctx->num_sms);
+    if (!lws || !aligned(lws, 256) || lws_bytes < LL.total) return FLA_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = deposit_impl(ctx, cloud, mesh, cfg, out, ws, ws_bytes, stream, at<float>(lws, LL.aux));
+    if (st != FLA_OK) return st;
+    const WsLayout L = layout(*mesh, cloud->dtype, cfg->kernel, cloud->n);
+    const int cur = sorted_buffer(*mesh, cloud->n);
+    LearnArgs a{};
+    a.dim = mesh->dim;
+    a.N = mesh->n;
+    a.n_cells = cells_of(*mesh);
+    a.s_mass = (const float*)out->s_mass_dev;
+    a.s_mom = (const float*)out->s_mom_dev;
+    a.dsum = (const float*)out->dsum_dev;
+    a.cells = cells_dev;
+    a.n_train = n_train;
+    a.targets = targets_dev;
+    a.q = at<float>(lws, LL.q);
+    a.q_stride = mesh->dim == 2 ? 4 : 8;
+    a.scal = at<float>(lws, LL.scal);
+    a.loss = loss_dev;
+    a.bin_start = at<uint32_t>(ws, L.bin_start);
+    a.rec = at<void>(ws, L.rec);
+    a.aux = at<float>(lws, LL.aux);
+    a.dldc = at<float>(lws, LL.dldc);
+    if (launch_learn_cells(a, s) != cudaSuccess) return FLA_ERR_CUDA;
+    if (launch_learn_dc(a, cloud->n, s) != cudaSuccess) return FLA_ERR_CUDA;
+    const int parts = backward_parts(ctx, cloud->n);
+    if (launch_learn_backward(*cloud, *mesh, *cfg, at<uint32_t>(ws, L.vals[cur]), a.bin_start, a.n_cells, a.dldc,
+                              at<float>(lws, LL.partial), parts, (DevStatus*)ctx->status_dev, s) != cudaSuccess)
+        return FLA_ERR_CUDA;
+    return cuda_status(launch_grad_reduce(at<float>(lws, LL.partial), parts, grad_dev, s));
+}
+
+int fla_adam_step(fla_ctx* ctx, float* params_dev, const float* grad_dev, float* m_dev, float* v_dev, int64_t n,
+                  float lr, float beta1, float beta2, float eps, int32_t step, fla_stream_t stream)
+{
+    if (!ctx || n < 0 || step < 1 || !(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) ||
+        !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+        return FLA_ERR_ARG;
+    if (n > 0 && (!params_dev || !grad_dev || !m_dev || !v_dev)) return FLA_ERR_ARG;
+    return cuda_status(launch_adam(params_dev, grad_dev, m_dev, v_dev, n, lr, beta1, beta2, eps, step,
+                                   (cudaStream_t)stream));
 }
 
 int psicell_deposit(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, double window_dt, int32_t per_cell,

@@ -147,7 +147,10 @@ cudaError_t launch_bin_start(const uint32_t* keys_sorted, int64_t n, int64_t n_c
                              cudaStream_t s);
 cudaError_t launch_records(const fla_cloud& cl, const fla_mesh& m, const fla_deposit_cfg& cfg,
                            const uint32_t* perm, const uint32_t* bin_start, int64_t n_cells, void* rec,
-                           unsigned int* ext_max, DevStatus* st, cudaStream_t s);
+                           unsigned int* ext_max, DevStatus* st, cudaStream_t s, float* aux = nullptr);
+cudaError_t launch_learn_backward(const fla_cloud& cl, const fla_mesh& m, const fla_deposit_cfg& cfg,
+                                  const uint32_t* perm, const uint32_t* bin_start, int64_t n_cells,
+                                  const float* dldc, float* partial, int n_parts, DevStatus* st, cudaStream_t s);
 cudaError_t launch_nw_gather(const fla_cloud& cl, const fla_mesh& m, const fla_deposit_cfg& cfg, const void* rec,
                              const uint32_t* bin_start, const unsigned int* ext_max, const fla_sources& out,
                              DevStatus* st, cudaStream_t s);

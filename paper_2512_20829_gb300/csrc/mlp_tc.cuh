@@ -306,6 +306,106 @@ __device__ __forceinline__ float mlp_cta_forward(MlpCta& m, const float* f, bool
     return c;
 }
 
+// The forward of mlp_cta_forward that also keeps, for the backward pass, this
+// row's pre-activations z1, z2, z3 (FP32) and the BF16 activations a1, a2 (as
+// FP32 values) in the given shared-memory rows (64 values each).
+__device__ __forceinline__ float mlp_cta_forward_keep(MlpCta& m, const float* f, float* z1, float* z2, float* z3,
+                                                      float* a1, float* a2, bool* ok)
+{
+    const int row = threadIdx.x;
+    {
+        uint4 u0;
+        u0.x = pack_bf16x2(f[0], f[1]);
+        u0.y = pack_bf16x2(f[2], f[3]);
+        u0.z = pack_bf16x2(f[4], f[5]);
+        u0.w = 0u;
+        *reinterpret_cast<uint4*>(m.act + cm_offset(row, 0, 16)) = u0;
+        *reinterpret_cast<uint4*>(m.act + cm_offset(row, 8, 16)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    const uint32_t lane_base = *m.tmem_slot + ((uint32_t)((threadIdx.x >> 5) * 32) << 16);
+    bool good = true;
+    float c = 0.0f;
+    const float* w4 = reinterpret_cast<const float*>(m.img + kPkW4);
+    for (int layer = 0; layer < 3; ++layer) {
+        good &= mlp_layer(m, layer == 0 ? kPkW1 : (layer == 1 ? kPkW2 : kPkW3), layer == 0 ? 16 : kMlpH);
+        const float* bias = reinterpret_cast<const float*>(m.img + (layer == 0 ? kPkB1 : (layer == 1 ? kPkB2 : kPkB3)));
+        float* zr = layer == 0 ? z1 : (layer == 1 ? z2 : z3);
+        float* ar = layer == 0 ? a1 : a2;
+#pragma unroll 1
+        for (int c0 = 0; c0 < kMlpH; c0 += 16) {
+            float v[16];
+            tmem_ld16(lane_base + (uint32_t)c0, v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const float z = v[q] + bias[c0 + q];
+                zr[c0 + q] = z;
+                v[q] = silu_f(z);
+            }
+            if (layer < 2) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint4 u;
+                    u.x = pack_bf16x2(v[8 * h + 0], v[8 * h + 1]);
+                    u.y = pack_bf16x2(v[8 * h + 2], v[8 * h + 3]);
+                    u.z = pack_bf16x2(v[8 * h + 4], v[8 * h + 5]);
+                    u.w = pack_bf16x2(v[8 * h + 6], v[8 * h + 7]);
+                    *reinterpret_cast<uint4*>(m.act + cm_offset(row, c0 + 8 * h, kMlpH)) = u;
+                }
+#pragma unroll
+                for (int q = 0; q < 16; ++q) ar[c0 + q] = __bfloat162float(__float2bfloat16_rn(v[q]));
+            } else {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) c = fmaf(w4[c0 + q], v[q], c);
+            }
+        }
+    }
+    c += *reinterpret_cast<const float*>(m.img + kPkB4);
+    *ok = good;
+    return c;
+}
+
+__device__ __forceinline__ float silu_grad_f(float z)
+{
+    const float s = 1.0f / (1.0f + __expf(-z));
+    return s * (1.0f + z * (1.0f - s));
+}
+
+// BF16 weight (n, k) of a K-major operand image, as FP32.
+__device__ __forceinline__ float img_weight(const unsigned char* img, int off, int n, int k, int K)
+{
+    return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(img + off + cm_offset(n, k, K)));
+}
+
+// Arguments of the training kernels (learn.cu).
+struct LearnArgs {
+    int dim, N;
+    int64_t n_cells;
+    const float* s_mass;        // deposit outputs of the learned forward
+    const float* s_mom;
+    const float* dsum;
+    const uint32_t* cells;      // training cells (distinct), n_train
+    int64_t n_train;
+    const float* targets;       // n_train x (1 + dim)
+    float* q;                   // per cell: H_0..H_dim, G/D (q_stride floats)
+    int q_stride;
+    float* scal;                // norm_k of the targets
+    float* loss;                // += loss
+    const uint32_t* bin_start;  // cell list of the deposit
+    const void* rec;            // records in sorted order
+    const float* aux;           // per sorted record: g(f), 1 if h moves with it
+    float* dldc;                // per sorted record: dL/dc
+};
+
+constexpr int kLearnRowPad = kMlpH + 1;   // padded FP32 rows of the backward's shared arrays
+constexpr int kLearnSmemBytes =
+    kMlpSmemBytes + (5 * kMlpRows * kLearnRowPad + kMlpRows * 8 + kMlpRows) * 4;
+
+cudaError_t launch_learn_cells(const LearnArgs& a, cudaStream_t s);
+cudaError_t launch_learn_dc(const LearnArgs& a, int64_t n, cudaStream_t s);
+cudaError_t launch_grad_reduce(const float* partial, int n_parts, float* grad, cudaStream_t s);
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2,
+                        float eps, int step, cudaStream_t s);
+
 cudaError_t launch_mlp_pack(const float* params, void* packed, cudaStream_t s);
 cudaError_t launch_mlp_forward(const void* packed, const float* feats, int64_t n, float* out, DevStatus* st,
                                cudaStream_t s);

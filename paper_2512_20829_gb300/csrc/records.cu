@@ -43,6 +43,7 @@ struct RecArgs {
     const unsigned char* mlp;   // packed learned correction, or null
     float* mlp_out;             // g(f) per droplet index, or null
     double dx;                  // cell size (network feature f4)
+    float* aux;                 // per sorted record: g(f) and 1 if h moves with it, or null
 };
 
 template <typename T, int D>
@@ -149,7 +150,7 @@ __device__ __forceinline__ void sigma_inverse_f32(const float* j, float h0f, flo
 // lih = log2(1/h), lpref = log2(det(Sigma)^-1/2): the weight is 2^(c r^2 + lih)).
 template <int D, int KER>
 __device__ __forceinline__ void record_f32(const RecArgs& a, const float* sv, double adet, float n, double h0,
-                                           double corr, float* r, float& ext2, bool& bad)
+                                           double corr, float* r, float& ext2, bool& bad, bool* h_free = nullptr)
 {
     constexpr int OA = acc_offset(FLA_CLOUD_FLA, D);
     const float* J = sv + 2 * D;
@@ -159,6 +160,7 @@ __device__ __forceinline__ void record_f32(const RecArgs& a, const float* sv, do
     if (KER == FLA_KERNEL_ISO) {
         double h = (a.p == 1.0) ? h0 * adet : h0 * pow(adet, a.p);
         h *= corr;   // learned correction (1 without the network)
+        if (h_free) *h_free = h > a.h_min && h < a.h_max;
         h = h < a.h_min ? a.h_min : h;
         h = h > a.h_max ? a.h_max : h;
         const float hf = (float)h;
@@ -412,11 +414,16 @@ __global__ void __launch_bounds__(kMlpRows) k_records_mlp(RecArgs a)
         float r[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) r[q] = 0.0f;
-        record_f32<D, FLA_KERNEL_ISO>(a, sv, adet, n, h0, exp((double)ct), r, ext2, bad);
+        bool h_free = false;
+        record_f32<D, FLA_KERNEL_ISO>(a, sv, adet, n, h0, exp((double)ct), r, ext2, bad, &h_free);
 #pragma unroll
         for (int v = 0; v < RV / 4; ++v) store4<float>((float*)a.rec, j * (RV / 4) + v, r + 4 * v);
         if (!(ext2 >= 0.0f) || !isfinite(ext2)) ext2 = 0.0f;
         if (a.mlp_out) a.mlp_out[i] = c;
+        if (a.aux) {
+            a.aux[2 * j] = c;
+            a.aux[2 * j + 1] = (h_free && c > -2.0f && c < 2.0f) ? 1.0f : 0.0f;
+        }
     }
     if (!ok && threadIdx.x == 0) atomicOr(&a.status->flags, kFlagMlpTimeout);
     __shared__ float s_ext[4];
@@ -441,6 +448,160 @@ __global__ void __launch_bounds__(kMlpRows) k_records_mlp(RecArgs a)
     }
 }
 
+// Backward of the learned correction over tiles of 128 sorted records
+// (persistent CTAs): the tensor-core forward is repeated with its
+// activations kept in shared memory, then on the CUDA cores
+//   d3 = dL/dc W4 silu'(z3), d2 = silu'(z2) W3^T d3, d1 = silu'(z1) W2^T d2
+// (BF16 weights as in the forward) and the parameter gradients
+//   dW4 = sum dL/dc a3, dW3 = sum d3 a2^T, dW2 = sum d2 a1^T, dW1 = sum d1 a0^T
+// and the bias sums, accumulated per thread over the CTA's tiles and written
+// as one partial gradient per CTA.
+template <int D>
+__global__ void __launch_bounds__(kMlpRows, 1) k_learn_backward(RecArgs a, const float* __restrict__ dldc,
+                                                                float* __restrict__ partial)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int NP = state_planes(FLA_CLOUD_FLA, D);
+    constexpr int RP = kLearnRowPad;
+    MlpCta m = mlp_cta_layout(smem);
+    float* Z1 = reinterpret_cast<float*>(smem + kMlpSmemBytes);
+    float* Z2 = Z1 + kMlpRows * RP;
+    float* Z3 = Z2 + kMlpRows * RP;
+    float* A1 = Z3 + kMlpRows * RP;
+    float* A2 = A1 + kMlpRows * RP;
+    float* A0 = A2 + kMlpRows * RP;     // 8 per row
+    float* GC = A0 + kMlpRows * 8;      // dL/dc per row
+    mlp_cta_begin(m, a.mlp);
+    const int t = threadIdx.x;
+    const int64_t nvalid = a.bin_start[a.n_cells];
+    const int64_t tiles = (nvalid + kMlpRows - 1) / kMlpRows;
+    const float* w4 = reinterpret_cast<const float*>(m.img + kPkW4);
+    float gW3[32], gW2[32], gW1[3];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) { gW3[q] = 0.0f; gW2[q] = 0.0f; }
+    gW1[0] = gW1[1] = gW1[2] = 0.0f;
+    float gb1 = 0.0f, gb2 = 0.0f, gb3 = 0.0f, gW4 = 0.0f, gb4 = 0.0f;
+    bool all_ok = true;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t j = tile * kMlpRows + t;
+        float f[kMlpIn] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        float g = 0.0f;
+        if (j < nvalid) {
+            const uint32_t i = a.perm[j];
+            float sv[NP * 4];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) load4<float>((const float*)a.state, p * a.n + i, sv + 4 * p);
+            const uint32_t meta = a.meta[i];
+            const fla_batch* B = a.batches + (meta & FLA_META_BATCH_MASK);
+            double adet;
+            float n;
+            det_and_n<D>(a, sv + 2 * D, meta, i, __ldg(&B->n0), adet, n);
+            mlp_features<D>(sv + 2 * D, adet, n, __ldg(&B->h0), a.dx, f);
+            g = dldc[j];
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) A0[t * 8 + k] = k < kMlpIn ? __bfloat162float(__float2bfloat16_rn(f[k])) : 0.0f;
+        GC[t] = g;
+        bool ok = true;
+        mlp_cta_forward_keep(m, f, Z1 + t * RP, Z2 + t * RP, Z3 + t * RP, A1 + t * RP, A2 + t * RP, &ok);
+        all_ok &= ok;
+        __syncthreads();
+        // last layer: dW4_k = sum_r g_r silu(z3_rk), db4 = sum_r g_r
+        if (t < kMlpH) {
+            float sacc = 0.0f;
+            for (int r = 0; r < kMlpRows; ++r) sacc = fmaf(GC[r], silu_f(Z3[r * RP + t]), sacc);
+            gW4 += sacc;
+        }
+        if (t == 0) {
+            float sacc = 0.0f;
+            for (int r = 0; r < kMlpRows; ++r) sacc += GC[r];
+            gb4 += sacc;
+        }
+        __syncthreads();
+        // d3 (own row, in place of z3)
+        for (int k = 0; k < kMlpH; ++k) Z3[t * RP + k] = g * w4[k] * silu_grad_f(Z3[t * RP + k]);
+        __syncthreads();
+        // dW3[k][k'] = sum_r d3_rk a2_rk', db3
+        {
+            const int kp = t & 63, k0 = t >> 6;
+            for (int r = 0; r < kMlpRows; ++r) {
+                const float av = A2[r * RP + kp];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) gW3[q] = fmaf(Z3[r * RP + k0 + 2 * q], av, gW3[q]);
+            }
+            if (t < kMlpH) {
+                float sacc = 0.0f;
+                for (int r = 0; r < kMlpRows; ++r) sacc += Z3[r * RP + t];
+                gb3 += sacc;
+            }
+        }
+        // d2 (own row, in place of z2): silu'(z2_k') sum_k d3_k W3[k][k']
+        for (int kp = 0; kp < kMlpH; ++kp) {
+            float sacc = 0.0f;
+            for (int k = 0; k < kMlpH; ++k) sacc = fmaf(Z3[t * RP + k], img_weight(m.img, kPkW3, k, kp, kMlpH), sacc);
+            Z2[t * RP + kp] = sacc * silu_grad_f(Z2[t * RP + kp]);
+        }
+        __syncthreads();
+        {
+            const int kp = t & 63, k0 = t >> 6;
+            for (int r = 0; r < kMlpRows; ++r) {
+                const float av = A1[r * RP + kp];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) gW2[q] = fmaf(Z2[r * RP + k0 + 2 * q], av, gW2[q]);
+            }
+            if (t >= kMlpH) {
+                float sacc = 0.0f;
+                for (int r = 0; r < kMlpRows; ++r) sacc += Z2[r * RP + t - kMlpH];
+                gb2 += sacc;
+            }
+        }
+        // d1 (own row, in place of z1): silu'(z1_k'') sum_k' d2_k' W2[k'][k'']
+        for (int kq = 0; kq < kMlpH; ++kq) {
+            float sacc = 0.0f;
+            for (int k = 0; k < kMlpH; ++k) sacc = fmaf(Z2[t * RP + k], img_weight(m.img, kPkW2, k, kq, kMlpH), sacc);
+            Z1[t * RP + kq] = sacc * silu_grad_f(Z1[t * RP + kq]);
+        }
+        __syncthreads();
+        {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int e = t + kMlpRows * q;          // W1 entry (k'', f)
+                const int kq = e / kMlpIn, fi = e % kMlpIn;
+                float sacc = 0.0f;
+                for (int r = 0; r < kMlpRows; ++r) sacc = fmaf(Z1[r * RP + kq], A0[r * 8 + fi], sacc);
+                gW1[q] += sacc;
+            }
+            if (t < kMlpH) {
+                float sacc = 0.0f;
+                for (int r = 0; r < kMlpRows; ++r) sacc += Z1[r * RP + t];
+                gb1 += sacc;
+            }
+        }
+        __syncthreads();   // the next tile's forward overwrites the shared arrays
+    }
+    float* out = partial + (int64_t)blockIdx.x * kMlpParams;
+    {
+        const int kp = t & 63, k0 = t >> 6;
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            out[kOffW3 + (k0 + 2 * q) * kMlpH + kp] = gW3[q];
+            out[kOffW2 + (k0 + 2 * q) * kMlpH + kp] = gW2[q];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) out[kOffW1 + t + kMlpRows * q] = gW1[q];
+    if (t < kMlpH) {
+        out[kOffB1 + t] = gb1;
+        out[kOffB3 + t] = gb3;
+        out[kOffW4 + t] = gW4;
+    } else {
+        out[kOffB2 + t - kMlpH] = gb2;
+    }
+    if (t == 0) out[kOffB4] = gb4;
+    if (!all_ok && t == 0) atomicOr(&a.status->flags, kFlagMlpTimeout);
+    mlp_cta_end(m);
+}
+
 template <typename T, int D, int KER>
 cudaError_t launch_t(const RecArgs& a, cudaStream_t s)
 {
@@ -451,9 +612,9 @@ cudaError_t launch_t(const RecArgs& a, cudaStream_t s)
 
 }  // namespace
 
-cudaError_t launch_records(const fla_cloud& cl, const fla_mesh& m, const fla_deposit_cfg& cfg,
-                           const uint32_t* perm, const uint32_t* bin_start, int64_t n_cells, void* rec,
-                           unsigned int* ext_max, DevStatus* st, cudaStream_t s)
+namespace {
+RecArgs make_rec_args(const fla_cloud& cl, const fla_mesh& m, const fla_deposit_cfg& cfg, const uint32_t* perm,
+                      const uint32_t* bin_start, int64_t n_cells, void* rec, unsigned int* ext_max, DevStatus* st)
 {
     RecArgs a{};
     a.state = cl.state_dev;
@@ -478,6 +639,16 @@ cudaError_t launch_records(const fla_cloud& cl, const fla_mesh& m, const fla_dep
     a.mlp = (const unsigned char*)cfg.mlp_dev;
     a.mlp_out = cfg.mlp_out_dev;
     a.dx = 1.0 / m.n;
+    return a;
+}
+}  // namespace
+
+cudaError_t launch_records(const fla_cloud& cl, const fla_mesh& m, const fla_deposit_cfg& cfg,
+                           const uint32_t* perm, const uint32_t* bin_start, int64_t n_cells, void* rec,
+                           unsigned int* ext_max, DevStatus* st, cudaStream_t s, float* aux)
+{
+    RecArgs a = make_rec_args(cl, m, cfg, perm, bin_start, n_cells, rec, ext_max, st);
+    a.aux = aux;
     if (a.n == 0) return cudaSuccess;
     if (a.mlp) {   // validated by the caller: single precision, spherical kernel
         const unsigned blocks = (unsigned)((a.n + kMlpRows - 1) / kMlpRows);
@@ -492,6 +663,28 @@ cudaError_t launch_records(const fla_cloud& cl, const fla_mesh& m, const fla_dep
     }
     if (m.dim == 2) return iso ? launch_t<double, 2, 0>(a, s) : launch_t<double, 2, 1>(a, s);
     return iso ? launch_t<double, 3, 0>(a, s) : launch_t<double, 3, 1>(a, s);
+}
+
+}  // namespace fla
+
+namespace fla {
+
+cudaError_t launch_learn_backward(const fla_cloud& cl, const fla_mesh& m, const fla_deposit_cfg& cfg,
+                                  const uint32_t* perm, const uint32_t* bin_start, int64_t n_cells,
+                                  const float* dldc, float* partial, int n_parts, DevStatus* st, cudaStream_t s)
+{
+    RecArgs a = make_rec_args(cl, m, cfg, perm, bin_start, n_cells, nullptr, nullptr, st);
+    cudaError_t e;
+    if (m.dim == 2) {
+        e = cudaFuncSetAttribute(k_learn_backward<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLearnSmemBytes);
+        if (e != cudaSuccess) return e;
+        k_learn_backward<2><<<n_parts, kMlpRows, kLearnSmemBytes, s>>>(a, dldc, partial);
+    } else {
+        e = cudaFuncSetAttribute(k_learn_backward<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLearnSmemBytes);
+        if (e != cudaSuccess) return e;
+        k_learn_backward<3><<<n_parts, kMlpRows, kLearnSmemBytes, s>>>(a, dldc, partial);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace fla

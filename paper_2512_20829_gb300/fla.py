@@ -18,7 +18,7 @@ from . import inputs as I
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfla.so")
 
-ABI_VERSION = 3            # FLA_ABI_VERSION of include/fla.h that these structures mirror
+ABI_VERSION = 4            # FLA_ABI_VERSION of include/fla.h that these structures mirror
 F32, F64 = 0, 1
 CLOUD_FLA, CLOUD_LPT = 0, 1
 KERNEL_ISO, KERNEL_ANISO = 0, 1
@@ -33,7 +33,7 @@ EXPORTED = ["fla_abi_version", "fla_status_string", "fla_create", "fla_destroy",
             "fla_carrier_nodes_bytes", "fla_carrier_sample", "fla_batch_deadline", "fla_advance",
             "fla_workspace_size", "fla_cell_bins", "fla_deposit_sources", "psicell_deposit", "fla_sync_status",
             "fla_profile_enable", "fla_profile_read", "fla_phase_name", "fla_fold_bytes", "fla_mlp_pack",
-            "fla_mlp_forward"]
+            "fla_mlp_forward", "fla_learn_workspace_size", "fla_learn_grad", "fla_adam_step"]
 MLP_FEATURES, MLP_HIDDEN, MLP_PARAMS, MLP_PACKED_BYTES = 6, 64, 8833, 19472
 PREC_MIXED, PREC_PLAIN = 0, 1
 TAU_FOLD = 1e-2
@@ -123,6 +123,10 @@ def lib() -> C.CDLL:
         L.fla_fold_bytes.restype = C.c_size_t
         L.fla_mlp_pack.argtypes = [v, v, v, v]
         L.fla_mlp_forward.argtypes = [v, v, v, i64, v, v]
+        L.fla_learn_workspace_size.argtypes = [v, P(Mesh), i64, P(C.c_size_t)]
+        L.fla_learn_grad.argtypes = [v, P(Cloud), P(Mesh), P(DepositCfg), v, i64, v, P(Sources), v, v, v,
+                                     C.c_size_t, v, C.c_size_t, v]
+        L.fla_adam_step.argtypes = [v, v, v, v, v, i64, C.c_float, C.c_float, C.c_float, C.c_float, i32, v]
         if L.fla_abi_version() != ABI_VERSION:
             raise FlaError(f"{LIB_PATH} has ABI version {L.fla_abi_version()}, the binding expects "
                            f"{ABI_VERSION}: rebuild it with __graft_entry__.build()")
@@ -452,6 +456,41 @@ class LearnedCorrection:
         check(lib().fla_mlp_forward(self.ctx.handle, _ptr(self.packed), _ptr(features), int(n), _ptr(out),
                                     _stream_ptr(stream)), "fla_mlp_forward")
         return out[:n]
+
+
+class LearnBuffers:
+    """Device buffers of one training sample: the cloud state (fixed), its
+    workspaces, the training cells and their targets."""
+
+    def __init__(self, ctx: "Context", cloud: "DeviceCloud", m: "Mesh", cells, targets, kernel: int = KERNEL_ISO):
+        torch = _torch()
+        dev = cloud.state.device
+        self.ctx, self.cloud, self.m = ctx, cloud, m
+        self.ws = aligned_ws(workspace(m, F32, kernel, cloud.n, dev))
+        nb = C.c_size_t()
+        check(lib().fla_learn_workspace_size(ctx.handle, C.byref(m), int(cloud.n), C.byref(nb)),
+              "fla_learn_workspace_size")
+        self.lws = aligned_ws(torch.empty(nb.value + 256, dtype=torch.uint8, device=dev))
+        self.cells = torch.as_tensor(np.asarray(cells, np.int64).astype(np.int32)).to(dev)
+        self.targets = torch.as_tensor(np.ascontiguousarray(targets, np.float32)).to(dev)
+        self.out = SourceFields(m, F32, dev)
+
+
+def learn_grad(ctx: "Context", b: LearnBuffers, cfg: DepositCfg, grad, loss, stream=None):
+    """Adds this sample's loss to loss[0] and its parameter gradient to grad."""
+    cs = b.cloud.struct()
+    so = b.out.struct()
+    check(lib().fla_learn_grad(ctx.handle, C.byref(cs), C.byref(b.m), C.byref(cfg), _ptr(b.cells),
+                               int(b.cells.numel()), _ptr(b.targets), C.byref(so), _ptr(grad), _ptr(loss),
+                               _ptr(b.ws), b.ws.numel(), _ptr(b.lws), b.lws.numel(), _stream_ptr(stream)),
+          "fla_learn_grad")
+
+
+def adam_step(ctx: "Context", params, grad, m, v, step: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+              stream=None):
+    check(lib().fla_adam_step(ctx.handle, _ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(params.numel()),
+                              float(lr), float(beta1), float(beta2), float(eps), int(step), _stream_ptr(stream)),
+          "fla_adam_step")
 
 
 def init_mlp_params(seed: int = 0, scale: float = 1.0, zero_last: bool = False) -> np.ndarray:

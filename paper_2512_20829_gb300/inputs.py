@@ -153,20 +153,27 @@ def _jet_vortices(rng: np.random.Generator, n_vort: int, width: float) -> np.nda
     return np.stack([x0, yc, gam, rc, uadv], axis=1)
 
 
-def jet_vortex_2d(scale: int = 1, nsteps: int = 1000, lpt_per_batch: int = 65_536) -> Workload:
+def jet_vortex_2d(scale: int = 1, nsteps: int = 1000, lpt_per_batch: int = 65_536, flow_seed: int = 2,
+                  seeding: int = 1) -> Workload:
     """512^2 cells, planar jet + 8 Lamb-Oseen vortices, inlet releases.
 
     ``scale`` divides the mesh by ``scale`` and the release count and release
     size by ``scale``; the number of steps is kept unless ``nsteps`` is given.
+    ``flow_seed`` draws the vortices and the releases' Stokes numbers.
+    ``seeding`` multiplies both the release count and the seeds per release
+    (``seeding**2`` times the seeds of the same droplet population: each
+    release of the base seeding is split into ``seeding`` releases with its
+    Stokes number); the PSI-CELL parcels are built for ``seeding == 1`` only.
     """
     N = 512 // scale
-    n_batches = 256 // scale
-    per_batch = 1024 // scale
+    base_batches = 256 // scale
+    n_batches = base_batches * seeding
+    per_batch = (1024 // scale) * seeding
     width = 0.05
-    rng = np.random.default_rng(2)
+    rng = np.random.default_rng(flow_seed)
     car = Carrier(kind=CARRIER_JET_VORTEX_2D, dim=2, vortices=_jet_vortices(rng, 8, width),
                   jet_width=width, steady=False)
-    St0 = rng.uniform(0.2, 2.0, n_batches)
+    St0 = np.repeat(rng.uniform(0.2, 2.0, base_batches), seeding)
     step_start = np.floor(nsteps * np.arange(n_batches) / n_batches).astype(np.int32)
     ys = 0.45 + (np.arange(per_batch) + 0.5) * (0.1 / per_batch)
     x0 = np.zeros((n_batches * per_batch, 2))
@@ -181,7 +188,7 @@ def jet_vortex_2d(scale: int = 1, nsteps: int = 1000, lpt_per_batch: int = 65_53
     fla = Cloud(kind=CLOUD_FLA, x0=x0, batch=batch, step_start=step_start, St0=St0,
                 n0=np.ones(n_batches), h0=np.full(n_batches, h0))
     lpt = None
-    if lpt_per_batch:
+    if lpt_per_batch and seeding == 1:
         m_b = lpt_per_batch // (scale * scale) if scale > 1 else lpt_per_batch
         rng3 = np.random.default_rng(3)
         xl = np.zeros((n_batches * m_b, 2))
@@ -191,7 +198,7 @@ def jet_vortex_2d(scale: int = 1, nsteps: int = 1000, lpt_per_batch: int = 65_53
                     step_start=step_start.copy(), St0=St0.copy(),
                     n0=np.full(n_batches, V_inj / m_b), h0=np.zeros(n_batches))
     dx = 1.0 / N
-    return Workload(name=f"jet_vortex_2d_{N}x{N}_{x0.shape[0]}fla", dim=2, n_cells_axis=N, dt=dt,
+    return Workload(name=f"jet_vortex_2d_{N}x{N}_{x0.shape[0]}fla_flow{flow_seed}", dim=2, n_cells_axis=N, dt=dt,
                     nsteps=nsteps, window=10, delta=-0.2, carrier=car, fla=fla, lpt=lpt,
                     kernel=KERNEL_ISO, h_min=0.5 * dx, h_max=4.0 * dx)
 
