@@ -157,7 +157,7 @@ class JetPath:
     """Device buffers and the issue order of one whole run of a workload."""
 
     def __init__(self, ctx, wl, fla, with_fla=True, with_lpt=False, dtype=None, precision=None,
-                 fold_guard=False):
+                 fold_guard=False, mlp=None):
         import torch
         self.fla, self.ctx, self.wl = fla, ctx, wl
         self.dtype = fla.F32 if dtype is None else dtype
@@ -165,7 +165,9 @@ class JetPath:
         self.m = fla.mesh(wl.dim, wl.n_cells_axis)
         self.desc = fla.carrier_desc(wl.carrier)
         self.nodes = fla.nodes_buffer(self.m, self.dtype)
-        self.cfg = fla.deposit_cfg(wl.kernel, wl.h_min, wl.h_max, wl.window * wl.dt, wl.p, precision=self.precision)
+        self.mlp = mlp
+        self.cfg = fla.deposit_cfg(wl.kernel, wl.h_min, wl.h_max, wl.window * wl.dt, wl.p, precision=self.precision,
+                                   mlp=mlp)
         self.cloud = fla.DeviceCloud.from_seeds(wl.fla, wl.dim, wl.delta, wl.dt, self.dtype) if with_fla else None
         if self.cloud is not None and self.dtype == fla.F32 and self.precision == fla.PREC_MIXED and fold_guard:
             self.cloud.enable_fold()   # double-precision J, W near fold caustics
@@ -367,8 +369,15 @@ def run_ours(args):
     precision = None
     if dtype == fla.F32 and not args.no_variants:
         variants = {}
-        for name, prec, guard in (("plain_fp32", fla.PREC_PLAIN, False), ("mixed_fold_guard", fla.PREC_MIXED, True)):
-            vp = JetPath(ctx, wl, fla, with_fla=True, dtype=dtype, precision=prec, fold_guard=guard)
+        learned = None
+        if wl.kernel == fla.KERNEL_ISO:
+            # zero last layer: the same h as the plain method, so the difference is the network's cost
+            learned = fla.LearnedCorrection(ctx, fla.init_mlp_params(0, 0.5, zero_last=True))
+        forms = [("plain_fp32", fla.PREC_PLAIN, False, None), ("mixed_fold_guard", fla.PREC_MIXED, True, None)]
+        if learned is not None:
+            forms.append(("learned_tensor_core_mlp", fla.PREC_MIXED, False, learned))
+        for name, prec, guard, mlp in forms:
+            vp = JetPath(ctx, wl, fla, with_fla=True, dtype=dtype, precision=prec, fold_guard=guard, mlp=mlp)
             vg, _ = capture(vp)
             vg.replay()
             torch.cuda.synchronize()
@@ -376,9 +385,10 @@ def run_ours(args):
             vt = timed_replays(vp, vg, 3, flush)
             vst = ctx.sync_status(reset=True)
             variants[name] = {"ms_per_step": round(float(np.mean(vt)), 4),
+                              "cells_per_s": cells * deposits / (float(np.mean(vt)) * 1e-3),
                               "fold_steps_per_run": vst.fold_steps / 3}
             del vg, vp
-        precision = {"mode": "mixed: FP32 trajectories and kernels, det J and n in FP64 where det J cancels",
+        precision = {"headline": "mixed: FP32 trajectories and kernels, det J and n in FP64 where det J cancels",
                      "variants": variants}
 
     # ---------------- PSI-CELL reference leg (2^24 parcels, same flow, same windows)
@@ -420,7 +430,7 @@ def run_ours(args):
             "phases": phases,
             "e2e": {"value": world * cells * deposits / (e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
-            "precision": precision,
+            "forms": precision,
             "psicell_reference": psi,
             "cpu_baseline": cpu,
         }

@@ -85,8 +85,13 @@ def test_adam_step_matches_definition(ctx):
 
 
 def test_short_training_lowers_the_loss(ctx):
+    """Targets made by the oracle with every h0 scaled by e^0.5: a network with
+    c = 0.5 reaches zero loss wherever h is not clamped."""
     dim, N, n = 2, 48, 3000
-    s, cells, T = _problem(dim, N, n, 11)
+    s, cells, _ = _problem(dim, N, n, 11)
+    D0 = O.dep_struct(dim=dim, N=N, kernel=0, h_min=0.5 / N, h_max=4.0 / N, p=1.0, window_dt=0.01)
+    sm, sv, _ = O.nw_deposit_celllist(D0, s.x, s.J, s.acc, s.status, s.batch, s.n0, s.h0 * np.exp(0.5), cells=cells)
+    T = np.concatenate([sm[:, None], sv], axis=1)
     net = fla.LearnedCorrection(ctx, fla.init_mlp_params(12, 0.5, zero_last=True))
     cl = gpu_cloud_from_state(s, fla.F32)
     m = fla.mesh(dim, N)
@@ -97,12 +102,12 @@ def test_short_training_lowers_the_loss(ctx):
     mom = torch.zeros_like(grad)
     var = torch.zeros_like(grad)
     losses = []
-    for step in range(1, 41):
+    for step in range(1, 61):
         grad.zero_()
         loss.zero_()
         fla.learn_grad(ctx, b, cfg, grad, loss)
-        fla.adam_step(ctx, net.params, grad, mom, var, step, lr=3e-3)
+        fla.adam_step(ctx, net.params, grad, mom, var, step, lr=2e-2)
         net.pack()
         losses.append(float(loss.item()))
     print("\nloss", losses[0], "->", losses[-1])
-    assert losses[-1] < 0.97 * losses[0]
+    assert losses[-1] < 0.5 * losses[0]
