@@ -91,6 +91,7 @@ def parse():
     ap.add_argument("--no-psicell", action="store_true", help="skip the PSI-CELL reference leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-variants", action="store_true", help="skip the other precision forms")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-clouds leg")
     ap.add_argument("--profile-only", action="store_true",
                     help="one eager run of the whole path, nothing else (for external profilers)")
     return ap.parse_args()
@@ -199,6 +200,74 @@ class JetPath:
                 fla.deposit_sources(self.ctx, self.cloud, m, self.cfg, self.out, self.ws)
             if self.lpt is not None:
                 fla.psicell(self.ctx, self.lpt, m, wl.window * wl.dt, self.psi, self.ws)
+
+
+def batch_leg(ctx, fla, I, flush, steps):
+    """64 clouds of uneven size and mesh, 100 steps (10 deposits) per run: the
+    batched launches of fla_batch_run (one graph) against the same clouds
+    issued one by one through the per-cloud calls (also one graph)."""
+    import torch
+    wls = I.batch_clouds()
+    b = fla.Batch(ctx, wls)
+    s = torch.cuda.Stream()
+    windows = wls[0].nsteps // wls[0].window
+    with torch.cuda.stream(s):
+        b.run(windows, stream=s)            # tuning windows, then the graph
+        torch.cuda.synchronize()
+        b.reset(s)
+        b.run(windows, stream=s)            # the graph of a whole run
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(steps):
+            b.reset(s)
+            flush.add_(1.0)
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record(s)
+            b.run(windows, stream=s)
+            eb.record(s)
+            torch.cuda.synchronize()
+            times.append(ea.elapsed_time(eb))
+    batched = float(np.median(times))
+    tun = b.tuning()
+    del b
+    torch.cuda.empty_cache()
+    # the same clouds through the per-cloud calls
+    paths = [JetPath(ctx, wl, fla, with_fla=True, dtype=fla.F32) for wl in wls]
+
+    class _All:
+        def __init__(self, ps):
+            self.ps, self.ctx = ps, ctx
+
+        def reset(self):
+            for p in self.ps:
+                p.reset()
+
+        def issue(self):
+            for p in self.ps:
+                p.issue()
+    allp = _All(paths)
+    g, launches = capture(allp)
+    ut = []
+    for _ in range(steps):
+        allp.reset()
+        flush.add_(1.0)
+        torch.cuda.synchronize()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record()
+        g.replay()
+        eb.record()
+        torch.cuda.synchronize()
+        ut.append(ea.elapsed_time(eb))
+    unbatched = float(np.median(ut))
+    del g, paths, allp
+    torch.cuda.empty_cache()
+    cells = sum(w.n_cells for w in wls)
+    return {"workload": f"{len(wls)} clouds (seed 4): {sum(w.fla.n for w in wls):,} seeds, 1e3-5e5 per cloud, "
+                        f"2D 32^2-256^2 spherical / 3D 32^3-64^3 J-scaled, {windows} windows of 10 steps",
+            "cells": cells, "ms_per_run": round(batched, 4), "cells_per_s": cells * windows / (batched * 1e-3),
+            "unbatched_ms_per_run": round(unbatched, 4), "speedup_vs_unbatched": round(unbatched / batched, 3),
+            "launches_per_run": tun["launches_per_window"] * windows, "unbatched_launches_per_run": launches,
+            "tuning": tun}
 
 
 def capture(path):
@@ -410,6 +479,10 @@ def run_ours(args):
                "fla_speedup_vs_psicell": round(pms / ms_per_step, 2)}
         del pg, ppath
 
+    batch = None
+    if rank == 0 and not args.no_batch and args.workload == "jet_vortex_2d":
+        batch = batch_leg(ctx, fla, I, flush, max(3, args.steps // 2))
+
     cpu = None
     if rank == 0 and not args.no_cpu and args.workload == "jet_vortex_2d":
         cpu = cpu_baseline(wl)
@@ -432,6 +505,7 @@ def run_ours(args):
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
             "forms": precision,
             "psicell_reference": psi,
+            "batch": batch,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))

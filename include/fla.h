@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define FLA_ABI_VERSION 4
+#define FLA_ABI_VERSION 5
 
 /* cudaStream_t without including the CUDA headers. */
 typedef struct CUstream_st* fla_stream_t;
@@ -357,6 +357,57 @@ int fla_learn_grad(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, c
  *   p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps). */
 int fla_adam_step(fla_ctx* ctx, float* params_dev, const float* grad_dev, float* m_dev, float* v_dev, int64_t n,
                   float lr, float beta1, float beta2, float eps, int32_t step, fla_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Batched clouds.  Many single-precision FLA clouds of different sizes,
+ * meshes (2D or 3D), carriers and kernels advance and deposit together: each
+ * window (window_steps steps of dt) samples every carrier at the window's
+ * start, advances every cloud with its window sums reset, and deposits every
+ * cloud's kernel-regression sources into its own outputs -- per window a few
+ * launches for all clouds instead of a dozen per cloud.  The clouds share one
+ * global cell space, so one key pass and one radix sort bin all of them; each
+ * cloud's results are those of fla_carrier_sample + fla_advance +
+ * fla_deposit_sources for it alone (the advance bit for bit; the deposit with
+ * the tile gather that those calls use for 3D, FP64 and anisotropic clouds).
+ * The window start step lives on the device (fla_batch_set_step), so
+ * fla_batch_run captures its windows once into a CUDA graph and replays it.
+ * The first fla_batch_run tunes the launch shapes (advance block size,
+ * persistent gather CTAs per SM, gather tile order) on its first windows,
+ * timing them with events (it synchronises the stream); none of these
+ * changes any result.  The caller owns every buffer; the plan's tables live in
+ * the workspace (fla_batch_workspace_size bytes, 256-byte aligned), and the
+ * items' buffers must stay valid for the plan's life.
+ * ------------------------------------------------------------------------ */
+typedef struct fla_batch_plan fla_batch_plan;
+
+typedef struct {
+    fla_cloud cloud;           /* FLA_CLOUD_FLA, FLA_F32, no fold guard */
+    fla_mesh mesh;
+    fla_carrier_desc carrier;  /* sampled at t = step * dt at each window start */
+    void* nodes_dev;           /* fla_carrier_nodes_bytes(&mesh, FLA_F32) bytes, 16-byte aligned */
+    fla_deposit_cfg cfg;       /* without the learned correction */
+    fla_sources out;           /* FP32 outputs on this cloud's mesh */
+} fla_batch_item;
+
+int fla_batch_workspace_size(const fla_batch_item* items, int32_t n_items, size_t* bytes);
+/* Validates the items, writes the tables into the workspace (synchronous
+ * copies) and sets the device step to step0. */
+int fla_batch_create(fla_ctx* ctx, const fla_batch_item* items, int32_t n_items, double dt, int32_t window_steps,
+                     int32_t step0, void* workspace_dev, size_t workspace_bytes, fla_batch_plan** out);
+/* Runs n_windows windows from the device step on stream (a stream other than
+ * the legacy default stream for the graph; on the legacy stream, or inside the
+ * caller's own capture, the windows are plain launches). */
+int fla_batch_run(fla_ctx* ctx, fla_batch_plan* plan, int32_t n_windows, fla_stream_t stream);
+int fla_batch_set_step(fla_batch_plan* plan, int32_t step, fla_stream_t stream);
+/* The launch shapes in use and the kernel launches per window; returns
+ * FLA_ERR_UNSUPPORTED (values still written) before the tuning has run. */
+int fla_batch_tuning(const fla_batch_plan* plan, int32_t* advance_threads, int32_t* gather_ctas_per_sm,
+                     int32_t* tile_order, int32_t* launches_per_window);
+/* Fixes the launch shapes (advance 64/128/256, gather CTAs per SM 1..8, tile
+ * order 0 natural / 1 interleaved) and skips the tuning. */
+int fla_batch_set_tuning(fla_batch_plan* plan, int32_t advance_threads, int32_t gather_ctas_per_sm,
+                         int32_t tile_order);
+void fla_batch_destroy(fla_batch_plan* plan);
 
 /* Read the device status block (synchronises `stream`); reset != 0 zeroes it
  * afterwards.  Returns FLA_ERR_NONFINITE when nonfinite > 0, else FLA_OK. */

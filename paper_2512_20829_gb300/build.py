@@ -20,7 +20,7 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libfla.so")
 
 SOURCES = ["api.cu", "carrier.cu", "advance.cu", "binning.cu", "records.cu", "deposit.cu", "gather2d.cu", "noalloc.cu",
-           "mlp.cu", "learn.cu"]
+           "mlp.cu", "learn.cu", "batch.cu"]
 NO_FMA = {"records.cu"}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

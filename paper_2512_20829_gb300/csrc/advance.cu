@@ -19,7 +19,7 @@
 // appended to a list, and a second pass integrates the listed droplets from
 // the same starting state with the guard logic.  The result equals one pass
 // that applies the guard at every step.
-#include "fla_internal.cuh"
+#include "batch.cuh"
 
 namespace fla {
 namespace {
@@ -422,6 +422,46 @@ __global__ void __launch_bounds__(128) k_advance(AdvArgs a)
     }
 }
 
+// Batched clouds of one dimension (single precision, FLA): droplet g of the
+// group belongs to cloud k with pre[k] <= g < pre[k + 1] of the group's
+// prefix; the per-droplet work is that of k_advance.
+template <int D>
+__global__ void __launch_bounds__(256) k_batch_advance(BatchDev b, int first, int count, int64_t n_dim,
+                                                       int nsteps, double dt, int reset, DevStatus* st)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int n = 0, nf = 0;
+    if (g < n_dim) {
+        // droplets of the group's clouds are contiguous in the global droplet order
+        const int64_t base = b.drop_pre[first];
+        const int k = first + batch_find(b.drop_pre + first, count, base + g);
+        const BatchCloud& c = b.clouds[k];
+        AdvArgs a{};
+        a.state = c.state;
+        a.meta = c.meta;
+        a.batches = c.batches;
+        a.nodes = c.nodes;
+        a.n = c.n;
+        a.N = c.N;
+        a.step0 = *b.step;
+        a.nsteps = nsteps;
+        a.dt = dt;
+        a.delta = c.delta;
+        a.reset = reset;
+        a.status = st;
+        n = advance_one<float, D, true, kPlain>(a, base + g - b.drop_pre[k], nf);
+    }
+    __shared__ int s_sum[8];
+    const int w = __reduce_add_sync(0xffffffffu, n);
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += s_sum[q];
+        if (t) atomicAdd(&st->droplet_steps, (unsigned long long)t);
+    }
+}
+
 template <typename T, int D, bool FLA, int MODE = kPlain>
 cudaError_t launch_t(const AdvArgs& a, cudaStream_t s, int guarded_blocks = 0)
 {
@@ -475,6 +515,27 @@ cudaError_t launch_advance(const fla_cloud& cl, const fla_mesh& m, const void* n
     }
     if (cl.dim == 2) return fla ? launch_t<double, 2, true>(a, s) : launch_t<double, 2, false>(a, s);
     return fla ? launch_t<double, 3, true>(a, s) : launch_t<double, 3, false>(a, s);
+}
+
+// Loads the batched advance kernels' module before the autotuner times them.
+cudaError_t batch_prepare_advance()
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_batch_advance<2>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_batch_advance<3>);
+    return e;
+}
+
+cudaError_t launch_batch_advance(const BatchDev& b, int dim, int64_t n_dim, int nsteps, double dt, bool reset,
+                                 int threads, DevStatus* st, cudaStream_t s)
+{
+    if (n_dim == 0 || nsteps == 0) return cudaSuccess;
+    const int g0 = batch_group(dim, 0);
+    const int first = b.group_first[g0], count = b.group_first[g0 + 2] - first;
+    const unsigned blocks = (unsigned)((n_dim + threads - 1) / threads);
+    if (dim == 2) k_batch_advance<2><<<blocks, threads, 0, s>>>(b, first, count, n_dim, nsteps, dt, reset ? 1 : 0, st);
+    else k_batch_advance<3><<<blocks, threads, 0, s>>>(b, first, count, n_dim, nsteps, dt, reset ? 1 : 0, st);
+    return cudaGetLastError();
 }
 
 }  // namespace fla

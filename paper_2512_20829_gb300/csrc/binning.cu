@@ -6,7 +6,7 @@
 // exclusive scans over tiles, (3) a stable scatter in which each warp ranks
 // its keys with __match_any_sync and per-warp running digit counters, so a
 // key's destination depends only on the input order.
-#include "fla_internal.cuh"
+#include "batch.cuh"
 
 namespace fla {
 namespace {
@@ -24,20 +24,28 @@ __global__ void __launch_bounds__(256) k_cell_keys(const T* __restrict__ state, 
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    T x[4];
-    load4<T>(state, i, x);   // plane 0 starts with the position
-    bool ok = (meta[i] & FLA_META_ACTIVE) != 0;
-    uint32_t key = 0, mul = 1;
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        ok &= (x[a] >= T(0) && x[a] <= T(1));
-        const T s = x[a] * T(N);            // formed in the cloud's precision
-        int c = ok ? (int)floor(s) : 0;
-        c = c > N - 1 ? N - 1 : c;
-        key += (uint32_t)c * mul;
-        mul *= (uint32_t)N;
-    }
-    keys[i] = ok ? key : sentinel;
+    uint32_t key;
+    keys[i] = cell_key_of<T, D>(state, meta, i, N, &key) ? key : sentinel;
+}
+
+// Batched clouds: global key = the cloud's cell offset + its cell key;
+// droplets without a cell get the sentinel cells_total.
+__global__ void __launch_bounds__(256) k_batch_keys(BatchDev b, uint32_t* __restrict__ keys)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= b.n_total) return;
+    const int k = batch_find(b.drop_pre, b.n_clouds, g);
+    const BatchCloud& c = b.clouds[k];
+    const int64_t i = g - b.drop_pre[k];
+    uint32_t key;
+    const bool ok = c.dim == 2 ? cell_key_of<float, 2>(c.state, c.meta, i, c.N, &key)
+                               : cell_key_of<float, 3>(c.state, c.meta, i, c.N, &key);
+    keys[g] = ok ? (uint32_t)(c.cell_off + key) : (uint32_t)b.cells_total;
+}
+
+__global__ void k_batch_step(int* step, int nsteps)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *step += nsteps;
 }
 
 __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
@@ -260,6 +268,19 @@ cudaError_t launch_bin_start(const uint32_t* keys_sorted, int64_t n, int64_t n_c
 {
     const unsigned blocks = (unsigned)((n_cells + 1 + 255) / 256);
     k_bin_start<<<blocks, 256, 0, s>>>(keys_sorted, n, n_cells, bin_start);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_keys(const BatchDev& b, uint32_t* keys, cudaStream_t s)
+{
+    if (b.n_total == 0) return cudaSuccess;
+    k_batch_keys<<<(unsigned)((b.n_total + 255) / 256), 256, 0, s>>>(b, keys);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_step(const BatchDev& b, int nsteps, cudaStream_t s)
+{
+    k_batch_step<<<1, 32, 0, s>>>(b.step, nsteps);
     return cudaGetLastError();
 }
 

@@ -5,7 +5,7 @@
 // and 8).  Here synthetic analytic carriers stand in for it: they are sampled
 // once per carrier step on the (n+1)^dim mesh nodes and the advance kernel
 // interpolates the node values, as a mesh-based solver would.
-#include "fla_internal.cuh"
+#include "batch.cuh"
 
 namespace fla {
 namespace {
@@ -160,11 +160,10 @@ __device__ void eval_carrier(const CarrierArgs& p, const T* x, T* u, T* G)
     }
 }
 
+// u and grad u at node k (x fastest) written as one node record.
 template <typename T, int D>
-__global__ void __launch_bounds__(256) k_carrier_sample(CarrierArgs p, T* __restrict__ nodes, int64_t total)
+__device__ __forceinline__ void sample_node(const CarrierArgs& p, T* __restrict__ nodes, int64_t k)
 {
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= total) return;
     const int nn = p.N + 1;
     T x[3];
     int64_t r = k;
@@ -187,15 +186,22 @@ __global__ void __launch_bounds__(256) k_carrier_sample(CarrierArgs p, T* __rest
     for (int v = 0; v < S / 4; ++v) store4<T>(nodes, k * (S / 4) + v, out + 4 * v);
 }
 
-}  // namespace
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_carrier_sample(CarrierArgs p, T* __restrict__ nodes, int64_t total)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= total) return;
+    sample_node<T, D>(p, nodes, k);
+}
 
-cudaError_t launch_carrier_sample(const fla_carrier_desc& c, const fla_mesh& m, double t, int dtype, void* nodes,
-                                  cudaStream_t s)
+// The carrier's arguments at time t (vortex centres carried with the jet and
+// wrapped; Lamb-Oseen constants), each operation rounded once.
+__host__ __device__ inline CarrierArgs carrier_args(const fla_carrier_desc& c, int N, double t)
 {
     CarrierArgs p{};
     p.kind = c.kind;
     p.dim = c.dim;
-    p.N = m.n;
+    p.N = N;
     p.n_vortex = c.n_vortex;
     for (int i = 0; i < 3; ++i) {
         p.U[i] = c.U[i];
@@ -203,20 +209,62 @@ cudaError_t launch_carrier_sample(const fla_carrier_desc& c, const fla_mesh& m, 
         p.abc[i] = c.abc[i];
     }
     for (int i = 0; i < 9; ++i) p.A[i] = c.A[i];
-    for (int k = 0; k < c.n_vortex; ++k) {
+    for (int k = 0; k < c.n_vortex && k < FLA_MAX_VORTICES; ++k) {
+#ifdef __CUDA_ARCH__
+        double xc = __dadd_rn(c.vortex[k][0], __dmul_rn(c.vortex[k][4], t));
+        xc = __dsub_rn(xc, floor(xc));
+        const double rc2 = __dmul_rn(c.vortex[k][3], c.vortex[k][3]);
+        const double cg = __ddiv_rn(c.vortex[k][2], 2.0 * 3.14159265358979323846);
+        p.vort[k][2] = __ddiv_rn(1.0, rc2);
+        p.vort[k][3] = __ddiv_rn(cg, rc2);
+        p.vort[k][4] = __ddiv_rn(cg, __dmul_rn(rc2, rc2));
+#else
         double xc = c.vortex[k][0] + c.vortex[k][4] * t;   // carried with the jet
         xc -= floor(xc);                                   // wrapped into [0, 1)
         const double rc2 = c.vortex[k][3] * c.vortex[k][3];
         const double cg = c.vortex[k][2] / (2.0 * 3.14159265358979323846);   // Gamma / (2 pi)
-        p.vort[k][0] = xc;
-        p.vort[k][1] = c.vortex[k][1];
         p.vort[k][2] = 1.0 / rc2;
         p.vort[k][3] = cg / rc2;
         p.vort[k][4] = cg / (rc2 * rc2);
+#endif
+        p.vort[k][0] = xc;
+        p.vort[k][1] = c.vortex[k][1];
     }
     p.jet_width = c.jet_width;
     p.jet_amp = c.jet_amp;
     p.jet_radius = c.jet_radius;
+    return p;
+}
+
+// Batched clouds: the carrier arguments of each cloud at the window's start ...
+__global__ void k_batch_carrier_args(BatchDev b, double dt)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= b.n_clouds) return;
+    const BatchCloud& c = b.clouds[k];
+    const double t = __dmul_rn((double)*b.step, dt);
+    reinterpret_cast<CarrierArgs*>(b.cargs)[k] = carrier_args(c.car, c.N, t);
+}
+
+// ... and every node of every cloud (single precision).
+__global__ void __launch_bounds__(256) k_batch_carrier_sample(BatchDev b)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= b.nodes_total) return;
+    const int k = batch_find(b.node_pre, b.n_clouds, g);
+    const BatchCloud& c = b.clouds[k];
+    const CarrierArgs& p = reinterpret_cast<const CarrierArgs*>(b.cargs)[k];
+    const int64_t r = g - b.node_pre[k];
+    if (c.dim == 2) sample_node<float, 2>(p, c.nodes, r);
+    else sample_node<float, 3>(p, c.nodes, r);
+}
+
+}  // namespace
+
+cudaError_t launch_carrier_sample(const fla_carrier_desc& c, const fla_mesh& m, double t, int dtype, void* nodes,
+                                  cudaStream_t s)
+{
+    const CarrierArgs p = carrier_args(c, m.n, t);
     const int64_t nn = m.n + 1;
     const int64_t total = m.dim == 2 ? nn * nn : nn * nn * nn;
     const int threads = 256;
@@ -228,6 +276,16 @@ cudaError_t launch_carrier_sample(const fla_carrier_desc& c, const fla_mesh& m, 
         if (m.dim == 2) k_carrier_sample<double, 2><<<blocks, threads, 0, s>>>(p, (double*)nodes, total);
         else k_carrier_sample<double, 3><<<blocks, threads, 0, s>>>(p, (double*)nodes, total);
     }
+    return cudaGetLastError();
+}
+
+size_t batch_carrier_args_bytes() { return sizeof(CarrierArgs); }
+
+cudaError_t launch_batch_carrier(const BatchDev& b, double dt, cudaStream_t s)
+{
+    k_batch_carrier_args<<<(b.n_clouds + 63) / 64, 64, 0, s>>>(b, dt);
+    if (b.nodes_total > 0)
+        k_batch_carrier_sample<<<(unsigned)((b.nodes_total + 255) / 256), 256, 0, s>>>(b);
     return cudaGetLastError();
 }
 

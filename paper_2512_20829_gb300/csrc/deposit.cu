@@ -12,7 +12,7 @@
 // precision, FMA accumulation.  Each staged chunk is summed plainly and chunk
 // sums are added with Neumaier compensation.  Every cell sums its records in
 // staging order and no atomics touch the outputs, so results are deterministic.
-#include "fla_internal.cuh"
+#include "batch.cuh"
 
 namespace fla {
 namespace {
@@ -36,6 +36,7 @@ __device__ __forceinline__ void neumaier(T& s, T& c, T v)
 
 struct GatherArgs {
     const void* rec;
+    int64_t rec_base;             // sorted position of rec[0]
     const uint32_t* bin_start;
     const unsigned int* ext_max;
     int N;
@@ -145,8 +146,9 @@ __device__ __forceinline__ T weight_of(const T* r, const float* xcf, const T* xc
     }
 }
 
+// One CTA tile of cells with origin (tx0, ty0, tz0).
 template <typename T, int D, int KER>
-__global__ void __launch_bounds__(GT) k_nw_gather(GatherArgs a)
+__device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty0, int tz0)
 {
     constexpr int RV = record_values(D, KER);
     constexpr int R4 = RV / 4;
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(GT) k_nw_gather(GatherArgs a)
 
     const int N = a.N;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int t0[3] = {(int)blockIdx.x * TX, (int)blockIdx.y * TY, (int)blockIdx.z * TZ};
+    const int t0[3] = {tx0, ty0, tz0};
     // warp sub-tile origin and this lane's cell
     int w0[3], cc[3];
     if (D == 2) {
@@ -277,7 +279,8 @@ __global__ void __launch_bounds__(GT) k_nw_gather(GatherArgs a)
                 bool keep = false;
                 if (j < end) {
 #pragma unroll
-                    for (int v = 0; v < R4; ++v) load4<T>((const T*)a.rec, (int64_t)j * R4 + v, rv + 4 * v);
+                    for (int v = 0; v < R4; ++v)
+                        load4<T>((const T*)a.rec, ((int64_t)j - a.rec_base) * R4 + v, rv + 4 * v);
                     T d2 = T(0);
 #pragma unroll
                     for (int q = 0; q < D; ++q) {
@@ -344,11 +347,50 @@ __global__ void __launch_bounds__(GT) k_nw_gather(GatherArgs a)
 }
 
 template <typename T, int D, int KER>
+__global__ void __launch_bounds__(GT) k_nw_gather(GatherArgs a)
+{
+    gather_tile<T, D, KER>(a, (int)blockIdx.x * Tile<D>::X, (int)blockIdx.y * Tile<D>::Y, (int)blockIdx.z * Tile<D>::Z);
+}
+
+// Batched clouds of one group: persistent CTAs take tiles from the group's
+// tile table in order through an atomic counter; each tile is computed as by
+// k_nw_gather, so the result does not depend on which CTA takes it.
+template <int D, int KER>
+__global__ void __launch_bounds__(GT) k_batch_gather(BatchDev b, int group, DevStatus* st)
+{
+    __shared__ int s_tile;
+    const BatchTile* tiles = b.tiles[group];
+    const int nt = b.n_tiles[group];
+    const int64_t rec_base = b.bin_start[b.group_cells[group]];
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(&b.tile_counter[group], 1u);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= nt) break;
+        const BatchTile bt = tiles[t];
+        const BatchCloud& c = b.clouds[bt.cloud];
+        GatherArgs a{};
+        a.rec = b.rec[group];
+        a.rec_base = rec_base;
+        a.bin_start = b.bin_start + c.cell_off;
+        a.ext_max = b.ext_max + bt.cloud;
+        a.N = c.N;
+        a.per_cell = c.per_cell;
+        a.s_mass = c.s_mass;
+        a.s_mom = c.s_mom;
+        a.dsum = c.dsum;
+        a.status = st;
+        gather_tile<float, D, KER>(a, bt.x0, bt.y0, bt.z0);
+    }
+}
+
+template <typename T, int D, int KER>
 cudaError_t launch_gather_t(const GatherArgs& a, cudaStream_t s)
 {
     constexpr int RV = record_values(D, KER);
     const size_t smem = (size_t)CAP * RV * sizeof(T);
-    auto fn = k_nw_gather<T, D, KER>;
+    auto fn = k_nw_gather<T, D, KER>;   // tiles of one mesh
     static bool attr_set = false;   // set once, before any stream capture that uses it
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -499,6 +541,51 @@ cudaError_t launch_psicell(const fla_cloud& cl, const fla_mesh& m, double window
                                                       (double*)out.s_mass_dev, (double*)out.s_mom_dev);
     }
     return cudaGetLastError();
+}
+
+namespace {
+template <int D, int KER>
+cudaError_t launch_batch_gather_t(const BatchDev& b, int group, int ctas, DevStatus* st, cudaStream_t s)
+{
+    constexpr int RV = record_values(D, KER);
+    const size_t smem = (size_t)CAP * RV * sizeof(float);
+    auto fn = k_batch_gather<D, KER>;   // shared-memory attribute set by batch_prepare_gathers
+    cudaError_t e = cudaMemsetAsync(b.tile_counter + group, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    fn<<<ctas, GT, smem, s>>>(b, group, st);
+    return cudaGetLastError();
+}
+}  // namespace
+
+template <int D, int KER>
+cudaError_t prepare_gather_t()
+{
+    constexpr int RV = record_values(D, KER);
+    return cudaFuncSetAttribute(k_batch_gather<D, KER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)((size_t)CAP * RV * sizeof(float)));
+}
+
+// Shared-memory limits of the batched gathers (and their modules loaded), set
+// once when a plan is created, before any launch or capture.
+cudaError_t batch_prepare_gathers()
+{
+    cudaError_t e = prepare_gather_t<2, FLA_KERNEL_ISO>();
+    if (e == cudaSuccess) e = prepare_gather_t<2, FLA_KERNEL_ANISO>();
+    if (e == cudaSuccess) e = prepare_gather_t<3, FLA_KERNEL_ISO>();
+    if (e == cudaSuccess) e = prepare_gather_t<3, FLA_KERNEL_ANISO>();
+    return e;
+}
+
+cudaError_t launch_batch_gather(const BatchDev& b, int group, int ctas, DevStatus* st, cudaStream_t s)
+{
+    if (b.n_tiles[group] == 0) return cudaSuccess;
+    if (ctas > b.n_tiles[group]) ctas = b.n_tiles[group];
+    switch (group) {
+    case 0: return launch_batch_gather_t<2, FLA_KERNEL_ISO>(b, group, ctas, st, s);
+    case 1: return launch_batch_gather_t<2, FLA_KERNEL_ANISO>(b, group, ctas, st, s);
+    case 2: return launch_batch_gather_t<3, FLA_KERNEL_ISO>(b, group, ctas, st, s);
+    default: return launch_batch_gather_t<3, FLA_KERNEL_ANISO>(b, group, ctas, st, s);
+    }
 }
 
 }  // namespace fla

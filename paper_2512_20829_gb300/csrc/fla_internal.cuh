@@ -95,6 +95,30 @@ __host__ __device__ constexpr int record_values(int dim, int kernel)
 }
 
 // Device status block layout (matches fla_device_status).
+// Cell key of droplet i (plane 0 holds the position): floor(x N) per axis in
+// the cloud's precision, clamped to N - 1, x fastest; false when the droplet
+// is not active or lies outside [0,1]^D.
+template <typename T, int D>
+__device__ __forceinline__ bool cell_key_of(const T* __restrict__ state, const uint32_t* __restrict__ meta, int64_t i,
+                                            int N, uint32_t* key_out)
+{
+    T x[4];
+    load4<T>(state, i, x);
+    bool ok = (meta[i] & FLA_META_ACTIVE) != 0;
+    uint32_t key = 0, mul = 1;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        ok &= (x[a] >= T(0) && x[a] <= T(1));
+        const T s = x[a] * T(N);            // formed in the cloud's precision
+        int c = ok ? (int)floor(s) : 0;
+        c = c > N - 1 ? N - 1 : c;
+        key += (uint32_t)c * mul;
+        mul *= (uint32_t)N;
+    }
+    *key_out = key;
+    return ok;
+}
+
 struct DevStatus {
     unsigned long long nonfinite, deposited, droplet_steps, pairs, fold_steps;
     unsigned int flags, pad;

@@ -19,6 +19,7 @@
 // formed one rounding per operation in a fixed order: this file is compiled
 // without FMA contraction so that the decision is reproducible.
 #include "mlp_tc.cuh"
+#include "batch.cuh"
 
 namespace fla {
 namespace {
@@ -602,6 +603,72 @@ __global__ void __launch_bounds__(kMlpRows, 1) k_learn_backward(RecArgs a, const
     mlp_cta_end(m);
 }
 
+// Batched clouds of one group (single precision): the sorted positions of the
+// group's cells, each record computed as k_records does for its cloud.
+template <int D, int KER>
+__global__ void __launch_bounds__(256) k_batch_records(BatchDev b, int group, DevStatus* st)
+{
+    constexpr int NP = state_planes(FLA_CLOUD_FLA, D);
+    constexpr int RV = record_values(D, KER);
+    const int64_t jb = b.bin_start[b.group_cells[group]], je = b.bin_start[b.group_cells[group + 1]];
+    const int64_t j = jb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    float ext2 = 0.0f;
+    bool bad = false;
+    int k = -1;
+    if (j < je) {
+        const uint32_t g = b.perm[j];
+        k = batch_find(b.drop_pre, b.n_clouds, g);
+        const BatchCloud& c = b.clouds[k];
+        const int64_t i = g - b.drop_pre[k];
+        RecArgs a{};
+        a.h_min = c.h_min;
+        a.h_max = c.h_max;
+        a.p = c.p;
+        a.window_dt = c.window_dt;
+        a.inv_window = (float)(1.0 / c.window_dt);
+        a.room = (float)(c.h_max * c.h_max - (double)D * c.h_min * c.h_min);
+        a.hmin2 = (float)(c.h_min * c.h_min);
+        a.plain = c.plain;
+        a.n = c.n;
+        float sv[NP * 4];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) load4<float>(c.state, p * c.n + i, sv + 4 * p);
+        const uint32_t meta = c.meta[i];
+        const fla_batch* B = c.batches + (meta & FLA_META_BATCH_MASK);
+        double adet;
+        float n;
+        det_and_n<D>(a, sv + 2 * D, meta, i, __ldg(&B->n0), adet, n);
+        float r[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) r[q] = 0.0f;
+        record_f32<D, KER>(a, sv, adet, n, __ldg(&B->h0), 1.0, r, ext2, bad);
+#pragma unroll
+        for (int v = 0; v < RV / 4; ++v) store4<float>((float*)b.rec[group], (j - jb) * (RV / 4) + v, r + 4 * v);
+        if (!(ext2 >= 0.0f) || !isfinite(ext2)) ext2 = 0.0f;
+    }
+    // per-cloud maximum support: one atomic per warp when the warp holds one cloud
+    const int k0 = __shfl_sync(0xffffffffu, k, 0);
+    if (__all_sync(0xffffffffu, k == k0)) {
+        float e = ext2;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e = fmaxf(e, __shfl_xor_sync(0xffffffffu, e, o));
+        if ((threadIdx.x & 31) == 0 && k0 >= 0 && e > 0.0f) atomicMax(b.ext_max + k0, __float_as_uint(e));
+    } else if (k >= 0 && ext2 > 0.0f) {
+        atomicMax(b.ext_max + k, __float_as_uint(ext2));
+    }
+    __shared__ unsigned s_cnt[8], s_bad[8];
+    const unsigned nv = __reduce_add_sync(0xffffffffu, k >= 0 ? 1u : 0u);
+    const unsigned nb = __reduce_add_sync(0xffffffffu, bad ? 1u : 0u);
+    if ((threadIdx.x & 31) == 0) { s_cnt[threadIdx.x >> 5] = nv; s_bad[threadIdx.x >> 5] = nb; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long tc = 0, tb = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { tc += s_cnt[q]; tb += s_bad[q]; }
+        if (tc) atomicAdd(&st->deposited, tc);
+        if (tb) atomicAdd(&st->nonfinite, tb);
+    }
+}
+
 template <typename T, int D, int KER>
 cudaError_t launch_t(const RecArgs& a, cudaStream_t s)
 {
@@ -683,6 +750,20 @@ cudaError_t launch_learn_backward(const fla_cloud& cl, const fla_mesh& m, const 
         e = cudaFuncSetAttribute(k_learn_backward<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLearnSmemBytes);
         if (e != cudaSuccess) return e;
         k_learn_backward<3><<<n_parts, kMlpRows, kLearnSmemBytes, s>>>(a, dldc, partial);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_records(const BatchDev& b, int group, DevStatus* st, cudaStream_t s)
+{
+    const int64_t n = b.group_drops[group];   // upper bound on the group's binned droplets
+    if (n == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    switch (group) {
+    case 0: k_batch_records<2, FLA_KERNEL_ISO><<<blocks, 256, 0, s>>>(b, group, st); break;
+    case 1: k_batch_records<2, FLA_KERNEL_ANISO><<<blocks, 256, 0, s>>>(b, group, st); break;
+    case 2: k_batch_records<3, FLA_KERNEL_ISO><<<blocks, 256, 0, s>>>(b, group, st); break;
+    default: k_batch_records<3, FLA_KERNEL_ANISO><<<blocks, 256, 0, s>>>(b, group, st); break;
     }
     return cudaGetLastError();
 }

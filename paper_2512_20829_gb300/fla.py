@@ -18,7 +18,7 @@ from . import inputs as I
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfla.so")
 
-ABI_VERSION = 4            # FLA_ABI_VERSION of include/fla.h that these structures mirror
+ABI_VERSION = 5            # FLA_ABI_VERSION of include/fla.h that these structures mirror
 F32, F64 = 0, 1
 CLOUD_FLA, CLOUD_LPT = 0, 1
 KERNEL_ISO, KERNEL_ANISO = 0, 1
@@ -33,7 +33,9 @@ EXPORTED = ["fla_abi_version", "fla_status_string", "fla_create", "fla_destroy",
             "fla_carrier_nodes_bytes", "fla_carrier_sample", "fla_batch_deadline", "fla_advance",
             "fla_workspace_size", "fla_cell_bins", "fla_deposit_sources", "psicell_deposit", "fla_sync_status",
             "fla_profile_enable", "fla_profile_read", "fla_phase_name", "fla_fold_bytes", "fla_mlp_pack",
-            "fla_mlp_forward", "fla_learn_workspace_size", "fla_learn_grad", "fla_adam_step"]
+            "fla_mlp_forward", "fla_learn_workspace_size", "fla_learn_grad", "fla_adam_step",
+            "fla_batch_workspace_size", "fla_batch_create", "fla_batch_run", "fla_batch_set_step",
+            "fla_batch_tuning", "fla_batch_set_tuning", "fla_batch_destroy"]
 MLP_FEATURES, MLP_HIDDEN, MLP_PARAMS, MLP_PACKED_BYTES = 6, 64, 8833, 19472
 PREC_MIXED, PREC_PLAIN = 0, 1
 TAU_FOLD = 1e-2
@@ -74,6 +76,11 @@ class Sources(C.Structure):
 
 class PsicellOut(C.Structure):
     _fields_ = [("counts_dev", C.c_void_p), ("s_mass_dev", C.c_void_p), ("s_mom_dev", C.c_void_p)]
+
+
+class BatchItem(C.Structure):
+    _fields_ = [("cloud", Cloud), ("mesh", Mesh), ("carrier", CarrierDesc), ("nodes_dev", C.c_void_p),
+                ("cfg", DepositCfg), ("out", Sources)]
 
 
 class DeviceStatus(C.Structure):
@@ -127,6 +134,14 @@ def lib() -> C.CDLL:
         L.fla_learn_grad.argtypes = [v, P(Cloud), P(Mesh), P(DepositCfg), v, i64, v, P(Sources), v, v, v,
                                      C.c_size_t, v, C.c_size_t, v]
         L.fla_adam_step.argtypes = [v, v, v, v, v, i64, C.c_float, C.c_float, C.c_float, C.c_float, i32, v]
+        L.fla_batch_workspace_size.argtypes = [P(BatchItem), i32, P(C.c_size_t)]
+        L.fla_batch_create.argtypes = [v, P(BatchItem), i32, d, i32, i32, v, C.c_size_t, P(v)]
+        L.fla_batch_run.argtypes = [v, v, i32, v]
+        L.fla_batch_set_step.argtypes = [v, i32, v]
+        L.fla_batch_tuning.argtypes = [v, P(i32), P(i32), P(i32), P(i32)]
+        L.fla_batch_set_tuning.argtypes = [v, i32, i32, i32]
+        L.fla_batch_destroy.argtypes = [v]
+        L.fla_batch_destroy.restype = None
         if L.fla_abi_version() != ABI_VERSION:
             raise FlaError(f"{LIB_PATH} has ABI version {L.fla_abi_version()}, the binding expects "
                            f"{ABI_VERSION}: rebuild it with __graft_entry__.build()")
@@ -627,3 +642,80 @@ class Simulation:
         while self.step < total:
             last = self.step + self.wl.window >= total
             self.window(deposit=deposit_every or last, with_psicell=deposit_every or last, stream=stream)
+
+
+class Batch:
+    """Many single-precision FLA clouds (one Workload each, same dt and window)
+    advanced and deposited together by the batched launches of fla_batch_run."""
+
+    def __init__(self, ctx: "Context", workloads, device="cuda", step0: int = 0):
+        torch = _torch()
+        self.ctx, self.workloads = ctx, list(workloads)
+        wl0 = self.workloads[0]
+        self.dt, self.window = wl0.dt, wl0.window
+        self.clouds, self.meshes, self.nodes, self.outs, self.cfgs = [], [], [], [], []
+        items = (BatchItem * len(self.workloads))()
+        for k, wl in enumerate(self.workloads):
+            assert wl.dt == self.dt and wl.window == self.window
+            m = mesh(wl.dim, wl.n_cells_axis)
+            c = DeviceCloud.from_seeds(wl.fla, wl.dim, wl.delta, wl.dt, F32, device)
+            nodes = nodes_buffer(m, F32, device)
+            out = SourceFields(m, F32, device)
+            cfg = deposit_cfg(wl.kernel, wl.h_min, wl.h_max, wl.window * wl.dt, wl.p)
+            items[k].cloud = c.struct()
+            items[k].mesh = m
+            items[k].carrier = carrier_desc(wl.carrier)
+            items[k].nodes_dev = nodes.data_ptr()
+            items[k].cfg = cfg
+            items[k].out = out.struct()
+            self.clouds.append(c)
+            self.meshes.append(m)
+            self.nodes.append(nodes)
+            self.outs.append(out)
+            self.cfgs.append(cfg)
+        self._items = items
+        nb = C.c_size_t()
+        check(lib().fla_batch_workspace_size(items, len(self.workloads), C.byref(nb)), "fla_batch_workspace_size")
+        self.ws = aligned_ws(torch.empty(nb.value + 256, dtype=torch.uint8, device=device))
+        self.pristine = [(c.state.clone(), c.meta.clone()) for c in self.clouds]
+        torch.cuda.synchronize()
+        h = C.c_void_p()
+        check(lib().fla_batch_create(ctx.handle, items, len(self.workloads), float(self.dt), int(self.window),
+                                     int(step0), _ptr(self.ws), self.ws.numel(), C.byref(h)), "fla_batch_create")
+        self.handle = h
+        self.n_droplets = sum(c.n for c in self.clouds)
+        self.n_cells = sum(m.n ** m.dim for m in self.meshes)
+
+    def run(self, n_windows: int, stream=None):
+        check(lib().fla_batch_run(self.ctx.handle, self.handle, int(n_windows), _stream_ptr(stream)), "fla_batch_run")
+
+    def set_step(self, step: int, stream=None):
+        check(lib().fla_batch_set_step(self.handle, int(step), _stream_ptr(stream)), "fla_batch_set_step")
+
+    def reset(self, stream=None):
+        """Seeds back in place and the device step at 0."""
+        for c, (st, me) in zip(self.clouds, self.pristine):
+            c.state.copy_(st)
+            c.meta.copy_(me)
+        self.set_step(0, stream)
+
+    def tuning(self) -> dict:
+        a, g, o, n = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        rc = lib().fla_batch_tuning(self.handle, C.byref(a), C.byref(g), C.byref(o), C.byref(n))
+        return {"tuned": rc == 0, "advance_threads": a.value, "gather_ctas_per_sm": g.value,
+                "tile_order": ["natural", "interleaved"][o.value], "launches_per_window": n.value}
+
+    def set_tuning(self, advance_threads: int, gather_ctas_per_sm: int, tile_order: int):
+        check(lib().fla_batch_set_tuning(self.handle, int(advance_threads), int(gather_ctas_per_sm), int(tile_order)),
+              "fla_batch_set_tuning")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().fla_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -293,3 +293,42 @@ def synthetic_state(dim: int, n: int, n_cells_axis: int, seed: int, *, band=(0.3
     return CloudState(dim=dim, x=x.astype(np.float32), v=v.astype(np.float32), J=J.astype(np.float32),
                       W=W.astype(np.float32), acc=acc.astype(np.float32), status=status, batch=batch,
                       n0=n0, h0=h0)
+
+
+def batch_clouds(seed: int = 4, n_clouds: int = 64, nsteps: int = 100, n_min: float = 1e3, n_max: float = 5e5,
+                 meshes2=(32, 64, 128, 256), meshes3=(32, 64)) -> list[Workload]:
+    """Many clouds of uneven size and resolution for the batched path: sizes
+    log-uniform in [n_min, n_max], half 2D (meshes ``meshes2``, Taylor-Green or
+    jet + vortices, spherical kernel, h_max = 4 dx) and half 3D (meshes
+    ``meshes3``, ABC + round jet, J-scaled kernel, h_max = 2 dx).  Each cloud
+    is one release at step 0 of seeds uniform in a random box, Stokes number
+    U[0.2, 2], delta = -0.2, h0 = (box volume / seeds)^(1/dim), dt = 1e-3,
+    windows of 10 steps."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_clouds):
+        dim = 2 if k % 2 == 0 else 3
+        n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        N = int(rng.choice(meshes2 if dim == 2 else meshes3))
+        lo = rng.uniform(0.1, 0.5, dim)
+        size = np.minimum(rng.uniform(0.2, 0.4, dim), 0.9 - lo)
+        x0 = lo + size * rng.uniform(0.0, 1.0, (n, dim))
+        if dim == 2:
+            if rng.uniform() < 0.5:
+                car = Carrier(kind=CARRIER_TAYLOR_GREEN_2D, dim=2)
+            else:
+                car = Carrier(kind=CARRIER_JET_VORTEX_2D, dim=2, vortices=_jet_vortices(rng, 8, 0.05),
+                              jet_width=0.05, steady=False)
+            kernel, hmax = KERNEL_ISO, 4.0
+        else:
+            car = Carrier(kind=CARRIER_ABC_JET_3D, dim=3)
+            kernel, hmax = KERNEL_ANISO, 2.0
+        St0 = rng.uniform(0.2, 2.0, 1)
+        h0 = float(np.prod(size) / n) ** (1.0 / dim)
+        cl = Cloud(kind=CLOUD_FLA, x0=x0, batch=np.zeros(n, np.int32), step_start=np.zeros(1, np.int32), St0=St0,
+                   n0=np.ones(1), h0=np.array([h0]))
+        dx = 1.0 / N
+        out.append(Workload(name=f"batch{seed}_{k}_{dim}d_{N}_{n}", dim=dim, n_cells_axis=N, dt=1e-3, nsteps=nsteps,
+                            window=10, delta=-0.2, carrier=car, fla=cl, lpt=None, kernel=kernel, h_min=0.5 * dx,
+                            h_max=hmax * dx))
+    return out
