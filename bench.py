@@ -92,6 +92,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-variants", action="store_true", help="skip the other precision forms")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-clouds leg")
+    ap.add_argument("--form", choices=["mixed", "plain", "fold", "learned"], default="mixed",
+                    help="precision form of the headline path (the default is the mixed form)")
     ap.add_argument("--profile-only", action="store_true",
                     help="one eager run of the whole path, nothing else (for external profilers)")
     return ap.parse_args()
@@ -357,7 +359,12 @@ def run_ours(args):
     cells = wl.n_cells
     deposits = wl.nsteps // wl.window
 
-    path = JetPath(ctx, wl, fla, with_fla=True, dtype=dtype)
+    form_mlp = None
+    if args.form == "learned":
+        form_mlp = fla.LearnedCorrection(ctx, fla.init_mlp_params(0, 0.5, zero_last=True))
+    path = JetPath(ctx, wl, fla, with_fla=True, dtype=dtype,
+                   precision=fla.PREC_PLAIN if args.form == "plain" else fla.PREC_MIXED,
+                   fold_guard=args.form == "fold", mlp=form_mlp)
     if args.profile_only:
         # one eager run of the whole path (no graph), for external profilers
         path.reset()
@@ -493,7 +500,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (f64 det J)" if dtype == fla.F32 else "f64",
             "data": "synthetic (seeded, " + args.workload + ")",
-            "config": {"workload": desc, "global_batch": world * wl.fla.n, "cells": cells,
+            "config": {"workload": desc, "form": args.form, "global_batch": world * wl.fla.n, "cells": cells,
                        "deposits_per_step": deposits, "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"replicas x{world} (independent clouds, no collective)"},
             "droplet_steps_per_s": world * droplet_steps_per_run * args.steps / (total_ms * 1e-3),

@@ -15,12 +15,20 @@ struct CarrierArgs {
     double U[3], A[9], xref[3];
     double vort[FLA_MAX_VORTICES][5];  // centre x at the sampling time (wrapped), yc, 1/rc^2, c/rc^2, c/rc^4
     double jet_width, abc[3], jet_amp, jet_radius;
+    // the same values rounded to single precision once, for the single-precision
+    // kernels (a conversion from double per node would run on the FP64 pipe)
+    float Uf[3], Af[9], xreff[3];
+    float vortf[FLA_MAX_VORTICES][5];
+    float jet_width_f, abcf[3], jet_amp_f, jet_radius_f;
 };
+
+// A carrier constant in the kernel's precision.
+template <typename T> __device__ __forceinline__ T cv(double d, float f);
+template <> __device__ __forceinline__ float cv<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double cv<double>(double d, float) { return d; }
 
 __device__ __forceinline__ float m_exp(float x) { return expf(x); }
 __device__ __forceinline__ double m_exp(double x) { return exp(x); }
-__device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
-__device__ __forceinline__ double m_expm1(double x) { return expm1(x); }
 __device__ __forceinline__ float m_sinpi(float x) { return sinpif(x); }
 __device__ __forceinline__ double m_sinpi(double x) { return sinpi(x); }
 __device__ __forceinline__ float m_cospi(float x) { return cospif(x); }
@@ -91,14 +99,14 @@ __device__ void eval_carrier(const CarrierArgs& p, const T* x, T* u, T* G)
     for (int i = 0; i < D * D; ++i) G[i] = T(0);
     switch (p.kind) {
     case FLA_CARRIER_UNIFORM:
-        for (int i = 0; i < D; ++i) u[i] = T(p.U[i]);
+        for (int i = 0; i < D; ++i) u[i] = cv<T>(p.U[i], p.Uf[i]);
         break;
     case FLA_CARRIER_LINEAR:
         for (int i = 0; i < D; ++i) {
-            T s = T(p.U[i]);
+            T s = cv<T>(p.U[i], p.Uf[i]);
             for (int j = 0; j < D; ++j) {
-                s += T(p.A[3 * i + j]) * (x[j] - T(p.xref[j]));
-                G[i * D + j] = T(p.A[3 * i + j]);
+                s += cv<T>(p.A[3 * i + j], p.Af[3 * i + j]) * (x[j] - cv<T>(p.xref[j], p.xreff[j]));
+                G[i * D + j] = cv<T>(p.A[3 * i + j], p.Af[3 * i + j]);
             }
             u[i] = s;
         }
@@ -118,14 +126,15 @@ __device__ void eval_carrier(const CarrierArgs& p, const T* x, T* u, T* G)
         break;
     case FLA_CARRIER_JETVORT2:
         if (D == 2) {
-            const T w = T(p.jet_width);
+            const T w = cv<T>(p.jet_width, p.jet_width_f);
             const T eta = (x[1] - T(0.5)) / w;
             const T uj = m_exp(-eta * eta);
             u[0] = uj;
             G[1] = T(-2) * eta / w * uj;
             for (int k = 0; k < p.n_vortex; ++k) {
-                const T xc = T(p.vort[k][0]), yc = T(p.vort[k][1]);
-                const T inv_a = T(p.vort[k][2]), ca = T(p.vort[k][3]), ca2 = T(p.vort[k][4]);
+                const T xc = cv<T>(p.vort[k][0], p.vortf[k][0]), yc = cv<T>(p.vort[k][1], p.vortf[k][1]);
+                const T inv_a = cv<T>(p.vort[k][2], p.vortf[k][2]), ca = cv<T>(p.vort[k][3], p.vortf[k][3]);
+                const T ca2 = cv<T>(p.vort[k][4], p.vortf[k][4]);
                 for (int img = -1; img <= 1; ++img)   // periodic images along x
                     lamb_oseen<T>(inv_a, ca, ca2, xc + T(img), yc, x[0], x[1], u, G);
             }
@@ -133,7 +142,7 @@ __device__ void eval_carrier(const CarrierArgs& p, const T* x, T* u, T* G)
         break;
     case FLA_CARRIER_ABCJET3:
         if (D == 3) {
-            const T A = T(p.abc[0]), B = T(p.abc[1]), C = T(p.abc[2]);
+            const T A = cv<T>(p.abc[0], p.abcf[0]), B = cv<T>(p.abc[1], p.abcf[1]), C = cv<T>(p.abc[2], p.abcf[2]);
             const T k = T(6.28318530717958647692);
             const T sxv = m_sinpi(T(2) * x[0]), cxv = m_cospi(T(2) * x[0]);
             const T syv = m_sinpi(T(2) * x[1]), cyv = m_cospi(T(2) * x[1]);
@@ -148,8 +157,9 @@ __device__ void eval_carrier(const CarrierArgs& p, const T* x, T* u, T* G)
             G[6] = -k * B * sxv;
             G[7] = k * C * cyv;
             const T rx = x[0] - T(0.5), ry = x[1] - T(0.5);
-            const T r2j = T(p.jet_radius) * T(p.jet_radius);
-            const T e = T(p.jet_amp) * m_exp(-(rx * rx + ry * ry) / r2j);
+            const T jr = cv<T>(p.jet_radius, p.jet_radius_f);
+            const T r2j = jr * jr;
+            const T e = cv<T>(p.jet_amp, p.jet_amp_f) * m_exp(-(rx * rx + ry * ry) / r2j);
             u[2] += e;
             G[6] += T(-2) * rx / r2j * e;
             G[7] += T(-2) * ry / r2j * e;
@@ -233,6 +243,17 @@ __host__ __device__ inline CarrierArgs carrier_args(const fla_carrier_desc& c, i
     p.jet_width = c.jet_width;
     p.jet_amp = c.jet_amp;
     p.jet_radius = c.jet_radius;
+    for (int i = 0; i < 3; ++i) {
+        p.Uf[i] = (float)p.U[i];
+        p.xreff[i] = (float)p.xref[i];
+        p.abcf[i] = (float)p.abc[i];
+    }
+    for (int i = 0; i < 9; ++i) p.Af[i] = (float)p.A[i];
+    for (int k = 0; k < FLA_MAX_VORTICES; ++k)
+        for (int q = 0; q < 5; ++q) p.vortf[k][q] = (float)p.vort[k][q];
+    p.jet_width_f = (float)p.jet_width;
+    p.jet_amp_f = (float)p.jet_amp;
+    p.jet_radius_f = (float)p.jet_radius;
     return p;
 }
 

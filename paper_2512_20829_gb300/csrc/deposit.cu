@@ -174,13 +174,18 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty
     }
     bool in_mesh = cc[0] < N && cc[1] < N && (D == 2 || cc[2] < N);
     bool warp_live = w0[0] < N && w0[1] < N && (D == 2 || w0[2] < N);
+    // cell centres (i + 1/2)/N in the kernel's precision: single-precision tiles
+    // need no double-precision division (slow on this GPU)
+    auto centre = [&](int i) -> T {
+        if (sizeof(T) == 4) return T(((float)i + 0.5f) / (float)N);
+        return T(((double)i + 0.5) / (double)N);
+    };
     T xc[3];
     float xcf[3];
 #pragma unroll
     for (int q = 0; q < D; ++q) {
-        const float v = ((float)cc[q] + 0.5f) / (float)N;
-        xc[q] = T(((double)cc[q] + 0.5) / (double)N);
-        xcf[q] = sizeof(T) == 4 ? v : (float)xc[q];
+        xc[q] = centre(cc[q]);
+        xcf[q] = sizeof(T) == 4 ? ((float)cc[q] + 0.5f) / (float)N : (float)xc[q];
     }
     // boxes of cell centres: the CTA tile (staging cull) and the warp sub-tile (flush cull)
     T lo[3], hi[3], wlo[3], whi[3];
@@ -190,10 +195,10 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty
         const int sq = q == 0 ? SX : (q == 1 ? SY : SZ);
         const int last = (t0[q] + tq < N ? t0[q] + tq : N) - 1;
         const int wlast = (w0[q] + sq < N ? w0[q] + sq : N) - 1;
-        lo[q] = T(((double)t0[q] + 0.5) / (double)N);
-        hi[q] = T(((double)last + 0.5) / (double)N);
-        wlo[q] = T(((double)w0[q] + 0.5) / (double)N);
-        whi[q] = T(((double)wlast + 0.5) / (double)N);
+        lo[q] = centre(t0[q]);
+        hi[q] = centre(last);
+        wlo[q] = centre(w0[q]);
+        whi[q] = centre(wlast);
     }
     const float ext2max = __uint_as_float(__ldg(a.ext_max));
     const int R = (int)floorf(sqrtf(ext2max) * (float)N + 0.5f) + 1;
@@ -437,7 +442,8 @@ __global__ void __launch_bounds__(256) k_psi_records(PsiArgs a)
     for (int q = 0; q <= D; ++q) {
         const int o = OA % 4 + q;
         const T v = o < 4 ? v0[o] : v1[o - 4];
-        out[q] = T(w * (double)v * a.inv_window);
+        // single precision stays single: double arithmetic runs on the slow FP64 pipe
+        out[q] = sizeof(T) == 4 ? T((float)w * (float)v * (float)a.inv_window) : T(w * (double)v * a.inv_window);
     }
     store4<T>((T*)a.rec, j, out);
 }

@@ -160,7 +160,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
     for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
+// z sigma(z) with the fast exponential and reciprocal (a few ulp)
+__device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 {

@@ -378,7 +378,9 @@ __device__ __forceinline__ void mlp_features(const float* J, double adet, float 
 }
 
 // Records with the learned correction (single precision, spherical kernel):
-// 128 sorted positions per CTA, the network on the tensor cores.
+// persistent CTAs take tiles of 128 sorted positions (the packed weights are
+// copied and the TMEM columns allocated once per CTA), the network on the
+// tensor cores.
 template <int D>
 __global__ void __launch_bounds__(kMlpRows) k_records_mlp(RecArgs a)
 {
@@ -387,65 +389,77 @@ __global__ void __launch_bounds__(kMlpRows) k_records_mlp(RecArgs a)
     constexpr int RV = record_values(D, FLA_KERNEL_ISO);
     MlpCta m = mlp_cta_layout(smem);
     mlp_cta_begin(m, a.mlp);
-    const int64_t j = blockIdx.x * (int64_t)kMlpRows + threadIdx.x;
     const int64_t nvalid = a.bin_start[a.n_cells];
-    const bool valid = j < nvalid;
-    float sv[NP * 4];
-    float f[kMlpIn] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-    uint32_t i = 0;
-    double adet = 1.0, h0 = 0.0;
-    float n = 0.0f;
-    if (valid) {
-        i = a.perm[j];
+    const int64_t tiles = (nvalid + kMlpRows - 1) / kMlpRows;
+    float ext_max = 0.0f;
+    unsigned n_bad = 0, n_dep = 0;
+    bool all_ok = true;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t j = tile * kMlpRows + threadIdx.x;
+        const bool valid = j < nvalid;
+        float sv[NP * 4];
+        float f[kMlpIn] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        uint32_t i = 0;
+        double adet = 1.0, h0 = 0.0;
+        float n = 0.0f;
+        if (valid) {
+            i = a.perm[j];
 #pragma unroll
-        for (int p = 0; p < NP; ++p) load4<float>((const float*)a.state, p * a.n + i, sv + 4 * p);
-        const uint32_t meta = a.meta[i];
-        const fla_batch* B = a.batches + (meta & FLA_META_BATCH_MASK);
-        const double n0 = __ldg(&B->n0);
-        h0 = __ldg(&B->h0);
-        det_and_n<D>(a, sv + 2 * D, meta, i, n0, adet, n);
-        mlp_features<D>(sv + 2 * D, adet, n, h0, a.dx, f);
-    }
-    bool ok = true;
-    const float c = mlp_cta_forward(m, f, &ok);
-    float ext2 = 0.0f;
-    bool bad = false;
-    if (valid) {
-        const float ct = fminf(fmaxf(c, -2.0f), 2.0f);
-        float r[16];
+            for (int p = 0; p < NP; ++p) load4<float>((const float*)a.state, p * a.n + i, sv + 4 * p);
+            const uint32_t meta = a.meta[i];
+            const fla_batch* B = a.batches + (meta & FLA_META_BATCH_MASK);
+            const double n0 = __ldg(&B->n0);
+            h0 = __ldg(&B->h0);
+            det_and_n<D>(a, sv + 2 * D, meta, i, n0, adet, n);
+            mlp_features<D>(sv + 2 * D, adet, n, h0, a.dx, f);
+        }
+        bool ok = true;
+        const float c = mlp_cta_forward(m, f, &ok);
+        all_ok &= ok;
+        if (valid) {
+            const float ct = fminf(fmaxf(c, -2.0f), 2.0f);
+            float r[16];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) r[q] = 0.0f;
-        bool h_free = false;
-        record_f32<D, FLA_KERNEL_ISO>(a, sv, adet, n, h0, exp((double)ct), r, ext2, bad, &h_free);
+            for (int q = 0; q < 16; ++q) r[q] = 0.0f;
+            bool h_free = false, bad = false;
+            float ext2 = 0.0f;
+            record_f32<D, FLA_KERNEL_ISO>(a, sv, adet, n, h0, exp((double)ct), r, ext2, bad, &h_free);
 #pragma unroll
-        for (int v = 0; v < RV / 4; ++v) store4<float>((float*)a.rec, j * (RV / 4) + v, r + 4 * v);
-        if (!(ext2 >= 0.0f) || !isfinite(ext2)) ext2 = 0.0f;
-        if (a.mlp_out) a.mlp_out[i] = c;
-        if (a.aux) {
-            a.aux[2 * j] = c;
-            a.aux[2 * j + 1] = (h_free && c > -2.0f && c < 2.0f) ? 1.0f : 0.0f;
+            for (int v = 0; v < RV / 4; ++v) store4<float>((float*)a.rec, j * (RV / 4) + v, r + 4 * v);
+            if (ext2 >= 0.0f && isfinite(ext2)) ext_max = fmaxf(ext_max, ext2);
+            n_bad += bad ? 1u : 0u;
+            n_dep += 1u;
+            if (a.mlp_out) a.mlp_out[i] = c;
+            if (a.aux) {
+                a.aux[2 * j] = c;
+                a.aux[2 * j + 1] = (h_free && c > -2.0f && c < 2.0f) ? 1.0f : 0.0f;
+            }
         }
     }
-    if (!ok && threadIdx.x == 0) atomicOr(&a.status->flags, kFlagMlpTimeout);
+    if (!all_ok && threadIdx.x == 0) atomicOr(&a.status->flags, kFlagMlpTimeout);
     __shared__ float s_ext[4];
-    __shared__ unsigned s_bad[4];
-    float e = ext2;
-    unsigned b = bad ? 1u : 0u;
+    __shared__ unsigned s_bad[4], s_dep[4];
+    float e = ext_max;
+    unsigned b = n_bad, dcount = n_dep;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         e = fmaxf(e, __shfl_xor_sync(0xffffffffu, e, o));
         b += __shfl_xor_sync(0xffffffffu, b, o);
+        dcount += __shfl_xor_sync(0xffffffffu, dcount, o);
     }
-    if ((threadIdx.x & 31) == 0) { s_ext[threadIdx.x >> 5] = e; s_bad[threadIdx.x >> 5] = b; }
+    if ((threadIdx.x & 31) == 0) {
+        s_ext[threadIdx.x >> 5] = e;
+        s_bad[threadIdx.x >> 5] = b;
+        s_dep[threadIdx.x >> 5] = dcount;
+    }
     mlp_cta_end(m);   // synchronises the CTA
     if (threadIdx.x == 0) {
         const float mx = fmaxf(fmaxf(s_ext[0], s_ext[1]), fmaxf(s_ext[2], s_ext[3]));
         const unsigned nb = s_bad[0] + s_bad[1] + s_bad[2] + s_bad[3];
-        const int64_t lo = blockIdx.x * (int64_t)kMlpRows;
-        const int64_t cnt = nvalid > lo ? ((nvalid - lo) < kMlpRows ? (nvalid - lo) : kMlpRows) : 0;
+        const unsigned nd = s_dep[0] + s_dep[1] + s_dep[2] + s_dep[3];
         if (mx > 0.0f) atomicMax(a.ext_max, __float_as_uint(mx));
         if (nb) atomicAdd(&a.status->nonfinite, (unsigned long long)nb);
-        if (cnt) atomicAdd(&a.status->deposited, (unsigned long long)cnt);
+        if (nd) atomicAdd(&a.status->deposited, (unsigned long long)nd);
     }
 }
 
@@ -718,7 +732,12 @@ cudaError_t launch_records(const fla_cloud& cl, const fla_mesh& m, const fla_dep
     a.aux = aux;
     if (a.n == 0) return cudaSuccess;
     if (a.mlp) {   // validated by the caller: single precision, spherical kernel
-        const unsigned blocks = (unsigned)((a.n + kMlpRows - 1) / kMlpRows);
+        // persistent: as many CTAs as fit at once (shared memory allows 6 per SM), at most one per tile
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t tiles = (a.n + kMlpRows - 1) / kMlpRows;
+        const unsigned blocks = (unsigned)(tiles < 6LL * sms ? tiles : 6LL * sms);
         if (m.dim == 2) k_records_mlp<2><<<blocks, kMlpRows, kMlpSmemBytes, s>>>(a);
         else k_records_mlp<3><<<blocks, kMlpRows, kMlpSmemBytes, s>>>(a);
         return cudaGetLastError();
