@@ -338,6 +338,23 @@ def roofline_entry(phase_name, prof, peaks, status_pairs, droplet_steps_per_run,
             "traffic": None, "kernel": phase_name}
 
 
+def max_over_ranks(value: float, world: int, device: str = "cuda") -> float:
+    """The largest of the ranks' values (all ranks receive it); world 1 returns value."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(world: int, cells: int, deposits: int, steps: int, total_ms: float) -> float:
+    """Whole-job cells/s: every rank deposits its own replica's cells each window,
+    timed by the slowest rank."""
+    return world * cells * deposits * steps / (total_ms * 1e-3)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -393,14 +410,10 @@ def run_ours(args):
         dist.barrier()
     clocks = sampler.stop()
     st = ctx.sync_status(reset=True)
-    total_ms = float(sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(times)), world)
     ms_per_step = total_ms / args.steps
     droplet_steps_per_run = st.droplet_steps / args.steps
-    value = world * cells * deposits * args.steps / (total_ms * 1e-3)
+    value = weak_value(world, cells, deposits, args.steps, total_ms)
 
     # ---------------- instrumented eager run: per-phase CUDA-event times
     path.reset()
