@@ -448,7 +448,7 @@ int deposit_impl(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, con
         }
     }
     if (use_gather2d(*mesh, cloud->dtype, cfg->kernel)) {
-        PhaseScope ps(ctx, FLA_PHASE_GATHER, s, 4);
+        PhaseScope ps(ctx, FLA_PHASE_GATHER, s, 3);
         const int nt = gather2d_tiles(mesh->n);
         uint32_t* tiles = at<uint32_t>(ws, L.tiles);
         return cuda_status(launch_gather2d(*mesh, *cfg, at<void>(ws, L.rec), bins, ext, tiles, tiles + nt,

@@ -55,36 +55,19 @@ struct PlanArgs {
     uint32_t* tile_items;      // n_tiles + 1
     int N, tiles_x, n_tiles;
     uint32_t budget;           // maximum number of work items (temp buffer size)
+    unsigned int* done;        // CTAs of the plan that have finished (the last one scans; reset by it)
 };
 
-// Candidates of each tile and the number of work items it needs.
-__global__ void __launch_bounds__(256) k_plan2d(PlanArgs a)
-{
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.n_tiles) return;
-    const int N = a.N, R = support_cells(a.ext_max, N);
-    const int tx0 = (t % a.tiles_x) * kTile, ty0 = (t / a.tiles_x) * kTile;
-    const int xlo = max(tx0 - R, 0), xhi = min(tx0 + kTile - 1 + R, N - 1);
-    const int ylo = max(ty0 - R, 0), yhi = min(ty0 + kTile - 1 + R, N - 1);
-    uint32_t cand = 0;
-    for (int y = ylo; y <= yhi; ++y) {
-        const int64_t rb = (int64_t)y * N;
-        cand += __ldg(a.bin_start + rb + xhi + 1) - __ldg(a.bin_start + rb + xlo);
-    }
-    a.tile_cand[t] = cand;
-    a.tile_items[t] = cand ? (cand + kChunk - 1) / kChunk : 0;
-}
-
-// Exclusive scan of the per-tile item counts (one block); if the total exceeds
+// Exclusive scan of the per-tile item counts by one CTA; if the total exceeds
 // the budget, every non-empty tile gets a single item instead.
-__global__ void __launch_bounds__(1024) k_scan_items(PlanArgs a)
+__device__ void scan_items(const PlanArgs& a)
 {
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_total;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
     for (int pass = 0; pass < 2; ++pass) {
         uint32_t running = 0;
-        for (int base = 0; base < a.n_tiles; base += 1024) {
+        for (int base = 0; base < a.n_tiles; base += blockDim.x) {
             const int t = base + tid;
             uint32_t v = 0;
             if (t < a.n_tiles) v = pass == 0 ? a.tile_items[t] : (a.tile_cand[t] ? 1u : 0u);
@@ -97,18 +80,18 @@ __global__ void __launch_bounds__(1024) k_scan_items(PlanArgs a)
             if (lane == 31) s_warp[w] = x;
             __syncthreads();
             if (w == 0) {
-                uint32_t s = s_warp[lane];
+                uint32_t sw = lane < nw ? s_warp[lane] : 0u;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
-                    if (lane >= o) s += y;
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, sw, o);
+                    if (lane >= o) sw += y;
                 }
-                s_warp[lane] = s;
+                if (lane < nw) s_warp[lane] = sw;
             }
             __syncthreads();
             const uint32_t excl = running + (w > 0 ? s_warp[w - 1] : 0) + x - v;
             if (t < a.n_tiles) a.tile_items[t] = excl;
-            running += s_warp[31];
+            running += s_warp[nw - 1];
             __syncthreads();
         }
         if (tid == 0) {
@@ -118,6 +101,41 @@ __global__ void __launch_bounds__(1024) k_scan_items(PlanArgs a)
         __syncthreads();
         if (pass == 0 && s_total <= a.budget) break;
     }
+}
+
+// Candidates of each tile (one warp per tile, lanes over the neighbourhood
+// rows) and the number of work items it needs; the last CTA to finish scans
+// the item counts into item offsets.
+__global__ void __launch_bounds__(256) k_plan2d(PlanArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int t = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (t < a.n_tiles) {
+        const int N = a.N, R = support_cells(a.ext_max, N);
+        const int tx0 = (t % a.tiles_x) * kTile, ty0 = (t / a.tiles_x) * kTile;
+        const int xlo = max(tx0 - R, 0), xhi = min(tx0 + kTile - 1 + R, N - 1);
+        const int ylo = max(ty0 - R, 0), yhi = min(ty0 + kTile - 1 + R, N - 1);
+        uint32_t cand = 0;
+        for (int y = ylo + lane; y <= yhi; y += 32) {
+            const int64_t rb = (int64_t)y * N;
+            cand += __ldg(a.bin_start + rb + xhi + 1) - __ldg(a.bin_start + rb + xlo);
+        }
+        cand = __reduce_add_sync(0xffffffffu, cand);
+        if (lane == 0) {
+            a.tile_cand[t] = cand;
+            a.tile_items[t] = cand ? (cand + kChunk - 1) / kChunk : 0;
+        }
+    }
+    // the last CTA to finish does the scan
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(a.done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    scan_items(a);
+    if (threadIdx.x == 0) *a.done = 0u;
 }
 
 struct G2Args {
@@ -435,10 +453,10 @@ cudaError_t launch_gather2d(const fla_mesh& m, const fla_deposit_cfg& cfg, const
     const int N = m.n;
     const int tiles_x = (N + kTile - 1) / kTile;
     const int n_tiles = tiles_x * tiles_x;
-    PlanArgs p{bin_start, ext_max, tile_cand, tile_items, N, tiles_x, n_tiles, budget};
-    k_plan2d<<<(n_tiles + 255) / 256, 256, 0, s>>>(p);
-    k_scan_items<<<1, 1024, 0, s>>>(p);
-    cudaError_t e = cudaMemsetAsync(counter, 0, 4, s);
+    PlanArgs p{bin_start, ext_max, tile_cand, tile_items, N, tiles_x, n_tiles, budget, counter + 1};
+    cudaError_t e = cudaMemsetAsync(counter, 0, 8, s);   // the gather's unit counter and the plan's CTA counter
+    if (e != cudaSuccess) return e;
+    k_plan2d<<<(unsigned)((n_tiles * 32 + 255) / 256), 256, 0, s>>>(p);
     if (e != cudaSuccess) return e;
     G2Args g{};
     g.rec = (const float4*)rec;
