@@ -136,3 +136,54 @@ def test_entry_points_reject_bad_arguments_before_launching(lib):
     assert lib.psicell_deposit(fake_ctx, C.byref(cl), C.byref(m), 0.01, 0, C.byref(po), null, 0, null) == -1
     desc = fla.carrier_desc(__import__("paper_2512_20829_gb300.inputs", fromlist=["x"]).Carrier(kind=2, dim=3))
     assert lib.fla_carrier_sample(fake_ctx, C.byref(desc), C.byref(fla.mesh(3, 8)), 0.0, 0, C.c_void_p(256), null) == -1
+
+
+def test_fold_array_sizes(lib):
+    # J and W in planes of 4 doubles, then the hand-over list (n u32) and its counter, 16-byte aligned
+    assert lib.fla_fold_bytes(2, 1000) == 2 * 1000 * 32 + 4000 + 16
+    assert lib.fla_fold_bytes(3, 1000) == 5 * 1000 * 32 + 4000 + 16
+    assert lib.fla_fold_bytes(3, 3) == 5 * 3 * 32 + 16 + 16
+    assert lib.fla_fold_bytes(4, 10) == 0 and lib.fla_fold_bytes(2, -1) == 0
+
+
+def _batch_item(dim=2, N=16, n=100, kernel=fla.KERNEL_ISO, dtype=fla.F32):
+    it = fla.BatchItem()
+    it.cloud.kind, it.cloud.dim, it.cloud.dtype, it.cloud.n_batches, it.cloud.n = fla.CLOUD_FLA, dim, dtype, 1, n
+    # non-null, aligned stand-in addresses: the size query reads no memory
+    it.cloud.state_dev = it.cloud.meta_dev = it.cloud.batches_dev = 1 << 20
+    it.mesh = fla.mesh(dim, N)
+    it.carrier.kind, it.carrier.dim = 2 if dim == 2 else 4, dim
+    it.nodes_dev = 1 << 20
+    it.cfg = fla.deposit_cfg(kernel, 0.5 / N, 2.0 / N, 0.01)
+    it.out.s_mass_dev = it.out.s_mom_dev = 1 << 20
+    return it
+
+
+def test_batch_workspace_size_and_argument_checks(lib):
+    items = (fla.BatchItem * 3)(_batch_item(2, 16, 100), _batch_item(3, 8, 50, fla.KERNEL_ANISO),
+                                _batch_item(2, 32, 1000))
+    nb = C.c_size_t()
+    assert lib.fla_batch_workspace_size(items, 3, C.byref(nb)) == 0
+    base = nb.value
+    # the workspace grows with the droplets and the cells
+    items[2] = _batch_item(2, 32, 5000)
+    assert lib.fla_batch_workspace_size(items, 3, C.byref(nb)) == 0 and nb.value > base
+    items[2] = _batch_item(2, 64, 1000)
+    assert lib.fla_batch_workspace_size(items, 3, C.byref(nb)) == 0 and nb.value > base
+    # rejected items
+    bad = _batch_item(2, 16, 100, dtype=fla.F64)
+    assert lib.fla_batch_workspace_size((fla.BatchItem * 1)(bad), 1, C.byref(nb)) == -1
+    bad = _batch_item(2, 16, 100)
+    bad.mesh = fla.mesh(3, 16)                      # cloud and mesh dimensions differ
+    assert lib.fla_batch_workspace_size((fla.BatchItem * 1)(bad), 1, C.byref(nb)) == -1
+    bad = _batch_item(2, 16, 100)
+    bad.nodes_dev = None
+    assert lib.fla_batch_workspace_size((fla.BatchItem * 1)(bad), 1, C.byref(nb)) == -1
+    bad = _batch_item(2, 16, 100)
+    bad.cfg.mlp_dev = 1 << 20                       # no learned correction in a batch
+    assert lib.fla_batch_workspace_size((fla.BatchItem * 1)(bad), 1, C.byref(nb)) == -6
+    bad = _batch_item(2, 16, 100)
+    bad.cfg.h_max = 8.0                             # support wider than 192 cells
+    assert lib.fla_batch_workspace_size((fla.BatchItem * 1)(bad), 1, C.byref(nb)) == -6
+    assert lib.fla_batch_workspace_size(items, 0, C.byref(nb)) == -1
+    assert lib.fla_batch_workspace_size(None, 1, C.byref(nb)) == -1
