@@ -94,6 +94,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-clouds leg")
     ap.add_argument("--form", choices=["mixed", "plain", "fold", "learned"], default="mixed",
                     help="precision form of the headline path (the default is the mixed form)")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="one run of the 64-cloud batch with plain launches (no graph), for external profilers")
     ap.add_argument("--profile-only", action="store_true",
                     help="one eager run of the whole path, nothing else (for external profilers)")
     return ap.parse_args()
@@ -382,6 +384,14 @@ def run_ours(args):
     path = JetPath(ctx, wl, fla, with_fla=True, dtype=dtype,
                    precision=fla.PREC_PLAIN if args.form == "plain" else fla.PREC_MIXED,
                    fold_guard=args.form == "fold", mlp=form_mlp)
+    if args.profile_batch:
+        b = fla.Batch(ctx, I.batch_clouds())
+        b.set_tuning(128, 4, 1)
+        b.run(b.workloads[0].nsteps // b.workloads[0].window)   # legacy stream: plain launches
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile_batch": True, "launches_per_window": b.tuning()["launches_per_window"]}))
+        return
     if args.profile_only:
         # one eager run of the whole path (no graph), for external profilers
         path.reset()
