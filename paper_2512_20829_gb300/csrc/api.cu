@@ -77,6 +77,10 @@ WsLayout layout(const fla_mesh& m, int dtype, int kernel, int64_t n)
         o += up256((size_t)(2 * gather2d_tiles(m.n) + 1) * 4);
         L.temp = o;
         o += up256(gather2d_temp_bytes(m.n, n));
+    } else {   // the tile gather's work items
+        o += up256((size_t)(2 * nw_tiles(m.dim, m.n) + 1) * 4);
+        L.temp = o;
+        o += up256(nw_temp_bytes(m.dim, m.n, n, T));
     }
     L.total = o;
     return L;
@@ -455,9 +459,17 @@ int deposit_impl(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, con
                                            ext + 1, at<void>(ws, L.temp), gather2d_item_budget(mesh->n, cloud->n),
                                            *out, (DevStatus*)ctx->status_dev, ctx->num_sms, s));
     }
-    PhaseScope ps(ctx, FLA_PHASE_GATHER, s, 1);
-    return cuda_status(launch_nw_gather(*cloud, *mesh, *cfg, at<void>(ws, L.rec), bins, ext, *out,
-                                        (DevStatus*)ctx->status_dev, s));
+    PhaseScope ps(ctx, FLA_PHASE_GATHER, s, 3);
+    NwWork w{};
+    w.tile_cand = at<uint32_t>(ws, L.tiles);
+    w.tile_items = w.tile_cand + nw_tiles(mesh->dim, mesh->n);
+    w.counter = at<unsigned int>(ws, L.misc + 16);
+    w.done = at<unsigned int>(ws, L.misc + 20);
+    w.cand_total = at<unsigned long long>(ws, L.misc + 24);
+    w.temp = at<void>(ws, L.temp);
+    if (cudaMemsetAsync(w.counter, 0, 16, s) != cudaSuccess) return FLA_ERR_CUDA;
+    return cuda_status(launch_nw_gather(*cloud, *mesh, *cfg, at<void>(ws, L.rec), bins, ext, w, *out,
+                                        (DevStatus*)ctx->status_dev, ctx->num_sms, s));
 }
 
 // Which of the sort's ping-pong buffers holds the sorted order of a cloud of n.

@@ -39,8 +39,8 @@ size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct BatchLayout {
     size_t clouds, drop_pre, node_pre, misc, ext, cargs, tiles[2][kBatchGroups], keys[2], vals[2], counts, totals,
-        bin_start, rec[kBatchGroups], total;
-    int64_t n_total, cells_total, nodes_total, group_drops[kBatchGroups];
+        bin_start, rec[kBatchGroups], tile_cand[kBatchGroups], tile_items[kBatchGroups], cloud_cand, item_temp, total;
+    int64_t n_total, cells_total, nodes_total, group_drops[kBatchGroups], group_items[kBatchGroups];
     int n_tiles[kBatchGroups];
 };
 
@@ -102,6 +102,7 @@ BatchLayout batch_layout(const fla_batch_item* items, int n)
         L.nodes_total += nodes_of_mesh(items[k].mesh);
         L.group_drops[g] += items[k].cloud.n;
         L.n_tiles[g] += tiles_of_mesh(items[k].mesh);
+        L.group_items[g] += nw_item_budget(items[k].mesh.dim, items[k].mesh.n, items[k].cloud.n);
     }
     const size_t nn = (size_t)(L.n_total > 0 ? L.n_total : 1);
     size_t o = 0;
@@ -123,6 +124,15 @@ BatchLayout batch_layout(const fla_batch_item* items, int n)
         L.rec[g] = o;
         o += up256((size_t)L.group_drops[g] * rv * 4);
     }
+    size_t temp = 0;
+    for (int g = 0; g < kBatchGroups; ++g) {
+        L.tile_cand[g] = o; o += up256(4 * (size_t)L.n_tiles[g]);
+        L.tile_items[g] = o; o += up256(4 * ((size_t)L.n_tiles[g] + 1));
+        const int dim = g < 2 ? 2 : 3;
+        temp = std::max(temp, (size_t)L.group_items[g] * (size_t)(dim + 2) * 256 * 4);
+    }
+    L.cloud_cand = o; o += up256(8 * (size_t)n);
+    L.item_temp = o; o += up256(temp);
     L.total = o;
     return L;
 }
@@ -173,7 +183,8 @@ int issue_gathers(fla_ctx* ctx, fla_batch_plan* p, int ctas_per_sm, int order, c
     BatchDev& b = p->dev;
     for (int g = 0; g < kBatchGroups; ++g) b.tiles[g] = p->tiles_order[order][g];
     for (int g = 0; g < kBatchGroups; ++g)
-        if (launch_batch_gather(b, g, ctas_per_sm * p->num_sms, (DevStatus*)ctx->status_dev, s) != cudaSuccess)
+        if (launch_batch_gather(b, g, ctas_per_sm * p->num_sms, (DevStatus*)ctx->status_dev, p->num_sms, s) !=
+            cudaSuccess)
             return FLA_ERR_CUDA;
     return FLA_OK;
 }
@@ -194,7 +205,7 @@ int window_launches(const fla_batch_plan* p)
     if (p->dev.n_total > 0) n += 1 + 3 * sort_passes_n(p->sort_bits, p->dev.n_total) + 1;
     for (int g = 0; g < kBatchGroups; ++g) {
         if (p->dev.group_first[g + 1] > p->dev.group_first[g]) n += 1;
-        if (p->dev.n_tiles[g] > 0) n += 1;
+        if (p->dev.n_tiles[g] > 0) n += 3;   // gather plan, items, combine
     }
     return n;
 }
@@ -213,8 +224,9 @@ struct EventPair {
 
 // Autotuning on the first windows of a run.  Every knob leaves the results
 // unchanged: the advance's block size (droplets are independent), the number
-// of persistent gather CTAs and the order of the tile table (each tile is
-// computed whole by one CTA).  Window w < 3 advances with 64 << w threads per
+// of persistent gather CTAs and the order of the tile table (a tile's work
+// items depend only on its candidates, each is computed whole by one CTA, and
+// the items of a tile are combined in their own order).  Window w < 3 advances with 64 << w threads per
 // block and times it; the first window also times the gathers for each
 // (CTAs per SM, order) pair by repeating them, which rewrites the same
 // outputs.  Returns the windows issued, or -1.
@@ -377,6 +389,7 @@ extern "C" int fla_batch_create(fla_ctx* ctx, const fla_batch_item* items, int32
     int misc[64] = {0};
     misc[0] = step0;
     ok = ok && cudaMemcpy(at<void>(ws, L.misc), misc, sizeof(misc), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemset(at<void>(ws, L.cloud_cand), 0, 8 * (size_t)n_items) == cudaSuccess;
     if (!ok) {
         delete p;
         return FLA_ERR_CUDA;
@@ -390,6 +403,9 @@ extern "C" int fla_batch_create(fla_ctx* ctx, const fla_batch_item* items, int32
     b.node_pre = at<int64_t>(ws, L.node_pre);
     b.step = at<int>(ws, L.misc);
     b.tile_counter = at<unsigned int>(ws, L.misc + 16);
+    b.plan_done = at<unsigned int>(ws, L.misc + 32);
+    b.cloud_cand = at<unsigned long long>(ws, L.cloud_cand);
+    b.item_temp = at<void>(ws, L.item_temp);
     b.ext_max = at<unsigned int>(ws, L.ext);
     b.cargs = at<void>(ws, L.cargs);
     for (int r = 0; r < 2; ++r)
@@ -397,6 +413,8 @@ extern "C" int fla_batch_create(fla_ctx* ctx, const fla_batch_item* items, int32
     for (int g = 0; g < kBatchGroups; ++g) {
         b.tiles[g] = p->tiles_order[0][g];
         b.rec[g] = at<void>(ws, L.rec[g]);
+        b.tile_cand[g] = at<uint32_t>(ws, L.tile_cand[g]);
+        b.tile_items[g] = at<uint32_t>(ws, L.tile_items[g]);
     }
     for (int k = 0; k < 2; ++k) {
         p->sort.keys[k] = at<uint32_t>(ws, L.keys[k]);

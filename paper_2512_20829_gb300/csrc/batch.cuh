@@ -59,6 +59,11 @@ struct BatchDev {
     int64_t group_drops[kBatchGroups];       // droplets of each group's clouds
     const BatchTile* tiles[kBatchGroups];    // gather tiles per group, in the tuned order
     int n_tiles[kBatchGroups];
+    uint32_t* tile_cand[kBatchGroups];       // per tile: candidates (gather plan)
+    uint32_t* tile_items[kBatchGroups];      // per tile: first work item (n_tiles + 1)
+    unsigned long long* cloud_cand;          // per cloud: candidates of its tiles (zero between plans)
+    unsigned int* plan_done;                 // per group: plan CTAs finished
+    void* item_temp;                         // partial sums of the work items (shared by the groups)
 };
 
 // index k with pre[k] <= v < pre[k + 1] (pre ascending, n + 1 entries)
@@ -81,7 +86,7 @@ cudaError_t launch_batch_advance(const BatchDev& b, int dim, int64_t n_dim, int 
                                  int threads, DevStatus* st, cudaStream_t s);
 cudaError_t launch_batch_keys(const BatchDev& b, uint32_t* keys, cudaStream_t s);
 cudaError_t launch_batch_records(const BatchDev& b, int group, DevStatus* st, cudaStream_t s);
-cudaError_t launch_batch_gather(const BatchDev& b, int group, int ctas, DevStatus* st, cudaStream_t s);
+cudaError_t launch_batch_gather(const BatchDev& b, int group, int ctas, DevStatus* st, int num_sms, cudaStream_t s);
 cudaError_t launch_batch_step(const BatchDev& b, int nsteps, cudaStream_t s);
 
 }  // namespace fla

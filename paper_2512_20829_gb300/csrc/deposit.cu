@@ -1,11 +1,13 @@
 // Kernel-regression gather (Eqs. 13 and 16) and PSI-CELL box counting (Eqs. 10-11).
 //
-// Gather: one CTA per tile of cells (16x16 in 2D, 8x8x4 in 3D), one cell per
-// thread, each warp owning a 32-cell sub-tile.  Droplet records are sorted by
+// Gather: tiles of cells (16x16 in 2D, 8x8x4 in 3D), one cell per thread of
+// a CTA, each warp owning a 32-cell sub-tile.  Droplet records are sorted by
 // cell key, so the records of the cells in one mesh row of the tile's
-// neighbourhood are contiguous.  The CTA walks those rows, each thread loads
-// one record, records whose support cannot reach the tile are culled, and the
-// survivors are compacted (order kept) into shared memory.  Each warp then
+// neighbourhood are contiguous; a tile's candidates are those rows' records
+// in row order, cut into work items (below) that persistent CTAs take.  A CTA
+// walks its item's candidates, each thread loads one record, records whose
+// support cannot reach the tile are culled, and the survivors are compacted
+// (order kept) into shared memory.  Each warp then
 // tests 32 staged records at a time against its own sub-tile with one ballot
 // and evaluates only the records that can reach it: truncation test (as a
 // predicate), Gaussian weight 2^(c r^2 + log2(1/h)) with one MUFU ex2 in single
@@ -146,9 +148,49 @@ __device__ __forceinline__ T weight_of(const T* r, const float* xcf, const T* xc
     }
 }
 
-// One CTA tile of cells with origin (tx0, ty0, tz0).
+// Cell of thread tid in the tile with origin t0: warp = sub-tile, lane = cell.
+template <int D>
+__device__ __forceinline__ void tile_cell(int tid, const int t0[3], int w0[3], int cc[3])
+{
+    const int lane = tid & 31, warp = tid >> 5;
+    constexpr int SX = Tile<D>::SX, SY = Tile<D>::SY, SZ = Tile<D>::SZ;
+    if (D == 2) {
+        w0[0] = t0[0] + (warp & 1) * SX; w0[1] = t0[1] + (warp >> 1) * SY; w0[2] = 0;
+        cc[0] = w0[0] + (lane & 7); cc[1] = w0[1] + (lane >> 3); cc[2] = 0;
+    } else {
+        w0[0] = t0[0] + (warp & 1) * SX; w0[1] = t0[1] + ((warp >> 1) & 1) * SY; w0[2] = t0[2] + (warp >> 2) * SZ;
+        cc[0] = w0[0] + (lane & 3); cc[1] = w0[1] + ((lane >> 2) & 3); cc[2] = w0[2] + (lane >> 4);
+    }
+}
+
+// Source terms of one cell from its weight sum Dt and weighted sums Nq (Eq. 13).
+template <typename T, int D>
+__device__ __forceinline__ void write_cell(const GatherArgs& a, const int cc[3], T Dt, const T Nq[4])
+{
+    const int N = a.N;
+    const int64_t cell = cc[0] + (int64_t)N * (cc[1] + (D == 3 ? (int64_t)N * cc[2] : 0));
+    const int64_t nc = D == 2 ? (int64_t)N * N : (int64_t)N * N * N;
+    T scale = T(1);
+    if (a.per_cell) {
+        const double dx = 1.0 / N;
+        scale = T(D == 2 ? dx * dx : dx * dx * dx);
+    }
+    const bool cov = Dt > T(0);
+    ((T*)a.s_mass)[cell] = cov ? -Nq[0] / Dt * scale : T(0);
+#pragma unroll
+    for (int q = 0; q < D; ++q) ((T*)a.s_mom)[q * nc + cell] = cov ? -Nq[1 + q] / Dt * scale : T(0);
+    if (a.dsum) ((T*)a.dsum)[cell] = Dt;
+}
+
+// The candidates [c0, c1) of one CTA tile of cells with origin (tx0, ty0, tz0).
+// The candidates of a tile are the records of the mesh rows within R of it
+// (R from the largest support in the cloud), concatenated in row order (z
+// outer, y inner).  part == nullptr: the tile is one work item and the source
+// terms are written; otherwise the item's D + 2 sums per cell go to part
+// (value-major, GT cells each).
 template <typename T, int D, int KER>
-__device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty0, int tz0)
+__device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty0, int tz0, uint32_t c0, uint32_t c1,
+                                            T* part)
 {
     constexpr int RV = record_values(D, KER);
     constexpr int R4 = RV / 4;
@@ -159,19 +201,14 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty
     T* srec = reinterpret_cast<T*>(smem_raw);
     __shared__ int s_wcount[GT / 32];
     __shared__ int s_count;
+    __shared__ uint32_t s_rbeg[GT], s_rexc[GT];   // a batch of rows: segment start, candidates before it
+    __shared__ uint32_t s_wsum[GT / 32];
 
     const int N = a.N;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int t0[3] = {tx0, ty0, tz0};
-    // warp sub-tile origin and this lane's cell
     int w0[3], cc[3];
-    if (D == 2) {
-        w0[0] = t0[0] + (warp & 1) * SX; w0[1] = t0[1] + (warp >> 1) * SY; w0[2] = 0;
-        cc[0] = w0[0] + (lane & 7); cc[1] = w0[1] + (lane >> 3); cc[2] = 0;
-    } else {
-        w0[0] = t0[0] + (warp & 1) * SX; w0[1] = t0[1] + ((warp >> 1) & 1) * SY; w0[2] = t0[2] + (warp >> 2) * SZ;
-        cc[0] = w0[0] + (lane & 3); cc[1] = w0[1] + ((lane >> 2) & 3); cc[2] = w0[2] + (lane >> 4);
-    }
+    tile_cell<D>(tid, t0, w0, cc);
     bool in_mesh = cc[0] < N && cc[1] < N && (D == 2 || cc[2] < N);
     bool warp_live = w0[0] < N && w0[1] < N && (D == 2 || w0[2] < N);
     // cell centres (i + 1/2)/N in the kernel's precision: single-precision tiles
@@ -217,6 +254,8 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty
         zlo = t0[2] - R < 0 ? 0 : t0[2] - R;
         zhi = t0[2] + TZ - 1 + R > N - 1 ? N - 1 : t0[2] + TZ - 1 + R;
     }
+    const int ny = yhi - ylo + 1;
+    const int nrows = ny * (zhi - zlo + 1);
     __syncthreads();
 
     // Evaluate the staged records for this warp's cells in staging order: 32 records
@@ -272,51 +311,86 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty
         for (int q2 = 0; q2 <= D; ++q2) neumaier(sN[q2], cN[q2], pN[q2]);
     };
 
-    // walk the neighbourhood rows; each row's records are contiguous
-    for (int z = zlo; z <= zhi; ++z) {
-        for (int y = ylo; y <= yhi; ++y) {
+    // Walk the candidates [c0, c1) a batch of GT rows at a time: each thread reads
+    // one row's segment, a CTA scan gives the candidates before each row, and then
+    // GT consecutive candidates at a time are loaded (thread j finds the row of
+    // candidate j by binary search), culled against the tile and staged in order.
+    uint32_t off = 0;   // candidates before the current batch of rows
+    for (int rb = 0; rb < nrows && off < c1; rb += GT) {
+        const int r = rb + tid;
+        uint32_t beg = 0, len = 0;
+        if (r < nrows) {
+            const int y = ylo + r % ny, z = zlo + r / ny;
             const int64_t rowbase = ((int64_t)z * N + y) * N;
-            const uint32_t beg = __ldg(a.bin_start + rowbase + xlo);
-            const uint32_t end = __ldg(a.bin_start + rowbase + xhi + 1);
-            for (uint32_t j0 = beg; j0 < end; j0 += GT) {
-                const uint32_t j = j0 + tid;
-                T rv[16];
-                bool keep = false;
-                if (j < end) {
-#pragma unroll
-                    for (int v = 0; v < R4; ++v)
-                        load4<T>((const T*)a.rec, ((int64_t)j - a.rec_base) * R4 + v, rv + 4 * v);
-                    T d2 = T(0);
-#pragma unroll
-                    for (int q = 0; q < D; ++q) {
-                        const T dl = lo[q] - rv[q], dh = rv[q] - hi[q];
-                        const T dd = dl > T(0) ? dl : (dh > T(0) ? dh : T(0));
-                        d2 += dd * dd;
-                    }
-                    keep = d2 <= rv[EXT] * T(1.0009765625);   // small margin over rounding of the test
-                }
-                const unsigned ballot = __ballot_sync(0xffffffffu, keep);
-                if (lane == 0) s_wcount[warp] = __popc(ballot);
-                __syncthreads();
-                int off = s_count;
-                for (int w2 = 0; w2 < warp; ++w2) off += s_wcount[w2];
-                int total = s_count;
-                for (int w2 = 0; w2 < GT / 32; ++w2) total += s_wcount[w2];
-                if (keep) {
-                    const int pos = off + __popc(ballot & ((1u << lane) - 1u));
-#pragma unroll
-                    for (int v = 0; v < R4; ++v) store4<T>(srec, (int64_t)pos * R4 + v, rv + 4 * v);
-                }
-                __syncthreads();
-                if (total > CAP - GT) {
-                    flush(total);
-                    total = 0;
-                }
-                __syncthreads();
-                if (tid == 0) s_count = total;
-                __syncthreads();
-            }
+            beg = __ldg(a.bin_start + rowbase + xlo);
+            len = __ldg(a.bin_start + rowbase + xhi + 1) - beg;
         }
+        uint32_t x = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += v;
+        }
+        if (lane == 31) s_wsum[warp] = x;
+        __syncthreads();
+        uint32_t wpre = 0, btotal = 0;
+#pragma unroll
+        for (int w2 = 0; w2 < GT / 32; ++w2) {
+            const uint32_t v = s_wsum[w2];
+            wpre += w2 < warp ? v : 0u;
+            btotal += v;
+        }
+        s_rbeg[tid] = beg;
+        s_rexc[tid] = wpre + x - len;
+        __syncthreads();
+        const uint32_t jlo = c0 > off ? c0 - off : 0u;
+        const uint32_t jhi = c1 - off < btotal ? c1 - off : btotal;
+        for (uint32_t j0 = jlo; j0 < jhi; j0 += GT) {
+            const uint32_t j = j0 + tid;
+            T rv[16];
+            bool keep = false;
+            if (j < jhi) {
+                int rl = 0, rh = GT - 1;   // last row with s_rexc <= j
+                while (rl < rh) {
+                    const int mid = (rl + rh + 1) >> 1;
+                    if (s_rexc[mid] <= j) rl = mid;
+                    else rh = mid - 1;
+                }
+                const int64_t pos = (int64_t)(s_rbeg[rl] + (j - s_rexc[rl])) - a.rec_base;
+#pragma unroll
+                for (int v = 0; v < R4; ++v) load4<T>((const T*)a.rec, pos * R4 + v, rv + 4 * v);
+                T d2 = T(0);
+#pragma unroll
+                for (int q = 0; q < D; ++q) {
+                    const T dl = lo[q] - rv[q], dh = rv[q] - hi[q];
+                    const T dd = dl > T(0) ? dl : (dh > T(0) ? dh : T(0));
+                    d2 += dd * dd;
+                }
+                keep = d2 <= rv[EXT] * T(1.0009765625);   // small margin over rounding of the test
+            }
+            const unsigned ballot = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0) s_wcount[warp] = __popc(ballot);
+            __syncthreads();
+            int pos0 = s_count;
+            for (int w2 = 0; w2 < warp; ++w2) pos0 += s_wcount[w2];
+            int total = s_count;
+            for (int w2 = 0; w2 < GT / 32; ++w2) total += s_wcount[w2];
+            if (keep) {
+                const int pos = pos0 + __popc(ballot & ((1u << lane) - 1u));
+#pragma unroll
+                for (int v = 0; v < R4; ++v) store4<T>(srec, (int64_t)pos * R4 + v, rv + 4 * v);
+            }
+            __syncthreads();
+            if (total > CAP - GT) {
+                flush(total);
+                total = 0;
+            }
+            __syncthreads();
+            if (tid == 0) s_count = total;
+            __syncthreads();
+        }
+        off += btotal;
+        __syncthreads();   // the row batch's tables are rewritten next
     }
     const int rem = s_count;
     if (rem > 0) flush(rem);
@@ -335,77 +409,282 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty
     }
 
     if (in_mesh) {
-        const int64_t cell = cc[0] + (int64_t)N * (cc[1] + (D == 3 ? (int64_t)N * cc[2] : 0));
-        const int64_t nc = D == 2 ? (int64_t)N * N : (int64_t)N * N * N;
-        const T Dt = sD + cD;
-        T scale = T(1);
-        if (a.per_cell) {
-            const double dx = 1.0 / N;
-            scale = T(D == 2 ? dx * dx : dx * dx * dx);
-        }
-        const bool cov = Dt > T(0);
-        ((T*)a.s_mass)[cell] = cov ? -(sN[0] + cN[0]) / Dt * scale : T(0);
+        if (part) {
+            part[tid] = sD + cD;
 #pragma unroll
-        for (int q = 0; q < D; ++q) ((T*)a.s_mom)[q * nc + cell] = cov ? -(sN[1 + q] + cN[1 + q]) / Dt * scale : T(0);
-        if (a.dsum) ((T*)a.dsum)[cell] = Dt;
+            for (int q = 0; q <= D; ++q) part[(1 + q) * GT + tid] = sN[q] + cN[q];
+        } else {
+            T Nq[4];
+#pragma unroll
+            for (int q = 0; q <= D; ++q) Nq[q] = sN[q] + cN[q];
+            write_cell<T, D>(a, cc, sD + cD, Nq);
+        }
     }
 }
 
-template <typename T, int D, int KER>
-__global__ void __launch_bounds__(GT) k_nw_gather(GatherArgs a)
+// ------------------------------------------------------------ work items
+//
+// A tile whose candidate list is long (a dense cluster of droplets, or a wide
+// support) would hold one CTA for as long as the rest of the mesh takes.  A
+// plan kernel therefore counts each tile's candidates and cuts the list into
+// work items of about kItemChunk candidates; persistent CTAs take items from
+// a counter, and the items of a tile leave per-cell partial sums that a
+// combine kernel adds in item order (Neumaier-compensated) before dividing.
+// A tile of one item writes its cells directly.  The item budget of a cloud
+// is its tiles plus ceil(16 n / kItemChunk) + 1; when the candidates need
+// more, the cloud's chunk grows so that its items fit.  Item boundaries
+// depend only on the candidate counts, so the result is deterministic and the
+// same for a cloud gathered alone or in a batch.
+
+struct NwItems {
+    // tile source: a batch tile table (clouds != nullptr) or the tile grid of one mesh
+    const BatchTile* tiles;
+    const BatchCloud* clouds;
+    const uint32_t* bin_start;        // batch: bin starts of all clouds (cloud k from cell_off)
+    const unsigned int* ext_max;      // per cloud
+    int N, per_cell, tiles_x, tiles_y;
+    int64_t n_drops;                  // one mesh: droplets (item budget)
+    void* s_mass;
+    void* s_mom;
+    void* dsum;
+    // records
+    const void* rec;
+    const uint32_t* rec_base_at;      // batch: sorted position of rec[0] (device); else 0
+    // plan and items
+    int n_tiles, cloud_lo, cloud_hi;  // tiles; clouds whose totals the plan resets
+    uint32_t* tile_cand;              // n_tiles
+    uint32_t* tile_items;             // n_tiles + 1 (exclusive prefix)
+    unsigned long long* cloud_cand;   // per cloud: candidates of all its tiles (zero between plans)
+    unsigned int* done;               // plan CTAs finished (reset by the last)
+    unsigned int* counter;            // items taken (zeroed before the items kernel)
+    void* temp;                       // item partials
+    DevStatus* status;
+};
+
+struct TileRef {
+    GatherArgs g;
+    int o[3];
+    int cloud;
+    int64_t n;        // droplets of the cloud
+};
+
+template <int D>
+__device__ __forceinline__ TileRef tile_ref(const NwItems& a, int t)
 {
-    gather_tile<T, D, KER>(a, (int)blockIdx.x * Tile<D>::X, (int)blockIdx.y * Tile<D>::Y, (int)blockIdx.z * Tile<D>::Z);
+    TileRef r;
+    r.g.rec = a.rec;
+    r.g.rec_base = a.rec_base_at ? (int64_t)__ldg(a.rec_base_at) : 0;
+    r.g.status = a.status;
+    if (a.clouds) {
+        const BatchTile bt = a.tiles[t];
+        const BatchCloud& c = a.clouds[bt.cloud];
+        r.g.bin_start = a.bin_start + c.cell_off;
+        r.g.ext_max = a.ext_max + bt.cloud;
+        r.g.N = c.N;
+        r.g.per_cell = c.per_cell;
+        r.g.s_mass = c.s_mass;
+        r.g.s_mom = c.s_mom;
+        r.g.dsum = c.dsum;
+        r.o[0] = bt.x0; r.o[1] = bt.y0; r.o[2] = bt.z0;
+        r.cloud = bt.cloud;
+        r.n = c.n;
+    } else {
+        r.g.bin_start = a.bin_start;
+        r.g.ext_max = a.ext_max;
+        r.g.N = a.N;
+        r.g.per_cell = a.per_cell;
+        r.g.s_mass = a.s_mass;
+        r.g.s_mom = a.s_mom;
+        r.g.dsum = a.dsum;
+        r.o[0] = (t % a.tiles_x) * Tile<D>::X;
+        r.o[1] = ((t / a.tiles_x) % a.tiles_y) * Tile<D>::Y;
+        r.o[2] = (t / (a.tiles_x * a.tiles_y)) * Tile<D>::Z;
+        r.cloud = 0;
+        r.n = a.n_drops;
+    }
+    return r;
 }
 
-// Batched clouds of one group: persistent CTAs take tiles from the group's
-// tile table in order through an atomic counter; each tile is computed as by
-// k_nw_gather, so the result does not depend on which CTA takes it.
-template <int D, int KER>
-__global__ void __launch_bounds__(GT) k_batch_gather(BatchDev b, int group, DevStatus* st)
+constexpr uint32_t kItemChunk = 4096;
+
+__host__ __device__ inline int64_t nw_extra_items(int64_t n)
 {
-    __shared__ int s_tile;
-    const BatchTile* tiles = b.tiles[group];
-    const int nt = b.n_tiles[group];
-    const int64_t rec_base = b.bin_start[b.group_cells[group]];
+    return (16 * (n > 0 ? n : 1) + kItemChunk - 1) / kItemChunk + 1;
+}
+
+// Candidates of each tile (one warp per tile, lanes over the neighbourhood
+// rows); the last CTA to finish turns them into item counts and offsets.
+template <int D>
+__global__ void __launch_bounds__(256) k_nw_plan(NwItems a)
+{
+    const int lane = threadIdx.x & 31;
+    const int t = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (t < a.n_tiles) {
+        const TileRef tr = tile_ref<D>(a, t);
+        const int N = tr.g.N;
+        const float ext2max = __uint_as_float(__ldg(tr.g.ext_max));
+        const int R = (int)floorf(sqrtf(ext2max) * (float)N + 0.5f) + 1;
+        const int xlo = max(tr.o[0] - R, 0), xhi = min(tr.o[0] + Tile<D>::X - 1 + R, N - 1);
+        const int ylo = max(tr.o[1] - R, 0), yhi = min(tr.o[1] + Tile<D>::Y - 1 + R, N - 1);
+        const int zlo = D == 3 ? max(tr.o[2] - R, 0) : 0;
+        const int zhi = D == 3 ? min(tr.o[2] + Tile<D>::Z - 1 + R, N - 1) : 0;
+        const int ny = yhi - ylo + 1, nrows = ny * (zhi - zlo + 1);
+        uint32_t cand = 0;
+        for (int r = lane; r < nrows; r += 32) {
+            const int64_t rb = ((int64_t)(zlo + r / ny) * N + ylo + r % ny) * N;
+            cand += __ldg(tr.g.bin_start + rb + xhi + 1) - __ldg(tr.g.bin_start + rb + xlo);
+        }
+        cand = __reduce_add_sync(0xffffffffu, cand);
+        if (lane == 0) {
+            a.tile_cand[t] = cand;
+            if (cand) atomicAdd(a.cloud_cand + tr.cloud, (unsigned long long)cand);
+        }
+    }
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(a.done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+
+    // item counts: max(1, ceil(cand / chunk)), chunk = max(kItemChunk,
+    // ceil(cloud candidates / extra items)); exclusive scan over the tiles
+    __shared__ uint32_t s_warp[32];
+    const int tid = threadIdx.x, w = tid >> 5, nw = blockDim.x >> 5;
+    uint32_t running = 0;
+    for (int base = 0; base < a.n_tiles; base += blockDim.x) {
+        const int tt = base + tid;
+        uint32_t v = 0;
+        if (tt < a.n_tiles) {
+            const int k = a.clouds ? a.tiles[tt].cloud : 0;
+            const int64_t nk = a.clouds ? a.clouds[k].n : a.n_drops;
+            const unsigned long long tot = __ldcg(a.cloud_cand + k);
+            const unsigned long long extra = (unsigned long long)nw_extra_items(nk);
+            unsigned long long chunk = (tot + extra - 1) / extra;
+            if (chunk < kItemChunk) chunk = kItemChunk;
+            const unsigned long long cand = __ldcg(a.tile_cand + tt);
+            v = cand ? (uint32_t)((cand + chunk - 1) / chunk) : 1u;
+        }
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            uint32_t sw = lane < nw ? s_warp[lane] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, sw, o);
+                if (lane >= o) sw += y;
+            }
+            if (lane < nw) s_warp[lane] = sw;
+        }
+        __syncthreads();
+        if (tt < a.n_tiles) a.tile_items[tt] = running + (w > 0 ? s_warp[w - 1] : 0) + x - v;
+        running += s_warp[nw - 1];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        a.tile_items[a.n_tiles] = running;
+        *a.done = 0u;
+    }
+    for (int k = a.cloud_lo + tid; k < a.cloud_hi; k += blockDim.x) a.cloud_cand[k] = 0ull;
+}
+
+// Persistent CTAs: one work item at a time from the counter.
+template <typename T, int D, int KER>
+__global__ void __launch_bounds__(GT) k_nw_items(NwItems a)
+{
+    __shared__ uint32_t s_item;
+    const uint32_t total = __ldg(a.tile_items + a.n_tiles);
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) s_tile = (int)atomicAdd(&b.tile_counter[group], 1u);
+        if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1u);
         __syncthreads();
-        const int t = s_tile;
-        if (t >= nt) break;
-        const BatchTile bt = tiles[t];
-        const BatchCloud& c = b.clouds[bt.cloud];
-        GatherArgs a{};
-        a.rec = b.rec[group];
-        a.rec_base = rec_base;
-        a.bin_start = b.bin_start + c.cell_off;
-        a.ext_max = b.ext_max + bt.cloud;
-        a.N = c.N;
-        a.per_cell = c.per_cell;
-        a.s_mass = c.s_mass;
-        a.s_mom = c.s_mom;
-        a.dsum = c.dsum;
-        a.status = st;
-        gather_tile<float, D, KER>(a, bt.x0, bt.y0, bt.z0);
+        const uint32_t item = s_item;
+        if (item >= total) break;
+        int lo = 0, hi = a.n_tiles - 1;   // last tile with tile_items <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(a.tile_items + mid) <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const int t = lo;
+        const uint32_t i0 = __ldg(a.tile_items + t), ni = __ldg(a.tile_items + t + 1) - i0;
+        const uint32_t cand = __ldg(a.tile_cand + t);
+        const uint32_t csize = (cand + ni - 1) / ni;
+        const uint32_t c0 = (item - i0) * csize, c1 = min(c0 + csize, cand);
+        const TileRef tr = tile_ref<D>(a, t);
+        T* part = ni > 1 ? (T*)a.temp + (int64_t)item * (D + 2) * GT : nullptr;
+        gather_tile<T, D, KER>(tr.g, tr.o[0], tr.o[1], tr.o[2], c0, c1, part);
+    }
+}
+
+// Tiles of several items: the items' partials of each cell in item order.
+template <typename T, int D>
+__global__ void __launch_bounds__(GT) k_nw_combine(NwItems a)
+{
+    const int tid = threadIdx.x;
+    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+        const uint32_t i0 = __ldg(a.tile_items + t), i1 = __ldg(a.tile_items + t + 1);
+        if (i1 - i0 <= 1) continue;
+        const TileRef tr = tile_ref<D>(a, t);
+        int w0[3], cc[3];
+        tile_cell<D>(tid, tr.o, w0, cc);
+        const int N = tr.g.N;
+        if (!(cc[0] < N && cc[1] < N && (D == 2 || cc[2] < N))) continue;
+        T s[D + 2], c[D + 2];
+#pragma unroll
+        for (int q = 0; q < D + 2; ++q) s[q] = c[q] = T(0);
+        for (uint32_t it = i0; it < i1; ++it) {
+            const T* p = (const T*)a.temp + (int64_t)it * (D + 2) * GT + tid;
+#pragma unroll
+            for (int q = 0; q < D + 2; ++q) neumaier(s[q], c[q], p[q * GT]);
+        }
+        T Nq[4];
+#pragma unroll
+        for (int q = 0; q <= D; ++q) Nq[q] = s[1 + q] + c[1 + q];
+        write_cell<T, D>(tr.g, cc, s[0] + c[0], Nq);
     }
 }
 
 template <typename T, int D, int KER>
-cudaError_t launch_gather_t(const GatherArgs& a, cudaStream_t s)
+size_t items_smem() { return (size_t)CAP * record_values(D, KER) * sizeof(T); }
+
+// Shared-memory limit of the items kernel (set once, before any capture) and
+// its resident CTAs per SM.
+template <typename T, int D, int KER>
+int items_prepare()
 {
-    constexpr int RV = record_values(D, KER);
-    const size_t smem = (size_t)CAP * RV * sizeof(T);
-    auto fn = k_nw_gather<T, D, KER>;   // tiles of one mesh
-    static bool attr_set = false;   // set once, before any stream capture that uses it
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        auto fn = k_nw_items<T, D, KER>;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)items_smem<T, D, KER>()) !=
+            cudaSuccess)
+            return -1;
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, GT, items_smem<T, D, KER>()) != cudaSuccess)
+            return -1;
+        per_sm = b > 0 ? b : 1;
     }
-    const int N = a.N;
-    dim3 grid((N + Tile<D>::X - 1) / Tile<D>::X, (N + Tile<D>::Y - 1) / Tile<D>::Y,
-              D == 3 ? (N + Tile<D>::Z - 1) / Tile<D>::Z : 1);
-    fn<<<grid, GT, smem, s>>>(a);
+    return per_sm;
+}
+
+// Plan, items and combine of one tile set (one mesh, or one batch group).
+template <typename T, int D, int KER>
+cudaError_t launch_items_t(const NwItems& a, int ctas, int num_sms, cudaStream_t s)
+{
+    if (a.n_tiles <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    k_nw_plan<D><<<(unsigned)(((int64_t)a.n_tiles * 32 + 255) / 256), 256, 0, s>>>(a);
+    k_nw_items<T, D, KER><<<ctas, GT, items_smem<T, D, KER>(), s>>>(a);
+    const int cb = a.n_tiles < 8 * num_sms ? a.n_tiles : 8 * num_sms;
+    k_nw_combine<T, D><<<cb, GT, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -477,29 +756,63 @@ __global__ void __launch_bounds__(256) k_psi_cells(const T* __restrict__ rec, co
     }
 }
 
+
+template <typename T, int D, int KER>
+cudaError_t launch_nw_t(const NwItems& a, int num_sms, cudaStream_t s)
+{
+    const int per_sm = items_prepare<T, D, KER>();
+    if (per_sm < 0) return cudaErrorInvalidValue;
+    return launch_items_t<T, D, KER>(a, per_sm * num_sms, num_sms, s);
+}
+
 }  // namespace
 
-cudaError_t launch_nw_gather(const fla_cloud& cl, const fla_mesh& m, const fla_deposit_cfg& cfg, const void* rec,
-                             const uint32_t* bin_start, const unsigned int* ext_max, const fla_sources& out,
-                             DevStatus* st, cudaStream_t s)
+int nw_tiles(int dim, int N)
 {
-    GatherArgs a{};
-    a.status = st;
-    a.rec = rec;
+    if (dim == 2) return ((N + 15) / 16) * ((N + 15) / 16);
+    return ((N + 7) / 8) * ((N + 7) / 8) * ((N + 3) / 4);
+}
+
+int64_t nw_item_budget(int dim, int N, int64_t n) { return nw_tiles(dim, N) + nw_extra_items(n); }
+
+size_t nw_temp_bytes(int dim, int N, int64_t n, size_t elem)
+{
+    return (size_t)nw_item_budget(dim, N, n) * (size_t)(dim + 2) * GT * elem;
+}
+
+cudaError_t launch_nw_gather(const fla_cloud& cl, const fla_mesh& m, const fla_deposit_cfg& cfg, const void* rec,
+                             const uint32_t* bin_start, const unsigned int* ext_max, const NwWork& w,
+                             const fla_sources& out, DevStatus* st, int num_sms, cudaStream_t s)
+{
+    NwItems a{};
     a.bin_start = bin_start;
     a.ext_max = ext_max;
     a.N = m.n;
     a.per_cell = cfg.per_cell;
+    a.tiles_x = m.dim == 2 ? (m.n + 15) / 16 : (m.n + 7) / 8;
+    a.tiles_y = a.tiles_x;
+    a.n_drops = cl.n;
     a.s_mass = out.s_mass_dev;
     a.s_mom = out.s_mom_dev;
     a.dsum = out.dsum_dev;
+    a.rec = rec;
+    a.n_tiles = nw_tiles(m.dim, m.n);
+    a.cloud_lo = 0;
+    a.cloud_hi = 1;
+    a.tile_cand = w.tile_cand;
+    a.tile_items = w.tile_items;
+    a.cloud_cand = w.cand_total;
+    a.done = w.done;
+    a.counter = w.counter;
+    a.temp = w.temp;
+    a.status = st;
     const bool iso = cfg.kernel == FLA_KERNEL_ISO;
     if (cl.dtype == FLA_F32) {
-        if (m.dim == 2) return iso ? launch_gather_t<float, 2, 0>(a, s) : launch_gather_t<float, 2, 1>(a, s);
-        return iso ? launch_gather_t<float, 3, 0>(a, s) : launch_gather_t<float, 3, 1>(a, s);
+        if (m.dim == 2) return iso ? launch_nw_t<float, 2, 0>(a, num_sms, s) : launch_nw_t<float, 2, 1>(a, num_sms, s);
+        return iso ? launch_nw_t<float, 3, 0>(a, num_sms, s) : launch_nw_t<float, 3, 1>(a, num_sms, s);
     }
-    if (m.dim == 2) return iso ? launch_gather_t<double, 2, 0>(a, s) : launch_gather_t<double, 2, 1>(a, s);
-    return iso ? launch_gather_t<double, 3, 0>(a, s) : launch_gather_t<double, 3, 1>(a, s);
+    if (m.dim == 2) return iso ? launch_nw_t<double, 2, 0>(a, num_sms, s) : launch_nw_t<double, 2, 1>(a, num_sms, s);
+    return iso ? launch_nw_t<double, 3, 0>(a, num_sms, s) : launch_nw_t<double, 3, 1>(a, num_sms, s);
 }
 
 cudaError_t launch_psicell(const fla_cloud& cl, const fla_mesh& m, double window_dt, int per_cell,
@@ -551,46 +864,46 @@ cudaError_t launch_psicell(const fla_cloud& cl, const fla_mesh& m, double window
 
 namespace {
 template <int D, int KER>
-cudaError_t launch_batch_gather_t(const BatchDev& b, int group, int ctas, DevStatus* st, cudaStream_t s)
+cudaError_t launch_batch_gather_t(const BatchDev& b, int group, int ctas, DevStatus* st, int num_sms, cudaStream_t s)
 {
-    constexpr int RV = record_values(D, KER);
-    const size_t smem = (size_t)CAP * RV * sizeof(float);
-    auto fn = k_batch_gather<D, KER>;   // shared-memory attribute set by batch_prepare_gathers
-    cudaError_t e = cudaMemsetAsync(b.tile_counter + group, 0, sizeof(unsigned int), s);
-    if (e != cudaSuccess) return e;
-    fn<<<ctas, GT, smem, s>>>(b, group, st);
-    return cudaGetLastError();
+    NwItems a{};
+    a.tiles = b.tiles[group];
+    a.clouds = b.clouds;
+    a.bin_start = b.bin_start;
+    a.ext_max = b.ext_max;
+    a.rec = b.rec[group];
+    a.rec_base_at = b.bin_start + b.group_cells[group];
+    a.n_tiles = b.n_tiles[group];
+    a.cloud_lo = b.group_first[group];
+    a.cloud_hi = b.group_first[group + 1];
+    a.tile_cand = b.tile_cand[group];
+    a.tile_items = b.tile_items[group];
+    a.cloud_cand = b.cloud_cand;
+    a.done = b.plan_done + group;
+    a.counter = b.tile_counter + group;
+    a.temp = b.item_temp;
+    a.status = st;
+    return launch_items_t<float, D, KER>(a, ctas, num_sms, s);
 }
 }  // namespace
-
-template <int D, int KER>
-cudaError_t prepare_gather_t()
-{
-    constexpr int RV = record_values(D, KER);
-    return cudaFuncSetAttribute(k_batch_gather<D, KER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)((size_t)CAP * RV * sizeof(float)));
-}
 
 // Shared-memory limits of the batched gathers (and their modules loaded), set
 // once when a plan is created, before any launch or capture.
 cudaError_t batch_prepare_gathers()
 {
-    cudaError_t e = prepare_gather_t<2, FLA_KERNEL_ISO>();
-    if (e == cudaSuccess) e = prepare_gather_t<2, FLA_KERNEL_ANISO>();
-    if (e == cudaSuccess) e = prepare_gather_t<3, FLA_KERNEL_ISO>();
-    if (e == cudaSuccess) e = prepare_gather_t<3, FLA_KERNEL_ANISO>();
-    return e;
+    const bool ok = items_prepare<float, 2, FLA_KERNEL_ISO>() > 0 && items_prepare<float, 2, FLA_KERNEL_ANISO>() > 0 &&
+                    items_prepare<float, 3, FLA_KERNEL_ISO>() > 0 && items_prepare<float, 3, FLA_KERNEL_ANISO>() > 0;
+    return ok ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t launch_batch_gather(const BatchDev& b, int group, int ctas, DevStatus* st, cudaStream_t s)
+cudaError_t launch_batch_gather(const BatchDev& b, int group, int ctas, DevStatus* st, int num_sms, cudaStream_t s)
 {
     if (b.n_tiles[group] == 0) return cudaSuccess;
-    if (ctas > b.n_tiles[group]) ctas = b.n_tiles[group];
     switch (group) {
-    case 0: return launch_batch_gather_t<2, FLA_KERNEL_ISO>(b, group, ctas, st, s);
-    case 1: return launch_batch_gather_t<2, FLA_KERNEL_ANISO>(b, group, ctas, st, s);
-    case 2: return launch_batch_gather_t<3, FLA_KERNEL_ISO>(b, group, ctas, st, s);
-    default: return launch_batch_gather_t<3, FLA_KERNEL_ANISO>(b, group, ctas, st, s);
+    case 0: return launch_batch_gather_t<2, FLA_KERNEL_ISO>(b, group, ctas, st, num_sms, s);
+    case 1: return launch_batch_gather_t<2, FLA_KERNEL_ANISO>(b, group, ctas, st, num_sms, s);
+    case 2: return launch_batch_gather_t<3, FLA_KERNEL_ISO>(b, group, ctas, st, num_sms, s);
+    default: return launch_batch_gather_t<3, FLA_KERNEL_ANISO>(b, group, ctas, st, num_sms, s);
     }
 }
 

@@ -175,9 +175,21 @@ cudaError_t launch_records(const fla_cloud& cl, const fla_mesh& m, const fla_dep
 cudaError_t launch_learn_backward(const fla_cloud& cl, const fla_mesh& m, const fla_deposit_cfg& cfg,
                                   const uint32_t* perm, const uint32_t* bin_start, int64_t n_cells,
                                   const float* dldc, float* partial, int n_parts, DevStatus* st, cudaStream_t s);
+// Work-item buffers of the tile gather (in the caller's workspace).
+struct NwWork {
+    uint32_t* tile_cand;               // tiles
+    uint32_t* tile_items;              // tiles + 1
+    unsigned long long* cand_total;    // zero before the launch
+    unsigned int* done;                // zero before the launch (reset by the plan)
+    unsigned int* counter;
+    void* temp;                        // nw_temp_bytes
+};
+int nw_tiles(int dim, int N);
+int64_t nw_item_budget(int dim, int N, int64_t n);
+size_t nw_temp_bytes(int dim, int N, int64_t n, size_t elem);
 cudaError_t launch_nw_gather(const fla_cloud& cl, const fla_mesh& m, const fla_deposit_cfg& cfg, const void* rec,
-                             const uint32_t* bin_start, const unsigned int* ext_max, const fla_sources& out,
-                             DevStatus* st, cudaStream_t s);
+                             const uint32_t* bin_start, const unsigned int* ext_max, const NwWork& w,
+                             const fla_sources& out, DevStatus* st, int num_sms, cudaStream_t s);
 int gather2d_tiles(int N);
 uint32_t gather2d_item_budget(int N, int64_t n);
 size_t gather2d_temp_bytes(int N, int64_t n);
