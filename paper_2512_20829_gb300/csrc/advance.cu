@@ -393,6 +393,7 @@ __device__ __forceinline__ int advance_one(const AdvArgs& a, int64_t i, int& fol
 template <typename T, int D, bool FLA, int MODE>
 __global__ void __launch_bounds__(128) k_advance(AdvArgs a)
 {
+    pdl_entry();
     constexpr bool FOLD = MODE == kGuarded;
     int nf = 0, n = 0;
     if (MODE != kGuarded) {
@@ -429,6 +430,7 @@ template <int D>
 __global__ void __launch_bounds__(256) k_batch_advance(BatchDev b, int first, int count, int64_t n_dim,
                                                        int nsteps, double dt, int reset, DevStatus* st)
 {
+    pdl_entry();
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int n = 0, nf = 0;
     if (g < n_dim) {
@@ -467,12 +469,12 @@ cudaError_t launch_t(const AdvArgs& a, cudaStream_t s, int guarded_blocks = 0)
 {
     const int threads = 128;
     const unsigned blocks = (unsigned)((a.n + threads - 1) / threads);
-    k_advance<T, D, FLA, MODE><<<blocks, threads, 0, s>>>(a);
+    launch_pdl(k_advance<T, D, FLA, MODE>, dim3(blocks), dim3(threads), 0, s, a);
     if constexpr (MODE == kScreen) {
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         const unsigned gb = (unsigned)(guarded_blocks < (int)blocks ? guarded_blocks : (int)blocks);
-        k_advance<T, D, FLA, kGuarded><<<gb, threads, 0, s>>>(a);
+        launch_pdl(k_advance<T, D, FLA, kGuarded>, dim3(gb), dim3(threads), 0, s, a);
     }
     return cudaGetLastError();
 }
@@ -533,8 +535,8 @@ cudaError_t launch_batch_advance(const BatchDev& b, int dim, int64_t n_dim, int 
     const int g0 = batch_group(dim, 0);
     const int first = b.group_first[g0], count = b.group_first[g0 + 2] - first;
     const unsigned blocks = (unsigned)((n_dim + threads - 1) / threads);
-    if (dim == 2) k_batch_advance<2><<<blocks, threads, 0, s>>>(b, first, count, n_dim, nsteps, dt, reset ? 1 : 0, st);
-    else k_batch_advance<3><<<blocks, threads, 0, s>>>(b, first, count, n_dim, nsteps, dt, reset ? 1 : 0, st);
+    if (dim == 2) launch_pdl(k_batch_advance<2>, dim3(blocks), dim3(threads), 0, s, b, first, count, n_dim, nsteps, dt, reset ? 1 : 0, st);
+    else launch_pdl(k_batch_advance<3>, dim3(blocks), dim3(threads), 0, s, b, first, count, n_dim, nsteps, dt, reset ? 1 : 0, st);
     return cudaGetLastError();
 }
 

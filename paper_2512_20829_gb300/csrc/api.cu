@@ -127,7 +127,7 @@ struct PhaseScope {
 
 // keys + sort; returns the buffer index that holds the sorted keys / permutation.
 int bin_cloud(fla_ctx* ctx, const fla_cloud& c, const fla_mesh& m, void* ws, const WsLayout& L, cudaStream_t s,
-              int* cur_out)
+              int* cur_out, uint32_t* zero = nullptr, int nzero = 0)
 {
     SortWork w{};
     for (int b = 0; b < 2; ++b) {
@@ -140,7 +140,7 @@ int bin_cloud(fla_ctx* ctx, const fla_cloud& c, const fla_mesh& m, void* ws, con
     cudaError_t e;
     {
         PhaseScope ps(ctx, FLA_PHASE_KEYS, s, 1);
-        e = launch_cell_keys(c, m, w.keys[0], s);
+        e = launch_cell_keys(c, m, w.keys[0], s, zero, nzero);
     }
     if (e != cudaSuccess) return FLA_ERR_CUDA;
     const int bits = sort_bits((uint32_t)nc);
@@ -431,13 +431,15 @@ int deposit_impl(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, con
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t nc = cells_of(*mesh);
     uint32_t* bins = at<uint32_t>(ws, L.bin_start);
+    // misc words 0-7: ext_max, the 2D gather's counters (1, 2), the tile
+    // gather's counters (4, 5) and candidate total (6, 7); all start at zero
     unsigned int* ext = at<unsigned int>(ws, L.misc);
-    if (cudaMemsetAsync(ext, 0, 4, s) != cudaSuccess) return FLA_ERR_CUDA;
     if (cloud->n == 0) {
+        if (cudaMemsetAsync(ext, 0, 32, s) != cudaSuccess) return FLA_ERR_CUDA;
         if (cudaMemsetAsync(bins, 0, (size_t)(nc + 1) * 4, s) != cudaSuccess) return FLA_ERR_CUDA;
     } else {
         int cur = 0;
-        st = bin_cloud(ctx, *cloud, *mesh, ws, L, s, &cur);
+        st = bin_cloud(ctx, *cloud, *mesh, ws, L, s, &cur, ext, 8);   // the keys kernel clears misc
         if (st != FLA_OK) return st;
         {
             PhaseScope ps(ctx, FLA_PHASE_BINS, s, 1);
@@ -467,7 +469,6 @@ int deposit_impl(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, con
     w.done = at<unsigned int>(ws, L.misc + 20);
     w.cand_total = at<unsigned long long>(ws, L.misc + 24);
     w.temp = at<void>(ws, L.temp);
-    if (cudaMemsetAsync(w.counter, 0, 16, s) != cudaSuccess) return FLA_ERR_CUDA;
     return cuda_status(launch_nw_gather(*cloud, *mesh, *cfg, at<void>(ws, L.rec), bins, ext, w, *out,
                                         (DevStatus*)ctx->status_dev, ctx->num_sms, s));
 }

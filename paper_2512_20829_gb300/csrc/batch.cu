@@ -149,7 +149,6 @@ namespace {
 int issue_advance(fla_ctx* ctx, fla_batch_plan* p, int threads, cudaStream_t s)
 {
     BatchDev& b = p->dev;
-    if (cudaMemsetAsync(b.ext_max, 0, 4 * (size_t)p->n_clouds, s) != cudaSuccess) return FLA_ERR_CUDA;
     if (launch_batch_carrier(b, p->dt, s) != cudaSuccess) return FLA_ERR_CUDA;
     for (int d = 0; d < 2; ++d)
         if (launch_batch_advance(b, 2 + d, p->n_dim[d], p->window, p->dt, true, threads, (DevStatus*)ctx->status_dev,

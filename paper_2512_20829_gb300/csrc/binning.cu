@@ -20,8 +20,13 @@ constexpr int RS_MAX_DIGITS = 2048;               // digits of up to 11 bits
 
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_cell_keys(const T* __restrict__ state, const uint32_t* __restrict__ meta,
-                                                   int64_t n, int N, uint32_t sentinel, uint32_t* __restrict__ keys)
+                                                   int64_t n, int N, uint32_t sentinel, uint32_t* __restrict__ keys,
+                                                   uint32_t* __restrict__ zero, int nzero)
 {
+    pdl_entry();
+    // words the caller's later kernels need at zero (counters), cleared here
+    // instead of by a separate memset in the stream
+    if (blockIdx.x == 0 && (int)threadIdx.x < nzero) zero[threadIdx.x] = 0u;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t key;
@@ -32,6 +37,7 @@ __global__ void __launch_bounds__(256) k_cell_keys(const T* __restrict__ state, 
 // droplets without a cell get the sentinel cells_total.
 __global__ void __launch_bounds__(256) k_batch_keys(BatchDev b, uint32_t* __restrict__ keys)
 {
+    pdl_entry();
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= b.n_total) return;
     const int k = batch_find(b.drop_pre, b.n_clouds, g);
@@ -45,12 +51,14 @@ __global__ void __launch_bounds__(256) k_batch_keys(BatchDev b, uint32_t* __rest
 
 __global__ void k_batch_step(int* step, int nsteps)
 {
+    pdl_entry();
     if (threadIdx.x == 0 && blockIdx.x == 0) *step += nsteps;
 }
 
 __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
                                                            int width, uint32_t* __restrict__ counts, int tiles)
 {
+    pdl_entry();
     __shared__ uint32_t h[RS_MAX_DIGITS];
     const int nd = 1 << width;
     for (int t = threadIdx.x; t < nd; t += RS_THREADS) h[t] = 0;
@@ -101,6 +109,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
 __global__ void __launch_bounds__(RS_THREADS) k_radix_scan(uint32_t* __restrict__ counts, int tiles,
                                                            uint32_t* __restrict__ totals)
 {
+    pdl_entry();
     __shared__ uint32_t s_warp[RS_WARPS];
     uint32_t* row = counts + (int64_t)blockIdx.x * tiles;
     uint32_t running = 0;
@@ -122,6 +131,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint32_t* __
                                                               const uint32_t* __restrict__ counts,
                                                               const uint32_t* __restrict__ totals, int tiles)
 {
+    pdl_entry();
     __shared__ uint32_t s_base[RS_MAX_DIGITS];
     __shared__ uint16_t s_cnt[RS_WARPS][RS_MAX_DIGITS];
     __shared__ uint32_t s_warp[RS_WARPS];
@@ -193,6 +203,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint32_t* __
 __global__ void __launch_bounds__(256) k_bin_start(const uint32_t* __restrict__ keys, int64_t n, int64_t n_cells,
                                                    uint32_t* __restrict__ bin_start)
 {
+    pdl_entry();
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c > n_cells) return;
     int64_t lo = 0, hi = n;
@@ -227,17 +238,19 @@ int sort_passes_n(int bits, int64_t n)
     return (bits + w - 1) / w;
 }
 
-cudaError_t launch_cell_keys(const fla_cloud& cl, const fla_mesh& m, uint32_t* keys, cudaStream_t s)
+cudaError_t launch_cell_keys(const fla_cloud& cl, const fla_mesh& m, uint32_t* keys, cudaStream_t s, uint32_t* zero,
+                             int nzero)
 {
+    if (nzero > 256) return cudaErrorInvalidValue;
     if (cl.n == 0) return cudaSuccess;
     const int64_t nc = m.dim == 2 ? (int64_t)m.n * m.n : (int64_t)m.n * m.n * m.n;
     const unsigned blocks = (unsigned)((cl.n + 255) / 256);
     if (cl.dtype == FLA_F32) {
-        if (m.dim == 2) k_cell_keys<float, 2><<<blocks, 256, 0, s>>>((const float*)cl.state_dev, cl.meta_dev, cl.n, m.n, (uint32_t)nc, keys);
-        else k_cell_keys<float, 3><<<blocks, 256, 0, s>>>((const float*)cl.state_dev, cl.meta_dev, cl.n, m.n, (uint32_t)nc, keys);
+        if (m.dim == 2) launch_pdl(k_cell_keys<float, 2>, dim3(blocks), dim3(256), 0, s, (const float*)cl.state_dev, cl.meta_dev, cl.n, m.n, (uint32_t)nc, keys, zero, nzero);
+        else launch_pdl(k_cell_keys<float, 3>, dim3(blocks), dim3(256), 0, s, (const float*)cl.state_dev, cl.meta_dev, cl.n, m.n, (uint32_t)nc, keys, zero, nzero);
     } else {
-        if (m.dim == 2) k_cell_keys<double, 2><<<blocks, 256, 0, s>>>((const double*)cl.state_dev, cl.meta_dev, cl.n, m.n, (uint32_t)nc, keys);
-        else k_cell_keys<double, 3><<<blocks, 256, 0, s>>>((const double*)cl.state_dev, cl.meta_dev, cl.n, m.n, (uint32_t)nc, keys);
+        if (m.dim == 2) launch_pdl(k_cell_keys<double, 2>, dim3(blocks), dim3(256), 0, s, (const double*)cl.state_dev, cl.meta_dev, cl.n, m.n, (uint32_t)nc, keys, zero, nzero);
+        else launch_pdl(k_cell_keys<double, 3>, dim3(blocks), dim3(256), 0, s, (const double*)cl.state_dev, cl.meta_dev, cl.n, m.n, (uint32_t)nc, keys, zero, nzero);
     }
     return cudaGetLastError();
 }
@@ -254,9 +267,9 @@ cudaError_t launch_radix_sort(SortWork w, int64_t n, int bits, int first, cudaSt
         const int shift = p * width;
         const int wp = (bits - shift) < width ? (bits - shift) : width;
         const int nd = 1 << wp;
-        k_radix_hist<<<tiles, RS_THREADS, 0, s>>>(w.keys[cur], n, shift, wp, w.counts, tiles);
-        k_radix_scan<<<nd, RS_THREADS, 0, s>>>(w.counts, tiles, w.totals);
-        k_radix_scatter<<<tiles, RS_THREADS, 0, s>>>(w.keys[cur], p == 0 ? nullptr : w.vals[cur], w.keys[cur ^ 1],
+        launch_pdl(k_radix_hist, dim3(tiles), dim3(RS_THREADS), 0, s, w.keys[cur], n, shift, wp, w.counts, tiles);
+        launch_pdl(k_radix_scan, dim3(nd), dim3(RS_THREADS), 0, s, w.counts, tiles, w.totals);
+        launch_pdl(k_radix_scatter, dim3(tiles), dim3(RS_THREADS), 0, s, w.keys[cur], p == 0 ? nullptr : w.vals[cur], w.keys[cur ^ 1],
                                                      w.vals[cur ^ 1], n, shift, wp, w.counts, w.totals, tiles);
         cur ^= 1;
     }
@@ -267,20 +280,20 @@ cudaError_t launch_bin_start(const uint32_t* keys_sorted, int64_t n, int64_t n_c
                              cudaStream_t s)
 {
     const unsigned blocks = (unsigned)((n_cells + 1 + 255) / 256);
-    k_bin_start<<<blocks, 256, 0, s>>>(keys_sorted, n, n_cells, bin_start);
+    launch_pdl(k_bin_start, dim3(blocks), dim3(256), 0, s, keys_sorted, n, n_cells, bin_start);
     return cudaGetLastError();
 }
 
 cudaError_t launch_batch_keys(const BatchDev& b, uint32_t* keys, cudaStream_t s)
 {
     if (b.n_total == 0) return cudaSuccess;
-    k_batch_keys<<<(unsigned)((b.n_total + 255) / 256), 256, 0, s>>>(b, keys);
+    launch_pdl(k_batch_keys, dim3((unsigned)((b.n_total + 255) / 256)), dim3(256), 0, s, b, keys);
     return cudaGetLastError();
 }
 
 cudaError_t launch_batch_step(const BatchDev& b, int nsteps, cudaStream_t s)
 {
-    k_batch_step<<<1, 32, 0, s>>>(b.step, nsteps);
+    launch_pdl(k_batch_step, dim3(1), dim3(32), 0, s, b.step, nsteps);
     return cudaGetLastError();
 }
 

@@ -199,6 +199,7 @@ __device__ __forceinline__ void sample_node(const CarrierArgs& p, T* __restrict_
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_carrier_sample(CarrierArgs p, T* __restrict__ nodes, int64_t total)
 {
+    pdl_entry();
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= total) return;
     sample_node<T, D>(p, nodes, k);
@@ -257,11 +258,14 @@ __host__ __device__ inline CarrierArgs carrier_args(const fla_carrier_desc& c, i
     return p;
 }
 
-// Batched clouds: the carrier arguments of each cloud at the window's start ...
+// Batched clouds: the carrier arguments of each cloud at the window's start
+// (and its largest support cleared for this window's records) ...
 __global__ void k_batch_carrier_args(BatchDev b, double dt)
 {
+    pdl_entry();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= b.n_clouds) return;
+    b.ext_max[k] = 0u;
     const BatchCloud& c = b.clouds[k];
     const double t = __dmul_rn((double)*b.step, dt);
     reinterpret_cast<CarrierArgs*>(b.cargs)[k] = carrier_args(c.car, c.N, t);
@@ -270,6 +274,7 @@ __global__ void k_batch_carrier_args(BatchDev b, double dt)
 // ... and every node of every cloud (single precision).
 __global__ void __launch_bounds__(256) k_batch_carrier_sample(BatchDev b)
 {
+    pdl_entry();
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= b.nodes_total) return;
     const int k = batch_find(b.node_pre, b.n_clouds, g);
@@ -291,11 +296,11 @@ cudaError_t launch_carrier_sample(const fla_carrier_desc& c, const fla_mesh& m, 
     const int threads = 256;
     const unsigned blocks = (unsigned)((total + threads - 1) / threads);
     if (dtype == FLA_F32) {
-        if (m.dim == 2) k_carrier_sample<float, 2><<<blocks, threads, 0, s>>>(p, (float*)nodes, total);
-        else k_carrier_sample<float, 3><<<blocks, threads, 0, s>>>(p, (float*)nodes, total);
+        if (m.dim == 2) launch_pdl(k_carrier_sample<float, 2>, dim3(blocks), dim3(threads), 0, s, p, (float*)nodes, total);
+        else launch_pdl(k_carrier_sample<float, 3>, dim3(blocks), dim3(threads), 0, s, p, (float*)nodes, total);
     } else {
-        if (m.dim == 2) k_carrier_sample<double, 2><<<blocks, threads, 0, s>>>(p, (double*)nodes, total);
-        else k_carrier_sample<double, 3><<<blocks, threads, 0, s>>>(p, (double*)nodes, total);
+        if (m.dim == 2) launch_pdl(k_carrier_sample<double, 2>, dim3(blocks), dim3(threads), 0, s, p, (double*)nodes, total);
+        else launch_pdl(k_carrier_sample<double, 3>, dim3(blocks), dim3(threads), 0, s, p, (double*)nodes, total);
     }
     return cudaGetLastError();
 }
@@ -304,9 +309,9 @@ size_t batch_carrier_args_bytes() { return sizeof(CarrierArgs); }
 
 cudaError_t launch_batch_carrier(const BatchDev& b, double dt, cudaStream_t s)
 {
-    k_batch_carrier_args<<<(b.n_clouds + 63) / 64, 64, 0, s>>>(b, dt);
+    launch_pdl(k_batch_carrier_args, dim3((b.n_clouds + 63) / 64), dim3(64), 0, s, b, dt);
     if (b.nodes_total > 0)
-        k_batch_carrier_sample<<<(unsigned)((b.nodes_total + 255) / 256), 256, 0, s>>>(b);
+        launch_pdl(k_batch_carrier_sample, dim3((unsigned)((b.nodes_total + 255) / 256)), dim3(256), 0, s, b);
     return cudaGetLastError();
 }
 

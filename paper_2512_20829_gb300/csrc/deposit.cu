@@ -456,7 +456,7 @@ struct NwItems {
     uint32_t* tile_items;             // n_tiles + 1 (exclusive prefix)
     unsigned long long* cloud_cand;   // per cloud: candidates of all its tiles (zero between plans)
     unsigned int* done;               // plan CTAs finished (reset by the last)
-    unsigned int* counter;            // items taken (zeroed before the items kernel)
+    unsigned int* counter;            // items taken (zeroed by the plan)
     void* temp;                       // item partials
     DevStatus* status;
 };
@@ -517,7 +517,9 @@ __host__ __device__ inline int64_t nw_extra_items(int64_t n)
 template <int D>
 __global__ void __launch_bounds__(256) k_nw_plan(NwItems a)
 {
+    pdl_entry();
     const int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.counter = 0u;   // the items kernel's counter
     const int t = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (t < a.n_tiles) {
         const TileRef tr = tile_ref<D>(a, t);
@@ -599,6 +601,7 @@ __global__ void __launch_bounds__(256) k_nw_plan(NwItems a)
 template <typename T, int D, int KER>
 __global__ void __launch_bounds__(GT) k_nw_items(NwItems a)
 {
+    pdl_entry();
     __shared__ uint32_t s_item;
     const uint32_t total = __ldg(a.tile_items + a.n_tiles);
     for (;;) {
@@ -628,6 +631,7 @@ __global__ void __launch_bounds__(GT) k_nw_items(NwItems a)
 template <typename T, int D>
 __global__ void __launch_bounds__(GT) k_nw_combine(NwItems a)
 {
+    pdl_entry();
     const int tid = threadIdx.x;
     for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
         const uint32_t i0 = __ldg(a.tile_items + t), i1 = __ldg(a.tile_items + t + 1);
@@ -679,12 +683,11 @@ template <typename T, int D, int KER>
 cudaError_t launch_items_t(const NwItems& a, int ctas, int num_sms, cudaStream_t s)
 {
     if (a.n_tiles <= 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), s);
+    const cudaError_t e = launch_pdl(k_nw_plan<D>, dim3((unsigned)(((int64_t)a.n_tiles * 32 + 255) / 256)), dim3(256), 0, s, a);
     if (e != cudaSuccess) return e;
-    k_nw_plan<D><<<(unsigned)(((int64_t)a.n_tiles * 32 + 255) / 256), 256, 0, s>>>(a);
-    k_nw_items<T, D, KER><<<ctas, GT, items_smem<T, D, KER>(), s>>>(a);
+    launch_pdl(k_nw_items<T, D, KER>, dim3(ctas), dim3(GT), items_smem<T, D, KER>(), s, a);
     const int cb = a.n_tiles < 8 * num_sms ? a.n_tiles : 8 * num_sms;
-    k_nw_combine<T, D><<<cb, GT, 0, s>>>(a);
+    launch_pdl(k_nw_combine<T, D>, dim3(cb), dim3(GT), 0, s, a);
     return cudaGetLastError();
 }
 
@@ -706,6 +709,7 @@ struct PsiArgs {
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_psi_records(PsiArgs a)
 {
+    pdl_entry();
     constexpr int OA = acc_offset(FLA_CLOUD_LPT, D);
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nvalid = a.bin_start[a.n_cells];
@@ -733,6 +737,7 @@ __global__ void __launch_bounds__(256) k_psi_cells(const T* __restrict__ rec, co
                                                    int64_t n_cells, T scale, uint32_t* __restrict__ counts,
                                                    T* __restrict__ s_mass, T* __restrict__ s_mom)
 {
+    pdl_entry();
     const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (c >= n_cells) return;
@@ -838,25 +843,25 @@ cudaError_t launch_psicell(const fla_cloud& cl, const fla_mesh& m, double window
     const unsigned cb = (unsigned)((nc * 32 + 255) / 256);
     if (cl.dtype == FLA_F32) {
         if (cl.n > 0) {
-            if (m.dim == 2) k_psi_records<float, 2><<<rb, 256, 0, s>>>(a);
-            else k_psi_records<float, 3><<<rb, 256, 0, s>>>(a);
+            if (m.dim == 2) launch_pdl(k_psi_records<float, 2>, dim3(rb), dim3(256), 0, s, a);
+            else launch_pdl(k_psi_records<float, 3>, dim3(rb), dim3(256), 0, s, a);
         }
         if (m.dim == 2)
-            k_psi_cells<float, 2><<<cb, 256, 0, s>>>((const float*)rec, bin_start, nc, (float)scale, out.counts_dev,
+            launch_pdl(k_psi_cells<float, 2>, dim3(cb), dim3(256), 0, s, (const float*)rec, bin_start, nc, (float)scale, out.counts_dev,
                                                      (float*)out.s_mass_dev, (float*)out.s_mom_dev);
         else
-            k_psi_cells<float, 3><<<cb, 256, 0, s>>>((const float*)rec, bin_start, nc, (float)scale, out.counts_dev,
+            launch_pdl(k_psi_cells<float, 3>, dim3(cb), dim3(256), 0, s, (const float*)rec, bin_start, nc, (float)scale, out.counts_dev,
                                                      (float*)out.s_mass_dev, (float*)out.s_mom_dev);
     } else {
         if (cl.n > 0) {
-            if (m.dim == 2) k_psi_records<double, 2><<<rb, 256, 0, s>>>(a);
-            else k_psi_records<double, 3><<<rb, 256, 0, s>>>(a);
+            if (m.dim == 2) launch_pdl(k_psi_records<double, 2>, dim3(rb), dim3(256), 0, s, a);
+            else launch_pdl(k_psi_records<double, 3>, dim3(rb), dim3(256), 0, s, a);
         }
         if (m.dim == 2)
-            k_psi_cells<double, 2><<<cb, 256, 0, s>>>((const double*)rec, bin_start, nc, scale, out.counts_dev,
+            launch_pdl(k_psi_cells<double, 2>, dim3(cb), dim3(256), 0, s, (const double*)rec, bin_start, nc, scale, out.counts_dev,
                                                       (double*)out.s_mass_dev, (double*)out.s_mom_dev);
         else
-            k_psi_cells<double, 3><<<cb, 256, 0, s>>>((const double*)rec, bin_start, nc, scale, out.counts_dev,
+            launch_pdl(k_psi_cells<double, 3>, dim3(cb), dim3(256), 0, s, (const double*)rec, bin_start, nc, scale, out.counts_dev,
                                                       (double*)out.s_mass_dev, (double*)out.s_mom_dev);
     }
     return cudaGetLastError();

@@ -28,6 +28,37 @@ namespace fla {
 
 constexpr int kMaxPlanes = 7;
 
+// Programmatic dependent launch.  Kernels launched by launch_pdl are set up
+// by the GPU while the previous grid in the stream runs, and their CTAs begin
+// as soon as it completes, instead of after a full launch round trip.  Every
+// kernel starts with pdl_entry(), which waits until the previous grid has
+// completed and its writes are visible, so memory accesses keep plain stream
+// order.  (No kernel signals its dependents early: CTAs launched ahead and
+// left waiting slowed the grids they waited on.)  Outside a programmatic
+// launch the wait returns at once.
+__device__ __forceinline__ void pdl_entry()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Launch with programmatic stream serialization (the kernel begins with pdl_entry()).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = s == nullptr ? 0 : 1;   // the legacy stream: a plain launch
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // vec4 of the storage type: float4 or a 32-byte pair of double2.
 template <typename T> struct V4;
 template <> struct V4<float> {
@@ -163,7 +194,9 @@ cudaError_t launch_advance(const fla_cloud& cl, const fla_mesh& m, const void* n
                            double dt, bool reset, DevStatus* st, int num_sms, cudaStream_t s);
 int sort_passes(int bits);
 int sort_passes_n(int bits, int64_t n);
-cudaError_t launch_cell_keys(const fla_cloud& cl, const fla_mesh& m, uint32_t* keys, cudaStream_t s);
+// zero[0, nzero) (nzero <= 256) is cleared by the launch: counters of later kernels.
+cudaError_t launch_cell_keys(const fla_cloud& cl, const fla_mesh& m, uint32_t* keys, cudaStream_t s,
+                             uint32_t* zero = nullptr, int nzero = 0);
 int sort_bits(uint32_t max_key);
 int radix_tiles(int64_t n);
 cudaError_t launch_radix_sort(SortWork w, int64_t n, int bits, int first_buf, cudaStream_t s);

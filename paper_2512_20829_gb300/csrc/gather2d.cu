@@ -108,6 +108,7 @@ __device__ void scan_items(const PlanArgs& a)
 // the item counts into item offsets.
 __global__ void __launch_bounds__(256) k_plan2d(PlanArgs a)
 {
+    pdl_entry();
     const int lane = threadIdx.x & 31;
     const int t = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (t < a.n_tiles) {
@@ -152,6 +153,7 @@ struct G2Args {
 
 __global__ void __launch_bounds__(kThreads, 1) k_gather2d_items(G2Args a)
 {
+    pdl_entry();
     extern __shared__ __align__(16) float4 smem4[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float4* ring = smem4 + warp * (kScratchFloats / 4 + 8);   // per-warp region (two rings, then scratch)
@@ -406,6 +408,7 @@ struct CombineArgs {
 // Sum a cell's work-item partials in item order (compensated) and divide.
 __global__ void __launch_bounds__(256) k_combine2d(CombineArgs a)
 {
+    pdl_entry();
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int N = a.N;
     const int64_t nc = (int64_t)N * N;
@@ -454,9 +457,8 @@ cudaError_t launch_gather2d(const fla_mesh& m, const fla_deposit_cfg& cfg, const
     const int tiles_x = (N + kTile - 1) / kTile;
     const int n_tiles = tiles_x * tiles_x;
     PlanArgs p{bin_start, ext_max, tile_cand, tile_items, N, tiles_x, n_tiles, budget, counter + 1};
-    cudaError_t e = cudaMemsetAsync(counter, 0, 8, s);   // the gather's unit counter and the plan's CTA counter
-    if (e != cudaSuccess) return e;
-    k_plan2d<<<(unsigned)((n_tiles * 32 + 255) / 256), 256, 0, s>>>(p);
+    // the gather's unit counter and the plan's CTA counter are zero on entry
+    cudaError_t e = launch_pdl(k_plan2d, dim3((unsigned)((n_tiles * 32 + 255) / 256)), dim3(256), 0, s, p);
     if (e != cudaSuccess) return e;
     G2Args g{};
     g.rec = (const float4*)rec;
@@ -477,7 +479,7 @@ cudaError_t launch_gather2d(const fla_mesh& m, const fla_deposit_cfg& cfg, const
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_gather2d_items<<<num_sms, kThreads, smem, s>>>(g);
+    launch_pdl(k_gather2d_items, dim3(num_sms), dim3(kThreads), smem, s, g);
     CombineArgs c{};
     c.temp = (const float4*)temp;
     c.tile_items = tile_items;
@@ -489,7 +491,7 @@ cudaError_t launch_gather2d(const fla_mesh& m, const fla_deposit_cfg& cfg, const
     c.s_mom = (float*)out.s_mom_dev;
     c.dsum = (float*)out.dsum_dev;
     const int64_t nc = (int64_t)N * N;
-    k_combine2d<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(c);
+    launch_pdl(k_combine2d, dim3((unsigned)((nc + 255) / 256)), dim3(256), 0, s, c);
     return cudaGetLastError();
 }
 

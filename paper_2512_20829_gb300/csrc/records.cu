@@ -290,6 +290,7 @@ __device__ __forceinline__ void record_f64(const RecArgs& a, const double* sv, d
 template <typename T, int D, int KER>
 __global__ void __launch_bounds__(256) k_records(RecArgs a)
 {
+    pdl_entry();
     constexpr int NP = state_planes(FLA_CLOUD_FLA, D);
     constexpr int RV = record_values(D, KER);
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -384,6 +385,7 @@ __device__ __forceinline__ void mlp_features(const float* J, double adet, float 
 template <int D>
 __global__ void __launch_bounds__(kMlpRows) k_records_mlp(RecArgs a)
 {
+    pdl_entry();
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int NP = state_planes(FLA_CLOUD_FLA, D);
     constexpr int RV = record_values(D, FLA_KERNEL_ISO);
@@ -475,6 +477,7 @@ template <int D>
 __global__ void __launch_bounds__(kMlpRows, 1) k_learn_backward(RecArgs a, const float* __restrict__ dldc,
                                                                 float* __restrict__ partial)
 {
+    pdl_entry();
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int NP = state_planes(FLA_CLOUD_FLA, D);
     constexpr int RP = kLearnRowPad;
@@ -622,6 +625,7 @@ __global__ void __launch_bounds__(kMlpRows, 1) k_learn_backward(RecArgs a, const
 template <int D, int KER>
 __global__ void __launch_bounds__(256) k_batch_records(BatchDev b, int group, DevStatus* st)
 {
+    pdl_entry();
     constexpr int NP = state_planes(FLA_CLOUD_FLA, D);
     constexpr int RV = record_values(D, KER);
     const int64_t jb = b.bin_start[b.group_cells[group]], je = b.bin_start[b.group_cells[group + 1]];
@@ -687,7 +691,7 @@ template <typename T, int D, int KER>
 cudaError_t launch_t(const RecArgs& a, cudaStream_t s)
 {
     const unsigned blocks = (unsigned)((a.n + 255) / 256);
-    k_records<T, D, KER><<<blocks, 256, 0, s>>>(a);
+    launch_pdl(k_records<T, D, KER>, dim3(blocks), dim3(256), 0, s, a);
     return cudaGetLastError();
 }
 
@@ -738,8 +742,8 @@ cudaError_t launch_records(const fla_cloud& cl, const fla_mesh& m, const fla_dep
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int64_t tiles = (a.n + kMlpRows - 1) / kMlpRows;
         const unsigned blocks = (unsigned)(tiles < 6LL * sms ? tiles : 6LL * sms);
-        if (m.dim == 2) k_records_mlp<2><<<blocks, kMlpRows, kMlpSmemBytes, s>>>(a);
-        else k_records_mlp<3><<<blocks, kMlpRows, kMlpSmemBytes, s>>>(a);
+        if (m.dim == 2) launch_pdl(k_records_mlp<2>, dim3(blocks), dim3(kMlpRows), kMlpSmemBytes, s, a);
+        else launch_pdl(k_records_mlp<3>, dim3(blocks), dim3(kMlpRows), kMlpSmemBytes, s, a);
         return cudaGetLastError();
     }
     const bool iso = cfg.kernel == FLA_KERNEL_ISO;
@@ -779,10 +783,10 @@ cudaError_t launch_batch_records(const BatchDev& b, int group, DevStatus* st, cu
     if (n == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((n + 255) / 256);
     switch (group) {
-    case 0: k_batch_records<2, FLA_KERNEL_ISO><<<blocks, 256, 0, s>>>(b, group, st); break;
-    case 1: k_batch_records<2, FLA_KERNEL_ANISO><<<blocks, 256, 0, s>>>(b, group, st); break;
-    case 2: k_batch_records<3, FLA_KERNEL_ISO><<<blocks, 256, 0, s>>>(b, group, st); break;
-    default: k_batch_records<3, FLA_KERNEL_ANISO><<<blocks, 256, 0, s>>>(b, group, st); break;
+    case 0: launch_pdl(k_batch_records<2, FLA_KERNEL_ISO>, dim3(blocks), dim3(256), 0, s, b, group, st); break;
+    case 1: launch_pdl(k_batch_records<2, FLA_KERNEL_ANISO>, dim3(blocks), dim3(256), 0, s, b, group, st); break;
+    case 2: launch_pdl(k_batch_records<3, FLA_KERNEL_ISO>, dim3(blocks), dim3(256), 0, s, b, group, st); break;
+    default: launch_pdl(k_batch_records<3, FLA_KERNEL_ANISO>, dim3(blocks), dim3(256), 0, s, b, group, st); break;
     }
     return cudaGetLastError();
 }
