@@ -7,9 +7,11 @@
 // in row order, cut into work items (below) that persistent CTAs take.  A CTA
 // walks its item's candidates, each thread loads one record, records whose
 // support cannot reach the tile are culled, and the survivors are compacted
-// (order kept) into shared memory.  Each warp then
-// tests 32 staged records at a time against its own sub-tile with one ballot
-// and evaluates only the records that can reach it: truncation test (as a
+// (order kept) into shared memory with a mask of the warp sub-tiles each can
+// reach (support sphere, and for the J-scaled kernel the support's bounding
+// box).  Each warp then selects, 32 staged records at a time with one ballot
+// over their masks, the records that reach its own sub-tile and evaluates
+// only those: truncation test (as a
 // predicate), Gaussian weight 2^(c r^2 + log2(1/h)) with one MUFU ex2 in single
 // precision, FMA accumulation.  Each staged chunk is summed plainly and chunk
 // sums are added with Neumaier compensation.  Every cell sums its records in
@@ -148,6 +150,87 @@ __device__ __forceinline__ T weight_of(const T* r, const float* xcf, const T* xc
     }
 }
 
+// Squared half-widths per axis of the axis-aligned box that holds a J-scaled
+// record's truncated support {d : d' P d <= 9}: 9 (P^-1)_qq, from the
+// cofactors of P.  The margin covers the rounding of the single- or double-
+// precision evaluation and of this bound; it grows with a bound on the
+// condition number of Sigma, kappa <= tr(Sigma)^D det(P).  Where that bound is
+// large or P is not positive definite, no box is used (+inf) and the sphere
+// test alone decides.  The spherical kernel needs no box: its sphere test is exact.
+template <typename T, int D, int KER>
+__device__ __forceinline__ void support_box(const T* r, T W2[3])
+{
+    W2[0] = W2[1] = W2[2] = T(INFINITY);
+    if (KER == FLA_KERNEL_ISO) return;
+    const T eps = sizeof(T) == 4 ? T(5.9604644775390625e-8) : T(1.1102230246251565e-16);
+    T diag[3] = {T(0), T(0), T(0)}, det;
+    if (D == 2) {
+        const T a = r[4], b = r[5], c = r[6];
+        det = a * c - b * b;
+        diag[0] = c;
+        diag[1] = a;
+    } else {
+        const T p00 = r[4], p01 = r[5], p02 = r[6], p11 = r[7], p12 = r[8], p22 = r[9];
+        const T c00 = p11 * p22 - p12 * p12, c11 = p00 * p22 - p02 * p02, c22 = p00 * p11 - p01 * p01;
+        const T c01 = p12 * p02 - p01 * p22, c02 = p01 * p12 - p11 * p02;
+        det = p00 * c00 + p01 * c01 + p02 * c02;
+        diag[0] = c00;
+        diag[1] = c11;
+        diag[2] = c22;
+    }
+    const T tr = r[ExtSlot<D, KER>::v] * T(1.0 / 9.0);
+    const T kb = (D == 2 ? tr * tr : tr * tr * tr) * det;
+    if (!(det > T(0)) || !(kb <= T(1e4))) return;
+    const T grow = T(9) * (T(1) + T(0.0009765625) + T(64) * kb * eps) / det;
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+        const T w2 = diag[q] * grow;
+        if (w2 >= T(0) && w2 < T(INFINITY)) W2[q] = w2;
+    }
+}
+
+// The warp sub-tiles of a tile that a staged record can reach: bit w set when
+// the record's support sphere (radius^2 in slot EXT, with the 2^-10 margin of
+// the tile test) reaches sub-tile w's box of cell centres and, for the J-scaled
+// kernel, its support box overlaps that box too.  slab[q][s] = {lo, hi} of the
+// s-th slab of sub-tiles along axis q (2D: 2 in x, 4 in y; 3D: 2 per axis).
+template <typename T, int D, int KER>
+__device__ __forceinline__ unsigned subtile_mask(const T* rv, const T (*slab)[4][2])
+{
+    constexpr int NS1 = D == 2 ? 4 : 2;
+    constexpr int NS2 = D == 2 ? 1 : 2;
+    T W2[3];
+    support_box<T, D, KER>(rv, W2);
+    const T e2m = rv[ExtSlot<D, KER>::v] * T(1.0009765625);
+    T d2a[2], d2b[4], d2c[2];
+    bool ba[2], bb[4], bc[2];
+    auto dist2 = [&](int q, int sl) {
+        const T dl = slab[q][sl][0] - rv[q], dh = rv[q] - slab[q][sl][1];
+        const T dd = dl > T(0) ? dl : (dh > T(0) ? dh : T(0));
+        return dd * dd;
+    };
+#pragma unroll
+    for (int sl = 0; sl < 2; ++sl) { d2a[sl] = dist2(0, sl); ba[sl] = d2a[sl] <= W2[0]; }
+#pragma unroll
+    for (int sl = 0; sl < NS1; ++sl) { d2b[sl] = dist2(1, sl); bb[sl] = d2b[sl] <= W2[1]; }
+#pragma unroll
+    for (int sl = 0; sl < NS2; ++sl) {
+        d2c[sl] = D == 3 ? dist2(2, sl) : T(0);
+        bc[sl] = D == 3 ? d2c[sl] <= W2[2] : true;
+    }
+    unsigned m = 0;
+#pragma unroll
+    for (int w = 0; w < GT / 32; ++w) {
+        const int sx = w & 1, sy = D == 2 ? (w >> 1) : ((w >> 1) & 1), sz = D == 2 ? 0 : (w >> 2);
+        T d2 = T(0);
+        d2 += d2a[sx];
+        d2 += d2b[sy];
+        if (D == 3) d2 += d2c[sz];
+        if (d2 <= e2m && ba[sx] && bb[sy] && bc[sz]) m |= 1u << w;
+    }
+    return m;
+}
+
 // Cell of thread tid in the tile with origin t0: warp = sub-tile, lane = cell.
 template <int D>
 __device__ __forceinline__ void tile_cell(int tid, const int t0[3], int w0[3], int cc[3])
@@ -203,6 +286,8 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty
     __shared__ int s_count;
     __shared__ uint32_t s_rbeg[GT], s_rexc[GT];   // a batch of rows: segment start, candidates before it
     __shared__ uint32_t s_wsum[GT / 32];
+    __shared__ uint8_t s_mask[CAP];               // per staged record: the warp sub-tiles it reaches
+    __shared__ T s_slab[3][4][2];                 // sub-tile slabs of cell centres per axis
 
     const int N = a.N;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -224,18 +309,21 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty
         xc[q] = centre(cc[q]);
         xcf[q] = sizeof(T) == 4 ? ((float)cc[q] + 0.5f) / (float)N : (float)xc[q];
     }
-    // boxes of cell centres: the CTA tile (staging cull) and the warp sub-tile (flush cull)
-    T lo[3], hi[3], wlo[3], whi[3];
+    // box of cell centres of the CTA tile (staging cull) and the sub-tile slabs (flush masks)
+    T lo[3], hi[3];
 #pragma unroll
     for (int q = 0; q < D; ++q) {
         const int tq = q == 0 ? TX : (q == 1 ? TY : TZ);
-        const int sq = q == 0 ? SX : (q == 1 ? SY : SZ);
         const int last = (t0[q] + tq < N ? t0[q] + tq : N) - 1;
-        const int wlast = (w0[q] + sq < N ? w0[q] + sq : N) - 1;
         lo[q] = centre(t0[q]);
         hi[q] = centre(last);
-        wlo[q] = centre(w0[q]);
-        whi[q] = centre(wlast);
+    }
+    if (tid < 3 * 4 * 2) {
+        const int q = tid >> 3, sl = (tid >> 1) & 3, end = tid & 1;
+        const int sq = q == 0 ? SX : (q == 1 ? SY : SZ);
+        const int first = (q == 0 ? tx0 : (q == 1 ? ty0 : tz0)) + sl * sq;
+        const int last = (first + sq < N ? first + sq : N) - 1;
+        s_slab[q][sl][end] = centre(end ? last : first);
     }
     const float ext2max = __uint_as_float(__ldg(a.ext_max));
     const int R = (int)floorf(sqrtf(ext2max) * (float)N + 0.5f) + 1;
@@ -258,26 +346,16 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty
     const int nrows = ny * (zhi - zlo + 1);
     __syncthreads();
 
-    // Evaluate the staged records for this warp's cells in staging order: 32 records
-    // at a time are tested against the warp's sub-tile (one per lane, one ballot),
-    // and only those that can reach it are evaluated by every lane.
+    // Evaluate the staged records for this warp's cells in staging order: for 32
+    // records at a time each lane reads one record's sub-tile mask (set when it was
+    // staged), one ballot selects those that reach this warp's sub-tile, and
+    // every lane evaluates only those.
     auto flush = [&](int count) {
         if (!warp_live) return;
         T pD = T(0), pN[4] = {T(0), T(0), T(0), T(0)};
         for (int k0 = 0; k0 < count; k0 += 32) {
             const int k = k0 + lane;
-            bool ov = false;
-            if (k < count) {
-                const T* r = srec + k * RV;
-                T d2 = T(0);
-#pragma unroll
-                for (int q = 0; q < D; ++q) {
-                    const T dl = wlo[q] - r[q], dh = r[q] - whi[q];
-                    const T dd = dl > T(0) ? dl : (dh > T(0) ? dh : T(0));
-                    d2 += dd * dd;
-                }
-                ov = d2 <= r[EXT] * T(1.0009765625);
-            }
+            const bool ov = k < count && ((s_mask[k] >> warp) & 1u);
             unsigned m = __ballot_sync(0xffffffffu, ov);
             while (m) {
                 const int j1 = __ffs(m) - 1;
@@ -349,6 +427,7 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty
             const uint32_t j = j0 + tid;
             T rv[16];
             bool keep = false;
+            unsigned msk = 0u;
             if (j < jhi) {
                 int rl = 0, rh = GT - 1;   // last row with s_rexc <= j
                 while (rl < rh) {
@@ -367,6 +446,10 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty
                     d2 += dd * dd;
                 }
                 keep = d2 <= rv[EXT] * T(1.0009765625);   // small margin over rounding of the test
+                if (keep) {
+                    msk = subtile_mask<T, D, KER>(rv, s_slab);
+                    keep = msk != 0u;
+                }
             }
             const unsigned ballot = __ballot_sync(0xffffffffu, keep);
             if (lane == 0) s_wcount[warp] = __popc(ballot);
@@ -379,6 +462,7 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty
                 const int pos = pos0 + __popc(ballot & ((1u << lane) - 1u));
 #pragma unroll
                 for (int v = 0; v < R4; ++v) store4<T>(srec, (int64_t)pos * R4 + v, rv + 4 * v);
+                s_mask[pos] = (uint8_t)msk;
             }
             __syncthreads();
             if (total > CAP - GT) {
@@ -599,7 +683,7 @@ __global__ void __launch_bounds__(256) k_nw_plan(NwItems a)
 
 // Persistent CTAs: one work item at a time from the counter.
 template <typename T, int D, int KER>
-__global__ void __launch_bounds__(GT) k_nw_items(NwItems a)
+__global__ void __launch_bounds__(GT, D == 2 ? 3 : 2) k_nw_items(NwItems a)
 {
     pdl_entry();
     __shared__ uint32_t s_item;
