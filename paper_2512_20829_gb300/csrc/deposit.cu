@@ -282,8 +282,7 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty
     constexpr int EXT = ExtSlot<D, KER>::v;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* srec = reinterpret_cast<T*>(smem_raw);
-    __shared__ int s_wcount[GT / 32];
-    __shared__ int s_count;
+    __shared__ int s_wcount[2][GT / 32];          // kept records per warp, double-buffered by chunk
     __shared__ uint32_t s_rbeg[GT], s_rexc[GT];   // a batch of rows: segment start, candidates before it
     __shared__ uint32_t s_wsum[GT / 32];
     __shared__ uint8_t s_mask[CAP];               // per staged record: the warp sub-tiles it reaches
@@ -331,7 +330,8 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty
     T sD = T(0), cD = T(0);
     T sN[4] = {T(0), T(0), T(0), T(0)}, cN[4] = {T(0), T(0), T(0), T(0)};
     int npairs = 0;
-    if (tid == 0) s_count = 0;
+    int count = 0;      // staged records (the same in every thread)
+    int wbuf = 0;       // s_wcount buffer of the current chunk
 
     const int xlo = t0[0] - R < 0 ? 0 : t0[0] - R;
     const int xhi = t0[0] + TX - 1 + R > N - 1 ? N - 1 : t0[0] + TX - 1 + R;
@@ -452,42 +452,49 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty
                 }
             }
             const unsigned ballot = __ballot_sync(0xffffffffu, keep);
-            if (lane == 0) s_wcount[warp] = __popc(ballot);
+            if (lane == 0) s_wcount[wbuf][warp] = __popc(ballot);
             __syncthreads();
-            int pos0 = s_count;
-            for (int w2 = 0; w2 < warp; ++w2) pos0 += s_wcount[w2];
-            int total = s_count;
-            for (int w2 = 0; w2 < GT / 32; ++w2) total += s_wcount[w2];
+            // Records are appended after the staged ones, which nothing reads until a
+            // flush, and the counts alternate between two buffers (a warp can reach
+            // this chunk's buffer again only after every warp has passed the next
+            // chunk's barrier): one barrier per chunk unless the stage is flushed.
+            int pos0 = count, total = count;
+#pragma unroll
+            for (int w2 = 0; w2 < GT / 32; ++w2) {
+                const int c = s_wcount[wbuf][w2];
+                pos0 += w2 < warp ? c : 0;
+                total += c;
+            }
+            wbuf ^= 1;
             if (keep) {
                 const int pos = pos0 + __popc(ballot & ((1u << lane) - 1u));
 #pragma unroll
                 for (int v = 0; v < R4; ++v) store4<T>(srec, (int64_t)pos * R4 + v, rv + 4 * v);
                 s_mask[pos] = (uint8_t)msk;
             }
-            __syncthreads();
             if (total > CAP - GT) {
+                __syncthreads();   // the staged records are complete
                 flush(total);
+                __syncthreads();   // every warp has read them before they are overwritten
                 total = 0;
             }
-            __syncthreads();
-            if (tid == 0) s_count = total;
-            __syncthreads();
+            count = total;
         }
         off += btotal;
         __syncthreads();   // the row batch's tables are rewritten next
     }
-    const int rem = s_count;
-    if (rem > 0) flush(rem);
+    __syncthreads();
+    if (count > 0) flush(count);
 
     // pairs inside the truncation (cells of the mesh only): one atomic per CTA
     {
         const int w = __reduce_add_sync(0xffffffffu, in_mesh ? npairs : 0);
         __syncthreads();
-        if (lane == 0) s_wcount[warp] = w;
+        if (lane == 0) s_wcount[0][warp] = w;
         __syncthreads();
         if (tid == 0) {
             long long t = 0;
-            for (int q = 0; q < GT / 32; ++q) t += s_wcount[q];
+            for (int q = 0; q < GT / 32; ++q) t += s_wcount[0][q];
             if (t) atomicAdd(&a.status->pairs, (unsigned long long)t);
         }
     }
