@@ -65,11 +65,17 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t* __res
     __syncthreads();
     const int64_t base = blockIdx.x * (int64_t)RS_TILE;
     const int lane = threadIdx.x & 31;
+    uint32_t kv[RS_ITEMS];   // all of this thread's loads in flight before the ranking
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        const int64_t j = base + k * RS_THREADS + threadIdx.x;
+        kv[k] = j < n ? __ldg(keys + j) : 0u;
+    }
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
         const int64_t j = base + k * RS_THREADS + threadIdx.x;
         const bool valid = j < n;
-        const uint32_t dg = valid ? (keys[j] >> shift) & (uint32_t)(nd - 1) : 0xFFFFu;
+        const uint32_t dg = valid ? (kv[k] >> shift) & (uint32_t)(nd - 1) : 0xFFFFu;
         const unsigned peers = __match_any_sync(0xffffffffu, dg);
         if (valid && (__ffs(peers) - 1) == lane) atomicAdd(&h[dg], (uint32_t)__popc(peers));
     }
@@ -124,7 +130,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scan(uint32_t* __restrict_
     if (threadIdx.x == 0) totals[blockIdx.x] = running;
 }
 
-__global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint32_t* __restrict__ kin,
+__global__ void __launch_bounds__(RS_THREADS, 1) k_radix_scatter(const uint32_t* __restrict__ kin,
                                                               const uint32_t* __restrict__ vin,
                                                               uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                               int64_t n, int shift, int width,
@@ -137,45 +143,53 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint32_t* __
     __shared__ uint32_t s_warp[RS_WARPS];
     const int nd = 1 << width;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    // this warp's keys and values, loaded before anything else so that their
+    // latency overlaps the digit bases below
+    const int64_t wbase = blockIdx.x * (int64_t)RS_TILE + w * (RS_ITEMS * 32);
+    uint32_t key[RS_ITEMS], val[RS_ITEMS], rank[RS_ITEMS];
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        const int64_t j = wbase + k * 32 + lane;
+        const bool valid = j < n;
+        key[k] = valid ? __ldg(kin + j) : 0u;
+        val[k] = valid ? (vin ? __ldg(vin + j) : (uint32_t)j) : 0u;
+    }
     // digit bases: exclusive scan of the digit totals plus this tile's offset
     {
         constexpr int PER = RS_MAX_DIGITS / RS_THREADS;   // 8 digits per thread
-        uint32_t v[PER], sum = 0;
+        uint32_t v[PER], c[PER], sum = 0;
 #pragma unroll
-        for (int q = 0; q < PER; ++q) {
+        for (int q = 0; q < PER; ++q) {   // both loads issued before the scan
             const int d = tid * PER + q;
-            v[q] = d < nd ? totals[d] : 0;
-            sum += v[q];
+            v[q] = d < nd ? __ldg(totals + d) : 0u;
+            c[q] = d < nd ? __ldg(counts + (int64_t)d * tiles + blockIdx.x) : 0u;
         }
+#pragma unroll
+        for (int q = 0; q < PER; ++q) sum += v[q];
         uint32_t tot;
         uint32_t ex = block_exclusive_scan(sum, s_warp, tot);
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
             const int d = tid * PER + q;
-            if (d < nd) s_base[d] = ex + counts[(int64_t)d * tiles + blockIdx.x];
+            if (d < nd) s_base[d] = ex + c[q];
             ex += v[q];
         }
     }
     for (int q = tid; q < RS_WARPS * RS_MAX_DIGITS; q += RS_THREADS) (&s_cnt[0][0])[q] = 0;
     __syncthreads();
 
-    const int64_t wbase = blockIdx.x * (int64_t)RS_TILE + w * (RS_ITEMS * 32);
     const unsigned lt = (1u << lane) - 1u;
-    uint32_t key[RS_ITEMS], val[RS_ITEMS], rank[RS_ITEMS];
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
         const int64_t j = wbase + k * 32 + lane;
         const bool valid = j < n;
-        const uint32_t kk = valid ? kin[j] : 0u;
-        const uint32_t vv = valid ? (vin ? vin[j] : (uint32_t)j) : 0u;
+        const uint32_t kk = key[k];
         const uint32_t dg = valid ? (kk >> shift) & (uint32_t)(nd - 1) : 0xFFFFu;
         const unsigned peers = __match_any_sync(0xffffffffu, dg);
         const uint32_t before = valid ? s_cnt[w][dg] : 0u;
         __syncwarp();
         if (valid && (peers & lt) == 0) s_cnt[w][dg] = (uint16_t)(before + (uint32_t)__popc(peers));
         __syncwarp();
-        key[k] = kk;
-        val[k] = vv;
         rank[k] = valid ? before + (uint32_t)__popc(peers & lt) : 0xffffffffu;
     }
     __syncthreads();
