@@ -19,10 +19,10 @@
 // per record instead of one per cell: w = 2^(c dx^2) * 2^(c dy^2 + log2(1/h)).
 // The truncation test keeps the single-precision form r^2 = fma(dy, dy, dx*dx)
 // <= 9 h^2.  Each lane accumulates its own records; the 32 lane partials of a
-// cell are then combined with Neumaier compensation in lane order, written per
-// work item, and a combine kernel adds the items of a tile in item order
-// (again compensated) and divides.  Every step has a fixed order: the result
-// does not depend on timing.
+// cell are then summed in a fixed lane order, written per work item, and a
+// combine kernel adds the items of a tile in item order (Neumaier-compensated)
+// and divides.  Every step has a fixed order: the result does not depend on
+// timing.
 #include "fla_internal.cuh"
 
 namespace fla {
@@ -363,8 +363,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gather2d_items(G2Args a)
         }
         __syncwarp();
 
-        // combine the 32 lane partials of each value with Neumaier compensation,
-        // 32 values at a time through the warp's scratch (rows padded to 33)
+        // combine the 32 lane partials of each value, 32 values at a time through
+        // the warp's scratch (rows padded to 33): four running sums over lanes
+        // l = 0, 4, 8, ... / 1, 5, 9, ... in lane order, then (s0 + s1) + (s2 + s3).
+        // The order is fixed, and the rounding (at most 31 u of the sum of the
+        // partials' magnitudes) is far below that of a lane's own plain sum.
         float* scr = reinterpret_cast<float*>(ring);
         float4* out = a.temp + (int64_t)item * (kTile * kTile);
 #pragma unroll
@@ -372,20 +375,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gather2d_items(G2Args a)
 #pragma unroll
             for (int v = 0; v < 32; ++v) scr[lane * 33 + v] = acc[(32 * half + v) >> 2][v & 3];
             __syncwarp();
-            float sum = 0.0f, comp = 0.0f;
-#pragma unroll 8
-            for (int l = 0; l < 32; ++l) {
-                const float v = scr[l * 33 + lane];
-                const float tt = sum + v;
-                if (fabsf(sum) >= fabsf(v)) comp += (sum - tt) + v;
-                else comp += (v - tt) + sum;
-                sum = tt;
-            }
+            float s4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int l = 0; l < 32; ++l) s4[l & 3] += scr[l * 33 + lane];
             __syncwarp();
             const int f = 32 * half + lane;      // value f of the block: cell f/4, component f%4
             const int k = f >> 2;
             const int local = (4 * (blk & 3) + (k & 3)) + kTile * (4 * (blk >> 2) + (k >> 2));
-            reinterpret_cast<float*>(out + local)[f & 3] = sum + comp;
+            reinterpret_cast<float*>(out + local)[f & 3] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
         }
         __syncwarp();
     }
