@@ -31,7 +31,7 @@ namespace {
 constexpr int kTile = 16;          // tile edge in cells
 constexpr int kWarps = 16;         // 4 x 4 blocks of 4 x 4 cells
 constexpr int kThreads = kWarps * 32;
-constexpr int kChunk = 4096;       // candidates per work item
+constexpr int kChunk = 2048;       // candidates per work item (2,048-3,072 measured best on the 512^2 jet)
 constexpr int kRing = 64;          // queued records per warp
 constexpr int kScratchFloats = 32 * 33;  // per-warp reduction scratch (padded rows)
 
