@@ -41,8 +41,8 @@ __device__ __forceinline__ double m_cospi(double x) { return cospi(x); }
 // with a = rc^2, c = Gam/(2 pi); h and g use their Taylor series near X = 0.
 // inv_a = 1/a, ca = c/a and ca2 = c/a^2 are formed on the host.
 // Single precision: the series near X = 0, expm1 up to X = 1.5 (where e^-X - 1
-// and X e^-X + e^-X - 1 would otherwise cancel), and the fast exponential above,
-// where neither cancels (error below 1e-6 relative).
+// and X e^-X + e^-X - 1 would otherwise cancel), and the fast exponential and
+// reciprocal above, where neither cancels (error below 1e-6 relative).
 __device__ __forceinline__ void lo_hg(float X, float& h, float& g)
 {
     if (X < 1e-2f) {
@@ -53,9 +53,9 @@ __device__ __forceinline__ void lo_hg(float X, float& h, float& g)
         const float iX = 1.0f / X;
         h = -em * iX;
         g = (X * (em + 1.0f) + em) * iX * iX;
-    } else {
+    } else {   // the path nearly every node takes: approximate reciprocal (<= 2 ulp)
         const float e = __expf(-X);
-        const float iX = __frcp_rn(X);
+        const float iX = __fdividef(1.0f, X);
         h = (1.0f - e) * iX;
         g = (X * e + (e - 1.0f)) * iX * iX;
     }
