@@ -301,9 +301,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gather2d_items(G2Args a)
         };
 
         // Row segments, 32 rows at a time: lane l reads the bin offsets of row l so
-        // that the offsets of all rows arrive together.
+        // that the offsets of all rows arrive together.  Rows before this block's
+        // window enter only through the scan of the row lengths (the item's
+        // candidate offsets); rows after it end the walk.
         uint32_t offset = 0;
-        for (int yg = ylo; yg <= yhi && offset < c1; yg += 32) {
+        for (int yg = ylo; yg <= yhi && yg <= wyhi && offset < c1; yg += 32) {
             const int yl = yg + lane;
             uint32_t beg = 0, len = 0, wb = 0, we = 0;
             if (yl <= yhi) {
@@ -322,7 +324,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gather2d_items(G2Args a)
                 if (lane >= o) incl += v;
             }
             const int nrows = min(32, yhi - yg + 1);
-            for (int r = 0; r < nrows; ++r) {
+            const int r1 = min(nrows, wyhi - yg + 1);
+            for (int r = live ? max(0, wylo - yg) : r1; r < r1; ++r) {
                 const uint32_t rbeg = __shfl_sync(0xffffffffu, beg, r);
                 const uint32_t rlen = __shfl_sync(0xffffffffu, len, r);
                 const uint32_t rwb = __shfl_sync(0xffffffffu, wb, r);
