@@ -29,7 +29,8 @@ namespace fla {
 namespace {
 
 constexpr int kTile = 16;          // tile edge in cells
-constexpr int kWarps = 16;         // 4 x 4 blocks of 4 x 4 cells
+constexpr int kBlocks = 16;        // 4 x 4 blocks of 4 x 4 cells per tile
+constexpr int kWarps = 16;         // warps per CTA (one CTA per SM; 8 / 12 warps measured slower)
 constexpr int kThreads = kWarps * 32;
 constexpr int kChunk = 2048;       // candidates per work item (2,048-3,072 measured best on the 512^2 jet)
 constexpr int kRing = 64;          // queued records per warp
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gather2d_items(G2Args a)
     const int N = a.N;
     const float fN = (float)N;
     const int R = support_cells(a.ext_max, N);
-    const uint32_t total = __ldg(a.tile_items + a.n_tiles) * kWarps;   // (item, block) units
+    const uint32_t total = __ldg(a.tile_items + a.n_tiles) * kBlocks;   // (item, block) units
     const unsigned lt = (1u << lane) - 1u;
     unsigned npairs = 0;
 
@@ -170,8 +171,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gather2d_items(G2Args a)
         if (lane == 0) unit = atomicAdd(a.counter, 1u);
         unit = __shfl_sync(0xffffffffu, unit, 0);
         if (unit >= total) break;
-        const uint32_t item = unit / kWarps;
-        const int blk = (int)(unit % kWarps);
+        const uint32_t item = unit / kBlocks;
+        const int blk = (int)(unit % kBlocks);
         // tile of this item: last t with tile_items[t] <= item
         int lo = 0, hi = a.n_tiles - 1;
         while (lo < hi) {
