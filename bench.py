@@ -76,7 +76,7 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 FP64, per the hardware description
 # DRAM bytes (read + write) of one k_gather2d_items launch from an ncu capture
 # (profiles/gather2d_jet512_window81.md); None once the kernel changes.
 GATHER_TRAFFIC = {
-    (2, 0, False): (6246144, "ncu dram__bytes_read+write of k_gather2d_items, jet 512^2 deposit 81"),
+    (2, 0, False): (6245888, "ncu dram__bytes_read+write of k_gather2d_items, jet 512^2 deposit 81"),
 }
 
 
