@@ -102,7 +102,7 @@ BatchLayout batch_layout(const fla_batch_item* items, int n)
         L.nodes_total += nodes_of_mesh(items[k].mesh);
         L.group_drops[g] += items[k].cloud.n;
         L.n_tiles[g] += tiles_of_mesh(items[k].mesh);
-        L.group_items[g] += nw_item_budget(items[k].mesh.dim, items[k].mesh.n, items[k].cloud.n);
+        L.group_items[g] += nw_item_budget(items[k].mesh.dim, items[k].mesh.n, items[k].cloud.n, 4);
     }
     const size_t nn = (size_t)(L.n_total > 0 ? L.n_total : 1);
     size_t o = 0;

@@ -518,11 +518,11 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty
 // A tile whose candidate list is long (a dense cluster of droplets, or a wide
 // support) would hold one CTA for as long as the rest of the mesh takes.  A
 // plan kernel therefore counts each tile's candidates and cuts the list into
-// work items of about kItemChunk candidates; persistent CTAs take items from
+// work items of about `chunk` candidates; persistent CTAs take items from
 // a counter, and the items of a tile leave per-cell partial sums that a
 // combine kernel adds in item order (Neumaier-compensated) before dividing.
 // A tile of one item writes its cells directly.  The item budget of a cloud
-// is its tiles plus ceil(16 n / kItemChunk) + 1; when the candidates need
+// is its tiles plus min(ceil(16 n / chunk) + 1, 65,536); when the candidates need
 // more, the cloud's chunk grows so that its items fit.  Item boundaries
 // depend only on the candidate counts, so the result is deterministic and the
 // same for a cloud gathered alone or in a batch.
@@ -550,6 +550,7 @@ struct NwItems {
     unsigned int* counter;            // items taken (zeroed by the plan)
     void* temp;                       // item partials
     DevStatus* status;
+    uint32_t chunk;                   // candidates per work item (nw_chunk)
 };
 
 struct TileRef {
@@ -596,11 +597,21 @@ __device__ __forceinline__ TileRef tile_ref(const NwItems& a, int t)
     return r;
 }
 
-constexpr uint32_t kItemChunk = 4096;
+// Candidates per work item: 4,096 in single precision; 64 in double
+// precision, whose candidates cost many times more, so that a small mesh
+// still spreads over many SMs (on a 64^2 Taylor-Green cloud the FP64 gather
+// took 27.3 / 11.5 / 7.5 / 4.8 / 3.6 / 3.5 ms per run at 2,048 / 512 / 256 /
+// 128 / 64 / 32 candidates).
+constexpr uint32_t kItemChunkF32 = 4096, kItemChunkF64 = 64;
+__host__ __device__ inline uint32_t nw_chunk(size_t elem) { return elem == 8 ? kItemChunkF64 : kItemChunkF32; }
 
-__host__ __device__ inline int64_t nw_extra_items(int64_t n)
+// Items beyond one per tile that a cloud may use: ceil(16 n / chunk) + 1, at
+// most 65,536 (the partials of a 3D double-precision item are 10 KB); a cloud
+// whose candidates need more widens its chunk instead.
+__host__ __device__ inline int64_t nw_extra_items(int64_t n, uint32_t chunk)
 {
-    return (16 * (n > 0 ? n : 1) + kItemChunk - 1) / kItemChunk + 1;
+    const int64_t e = (16 * (n > 0 ? n : 1) + chunk - 1) / chunk + 1;
+    return e < 65536 ? e : 65536;
 }
 
 // Candidates of each tile (one warp per tile, lanes over the neighbourhood
@@ -641,7 +652,7 @@ __global__ void __launch_bounds__(256) k_nw_plan(NwItems a)
     if (!s_last) return;
     __threadfence();
 
-    // item counts: max(1, ceil(cand / chunk)), chunk = max(kItemChunk,
+    // item counts: max(1, ceil(cand / chunk)), chunk = max(a.chunk,
     // ceil(cloud candidates / extra items)); exclusive scan over the tiles
     __shared__ uint32_t s_warp[32];
     const int tid = threadIdx.x, w = tid >> 5, nw = blockDim.x >> 5;
@@ -653,9 +664,9 @@ __global__ void __launch_bounds__(256) k_nw_plan(NwItems a)
             const int k = a.clouds ? a.tiles[tt].cloud : 0;
             const int64_t nk = a.clouds ? a.clouds[k].n : a.n_drops;
             const unsigned long long tot = __ldcg(a.cloud_cand + k);
-            const unsigned long long extra = (unsigned long long)nw_extra_items(nk);
+            const unsigned long long extra = (unsigned long long)nw_extra_items(nk, a.chunk);
             unsigned long long chunk = (tot + extra - 1) / extra;
-            if (chunk < kItemChunk) chunk = kItemChunk;
+            if (chunk < a.chunk) chunk = a.chunk;
             const unsigned long long cand = __ldcg(a.tile_cand + tt);
             v = cand ? (uint32_t)((cand + chunk - 1) / chunk) : 1u;
         }
@@ -690,7 +701,7 @@ __global__ void __launch_bounds__(256) k_nw_plan(NwItems a)
 
 // Persistent CTAs: one work item at a time from the counter.
 template <typename T, int D, int KER>
-__global__ void __launch_bounds__(GT, D == 2 ? 3 : 2) k_nw_items(NwItems a)
+__global__ void __launch_bounds__(GT, sizeof(T) == 8 ? 1 : (D == 2 ? 3 : 2)) k_nw_items(NwItems a)
 {
     pdl_entry();
     __shared__ uint32_t s_item;
@@ -869,11 +880,14 @@ int nw_tiles(int dim, int N)
     return ((N + 7) / 8) * ((N + 7) / 8) * ((N + 3) / 4);
 }
 
-int64_t nw_item_budget(int dim, int N, int64_t n) { return nw_tiles(dim, N) + nw_extra_items(n); }
+int64_t nw_item_budget(int dim, int N, int64_t n, size_t elem)
+{
+    return nw_tiles(dim, N) + nw_extra_items(n, nw_chunk(elem));
+}
 
 size_t nw_temp_bytes(int dim, int N, int64_t n, size_t elem)
 {
-    return (size_t)nw_item_budget(dim, N, n) * (size_t)(dim + 2) * GT * elem;
+    return (size_t)nw_item_budget(dim, N, n, elem) * (size_t)(dim + 2) * GT * elem;
 }
 
 cudaError_t launch_nw_gather(const fla_cloud& cl, const fla_mesh& m, const fla_deposit_cfg& cfg, const void* rec,
@@ -902,6 +916,7 @@ cudaError_t launch_nw_gather(const fla_cloud& cl, const fla_mesh& m, const fla_d
     a.counter = w.counter;
     a.temp = w.temp;
     a.status = st;
+    a.chunk = nw_chunk(cl.dtype == FLA_F64 ? 8 : 4);
     const bool iso = cfg.kernel == FLA_KERNEL_ISO;
     if (cl.dtype == FLA_F32) {
         if (m.dim == 2) return iso ? launch_nw_t<float, 2, 0>(a, num_sms, s) : launch_nw_t<float, 2, 1>(a, num_sms, s);
@@ -979,6 +994,7 @@ cudaError_t launch_batch_gather_t(const BatchDev& b, int group, int ctas, DevSta
     a.counter = b.tile_counter + group;
     a.temp = b.item_temp;
     a.status = st;
+    a.chunk = nw_chunk(4);
     return launch_items_t<float, D, KER>(a, ctas, num_sms, s);
 }
 }  // namespace

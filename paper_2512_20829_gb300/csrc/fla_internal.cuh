@@ -218,7 +218,7 @@ struct NwWork {
     void* temp;                        // nw_temp_bytes
 };
 int nw_tiles(int dim, int N);
-int64_t nw_item_budget(int dim, int N, int64_t n);
+int64_t nw_item_budget(int dim, int N, int64_t n, size_t elem);
 size_t nw_temp_bytes(int dim, int N, int64_t n, size_t elem);
 cudaError_t launch_nw_gather(const fla_cloud& cl, const fla_mesh& m, const fla_deposit_cfg& cfg, const void* rec,
                              const uint32_t* bin_start, const unsigned int* ext_max, const NwWork& w,

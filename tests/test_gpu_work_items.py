@@ -1,10 +1,10 @@
 """The tile gather's work items against the FP64 oracle.
 
 A tile's candidates (the records of the mesh rows within the cloud's largest
-support) are cut into work items of about 4,096; a tile of several items
-leaves per-cell partials that a combine kernel adds in item order.  When a
-cloud's candidates exceed its item budget (its tiles + ceil(16 n / 4,096) + 1
-items) the chunk grows instead.  These cases are built so that each path is
+support) are cut into work items of about 4,096 (64 in double precision); a
+tile of several items leaves per-cell partials that a combine kernel adds in
+item order.  When a cloud's candidates exceed its item budget (its tiles +
+ceil(16 n / chunk) + 1 items) the chunk grows instead.  These cases are built so that each path is
 taken: a dense cluster whose tile holds many times 4,096 candidates, and a
 wide support that makes every record a candidate of most tiles.  Tolerances
 are those of the deposit tests: rel-L2 1e-4 per field in single precision
@@ -73,8 +73,8 @@ def test_dense_tile_cut_into_items_matches_oracle(ctx, dim, N, n, kernel, dtype)
 
 def test_chunk_grows_past_the_item_budget_matches_oracle(ctx):
     """Supports of 16 cells on a 128^2 mesh: each record is a candidate of
-    about 40 of the 64 tiles, far more than the 16 items per 4,096 records the
-    budget allows, so the plan widens the chunk."""
+    about 40 of the 64 tiles, far more than the 16 items per chunk of records
+    that the budget allows, so the plan widens the chunk."""
     N, n, hmax_cells = 128, 6000, 16.0
     s = I.synthetic_state(2, n, N, seed=77, h0_cells=200.0, band=(0.05, 0.95))
     R = math.floor(3 * hmax_cells + 0.5) + 1
