@@ -4,9 +4,10 @@ A tile's candidates (the records of the mesh rows within the cloud's largest
 support) are cut into work items of about 4,096 (64 in double precision); a
 tile of several items leaves per-cell partials that a combine kernel adds in
 item order.  When a cloud's candidates exceed its item budget (its tiles +
-ceil(16 n / chunk) + 1 items) the chunk grows instead.  These cases are built so that each path is
-taken: a dense cluster whose tile holds many times 4,096 candidates, and a
-wide support that makes every record a candidate of most tiles.  Tolerances
+ceil(16 n / chunk) + 1 items) the chunk grows instead.  These cases are built
+so that each path is taken: a dense cluster whose tile holds many times 4,096
+candidates, and a wide support that makes every record a candidate of most
+tiles.  Tolerances
 are those of the deposit tests: rel-L2 1e-4 per field in single precision
 (1e-5 for D), 1e-12 in double precision.
 """
