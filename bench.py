@@ -29,6 +29,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -90,6 +91,8 @@ def parse():
                     help="configuration to run (the headline metric is quoted on jet_vortex_2d)")
     ap.add_argument("--no-psicell", action="store_true", help="skip the PSI-CELL reference leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--clocks-dir", default=tempfile.gettempdir(),
+                    help="where the nvidia-smi clock samples of the timed region are written")
     ap.add_argument("--no-variants", action="store_true", help="skip the other precision forms")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-clouds leg")
     ap.add_argument("--form", choices=["mixed", "plain", "fold", "learned"], default="mixed",
@@ -114,10 +117,10 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device_index: int):
+    def __init__(self, device_index: int, directory: str):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        self.path = os.path.join(directory, f"clocks_rank{device_index}.csv")
 
     def start(self):
         try:
@@ -409,7 +412,7 @@ def run_ours(args):
 
     # ---------------- timed region (graph replays)
     ctx.sync_status(reset=True)
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(local, args.clocks_dir)
     sampler.start()
     if world > 1:
         dist.barrier()
