@@ -97,9 +97,13 @@ def evaluate(ctx, samples: list[Sample], net=None) -> float:
 
 
 def train(ctx, samples: list[Sample], iters: int = 200, cells_per_sample: int = 1700, lr: float = 2e-3,
-          seed: int = 0, init_scale: float = 0.5, log=None) -> "fla.LearnedCorrection":
+          seed: int = 0, init_scale: float = 0.5, log=None, stats: dict | None = None) -> "fla.LearnedCorrection":
     """Adam on the sum of the samples' losses; the training cells of each sample
-    are drawn once (seeded) from its covered cells."""
+    are drawn once (seeded) from its covered cells.  stats (optional) receives
+    the wall time per iteration of the loop (gradients of every sample, Adam,
+    re-pack), in milliseconds."""
+    import time
+
     import torch
     rng = np.random.default_rng(seed)
     net = fla.LearnedCorrection(ctx, fla.init_mlp_params(seed, init_scale, zero_last=True))
@@ -112,6 +116,8 @@ def train(ctx, samples: list[Sample], iters: int = 200, cells_per_sample: int = 
     grad = torch.zeros(fla.MLP_PARAMS, dtype=torch.float32, device="cuda")
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     mom, var = torch.zeros_like(grad), torch.zeros_like(grad)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     for it in range(1, iters + 1):
         grad.zero_()
         loss.zero_()
@@ -123,4 +129,7 @@ def train(ctx, samples: list[Sample], iters: int = 200, cells_per_sample: int = 
         net.pack()
         if log is not None and (it == 1 or it % 25 == 0 or it == iters):
             log(it, float(loss.item()) / len(samples))
+    torch.cuda.synchronize()
+    if stats is not None:
+        stats["ms_per_iter"] = 1e3 * (time.perf_counter() - t0) / max(iters, 1)
     return net
