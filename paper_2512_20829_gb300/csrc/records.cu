@@ -389,10 +389,14 @@ __global__ void __launch_bounds__(kMlpRows) k_records_mlp(RecArgs a)
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int NP = state_planes(FLA_CLOUD_FLA, D);
     constexpr int RV = record_values(D, FLA_KERNEL_ISO);
-    MlpCta m = mlp_cta_layout(smem);
-    mlp_cta_begin(m, a.mlp);
     const int64_t nvalid = a.bin_start[a.n_cells];
     const int64_t tiles = (nvalid + kMlpRows - 1) / kMlpRows;
+    // the grid is sized for every droplet of the cloud; a CTA without a tile of
+    // binned records leaves before copying the weights and allocating TMEM
+    // (it would contribute nothing to the counters below)
+    if ((int64_t)blockIdx.x >= tiles) return;
+    MlpCta m = mlp_cta_layout(smem);
+    mlp_cta_begin(m, a.mlp);
     float ext_max = 0.0f;
     unsigned n_bad = 0, n_dep = 0;
     bool all_ok = true;
