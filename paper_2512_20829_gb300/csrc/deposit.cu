@@ -11,11 +11,12 @@
 // reach (support sphere, and for the J-scaled kernel the support's bounding
 // box).  Each warp then selects, 32 staged records at a time with one ballot
 // over their masks, the records that reach its own sub-tile and evaluates
-// only those: truncation test (as a
-// predicate), Gaussian weight 2^(c r^2 + log2(1/h)) with one MUFU ex2 in single
-// precision, FMA accumulation.  Each staged chunk is summed plainly and chunk
-// sums are added with Neumaier compensation.  Every cell sums its records in
-// staging order and no atomics touch the outputs, so results are deterministic.
+// only those: truncation test (as a predicate), Gaussian weight
+// 2^(c r^2 + log2(1/h)) with one MUFU ex2 in single precision, FMA
+// accumulation.  Each staged chunk (up to 1,024 records) is summed plainly and
+// chunk sums are added with Neumaier compensation.  Every cell sums its records
+// in staging order and no atomics touch the outputs, so results are
+// deterministic.
 #include "batch.cuh"
 
 namespace fla {
@@ -522,8 +523,8 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty
 // a counter, and the items of a tile leave per-cell partial sums that a
 // combine kernel adds in item order (Neumaier-compensated) before dividing.
 // A tile of one item writes its cells directly.  The item budget of a cloud
-// is its tiles plus min(ceil(16 n / chunk) + 1, 65,536); when the candidates need
-// more, the cloud's chunk grows so that its items fit.  Item boundaries
+// is its tiles plus min(ceil(16 n / chunk) + 1, 65,536); when the candidates
+// need more, the cloud's chunk grows so that its items fit.  Item boundaries
 // depend only on the candidate counts, so the result is deterministic and the
 // same for a cloud gathered alone or in a batch.
 
