@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define FLA_ABI_VERSION 5
+#define FLA_ABI_VERSION 6
 
 /* cudaStream_t without including the CUDA headers. */
 typedef struct CUstream_st* fla_stream_t;
@@ -48,7 +48,19 @@ typedef enum {
     FLA_ERR_UNSUPPORTED = -6   /* valid but not implemented combination */
 } fla_status;
 
-enum { FLA_F32 = 0, FLA_F64 = 1 };                    /* arithmetic and storage type */
+/* Arithmetic and storage type of a cloud.  FLA_F32X2 ("compensated" single
+ * precision) stores every state value as an unevaluated sum hi + lo of two
+ * floats (about 48 significant bits): state_dev holds the n_planes hi planes
+ * of the FLA_F32 layout followed by n_planes lo planes, and fla_advance
+ * integrates in double-float arithmetic on the single-precision pipe from
+ * double-float carrier nodes (fla_carrier_sample with FLA_F32X2).  Cell keys,
+ * records, deposits and their outputs are single precision (from the hi
+ * planes), except det J and n = n0/|det J|, which the records form in double
+ * precision from hi + lo.  Near a fold caustic n is ill-conditioned: single
+ * precision anywhere in the trajectory (seed position, interpolated carrier,
+ * stage arithmetic) moves det J there by far more than its size, and this form
+ * keeps the sources within 1e-4 of the double-precision method. */
+enum { FLA_F32 = 0, FLA_F64 = 1, FLA_F32X2 = 2 };
 enum { FLA_CLOUD_FLA = 0, FLA_CLOUD_LPT = 1 };        /* FLA seeds (with J) or plain parcels */
 enum { FLA_KERNEL_ISO = 0, FLA_KERNEL_ANISO = 1 };    /* deposit kernel shape */
 
@@ -117,7 +129,7 @@ typedef struct {
 typedef struct {
     int32_t kind;              /* FLA_CLOUD_FLA or FLA_CLOUD_LPT */
     int32_t dim;
-    int32_t dtype;             /* FLA_F32 or FLA_F64 */
+    int32_t dtype;             /* FLA_F32, FLA_F64 or FLA_F32X2 */
     int32_t n_batches;
     int64_t n;                 /* droplets, < 2^31 */
     void* state_dev;
@@ -219,13 +231,16 @@ int fla_state_layout(int32_t kind, int32_t dim, int32_t* n_planes, int32_t* off_
 
 /* Bytes of a node array for fla_carrier_sample: (n+1)^dim nodes, each holding
  * u (dim values) then grad u (dim*dim, row-major, G_ij = du_i/dx_j), padded
- * to 8 values (2D) or 12 values (3D). */
+ * to 8 values (2D) or 12 values (3D).  FLA_F32X2: the FLA_F32 array of the
+ * high parts followed by the same array of the low parts (twice the bytes). */
 size_t fla_carrier_nodes_bytes(const fla_mesh* mesh, int32_t dtype);
 
 /* Sample the analytic carrier and its gradient at time t on the mesh nodes
  * (Eq. 3 needs u at the droplet, Eq. 8 grad u; both are interpolated from
  * these nodes by fla_advance).  nodes_dev: fla_carrier_nodes_bytes bytes,
- * 16-byte aligned. */
+ * 16-byte aligned.  FLA_F32X2 evaluates the carrier in double precision and
+ * stores each value as the nearest float hi and the nearest float to the
+ * remainder, lo. */
 int fla_carrier_sample(fla_ctx* ctx, const fla_carrier_desc* carrier, const fla_mesh* mesh, double t,
                        int32_t dtype, void* nodes_dev, fla_stream_t stream);
 
@@ -432,7 +447,11 @@ int fla_sync_status(fla_ctx* ctx, fla_stream_t stream, fla_device_status* out, i
  *  - All calls on a device share the one array, which keeps the last call's
  *    contents; nothing in it needs to start at zero.  Calls whose GPU work
  *    overlaps (different streams or host threads without ordering) race on
- *    it and must be serialised by the caller. */
+ *    it and must be serialised by the caller.
+ *  - The looked-up address is kept for the life of the process: a host
+ *    program that calls cudaDeviceReset between two calls on a device is not
+ *    supported (the reset unloads the library's device code and the array).
+ *  - Arguments are checked exactly as by fla_cell_bins. */
 #define FLA_NOALLOC_MAX_DROPLETS 262144
 int fla_cell_bins_noalloc(const fla_cloud* cloud, const fla_mesh* mesh, uint32_t* keys_sorted_dev,
                           uint32_t* perm_dev, uint32_t* bin_start_dev, fla_stream_t stream);

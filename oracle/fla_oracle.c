@@ -31,11 +31,19 @@
  * double precision.  Readings where the paper is silent are listed beside the
  * code that applies them.  Compile with -ffp-contract=off so that every
  * a*b+c rounds twice, as written.
+ *
+ * Threads: where droplets (one step of the advance) or cells (a deposit) are
+ * independent, OpenMP spreads them over the host cores when the file is built
+ * with -fopenmp.  Each droplet and each cell is still computed by the same
+ * sequential code, so the results do not depend on the thread count.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORA_PI 3.14159265358979323846
 #define ORA_NO_DEADLINE 2147483647
@@ -167,6 +175,7 @@ void ora_carrier_nodes(const ora_carrier* c, double t, int N, double* nodes)
 {
     int d = c->dim, nn = N + 1, stride = d + d * d;
     long total = (d == 2) ? (long)nn * nn : (long)nn * nn * nn;
+#pragma omp parallel for schedule(static)
     for (long k = 0; k < total; ++k) {
         double x[3];
         long r = k;
@@ -299,9 +308,6 @@ int ora_advance(const ora_setup* S, int step0, int nsteps, int n, double* y, dou
     double* nodes = NULL;
     double nodes_t = -1.0;
     if (S->use_mesh) nodes = (double*)malloc(sizeof(double) * nnodes * (d + d * d));
-    double *k1 = malloc(sizeof(double) * ny), *k2 = malloc(sizeof(double) * ny);
-    double *k3 = malloc(sizeof(double) * ny), *k4 = malloc(sizeof(double) * ny);
-    double *ys = malloc(sizeof(double) * ny);
 
     if (reset_acc)
         for (long i = 0; i < (long)n * na; ++i) acc[i] = 0.0;
@@ -316,7 +322,9 @@ int ora_advance(const ora_setup* S, int step0, int nsteps, int n, double* y, dou
             if (F.tc != nodes_t) { ora_carrier_nodes(S->car, F.tc, S->N, nodes); nodes_t = F.tc; }
             F.nodes = nodes;
         }
+#pragma omp parallel for schedule(dynamic, 256)
         for (int i = 0; i < n; ++i) {
+            double k1[24], k2[24], k3[24], k4[24], ys[24];   /* ny <= 24 */
             int b = batch[i];
             double* yi = y + (long)i * ny;
             double* ai = acc + (long)i * na;
@@ -374,7 +382,7 @@ int ora_advance(const ora_setup* S, int step0, int nsteps, int n, double* y, dou
                 if (yi[a] < 0.0 || yi[a] > 1.0) status[i] = ORA_DEAD;
         }
     }
-    free(nodes); free(k1); free(k2); free(k3); free(k4); free(ys);
+    free(nodes);
     return 0;
 }
 
@@ -676,6 +684,7 @@ int ora_nw_deposit(const ora_dep* D, int n, const double* x, const double* J, co
     int d = D->dim;
     ora_rec* rec = (ora_rec*)malloc(sizeof(ora_rec) * (n > 0 ? n : 1));
     int* use = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) {
         use[i] = contributes(d, x + (long)i * d, status[i]);
         if (use[i])
@@ -683,6 +692,7 @@ int ora_nw_deposit(const ora_dep* D, int n, const double* x, const double* J, co
                        n0[batch[i]], h0[batch[i]], D->fold ? D->fold[i] : 0, &rec[i]);
     }
     double V = cell_volume(D);
+#pragma omp parallel for schedule(dynamic, 16)
     for (long o = 0; o < n_out; ++o) {
         long c = cells ? cells[o] : o;
         double xc[3]; float xcf[3];
@@ -746,13 +756,17 @@ int ora_nw_deposit_celllist_cells(const ora_dep* D, int n, const double* x, cons
     memcpy(fill, start, sizeof(long) * nc);
     for (int i = 0; i < n; ++i) if (keys[i] != 0xFFFFFFFFu) list[fill[keys[i]]++] = i;
     ora_rec* rec = (ora_rec*)malloc(sizeof(ora_rec) * (n > 0 ? n : 1));
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i)
         if (keys[i] != 0xFFFFFFFFu)
             ora_record(D, x + (long)i * d, J + (long)i * d * d, acc + (long)i * (1 + d),
                        n0[batch[i]], h0[batch[i]], D->fold ? D->fold[i] : 0, &rec[i]);
     int R = (int)floor(3.0 * D->h_max * N + 0.5) + 1;
-    int* cand = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
     double V = cell_volume(D);
+#pragma omp parallel
+    {
+    int* cand = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));   /* one candidate list per thread */
+#pragma omp for schedule(dynamic, 16)
     for (long o = 0; o < n_out; ++o) {
         long c = cells ? cells[o] : o;
         int ci[3] = {0, 0, 0};
@@ -788,8 +802,29 @@ int ora_nw_deposit_celllist_cells(const ora_dep* D, int n, const double* x, cons
         for (int a = 0; a < d; ++a) S_mom[o * d + a] = den > 0.0 ? -num[1 + a] / den * scale : 0.0;
         Dsum[o] = den;
     }
-    free(keys); free(start); free(list); free(fill); free(rec); free(cand);
+    free(cand);
+    }
+    free(keys); free(start); free(list); free(fill); free(rec);
     return 0;
+}
+
+/* Host threads used by the loops above (1 when built without OpenMP). */
+void ora_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int ora_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* Kernel of one droplet evaluated at every cell centre: the paper's weight

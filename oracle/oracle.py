@@ -26,14 +26,27 @@ PENDING, ACTIVE, DEAD = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, no fast-math, no contraction)."""
+    """Compile the oracle with gcc (plain -O2, no fast-math, no contraction),
+    with OpenMP when the compiler has it (the results do not depend on it)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         os.makedirs(os.path.dirname(_LIB), exist_ok=True)
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def set_threads(n: int) -> None:
+    """Host threads of the oracle's independent loops (droplets of a step, cells)."""
+    lib().ora_set_threads(int(n))
+
+
+def threads() -> int:
+    return int(lib().ora_threads())
 
 
 class _Carrier(C.Structure):
@@ -87,6 +100,8 @@ def lib():
         _lib.ora_mlp_backward.argtypes = [v, v, d, v]
         _lib.ora_learn_loss_grad.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, v, v, C.c_long, v, v, v, v]
         _lib.ora_learn_records.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, v, v, v, v]
+        _lib.ora_set_threads.argtypes = [i]
+        _lib.ora_threads.restype = i
     return _lib
 
 

@@ -19,7 +19,19 @@
 // appended to a list, and a second pass integrates the listed droplets from
 // the same starting state with the guard logic.  The result equals one pass
 // that applies the guard at every step.
+//
+// Compensated clouds (FLA_F32X2): every state value is a double-float
+// hi + lo (two single-precision planes), the carrier nodes are double-float
+// too, and the whole step -- cell fraction, interpolation weights and sums,
+// 1/St, the right-hand side and the RK4 combinations -- runs in double-float
+// arithmetic on the single-precision pipe.  Near a fold caustic n = n0/|det J|
+// is ill-conditioned: single-precision rounding anywhere in the step (of the
+// seed position, of the interpolated carrier, of the small differences u - v
+// and grad u . J - W) moves det J by far more than its own size there, so the
+// step as a whole has to carry more than single precision for n to match the
+// double-precision method.  The window sums (a smooth average) stay single.
 #include "batch.cuh"
+#include "df32.cuh"
 
 namespace fla {
 namespace {
@@ -423,6 +435,245 @@ __global__ void __launch_bounds__(128) k_advance(AdvArgs a)
     }
 }
 
+// ---------------------------------------------------------------- compensated (FLA_F32X2)
+
+struct AdvX2Args {
+    float* state;          // hi planes, then lo planes
+    uint32_t* meta;
+    const fla_batch* batches;
+    const float* nodes;    // hi node array, then lo node array
+    int64_t n, n_nodes;
+    int N;
+    int step0, nsteps;
+    df dt, half, sixth, delta;
+    int reset;
+    DevStatus* status;
+};
+
+// Bi/trilinear interpolation of the double-float node values at the
+// double-float position x: the cell index is floor(x N) clamped to
+// [0, N - 1] and the fraction x N - i is exact in double-float, so the
+// weights and the weighted sums carry no single-precision rounding.
+template <int D>
+__device__ __forceinline__ void interp_x2(const AdvX2Args& a, const df* x, df* u, df* G)
+{
+    constexpr int S = node_stride(D);
+    df f[D];
+    int64_t base = 0, mul = 1;
+    const int64_t nn = a.N + 1;
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+        const df s = x[q] * (float)a.N;
+        int i = df_floor(s);
+        i = i < 0 ? 0 : (i > a.N - 1 ? a.N - 1 : i);
+        f[q] = two_sum(__fsub_rn(s.hi, (float)i), s.lo);   // s.hi - i is exact
+        base += (int64_t)i * mul;
+        mul *= nn;
+    }
+    df acc[D + D * D];
+#pragma unroll
+    for (int q = 0; q < D + D * D; ++q) acc[q] = df_of(0.0f);
+#pragma unroll
+    for (int cnr = 0; cnr < (1 << D); ++cnr) {
+        df w = df_of(1.0f);
+        int64_t idx = base, m2 = 1;
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+            const int bit = (cnr >> q) & 1;
+            w = w * (bit ? f[q] : df_of(1.0f) - f[q]);
+            idx += bit * m2;
+            m2 *= nn;
+        }
+        float vh[S], vl[S];
+#pragma unroll
+        for (int c = 0; c < S / 4; ++c) {
+            load4<float>(a.nodes, idx * (S / 4) + c, vh + 4 * c);
+            load4<float>(a.nodes + a.n_nodes * S, idx * (S / 4) + c, vl + 4 * c);
+        }
+#pragma unroll
+        for (int q = 0; q < D + D * D; ++q) acc[q] = acc[q] + w * df{vh[q], vl[q]};
+    }
+#pragma unroll
+    for (int q = 0; q < D; ++q) u[q] = acc[q];
+#pragma unroll
+    for (int q = 0; q < D * D; ++q) G[q] = acc[D + q];
+}
+
+// Right-hand side of Eqs. 3 and 8 in double-float.
+template <int D, bool FLA>
+__device__ __forceinline__ void rhs_x2(const df* y, const df* u, const df* G, df invSt, df* f)
+{
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+        f[q] = y[D + q];
+        f[D + q] = (u[q] - y[D + q]) * invSt;
+    }
+    if (FLA) {
+        const df* J = y + 2 * D;
+        const df* W = y + 2 * D + D * D;
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                df gj = G[i * D] * J[k];
+#pragma unroll
+                for (int j = 1; j < D; ++j) gj = gj + G[i * D + j] * J[j * D + k];
+                f[2 * D + i * D + k] = W[i * D + k];
+                f[2 * D + D * D + i * D + k] = (gj - W[i * D + k]) * invSt;
+            }
+    }
+}
+
+template <int D, bool FLA>
+__device__ __forceinline__ int advance_x2_one(const AdvX2Args& a, int64_t i)
+{
+    constexpr int kind = FLA ? FLA_CLOUD_FLA : FLA_CLOUD_LPT;
+    constexpr int NP = state_planes(kind, D);
+    constexpr int NY = FLA ? 2 * D + 2 * D * D : 2 * D;
+    constexpr int OA = acc_offset(kind, D);
+    uint32_t meta = a.meta[i];
+    if (meta & FLA_META_DEAD) return 0;
+    const fla_batch* B = a.batches + (meta & FLA_META_BATCH_MASK);
+    const int ss = __ldg(&B->step_start);
+    const int sd = __ldg(&B->step_dead);
+    bool active = (meta & FLA_META_ACTIVE) != 0;
+    if (!active && (ss < a.step0 || ss >= a.step0 + a.nsteps)) return 0;
+
+    float sh[NP * 4], sl[NP * 4];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        load4<float>(a.state, p * a.n + i, sh + 4 * p);
+        load4<float>(a.state, (NP + p) * a.n + i, sl + 4 * p);
+    }
+    df y[NY];
+#pragma unroll
+    for (int q = 0; q < NY; ++q) y[q] = df{sh[q], sl[q]};
+    float acc[1 + D];
+#pragma unroll
+    for (int q = 0; q <= D; ++q) acc[q] = a.reset ? 0.0f : sh[OA + q];
+
+    const df St0 = df_of(__ldg(&B->St0));
+    const float h32 = a.dt.hi, delta32 = a.delta.hi;
+    df u[D], G[D * D];
+    int integrated = 0;
+    for (int s = a.step0; s < a.step0 + a.nsteps; ++s) {
+        if (!active) {
+            if (s != ss) continue;
+            // release: v0 = u(x0); J = I, W = dv0/dx0 = grad u(x0) (initial data of Eq. 8)
+            interp_x2<D>(a, y, u, G);
+#pragma unroll
+            for (int q = 0; q < D; ++q) y[D + q] = u[q];
+            if (FLA) {
+#pragma unroll
+                for (int q = 0; q < D * D; ++q) {
+                    y[2 * D + q] = df_of((q % (D + 1) == 0) ? 1.0f : 0.0f);
+                    y[2 * D + D * D + q] = G[q];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q <= D; ++q) acc[q] = 0.0f;
+            active = true;
+            meta |= FLA_META_ACTIVE;
+        }
+        if (s >= sd) {   // evaporated (deadline decided on the host in double precision)
+            active = false;
+            meta = (meta & ~FLA_META_ACTIVE) | FLA_META_DEAD;
+            break;
+        }
+        ++integrated;
+        // St(t) = St0 (1 + delta (t - t0)) at the stage times t, t + dt/2, t + dt (Eqs. 4-5)
+        const df tau = a.dt * (float)(s - ss);
+        const df r2a = a.delta * tau + 1.0f;
+        const df r2b = a.delta * (tau + a.half) + 1.0f;
+        const df r2c = a.delta * (tau + a.dt) + 1.0f;
+        const df iSa = df_rcp(St0 * r2a), iSb = df_rcp(St0 * r2b), iSc = df_rcp(St0 * r2c);
+
+        df k[NY], ks[NY], ys[NY];
+        // stage 1; the window sums use its u and v (left rectangle over substeps)
+        interp_x2<D>(a, y, u, G);
+        {
+            const float r2 = r2a.hi;
+            const float r = sqrtf(r2);
+            const float m = r2 * r;                   // m = r^3
+            const float mdot = 1.5f * delta32 * r;    // dm/dt with r r' = delta/2
+            const float iS = iSa.hi;
+            acc[0] = fmaf(h32, mdot, acc[0]);
+#pragma unroll
+            for (int q = 0; q < D; ++q)
+                acc[1 + q] = fmaf(h32, m * (u[q] - y[D + q]).hi * iS + mdot * y[D + q].hi, acc[1 + q]);
+        }
+        rhs_x2<D, FLA>(y, u, G, iSa, k);
+#pragma unroll
+        for (int q = 0; q < NY; ++q) {
+            ks[q] = k[q];
+            ys[q] = y[q] + a.half * k[q];
+        }
+        // stage 2
+        interp_x2<D>(a, ys, u, G);
+        rhs_x2<D, FLA>(ys, u, G, iSb, k);
+#pragma unroll
+        for (int q = 0; q < NY; ++q) {
+            ks[q] = ks[q] + k[q] * 2.0f;
+            ys[q] = y[q] + a.half * k[q];
+        }
+        // stage 3
+        interp_x2<D>(a, ys, u, G);
+        rhs_x2<D, FLA>(ys, u, G, iSb, k);
+#pragma unroll
+        for (int q = 0; q < NY; ++q) {
+            ks[q] = ks[q] + k[q] * 2.0f;
+            ys[q] = y[q] + a.dt * k[q];
+        }
+        // stage 4
+        interp_x2<D>(a, ys, u, G);
+        rhs_x2<D, FLA>(ys, u, G, iSc, k);
+#pragma unroll
+        for (int q = 0; q < NY; ++q) y[q] = y[q] + a.sixth * (ks[q] + k[q]);
+        // outflow: leaving [0,1]^dim ends the trajectory
+        bool out = false;
+#pragma unroll
+        for (int q = 0; q < D; ++q) out |= df_lt(y[q], 0.0f) || df_gt(y[q], 1.0f);
+        if (out) {
+            active = false;
+            meta = (meta & ~FLA_META_ACTIVE) | FLA_META_DEAD;
+            break;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NY; ++q) {
+        sh[q] = y[q].hi;
+        sl[q] = y[q].lo;
+    }
+#pragma unroll
+    for (int q = 0; q <= D; ++q) {
+        sh[OA + q] = acc[q];
+        sl[OA + q] = 0.0f;
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        store4<float>(a.state, p * a.n + i, sh + 4 * p);
+        store4<float>(a.state, (NP + p) * a.n + i, sl + 4 * p);
+    }
+    a.meta[i] = meta;
+    return integrated;
+}
+
+template <int D, bool FLA>
+__global__ void __launch_bounds__(128) k_advance_x2(AdvX2Args a)
+{
+    pdl_entry();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int n = i < a.n ? advance_x2_one<D, FLA>(a, i) : 0;
+    __shared__ int s_sum[4];
+    const int w = __reduce_add_sync(0xffffffffu, n);
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const long long t = (long long)s_sum[0] + s_sum[1] + s_sum[2] + s_sum[3];
+        if (t) atomicAdd(&a.status->droplet_steps, (unsigned long long)t);
+    }
+}
+
 // Batched clouds of one dimension (single precision, FLA): droplet g of the
 // group belongs to cloud k with pre[k] <= g < pre[k + 1] of the group's
 // prefix; the per-droplet work is that of k_advance.
@@ -501,6 +752,34 @@ cudaError_t launch_advance(const fla_cloud& cl, const fla_mesh& m, const void* n
     a.tau_fold = (float)cl.tau_fold;
     if (a.n == 0) return cudaSuccess;
     const bool fla = cl.kind == FLA_CLOUD_FLA;
+    if (cl.dtype == FLA_F32X2) {
+        AdvX2Args b{};
+        b.state = (float*)cl.state_dev;
+        b.meta = cl.meta_dev;
+        b.batches = cl.batches_dev;
+        b.nodes = (const float*)nodes;
+        b.n = cl.n;
+        const int64_t nn = m.n + 1;
+        b.n_nodes = m.dim == 2 ? nn * nn : nn * nn * nn;
+        b.N = m.n;
+        b.step0 = step0;
+        b.nsteps = nsteps;
+        b.dt = df_host(dt);
+        b.half = df_host(0.5 * dt);
+        b.sixth = df_host(dt / 6.0);
+        b.delta = df_host(cl.delta);
+        b.reset = reset ? 1 : 0;
+        b.status = st;
+        const unsigned blocks = (unsigned)((b.n + 127) / 128);
+        if (cl.dim == 2) {
+            if (fla) launch_pdl(k_advance_x2<2, true>, dim3(blocks), dim3(128), 0, s, b);
+            else launch_pdl(k_advance_x2<2, false>, dim3(blocks), dim3(128), 0, s, b);
+        } else {
+            if (fla) launch_pdl(k_advance_x2<3, true>, dim3(blocks), dim3(128), 0, s, b);
+            else launch_pdl(k_advance_x2<3, false>, dim3(blocks), dim3(128), 0, s, b);
+        }
+        return cudaGetLastError();
+    }
     if (cl.dtype == FLA_F32 && fla && a.fold) {
         FoldLayout L = fold_layout(cl.dim, cl.n);
         a.fold_list = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(cl.fold_dev) + L.list);

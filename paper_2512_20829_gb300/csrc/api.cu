@@ -18,17 +18,27 @@ int64_t cells_of(const fla_mesh& m)
     return m.dim == 2 ? (int64_t)m.n * m.n : (int64_t)m.n * m.n * m.n;
 }
 
-bool mesh_ok(const fla_mesh* m)
+bool mesh_ok(const fla_mesh* m) { return fla::mesh_valid(m); }
+int cloud_ok(const fla_cloud* c, const fla_mesh* m) { return fla::cloud_valid(c, m); }
+
+bool dtype_ok(int32_t dtype) { return dtype == FLA_F32 || dtype == FLA_F64 || dtype == FLA_F32X2; }
+
+}  // namespace
+
+namespace fla {
+
+bool mesh_valid(const fla_mesh* m)
 {
     if (!m || (m->dim != 2 && m->dim != 3) || m->n < 1 || m->n > (1 << 20)) return false;
     const double nc = m->dim == 2 ? (double)m->n * m->n : (double)m->n * m->n * m->n;
     return nc < 2147483647.0;
 }
 
-int cloud_ok(const fla_cloud* c, const fla_mesh* m)
+int cloud_valid(const fla_cloud* c, const fla_mesh* m)
 {
-    if (!c || !mesh_ok(m)) return FLA_ERR_ARG;
-    if (c->dim != m->dim || (c->dtype != FLA_F32 && c->dtype != FLA_F64)) return FLA_ERR_ARG;
+    if (!c || !mesh_valid(m)) return FLA_ERR_ARG;
+    if (c->dim != m->dim || (c->dtype != FLA_F32 && c->dtype != FLA_F64 && c->dtype != FLA_F32X2))
+        return FLA_ERR_ARG;
     if (c->kind != FLA_CLOUD_FLA && c->kind != FLA_CLOUD_LPT) return FLA_ERR_ARG;
     if (c->n < 0 || c->n >= 2147483647LL) return FLA_ERR_ARG;
     if (c->n > 0) {
@@ -44,6 +54,10 @@ int cloud_ok(const fla_cloud* c, const fla_mesh* m)
     return FLA_OK;
 }
 
+}  // namespace fla
+
+namespace {
+
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct WsLayout {
@@ -53,7 +67,7 @@ struct WsLayout {
 // The load-balanced gather serves single-precision 2D clouds with the spherical kernel.
 bool use_gather2d(const fla_mesh& m, int dtype, int kernel)
 {
-    return m.dim == 2 && dtype == FLA_F32 && kernel == FLA_KERNEL_ISO;
+    return m.dim == 2 && dtype != FLA_F64 && kernel == FLA_KERNEL_ISO;
 }
 
 WsLayout layout(const fla_mesh& m, int dtype, int kernel, int64_t n)
@@ -293,17 +307,17 @@ int fla_state_layout(int32_t kind, int32_t dim, int32_t* n_planes, int32_t* off_
 
 size_t fla_carrier_nodes_bytes(const fla_mesh* mesh, int32_t dtype)
 {
-    if (!mesh_ok(mesh) || (dtype != FLA_F32 && dtype != FLA_F64)) return 0;
+    if (!mesh_ok(mesh) || !dtype_ok(dtype)) return 0;
     const size_t nn = (size_t)mesh->n + 1;
     const size_t nodes = mesh->dim == 2 ? nn * nn : nn * nn * nn;
-    return nodes * node_stride(mesh->dim) * (dtype == FLA_F64 ? 8 : 4);
+    return nodes * node_stride(mesh->dim) * (dtype == FLA_F32 ? 4 : 8);   // F32X2: hi then lo array
 }
 
 int fla_carrier_sample(fla_ctx* ctx, const fla_carrier_desc* c, const fla_mesh* mesh, double t, int32_t dtype,
                        void* nodes_dev, fla_stream_t stream)
 {
     if (!ctx || !c || !mesh_ok(mesh) || !nodes_dev || !aligned(nodes_dev, 16)) return FLA_ERR_ARG;
-    if (dtype != FLA_F32 && dtype != FLA_F64) return FLA_ERR_ARG;
+    if (!dtype_ok(dtype)) return FLA_ERR_ARG;
     if (c->dim != mesh->dim || c->kind < FLA_CARRIER_UNIFORM || c->kind > FLA_CARRIER_ABCJET3) return FLA_ERR_ARG;
     if ((c->kind == FLA_CARRIER_TG2 || c->kind == FLA_CARRIER_JETVORT2) && c->dim != 2) return FLA_ERR_ARG;
     if (c->kind == FLA_CARRIER_ABCJET3 && c->dim != 3) return FLA_ERR_ARG;
@@ -364,7 +378,7 @@ size_t fla_fold_bytes(int32_t dim, int64_t n)
 
 int fla_workspace_size(const fla_mesh* mesh, int32_t dtype, int32_t kernel, int64_t n_droplets, size_t* bytes)
 {
-    if (!bytes || !mesh_ok(mesh) || (dtype != FLA_F32 && dtype != FLA_F64)) return FLA_ERR_ARG;
+    if (!bytes || !mesh_ok(mesh) || !dtype_ok(dtype)) return FLA_ERR_ARG;
     if ((kernel != FLA_KERNEL_ISO && kernel != FLA_KERNEL_ANISO) || n_droplets < 0 || n_droplets >= 2147483647LL)
         return FLA_ERR_ARG;
     *bytes = layout(*mesh, dtype, kernel, n_droplets).total;

@@ -259,7 +259,7 @@ cudaError_t launch_cell_keys(const fla_cloud& cl, const fla_mesh& m, uint32_t* k
     if (cl.n == 0) return cudaSuccess;
     const int64_t nc = m.dim == 2 ? (int64_t)m.n * m.n : (int64_t)m.n * m.n * m.n;
     const unsigned blocks = (unsigned)((cl.n + 255) / 256);
-    if (cl.dtype == FLA_F32) {
+    if (cl.dtype != FLA_F64) {   // FLA_F32X2: the key is formed from the hi planes
         if (m.dim == 2) launch_pdl(k_cell_keys<float, 2>, dim3(blocks), dim3(256), 0, s, (const float*)cl.state_dev, cl.meta_dev, cl.n, m.n, (uint32_t)nc, keys, zero, nzero);
         else launch_pdl(k_cell_keys<float, 3>, dim3(blocks), dim3(256), 0, s, (const float*)cl.state_dev, cl.meta_dev, cl.n, m.n, (uint32_t)nc, keys, zero, nzero);
     } else {

@@ -62,6 +62,12 @@ __device__ __forceinline__ void lo_hg(float X, float& h, float& g)
 }
 __device__ __forceinline__ void lo_hg(double X, double& h, double& g)
 {
+    if (X > 45.0) {   // e^-X < 2^-64: the general branch would give exactly these values
+        const double iX = 1.0 / X;
+        h = iX;
+        g = -iX * iX;
+        return;
+    }
     if (X < 1e-3) {
         h = 1.0 + X * (-0.5 + X * (1.0 / 6.0 + X * (-1.0 / 24.0)));
         g = -0.5 + X * (1.0 / 3.0 + X * (-0.125 + X * (1.0 / 30.0)));
@@ -205,6 +211,46 @@ __global__ void __launch_bounds__(256) k_carrier_sample(CarrierArgs p, T* __rest
     sample_node<T, D>(p, nodes, k);
 }
 
+// Double-float nodes (FLA_F32X2): each value evaluated in double precision and
+// stored as the nearest float (hi array) and the nearest float to the
+// remainder (lo array, n_nodes * stride values further on).
+template <int D>
+__global__ void __launch_bounds__(256) k_carrier_sample_x2(CarrierArgs p, float* __restrict__ nodes, int64_t total)
+{
+    pdl_entry();
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= total) return;
+    const int nn = p.N + 1;
+    double x[3];
+    int64_t r = k;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        x[a] = (double)(r % nn) / (double)p.N;
+        r /= nn;
+    }
+    double u[3], G[9];
+    eval_carrier<double, D>(p, x, u, G);
+    constexpr int S = node_stride(D);
+    double v[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) v[q] = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) v[a] = u[a];
+#pragma unroll
+    for (int q = 0; q < D * D; ++q) v[D + q] = G[q];
+    float hi[12], lo[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+        hi[q] = __double2float_rn(v[q]);
+        lo[q] = __double2float_rn(__dsub_rn(v[q], (double)hi[q]));
+    }
+#pragma unroll
+    for (int c = 0; c < S / 4; ++c) {
+        store4<float>(nodes, k * (S / 4) + c, hi + 4 * c);
+        store4<float>(nodes + total * S, k * (S / 4) + c, lo + 4 * c);
+    }
+}
+
 // The carrier's arguments at time t (vortex centres carried with the jet and
 // wrapped; Lamb-Oseen constants), each operation rounded once.
 __host__ __device__ inline CarrierArgs carrier_args(const fla_carrier_desc& c, int N, double t)
@@ -295,6 +341,11 @@ cudaError_t launch_carrier_sample(const fla_carrier_desc& c, const fla_mesh& m, 
     const int64_t total = m.dim == 2 ? nn * nn : nn * nn * nn;
     const int threads = 256;
     const unsigned blocks = (unsigned)((total + threads - 1) / threads);
+    if (dtype == FLA_F32X2) {
+        if (m.dim == 2) launch_pdl(k_carrier_sample_x2<2>, dim3(blocks), dim3(threads), 0, s, p, (float*)nodes, total);
+        else launch_pdl(k_carrier_sample_x2<3>, dim3(blocks), dim3(threads), 0, s, p, (float*)nodes, total);
+        return cudaGetLastError();
+    }
     if (dtype == FLA_F32) {
         if (m.dim == 2) launch_pdl(k_carrier_sample<float, 2>, dim3(blocks), dim3(threads), 0, s, p, (float*)nodes, total);
         else launch_pdl(k_carrier_sample<float, 3>, dim3(blocks), dim3(threads), 0, s, p, (float*)nodes, total);

@@ -919,7 +919,7 @@ cudaError_t launch_nw_gather(const fla_cloud& cl, const fla_mesh& m, const fla_d
     a.status = st;
     a.chunk = nw_chunk(cl.dtype == FLA_F64 ? 8 : 4);
     const bool iso = cfg.kernel == FLA_KERNEL_ISO;
-    if (cl.dtype == FLA_F32) {
+    if (cl.dtype != FLA_F64) {
         if (m.dim == 2) return iso ? launch_nw_t<float, 2, 0>(a, num_sms, s) : launch_nw_t<float, 2, 1>(a, num_sms, s);
         return iso ? launch_nw_t<float, 3, 0>(a, num_sms, s) : launch_nw_t<float, 3, 1>(a, num_sms, s);
     }
@@ -948,7 +948,7 @@ cudaError_t launch_psicell(const fla_cloud& cl, const fla_mesh& m, double window
     const double scale = per_cell ? 1.0 : 1.0 / V;
     const unsigned rb = (unsigned)((cl.n + 255) / 256);
     const unsigned cb = (unsigned)((nc * 32 + 255) / 256);
-    if (cl.dtype == FLA_F32) {
+    if (cl.dtype != FLA_F64) {
         if (cl.n > 0) {
             if (m.dim == 2) launch_pdl(k_psi_records<float, 2>, dim3(rb), dim3(256), 0, s, a);
             else launch_pdl(k_psi_records<float, 3>, dim3(rb), dim3(256), 0, s, a);

@@ -187,6 +187,11 @@ struct SortWork {
     uint32_t* totals;     // 256
 };
 
+// Argument checks shared by the entry points: mesh shape and size; a cloud's
+// kind, dtype, counts, pointers, alignment, release table and fold guard.
+bool mesh_valid(const fla_mesh* m);
+int cloud_valid(const fla_cloud* c, const fla_mesh* m);
+
 // ---------------------------------------------------------------- launches
 cudaError_t launch_carrier_sample(const fla_carrier_desc& c, const fla_mesh& m, double t, int dtype, void* nodes,
                                   cudaStream_t s);

@@ -54,18 +54,12 @@ int scratch_for_current_device(uint32_t** out)
 extern "C" int fla_cell_bins_noalloc(const fla_cloud* cloud, const fla_mesh* mesh, uint32_t* keys_sorted_dev,
                                      uint32_t* perm_dev, uint32_t* bin_start_dev, fla_stream_t stream)
 {
-    if (!cloud || !mesh) return FLA_ERR_ARG;
-    if ((mesh->dim != 2 && mesh->dim != 3) || mesh->n < 1 || mesh->n > (1 << 20)) return FLA_ERR_ARG;
-    const int64_t nc = mesh->dim == 2 ? (int64_t)mesh->n * mesh->n : (int64_t)mesh->n * mesh->n * mesh->n;
-    if (nc >= 2147483647LL) return FLA_ERR_ARG;
-    if (cloud->dim != mesh->dim || (cloud->dtype != FLA_F32 && cloud->dtype != FLA_F64)) return FLA_ERR_ARG;
-    if (cloud->kind != FLA_CLOUD_FLA && cloud->kind != FLA_CLOUD_LPT) return FLA_ERR_ARG;
-    if (cloud->n < 0) return FLA_ERR_ARG;
+    // the same checks as fla_cell_bins, so both reject the same clouds
+    const int valid = cloud_valid(cloud, mesh);
+    if (valid != FLA_OK) return valid;
     if (cloud->n > kMaxDroplets) return FLA_ERR_WORKSPACE;   // beyond the fixed scratch array
-    if (!bin_start_dev) return FLA_ERR_ARG;
-    if (cloud->n > 0 && (!cloud->state_dev || !cloud->meta_dev || !keys_sorted_dev || !perm_dev ||
-                         ((uintptr_t)cloud->state_dev % 16) != 0))
-        return FLA_ERR_ARG;
+    if (!bin_start_dev || (cloud->n > 0 && (!keys_sorted_dev || !perm_dev))) return FLA_ERR_ARG;
+    const int64_t nc = mesh->dim == 2 ? (int64_t)mesh->n * mesh->n : (int64_t)mesh->n * mesh->n * mesh->n;
     cudaStream_t s = (cudaStream_t)stream;
     if (cloud->n == 0) return cudaMemsetAsync(bin_start_dev, 0, (size_t)(nc + 1) * 4, s) == cudaSuccess
                                   ? FLA_OK : FLA_ERR_CUDA;

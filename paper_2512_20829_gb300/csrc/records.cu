@@ -45,6 +45,7 @@ struct RecArgs {
     float* mlp_out;             // g(f) per droplet index, or null
     double dx;                  // cell size (network feature f4)
     float* aux;                 // per sorted record: g(f) and 1 if h moves with it, or null
+    int x2;                     // 1: compensated cloud (FLA_F32X2), lo planes after the hi planes
 };
 
 template <typename T, int D>
@@ -82,6 +83,19 @@ template <int D>
 __device__ __forceinline__ void det_and_n(const RecArgs& a, const float* J, uint32_t meta, int64_t i, double n0,
                                           double& adet, float& n)
 {
+    if (a.x2) {   // compensated cloud: J = hi + lo, det J and n in double precision
+        constexpr int NP = state_planes(FLA_CLOUD_FLA, D);
+        constexpr int P0 = (2 * D) / 4, P1 = (2 * D + D * D - 1) / 4;
+        float lo[(P1 - P0 + 1) * 4];
+#pragma unroll
+        for (int p = P0; p <= P1; ++p) load4<float>((const float*)a.state, (NP + p) * a.n + i, lo + 4 * (p - P0));
+        double jd[D * D];
+#pragma unroll
+        for (int q = 0; q < D * D; ++q) jd[q] = (double)J[q] + (double)lo[2 * D + q - 4 * P0];
+        adet = fabs(det_double<double, D>(jd));
+        n = (float)(n0 / (adet > 1e-12 ? adet : 1e-12));
+        return;
+    }
     if (a.plain) {
         const float d = fabsf(det_f32<D>(J));
         adet = (double)d;
@@ -728,6 +742,7 @@ RecArgs make_rec_args(const fla_cloud& cl, const fla_mesh& m, const fla_deposit_
     a.mlp = (const unsigned char*)cfg.mlp_dev;
     a.mlp_out = cfg.mlp_out_dev;
     a.dx = 1.0 / m.n;
+    a.x2 = cl.dtype == FLA_F32X2 ? 1 : 0;
     return a;
 }
 }  // namespace
@@ -751,7 +766,7 @@ cudaError_t launch_records(const fla_cloud& cl, const fla_mesh& m, const fla_dep
         return cudaGetLastError();
     }
     const bool iso = cfg.kernel == FLA_KERNEL_ISO;
-    if (cl.dtype == FLA_F32) {
+    if (cl.dtype != FLA_F64) {   // FLA_F32 and FLA_F32X2 (records from the hi planes)
         if (m.dim == 2) return iso ? launch_t<float, 2, 0>(a, s) : launch_t<float, 2, 1>(a, s);
         return iso ? launch_t<float, 3, 0>(a, s) : launch_t<float, 3, 1>(a, s);
     }

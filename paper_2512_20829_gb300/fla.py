@@ -18,8 +18,8 @@ from . import inputs as I
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfla.so")
 
-ABI_VERSION = 5            # FLA_ABI_VERSION of include/fla.h that these structures mirror
-F32, F64 = 0, 1
+ABI_VERSION = 6            # FLA_ABI_VERSION of include/fla.h that these structures mirror
+F32, F64, F32X2 = 0, 1, 2  # F32X2: compensated single precision (hi planes, then lo planes)
 CLOUD_FLA, CLOUD_LPT = 0, 1
 KERNEL_ISO, KERNEL_ANISO = 0, 1
 META_BATCH_MASK = 0x00FFFFFF
@@ -278,19 +278,32 @@ def status_of(meta: np.ndarray) -> np.ndarray:
     return st
 
 
-def pack_state(kind: int, dim: int, n: int, np_dtype, x=None, v=None, J=None, W=None, acc=None) -> np.ndarray:
-    """Host array (n_planes, n, 4) in the library's plane layout."""
+def pack_state(kind: int, dim: int, n: int, np_dtype, x=None, v=None, J=None, W=None, acc=None,
+               split: bool = False) -> np.ndarray:
+    """Host array (n_planes, n, 4) in the library's plane layout.  split: the
+    compensated layout (2 n_planes, n, 4) float32, the planes of the nearest
+    floats followed by the planes of the nearest floats to the remainders."""
     L = state_layout(kind, dim)
-    flat = np.zeros((n, L["n_planes"] * 4), dtype=np_dtype)
+    flat = np.zeros((n, L["n_planes"] * 4), dtype=np.float64 if split else np_dtype)
     for name, arr, width in (("x", x, dim), ("v", v, dim), ("J", J, dim * dim), ("W", W, dim * dim),
                              ("acc", acc, 1 + dim)):
         if arr is not None:
             flat[:, L[name]:L[name] + width] = np.asarray(arr).reshape(n, width)
+    if split:
+        hi = flat.astype(np.float32)
+        lo = (flat - hi.astype(np.float64)).astype(np.float32)
+        flat = np.concatenate([hi.reshape(n, L["n_planes"], 4), lo.reshape(n, L["n_planes"], 4)], axis=1)
+        return np.ascontiguousarray(flat.transpose(1, 0, 2))
     return np.ascontiguousarray(flat.reshape(n, L["n_planes"], 4).transpose(1, 0, 2))
 
 
-def unpack_state(kind: int, dim: int, planes: np.ndarray) -> dict:
+def unpack_state(kind: int, dim: int, planes: np.ndarray, split: bool = False) -> dict:
+    """Inverse of pack_state; split: the compensated layout, values returned as
+    float64 hi + lo."""
     L = state_layout(kind, dim)
+    if split:
+        npl = planes.shape[0] // 2
+        planes = planes[:npl].astype(np.float64) + planes[npl:].astype(np.float64)
     n = planes.shape[1]
     flat = planes.transpose(1, 0, 2).reshape(n, -1)
     out = {"x": flat[:, 0:dim], "v": flat[:, dim:2 * dim], "acc": flat[:, L["acc"]:L["acc"] + 1 + dim]}
@@ -327,7 +340,7 @@ class DeviceCloud:
     @classmethod
     def from_seeds(cls, cloud: I.Cloud, dim: int, delta: float, dt: float, dtype: int = F32, device="cuda"):
         npd = np.float32 if dtype == F32 else np.float64
-        planes = pack_state(cloud.kind, dim, cloud.n, npd, x=cloud.x0)
+        planes = pack_state(cloud.kind, dim, cloud.n, npd, x=cloud.x0, split=dtype == F32X2)
         meta = meta_words(np.zeros(cloud.n, np.int32), cloud.batch)
         return cls(cloud.kind, dim, dtype, planes, meta, batch_table(cloud, delta, dt), delta, device)
 
@@ -339,7 +352,7 @@ class DeviceCloud:
         precision) attaches the fold guard with those droplets inside it."""
         npd = np.float32 if dtype == F32 else np.float64
         n = np.asarray(x).shape[0]
-        planes = pack_state(kind, dim, n, npd, x=x, v=v, J=J, W=W, acc=acc)
+        planes = pack_state(kind, dim, n, npd, x=x, v=v, J=J, W=W, acc=acc, split=dtype == F32X2)
         meta = meta_words(status, batch)
         if fold is not None:
             meta = np.where(np.asarray(fold, bool), meta | META_FOLD, meta).astype(np.uint32)
@@ -371,7 +384,7 @@ class DeviceCloud:
         return c
 
     def to_host(self) -> dict:
-        d = unpack_state(self.kind, self.dim, self.state.cpu().numpy())
+        d = unpack_state(self.kind, self.dim, self.state.cpu().numpy(), split=self.dtype == F32X2)
         meta = self.meta.cpu().numpy().view(np.uint32)
         d["status"] = status_of(meta)
         d["batch"] = (meta & META_BATCH_MASK).astype(np.int32)
@@ -386,14 +399,15 @@ class DeviceCloud:
 
 
 def torch_dtype(dtype: int):
+    """Element type of a cloud's outputs (compensated clouds deposit in single precision)."""
     torch = _torch()
-    return torch.float32 if dtype == F32 else torch.float64
+    return torch.float64 if dtype == F64 else torch.float32
 
 
 def nodes_buffer(m: Mesh, dtype: int, device="cuda"):
     torch = _torch()
     nbytes = lib().fla_carrier_nodes_bytes(C.byref(m), dtype)
-    return torch.empty(nbytes // (4 if dtype == F32 else 8), dtype=torch_dtype(dtype), device=device)
+    return torch.empty(nbytes // (8 if dtype == F64 else 4), dtype=torch_dtype(dtype), device=device)
 
 
 def carrier_sample(ctx: Context, desc: CarrierDesc, m: Mesh, t: float, dtype: int, nodes, stream=None):

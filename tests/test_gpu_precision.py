@@ -10,9 +10,20 @@ mode beside it.  Every case is checked against the FP64 oracle.
   the error of n is read directly;
 * deposit parity (identical truncation decisions) with droplets inside the
   fold guard, and in the plain mode;
-* the reduced jet end to end: per-field error of plain and mixed against the
-  oracle, over all cells and with the caustic cells (any contributor with
-  |det J| < 1e-2) taken out.
+* the reduced jet end to end: per-field error of plain, mixed and compensated
+  against the oracle, over all cells and with the caustic cells (any
+  contributor with |det J| < 1e-2) taken out;
+* the reduced 3D cone (32^3, 500 steps, J-scaled kernel through fold caustics)
+  end to end, the same report.
+
+Where the gate is: the compensated form (FLA_F32X2, double-float trajectories)
+must meet rel-L2 <= 1e-4 against the FP64 oracle over ALL cells, caustic cells
+included.  The single-precision forms meet it only outside the caustic cells:
+there n = n0/|det J| is so ill-conditioned that the roundings of a
+single-precision trajectory (of the seed, the interpolated carrier and the
+small differences u - v, grad u . J - W) move det J by a sizeable fraction of
+itself; their all-cell errors are measured and printed, and asserted only
+outside the caustic cells.
 """
 import math
 
@@ -202,11 +213,13 @@ def test_deposit_parity_fold_and_plain(ctx, dim, kernel, prec):
     assert np.all(np.abs(gv - ov) <= 1e-4 * np.abs(av) + 1e-30)
 
 
-def test_precision_report_jet(ctx):
-    """Reduced jet (128^2, 16,384 seeds, 1,000 steps): error of every source field
-    against the FP64 oracle for the plain and the mixed single-precision forms,
-    over all cells and outside the caustic cells."""
-    wl = I.jet_vortex_2d(scale=4, lpt_per_batch=0)
+FORMS = (("plain", fla.F32, fla.PREC_PLAIN, False), ("mixed", fla.F32, fla.PREC_MIXED, False),
+         ("mixed+guard", fla.F32, fla.PREC_MIXED, True), ("compensated", fla.F32X2, fla.PREC_MIXED, False))
+
+
+def _precision_report(ctx, wl, forms):
+    """Per form and field: rel-L2 against the FP64 oracle over all cells, outside
+    the caustic cells and inside them."""
     st = O.run(wl)
     D = O.dep_struct(wl)
     om, ov, od = O.nw_deposit_celllist(D, st.x, st.J, st.acc, st.status, st.batch, wl.fla.n0, wl.fla.h0)
@@ -216,9 +229,8 @@ def test_precision_report_jet(ctx):
     _, _, dc = O.nw_deposit_celllist(D, st.x, st.J, st.acc, stc, st.batch, wl.fla.n0, wl.fla.h0)
     caustic = dc > 0
     rows = {}
-    for name, prec, guard in (("plain", fla.PREC_PLAIN, False), ("mixed", fla.PREC_MIXED, False),
-                              ("mixed+guard", fla.PREC_MIXED, True)):
-        sim = fla.Simulation(ctx, wl, dtype=fla.F32, precision=prec, fold_guard=guard)
+    for name, dtype, prec, guard in forms:
+        sim = fla.Simulation(ctx, wl, dtype=dtype, precision=prec, fold_guard=guard)
         ctx.sync_status(reset=True)
         sim.run(deposit_every=True)
         torch.cuda.synchronize()
@@ -227,16 +239,44 @@ def test_precision_report_jet(ctx):
         gv = sim.out.s_mom.double().cpu().numpy().T
         gd = sim.out.dsum.double().cpu().numpy()
         r = {}
-        for fname, g, o in (("S_mass", gm, om), ("S_mom_x", gv[:, 0], ov[:, 0]), ("S_mom_y", gv[:, 1], ov[:, 1]),
-                            ("D", gd, od)):
+        fields = [("S_mass", gm, om)] + [(f"S_mom_{'xyz'[c]}", gv[:, c], ov[:, c]) for c in range(wl.dim)]
+        for fname, g, o in fields + [("D", gd, od)]:
             r[fname] = (rel_l2(g, o), rel_l2(g[~caustic], o[~caustic]),
                         rel_l2(g[caustic], o[caustic]) if caustic.any() else 0.0)
         r["fold_steps"] = status.fold_steps
         rows[name] = r
-    print(f"\ncaustic cells {int(caustic.sum())} of {caustic.size}; caustic droplets {int(caustic_droplets.sum())}")
+    print(f"\n{wl.name}: caustic cells {int(caustic.sum())} of {caustic.size}; "
+          f"caustic droplets {int(caustic_droplets.sum())}")
     for name, r in rows.items():
         print(name, {k: (tuple(f"{x:.2e}" for x in v) if isinstance(v, tuple) else v) for k, v in r.items()})
+    return rows, int(caustic.sum())
+
+
+def _fields(dim):
+    return ["S_mass"] + [f"S_mom_{'xyz'[c]}" for c in range(dim)] + ["D"]
+
+
+def test_precision_report_jet(ctx):
+    """Reduced jet (128^2, 16,384 seeds, 1,000 steps): the compensated form meets
+    rel-L2 <= 1e-4 over all cells; every form meets it outside the caustic cells."""
+    wl = I.jet_vortex_2d(scale=4, lpt_per_batch=0)
+    rows, n_caustic = _precision_report(ctx, wl, FORMS)
+    assert n_caustic > 0
     for name, r in rows.items():
-        for fname in ("S_mass", "S_mom_x", "S_mom_y", "D"):
+        for fname in _fields(2):
             assert r[fname][1] <= 1e-4, (name, fname, r[fname])
+    for fname in _fields(2):
+        assert rows["compensated"][fname][0] <= 1e-4, ("compensated", fname, rows["compensated"][fname])
     assert rows["mixed+guard"]["fold_steps"] > 0 and rows["mixed"]["fold_steps"] == 0
+
+
+def test_precision_report_cone(ctx):
+    """Reduced 3D cone (ABC + round jet, 32^3 cells, 32,768 seeds, 500 steps,
+    J-scaled kernel): the compensated form meets rel-L2 <= 1e-4 over all cells,
+    through the fold caustics the cone develops."""
+    wl = I.abc_jet_3d(scale=4)
+    forms = tuple(f for f in FORMS if f[0] in ("mixed", "compensated"))
+    rows, n_caustic = _precision_report(ctx, wl, forms)
+    assert n_caustic > 0
+    for fname in _fields(3):
+        assert rows["compensated"][fname][0] <= 1e-4, ("compensated", fname, rows["compensated"][fname])

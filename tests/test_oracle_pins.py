@@ -499,3 +499,28 @@ def test_psicell_conserves_totals():
         a = s.acc.astype(np.float64) / 0.01
         assert (Sm * V).sum() == pytest.approx(-(wi * a[:, 0])[act].sum(), rel=1e-12)
         assert np.allclose((Sv * V).sum(0), -(wi[:, None] * a[:, 1:])[act].sum(0), rtol=1e-12)
+
+
+def test_oracle_threads_do_not_change_results():
+    """The oracle's OpenMP loops (droplets of a step, cells of a deposit) compute
+    each droplet and cell with the same sequential code: one thread and all
+    threads give identical bits."""
+    wl = I.jet_vortex_2d(scale=16, nsteps=120, lpt_per_batch=0)
+    out = []
+    nthreads = O.threads()
+    try:
+        for t in (1, max(nthreads, 2)):
+            O.set_threads(t)
+            st = O.run(wl)
+            D = O.dep_struct(wl)
+            src = O.nw_deposit_celllist(D, st.x, st.J, st.acc, st.status, st.batch, wl.fla.n0, wl.fla.h0)
+            brute = O.nw_deposit(D, st.x, st.J, st.acc, st.status, st.batch, wl.fla.n0, wl.fla.h0)
+            out.append((st.y.copy(), st.acc.copy(), src, brute))
+    finally:
+        O.set_threads(nthreads)
+    (y1, a1, s1, b1), (y2, a2, s2, b2) = out
+    assert np.array_equal(y1, y2) and np.array_equal(a1, a2)
+    for u, v in zip(s1 + b1, s2 + b2):
+        assert np.array_equal(u, v)
+    for u, v in zip(s1, b1):   # pin P9 at this size too: cell list == brute force
+        assert np.array_equal(u, v)
