@@ -470,17 +470,18 @@ __device__ __forceinline__ void interp_x2(const AdvX2Args& a, const df* x, df* u
         base += (int64_t)i * mul;
         mul *= nn;
     }
-    df acc[D + D * D];
+    df g[D];   // 1 - f
 #pragma unroll
-    for (int q = 0; q < D + D * D; ++q) acc[q] = df_of(0.0f);
+    for (int q = 0; q < D; ++q) g[q] = df_of(1.0f) - f[q];
+    DotAcc acc[D + D * D];
 #pragma unroll
     for (int cnr = 0; cnr < (1 << D); ++cnr) {
-        df w = df_of(1.0f);
-        int64_t idx = base, m2 = 1;
+        df w = (cnr & 1) ? f[0] : g[0];
+        int64_t idx = base + (cnr & 1), m2 = nn;
 #pragma unroll
-        for (int q = 0; q < D; ++q) {
+        for (int q = 1; q < D; ++q) {
             const int bit = (cnr >> q) & 1;
-            w = w * (bit ? f[q] : df_of(1.0f) - f[q]);
+            w = w * (bit ? f[q] : g[q]);
             idx += bit * m2;
             m2 *= nn;
         }
@@ -491,12 +492,13 @@ __device__ __forceinline__ void interp_x2(const AdvX2Args& a, const df* x, df* u
             load4<float>(a.nodes + a.n_nodes * S, idx * (S / 4) + c, vl + 4 * c);
         }
 #pragma unroll
-        for (int q = 0; q < D + D * D; ++q) acc[q] = acc[q] + w * df{vh[q], vl[q]};
+        for (int q = 0; q < D + D * D; ++q)
+            acc[q] = cnr == 0 ? dot_first(w, df{vh[q], vl[q]}) : dot_add(acc[q], w, df{vh[q], vl[q]});
     }
 #pragma unroll
-    for (int q = 0; q < D; ++q) u[q] = acc[q];
+    for (int q = 0; q < D; ++q) u[q] = dot_value(acc[q]);
 #pragma unroll
-    for (int q = 0; q < D * D; ++q) G[q] = acc[D + q];
+    for (int q = 0; q < D * D; ++q) G[q] = dot_value(acc[D + q]);
 }
 
 // Right-hand side of Eqs. 3 and 8 in double-float.
@@ -515,11 +517,13 @@ __device__ __forceinline__ void rhs_x2(const df* y, const df* u, const df* G, df
         for (int i = 0; i < D; ++i)
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-                df gj = G[i * D] * J[k];
+                // grad u . J - W as one compensated sum
+                DotAcc gj = dot_first(G[i * D], J[k]);
 #pragma unroll
-                for (int j = 1; j < D; ++j) gj = gj + G[i * D + j] * J[j * D + k];
+                for (int j = 1; j < D; ++j) gj = dot_add(gj, G[i * D + j], J[j * D + k]);
+                gj = dot_add(gj, -W[i * D + k]);
                 f[2 * D + i * D + k] = W[i * D + k];
-                f[2 * D + D * D + i * D + k] = (gj - W[i * D + k]) * invSt;
+                f[2 * D + D * D + i * D + k] = dot_value(gj) * invSt;
             }
     }
 }
@@ -588,47 +592,39 @@ __device__ __forceinline__ int advance_x2_one(const AdvX2Args& a, int64_t i)
         const df r2c = a.delta * (tau + a.dt) + 1.0f;
         const df iSa = df_rcp(St0 * r2a), iSb = df_rcp(St0 * r2b), iSc = df_rcp(St0 * r2c);
 
+        // The four RK4 stages run as a loop (not unrolled): the double-float
+        // interpolation and right-hand side are long, and four inlined copies
+        // overflow the instruction cache.
         df k[NY], ks[NY], ys[NY];
-        // stage 1; the window sums use its u and v (left rectangle over substeps)
-        interp_x2<D>(a, y, u, G);
-        {
-            const float r2 = r2a.hi;
-            const float r = sqrtf(r2);
-            const float m = r2 * r;                   // m = r^3
-            const float mdot = 1.5f * delta32 * r;    // dm/dt with r r' = delta/2
-            const float iS = iSa.hi;
-            acc[0] = fmaf(h32, mdot, acc[0]);
 #pragma unroll
-            for (int q = 0; q < D; ++q)
-                acc[1 + q] = fmaf(h32, m * (u[q] - y[D + q]).hi * iS + mdot * y[D + q].hi, acc[1 + q]);
+        for (int q = 0; q < NY; ++q) ys[q] = y[q];
+#pragma unroll 1
+        for (int stage = 0; stage < 4; ++stage) {
+            interp_x2<D>(a, ys, u, G);
+            if (stage == 0) {   // window sums at the first stage (left rectangle over substeps)
+                const float r2 = r2a.hi;
+                const float r = sqrtf(r2);
+                const float m = r2 * r;                   // m = r^3
+                const float mdot = 1.5f * delta32 * r;    // dm/dt with r r' = delta/2
+                const float iS = iSa.hi;
+                acc[0] = fmaf(h32, mdot, acc[0]);
+#pragma unroll
+                for (int q = 0; q < D; ++q)
+                    acc[1 + q] = fmaf(h32, m * (u[q] - y[D + q]).hi * iS + mdot * y[D + q].hi, acc[1 + q]);
+            }
+            rhs_x2<D, FLA>(ys, u, G, stage == 0 ? iSa : (stage == 3 ? iSc : iSb), k);
+            // k1 + 2 k2 + 2 k3 + k4, and the next stage's state y + c k (c = dt/2, dt/2, dt)
+            const float wk = (stage == 1 || stage == 2) ? 2.0f : 1.0f;
+            const df c = stage == 2 ? a.dt : a.half;
+#pragma unroll
+            for (int q = 0; q < NY; ++q) ks[q] = stage == 0 ? k[q] : ks[q] + k[q] * wk;
+            if (stage < 3) {
+#pragma unroll
+                for (int q = 0; q < NY; ++q) ys[q] = df_axpy(c, k[q], y[q]);
+            }
         }
-        rhs_x2<D, FLA>(y, u, G, iSa, k);
 #pragma unroll
-        for (int q = 0; q < NY; ++q) {
-            ks[q] = k[q];
-            ys[q] = y[q] + a.half * k[q];
-        }
-        // stage 2
-        interp_x2<D>(a, ys, u, G);
-        rhs_x2<D, FLA>(ys, u, G, iSb, k);
-#pragma unroll
-        for (int q = 0; q < NY; ++q) {
-            ks[q] = ks[q] + k[q] * 2.0f;
-            ys[q] = y[q] + a.half * k[q];
-        }
-        // stage 3
-        interp_x2<D>(a, ys, u, G);
-        rhs_x2<D, FLA>(ys, u, G, iSb, k);
-#pragma unroll
-        for (int q = 0; q < NY; ++q) {
-            ks[q] = ks[q] + k[q] * 2.0f;
-            ys[q] = y[q] + a.dt * k[q];
-        }
-        // stage 4
-        interp_x2<D>(a, ys, u, G);
-        rhs_x2<D, FLA>(ys, u, G, iSc, k);
-#pragma unroll
-        for (int q = 0; q < NY; ++q) y[q] = y[q] + a.sixth * (ks[q] + k[q]);
+        for (int q = 0; q < NY; ++q) y[q] = df_axpy(a.sixth, ks[q], y[q]);
         // outflow: leaving [0,1]^dim ends the trajectory
         bool out = false;
 #pragma unroll

@@ -63,12 +63,13 @@ __device__ __forceinline__ df two_prod(float a, float b)
 __device__ __forceinline__ df operator-(df a) { return {-a.hi, -a.lo}; }
 
 // a + b: the exact sum of the high parts, the low parts added to its error,
-// and one renormalisation (two_sum, since cancellation can leave the error
-// term larger than the sum).
+// and one renormalisation.  Where the sum cancels, the error term can exceed
+// the sum and fast_two_sum's low part is then inexact by at most u times that
+// term: the result stays within u^2 (|a| + |b|) of a + b.
 __device__ __forceinline__ df operator+(df a, df b)
 {
     const df s = two_sum(a.hi, b.hi);
-    return two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
 }
 
 __device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
@@ -76,8 +77,52 @@ __device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
 __device__ __forceinline__ df operator+(df a, float b)
 {
     const df s = two_sum(a.hi, b);
-    return two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
 }
+
+// y + c k in one pass: the exact product of the high parts and the cross terms
+// added to the exact sum's error, one renormalisation.
+__device__ __forceinline__ df df_axpy(df c, df k, df y)
+{
+    const df p = two_prod(c.hi, k.hi);
+    const df s = two_sum(y.hi, p.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(y.lo, p.lo));
+    e = __fmaf_rn(c.hi, k.lo, __fmaf_rn(c.lo, k.hi, e));
+    return fast_two_sum(s.hi, e);
+}
+
+// Compensated dot product (Ogita, Rump and Oishi 2005, "Dot2"): the running
+// sum s of the rounded products of the high parts, with every rounding error
+// -- of the products (two_prod) and of the additions (two_sum) -- and the
+// cross terms with the low parts collected in e.  The result is as accurate
+// as a sum evaluated in twice the working precision.
+struct DotAcc {
+    float s, e;
+};
+
+__device__ __forceinline__ DotAcc dot_first(df a, df b)
+{
+    const df p = two_prod(a.hi, b.hi);
+    return {p.hi, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo))};
+}
+
+__device__ __forceinline__ DotAcc dot_add(DotAcc acc, df a, df b)
+{
+    const df p = two_prod(a.hi, b.hi);
+    const df s = two_sum(acc.s, p.hi);
+    float e = __fadd_rn(acc.e, __fadd_rn(s.lo, p.lo));
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    return {s.hi, e};
+}
+
+// acc + b (a df term added without a product)
+__device__ __forceinline__ DotAcc dot_add(DotAcc acc, df b)
+{
+    const df s = two_sum(acc.s, b.hi);
+    return {s.hi, __fadd_rn(acc.e, __fadd_rn(s.lo, b.lo))};
+}
+
+__device__ __forceinline__ df dot_value(DotAcc acc) { return fast_two_sum(acc.s, acc.e); }
 
 __device__ __forceinline__ df operator-(df a, float b) { return a + (-b); }
 
