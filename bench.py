@@ -1,31 +1,37 @@
 #!/usr/bin/env python
 """Benchmark of the FLA hot path on one GB300.
 
-Workload (the 512^2 planar-jet configuration): a 512 x 512 mesh on [0,1]^2, a
-Gaussian jet (centre speed 1, width 0.05) with 8 Lamb-Oseen vortices carried
-by it, 256 releases of 1,024 FLA seeds at the inlet over 1,000 RK4 steps of
-dt = 1e-3, St0 ~ U[0.2, 2] per release, d^2-law evaporation (delta = -0.2),
-the carrier re-sampled and the kernel-regression sources deposited every 10
-steps (100 deposits onto 262,144 cells), FP32 with FP64 det J.
+Headline workload (the largest single-GPU configuration): the 3D spray cone,
+a 128^3 mesh on [0,1]^3, ABC flow (1, 0.7, 0.43) at wavenumber 2 pi plus a
+round jet of radius 0.05, 2,097,152 FLA seeds on a volume-preserving lattice
+in a cone, St0 = 1, d^2-law evaporation (delta = -0.2), 500 RK4 steps of
+dt = 1e-3, the J-scaled anisotropic kernel truncated at 3 sigma, sources
+deposited every 10 steps (50 deposits onto 2,097,152 cells), in the
+compensated precision form (double-float trajectories and carrier, single-
+precision deposit, det J in double): the form that keeps the sources within
+rel-L2 1e-4 of the FP64 oracle over every cell, fold caustics included.
 
-One step = one whole run of the path over that input: 100 windows of
-{carrier sample, fused 10-step advance, cell keys, radix sort, bin starts,
-records, kernel-regression gather}.  The run is captured once in a CUDA graph
-and replayed; the cloud is reset to its seeds (device-to-device copy) and L2 is
-flushed (a 256 MB write) before each timed step, outside the step's events.
+One step = one whole run of the path over that input: per window {carrier
+sample (once for a steady carrier), fused 10-step advance, cell keys, radix
+sort, bin starts, records, kernel-regression gather}.  The run is captured
+once in a CUDA graph and replayed; the cloud is reset to its seeds (device-to-
+device copy) and L2 is flushed (a 256 MB write) before each timed step,
+outside the step's events.
 
-Reported: source-term cells/s (cells x deposits / step time) as the headline,
-droplet-steps/s from the device's own counter, the PSI-CELL reference run
-(2^24 parcels, same flow) as a separately timed leg, per-phase CUDA-event
-times from an instrumented eager run, the roofline of the dominant kernel, the
-end-to-end number with host buffers, and the FP64 CPU oracle on a bounded
-sample as the CPU baseline.
+Reported beside the headline: droplet-steps/s from the device's own counter;
+per-phase CUDA-event times of an instrumented eager run and a roofline entry
+per phase; the end-to-end number through the C-ABI with pinned host buffers;
+the single-precision forms of the same workload (their cells/s and, from the
+CPU-baseline leg, the rel-L2 each form reaches on the reduced configuration);
+the planar-jet and Taylor-Green configurations as secondary legs (the jet with
+its 2^24-parcel PSI-CELL reference); the 64-cloud batched leg; and the FP64 CPU
+oracle on a bounded sample, on one host core and on all of them.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
-import math
 import os
 import subprocess
 import sys
@@ -39,64 +45,87 @@ sys.path.insert(0, ROOT)
 
 METRIC = "source-term cells/s (kernel-regression deposit, with droplet-steps/s) at rel-L2 <= 1e-4 vs FP64 oracle"
 UNIT = "cells/s"
+# name: (description, headline form)
 WORKLOADS = {
-    # name: (description, dtype name, has PSI-CELL reference)
+    "abc_jet_3d": ("abc_jet_3d: 128^3 cells, 2,097,152 FLA seeds in a cone, ABC + round jet, 500 RK4 steps, "
+                   "50 deposits, J-scaled anisotropic kernel (3 sigma)", "compensated"),
     "jet_vortex_2d": ("jet_vortex_2d: 512^2 cells, 262,144 FLA seeds (256 releases x 1,024), 1,000 RK4 steps, "
-                      "100 deposits", "F32", True),
-    "taylor_green_2d": ("taylor_green_2d: 64^2 cells, 4,096 FLA seeds, 200 RK4 steps, 20 deposits, FP64", "F64", True),
-    "abc_jet_3d": ("abc_jet_3d: 128^3 cells, 2,097,152 FLA seeds in a cone, 500 RK4 steps, 50 deposits, "
-                   "J-scaled anisotropic kernel", "F32", False),
+                      "100 deposits, spherical kernel", "compensated"),
+    "taylor_green_2d": ("taylor_green_2d: 64^2 cells, 4,096 FLA seeds, 200 RK4 steps, 20 deposits, spherical kernel",
+                        "fp64"),
 }
-WORKLOAD = WORKLOADS["jet_vortex_2d"][0]
+# The precision forms: (cloud dtype name, deposit precision, fold guard, learned correction)
+FORMS = {
+    "compensated": ("F32X2", "PREC_MIXED", False, False),
+    "mixed": ("F32", "PREC_MIXED", False, False),
+    "plain": ("F32", "PREC_PLAIN", False, False),
+    "fold": ("F32", "PREC_MIXED", True, False),
+    "learned": ("F32", "PREC_MIXED", False, True),
+    "fp64": ("F64", "PREC_MIXED", False, False),
+}
+FORM_TEXT = {
+    "compensated": "double-float trajectories and carrier nodes, single-precision deposit, det J and n in FP64",
+    "mixed": "FP32 trajectories and kernels, det J and n in FP64 where det J cancels",
+    "plain": "FP32 throughout",
+    "fold": "mixed + FP64 J, W while |det J| < 1e-2",
+    "learned": "mixed + tensor-core bandwidth MLP fused into the records (zero last layer: same h)",
+    "fp64": "FP64 throughout",
+}
 
 
-def make_workload(name, with_lpt):
+def make_workload(name, with_lpt=False, scale=1):
     from paper_2512_20829_gb300 import inputs as I
     if name == "jet_vortex_2d":
-        return I.jet_vortex_2d(lpt_per_batch=65_536 if with_lpt else 0)
+        return I.jet_vortex_2d(scale=scale, lpt_per_batch=65_536 if with_lpt else 0)
     if name == "taylor_green_2d":
-        wl = I.taylor_green_2d()
+        wl = I.taylor_green_2d(scale=scale)
         if not with_lpt:
             wl.lpt = None
         return wl
-    return I.abc_jet_3d()
+    return I.abc_jet_3d(scale=scale)
 
-# Floating-point operations per droplet step of the fused advance, counted from the
-# kernel's operation list (FMA = 2).  2D: four stages of bilinear interpolation of 6
-# node values (58) and the right-hand side (28), the RK4 combinations (156), St(t)
-# (13) and the window sums (20).  3D: trilinear interpolation of 12 values (217) and
-# the right-hand side (78) per stage, combinations (312), St(t) and sums (40).
+
+# Floating-point operations per droplet step of the advance's algorithm, counted from the
+# single-precision kernel's operation list (FMA = 2).  2D: four stages of bilinear
+# interpolation of 6 node values (58) and the right-hand side (28), the RK4 combinations
+# (156), St(t) (13) and the window sums (20).  3D: trilinear interpolation of 12 values
+# (217) and the right-hand side (78) per stage, combinations (312), St(t) and sums (40).
+# The compensated form performs the same algorithm in double-float arithmetic (about
+# 6.5 FP32 instructions per algorithmic operation); its roofline is taken on these
+# algorithmic operations against the FP32 peak.
 FLOPS_PER_STEP = {2: 533, 3: 1532}
-# Operations per (cell, droplet) pair inside the truncated kernel, the paper's
-# form of the weight (one ex2 per pair besides these).  2D spherical: 2 differences,
-# r^2 (3), exponent (1), prefactor (1), 4 FMA sums (8).  3D spherical: 3 differences,
-# r^2 (5), exponent and prefactor (2), sums (9).  3D J-scaled: 3 differences,
-# P d (15), d.(P d) (5), exponent (2), sums (9).
+# Operations per (cell, droplet) pair inside the truncated kernel, the paper's form of the
+# weight (one ex2 per pair besides these).  2D spherical: 2 differences, r^2 (3), exponent
+# (1), prefactor (1), 4 FMA sums (8).  3D spherical: 3 differences, r^2 (5), exponent and
+# prefactor (2), sums (9).  3D J-scaled: 3 differences, P d (15), d.(P d) (5), exponent
+# (2), sums (9).
 FLOPS_PER_PAIR = {(2, 0): 15, (3, 0): 19, (2, 1): 24, (3, 1): 34}
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64, per the hardware description
-# DRAM bytes (read + write) of one k_gather2d_items launch from an ncu capture
-# (profiles/gather2d_jet512_window81.md); None once the kernel changes.
-GATHER_TRAFFIC = {
-    (2, 0, False): (6245888, "ncu dram__bytes_read+write of k_gather2d_items, jet 512^2 deposit 81"),
-}
+SM_COUNT, FP32_LANES, MUFU_LANES, SM_MAX_MHZ = 152, 128, 16, 2070.0
+# Carrier: double-precision operations per node, counted from the evaluation (the
+# double-float form samples in FP64; a steady carrier is sampled once per run).
+# Jet + 8 vortices x 3 periodic images: ~22 per image (far field, no exponential) + jet.
+# ABC + round jet: ~40 plus six sin/cos and one exponential.
+CARRIER_FLOPS_PER_NODE = {"jet_vortex_2d": 24 * 22 + 12, "abc_jet_3d": 60, "taylor_green_2d": 30}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="jet_vortex_2d",
-                    help="configuration to run (the headline metric is quoted on jet_vortex_2d)")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="abc_jet_3d",
+                    help="configuration to run (the headline is the largest single-GPU one, abc_jet_3d)")
+    ap.add_argument("--form", choices=sorted(FORMS), default=None,
+                    help="precision form of the headline path (default: the workload's form that meets 1e-4)")
     ap.add_argument("--no-psicell", action="store_true", help="skip the PSI-CELL reference leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-variants", action="store_true", help="skip the other precision forms")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the other configurations")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-clouds leg")
     ap.add_argument("--clocks-dir", default=tempfile.gettempdir(),
                     help="where the nvidia-smi clock samples of the timed region are written")
-    ap.add_argument("--no-variants", action="store_true", help="skip the other precision forms")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched-clouds leg")
-    ap.add_argument("--form", choices=["mixed", "plain", "fold", "learned"], default="mixed",
-                    help="precision form of the headline path (the default is the mixed form)")
     ap.add_argument("--profile-batch", action="store_true",
                     help="one run of the 64-cloud batch with plain launches (no graph), for external profilers")
     ap.add_argument("--profile-only", action="store_true",
@@ -108,82 +137,77 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
-# --------------------------------------------------------------------------- clocks
-
 class ClockSampler:
-    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
-
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
 
     def __init__(self, device_index: int, directory: str):
         self.dev = device_index
+        self.path = os.path.join(directory, f"bench_clocks_{os.getpid()}.csv")
         self.proc = None
-        self.path = os.path.join(directory, f"clocks_rank{device_index}.csv")
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
-                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}",
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
         except Exception:
             self.proc = None
 
     def stop(self):
         if self.proc is None:
-            return None
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        self.f.close()
-        rows = []
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in open(self.path):
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 7:
                 continue
             try:
-                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
             except ValueError:
                 continue
-        if not rows:
-            return None
-        sm = [r[0] for r in rows]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower().startswith("active")})
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(r[1] for r in rows)),
-                "samples": len(rows), "reasons": reasons}
+            for name, v in zip(names, p[3:7]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(np.max(smax)), "samples": len(sm),
+                "reasons": sorted(reasons)}
 
 
 # --------------------------------------------------------------------------- GPU path
 
-class JetPath:
+class RunPath:
     """Device buffers and the issue order of one whole run of a workload."""
 
-    def __init__(self, ctx, wl, fla, with_fla=True, with_lpt=False, dtype=None, precision=None,
-                 fold_guard=False, mlp=None):
-        import torch
-        self.fla, self.ctx, self.wl = fla, ctx, wl
-        self.dtype = fla.F32 if dtype is None else dtype
-        self.precision = fla.PREC_MIXED if precision is None else precision
+    def __init__(self, ctx, wl, fla, form, with_fla=True, with_lpt=False):
+        dname, pname, fold_guard, learned = FORMS[form]
+        self.fla, self.ctx, self.wl, self.form = fla, ctx, wl, form
+        self.dtype = getattr(fla, dname)
+        self.precision = getattr(fla, pname)
         self.m = fla.mesh(wl.dim, wl.n_cells_axis)
         self.desc = fla.carrier_desc(wl.carrier)
         self.nodes = fla.nodes_buffer(self.m, self.dtype)
-        self.mlp = mlp
+        self.mlp = fla.LearnedCorrection(ctx, fla.init_mlp_params(0, 0.5, zero_last=True)) if learned else None
         self.cfg = fla.deposit_cfg(wl.kernel, wl.h_min, wl.h_max, wl.window * wl.dt, wl.p, precision=self.precision,
-                                   mlp=mlp)
+                                   mlp=self.mlp)
         self.cloud = fla.DeviceCloud.from_seeds(wl.fla, wl.dim, wl.delta, wl.dt, self.dtype) if with_fla else None
-        if self.cloud is not None and self.dtype == fla.F32 and self.precision == fla.PREC_MIXED and fold_guard:
+        if self.cloud is not None and fold_guard:
             self.cloud.enable_fold()   # double-precision J, W near fold caustics
-        self.lpt = fla.DeviceCloud.from_seeds(wl.lpt, wl.dim, wl.delta, wl.dt, self.dtype) if with_lpt else None
+        ldt = fla.F64 if self.dtype == fla.F64 else fla.F32
+        self.lpt = fla.DeviceCloud.from_seeds(wl.lpt, wl.dim, wl.delta, wl.dt, ldt) if with_lpt else None
         n = max(c.n for c in (self.cloud, self.lpt) if c is not None)
         self.ws = fla.aligned_ws(fla.workspace(self.m, self.dtype, wl.kernel, n))
         self.out = fla.SourceFields(self.m, self.dtype) if with_fla else None
-        self.psi = fla.PsicellFields(self.m, self.dtype) if with_lpt else None
+        self.psi = fla.PsicellFields(self.m, ldt) if with_lpt else None
+        self.lnodes = fla.nodes_buffer(self.m, ldt) if (with_lpt and ldt != self.dtype) else None
         self.pristine = [(c.state.clone(), c.meta.clone()) for c in (self.cloud, self.lpt) if c is not None]
 
     def clouds(self):
@@ -199,14 +223,215 @@ class JetPath:
         fla, wl, m = self.fla, self.wl, self.m
         for s in range(0, wl.nsteps, wl.window):
             if s == 0 or not wl.carrier.steady:   # a steady carrier is sampled once per run
-                fla.carrier_sample(self.ctx, self.desc, m, 0.0 if wl.carrier.steady else s * wl.dt, self.dtype,
-                                   self.nodes)
-            for c in self.clouds():
-                fla.advance(self.ctx, c, m, self.nodes, s, wl.window, wl.dt, reset_acc=True)
+                t = 0.0 if wl.carrier.steady else s * wl.dt
+                if self.cloud is not None:
+                    fla.carrier_sample(self.ctx, self.desc, m, t, self.dtype, self.nodes)
+                if self.lnodes is not None or (self.cloud is None and self.lpt is not None):
+                    ln = self.lnodes if self.lnodes is not None else self.nodes
+                    fla.carrier_sample(self.ctx, self.desc, m, t, self.lpt.dtype, ln)
+            if self.cloud is not None:
+                fla.advance(self.ctx, self.cloud, m, self.nodes, s, wl.window, wl.dt, reset_acc=True)
+            if self.lpt is not None:
+                ln = self.lnodes if self.lnodes is not None else self.nodes
+                fla.advance(self.ctx, self.lpt, m, ln, s, wl.window, wl.dt, reset_acc=True)
             if self.cloud is not None:
                 fla.deposit_sources(self.ctx, self.cloud, m, self.cfg, self.out, self.ws)
             if self.lpt is not None:
                 fla.psicell(self.ctx, self.lpt, m, wl.window * wl.dt, self.psi, self.ws)
+
+
+def capture(path):
+    import torch
+    path.reset()
+    path.issue()                     # eager warm-up (sets kernel attributes once)
+    torch.cuda.synchronize()
+    path.reset()
+    torch.cuda.synchronize()
+    path.ctx.profile(False, reset=True)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        path.issue()
+    torch.cuda.synchronize()
+    launches = sum(v["launches"] for v in path.ctx.profile_read().values())
+    return g, launches
+
+
+def timed_replays(path, g, steps, flush):
+    import torch
+    times = []
+    for _ in range(steps):
+        path.reset()
+        flush.add_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.replay()
+        b.record()
+        times.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in times]
+
+
+def instrumented_run(path):
+    """One eager run with per-phase CUDA events; returns the phase table and the
+    device counters of that run."""
+    import torch
+    ctx = path.ctx
+    path.reset()
+    torch.cuda.synchronize()
+    ctx.sync_status(reset=True)
+    ctx.profile(True, reset=True)
+    path.issue()
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False, reset=True)
+    st = ctx.sync_status(reset=True)
+    return prof, st
+
+
+# --------------------------------------------------------------------------- rooflines
+
+def source_sha(*names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2512_20829_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel_key):
+    """DRAM bytes per full-size launch from profiles/traffic.json, if that figure was
+    taken from the kernel's current source (the file records the source hash of the
+    translation units it was measured on); None otherwise."""
+    try:
+        tab = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except Exception:
+        return None, None
+    e = tab.get(kernel_key)
+    if not e:
+        return None, None
+    if e.get("source_sha") != source_sha(*e["sources"]):
+        return None, f"stale: {kernel_key} changed since the capture"
+    return e["bytes_per_launch"], e["basis"]
+
+
+def rooflines(prof, st, wl, form, peaks, clocks):
+    """One entry per phase: achieved algorithmic work per launch over the phase's
+    average launch time (CUDA events), against the binding peak."""
+    dim, kernel = wl.dim, wl.kernel
+    f64 = form == "fp64"
+    sm = SM_MAX_MHZ
+    fp32_peak = SM_COUNT * FP32_LANES * 2 * sm * 1e6 / 1e12           # TFLOP/s
+    mufu_pairs = SM_COUNT * MUFU_LANES * sm * 1e6                      # ex2 per second
+    hbm = peaks.get("hbm_gbs")
+    out = {}
+    deposits = max(prof["records"]["calls"], 1)
+    binned = st.deposited / deposits                                    # droplets binned per deposit
+    n = wl.fla.n
+    nn = wl.n_cells_axis + 1
+    nodes = nn ** dim
+    planes = (2 * dim + 2 * dim * dim + 1 + dim + 3) // 4
+    elem = 8 if f64 else 4
+    for name, p in prof.items():
+        if not p["calls"] or p["ms"] <= 0:
+            continue
+        per_call = p["ms"] / p["calls"]
+        e = {"ms_per_run": round(p["ms"], 4), "launches_per_run": p["launches"]}
+        if name == "advance":
+            flops = st.droplet_steps * FLOPS_PER_STEP[dim] / p["calls"]
+            ach = flops / (per_call * 1e-3) / 1e12
+            peak = FP64_PEAK_TFLOPS if f64 else fp32_peak
+            e.update(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                     work=f"{FLOPS_PER_STEP[dim]} algorithmic flop per droplet step x "
+                          f"{st.droplet_steps / p['calls']:.4g} droplet steps per launch")
+        elif name == "gather":
+            fpp = FLOPS_PER_PAIR[(dim, kernel)]
+            flops = st.pairs / p["calls"] * fpp
+            ach = flops / (per_call * 1e-3) / 1e12
+            peak = FP64_PEAK_TFLOPS if f64 else min(fp32_peak, mufu_pairs * fpp / 1e12)
+            e.update(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                     work=f"{fpp} flop per pair inside the truncation x {st.pairs / p['calls']:.4g} pairs per deposit")
+        elif name == "carrier":
+            per_node = next((v for k, v in CARRIER_FLOPS_PER_NODE.items() if wl.name.startswith(k)), 40)
+            flops = per_node * nodes
+            ach = flops / (per_call * 1e-3) / 1e12
+            fp64_eval = form in ("compensated", "fp64")
+            peak = FP64_PEAK_TFLOPS if fp64_eval else fp32_peak
+            e.update(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                     work=f"analytic carrier, {flops / nodes:.0f} flop per node x {nodes} nodes "
+                          f"({'FP64' if fp64_eval else 'FP32'} evaluation)")
+        else:
+            # HBM phases: algorithmic bytes (each value moved once)
+            if name == "keys":
+                byts = n * (16 + 4 + 4)                       # position plane, meta, key
+            elif name == "sort":
+                byts = n * 16                                 # key and index read and written once
+            elif name == "bins":
+                byts = binned * 4 + wl.n_cells * 4            # sorted keys read, bin starts written
+            elif name == "records":
+                rec = 32 if (dim, kernel) == (2, 0) else (64 if (dim, kernel) == (3, 1) else 48)
+                lo = (2 if dim == 3 else 1) * 16 if form == "compensated" else 0   # J low parts
+                byts = binned * (planes * 16 * (2 if f64 else 1) + lo + 8 + rec)
+            elif name == "psicell":
+                byts = n * 20 + wl.n_cells * (4 + 4 * (1 + dim))
+            else:
+                continue
+            gbs = byts / (per_call * 1e-3) / 1e9
+            e.update(bound="hbm", achieved=gbs, peak=hbm, unit="GB/s", frac=gbs / hbm if hbm else None,
+                     work=f"{byts / 1e6:.4g} MB algorithmic per call")
+        out[name] = e
+    return out
+
+
+# --------------------------------------------------------------------------- legs
+
+def max_over_ranks(value: float, world: int, device: str = "cuda") -> float:
+    """The largest of the ranks' values (all ranks receive it); world 1 returns value."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(world: int, cells: int, deposits: int, steps: int, total_ms: float) -> float:
+    """Whole-job cells/s: every rank deposits its own replica's cells each window,
+    timed by the slowest rank."""
+    return world * cells * deposits * steps / (total_ms * 1e-3)
+
+
+def time_form(ctx, fla, wl, form, flush, reps=3, with_lpt=False, with_fla=True):
+    """Graph-replayed whole runs of one form; median ms, device counters per run."""
+    import torch
+    p = RunPath(ctx, wl, fla, form, with_fla=with_fla, with_lpt=with_lpt)
+    g, launches = capture(p)
+    g.replay()
+    torch.cuda.synchronize()
+    ctx.sync_status(reset=True)
+    t = timed_replays(p, g, reps, flush)
+    st = ctx.sync_status(reset=True)
+    ms = float(np.median(t))
+    res = {"ms_per_run": round(ms, 4), "launches_per_run": launches,
+           "droplet_steps_per_run": st.droplet_steps / reps}
+    del g
+    return p, ms, res
+
+
+def reduced_outputs(ctx, fla, wl_small, forms):
+    """Final sources of each form on the reduced configuration (the CPU baseline's sample)."""
+    import torch
+    outs = {}
+    for form in forms:
+        p = RunPath(ctx, wl_small, fla, form)
+        p.reset()
+        p.issue()
+        torch.cuda.synchronize()
+        outs[form] = (p.out.s_mass.double().cpu().numpy(), p.out.s_mom.double().cpu().numpy().T,
+                      p.out.dsum.double().cpu().numpy())
+        del p
+    return outs
 
 
 def batch_leg(ctx, fla, I, flush, steps):
@@ -239,7 +464,7 @@ def batch_leg(ctx, fla, I, flush, steps):
     del b
     torch.cuda.empty_cache()
     # the same clouds through the per-cloud calls
-    paths = [JetPath(ctx, wl, fla, with_fla=True, dtype=fla.F32) for wl in wls]
+    paths = [RunPath(ctx, wl, fla, "mixed") for wl in wls]
 
     class _All:
         def __init__(self, ps):
@@ -254,110 +479,17 @@ def batch_leg(ctx, fla, I, flush, steps):
                 p.issue()
     allp = _All(paths)
     g, launches = capture(allp)
-    ut = []
-    for _ in range(steps):
-        allp.reset()
-        flush.add_(1.0)
-        torch.cuda.synchronize()
-        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ea.record()
-        g.replay()
-        eb.record()
-        torch.cuda.synchronize()
-        ut.append(ea.elapsed_time(eb))
+    ut = timed_replays(allp, g, steps, flush)
     unbatched = float(np.median(ut))
     del g, paths, allp
     torch.cuda.empty_cache()
     cells = sum(w.n_cells for w in wls)
     return {"workload": f"{len(wls)} clouds (seed 4): {sum(w.fla.n for w in wls):,} seeds, 1e3-5e5 per cloud, "
-                        f"2D 32^2-256^2 spherical / 3D 32^3-64^3 J-scaled, {windows} windows of 10 steps",
+                        f"2D 32^2-256^2 spherical / 3D 32^3-64^3 J-scaled, {windows} windows of 10 steps, mixed form",
             "cells": cells, "ms_per_run": round(batched, 4), "cells_per_s": cells * windows / (batched * 1e-3),
             "unbatched_ms_per_run": round(unbatched, 4), "speedup_vs_unbatched": round(unbatched / batched, 3),
             "launches_per_run": tun["launches_per_window"] * windows, "unbatched_launches_per_run": launches,
             "tuning": tun}
-
-
-def capture(path):
-    import torch
-    path.reset()
-    path.issue()                     # eager warm-up (sets kernel attributes once)
-    torch.cuda.synchronize()
-    path.reset()
-    torch.cuda.synchronize()
-    path.ctx.profile(False, reset=True)
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
-        path.issue()
-    torch.cuda.synchronize()
-    launches = sum(v["launches"] for v in path.ctx.profile_read().values())
-    return g, launches
-
-
-def timed_replays(path, g, steps, flush, events=True):
-    import torch
-    times = []
-    for _ in range(steps):
-        path.reset()
-        flush.add_(1)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        g.replay()
-        b.record()
-        times.append((a, b))
-    torch.cuda.synchronize()
-    return [a.elapsed_time(b) for a, b in times]
-
-
-def roofline_entry(phase_name, prof, peaks, status_pairs, droplet_steps_per_run, dim, kernel, f64):
-    """Roofline of the dominant phase from the instrumented run's CUDA-event times
-    (one call = the phase's kernel launches for one window)."""
-    p = prof[phase_name]
-    calls = max(p["calls"], 1)
-    ms_per_call = p["ms"] / calls
-    sm_max = 2070.0
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s at the maximum SM clock
-    mufu_pairs = 152 * 16 * sm_max * 1e6                     # ex2 per second
-    if phase_name == "advance":
-        flops = droplet_steps_per_run * FLOPS_PER_STEP[dim] / calls
-        ach = flops / (ms_per_call * 1e-3) / 1e12
-        peak = FP64_PEAK_TFLOPS if f64 else fp32_peak
-        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "kernel": "k_advance",
-                "peak_basis": ("GB300 FP64 rate (derived)" if f64 else
-                               "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived, max clock)")}
-    if phase_name == "gather":
-        fpp = FLOPS_PER_PAIR[(dim, kernel)]
-        flops = status_pairs / calls * fpp
-        ach = flops / (ms_per_call * 1e-3) / 1e12
-        peak = FP64_PEAK_TFLOPS if f64 else min(fp32_peak, mufu_pairs * fpp / 1e12)
-        traffic = GATHER_TRAFFIC.get((dim, kernel, f64))
-        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": traffic[0] if traffic else None,
-                "traffic_basis": traffic[1] if traffic else None,
-                "kernel": "kernel-regression gather (all launches of one deposit)",
-                "peak_basis": ("GB300 FP64 rate (derived)" if f64 else
-                               f"min(FP32 152x128x2, MUFU ex2 152x16 per pair x {fpp} flops) at 2070 MHz (derived)")}
-    # HBM-bound phases: algorithmic bytes
-    return {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s", "frac": None,
-            "traffic": None, "kernel": phase_name}
-
-
-def max_over_ranks(value: float, world: int, device: str = "cuda") -> float:
-    """The largest of the ranks' values (all ranks receive it); world 1 returns value."""
-    if world <= 1:
-        return float(value)
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def weak_value(world: int, cells: int, deposits: int, steps: int, total_ms: float) -> float:
-    """Whole-job cells/s: every rank deposits its own replica's cells each window,
-    timed by the slowest rank."""
-    return world * cells * deposits * steps / (total_ms * 1e-3)
 
 
 def run_ours(args):
@@ -375,18 +507,12 @@ def run_ours(args):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    desc, dname, has_psi = WORKLOADS[args.workload]
-    dtype = getattr(fla, dname)
-    wl = make_workload(args.workload, has_psi and not args.no_psicell)
+    desc, default_form = WORKLOADS[args.workload]
+    form = args.form or default_form
+    wl = make_workload(args.workload)
     cells = wl.n_cells
     deposits = wl.nsteps // wl.window
 
-    form_mlp = None
-    if args.form == "learned":
-        form_mlp = fla.LearnedCorrection(ctx, fla.init_mlp_params(0, 0.5, zero_last=True))
-    path = JetPath(ctx, wl, fla, with_fla=True, dtype=dtype,
-                   precision=fla.PREC_PLAIN if args.form == "plain" else fla.PREC_MIXED,
-                   fold_guard=args.form == "fold", mlp=form_mlp)
     if args.profile_batch:
         b = fla.Batch(ctx, I.batch_clouds())
         b.set_tuning(128, 4, 1)
@@ -395,13 +521,14 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"profile_batch": True, "launches_per_window": b.tuning()["launches_per_window"]}))
         return
+    path = RunPath(ctx, wl, fla, form)
     if args.profile_only:
         # one eager run of the whole path (no graph), for external profilers
         path.reset()
         path.issue()
         torch.cuda.synchronize()
         if rank == 0:
-            print(json.dumps({"profile_only": True, "workload": desc}))
+            print(json.dumps({"profile_only": True, "workload": desc, "form": form}))
         return
     g, launches_per_run = capture(path)
     flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device="cuda")
@@ -428,20 +555,17 @@ def run_ours(args):
     droplet_steps_per_run = st.droplet_steps / args.steps
     value = weak_value(world, cells, deposits, args.steps, total_ms)
 
-    # ---------------- instrumented eager run: per-phase CUDA-event times
-    path.reset()
-    ctx.sync_status(reset=True)
-    ctx.profile(True, reset=True)
-    path.issue()
-    torch.cuda.synchronize()
-    prof = ctx.profile_read()
-    ctx.profile(False, reset=True)
-    stp = ctx.sync_status(reset=True)
-    dominant = max(prof, key=lambda k: prof[k]["ms"])
-    roof = roofline_entry(dominant, prof, peaks, stp.pairs, droplet_steps_per_run, wl.dim, wl.kernel,
-                          dtype == fla.F64)
-    phases = {k: {"ms_per_run": round(v["ms"], 4), "launches_per_run": v["launches"]} for k, v in prof.items()
-              if v["calls"]}
+    # ---------------- instrumented eager run: per-phase CUDA-event times and rooflines
+    prof, stp = instrumented_run(path)
+    roofs = rooflines(prof, stp, wl, form, peaks, clocks)
+    dominant = max(roofs, key=lambda k: roofs[k]["ms_per_run"])
+    roof = {k: roofs[dominant][k] for k in ("bound", "achieved", "peak", "unit", "frac")}
+    dom_key = {"advance": "advance_x2" if form == "compensated" else "advance", "gather": "gather"}.get(dominant,
+                                                                                                     dominant)
+    traffic, basis = measured_traffic(f"{dom_key}:{args.workload}")
+    roof.update(traffic=traffic, traffic_basis=basis, kernel=dominant,
+                peak_basis=("measured HBM copy (MEASURED_PEAKS.json)" if roof["bound"] == "hbm" else
+                            "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived, max clock)"))
 
     # ---------------- end to end: pinned host seeds in, final source fields out
     host_state = path.pristine[0][0].cpu().pin_memory()
@@ -451,7 +575,7 @@ def run_ours(args):
     h2d = host_state.numel() * host_state.element_size() + host_meta.numel() * host_meta.element_size()
     d2h = sum(t.numel() * t.element_size() for t in out_host)
     e2e = []
-    for k in range(max(2, args.steps // 2)):
+    for _ in range(max(2, args.steps // 2)):
         flush.add_(1)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -465,79 +589,90 @@ def run_ours(args):
         torch.cuda.synchronize()
         e2e.append(a.elapsed_time(b))
     e2e_ms = float(np.mean(e2e))
+    del g, path
+    torch.cuda.empty_cache()
 
-    # ---------------- the other precision forms of the same path, timed the same way:
-    # plain single precision (det J and n in FP32) and mixed with the advance's fold guard
-    precision = None
-    if dtype == fla.F32 and not args.no_variants:
-        variants = {}
-        learned = None
-        if wl.kernel == fla.KERNEL_ISO:
-            # zero last layer: the same h as the plain method, so the difference is the network's cost
-            learned = fla.LearnedCorrection(ctx, fla.init_mlp_params(0, 0.5, zero_last=True))
-        forms = [("plain_fp32", fla.PREC_PLAIN, False, None), ("mixed_fold_guard", fla.PREC_MIXED, True, None)]
-        if learned is not None:
-            forms.append(("learned_tensor_core_mlp", fla.PREC_MIXED, False, learned))
-        for name, prec, guard, mlp in forms:
-            vp = JetPath(ctx, wl, fla, with_fla=True, dtype=dtype, precision=prec, fold_guard=guard, mlp=mlp)
-            vg, _ = capture(vp)
-            vg.replay()
-            torch.cuda.synchronize()
-            ctx.sync_status(reset=True)
-            vt = timed_replays(vp, vg, 3, flush)
-            vst = ctx.sync_status(reset=True)
-            variants[name] = {"ms_per_step": round(float(np.mean(vt)), 4),
-                              "cells_per_s": cells * deposits / (float(np.mean(vt)) * 1e-3),
-                              "fold_steps_per_run": vst.fold_steps / 3}
-            del vg, vp
-        precision = {"headline": "mixed: FP32 trajectories and kernels, det J and n in FP64 where det J cancels",
-                     "variants": variants}
+    # ---------------- the other precision forms of the same workload
+    variants = {}
+    if rank == 0 and not args.no_variants and form != "fp64":
+        names = ["compensated", "mixed", "plain"]
+        if wl.dim == 2 and wl.kernel == fla.KERNEL_ISO:
+            names += ["fold", "learned"]
+        for name in names:
+            if name == form:
+                continue
+            p, ms, res = time_form(ctx, fla, wl, name, flush)
+            res.update(form=FORM_TEXT[name], cells_per_s=cells * deposits / (ms * 1e-3))
+            variants[name] = res
+            del p
+            torch.cuda.empty_cache()
 
-    # ---------------- PSI-CELL reference leg (2^24 parcels, same flow, same windows)
-    psi = None
-    if not args.no_psicell and wl.lpt is not None and rank == 0:
-        del g
-        ppath = JetPath(ctx, wl, fla, with_fla=False, with_lpt=True, dtype=dtype)
-        pg, plaunch = capture(ppath)
-        pg.replay()
-        torch.cuda.synchronize()
-        ctx.sync_status(reset=True)
-        pt = timed_replays(ppath, pg, 2, flush)
-        pst = ctx.sync_status(reset=True)
-        pms = float(np.mean(pt))
-        psi = {"parcels": wl.lpt.n, "ms_per_run": round(pms, 3),
-               "cells_per_s": cells * deposits / (pms * 1e-3),
-               "parcel_steps_per_s": pst.droplet_steps / 2 / (pms * 1e-3),
-               "gpu_launches_per_run": plaunch,
-               "fla_speedup_vs_psicell": round(pms / ms_per_step, 2)}
-        del pg, ppath
+    # ---------------- the other configurations
+    secondary = {}
+    if rank == 0 and not args.no_secondary:
+        for wname in WORKLOADS:
+            if wname == args.workload:
+                continue
+            w2 = make_workload(wname, with_lpt=(wname == "jet_vortex_2d" and not args.no_psicell))
+            f2 = WORKLOADS[wname][1]
+            leg = {"workload": WORKLOADS[wname][0], "forms": {}}
+            for name in ([f2, "mixed"] if f2 != "fp64" else [f2]):
+                p, ms, res = time_form(ctx, fla, w2, name, flush)
+                pr, sp = instrumented_run(p)
+                res.update(form=FORM_TEXT[name], cells_per_s=w2.n_cells * (w2.nsteps // w2.window) / (ms * 1e-3),
+                           phases={k: round(v["ms"], 4) for k, v in pr.items() if v["calls"]})
+                if name == f2:
+                    res["rooflines"] = rooflines(pr, sp, w2, name, peaks, clocks)
+                leg["forms"][name] = res
+                del p
+                torch.cuda.empty_cache()
+            if w2.lpt is not None:
+                pp, pms, pres = time_form(ctx, fla, w2, "mixed", flush, reps=2, with_lpt=True, with_fla=False)
+                leg["psicell_reference"] = {
+                    "parcels": w2.lpt.n, "ms_per_run": round(pms, 3),
+                    "cells_per_s": w2.n_cells * (w2.nsteps // w2.window) / (pms * 1e-3),
+                    "parcel_steps_per_s": pres["droplet_steps_per_run"] / (pms * 1e-3),
+                    "gpu_launches_per_run": pres["launches_per_run"],
+                    "fla_speedup_vs_psicell": round(pms / leg["forms"][f2]["ms_per_run"], 2)}
+                del pp
+                torch.cuda.empty_cache()
+            secondary[wname] = leg
 
     batch = None
-    if rank == 0 and not args.no_batch and args.workload == "jet_vortex_2d":
-        batch = batch_leg(ctx, fla, I, flush, max(3, args.steps // 2))
+    if rank == 0 and not args.no_batch:
+        batch = batch_leg(ctx, fla, I, flush, 3)
 
-    cpu = None
-    if rank == 0 and not args.no_cpu and args.workload == "jet_vortex_2d":
-        cpu = cpu_baseline(wl)
+    cpu, forms_error = None, None
+    if rank == 0 and not args.no_cpu:
+        cpu, ref_src, wl_small = cpu_baseline(args.workload, wl, droplet_steps_per_run)
+        gforms = [form] + [f for f in variants if f not in ("learned",)]
+        outs = reduced_outputs(ctx, fla, wl_small, gforms)
+        forms_error = {f: all_cell_errors(outs[f], ref_src, wl_small.dim) for f in gforms}
+        forms_error["basis"] = (f"all-cell rel-L2 of each form's final sources vs the FP64 oracle on {wl_small.name} "
+                                f"({wl_small.nsteps} steps), the CPU baseline's sample")
+        if form in forms_error and form in ("compensated", "fp64"):
+            cpu["tolerance_met"] = all(v <= 1e-4 for v in forms_error[form].values())
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 (f64 det J)" if dtype == fla.F32 else "f64",
+            "vs_baseline": None,
+            "dtype": {"compensated": "f32x2 (double-float) advance, f32 deposit, f64 det J", "fp64": "f64",
+                      "plain": "f32"}.get(form, "f32 (f64 det J)"),
             "data": "synthetic (seeded, " + args.workload + ")",
-            "config": {"workload": desc, "form": args.form, "global_batch": world * wl.fla.n, "cells": cells,
-                       "deposits_per_step": deposits, "l2": "flushed between steps (256 MB write)",
+            "config": {"workload": desc, "form": form, "form_text": FORM_TEXT[form], "global_batch": world * wl.fla.n,
+                       "cells": cells, "deposits_per_step": deposits, "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"replicas x{world} (independent clouds, no collective)"},
             "droplet_steps_per_s": world * droplet_steps_per_run * args.steps / (total_ms * 1e-3),
             "gpu_launches": launches_per_run * args.steps,
             "clocks": clocks,
             "roofline": roof,
-            "phases": phases,
+            "rooflines": roofs,
             "e2e": {"value": world * cells * deposits / (e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
-            "forms": precision,
-            "psicell_reference": psi,
+            "forms": {"headline": form, "variants": variants, "rel_l2_all_cells": forms_error},
+            "secondary": secondary,
             "batch": batch,
             "cpu_baseline": cpu,
         }
@@ -546,73 +681,118 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def all_cell_errors(g, ref, dim):
+    gm, gv, gd = g
+    om, ov, od = ref
+    out = {}
+
+    def rl2(a, b):
+        nb = np.linalg.norm(b)
+        return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a - b))
+    out["S_mass"] = rl2(gm, om)
+    for c in range(dim):
+        out[f"S_mom_{'xyz'[c]}"] = rl2(gv[:, c], ov[:, c])
+    out["D"] = rl2(gd, od)
+    return out
+
+
 # --------------------------------------------------------------------------- CPU oracle
 
-def cpu_baseline(wl, seeds=8192, cells_a=256, cells_b=4096, track=256):
-    """The FP64 oracle, single-threaded, on a bounded sample of the same workload,
-    scaled to the whole run from separately timed parts:
-      carrier  one node re-sample, times the number of carrier steps;
-      advance  cost per droplet step from `seeds` seeds of the first release over
-               two windows (their two re-samples subtracted), times the run's active
-               droplet steps, counted from `track` random seeds integrated through the
-               whole run with the analytic carrier;
-      deposit  cell-list deposit of a cloud state of the workload's size and shape at
-               cells_a and cells_b cells: fixed part (cell list and records) plus the
-               per-cell slope times all cells, times the number of deposits."""
+def oracle_sample(wl_small, threads, nsteps=None):
+    """The FP64 oracle on a reduced configuration with `threads` host threads:
+    carrier sampling, the advance over `nsteps` steps (window by window), and the
+    cell-list deposit at the end.  Returns timings, active droplet steps and the
+    final sources."""
     from oracle import oracle as O
-    from paper_2512_20829_gb300 import inputs as I
-    rng = np.random.default_rng(0)
-    n, nsteps, win = wl.fla.n, wl.nsteps, wl.window
-    deposits = nsteps // win
+    O.set_threads(threads)
+    nsteps = wl_small.nsteps if nsteps is None else nsteps
+    t0 = time.perf_counter()
+    O.carrier_nodes(wl_small.carrier, 0.0, wl_small.n_cells_axis)
+    t_car = time.perf_counter() - t0
+    adv = O.Advancer(wl_small, wl_small.fla)
+    st = O.initial_state(wl_small.fla, wl_small.dim)
+    ds = 0
+    t0 = time.perf_counter()
+    s = 0
+    while s < nsteps:
+        k = min(wl_small.window, nsteps - s)
+        adv.advance(st, s, k, reset_acc=True)
+        ds += k * int((st.status == O.ACTIVE).sum())
+        s += k
+    t_adv = time.perf_counter() - t0
+    D = O.dep_struct(wl_small)
+    t0 = time.perf_counter()
+    src = O.nw_deposit_celllist(D, st.x, st.J, st.acc, st.status, st.batch, wl_small.fla.n0, wl_small.fla.h0)
+    t_dep = time.perf_counter() - t0
+    return {"t_car": t_car, "t_adv": t_adv, "t_dep": t_dep, "droplet_steps": ds, "steps": nsteps,
+            "carrier_samples": (1 if wl_small.carrier.steady else -(-nsteps // wl_small.window)),
+            "state": st}, src
+
+
+def oracle_deposit_seconds(wl_small, st, threads):
+    """Time of the oracle's cell-list deposit of a given state on `threads` threads."""
+    from oracle import oracle as O
+    O.set_threads(threads)
+    D = O.dep_struct(wl_small)
+    t0 = time.perf_counter()
+    O.nw_deposit_celllist(D, st.x, st.J, st.acc, st.status, st.batch, wl_small.fla.n0, wl_small.fla.h0)
+    return time.perf_counter() - t0
+
+
+def oracle_run_seconds(smp, wl_small, wl, full_droplet_steps):
+    """Time of the whole configuration at the oracle's measured unit costs: per node
+    sample, per droplet step, per deposited cell (the reduced configuration keeps the
+    seeding density per cell, so the deposit's candidates per cell match)."""
+    nodes_s = (wl_small.n_cells_axis + 1) ** wl_small.dim
+    nodes = (wl.n_cells_axis + 1) ** wl.dim
+    per_node = smp["t_car"] / nodes_s
+    # the carrier time inside the advance (re-samples of an unsteady carrier) is removed
+    adv_only = max(smp["t_adv"] - per_node * nodes_s * max(smp["carrier_samples"] - 1, 0), 1e-9)
+    per_ds = adv_only / max(smp["droplet_steps"], 1)
+    per_cell = smp["t_dep"] / wl_small.n_cells
+    samples = 1 if wl.carrier.steady else wl.nsteps // wl.window
+    deposits = wl.nsteps // wl.window
+    t = per_node * nodes * samples + per_ds * full_droplet_steps + per_cell * wl.n_cells * deposits
+    return t, per_ds, per_cell, per_node
+
+
+def cpu_baseline(name, wl, gpu_droplet_steps=None):
+    """The FP64 oracle, as it stands, on the host cores, on the reduced
+    configuration of the same workload (scale 4: 1/64 of the seeds and cells in
+    3D, 1/16 in 2D): all threads over the whole reduced run, one thread over its
+    first windows; both scaled to the full configuration by their measured unit
+    costs.  Returns the baseline entry, the reduced run's sources and workload."""
     wall0 = time.perf_counter()
-    # carrier
-    t0 = time.perf_counter()
-    O.carrier_nodes(wl.carrier, 0.0, wl.n_cells_axis)
-    t_node = time.perf_counter() - t0
-    t_car = t_node * (1 if wl.carrier.steady else deposits)
-    # advance cost per droplet step
-    first = np.nonzero(wl.fla.batch == 0)[0][:seeds]
-    sub = I.Cloud(kind=wl.fla.kind, x0=wl.fla.x0[first], batch=wl.fla.batch[first], step_start=wl.fla.step_start,
-                  St0=wl.fla.St0, n0=wl.fla.n0, h0=wl.fla.h0)
-    adv = O.Advancer(wl, sub)
-    st = O.initial_state(sub, wl.dim)
-    t0 = time.perf_counter()
-    adv.advance(st, 0, win, reset_acc=True)
-    adv.advance(st, win, win, reset_acc=True)
-    t_two = time.perf_counter() - t0
-    per_step = max(t_two - 2 * t_node, 1e-9) / (len(first) * 2 * win)
-    # active droplet steps of the whole run (fraction from tracked seeds, analytic carrier)
-    idx = np.sort(rng.choice(n, track, replace=False))
-    tr = I.Cloud(kind=wl.fla.kind, x0=wl.fla.x0[idx], batch=wl.fla.batch[idx], step_start=wl.fla.step_start,
-                 St0=wl.fla.St0, n0=wl.fla.n0, h0=wl.fla.h0)
-    adv2 = O.Advancer(wl, tr, use_mesh=False)
-    st2 = O.initial_state(tr, wl.dim)
-    active_steps = 0
-    for s in range(0, nsteps, win):
-        adv2.advance(st2, s, win, reset_acc=True)
-        active_steps += win * int((st2.status == O.ACTIVE).sum())
-    droplet_steps = active_steps * n / track
-    # deposit: fixed + per-cell
-    s_ = I.synthetic_state(2, n, wl.n_cells_axis, seed=31, band=(0.4, 0.6), h0_cells=2.0, jac_spread=0.3)
-    D = O.dep_struct(wl)
-    band = np.arange(int(0.4 * wl.n_cells_axis), int(0.6 * wl.n_cells_axis))
-    times = []
-    for c in (cells_a, cells_b):
-        cells = rng.choice(band, c) * wl.n_cells_axis + rng.integers(0, wl.n_cells_axis, c)
-        t0 = time.perf_counter()
-        O.nw_deposit_celllist(D, s_.x, s_.J, s_.acc, s_.status, s_.batch, s_.n0, s_.h0, cells=cells)
-        times.append(time.perf_counter() - t0)
-    per_cell = max(times[1] - times[0], 1e-9) / (cells_b - cells_a)
-    fixed = max(times[0] - per_cell * cells_a, 0.0)
-    t_dep = fixed + per_cell * wl.n_cells
-    t_run = t_car + per_step * droplet_steps + deposits * t_dep
-    return {"value": wl.n_cells * deposits / t_run, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"carrier re-sample x{1 if wl.carrier.steady else deposits}; {len(first)} seeds x {2 * win} "
-                       f"steps ({per_step * 1e6:.2f} us per droplet step) x {droplet_steps:.3g} active droplet "
-                       f"steps (from {track} tracked seeds); cell-list deposit at {cells_a}/{cells_b} cells of a "
-                       f"{n}-droplet state ({per_cell * 1e6:.1f} us per cell + {fixed:.2f} s fixed) x {deposits}"),
-            "est_seconds_per_run": round(t_run, 1), "sample_seconds": round(time.perf_counter() - wall0, 2),
-            "cpu": platform_cpu()}
+    wl_small = make_workload(name, scale=4)
+    nthreads = os.cpu_count() or 1
+    from oracle import oracle as O
+    O.build()
+    smp_all, src = oracle_sample(wl_small, nthreads)
+    # the full run's active droplet steps: the reduced run's per seed and step, times the full seeds
+    full_ds = smp_all["droplet_steps"] * wl.fla.n / wl_small.fla.n
+    t_all, per_ds_all, per_cell_all, _ = oracle_run_seconds(smp_all, wl_small, wl, full_ds)
+    one_steps = max(wl_small.window, min(wl_small.nsteps, 60 if wl.dim == 3 else 200))
+    smp_one, _ = oracle_sample(wl_small, 1, nsteps=one_steps)
+    # the one-thread deposit is timed on the same end-of-run state as the all-thread one
+    smp_one["t_dep"] = oracle_deposit_seconds(wl_small, smp_all["state"], 1)
+    t_one, per_ds_one, per_cell_one, _ = oracle_run_seconds(smp_one, wl_small, wl, full_ds)
+    O.set_threads(nthreads)
+    deposits = wl.nsteps // wl.window
+    entry = {"value": wl.n_cells * deposits / t_all, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+             "sample": (f"{wl_small.name}: {wl_small.nsteps} steps on {nthreads} threads "
+                        f"({per_ds_all * 1e6:.3f} us per droplet step, {per_cell_all * 1e6:.1f} us per cell), "
+                        f"scaled to {wl.fla.n} seeds x {full_ds / wl.fla.n:.1f} active steps and "
+                        f"{wl.n_cells} cells x {deposits} deposits"),
+             "est_seconds_per_run": round(t_all, 1),
+             "single_thread": {"value": wl.n_cells * deposits / t_one, "unit": UNIT, "cores": 1,
+                               "sample": (f"{wl_small.name}: first {one_steps} steps and the end-of-run deposit "
+                                          f"on 1 thread ({per_ds_one * 1e6:.3f} us per droplet step, "
+                                          f"{per_cell_one * 1e6:.1f} us per cell), scaled the same way"),
+                               "est_seconds_per_run": round(t_one, 1)},
+             "sample_seconds": round(time.perf_counter() - wall0, 2), "cpu": platform_cpu()}
+    if gpu_droplet_steps:
+        entry["full_run_active_droplet_steps"] = {"scaled_from_sample": full_ds, "gpu_counter": gpu_droplet_steps}
+    return entry, src, wl_small
 
 
 def platform_cpu():
@@ -626,25 +806,40 @@ def platform_cpu():
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores (all of them), each step
+    a bounded sample of the workload (the reduced configuration's first windows and
+    its end-of-run deposit), scaled to the whole configuration."""
     rank, _, world = dist_env()
     if rank != 0:
         return
-    from paper_2512_20829_gb300 import inputs as I
-    wl = I.jet_vortex_2d(lpt_per_batch=0)
+    from oracle import oracle as O
+    name = args.workload
+    desc, _ = WORKLOADS[name]
+    wl = make_workload(name)
+    wl_small = make_workload(name, scale=4)
+    O.build()
+    nthreads = os.cpu_count() or 1
+    steps_sample = max(wl_small.window, min(wl_small.nsteps, 100 if wl.dim == 3 else 300))
+    # active droplet steps of the full run from one pass over the whole reduced run
+    smp_full, _ = oracle_sample(wl_small, nthreads)
+    full_ds = smp_full["droplet_steps"] * wl.fla.n / wl_small.fla.n
     per_step = []
-    last = None
     for k in range(args.warmup + args.steps):
-        last = cpu_baseline(wl, seeds=256, cells_a=32, cells_b=96, track=32)
+        smp, _ = oracle_sample(wl_small, nthreads, nsteps=steps_sample)
+        t, per_ds, per_cell, _ = oracle_run_seconds(smp, wl_small, wl, full_ds)
         if k >= args.warmup:
-            per_step.append(wl.n_cells * (wl.nsteps // wl.window) / last["value"])
+            per_step.append(t)
     ms = 1e3 * float(np.mean(per_step))
-    value = wl.n_cells * (wl.nsteps // wl.window) / (ms * 1e-3)
+    deposits = wl.nsteps // wl.window
+    value = wl.n_cells * deposits / (ms * 1e-3)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded jet + vortices)",
-            "config": {"workload": WORKLOAD, "cells": wl.n_cells},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "per step: " + last["sample"]},
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded, " + name + ")",
+            "config": {"workload": desc, "cells": wl.n_cells, "deposits_per_step": deposits},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                             "sample": (f"per step: {wl_small.name}, first {steps_sample} steps and their deposit "
+                                        f"on {nthreads} threads ({per_ds * 1e6:.3f} us per droplet step, "
+                                        f"{per_cell * 1e6:.1f} us per cell), scaled to the whole configuration")},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
