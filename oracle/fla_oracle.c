@@ -827,6 +827,71 @@ int ora_threads(void)
 #endif
 }
 
+/* Audit of the single-precision truncation decision (test support): for each
+ * listed cell, every candidate pair of the cell list is decided twice -- q <= 9
+ * in double, and on the single-precision operands (D->fp32_decision must be 1)
+ * -- and the pairs where the two disagree are recorded (list position of the
+ * cell, droplet, q in double), up to max_out of them.  *n_pairs receives the
+ * number of candidate pairs inside the double-precision support.  Returns the
+ * number of disagreeing pairs. */
+long ora_decision_audit(const ora_dep* D, int n, const double* x, const double* J, const double* acc,
+                        const int* status, const int* batch, const double* n0, const double* h0,
+                        long n_out, const long* cells, long max_out, long* out_cell, int* out_drop,
+                        double* out_q, long* n_pairs)
+{
+    int d = D->dim, N = D->N;
+    long nc = (d == 2) ? (long)N * N : (long)N * N * N;
+    uint32_t* keys = (uint32_t*)malloc(sizeof(uint32_t) * (n > 0 ? n : 1));
+    ora_cell_keys(d, N, n, x, status, 0, keys);
+    long* start = (long*)calloc(nc + 1, sizeof(long));
+    int* list = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) if (keys[i] != 0xFFFFFFFFu) start[keys[i] + 1]++;
+    for (long c = 0; c < nc; ++c) start[c + 1] += start[c];
+    long* fill = (long*)malloc(sizeof(long) * nc);
+    memcpy(fill, start, sizeof(long) * nc);
+    for (int i = 0; i < n; ++i) if (keys[i] != 0xFFFFFFFFu) list[fill[keys[i]]++] = i;
+    ora_rec* rec = (ora_rec*)malloc(sizeof(ora_rec) * (n > 0 ? n : 1));
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i)
+        if (keys[i] != 0xFFFFFFFFu)
+            ora_record(D, x + (long)i * d, J + (long)i * d * d, acc + (long)i * (1 + d),
+                       n0[batch[i]], h0[batch[i]], D->fold ? D->fold[i] : 0, &rec[i]);
+    int R = (int)floor(3.0 * D->h_max * N + 0.5) + 1;
+    long found = 0, inside = 0;
+    for (long o = 0; o < n_out; ++o) {
+        long c = cells[o];
+        int ci[3] = {0, 0, 0};
+        long r = c;
+        for (int a = 0; a < d; ++a) { ci[a] = (int)(r % N); r /= N; }
+        int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+        for (int a = 0; a < d; ++a) {
+            lo[a] = ci[a] - R < 0 ? 0 : ci[a] - R;
+            hi[a] = ci[a] + R > N - 1 ? N - 1 : ci[a] + R;
+        }
+        double xc[3]; float xcf[3];
+        cell_centre(d, N, c, xc, xcf);
+        for (int kz = lo[2]; kz <= hi[2]; ++kz)
+            for (int ky = lo[1]; ky <= hi[1]; ++ky)
+                for (int kx = lo[0]; kx <= hi[0]; ++kx) {
+                    long b = kx + (long)N * ky + (long)N * N * kz;
+                    for (long m = start[b]; m < start[b + 1]; ++m) {
+                        int i = list[m];
+                        double q;
+                        int dec32 = in_support(D, &rec[i], xc, xcf, &q);
+                        int dec64 = q <= 9.0;
+                        inside += dec64;
+                        if (dec32 != dec64) {
+                            if (found < max_out) { out_cell[found] = o; out_drop[found] = i; out_q[found] = q; }
+                            ++found;
+                        }
+                    }
+                }
+    }
+    *n_pairs = inside;
+    free(keys); free(start); free(list); free(fill); free(rec);
+    return found;
+}
+
 /* Kernel of one droplet evaluated at every cell centre: the paper's weight
  * (normalised = 0) or the unit-mass Gaussian (normalised = 1, i.e. divided by
  * (2 pi)^{d/2} h^d, resp. (2 pi)^{d/2} det(Sigma)^{1/2}), truncated at q <= 9.

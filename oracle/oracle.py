@@ -101,6 +101,9 @@ def lib():
         _lib.ora_learn_loss_grad.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, v, v, C.c_long, v, v, v, v]
         _lib.ora_learn_records.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, v, v, v, v]
         _lib.ora_set_threads.argtypes = [i]
+        _lib.ora_decision_audit.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, v, v, C.c_long, v, C.c_long, v, v,
+                                            v, v]
+        _lib.ora_decision_audit.restype = C.c_long
         _lib.ora_threads.restype = i
     return _lib
 
@@ -304,6 +307,25 @@ def nw_deposit_celllist(D: _Dep, x, J, acc, status, batch, n0, h0, cells=None):
     lib().ora_nw_deposit_celllist_cells(C.byref(D), x.shape[0], _p(x), _p(J), _p(acc), _p(status), _p(batch),
                                         _p(_f64(n0)), _p(_f64(h0)), n_out, cptr, _p(Sm), _p(Sv), _p(Ds))
     return Sm, Sv, Ds
+
+
+def decision_audit(D: _Dep, x, J, acc, status, batch, n0, h0, cells, max_out=100_000):
+    """Pairs whose single-precision truncation decision (D.fp32_decision = 1) differs
+    from q <= 9 in double: (list positions of the cells, droplets, q in double) and
+    the number of pairs inside the double-precision support."""
+    assert D.fp32_decision == 1
+    d = D.dim
+    x, J, acc = _f64(x).reshape(-1, d), _f64(J).reshape(-1, d * d), _f64(acc).reshape(-1, 1 + d)
+    cells = np.ascontiguousarray(cells, dtype=np.int64)
+    oc = np.zeros(max_out, np.int64)
+    od = np.zeros(max_out, np.int32)
+    oq = np.zeros(max_out)
+    inside = C.c_long(0)
+    found = lib().ora_decision_audit(C.byref(D), x.shape[0], _p(x), _p(J), _p(acc), _p(_i32(status)),
+                                     _p(_i32(batch)), _p(_f64(n0)), _p(_f64(h0)), cells.shape[0], _p(cells),
+                                     max_out, _p(oc), _p(od), _p(oq), C.byref(inside))
+    k = min(found, max_out)
+    return oc[:k], od[:k], oq[:k], int(found), int(inside.value)
 
 
 def kernel_on_cells(D: _Dep, x, J, n0: float, h0: float, normalised: bool) -> np.ndarray:

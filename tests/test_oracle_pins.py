@@ -524,3 +524,149 @@ def test_oracle_threads_do_not_change_results():
         assert np.array_equal(u, v)
     for u, v in zip(s1, b1):   # pin P9 at this size too: cell list == brute force
         assert np.array_equal(u, v)
+
+
+# ---------------------------------------------------------------------------
+# The single-precision truncation decision (fp32_decision) against q <= 9 in
+# double.  The GPU's single-precision kernels decide whether a pair is inside
+# the 3-sigma support on single-precision operands, and the parity tests give
+# the oracle the same decision.  These pins tie that mode to the decision in
+# double: every pair on which the two differ must lie within a rounding bound
+# of q = 9 derived from the unit roundoff u = 2^-24 and the operand sizes, and
+# the sources may differ only by the weights of those pairs.
+#
+# Bounds (first order in u).  Positions and cell centres in [0, 1] round with
+# absolute error <= u/2 each and their difference adds u |dx|: eps = u (1 + |dx|)
+# per coordinate.
+#   spherical: q = r^2/h^2 against r2max = 9 h^2.  r^2 from the rounded
+#     differences (d multiply-adds) is off by <= 2 sqrt(d) |r| eps + d u r^2;
+#     r2max (h rounded, 9 h^2 rounded) by <= 9 h^2 (3u + 2 rho), rho the relative
+#     error of |det J| in the decision: 0 in 2D (double from the given J), and in
+#     3D <= 5u H / |det J| <= 500 u where the single-precision cofactor expansion
+#     is used (only while |det J| >= 1e-2 H, H the product of the rows' L1 norms).
+#     At r = 3 h:  |q - 9| <= 6 sqrt(d) eps / h + 9 d u + 27 u + 18 rho.
+#   J-scaled: q = d^T P d with P the single-precision inverse of Sigma, whose
+#     condition number is at most tr(Sigma) / h_min^2 <= h_max^2 / h_min^2 = kappa:
+#     |P_f - P| <= 20 kappa u |P|; the position term is 2 |P d| eps sqrt(d) with
+#     |P d| <= 3 / h_min at q = 9; the products and sums add 2 d u q:
+#     |q - 9| <= 9 (20 kappa + 2 d) u + 6 sqrt(d) eps / h_min.
+U32 = 2.0 ** -24
+
+
+def _double_state(dim, n, N, seed, h0_cells, fold_frac):
+    """A synthetic state with double-precision positions and Jacobians (so that
+    the single-precision operands really are rounded), a fraction of them close
+    to a fold: J = R diag(s1, s2[, s3]) R' with the smallest singular value
+    1e-4..1e-2 of the largest."""
+    s = I.synthetic_state(dim, n, N, seed=seed, band=(0.4, 0.6), h0_cells=h0_cells, jac_spread=0.3)
+    rng = np.random.default_rng(seed + 100)
+    x = s.x.astype(np.float64) + rng.uniform(-0.5, 0.5, s.x.shape) * 2.0 ** -26
+    J = s.J.astype(np.float64) * (1.0 + 1e-7 * rng.standard_normal(s.J.shape))
+    k = rng.uniform(size=n) < fold_frac
+    m = int(k.sum())
+    Q1 = np.linalg.qr(rng.standard_normal((m, dim, dim)))[0]
+    Q2 = np.linalg.qr(rng.standard_normal((m, dim, dim)))[0]
+    sv = np.exp(rng.uniform(-0.3, 0.3, (m, dim)))
+    sv[:, -1] = sv[:, 0] * 10.0 ** rng.uniform(-4, -2, m)
+    J[k] = np.einsum("nij,nj,nkj->nik", Q1, sv, Q2)
+    return x, J, s
+
+
+def _audit(dim, kernel, N, n, hmax_cells, h0_cells, ncells, seed):
+    x, J, s = _double_state(dim, n, N, seed, h0_cells, fold_frac=0.2)
+    h_min, h_max = 0.5 / N, hmax_cells / N
+    kw = dict(dim=dim, N=N, kernel=kernel, h_min=h_min, h_max=h_max, p=1.0, window_dt=0.01)
+    D32 = O.dep_struct(fp32_decision=True, **kw)
+    D64 = O.dep_struct(fp32_decision=False, **kw)
+    rng = np.random.default_rng(seed)
+    band = np.arange(int(0.42 * N), int(0.58 * N))
+    cells = rng.integers(0, N, (ncells, dim))
+    cells[:, -1] = rng.choice(band, ncells)
+    lin = cells[:, 0] + N * cells[:, 1] + (N * N * cells[:, 2] if dim == 3 else 0)
+    lin = np.unique(lin)
+    oc, od, oq, found, inside = O.decision_audit(D32, x, J, s.acc, s.status, s.batch, s.n0, s.h0, lin)
+    eps = U32 * (1.0 + 3.0 * h_max * np.sqrt(dim))
+    if kernel == I.KERNEL_ISO:
+        rho = 0.0 if dim == 2 else 500.0 * U32
+        rec = O.records(D64, x, J, s.acc, s.batch, s.n0, s.h0)     # n, det J, h, pref per droplet
+        h = rec[od, 2]
+        bound = 6 * np.sqrt(dim) * eps / h + 9 * dim * U32 + 27 * U32 + 18 * rho
+    else:
+        kappa = h_max ** 2 / h_min ** 2
+        bound = np.full(len(oq), 9 * (20 * kappa + 2 * dim) * U32 + 6 * np.sqrt(dim) * eps / h_min)
+    return dict(x=x, J=J, s=s, D32=D32, D64=D64, cells=lin, oc=oc, od=od, oq=oq, found=found, inside=inside,
+                bound=bound)
+
+
+def _check_sources(a):
+    """Per cell: the two decisions' sources differ by at most the flipped pairs'
+    weights (w = pref exp(-q/2) at q near 9) times |a_i| + |S_c|, over D_c."""
+    s, x, J, lin = a["s"], a["x"], a["J"], a["cells"]
+    m32, v32, d32 = O.nw_deposit_celllist(a["D32"], x, J, s.acc, s.status, s.batch, s.n0, s.h0, cells=lin)
+    m64, v64, d64 = O.nw_deposit_celllist(a["D64"], x, J, s.acc, s.status, s.batch, s.n0, s.h0, cells=lin)
+    rec = O.records(a["D64"], x, J, s.acc, s.batch, s.n0, s.h0)
+    n_i, pref = rec[:, 0], rec[:, 3]
+    am = np.abs(n_i * s.acc[:, 0] / 0.01)
+    av = np.abs(n_i[:, None] * s.acc[:, 1:] / 0.01).max(axis=1)
+    w = pref[a["od"]] * np.exp(-0.5 * a["oq"])
+    jm = np.zeros(len(lin))
+    jv = np.zeros(len(lin))
+    jd = np.zeros(len(lin))
+    np.add.at(jd, a["oc"], w)
+    np.add.at(jm, a["oc"], w * (am[a["od"]] + np.abs(m64[a["oc"]])))
+    np.add.at(jv, a["oc"], w * (av[a["od"]] + np.abs(v64[a["oc"]]).max(axis=1)))
+    dmin = np.maximum(np.minimum(d32, d64), 1e-300)
+    tol = 1e-12 * (np.abs(m64) + 1.0)
+    assert np.all(np.abs(d32 - d64) <= jd * (1 + 1e-9) + 1e-12 * d64)
+    assert np.all(np.abs(m32 - m64) <= jm / dmin * (1 + 1e-6) + tol)
+    assert np.all(np.abs(v32 - v64).max(axis=1) <= jv / dmin * (1 + 1e-6) + tol)
+    return int((a["oc"] >= 0).sum())
+
+
+@pytest.mark.parametrize("dim,kernel,N,n,hmax,h0,ncells", [
+    (2, I.KERNEL_ISO, 512, 262_144, 4.0, 2.0, 20_000),
+    (3, I.KERNEL_ISO, 64, 262_144, 2.0, 1.2, 4_000),
+    (3, I.KERNEL_ANISO, 128, 2_097_152, 2.0, 0.45, 2_000),
+])
+def test_single_precision_decision_within_rounding_of_q9(dim, kernel, N, n, hmax, h0, ncells):
+    a = _audit(dim, kernel, N, n, hmax, h0, ncells, seed=41 + 3 * dim + kernel)
+    print(f"\n{dim}D kernel {kernel}: {a['found']} of {a['inside']} pairs decided differently; "
+          f"max |q - 9| {np.abs(a['oq'] - 9).max() if a['found'] else 0:.2e}, bound "
+          f"{a['bound'].min() if a['found'] else 0:.2e}..{a['bound'].max() if a['found'] else 0:.2e}")
+    assert a["inside"] > 100 * len(a["cells"])
+    assert a["found"] == len(a["oq"])                       # all recorded
+    assert np.all(np.abs(a["oq"] - 9.0) <= a["bound"]), np.abs(a["oq"] - 9.0).max()
+    assert a["found"] <= 1e-3 * a["inside"]
+    _check_sources(a)
+
+
+def test_decision_audit_detects_a_single_precision_det_near_folds():
+    """The audit separates a right decision from a wrong one.  Droplets with large,
+    ill-conditioned J (singular values 40, 40, 1/1600: |det J| = 1, so h is not
+    clamped, while the rows' L1 norms multiply to ~3e5) have a single-precision
+    cofactor det J off by up to ~10 %.  The mixed mode switches to double there
+    (|det J| < 1e-2 H) and stays within the bound; deciding with the
+    single-precision det J -- what a wrong threshold would do, and what the plain
+    mode does by design -- moves pairs far outside it."""
+    N, n = 32, 32_768
+    x, J, s = _double_state(3, n, N, seed=13, h0_cells=1.2, fold_frac=0.0)
+    rng = np.random.default_rng(14)
+    k = rng.uniform(size=n) < 0.3
+    m = int(k.sum())
+    Q1 = np.linalg.qr(rng.standard_normal((m, 3, 3)))[0]
+    Q2 = np.linalg.qr(rng.standard_normal((m, 3, 3)))[0]
+    J[k] = np.einsum("nij,j,nkj->nik", Q1, np.array([40.0, 40.0, 1.0 / 1600.0]), Q2)
+    lin = np.unique(rng.integers(0, N ** 3, 3000))
+    kw = dict(dim=3, N=N, kernel=I.KERNEL_ISO, h_min=0.5 / N, h_max=2.0 / N, p=1.0, window_dt=0.01,
+              fp32_decision=True)
+    rec = O.records(O.dep_struct(**{**kw, "fp32_decision": False}), x, J, s.acc, s.batch, s.n0, s.h0)
+    eps = U32 * (1.0 + 3.0 * (2.0 / N) * np.sqrt(3))
+    res = {}
+    for name, plain in (("mixed", False), ("single-precision det", True)):
+        oc, od, oq, found, inside = O.decision_audit(O.dep_struct(plain=plain, **kw), x, J, s.acc, s.status,
+                                                     s.batch, s.n0, s.h0, lin)
+        bound = 6 * np.sqrt(3) * eps / rec[od, 2] + 27 * U32 + 27 * U32 + 18 * 500 * U32
+        res[name] = (found, int((np.abs(oq - 9.0) > bound).sum()), inside)
+    print("\n", res)
+    assert res["mixed"][1] == 0
+    assert res["single-precision det"][1] > 10
