@@ -101,6 +101,8 @@ def lib():
         _lib.ora_learn_loss_grad.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, v, v, C.c_long, v, v, v, v]
         _lib.ora_learn_records.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, v, v, v, v]
         _lib.ora_set_threads.argtypes = [i]
+        _lib.ora_cic.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, v, v, v]
+        _lib.ora_cic_celllist.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, v, v, v]
         _lib.ora_decision_audit.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, v, v, C.c_long, v, C.c_long, v, v,
                                             v, v]
         _lib.ora_decision_audit.restype = C.c_long
@@ -359,6 +361,21 @@ def sort_and_bins(keys: np.ndarray, n_cells: int):
     sk = keys[perm]
     bin_start = np.searchsorted(sk, np.arange(n_cells + 1, dtype=np.uint64), side="left").astype(np.uint32)
     return sk, perm, bin_start
+
+
+def cic(D: _Dep, x, acc, status, batch, w, brute: bool = False):
+    """Cloud-In-Cell sources (tent weights to the cell centres around each parcel)
+    and the box counts; brute: over every parcel for each cell, else the cell list."""
+    d = D.dim
+    x, acc = _f64(x).reshape(-1, d), _f64(acc).reshape(-1, 1 + d)
+    nc = D.N ** d
+    counts = np.zeros(nc, np.uint32)
+    Sm = np.zeros(nc)
+    Sv = np.zeros((nc, d))
+    f = lib().ora_cic if brute else lib().ora_cic_celllist
+    f(C.byref(D), x.shape[0], _p(x), _p(acc), _p(_i32(status)), _p(_i32(batch)), _p(_f64(w)), _p(counts), _p(Sm),
+      _p(Sv))
+    return counts, Sm, Sv
 
 
 def psicell(D: _Dep, x, acc, status, batch, w, fp32_keys: bool):

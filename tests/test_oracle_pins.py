@@ -670,3 +670,67 @@ def test_decision_audit_detects_a_single_precision_det_near_folds():
     print("\n", res)
     assert res["mixed"][1] == 0
     assert res["single-precision det"][1] > 10
+
+
+# ---------------------------------------------------------------------------
+# Cloud-In-Cell deposit (Sec. 1: the C^1 alternative to PSI-CELL): tent
+# weights W = prod_a (1 - |x_a - xc_a| N)^+ to the cell centres around a parcel.
+
+def _cic_cloud(d, N, n, seed, margin):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(margin, 1.0 - margin, (n, d))
+    acc = rng.standard_normal((n, 1 + d))
+    status = np.ones(n, np.int32)
+    batch = rng.integers(0, 3, n).astype(np.int32)
+    w = rng.uniform(0.5, 2.0, 3)
+    return x, acc, status, batch, w
+
+
+@pytest.mark.parametrize("d,N", [(2, 32), (3, 12)])
+def test_cic_conserves_zeroth_and_first_moments(d, N):
+    """Away from the walls (parcels at least half a cell inside) the tent weights of
+    a parcel sum to 1 and reproduce linear functions: sum_c S_c V = -sum_i w_i a_i
+    and sum_c x_c S_c V = -sum_i w_i a_i x_i, for every source component."""
+    x, acc, status, batch, w = _cic_cloud(d, N, 400, 3 + d, margin=0.5 / N)
+    D = O.dep_struct(dim=d, N=N, kernel=0, h_min=0.1, h_max=0.1, p=1.0, window_dt=0.5)
+    counts, Sm, Sv = O.cic(D, x, acc, status, batch, w)
+    V = (1.0 / N) ** d
+    S = np.concatenate([Sm[:, None], Sv], axis=1)
+    a = w[batch][:, None] * acc / 0.5
+    assert np.allclose(S.sum(axis=0) * V, -a.sum(axis=0), rtol=1e-12, atol=1e-12)
+    idx = np.arange(N ** d)
+    xc = np.stack([((idx // N ** k) % N + 0.5) / N for k in range(d)], axis=1)
+    for k in range(d):
+        assert np.allclose((xc[:, k:k + 1] * S).sum(axis=0) * V, -(x[:, k:k + 1] * a).sum(axis=0),
+                           rtol=1e-12, atol=1e-12)
+    assert counts.sum() == 400
+
+
+def test_cic_single_parcels_split_by_tent_weights():
+    """A parcel at a cell centre stays in its cell; one on the face between two
+    centres splits 1/2 : 1/2; one on a node of four centres splits into quarters;
+    a quarter cell off a centre gives 3/4 : 1/4 along that axis."""
+    N = 8
+    D = O.dep_struct(dim=2, N=N, kernel=0, h_min=0.1, h_max=0.1, p=1.0, window_dt=1.0, per_cell=True)
+    one = np.ones((1, 3))
+    cases = [((2.5 / N, 3.5 / N), {(2, 3): 1.0}),
+             ((3.0 / N, 3.5 / N), {(2, 3): 0.5, (3, 3): 0.5}),
+             ((3.0 / N, 4.0 / N), {(2, 3): 0.25, (3, 3): 0.25, (2, 4): 0.25, (3, 4): 0.25}),
+             ((2.75 / N, 3.5 / N), {(2, 3): 0.75, (3, 3): 0.25})]
+    for pos, expect in cases:
+        _, Sm, _ = O.cic(D, np.array([pos]), one, np.ones(1, np.int32), np.zeros(1, np.int32), np.ones(1))
+        got = {(c % N, c // N): -v for c, v in enumerate(Sm) if v != 0.0}
+        assert set(got) == set(expect) and all(abs(got[k] - expect[k]) < 1e-15 for k in expect), (pos, got)
+
+
+@pytest.mark.parametrize("d,N", [(2, 16), (3, 8)])
+def test_cic_cell_list_equals_brute_force(d, N):
+    x, acc, status, batch, w = _cic_cloud(d, N, 300, 11 + d, margin=0.0)
+    x[:5] = np.round(x[:5] * N) / N          # parcels exactly on faces and nodes
+    x[5, 0] = 1.0                            # on the upper wall
+    status[7:12] = 2                         # inactive parcels
+    D = O.dep_struct(dim=d, N=N, kernel=0, h_min=0.1, h_max=0.1, p=1.0, window_dt=0.1)
+    a = O.cic(D, x, acc, status, batch, w, brute=True)
+    b = O.cic(D, x, acc, status, batch, w, brute=False)
+    for u, v in zip(a, b):
+        assert np.array_equal(u, v)
