@@ -187,8 +187,9 @@ class ClockSampler:
 class RunPath:
     """Device buffers and the issue order of one whole run of a workload."""
 
-    def __init__(self, ctx, wl, fla, form, with_fla=True, with_lpt=False):
+    def __init__(self, ctx, wl, fla, form, with_fla=True, with_lpt=False, parcel_deposit="psicell"):
         dname, pname, fold_guard, learned = FORMS[form]
+        self.parcel_deposit = fla.psicell if parcel_deposit == "psicell" else fla.cic
         self.fla, self.ctx, self.wl, self.form = fla, ctx, wl, form
         self.dtype = getattr(fla, dname)
         self.precision = getattr(fla, pname)
@@ -237,7 +238,7 @@ class RunPath:
             if self.cloud is not None:
                 fla.deposit_sources(self.ctx, self.cloud, m, self.cfg, self.out, self.ws)
             if self.lpt is not None:
-                fla.psicell(self.ctx, self.lpt, m, wl.window * wl.dt, self.psi, self.ws)
+                self.parcel_deposit(self.ctx, self.lpt, m, wl.window * wl.dt, self.psi, self.ws)
 
 
 def capture(path):
@@ -402,10 +403,10 @@ def weak_value(world: int, cells: int, deposits: int, steps: int, total_ms: floa
     return world * cells * deposits * steps / (total_ms * 1e-3)
 
 
-def time_form(ctx, fla, wl, form, flush, reps=3, with_lpt=False, with_fla=True):
+def time_form(ctx, fla, wl, form, flush, reps=3, with_lpt=False, with_fla=True, parcel_deposit="psicell"):
     """Graph-replayed whole runs of one form; median ms, device counters per run."""
     import torch
-    p = RunPath(ctx, wl, fla, form, with_fla=with_fla, with_lpt=with_lpt)
+    p = RunPath(ctx, wl, fla, form, with_fla=with_fla, with_lpt=with_lpt, parcel_deposit=parcel_deposit)
     g, launches = capture(p)
     g.replay()
     torch.cuda.synchronize()
@@ -635,6 +636,15 @@ def run_ours(args):
                     "gpu_launches_per_run": pres["launches_per_run"],
                     "fla_speedup_vs_psicell": round(pms / leg["forms"][f2]["ms_per_run"], 2)}
                 del pp
+                torch.cuda.empty_cache()
+                # Cloud-In-Cell on the same parcels (the paper's C^1 alternative to PSI-CELL)
+                cp, cms, cres = time_form(ctx, fla, w2, "mixed", flush, reps=2, with_lpt=True, with_fla=False,
+                                          parcel_deposit="cic")
+                leg["cic_reference"] = {
+                    "parcels": w2.lpt.n, "ms_per_run": round(cms, 3),
+                    "cells_per_s": w2.n_cells * (w2.nsteps // w2.window) / (cms * 1e-3),
+                    "gpu_launches_per_run": cres["launches_per_run"]}
+                del cp
                 torch.cuda.empty_cache()
             secondary[wname] = leg
 

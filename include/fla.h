@@ -318,6 +318,22 @@ int psicell_deposit(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, 
                     int32_t per_cell, const fla_psicell_out* out, void* workspace_dev, size_t workspace_bytes,
                     fla_stream_t stream);
 
+/* Cloud-In-Cell sources of a parcel cloud, the C^1 alternative to PSI-CELL
+ * that Sec. 1 of the paper names (parcel quantities interpolated linearly to
+ * the corners of the occupied cell).  With cell-centred sources the corners
+ * are the cell centres around the parcel: each active parcel inside [0,1]^dim
+ * gives the cell centred at x_c the weight
+ *   W = prod_a max(0, 1 - |x_a - x_c,a| N)
+ * (the overlap of a cell-sized cloud around the parcel with that cell), and
+ *   S_mass = -(1/V) sum W w_b acc_mass,i / window_dt,  S_mom likewise,
+ * over the parcels of the 3^dim cells around each cell; weight that falls on
+ * centres outside the mesh is dropped.  counts = parcels whose cell key is the
+ * cell (the box count of psicell_deposit).  Same arguments, outputs and
+ * workspace as psicell_deposit; the sums run in a fixed order (deterministic,
+ * no float atomics). */
+int cic_deposit(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, double window_dt, int32_t per_cell,
+                const fla_psicell_out* out, void* workspace_dev, size_t workspace_bytes, fla_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Learned bandwidth correction.  The paper has no counterpart: a small
  * network g corrects each droplet's smoothing length,

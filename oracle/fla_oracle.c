@@ -988,20 +988,31 @@ static double cic_weight(int d, int N, const double* x, const double* xc)
     return w;
 }
 
+/* Box counts of a parcel cloud: counts_c = parcels whose cell key is c, the
+ * key formed in double or, with fp32_keys, in single precision (R18). */
+static void box_counts(int d, int N, int n, const double* x, const int* status, int fp32_keys, uint32_t* counts)
+{
+    long nc = (d == 2) ? (long)N * N : (long)N * N * N;
+    uint32_t* keys = (uint32_t*)malloc(sizeof(uint32_t) * (n > 0 ? n : 1));
+    ora_cell_keys(d, N, n, x, status, fp32_keys, keys);
+    for (long c = 0; c < nc; ++c) counts[c] = 0;
+    for (int i = 0; i < n; ++i) if (keys[i] != 0xFFFFFFFFu) counts[keys[i]] += 1;
+    free(keys);
+}
+
 /* S_c = -(1/V) sum_i W(x_i, x_c) w_i acc_i / T over active parcels inside
  * [0,1]^d, in ascending parcel index (brute force over every parcel), and
  * counts_c = parcels whose cell key is c (the box count, as PSI-CELL).
  * Weight of centres outside the mesh is dropped (no redistribution). */
 int ora_cic(const ora_dep* D, int n, const double* x, const double* acc, const int* status, const int* batch,
-            const double* w, uint32_t* counts, double* S_mass, double* S_mom)
+            const double* w, int fp32_keys, uint32_t* counts, double* S_mass, double* S_mom)
 {
     int d = D->dim, N = D->N;
     long nc = (d == 2) ? (long)N * N : (long)N * N * N;
     uint32_t* keys = (uint32_t*)malloc(sizeof(uint32_t) * (n > 0 ? n : 1));
     ora_cell_keys(d, N, n, x, status, 0, keys);
     double scale = D->per_cell ? 1.0 : 1.0 / cell_volume(D);
-    for (long c = 0; c < nc; ++c) counts[c] = 0;
-    for (int i = 0; i < n; ++i) if (keys[i] != 0xFFFFFFFFu) counts[keys[i]] += 1;
+    box_counts(d, N, n, x, status, fp32_keys, counts);
 #pragma omp parallel for schedule(dynamic, 64)
     for (long c = 0; c < nc; ++c) {
         double xc[3]; float xcf[3];
@@ -1024,7 +1035,8 @@ int ora_cic(const ora_dep* D, int n, const double* x, const double* acc, const i
  * binned in the 3^d cells around it (W vanishes beyond one cell), taken in
  * ascending index; bit-identical to ora_cic. */
 int ora_cic_celllist(const ora_dep* D, int n, const double* x, const double* acc, const int* status,
-                     const int* batch, const double* w, uint32_t* counts, double* S_mass, double* S_mom)
+                     const int* batch, const double* w, int fp32_keys, uint32_t* counts, double* S_mass,
+                     double* S_mom)
 {
     int d = D->dim, N = D->N;
     long nc = (d == 2) ? (long)N * N : (long)N * N * N;
@@ -1033,7 +1045,8 @@ int ora_cic_celllist(const ora_dep* D, int n, const double* x, const double* acc
     long* start = (long*)calloc(nc + 1, sizeof(long));
     int* list = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
     for (int i = 0; i < n; ++i) if (keys[i] != 0xFFFFFFFFu) start[keys[i] + 1]++;
-    for (long c = 0; c < nc; ++c) { counts[c] = (uint32_t)start[c + 1]; start[c + 1] += start[c]; }
+    for (long c = 0; c < nc; ++c) start[c + 1] += start[c];
+    box_counts(d, N, n, x, status, fp32_keys, counts);
     long* fill = (long*)malloc(sizeof(long) * nc);
     memcpy(fill, start, sizeof(long) * nc);
     for (int i = 0; i < n; ++i) if (keys[i] != 0xFFFFFFFFu) list[fill[keys[i]]++] = i;

@@ -101,8 +101,8 @@ def lib():
         _lib.ora_learn_loss_grad.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, v, v, C.c_long, v, v, v, v]
         _lib.ora_learn_records.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, v, v, v, v]
         _lib.ora_set_threads.argtypes = [i]
-        _lib.ora_cic.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, v, v, v]
-        _lib.ora_cic_celllist.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, v, v, v]
+        _lib.ora_cic.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, i, v, v, v]
+        _lib.ora_cic_celllist.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, i, v, v, v]
         _lib.ora_decision_audit.argtypes = [C.POINTER(_Dep), i, v, v, v, v, v, v, v, C.c_long, v, C.c_long, v, v,
                                             v, v]
         _lib.ora_decision_audit.restype = C.c_long
@@ -363,9 +363,10 @@ def sort_and_bins(keys: np.ndarray, n_cells: int):
     return sk, perm, bin_start
 
 
-def cic(D: _Dep, x, acc, status, batch, w, brute: bool = False):
+def cic(D: _Dep, x, acc, status, batch, w, brute: bool = False, fp32_keys: bool = False):
     """Cloud-In-Cell sources (tent weights to the cell centres around each parcel)
-    and the box counts; brute: over every parcel for each cell, else the cell list."""
+    and the box counts (keys in single precision with fp32_keys); brute: over every
+    parcel for each cell, else the cell list."""
     d = D.dim
     x, acc = _f64(x).reshape(-1, d), _f64(acc).reshape(-1, 1 + d)
     nc = D.N ** d
@@ -373,8 +374,8 @@ def cic(D: _Dep, x, acc, status, batch, w, brute: bool = False):
     Sm = np.zeros(nc)
     Sv = np.zeros((nc, d))
     f = lib().ora_cic if brute else lib().ora_cic_celllist
-    f(C.byref(D), x.shape[0], _p(x), _p(acc), _p(_i32(status)), _p(_i32(batch)), _p(_f64(w)), _p(counts), _p(Sm),
-      _p(Sv))
+    f(C.byref(D), x.shape[0], _p(x), _p(acc), _p(_i32(status)), _p(_i32(batch)), _p(_f64(w)), 1 if fp32_keys else 0,
+      _p(counts), _p(Sm), _p(Sv))
     return counts, Sm, Sv
 
 

@@ -584,8 +584,10 @@ int fla_adam_step(fla_ctx* ctx, float* params_dev, const float* grad_dev, float*
                                    (cudaStream_t)stream));
 }
 
-int psicell_deposit(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, double window_dt, int32_t per_cell,
-                    const fla_psicell_out* out, void* ws, size_t ws_bytes, fla_stream_t stream)
+namespace {
+// The box-count (PSI-CELL) and Cloud-In-Cell deposits share their argument checks and binning.
+int parcel_deposit(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, double window_dt, int32_t per_cell,
+                   const fla_psicell_out* out, void* ws, size_t ws_bytes, fla_stream_t stream, bool cic)
 {
     if (!ctx || !out) return FLA_ERR_ARG;
     int st = cloud_ok(cloud, mesh);
@@ -594,8 +596,8 @@ int psicell_deposit(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, 
     if (!(window_dt > 0) || !isfinite(window_dt) || (per_cell != 0 && per_cell != 1)) return FLA_ERR_ARG;
     if (!out->counts_dev || !out->s_mass_dev || !out->s_mom_dev) return FLA_ERR_ARG;
     const WsLayout L = layout(*mesh, cloud->dtype, FLA_KERNEL_ISO, cloud->n);
-    const size_t psi_rec = up256((size_t)(cloud->n > 0 ? cloud->n : 1) * 4 * (cloud->dtype == FLA_F64 ? 8 : 4));
-    st = ws_ok(ws, ws_bytes, L.rec + psi_rec);
+    const size_t rec = up256((size_t)(cloud->n > 0 ? cloud->n : 1) * (cic ? 8 : 4) * (cloud->dtype == FLA_F64 ? 8 : 4));
+    st = ws_ok(ws, ws_bytes, L.rec + rec);
     if (st != FLA_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t nc = cells_of(*mesh);
@@ -610,8 +612,24 @@ int psicell_deposit(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, 
         if (launch_bin_start(at<uint32_t>(ws, L.keys[cur]), cloud->n, nc, bins, s) != cudaSuccess) return FLA_ERR_CUDA;
     }
     PhaseScope ps(ctx, FLA_PHASE_PSICELL, s, cloud->n > 0 ? 2 : 1);
+    if (cic)
+        return cuda_status(launch_cic(*cloud, *mesh, window_dt, per_cell, at<uint32_t>(ws, L.vals[cur]), bins,
+                                      at<void>(ws, L.rec), *out, (DevStatus*)ctx->status_dev, s));
     return cuda_status(launch_psicell(*cloud, *mesh, window_dt, per_cell, at<uint32_t>(ws, L.vals[cur]), bins,
                                       at<void>(ws, L.rec), *out, (DevStatus*)ctx->status_dev, s));
+}
+}  // namespace
+
+int cic_deposit(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, double window_dt, int32_t per_cell,
+                const fla_psicell_out* out, void* ws, size_t ws_bytes, fla_stream_t stream)
+{
+    return parcel_deposit(ctx, cloud, mesh, window_dt, per_cell, out, ws, ws_bytes, stream, true);
+}
+
+int psicell_deposit(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, double window_dt, int32_t per_cell,
+                    const fla_psicell_out* out, void* ws, size_t ws_bytes, fla_stream_t stream)
+{
+    return parcel_deposit(ctx, cloud, mesh, window_dt, per_cell, out, ws, ws_bytes, stream, false);
 }
 
 int fla_sync_status(fla_ctx* ctx, fla_stream_t stream, fla_device_status* out, int reset)

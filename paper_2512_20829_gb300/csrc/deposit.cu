@@ -865,6 +865,91 @@ __global__ void __launch_bounds__(256) k_psi_cells(const T* __restrict__ rec, co
 }
 
 
+// Cloud-In-Cell (CIC): each parcel's w * acc / T_window is spread over the
+// cell centres around it with the tent weights prod_a (1 - |x_a - xc_a| N)^+,
+// the overlap of a cell-sized cloud around the parcel with each cell.  The
+// records pass writes, per sorted parcel, its position and w * acc / T (two
+// vectors of 4); the cells pass takes one warp per cell over the parcels of
+// the 3^D cells around it (the tent vanishes one cell away), in a fixed lane
+// assignment with a butterfly reduction: deterministic, no float atomics.
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_cic_records(PsiArgs a)
+{
+    pdl_entry();
+    constexpr int OA = acc_offset(FLA_CLOUD_LPT, D);
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nvalid = a.bin_start[a.n_cells];
+    if (j >= nvalid) return;
+    const uint32_t i = a.perm[j];
+    const double w = __ldg(&a.batches[a.meta[i] & FLA_META_BATCH_MASK].n0);
+    T x[4], v0[4], v1[4], out[4];
+    load4<T>((const T*)a.state, i, x);
+    load4<T>((const T*)a.state, (OA / 4) * a.n + i, v0);
+    if (OA % 4 + D + 1 > 4) load4<T>((const T*)a.state, (OA / 4 + 1) * a.n + i, v1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[q] = T(0);
+#pragma unroll
+    for (int q = 0; q <= D; ++q) {
+        const int o = OA % 4 + q;
+        const T v = o < 4 ? v0[o] : v1[o - 4];
+        out[q] = sizeof(T) == 4 ? T((float)w * (float)v * (float)a.inv_window) : T(w * (double)v * a.inv_window);
+    }
+    if (D == 2) x[2] = T(0);
+    x[3] = T(0);
+    store4<T>((T*)a.rec, 2 * j, x);
+    store4<T>((T*)a.rec, 2 * j + 1, out);
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_cic_cells(const T* __restrict__ rec, const uint32_t* __restrict__ bin_start,
+                                                   int N, T scale, uint32_t* __restrict__ counts,
+                                                   T* __restrict__ s_mass, T* __restrict__ s_mom)
+{
+    pdl_entry();
+    const int64_t nc = D == 2 ? (int64_t)N * N : (int64_t)N * N * N;
+    const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= nc) return;
+    int ci[3] = {(int)(c % N), (int)((c / N) % N), D == 3 ? (int)(c / ((int64_t)N * N)) : 0};
+    T xc[3];
+#pragma unroll
+    for (int q = 0; q < D; ++q) xc[q] = (T(ci[q]) + T(0.5)) / T(N);
+    const T fN = T(N);
+    T s[4] = {T(0), T(0), T(0), T(0)};
+    const int zlo = D == 3 ? (ci[2] > 0 ? ci[2] - 1 : 0) : 0, zhi = D == 3 ? (ci[2] < N - 1 ? ci[2] + 1 : N - 1) : 0;
+    const int ylo = ci[1] > 0 ? ci[1] - 1 : 0, yhi = ci[1] < N - 1 ? ci[1] + 1 : N - 1;
+    const int xlo = ci[0] > 0 ? ci[0] - 1 : 0, xhi = ci[0] < N - 1 ? ci[0] + 1 : N - 1;
+    for (int kz = zlo; kz <= zhi; ++kz)
+        for (int ky = ylo; ky <= yhi; ++ky) {
+            // the cells xlo..xhi of one row are contiguous in the sorted order
+            const int64_t rb = ((int64_t)kz * N + ky) * N;
+            const uint32_t beg = bin_start[rb + xlo], end = bin_start[rb + xhi + 1];
+            for (uint32_t j = beg + lane; j < end; j += 32) {
+                T p[4], v[4];
+                load4<T>(rec, 2 * (int64_t)j, p);
+                load4<T>(rec, 2 * (int64_t)j + 1, v);
+                T W = T(1);
+#pragma unroll
+                for (int q = 0; q < D; ++q) {
+                    const T t = T(1) - fabs(p[q] - xc[q]) * fN;
+                    W = t > T(0) ? W * t : T(0);
+                }
+#pragma unroll
+                for (int q = 0; q <= D; ++q) s[q] = fma(W, v[q], s[q]);
+            }
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q <= D; ++q) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
+    if (lane == 0) {
+        counts[c] = bin_start[c + 1] - bin_start[c];
+        s_mass[c] = -scale * s[0];
+#pragma unroll
+        for (int q = 0; q < D; ++q) s_mom[q * nc + c] = -scale * s[1 + q];
+    }
+}
+
 template <typename T, int D, int KER>
 cudaError_t launch_nw_t(const NwItems& a, int num_sms, cudaStream_t s)
 {
@@ -970,6 +1055,52 @@ cudaError_t launch_psicell(const fla_cloud& cl, const fla_mesh& m, double window
         else
             launch_pdl(k_psi_cells<double, 3>, dim3(cb), dim3(256), 0, s, (const double*)rec, bin_start, nc, scale, out.counts_dev,
                                                       (double*)out.s_mass_dev, (double*)out.s_mom_dev);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cic(const fla_cloud& cl, const fla_mesh& m, double window_dt, int per_cell, const uint32_t* perm,
+                       const uint32_t* bin_start, void* rec, const fla_psicell_out& out, DevStatus* st, cudaStream_t s)
+{
+    const int64_t nc = m.dim == 2 ? (int64_t)m.n * m.n : (int64_t)m.n * m.n * m.n;
+    PsiArgs a{};
+    a.state = cl.state_dev;
+    a.meta = cl.meta_dev;
+    a.batches = cl.batches_dev;
+    a.perm = perm;
+    a.bin_start = bin_start;
+    a.n = cl.n;
+    a.n_cells = nc;
+    a.inv_window = 1.0 / window_dt;
+    a.rec = rec;
+    a.status = st;
+    const double dx = 1.0 / m.n;
+    const double V = m.dim == 2 ? dx * dx : dx * dx * dx;
+    const double scale = per_cell ? 1.0 : 1.0 / V;
+    const unsigned rb = (unsigned)((cl.n + 255) / 256);
+    const unsigned cb = (unsigned)((nc * 32 + 255) / 256);
+    if (cl.dtype != FLA_F64) {
+        if (cl.n > 0) {
+            if (m.dim == 2) launch_pdl(k_cic_records<float, 2>, dim3(rb), dim3(256), 0, s, a);
+            else launch_pdl(k_cic_records<float, 3>, dim3(rb), dim3(256), 0, s, a);
+        }
+        if (m.dim == 2)
+            launch_pdl(k_cic_cells<float, 2>, dim3(cb), dim3(256), 0, s, (const float*)rec, bin_start, m.n,
+                       (float)scale, out.counts_dev, (float*)out.s_mass_dev, (float*)out.s_mom_dev);
+        else
+            launch_pdl(k_cic_cells<float, 3>, dim3(cb), dim3(256), 0, s, (const float*)rec, bin_start, m.n,
+                       (float)scale, out.counts_dev, (float*)out.s_mass_dev, (float*)out.s_mom_dev);
+    } else {
+        if (cl.n > 0) {
+            if (m.dim == 2) launch_pdl(k_cic_records<double, 2>, dim3(rb), dim3(256), 0, s, a);
+            else launch_pdl(k_cic_records<double, 3>, dim3(rb), dim3(256), 0, s, a);
+        }
+        if (m.dim == 2)
+            launch_pdl(k_cic_cells<double, 2>, dim3(cb), dim3(256), 0, s, (const double*)rec, bin_start, m.n, scale,
+                       out.counts_dev, (double*)out.s_mass_dev, (double*)out.s_mom_dev);
+        else
+            launch_pdl(k_cic_cells<double, 3>, dim3(cb), dim3(256), 0, s, (const double*)rec, bin_start, m.n, scale,
+                       out.counts_dev, (double*)out.s_mass_dev, (double*)out.s_mom_dev);
     }
     return cudaGetLastError();
 }

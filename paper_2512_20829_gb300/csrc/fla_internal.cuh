@@ -238,5 +238,7 @@ cudaError_t launch_gather2d(const fla_mesh& m, const fla_deposit_cfg& cfg, const
 cudaError_t launch_psicell(const fla_cloud& cl, const fla_mesh& m, double window_dt, int per_cell,
                            const uint32_t* perm, const uint32_t* bin_start, void* rec, const fla_psicell_out& out,
                            DevStatus* st, cudaStream_t s);
+cudaError_t launch_cic(const fla_cloud& cl, const fla_mesh& m, double window_dt, int per_cell, const uint32_t* perm,
+                       const uint32_t* bin_start, void* rec, const fla_psicell_out& out, DevStatus* st, cudaStream_t s);
 
 }  // namespace fla

@@ -31,7 +31,8 @@ MAX_VORTICES = 16
 
 EXPORTED = ["fla_abi_version", "fla_status_string", "fla_create", "fla_destroy", "fla_state_layout",
             "fla_carrier_nodes_bytes", "fla_carrier_sample", "fla_batch_deadline", "fla_advance",
-            "fla_workspace_size", "fla_cell_bins", "fla_deposit_sources", "psicell_deposit", "fla_sync_status",
+            "fla_workspace_size", "fla_cell_bins", "fla_deposit_sources", "psicell_deposit", "cic_deposit",
+            "fla_sync_status",
             "fla_profile_enable", "fla_profile_read", "fla_phase_name", "fla_fold_bytes", "fla_mlp_pack",
             "fla_mlp_forward", "fla_learn_workspace_size", "fla_learn_grad", "fla_adam_step",
             "fla_batch_workspace_size", "fla_batch_create", "fla_batch_run", "fla_batch_set_step",
@@ -121,6 +122,7 @@ def lib() -> C.CDLL:
         L.fla_cell_bins.argtypes = [v, P(Cloud), P(Mesh), v, v, v, v, C.c_size_t, v]
         L.fla_deposit_sources.argtypes = [v, P(Cloud), P(Mesh), P(DepositCfg), P(Sources), v, C.c_size_t, v]
         L.psicell_deposit.argtypes = [v, P(Cloud), P(Mesh), d, i32, P(PsicellOut), v, C.c_size_t, v]
+        L.cic_deposit.argtypes = [v, P(Cloud), P(Mesh), d, i32, P(PsicellOut), v, C.c_size_t, v]
         L.fla_sync_status.argtypes = [v, v, P(DeviceStatus), C.c_int]
         L.fla_profile_enable.argtypes = [v, C.c_int, C.c_int]
         L.fla_profile_read.argtypes = [v, i32, P(C.c_double), P(i64), P(i64)]
@@ -576,6 +578,15 @@ def psicell(ctx: Context, cloud: DeviceCloud, m: Mesh, window_dt: float, out: Ps
     po = out.struct()
     check(lib().psicell_deposit(ctx.handle, C.byref(cs), C.byref(m), float(window_dt), 1 if per_cell else 0,
                                 C.byref(po), _ptr(ws), ws.numel(), _stream_ptr(stream)), "psicell_deposit")
+
+
+def cic(ctx: Context, cloud: DeviceCloud, m: Mesh, window_dt: float, out: PsicellFields, ws, per_cell: bool = False,
+        stream=None):
+    """Cloud-In-Cell sources of a parcel cloud into out (counts are the box counts)."""
+    cs = cloud.struct()
+    po = out.struct()
+    check(lib().cic_deposit(ctx.handle, C.byref(cs), C.byref(m), float(window_dt), 1 if per_cell else 0,
+                            C.byref(po), _ptr(ws), ws.numel(), _stream_ptr(stream)), "cic_deposit")
 
 
 def aligned_ws(ws):
