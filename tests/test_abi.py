@@ -187,3 +187,37 @@ def test_batch_workspace_size_and_argument_checks(lib):
     assert lib.fla_batch_workspace_size((fla.BatchItem * 1)(bad), 1, C.byref(nb)) == -6
     assert lib.fla_batch_workspace_size(items, 0, C.byref(nb)) == -1
     assert lib.fla_batch_workspace_size(None, 1, C.byref(nb)) == -1
+
+
+def test_noalloc_binning_rejects_the_clouds_the_workspace_version_rejects(lib):
+    """fla_cell_bins_noalloc checks its arguments with the library's shared cloud
+    checks (those of fla_cell_bins) before its size limit: bad dtype, bad kind, a
+    fold guard on a parcel cloud, a non-finite delta, a misaligned release table,
+    a missing meta array and a mesh of the wrong dimension are all FLA_ERR_ARG,
+    with nothing enqueued (no GPU is touched here)."""
+    f = lib.fla_cell_bins_noalloc
+    f.argtypes = [C.POINTER(fla.Cloud), C.POINTER(fla.Mesh), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    f.restype = C.c_int
+    state = np.zeros(64 * 4, np.float32)
+    meta = np.zeros(16, np.uint32)
+    batches = np.zeros(8, np.float64)
+    keys = np.zeros(16, np.uint32)
+
+    def cloud(**kw):
+        c = fla.Cloud()
+        c.kind, c.dim, c.dtype, c.n_batches, c.n = fla.CLOUD_FLA, 2, fla.F32, 1, 16
+        c.state_dev = state.ctypes.data
+        c.meta_dev = meta.ctypes.data
+        c.batches_dev = batches.ctypes.data
+        c.delta = 0.0
+        for k, v in kw.items():
+            setattr(c, k, v)
+        return c
+    m2, m3 = fla.mesh(2, 8), fla.mesh(3, 8)
+    bad = [cloud(dtype=7), cloud(kind=5), cloud(kind=fla.CLOUD_LPT, fold_dev=state.ctypes.data, tau_fold=0.01),
+           cloud(delta=float("nan")), cloud(batches_dev=batches.ctypes.data + 4), cloud(meta_dev=None)]
+    for c in bad:
+        assert f(C.byref(c), C.byref(m2), keys.ctypes.data, keys.ctypes.data, keys.ctypes.data, None) == -1
+    assert f(C.byref(cloud()), C.byref(m3), keys.ctypes.data, keys.ctypes.data, keys.ctypes.data, None) == -1
+    big = cloud(n=262_145)
+    assert f(C.byref(big), C.byref(m2), keys.ctypes.data, keys.ctypes.data, keys.ctypes.data, None) == -3

@@ -5,8 +5,12 @@ is formed in the cloud's precision; per cell the GPU sums at most the parcels
 of the 3^dim cells around it in a fixed order.  Counts (the box counts) are
 bit-exact; the sources are compared element by element against
 sum_i W_ic |w a_i| (the size of the terms each cell adds): 1e-12 of it in
-double precision, 1e-5 in single precision (a few roundings of the weight and
-a 32-lane sum).
+double precision, 1e-5 in single precision (a few roundings of the product and
+a 32-lane sum), plus, in single precision, the absolute error of each tent
+factor 1 - |x - x_c| N: the rounded centre, difference, product with N and
+subtraction from 1 leave at most (N + 3) u (u = 2^-24), so a weight is off by
+at most d (N + 3) u whatever its size, times sum |w a| over the parcels of
+the 3^dim cells around the cell.
 """
 import numpy as np
 import pytest
@@ -38,6 +42,21 @@ def _run(ctx, s, N, dtype, w, window_dt=0.01, per_cell=False):
             out.s_mom.double().cpu().numpy().T)
 
 
+def _near_abs(s, N, w, window_dt=0.01, per_cell=False):
+    """Per cell, sum |w a| (the largest of the components) over the parcels binned in
+    the 3^dim cells around it, in the sources' scaling."""
+    d = s.dim
+    D = O.dep_struct(dim=d, N=N, kernel=0, h_min=0.5 / N, h_max=0.5 / N, p=1.0, window_dt=window_dt,
+                     per_cell=per_cell)
+    _, pm, pv = O.psicell(D, s.x.astype(np.float64), np.abs(s.acc), s.status, s.batch, w, fp32_keys=False)
+    box = np.maximum(np.abs(pm), np.abs(pv).max(axis=1)).reshape((N,) * d)   # axes (z,) y, x
+    pad = np.pad(box, 1)
+    near = np.zeros_like(box)
+    for off in np.ndindex(*(3,) * d):
+        near += pad[tuple(slice(o, o + N) for o in off)]
+    return near.ravel()
+
+
 def _oracle(s, N, w, window_dt=0.01, per_cell=False, fp32_keys=False):
     """fp32_keys: the box counts' keys in single precision, as a single-precision
     cloud forms them (x N floored in the cloud's precision; the tent weights do
@@ -58,9 +77,11 @@ def test_cic_matches_oracle(ctx, dim, N, n, dtype):
     gc, gm, gv = _run(ctx, s, N, dtype, w)
     oc, om, ov, am, av = _oracle(s, N, w, fp32_keys=dtype == fla.F32)
     tol = 1e-12 if dtype == fla.F64 else 1e-5
+    absw = 0.0 if dtype == fla.F64 else dim * (N + 3) * 2.0 ** -24 * _near_abs(s, N, w)
     assert np.array_equal(gc, oc)
-    assert np.all(np.abs(gm - om) <= tol * am + 1e-300)
-    assert np.all(np.abs(gv - ov) <= tol * av + 1e-300)
+    assert np.all(np.abs(gm - om) <= tol * am + absw + 1e-300)
+    absv = absw[:, None] if dtype != fla.F64 else 0.0
+    assert np.all(np.abs(gv - ov) <= tol * av + absv + 1e-300)
 
 
 def test_cic_full_size_jet_mesh(ctx):
@@ -70,9 +91,10 @@ def test_cic_full_size_jet_mesh(ctx):
     w = np.array([0.7, 1.1, 1.3, 0.9])
     gc, gm, gv = _run(ctx, s, N, fla.F32, w, per_cell=True)
     oc, om, ov, am, av = _oracle(s, N, w, per_cell=True, fp32_keys=True)
+    absw = 2 * (N + 3) * 2.0 ** -24 * _near_abs(s, N, w, per_cell=True)
     assert np.array_equal(gc, oc)
-    assert np.all(np.abs(gm - om) <= 1e-5 * am + 1e-300)
-    assert np.all(np.abs(gv - ov) <= 1e-5 * av + 1e-300)
+    assert np.all(np.abs(gm - om) <= 1e-5 * am + absw + 1e-300)
+    assert np.all(np.abs(gv - ov) <= 1e-5 * av + absw[:, None] + 1e-300)
 
 
 def test_cic_edge_cases(ctx):
