@@ -528,8 +528,19 @@ __device__ __forceinline__ void rhs_x2(const df* y, const df* u, const df* G, df
     }
 }
 
-template <int D, bool FLA>
-__device__ __forceinline__ int advance_x2_one(const AdvX2Args& a, int64_t i)
+// The step-start state and the slope sum of one droplet (registers).  Keeping
+// them in shared memory instead, to fit more warps per SM, was slower on the 3D
+// cone (512 ms per run with 3 blocks per SM, 605 ms with 4 and spills, against
+// 448 ms in registers at 8 warps per SM).
+template <int NY>
+struct RegVec {
+    df v[NY];
+    __device__ __forceinline__ df get(int q) const { return v[q]; }
+    __device__ __forceinline__ void set(int q, df x) { v[q] = x; }
+};
+
+template <int D, bool FLA, class VecY, class VecK>
+__device__ __forceinline__ int advance_x2_one(const AdvX2Args& a, int64_t i, VecY& y, VecK& ks)
 {
     constexpr int kind = FLA ? FLA_CLOUD_FLA : FLA_CLOUD_LPT;
     constexpr int NP = state_planes(kind, D);
@@ -543,18 +554,19 @@ __device__ __forceinline__ int advance_x2_one(const AdvX2Args& a, int64_t i)
     bool active = (meta & FLA_META_ACTIVE) != 0;
     if (!active && (ss < a.step0 || ss >= a.step0 + a.nsteps)) return 0;
 
-    float sh[NP * 4], sl[NP * 4];
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-        load4<float>(a.state, p * a.n + i, sh + 4 * p);
-        load4<float>(a.state, (NP + p) * a.n + i, sl + 4 * p);
-    }
-    df y[NY];
-#pragma unroll
-    for (int q = 0; q < NY; ++q) y[q] = df{sh[q], sl[q]};
     float acc[1 + D];
+    {
+        float sh[NP * 4], sl[NP * 4];
 #pragma unroll
-    for (int q = 0; q <= D; ++q) acc[q] = a.reset ? 0.0f : sh[OA + q];
+        for (int p = 0; p < NP; ++p) {
+            load4<float>(a.state, p * a.n + i, sh + 4 * p);
+            load4<float>(a.state, (NP + p) * a.n + i, sl + 4 * p);
+        }
+#pragma unroll
+        for (int q = 0; q < NY; ++q) y.set(q, df{sh[q], sl[q]});
+#pragma unroll
+        for (int q = 0; q <= D; ++q) acc[q] = a.reset ? 0.0f : sh[OA + q];
+    }
 
     const df St0 = df_of(__ldg(&B->St0));
     const float h32 = a.dt.hi, delta32 = a.delta.hi;
@@ -564,14 +576,17 @@ __device__ __forceinline__ int advance_x2_one(const AdvX2Args& a, int64_t i)
         if (!active) {
             if (s != ss) continue;
             // release: v0 = u(x0); J = I, W = dv0/dx0 = grad u(x0) (initial data of Eq. 8)
-            interp_x2<D>(a, y, u, G);
+            df x0[D];
 #pragma unroll
-            for (int q = 0; q < D; ++q) y[D + q] = u[q];
+            for (int q = 0; q < D; ++q) x0[q] = y.get(q);
+            interp_x2<D>(a, x0, u, G);
+#pragma unroll
+            for (int q = 0; q < D; ++q) y.set(D + q, u[q]);
             if (FLA) {
 #pragma unroll
                 for (int q = 0; q < D * D; ++q) {
-                    y[2 * D + q] = df_of((q % (D + 1) == 0) ? 1.0f : 0.0f);
-                    y[2 * D + D * D + q] = G[q];
+                    y.set(2 * D + q, df_of((q % (D + 1) == 0) ? 1.0f : 0.0f));
+                    y.set(2 * D + D * D + q, G[q]);
                 }
             }
 #pragma unroll
@@ -595,9 +610,9 @@ __device__ __forceinline__ int advance_x2_one(const AdvX2Args& a, int64_t i)
         // The four RK4 stages run as a loop (not unrolled): the double-float
         // interpolation and right-hand side are long, and four inlined copies
         // overflow the instruction cache.
-        df k[NY], ks[NY], ys[NY];
+        df k[NY], ys[NY];
 #pragma unroll
-        for (int q = 0; q < NY; ++q) ys[q] = y[q];
+        for (int q = 0; q < NY; ++q) ys[q] = y.get(q);
 #pragma unroll 1
         for (int stage = 0; stage < 4; ++stage) {
             interp_x2<D>(a, ys, u, G);
@@ -610,64 +625,91 @@ __device__ __forceinline__ int advance_x2_one(const AdvX2Args& a, int64_t i)
                 acc[0] = fmaf(h32, mdot, acc[0]);
 #pragma unroll
                 for (int q = 0; q < D; ++q)
-                    acc[1 + q] = fmaf(h32, m * (u[q] - y[D + q]).hi * iS + mdot * y[D + q].hi, acc[1 + q]);
+                    acc[1 + q] = fmaf(h32, m * (u[q] - ys[D + q]).hi * iS + mdot * ys[D + q].hi, acc[1 + q]);
             }
             rhs_x2<D, FLA>(ys, u, G, stage == 0 ? iSa : (stage == 3 ? iSc : iSb), k);
-            // k1 + 2 k2 + 2 k3 + k4, and the next stage's state y + c k (c = dt/2, dt/2, dt)
+            // k1 + 2 k2 + 2 k3 + k4 (the factor 2 is exact), and the next stage's
+            // state y + c k (c = dt/2, dt/2, dt)
             const float wk = (stage == 1 || stage == 2) ? 2.0f : 1.0f;
             const df c = stage == 2 ? a.dt : a.half;
 #pragma unroll
-            for (int q = 0; q < NY; ++q) ks[q] = stage == 0 ? k[q] : ks[q] + k[q] * wk;
+            for (int q = 0; q < NY; ++q)
+                ks.set(q, stage == 0 ? k[q] : ks.get(q) + df{k[q].hi * wk, k[q].lo * wk});
             if (stage < 3) {
 #pragma unroll
-                for (int q = 0; q < NY; ++q) ys[q] = df_axpy(c, k[q], y[q]);
+                for (int q = 0; q < NY; ++q) ys[q] = df_axpy(c, k[q], y.get(q));
             }
         }
 #pragma unroll
-        for (int q = 0; q < NY; ++q) y[q] = df_axpy(a.sixth, ks[q], y[q]);
+        for (int q = 0; q < NY; ++q) y.set(q, df_axpy(a.sixth, ks.get(q), y.get(q)));
         // outflow: leaving [0,1]^dim ends the trajectory
         bool out = false;
 #pragma unroll
-        for (int q = 0; q < D; ++q) out |= df_lt(y[q], 0.0f) || df_gt(y[q], 1.0f);
+        for (int q = 0; q < D; ++q) out |= df_lt(y.get(q), 0.0f) || df_gt(y.get(q), 1.0f);
         if (out) {
             active = false;
             meta = (meta & ~FLA_META_ACTIVE) | FLA_META_DEAD;
             break;
         }
     }
+    {
+        float sh[NP * 4], sl[NP * 4];
 #pragma unroll
-    for (int q = 0; q < NY; ++q) {
-        sh[q] = y[q].hi;
-        sl[q] = y[q].lo;
-    }
+        for (int q = 0; q < NP * 4; ++q) sh[q] = sl[q] = 0.0f;
 #pragma unroll
-    for (int q = 0; q <= D; ++q) {
-        sh[OA + q] = acc[q];
-        sl[OA + q] = 0.0f;
-    }
+        for (int q = 0; q < NY; ++q) {
+            const df v = y.get(q);
+            sh[q] = v.hi;
+            sl[q] = v.lo;
+        }
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
-        store4<float>(a.state, p * a.n + i, sh + 4 * p);
-        store4<float>(a.state, (NP + p) * a.n + i, sl + 4 * p);
+        for (int q = 0; q <= D; ++q) sh[OA + q] = acc[q];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            store4<float>(a.state, p * a.n + i, sh + 4 * p);
+            store4<float>(a.state, (NP + p) * a.n + i, sl + 4 * p);
+        }
     }
     a.meta[i] = meta;
     return integrated;
 }
 
+constexpr int kAdvX2Threads = 128;
+
+// The 2D step fits in 128 registers (4 blocks per SM; uncapped it takes 187 and
+// runs 8 % slower); the 3D step keeps its 255.
 template <int D, bool FLA>
-__global__ void __launch_bounds__(128) k_advance_x2(AdvX2Args a)
+constexpr int x2_min_blocks() { return D == 2 && FLA ? 4 : 1; }
+
+template <int D, bool FLA>
+__global__ void __launch_bounds__(kAdvX2Threads, x2_min_blocks<D, FLA>()) k_advance_x2(AdvX2Args a)
 {
     pdl_entry();
+    constexpr int NY = FLA ? 2 * D + 2 * D * D : 2 * D;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int n = i < a.n ? advance_x2_one<D, FLA>(a, i) : 0;
-    __shared__ int s_sum[4];
+    int n = 0;
+    if (i < a.n) {
+        RegVec<NY> y, ks;
+        n = advance_x2_one<D, FLA>(a, i, y, ks);
+    }
+    __shared__ int s_sum[kAdvX2Threads / 32];
     const int w = __reduce_add_sync(0xffffffffu, n);
     if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = w;
     __syncthreads();
     if (threadIdx.x == 0) {
-        const long long t = (long long)s_sum[0] + s_sum[1] + s_sum[2] + s_sum[3];
+        long long t = 0;
+#pragma unroll
+        for (int q = 0; q < kAdvX2Threads / 32; ++q) t += s_sum[q];
         if (t) atomicAdd(&a.status->droplet_steps, (unsigned long long)t);
     }
+}
+
+template <int D, bool FLA>
+cudaError_t launch_x2(const AdvX2Args& b, cudaStream_t s)
+{
+    const unsigned blocks = (unsigned)((b.n + kAdvX2Threads - 1) / kAdvX2Threads);
+    launch_pdl(k_advance_x2<D, FLA>, dim3(blocks), dim3(kAdvX2Threads), 0, s, b);
+    return cudaGetLastError();
 }
 
 // Batched clouds of one dimension (single precision, FLA): droplet g of the
@@ -766,15 +808,8 @@ cudaError_t launch_advance(const fla_cloud& cl, const fla_mesh& m, const void* n
         b.delta = df_host(cl.delta);
         b.reset = reset ? 1 : 0;
         b.status = st;
-        const unsigned blocks = (unsigned)((b.n + 127) / 128);
-        if (cl.dim == 2) {
-            if (fla) launch_pdl(k_advance_x2<2, true>, dim3(blocks), dim3(128), 0, s, b);
-            else launch_pdl(k_advance_x2<2, false>, dim3(blocks), dim3(128), 0, s, b);
-        } else {
-            if (fla) launch_pdl(k_advance_x2<3, true>, dim3(blocks), dim3(128), 0, s, b);
-            else launch_pdl(k_advance_x2<3, false>, dim3(blocks), dim3(128), 0, s, b);
-        }
-        return cudaGetLastError();
+        if (cl.dim == 2) return fla ? launch_x2<2, true>(b, s) : launch_x2<2, false>(b, s);
+        return fla ? launch_x2<3, true>(b, s) : launch_x2<3, false>(b, s);
     }
     if (cl.dtype == FLA_F32 && fla && a.fold) {
         FoldLayout L = fold_layout(cl.dim, cl.n);
