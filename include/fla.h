@@ -338,7 +338,10 @@ int cic_deposit(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, doub
  * Learned bandwidth correction.  The paper has no counterpart: a small
  * network g corrects each droplet's smoothing length,
  *   h = clamp(h0 |det J|^p * exp(clip(g(f), -2, 2)), h_min, h_max),
- * for the spherical kernel (Eq. 14 with h of Eq. 15).  g is
+ * for the spherical kernel (Eq. 14 with h of Eq. 15), except near fold
+ * caustics: for droplets with |det J| < 1e-2 the plain kernel is the fallback
+ * (g is evaluated but not applied), because n = n0/|det J| is singular there
+ * and a bandwidth learned away from the folds does not transfer to them.  g is
  * 6 -> 64 -> 64 -> 64 -> 1 with SiLU after the hidden layers, evaluated on the
  * tensor cores with BF16 weights and activations and FP32 accumulation (the
  * last layer in FP32 on the CUDA cores).  The features of a droplet are

@@ -571,10 +571,16 @@ void ora_record(const ora_dep* D, const double* x, const double* J, const double
         if (D->mlp) {      /* learned correction: h <- h exp(clip(g(f), -2, 2)) */
             ora_mlp_features(d, J, n0, h0, 1.0 / D->N, r->f);
             r->c = ora_mlp_forward(D->mlp, r->f, NULL, NULL, NULL, NULL);
-            double ct = r->c < -2.0 ? -2.0 : (r->c > 2.0 ? 2.0 : r->c);
-            corr = exp(ct);
-            h *= corr;
-            r->dh_dc = (r->c > -2.0 && r->c < 2.0 && h > D->h_min && h < D->h_max);
+            /* it stays off near fold caustics (|det J| < 1e-2, in the precision of the
+             * truncation decision), where the plain kernel is the fallback: n is
+             * singular there and a bandwidth learned away from folds does not transfer */
+            double ad_fold = D->fp32_decision ? fabs(det_decision(d, J, D->plain, fold)) : adet;
+            if (ad_fold >= 1e-2) {
+                double ct = r->c < -2.0 ? -2.0 : (r->c > 2.0 ? 2.0 : r->c);
+                corr = exp(ct);
+                h *= corr;
+                r->dh_dc = (r->c > -2.0 && r->c < 2.0 && h > D->h_min && h < D->h_max);
+            }
         }
         if (h < D->h_min) h = D->h_min;
         if (h > D->h_max) h = D->h_max;

@@ -358,6 +358,9 @@ __global__ void __launch_bounds__(256) k_records(RecArgs a)
     }
 }
 
+// |det J| below which the learned correction is not applied (see fla.h).
+constexpr double kLearnFoldTau = 1e-2;
+
 // Network features of a droplet (see fla.h), single precision.
 template <int D>
 __device__ __forceinline__ void mlp_features(const float* J, double adet, float n, double h0, double dx, float* f)
@@ -437,7 +440,10 @@ __global__ void __launch_bounds__(kMlpRows) k_records_mlp(RecArgs a)
         const float c = mlp_cta_forward(m, f, &ok);
         all_ok &= ok;
         if (valid) {
-            const float ct = fminf(fmaxf(c, -2.0f), 2.0f);
+            // near a fold caustic (|det J| < 1e-2) the plain kernel is the fallback: n is
+            // singular there and no bandwidth learned away from it transfers
+            const bool fold = adet < kLearnFoldTau;
+            const float ct = fold ? 0.0f : fminf(fmaxf(c, -2.0f), 2.0f);
             float r[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) r[q] = 0.0f;
@@ -452,7 +458,7 @@ __global__ void __launch_bounds__(kMlpRows) k_records_mlp(RecArgs a)
             if (a.mlp_out) a.mlp_out[i] = c;
             if (a.aux) {
                 a.aux[2 * j] = c;
-                a.aux[2 * j + 1] = (h_free && c > -2.0f && c < 2.0f) ? 1.0f : 0.0f;
+                a.aux[2 * j + 1] = (!fold && h_free && c > -2.0f && c < 2.0f) ? 1.0f : 0.0f;
             }
         }
     }

@@ -216,10 +216,17 @@ def _square_to_disc(a: np.ndarray, b: np.ndarray):
     return r * np.cos(phi), r * np.sin(phi)
 
 
-def abc_jet_3d(scale: int = 1, nsteps: int = 500) -> Workload:
-    """128^3 cells, ABC flow + round jet, 2^21 seeds in a cone, anisotropic kernel."""
+def abc_jet_3d(scale: int = 1, nsteps: int = 500, seeds_side: int | None = None, flow_seed: int | None = None,
+               kernel: int = KERNEL_ANISO) -> Workload:
+    """128^3 cells, ABC flow + round jet, 2^21 seeds in a cone, anisotropic kernel.
+
+    ``scale`` divides the mesh and the seed lattice per axis; ``seeds_side``
+    sets the seed lattice (n_side^3 seeds) independently of the mesh.
+    ``flow_seed`` (None: the canonical flow) draws the ABC amplitudes and the
+    jet radius within +-10 % of (1, 0.7, 0.43) and 0.05, for families of
+    flows of the same kind.  ``kernel`` selects the deposit kernel."""
     N = 128 // scale
-    n_side = 128 // scale
+    n_side = seeds_side if seeds_side is not None else 128 // scale
     g = (np.arange(n_side) + 0.5) / n_side
     X1, X2, X3 = np.meshgrid(g, g, g, indexing="ij")
     xi1, xi2, xi3 = X1.ravel(), X2.ravel(), X3.ravel()
@@ -233,13 +240,19 @@ def abc_jet_3d(scale: int = 1, nsteps: int = 500) -> Workload:
     n = x0.shape[0]
     v_cone = math.pi * (length * math.tan(half_angle)) ** 2 * length / 3.0
     h0 = (v_cone / n) ** (1.0 / 3.0)
-    car = Carrier(kind=CARRIER_ABC_JET_3D, dim=3, jet_amp=1.0, jet_radius=0.05)
+    abc, radius = np.array([1.0, 0.7, 0.43]), 0.05
+    if flow_seed is not None:
+        rng = np.random.default_rng(flow_seed)
+        abc = abc * (1.0 + 0.1 * rng.uniform(-1.0, 1.0, 3))
+        radius = radius * (1.0 + 0.1 * rng.uniform(-1.0, 1.0))
+    car = Carrier(kind=CARRIER_ABC_JET_3D, dim=3, abc=abc, jet_amp=1.0, jet_radius=radius)
     fla = Cloud(kind=CLOUD_FLA, x0=x0, batch=np.zeros(n, np.int32), step_start=np.zeros(1, np.int32),
                 St0=np.array([1.0]), n0=np.array([1.0]), h0=np.array([h0]))
     dx = 1.0 / N
-    return Workload(name=f"abc_jet_3d_{N}^3_{n}fla", dim=3, n_cells_axis=N, dt=1e-3, nsteps=nsteps,
+    tag = "" if flow_seed is None else f"_flow{flow_seed}"
+    return Workload(name=f"abc_jet_3d_{N}^3_{n}fla{tag}", dim=3, n_cells_axis=N, dt=1e-3, nsteps=nsteps,
                     window=10, delta=-0.2, carrier=car, fla=fla, lpt=None,
-                    kernel=KERNEL_ANISO, h_min=0.5 * dx, h_max=2.0 * dx)
+                    kernel=kernel, h_min=0.5 * dx, h_max=2.0 * dx)
 
 
 # ---------------------------------------------------------------------------
