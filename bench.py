@@ -363,10 +363,10 @@ def rooflines(prof, st, wl, form, peaks, clocks):
                           f"({'FP64' if fp64_eval else 'FP32'} evaluation)")
         else:
             # HBM phases: algorithmic bytes (each value moved once)
-            if name == "keys":
-                byts = n * (16 + 4 + 4)                       # position plane, meta, key
-            elif name == "sort":
-                byts = n * 16                                 # key and index read and written once
+            if name == "sort":
+                # keys, sort and bin starts (one kernel): position plane and meta read,
+                # sorted keys and permutation written, bin starts written
+                byts = n * (16 + 4 + 8) + wl.n_cells * 4
             elif name == "bins":
                 byts = binned * 4 + wl.n_cells * 4            # sorted keys read, bin starts written
             elif name == "records":

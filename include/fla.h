@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define FLA_ABI_VERSION 6
+#define FLA_ABI_VERSION 7
 
 /* cudaStream_t without including the CUDA headers. */
 typedef struct CUstream_st* fla_stream_t;
@@ -44,7 +44,7 @@ typedef enum {
     FLA_ERR_CUDA = -2,         /* a CUDA runtime call or kernel launch failed */
     FLA_ERR_WORKSPACE = -3,    /* workspace pointer missing, misaligned or too small */
     FLA_ERR_NONFINITE = -4,    /* reported by fla_sync_status: non-finite records seen */
-    FLA_ERR_TIMEOUT = -5,      /* reserved for bounded device-side waits */
+    FLA_ERR_TIMEOUT = -5,      /* a bounded device-side wait ran out (fla_sync_status) */
     FLA_ERR_UNSUPPORTED = -6   /* valid but not implemented combination */
 } fla_status;
 
@@ -197,9 +197,15 @@ typedef struct {
     uint64_t droplet_steps;    /* droplet steps integrated by fla_advance (active droplet x step) */
     uint64_t pairs;            /* (cell, droplet) pairs inside the truncated kernels, summed over deposits */
     uint64_t fold_steps;       /* of droplet_steps, those whose J and W were integrated in double precision */
-    uint32_t flags;            /* reserved, 0 */
+    uint32_t flags;            /* FLA_STATUS_* bits: a bounded device-side wait that ran out */
     uint32_t pad;
 } fla_device_status;
+
+/* fla_device_status.flags.  A device-side wait that runs out (about a second)
+ * sets its bit and returns; the output of the call it belongs to is not valid,
+ * the context stays usable, and fla_sync_status returns FLA_ERR_TIMEOUT. */
+#define FLA_STATUS_MLP_TIMEOUT 1u  /* the tensor-core MLP's mbarrier wait */
+#define FLA_STATUS_WAIT_TIMEOUT 2u /* a look-back wait of the cell binning (inter-CTA) */
 
 /* Phases of the path, for fla_profile_read. */
 enum {
@@ -444,7 +450,8 @@ int fla_batch_set_tuning(fla_batch_plan* plan, int32_t advance_threads, int32_t 
 void fla_batch_destroy(fla_batch_plan* plan);
 
 /* Read the device status block (synchronises `stream`); reset != 0 zeroes it
- * afterwards.  Returns FLA_ERR_NONFINITE when nonfinite > 0, else FLA_OK. */
+ * afterwards.  Returns FLA_ERR_TIMEOUT when a FLA_STATUS_* timeout bit is set,
+ * else FLA_ERR_NONFINITE when nonfinite > 0, else FLA_OK. */
 int fla_sync_status(fla_ctx* ctx, fla_stream_t stream, fla_device_status* out, int reset);
 
 /* Allocation-free cell binning, for callers that cannot allocate device
@@ -485,6 +492,17 @@ int fla_cell_bins_noalloc(const fla_cloud* cloud, const fla_mesh* mesh, uint32_t
 int fla_profile_enable(fla_ctx* ctx, int enable, int reset);
 int fla_profile_read(fla_ctx* ctx, int32_t n_phases, double* ms, int64_t* launches, int64_t* calls);
 const char* fla_phase_name(int32_t phase);
+
+/* Test hook for the bounded device-side waits (no paper passage: the waits
+ * are this library's).  what = FLA_STALL_BINNING makes the next binning of this
+ * context (fla_cell_bins, a deposit or a parcel deposit) leave one look-back
+ * word of its first radix pass unpublished, so that the tiles after it wait
+ * for it until their limit (about a second) runs out.  They then set the abort
+ * word and FLA_STATUS_WAIT_TIMEOUT and return: the call's output is not valid,
+ * fla_sync_status returns FLA_ERR_TIMEOUT, and the context stays usable.  The
+ * hook acts once and clears itself.  FLA_ERR_ARG for unknown bits. */
+#define FLA_STALL_BINNING 1u
+int fla_test_stall(fla_ctx* ctx, uint32_t what);
 
 #ifdef __cplusplus
 }

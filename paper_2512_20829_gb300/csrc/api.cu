@@ -61,7 +61,7 @@ namespace {
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct WsLayout {
-    size_t keys[2], vals[2], counts, totals, bin_start, misc, rec, tiles, temp, total;
+    size_t keys[2], vals[2], scratch, bin_start, misc, rec, tiles, temp, total;
 };
 
 // The load-balanced gather serves single-precision 2D clouds with the spherical kernel.
@@ -80,8 +80,7 @@ WsLayout layout(const fla_mesh& m, int dtype, int kernel, int64_t n)
     size_t o = 0;
     for (int b = 0; b < 2; ++b) { L.keys[b] = o; o += up256(nn * 4); }
     for (int b = 0; b < 2; ++b) { L.vals[b] = o; o += up256(nn * 4); }
-    L.counts = o; o += up256((size_t)sort_counts_words(n) * 4);
-    L.totals = o; o += up256((size_t)kSortTotalsWords * 4);
+    L.scratch = o; o += up256(bin_plan(n, cells_of(m)).scratch_bytes);
     L.bin_start = o; o += up256(((size_t)cells_of(m) + 1) * 4);
     L.misc = o; o += 256;
     L.rec = o; o += up256(rec_bytes);
@@ -139,32 +138,27 @@ struct PhaseScope {
     }
 };
 
-// keys + sort; returns the buffer index that holds the sorted keys / permutation.
-int bin_cloud(fla_ctx* ctx, const fla_cloud& c, const fla_mesh& m, void* ws, const WsLayout& L, cudaStream_t s,
-              int* cur_out, uint32_t* zero = nullptr, int nzero = 0)
+// Keys, sort and bin starts (into bin_start, n_cells + 1 words) of a cloud
+// with n > 0: one kernel; *cur_out = the buffer that holds the sorted keys /
+// permutation.
+int bin_cloud(fla_ctx* ctx, const fla_cloud& c, const fla_mesh& m, void* ws, const WsLayout& L, uint32_t* bin_start,
+              cudaStream_t s, int* cur_out, uint32_t* zero = nullptr, int nzero = 0)
 {
-    SortWork w{};
+    BinWork w{};
     for (int b = 0; b < 2; ++b) {
         w.keys[b] = at<uint32_t>(ws, L.keys[b]);
         w.vals[b] = at<uint32_t>(ws, L.vals[b]);
     }
-    w.counts = at<uint32_t>(ws, L.counts);
-    w.totals = at<uint32_t>(ws, L.totals);
-    const int64_t nc = cells_of(m);
+    w.scratch = at<void>(ws, L.scratch);
+    const int stall = (ctx->stall & FLA_STALL_BINNING) != 0;
+    ctx->stall &= ~FLA_STALL_BINNING;
     cudaError_t e;
     {
-        PhaseScope ps(ctx, FLA_PHASE_KEYS, s, 1);
-        e = launch_cell_keys(c, m, w.keys[0], s, zero, nzero);
+        PhaseScope ps(ctx, FLA_PHASE_SORT, s, 1);   // keys, sort and bin starts
+        e = launch_binning(c, m, w, bin_start, (DevStatus*)ctx->status_dev, stall, s, zero, nzero);
     }
     if (e != cudaSuccess) return FLA_ERR_CUDA;
-    const int bits = sort_bits((uint32_t)nc);
-    const int passes = sort_passes_n(bits, c.n);
-    {
-        PhaseScope ps(ctx, FLA_PHASE_SORT, s, 3 * passes);
-        e = launch_radix_sort(w, c.n, bits, 0, s);
-    }
-    if (e != cudaSuccess) return FLA_ERR_CUDA;
-    *cur_out = passes & 1;
+    *cur_out = bin_sorted_buffer(bin_plan(c.n, cells_of(m)));
     return FLA_OK;
 }
 
@@ -401,16 +395,13 @@ int fla_cell_bins(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, ui
         return cuda_status(cudaMemsetAsync(bin_start_dev, 0, (size_t)(nc + 1) * 4, s));
     }
     int cur = 0;
-    st = bin_cloud(ctx, *cloud, *mesh, ws, L, s, &cur);
+    st = bin_cloud(ctx, *cloud, *mesh, ws, L, bin_start_dev, s, &cur);
     if (st != FLA_OK) return st;
     const uint32_t* ks = at<uint32_t>(ws, L.keys[cur]);
     const uint32_t* vs = at<uint32_t>(ws, L.vals[cur]);
     if (cudaMemcpyAsync(keys_sorted_dev, ks, (size_t)cloud->n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return FLA_ERR_CUDA;
-    if (cudaMemcpyAsync(perm_dev, vs, (size_t)cloud->n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return FLA_ERR_CUDA;
-    PhaseScope ps(ctx, FLA_PHASE_BINS, s, 1);
-    return cuda_status(launch_bin_start(ks, cloud->n, nc, bin_start_dev, s));
+    return cuda_status(cudaMemcpyAsync(perm_dev, vs, (size_t)cloud->n * 4, cudaMemcpyDeviceToDevice, s));
 }
 
 namespace {
@@ -453,13 +444,8 @@ int deposit_impl(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, con
         if (cudaMemsetAsync(bins, 0, (size_t)(nc + 1) * 4, s) != cudaSuccess) return FLA_ERR_CUDA;
     } else {
         int cur = 0;
-        st = bin_cloud(ctx, *cloud, *mesh, ws, L, s, &cur, ext, 8);   // the keys kernel clears misc
+        st = bin_cloud(ctx, *cloud, *mesh, ws, L, bins, s, &cur, ext, 8);   // the keys kernel clears misc
         if (st != FLA_OK) return st;
-        {
-            PhaseScope ps(ctx, FLA_PHASE_BINS, s, 1);
-            if (launch_bin_start(at<uint32_t>(ws, L.keys[cur]), cloud->n, nc, bins, s) != cudaSuccess)
-                return FLA_ERR_CUDA;
-        }
         {
             PhaseScope ps(ctx, FLA_PHASE_RECORDS, s, 1);
             if (launch_records(*cloud, *mesh, *cfg, at<uint32_t>(ws, L.vals[cur]), bins, nc, at<void>(ws, L.rec),
@@ -488,7 +474,7 @@ int deposit_impl(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, con
 }
 
 // Which of the sort's ping-pong buffers holds the sorted order of a cloud of n.
-int sorted_buffer(const fla_mesh& m, int64_t n) { return sort_passes_n(sort_bits((uint32_t)cells_of(m)), n) & 1; }
+int sorted_buffer(const fla_mesh& m, int64_t n) { return bin_sorted_buffer(bin_plan(n, cells_of(m))); }
 
 struct LearnLayout {
     size_t q, aux, dldc, partial, scal, total;
@@ -606,10 +592,8 @@ int parcel_deposit(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, d
     if (cloud->n == 0) {
         if (cudaMemsetAsync(bins, 0, (size_t)(nc + 1) * 4, s) != cudaSuccess) return FLA_ERR_CUDA;
     } else {
-        st = bin_cloud(ctx, *cloud, *mesh, ws, L, s, &cur);
+        st = bin_cloud(ctx, *cloud, *mesh, ws, L, bins, s, &cur);
         if (st != FLA_OK) return st;
-        PhaseScope ps(ctx, FLA_PHASE_BINS, s, 1);
-        if (launch_bin_start(at<uint32_t>(ws, L.keys[cur]), cloud->n, nc, bins, s) != cudaSuccess) return FLA_ERR_CUDA;
     }
     PhaseScope ps(ctx, FLA_PHASE_PSICELL, s, cloud->n > 0 ? 2 : 1);
     if (cic)
@@ -632,6 +616,13 @@ int psicell_deposit(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, 
     return parcel_deposit(ctx, cloud, mesh, window_dt, per_cell, out, ws, ws_bytes, stream, false);
 }
 
+int fla_test_stall(fla_ctx* ctx, uint32_t what)
+{
+    if (!ctx || (what & ~FLA_STALL_BINNING)) return FLA_ERR_ARG;
+    ctx->stall |= what;
+    return FLA_OK;
+}
+
 int fla_sync_status(fla_ctx* ctx, fla_stream_t stream, fla_device_status* out, int reset)
 {
     if (!ctx || !out) return FLA_ERR_ARG;
@@ -640,6 +631,7 @@ int fla_sync_status(fla_ctx* ctx, fla_stream_t stream, fla_device_status* out, i
         return FLA_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return FLA_ERR_CUDA;
     if (reset && cudaMemsetAsync(ctx->status_dev, 0, 64, s) != cudaSuccess) return FLA_ERR_CUDA;
+    if (out->flags & (FLA_STATUS_MLP_TIMEOUT | FLA_STATUS_WAIT_TIMEOUT)) return FLA_ERR_TIMEOUT;
     return out->nonfinite > 0 ? FLA_ERR_NONFINITE : FLA_OK;
 }
 

@@ -18,8 +18,8 @@ struct fla_batch_plan {
     double dt = 0.0;
     int window = 0;
     int64_t n_dim[2] = {0, 0};          // droplets of the 2D and 3D clouds
-    int sort_bits = 1;
-    SortWork sort{};
+    BinPlan bins{};
+    BinWork sort{};
     uint32_t* bin_start = nullptr;
     const BatchTile* tiles_order[2][kBatchGroups] = {};   // natural, interleaved
     // tuning
@@ -38,7 +38,7 @@ namespace {
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct BatchLayout {
-    size_t clouds, drop_pre, node_pre, misc, ext, cargs, tiles[2][kBatchGroups], keys[2], vals[2], counts, totals,
+    size_t clouds, drop_pre, node_pre, misc, ext, cargs, tiles[2][kBatchGroups], keys[2], vals[2], scratch,
         bin_start, rec[kBatchGroups], tile_cand[kBatchGroups], tile_items[kBatchGroups], cloud_cand, item_temp, total;
     int64_t n_total, cells_total, nodes_total, group_drops[kBatchGroups], group_items[kBatchGroups];
     int n_tiles[kBatchGroups];
@@ -116,8 +116,7 @@ BatchLayout batch_layout(const fla_batch_item* items, int n)
         for (int g = 0; g < kBatchGroups; ++g) { L.tiles[r][g] = o; o += up256(sizeof(BatchTile) * (size_t)L.n_tiles[g]); }
     for (int b = 0; b < 2; ++b) { L.keys[b] = o; o += up256(nn * 4); }
     for (int b = 0; b < 2; ++b) { L.vals[b] = o; o += up256(nn * 4); }
-    L.counts = o; o += up256((size_t)sort_counts_words(L.n_total) * 4);
-    L.totals = o; o += up256((size_t)kSortTotalsWords * 4);
+    L.scratch = o; o += up256(bin_plan(L.n_total, L.cells_total).scratch_bytes);
     L.bin_start = o; o += up256(((size_t)L.cells_total + 1) * 4);
     for (int g = 0; g < kBatchGroups; ++g) {
         const int rv = record_values(g < 2 ? 2 : 3, g & 1);
@@ -161,12 +160,9 @@ int issue_records(fla_ctx* ctx, fla_batch_plan* p, cudaStream_t s)
 {
     BatchDev& b = p->dev;
     if (b.n_total > 0) {
-        if (launch_batch_keys(b, p->sort.keys[0], s) != cudaSuccess) return FLA_ERR_CUDA;
-        if (launch_radix_sort(p->sort, b.n_total, p->sort_bits, 0, s) != cudaSuccess) return FLA_ERR_CUDA;
-        const int cur = sort_passes_n(p->sort_bits, b.n_total) & 1;
-        b.perm = p->sort.vals[cur];
-        if (launch_bin_start(p->sort.keys[cur], b.n_total, b.cells_total, p->bin_start, s) != cudaSuccess)
+        if (launch_batch_binning(b, p->sort, p->bin_start, (DevStatus*)ctx->status_dev, s) != cudaSuccess)
             return FLA_ERR_CUDA;
+        b.perm = p->sort.vals[bin_sorted_buffer(p->bins)];
     } else if (cudaMemsetAsync(p->bin_start, 0, ((size_t)b.cells_total + 1) * 4, s) != cudaSuccess) {
         return FLA_ERR_CUDA;
     }
@@ -201,7 +197,7 @@ int issue_window(fla_ctx* ctx, fla_batch_plan* p, cudaStream_t s)
 int window_launches(const fla_batch_plan* p)
 {
     int n = 2 + (p->n_dim[0] > 0) + (p->n_dim[1] > 0) + 1;   // carrier (2), advance, step
-    if (p->dev.n_total > 0) n += 1 + 3 * sort_passes_n(p->sort_bits, p->dev.n_total) + 1;
+    if (p->dev.n_total > 0) n += 1;   // keys, sort and bin starts: one kernel
     for (int g = 0; g < kBatchGroups; ++g) {
         if (p->dev.group_first[g + 1] > p->dev.group_first[g]) n += 1;
         if (p->dev.n_tiles[g] > 0) n += 3;   // gather plan, items, combine
@@ -419,11 +415,10 @@ extern "C" int fla_batch_create(fla_ctx* ctx, const fla_batch_item* items, int32
         p->sort.keys[k] = at<uint32_t>(ws, L.keys[k]);
         p->sort.vals[k] = at<uint32_t>(ws, L.vals[k]);
     }
-    p->sort.counts = at<uint32_t>(ws, L.counts);
-    p->sort.totals = at<uint32_t>(ws, L.totals);
+    p->sort.scratch = at<void>(ws, L.scratch);
     p->bin_start = at<uint32_t>(ws, L.bin_start);
     b.bin_start = p->bin_start;
-    p->sort_bits = sort_bits((uint32_t)L.cells_total);
+    p->bins = bin_plan(L.n_total, L.cells_total);
     *out = p;
     return FLA_OK;
 }

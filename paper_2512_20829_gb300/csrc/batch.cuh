@@ -2,8 +2,8 @@
 // advanced and deposited together, a few launches per window for all of them.
 //
 // The clouds share one global cell space: cloud k's cells occupy
-// [cell_off_k, cell_off_k + n_cells_k), so one key pass, one radix sort and one
-// bin-start pass bin every droplet of every cloud, and each cloud's sorted
+// [cell_off_k, cell_off_k + n_cells_k), so one key pass and one radix sort
+// (with the bin starts) bin every droplet of every cloud, and each cloud's sorted
 // records are contiguous.  Clouds are ordered by group (dim, kernel), so each
 // group's records are contiguous too and live in a record array of the
 // group's width.  Per-cloud parameters come from a device table.  The window
@@ -84,7 +84,9 @@ cudaError_t batch_prepare_advance();
 cudaError_t launch_batch_carrier(const BatchDev& b, double dt, cudaStream_t s);
 cudaError_t launch_batch_advance(const BatchDev& b, int dim, int64_t n_dim, int nsteps, double dt, bool reset,
                                  int threads, DevStatus* st, cudaStream_t s);
-cudaError_t launch_batch_keys(const BatchDev& b, uint32_t* keys, cudaStream_t s);
+// Keys, sort and bin starts (cells_total + 1 words) of all clouds: one kernel.
+cudaError_t launch_batch_binning(const BatchDev& b, const BinWork& w, uint32_t* bin_start, DevStatus* st,
+                                 cudaStream_t s);
 cudaError_t launch_batch_records(const BatchDev& b, int group, DevStatus* st, cudaStream_t s);
 cudaError_t launch_batch_gather(const BatchDev& b, int group, int ctas, DevStatus* st, int num_sms, cudaStream_t s);
 cudaError_t launch_batch_step(const BatchDev& b, int nsteps, cudaStream_t s);

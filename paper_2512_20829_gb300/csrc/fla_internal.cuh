@@ -22,6 +22,7 @@ struct fla_ctx {
     };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> pool;
+    unsigned int stall;   // fla_test_stall bits, cleared when used
 };
 
 namespace fla {
@@ -155,6 +156,19 @@ struct DevStatus {
     unsigned int flags, pad;
 };
 static_assert(sizeof(DevStatus) == sizeof(fla_device_status), "status block mirrors fla_device_status");
+constexpr unsigned int kFlagMlpTimeout = FLA_STATUS_MLP_TIMEOUT;
+constexpr unsigned int kFlagWaitTimeout = FLA_STATUS_WAIT_TIMEOUT;
+
+// Waits on words that other CTAs of the same grid publish give up after
+// kWaitLimitNs of the GPU's global timer (about a second), or at once when
+// another CTA has given up (its abort word is set).
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // Fold-guard array: planes of 4 doubles holding J[d*d] then W[d*d] (2D 8
 // values, 3D 18), then the hand-over list of the advance (n u32) and its
@@ -172,19 +186,63 @@ inline FoldLayout fold_layout(int dim, int64_t n)
     return L;
 }
 
-// Radix-sort scratch sizes (u32 words): tiles of 2,048 keys, digits of up to
-// 11 bits (2,048 values) for clouds of up to 2^21 droplets, 8 bits beyond.
+// Cell binning (binning.cu): one cooperative kernel per call over tiles of
+// 2,048 keys; radix digits of up to 11 bits (2,048 values) for clouds of up to
+// 2^21 droplets, 8 bits beyond.  Scratch besides the key and value buffers:
+// per-(pass, tile, digit) histograms, per-(block of 32 tiles, digit) sums,
+// per-(pass, digit) totals and per-chunk cell counts of the bin-start scan (all written by the kernel before it reads
+// them), then the barrier words, cleared before each call.  Where bin_start
+// directly follows the scratch (the workspace layouts place it there), one
+// memset clears the barrier words and bin_start.
 constexpr int64_t kSortTile = 2048;
-constexpr int64_t sort_tiles(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
-constexpr int64_t sort_digit_values(int64_t n) { return n <= (int64_t(1) << 21) ? 2048 : 256; }
-constexpr int64_t sort_counts_words(int64_t n) { return sort_digit_values(n) * sort_tiles(n > 0 ? n : 1); }
-constexpr int64_t kSortTotalsWords = 2048;
+constexpr int kSortMaxDigitBits = 11;
+constexpr int64_t kBinMaxChunks = 1024;         // chunks of cells of the bin-start scan
+constexpr size_t kBinControlBytes = 256;        // barrier counter, abort, done
+struct BinPlan {
+    int64_t n, n_cells;                         // droplets; cells (the key of droplets without a cell)
+    int bits, passes, width, tiles;
+    int64_t chunks, chunk_cells;
+    int64_t blocks;                             // blocks of 32 tiles of the tile-prefix scans
+    size_t off_hist, off_block, off_totals, off_chunk, off_clear, scratch_bytes;   // byte offsets; size
+};
+__host__ __device__ constexpr int sort_bits_of(uint64_t max_key)
+{
+    int b = 0;
+    while (b < 32 && (max_key >> b) != 0) ++b;
+    return b < 1 ? 1 : b;
+}
+__host__ __device__ constexpr size_t bin_up256(size_t x) { return (x + 255) & ~(size_t)255; }
+__host__ __device__ constexpr BinPlan bin_plan(int64_t n, int64_t n_cells)
+{
+    BinPlan p{};
+    p.n = n;
+    p.n_cells = n_cells;
+    p.bits = sort_bits_of((uint64_t)n_cells);
+    const int maxw = n <= (int64_t(1) << 21) ? kSortMaxDigitBits : 8;
+    p.passes = (p.bits + maxw - 1) / maxw;
+    p.width = (p.bits + p.passes - 1) / p.passes;
+    const int64_t nn = n > 0 ? n : 1;
+    p.tiles = (int)((nn + kSortTile - 1) / kSortTile);
+    const int64_t cells = n_cells + 1;
+    const int64_t blocks = (cells + kSortTile - 1) / kSortTile;
+    const int64_t per = (blocks + kBinMaxChunks - 1) / kBinMaxChunks;
+    p.chunk_cells = per * kSortTile;
+    p.chunks = (cells + p.chunk_cells - 1) / p.chunk_cells;
+    const size_t ndw = (size_t)1 << p.width;
+    p.blocks = (p.tiles + 31) / 32;
+    p.off_hist = 0;
+    p.off_block = bin_up256((size_t)p.passes * ndw * (size_t)p.tiles * 4);
+    p.off_totals = p.off_block + bin_up256((size_t)p.blocks * ndw * 4);
+    p.off_chunk = p.off_totals + bin_up256((size_t)p.passes * ndw * 4);
+    p.off_clear = p.off_chunk + bin_up256((size_t)p.chunks * 4);
+    p.scratch_bytes = p.off_clear + kBinControlBytes;
+    return p;
+}
 
-struct SortWork {
+struct BinWork {
     uint32_t* keys[2];
     uint32_t* vals[2];
-    uint32_t* counts;     // 256 * tiles
-    uint32_t* totals;     // 256
+    void* scratch;         // BinPlan::scratch_bytes
 };
 
 // Argument checks shared by the entry points: mesh shape and size; a cloud's
@@ -197,16 +255,15 @@ cudaError_t launch_carrier_sample(const fla_carrier_desc& c, const fla_mesh& m, 
                                   cudaStream_t s);
 cudaError_t launch_advance(const fla_cloud& cl, const fla_mesh& m, const void* nodes, int step0, int nsteps,
                            double dt, bool reset, DevStatus* st, int num_sms, cudaStream_t s);
-int sort_passes(int bits);
-int sort_passes_n(int bits, int64_t n);
-// zero[0, nzero) (nzero <= 256) is cleared by the launch: counters of later kernels.
-cudaError_t launch_cell_keys(const fla_cloud& cl, const fla_mesh& m, uint32_t* keys, cudaStream_t s,
-                             uint32_t* zero = nullptr, int nzero = 0);
-int sort_bits(uint32_t max_key);
-int radix_tiles(int64_t n);
-cudaError_t launch_radix_sort(SortWork w, int64_t n, int bits, int first_buf, cudaStream_t s);
-cudaError_t launch_bin_start(const uint32_t* keys_sorted, int64_t n, int64_t n_cells, uint32_t* bin_start,
-                             cudaStream_t s);
+// Binning of one cloud with n > 0 (one memset, one kernel): cell keys, the
+// stable sort of (key, index) and bin_start (n_cells + 1 words).  The sorted
+// keys and permutation end in buffer bin_sorted_buffer(plan).  zero[0, nzero)
+// (nzero <= 256) is cleared too: counters of the caller's later kernels.
+// stall (a test hook) keeps one CTA from arriving at the grid barrier after
+// the key phase, so that the others' waits run out.
+cudaError_t launch_binning(const fla_cloud& cl, const fla_mesh& m, const BinWork& w, uint32_t* bin_start,
+                           DevStatus* st, int stall, cudaStream_t s, uint32_t* zero = nullptr, int nzero = 0);
+inline int bin_sorted_buffer(const BinPlan& p) { return p.passes & 1; }
 cudaError_t launch_records(const fla_cloud& cl, const fla_mesh& m, const fla_deposit_cfg& cfg,
                            const uint32_t* perm, const uint32_t* bin_start, int64_t n_cells, void* rec,
                            unsigned int* ext_max, DevStatus* st, cudaStream_t s, float* aux = nullptr);

@@ -171,7 +171,6 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 
 // Bounded waits: about a second at most before giving up with an error flag.
 constexpr uint32_t kMbarPolls = 1u << 24;
-constexpr unsigned int kFlagMlpTimeout = 1u;
 
 // Shared state of one CTA's network evaluation.
 struct MlpCta {

@@ -22,10 +22,13 @@ using namespace fla;
 namespace {
 
 constexpr int64_t kMaxDroplets = FLA_NOALLOC_MAX_DROPLETS;
-constexpr int64_t kCountsWords = sort_counts_words(kMaxDroplets);
-// keys[2][max], vals[2][max], per-tile digit counts, digit totals  (u32 words)
-constexpr int64_t kWords = 4 * kMaxDroplets + kCountsWords + kSortTotalsWords;
-static_assert(sort_counts_words(kMaxDroplets) >= sort_counts_words(1), "counts sized for the largest cloud");
+// keys[2][max], vals[2][max], then the binning's scratch, sized for the
+// largest cell count a mesh may have (2^31 - 1 cells: the most radix passes)
+constexpr size_t kScratchBytes = bin_plan(kMaxDroplets, 2147483646LL).scratch_bytes;
+static_assert(bin_plan(kMaxDroplets, 1).scratch_bytes <= kScratchBytes, "scratch sized for the smallest mesh too");
+static_assert(bin_plan(kMaxDroplets, 262144).scratch_bytes <= kScratchBytes, "and for a mid-size one");
+static_assert(bin_plan(kMaxDroplets, 1LL << 22).scratch_bytes <= kScratchBytes, "and for 2^22 cells");
+constexpr int64_t kWords = 4 * kMaxDroplets + (int64_t)(kScratchBytes / 4);
 
 static __device__ __align__(256) uint32_t g_scratch[kWords];
 
@@ -66,23 +69,20 @@ extern "C" int fla_cell_bins_noalloc(const fla_cloud* cloud, const fla_mesh* mes
     uint32_t* base = nullptr;
     const int st = scratch_for_current_device(&base);
     if (st != FLA_OK) return st;
-    // Every word the sort reads is written earlier in the same call (keys by the
-    // key kernel, digit counts by each pass's histogram), so nothing needs clearing.
-    SortWork w{};
+    // Every scratch word the binning reads is written earlier in the same call.
+    // With no context there is no status block: a barrier wait that runs out
+    // ends the call without a report (its bin starts all zero).
+    BinWork w{};
     w.keys[0] = base;
     w.keys[1] = base + kMaxDroplets;
     w.vals[0] = base + 2 * kMaxDroplets;
     w.vals[1] = base + 3 * kMaxDroplets;
-    w.counts = base + 4 * kMaxDroplets;
-    w.totals = w.counts + kCountsWords;
-    if (launch_cell_keys(*cloud, *mesh, w.keys[0], s) != cudaSuccess) return FLA_ERR_CUDA;
-    const int bits = sort_bits((uint32_t)nc);
-    if (launch_radix_sort(w, cloud->n, bits, 0, s) != cudaSuccess) return FLA_ERR_CUDA;
-    const int cur = sort_passes_n(bits, cloud->n) & 1;
+    w.scratch = base + 4 * kMaxDroplets;
+    if (launch_binning(*cloud, *mesh, w, bin_start_dev, nullptr, 0, s) != cudaSuccess) return FLA_ERR_CUDA;
+    const int cur = bin_sorted_buffer(bin_plan(cloud->n, nc));
     if (cudaMemcpyAsync(keys_sorted_dev, w.keys[cur], (size_t)cloud->n * 4, cudaMemcpyDeviceToDevice, s) !=
         cudaSuccess)
         return FLA_ERR_CUDA;
-    if (cudaMemcpyAsync(perm_dev, w.vals[cur], (size_t)cloud->n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return FLA_ERR_CUDA;
-    return launch_bin_start(w.keys[cur], cloud->n, nc, bin_start_dev, s) == cudaSuccess ? FLA_OK : FLA_ERR_CUDA;
+    return cudaMemcpyAsync(perm_dev, w.vals[cur], (size_t)cloud->n * 4, cudaMemcpyDeviceToDevice, s) == cudaSuccess
+               ? FLA_OK : FLA_ERR_CUDA;
 }

@@ -18,7 +18,7 @@ from . import inputs as I
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfla.so")
 
-ABI_VERSION = 6            # FLA_ABI_VERSION of include/fla.h that these structures mirror
+ABI_VERSION = 7            # FLA_ABI_VERSION of include/fla.h that these structures mirror
 F32, F64, F32X2 = 0, 1, 2  # F32X2: compensated single precision (hi planes, then lo planes)
 CLOUD_FLA, CLOUD_LPT = 0, 1
 KERNEL_ISO, KERNEL_ANISO = 0, 1
@@ -36,7 +36,9 @@ EXPORTED = ["fla_abi_version", "fla_status_string", "fla_create", "fla_destroy",
             "fla_profile_enable", "fla_profile_read", "fla_phase_name", "fla_fold_bytes", "fla_mlp_pack",
             "fla_mlp_forward", "fla_learn_workspace_size", "fla_learn_grad", "fla_adam_step",
             "fla_batch_workspace_size", "fla_batch_create", "fla_batch_run", "fla_batch_set_step",
-            "fla_batch_tuning", "fla_batch_set_tuning", "fla_batch_destroy"]
+            "fla_batch_tuning", "fla_batch_set_tuning", "fla_batch_destroy", "fla_test_stall"]
+STALL_BINNING = 1           # fla_test_stall: one look-back word of the next binning stays unpublished
+STATUS_MLP_TIMEOUT, STATUS_WAIT_TIMEOUT = 1, 2   # fla_device_status.flags
 MLP_FEATURES, MLP_HIDDEN, MLP_PARAMS, MLP_PACKED_BYTES = 6, 64, 8833, 19472
 PREC_MIXED, PREC_PLAIN = 0, 1
 TAU_FOLD = 1e-2
@@ -124,6 +126,7 @@ def lib() -> C.CDLL:
         L.psicell_deposit.argtypes = [v, P(Cloud), P(Mesh), d, i32, P(PsicellOut), v, C.c_size_t, v]
         L.cic_deposit.argtypes = [v, P(Cloud), P(Mesh), d, i32, P(PsicellOut), v, C.c_size_t, v]
         L.fla_sync_status.argtypes = [v, v, P(DeviceStatus), C.c_int]
+        L.fla_test_stall.argtypes = [v, C.c_uint32]
         L.fla_profile_enable.argtypes = [v, C.c_int, C.c_int]
         L.fla_profile_read.argtypes = [v, i32, P(C.c_double), P(i64), P(i64)]
         L.fla_phase_name.argtypes = [i32]
@@ -209,12 +212,18 @@ class Context:
         check(lib().fla_profile_read(self.handle, n, ms, la, ca), "fla_profile_read")
         return {PHASES[i]: {"ms": ms[i], "launches": la[i], "calls": ca[i]} for i in range(n)}
 
-    def sync_status(self, stream=None, reset: bool = False) -> DeviceStatus:
+    def sync_status(self, stream=None, reset: bool = False, allow_timeout: bool = False) -> DeviceStatus:
+        """The device status block.  A device-side wait that ran out raises
+        (FLA_ERR_TIMEOUT) unless allow_timeout, when the caller reads .flags."""
         st = DeviceStatus()
         code = lib().fla_sync_status(self.handle, _stream_ptr(stream), C.byref(st), 1 if reset else 0)
-        if code not in (0, -4):
+        if code not in (0, -4) and not (allow_timeout and code == -5):
             check(code, "fla_sync_status")
         return st
+
+    def test_stall(self, what: int) -> None:
+        """Test hook: the next binning leaves one look-back word unpublished."""
+        check(lib().fla_test_stall(self.handle, what), "fla_test_stall")
 
 
 def mesh(dim: int, n: int) -> Mesh:

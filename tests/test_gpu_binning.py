@@ -1,5 +1,8 @@
 """Cell keys, stable sort and bin starts on the GPU are bit-identical to the
-oracle's keys, NumPy's stable argsort and searchsorted."""
+oracle's keys, NumPy's stable argsort and searchsorted; a look-back wait that
+runs out ends the call with a status flag and leaves the context usable."""
+import time
+
 import numpy as np
 import pytest
 
@@ -76,3 +79,30 @@ def test_large_sort_three_passes(ctx):
     """2^21 keys over 128^3 cells: 22-bit keys, three radix passes, 512 tiles."""
     s = I.synthetic_state(3, 2**21, 128, seed=12, inactive_frac=0.02, edge_cases=False)
     _check(ctx, s, 128, fla.F32)
+
+
+def test_lookback_wait_runs_out_and_context_survives(ctx):
+    """The test hook leaves tile 0's look-back words of the first radix pass
+    unpublished, so every later tile waits for them.  The waits give up after
+    about a second: the call ends, the status block carries
+    FLA_STATUS_WAIT_TIMEOUT (fla_sync_status: FLA_ERR_TIMEOUT), nothing is left
+    waiting (the stream synchronises), and the next binning, with the hook
+    cleared, is bit-exact again."""
+    s = I.synthetic_state(2, 70_000, 512, seed=7, inactive_frac=0.1)   # 35 tiles
+    m = fla.mesh(2, 512)
+    cl = gpu_cloud_from_state(s, fla.F32)
+    ws = fla.aligned_ws(fla.workspace(m, fla.F32, fla.KERNEL_ANISO, cl.n))
+    assert ctx.sync_status(reset=True).flags == 0
+    ctx.test_stall(fla.STALL_BINNING)
+    t0 = time.perf_counter()
+    _, _, bins = fla.cell_bins(ctx, cl, m, ws)
+    with pytest.raises(fla.FlaError, match="-5"):
+        ctx.sync_status()
+    dt = time.perf_counter() - t0
+    st = ctx.sync_status(reset=True, allow_timeout=True)
+    print(f"\nstalled binning ended after {dt:.2f} s with flags {st.flags:#x}")
+    assert st.flags & fla.STATUS_WAIT_TIMEOUT
+    assert 0.5 < dt < 30.0
+    assert not bins.any()        # bin starts cleared: every cell empty
+    _check(ctx, s, 512, fla.F32)
+    assert ctx.sync_status(reset=True).flags == 0
