@@ -237,16 +237,22 @@ int fla_state_layout(int32_t kind, int32_t dim, int32_t* n_planes, int32_t* off_
 
 /* Bytes of a node array for fla_carrier_sample: (n+1)^dim nodes, each holding
  * u (dim values) then grad u (dim*dim, row-major, G_ij = du_i/dx_j), padded
- * to 8 values (2D) or 12 values (3D).  FLA_F32X2: the FLA_F32 array of the
- * high parts followed by the same array of the low parts (twice the bytes). */
+ * to 8 values (2D) or 12 values (3D).  FLA_F32X2: two arrays of the FLA_F32
+ * layout, a then b (each value is a + b), then a 256-byte tail that
+ * fla_carrier_sample uses for the components' largest magnitudes. */
 size_t fla_carrier_nodes_bytes(const fla_mesh* mesh, int32_t dtype);
 
 /* Sample the analytic carrier and its gradient at time t on the mesh nodes
  * (Eq. 3 needs u at the droplet, Eq. 8 grad u; both are interpolated from
  * these nodes by fla_advance).  nodes_dev: fla_carrier_nodes_bytes bytes,
  * 16-byte aligned.  FLA_F32X2 evaluates the carrier in double precision and
- * stores each value as the nearest float hi and the nearest float to the
- * remainder, lo. */
+ * splits each value v into a + b: a is v rounded to a multiple of its
+ * component's grid Q = 2^(e - 11), where 2^e exceeds the component's largest
+ * magnitude over the nodes (so a has at most 12 significant bits), and b is
+ * the nearest float to v - a (|b| <= Q/2 + 2^(e - 25); a + b is within
+ * 2^(e - 36) of v).
+ * Weights on a coarse grid then multiply a exactly, which keeps the advance's
+ * interpolation accurate to about 2^(e - 30) at single-precision cost. */
 int fla_carrier_sample(fla_ctx* ctx, const fla_carrier_desc* carrier, const fla_mesh* mesh, double t,
                        int32_t dtype, void* nodes_dev, fla_stream_t stream);
 

@@ -441,7 +441,7 @@ struct AdvX2Args {
     float* state;          // hi planes, then lo planes
     uint32_t* meta;
     const fla_batch* batches;
-    const float* nodes;    // hi node array, then lo node array
+    const float* nodes;    // a node array, then b node array (k_carrier_split_x2)
     int64_t n, n_nodes;
     int N;
     int step0, nsteps;
@@ -451,13 +451,23 @@ struct AdvX2Args {
 };
 
 // Bi/trilinear interpolation of the double-float node values at the
-// double-float position x: the cell index is floor(x N) clamped to
-// [0, N - 1] and the fraction x N - i is exact in double-float, so the
-// weights and the weighted sums carry no single-precision rounding.
+// double-float position x.  The cell index is floor(x N) clamped to
+// [0, N - 1] and the fraction x N - i is exact in double-float; the corner
+// weights w are double-float products of the fractions.  Each node value is
+// stored as a + b, a on its component's grid Q (at most 12 significant bits,
+// |a| <= 2^11 Q) and b the rest (|b| <= Q/2).  With w = w1 + w2, w1 on the
+// grid 2^-10 (|w1| < 8 2^10 units while the fractions lie in (-1/2, 3/2)):
+//   sum w v = sum w1 a  (exact: products below 2^22 units of 2^-10 Q, sums
+//                        below 2^24 units)
+//           + sum (w2 a + w b)   (terms of size 2^-11 of the component's
+//                                 scale, plain single precision)
+// so the result carries about 2^-30 of the component's largest magnitude, at
+// three single-precision operations per corner and value.
 template <int D>
 __device__ __forceinline__ void interp_x2(const AdvX2Args& a, const df* x, df* u, df* G)
 {
     constexpr int S = node_stride(D);
+    constexpr int NV = D + D * D;
     df f[D];
     int64_t base = 0, mul = 1;
     const int64_t nn = a.N + 1;
@@ -473,7 +483,9 @@ __device__ __forceinline__ void interp_x2(const AdvX2Args& a, const df* x, df* u
     df g[D];   // 1 - f
 #pragma unroll
     for (int q = 0; q < D; ++q) g[q] = df_of(1.0f) - f[q];
-    DotAcc acc[D + D * D];
+    float sa[NV], sb[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sa[q] = sb[q] = 0.0f;
 #pragma unroll
     for (int cnr = 0; cnr < (1 << D); ++cnr) {
         df w = (cnr & 1) ? f[0] : g[0];
@@ -485,20 +497,24 @@ __device__ __forceinline__ void interp_x2(const AdvX2Args& a, const df* x, df* u
             idx += bit * m2;
             m2 *= nn;
         }
-        float vh[S], vl[S];
+        const float w1 = __fmul_rn(rintf(__fmul_rn(w.hi, 1024.0f)), 1.0f / 1024.0f);
+        const float w2 = __fadd_rn(__fsub_rn(w.hi, w1), w.lo);   // w.hi - w1 is exact
+        float va[S], vb[S];
 #pragma unroll
         for (int c = 0; c < S / 4; ++c) {
-            load4<float>(a.nodes, idx * (S / 4) + c, vh + 4 * c);
-            load4<float>(a.nodes + a.n_nodes * S, idx * (S / 4) + c, vl + 4 * c);
+            load4<float>(a.nodes, idx * (S / 4) + c, va + 4 * c);
+            load4<float>(a.nodes + a.n_nodes * S, idx * (S / 4) + c, vb + 4 * c);
         }
 #pragma unroll
-        for (int q = 0; q < D + D * D; ++q)
-            acc[q] = cnr == 0 ? dot_first(w, df{vh[q], vl[q]}) : dot_add(acc[q], w, df{vh[q], vl[q]});
+        for (int q = 0; q < NV; ++q) {
+            sa[q] = __fmaf_rn(w1, va[q], sa[q]);
+            sb[q] = __fmaf_rn(w.hi, vb[q], __fmaf_rn(w2, va[q], sb[q]));
+        }
     }
 #pragma unroll
-    for (int q = 0; q < D; ++q) u[q] = dot_value(acc[q]);
+    for (int q = 0; q < D; ++q) u[q] = two_sum(sa[q], sb[q]);
 #pragma unroll
-    for (int q = 0; q < D * D; ++q) G[q] = dot_value(acc[D + q]);
+    for (int q = 0; q < D * D; ++q) G[q] = two_sum(sa[D + q], sb[D + q]);
 }
 
 // Right-hand side of Eqs. 3 and 8 in double-float.

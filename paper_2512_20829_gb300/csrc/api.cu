@@ -304,7 +304,9 @@ size_t fla_carrier_nodes_bytes(const fla_mesh* mesh, int32_t dtype)
     if (!mesh_ok(mesh) || !dtype_ok(dtype)) return 0;
     const size_t nn = (size_t)mesh->n + 1;
     const size_t nodes = mesh->dim == 2 ? nn * nn : nn * nn * nn;
-    return nodes * node_stride(mesh->dim) * (dtype == FLA_F32 ? 4 : 8);   // F32X2: hi then lo array
+    if (dtype == FLA_F32X2)   // the a array, the b array, the tail of component maxima
+        return nodes * node_stride(mesh->dim) * 8 + kNodesX2TailBytes;
+    return nodes * node_stride(mesh->dim) * (dtype == FLA_F32 ? 4 : 8);
 }
 
 int fla_carrier_sample(fla_ctx* ctx, const fla_carrier_desc* c, const fla_mesh* mesh, double t, int32_t dtype,

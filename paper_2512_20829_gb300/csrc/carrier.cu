@@ -211,44 +211,94 @@ __global__ void __launch_bounds__(256) k_carrier_sample(CarrierArgs p, T* __rest
     sample_node<T, D>(p, nodes, k);
 }
 
-// Double-float nodes (FLA_F32X2): each value evaluated in double precision and
-// stored as the nearest float (hi array) and the nearest float to the
-// remainder (lo array, n_nodes * stride values further on).
+// Double-float nodes (FLA_F32X2), first pass: each value evaluated in double
+// precision and stored as the nearest float (first array) and the nearest
+// float to the remainder (second array, n_nodes * stride values further on);
+// the largest |value| of each component goes to its word of the tail (float
+// bits, cleared before the launch).
 template <int D>
 __global__ void __launch_bounds__(256) k_carrier_sample_x2(CarrierArgs p, float* __restrict__ nodes, int64_t total)
 {
     pdl_entry();
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= total) return;
-    const int nn = p.N + 1;
-    double x[3];
-    int64_t r = k;
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        x[a] = (double)(r % nn) / (double)p.N;
-        r /= nn;
-    }
-    double u[3], G[9];
-    eval_carrier<double, D>(p, x, u, G);
     constexpr int S = node_stride(D);
-    double v[12];
-#pragma unroll
-    for (int q = 0; q < 12; ++q) v[q] = 0.0;
-#pragma unroll
-    for (int a = 0; a < D; ++a) v[a] = u[a];
-#pragma unroll
-    for (int q = 0; q < D * D; ++q) v[D + q] = G[q];
+    __shared__ unsigned int s_max[S];
+    if (threadIdx.x < S) s_max[threadIdx.x] = 0u;
+    __syncthreads();
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     float hi[12], lo[12];
 #pragma unroll
-    for (int q = 0; q < 12; ++q) {
-        hi[q] = __double2float_rn(v[q]);
-        lo[q] = __double2float_rn(__dsub_rn(v[q], (double)hi[q]));
-    }
+    for (int q = 0; q < 12; ++q) hi[q] = lo[q] = 0.0f;
+    if (k < total) {
+        const int nn = p.N + 1;
+        double x[3];
+        int64_t r = k;
 #pragma unroll
-    for (int c = 0; c < S / 4; ++c) {
-        store4<float>(nodes, k * (S / 4) + c, hi + 4 * c);
-        store4<float>(nodes + total * S, k * (S / 4) + c, lo + 4 * c);
+        for (int a = 0; a < D; ++a) {
+            x[a] = (double)(r % nn) / (double)p.N;
+            r /= nn;
+        }
+        double u[3], G[9];
+        eval_carrier<double, D>(p, x, u, G);
+        double v[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) v[q] = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) v[a] = u[a];
+#pragma unroll
+        for (int q = 0; q < D * D; ++q) v[D + q] = G[q];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            hi[q] = __double2float_rn(v[q]);
+            lo[q] = __double2float_rn(__dsub_rn(v[q], (double)hi[q]));
+        }
+#pragma unroll
+        for (int c = 0; c < S / 4; ++c) {
+            store4<float>(nodes, k * (S / 4) + c, hi + 4 * c);
+            store4<float>(nodes + total * S, k * (S / 4) + c, lo + 4 * c);
+        }
     }
+    // |x| of a float orders like its bit pattern without the sign
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+        const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(hi[q]) & 0x7fffffffu);
+        if ((threadIdx.x & 31) == 0 && m) atomicMax(&s_max[q], m);
+    }
+    __syncthreads();
+    if (threadIdx.x < S && s_max[threadIdx.x])
+        atomicMax(reinterpret_cast<unsigned int*>(nodes + 2 * total * S) + threadIdx.x, s_max[threadIdx.x]);
+}
+
+// Second pass: each value v = hi + lo becomes a + b with a = RN(hi / Q) Q on
+// the component's grid Q = 2^(e - 11), where 2^e bounds the component's
+// largest |hi| (so |a / Q| <= 2^11, a has at most 12 significant bits), and
+// b = RN((hi - a) + lo) (hi - a is exact; |b| <= Q/2 + 2^(e - 25)).  a + b
+// is within 2^-24 |b|, about 2^(e - 36), of v.  The advance then sums weights
+// on a 2^-10 grid times a exactly in single precision (products of at most 22
+// bits on a common grid, partial sums below 2^24 units) and everything else,
+// 2^-11 of the value's scale, in plain single precision.
+template <int D>
+__global__ void __launch_bounds__(256) k_carrier_split_x2(float* __restrict__ nodes, int64_t total)
+{
+    pdl_entry();
+    constexpr int S = node_stride(D);
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= total * (S / 4)) return;
+    const int c0 = (int)(k % (S / 4)) * 4;
+    const unsigned int* mx = reinterpret_cast<const unsigned int*>(nodes + 2 * total * S);
+    float hi[4], lo[4];
+    load4<float>(nodes, k, hi);
+    load4<float>(nodes + total * S, k, lo);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int e;
+        frexpf(__uint_as_float(mx[c0 + q]), &e);     // largest |hi| < 2^e (e = 0 for an all-zero component)
+        const float iq = ldexpf(1.0f, 11 - e), qq = ldexpf(1.0f, e - 11);
+        const float a = __fmul_rn(rintf(__fmul_rn(hi[q], iq)), qq);
+        lo[q] = __fadd_rn(__fsub_rn(hi[q], a), lo[q]);
+        hi[q] = a;
+    }
+    store4<float>(nodes, k, hi);
+    store4<float>(nodes + total * S, k, lo);
 }
 
 // The carrier's arguments at time t (vortex centres carried with the jet and
@@ -342,8 +392,17 @@ cudaError_t launch_carrier_sample(const fla_carrier_desc& c, const fla_mesh& m, 
     const int threads = 256;
     const unsigned blocks = (unsigned)((total + threads - 1) / threads);
     if (dtype == FLA_F32X2) {
-        if (m.dim == 2) launch_pdl(k_carrier_sample_x2<2>, dim3(blocks), dim3(threads), 0, s, p, (float*)nodes, total);
-        else launch_pdl(k_carrier_sample_x2<3>, dim3(blocks), dim3(threads), 0, s, p, (float*)nodes, total);
+        const int S = node_stride(m.dim);
+        float* tail = (float*)nodes + 2 * total * S;
+        if (cudaMemsetAsync(tail, 0, kNodesX2TailBytes, s) != cudaSuccess) return cudaGetLastError();
+        const unsigned vblocks = (unsigned)((total * (S / 4) + threads - 1) / threads);
+        if (m.dim == 2) {
+            launch_pdl(k_carrier_sample_x2<2>, dim3(blocks), dim3(threads), 0, s, p, (float*)nodes, total);
+            launch_pdl(k_carrier_split_x2<2>, dim3(vblocks), dim3(threads), 0, s, (float*)nodes, total);
+        } else {
+            launch_pdl(k_carrier_sample_x2<3>, dim3(blocks), dim3(threads), 0, s, p, (float*)nodes, total);
+            launch_pdl(k_carrier_split_x2<3>, dim3(vblocks), dim3(threads), 0, s, (float*)nodes, total);
+        }
         return cudaGetLastError();
     }
     if (dtype == FLA_F32) {

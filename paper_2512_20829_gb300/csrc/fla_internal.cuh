@@ -110,6 +110,9 @@ __host__ __device__ constexpr int acc_offset(int kind, int dim)
     return kind == FLA_CLOUD_FLA ? 2 * dim + 2 * dim * dim : 2 * dim;
 }
 __host__ __device__ constexpr int node_stride(int dim) { return dim == 2 ? 8 : 12; }
+// Double-float (FLA_F32X2) node arrays end with this tail: the largest |value|
+// of each component (float bits), from which the split into a + b is formed.
+constexpr size_t kNodesX2TailBytes = 256;
 
 // Record of one binned droplet for the kernel-regression gather, in sorted order.
 // Single precision (the weight is 2^(c r^2 + lih), resp. 2^(-q log2(e)/2 + lpref)):

@@ -51,15 +51,26 @@ def test_carrier_nodes_match_oracle(ctx, idx, dtype):
     fla.carrier_sample(ctx, fla.carrier_desc(car), m, t, dtype, nodes)
     stride = 8 if dim == 2 else 12
     g = nodes.double().cpu().numpy()
-    if dtype == fla.F32X2:   # the array of high parts, then the array of low parts
-        hi, lo = g[: g.size // 2], g[g.size // 2:]
-        # each pair is the nearest float and the nearest float to the remainder
-        assert np.all(np.abs(lo) <= np.spacing(np.abs(hi).astype(np.float32)).astype(np.float64) / 2)
-        g = hi + lo
-    g = g.reshape(-1, stride)[:, :dim + dim * dim]
     o = O.carrier_nodes(car, t, N)
+    nv = dim + dim * dim
+    if dtype == fla.F32X2:
+        # the a array, then the b array, then the tail of component maxima: each a
+        # is a multiple of its component's grid Q = 2^(e - 11), 2^e above the
+        # component's largest magnitude, and |b| <= Q/2 + |lo| with the low part
+        # |lo| <= 2^(e - 25) of the double value's float split
+        total = o.shape[0] * stride
+        A = g[:total].reshape(-1, stride)[:, :nv]
+        B = g[total:2 * total].reshape(-1, stride)[:, :nv]
+        M = np.abs(A + B).max(axis=0)
+        e = np.frexp(M.astype(np.float32))[1].astype(np.float64)
+        Q = np.ldexp(1.0, (e - 11).astype(int))
+        assert np.array_equal(A / Q, np.rint(A / Q)) and np.all(np.abs(A / Q) <= 2048)
+        assert np.all(np.abs(B) <= Q * (0.5 + 2.0 ** -13))
+        g, tol = A + B, 2.0 ** -34      # a + b within 2^-24 |b| <= 2^(e - 36) of the value
+    else:
+        g = g.reshape(-1, stride)[:, :nv]
+        tol = 2e-6 if dtype == fla.F32 else 1e-13
     scale = np.abs(o).max(axis=0) + 1e-30
-    tol = 2e-6 if dtype == fla.F32 else 1e-13
     assert np.all(np.abs(g - o) <= tol * scale), np.abs(g - o).max(axis=0) / scale
 
 
