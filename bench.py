@@ -462,6 +462,28 @@ def batch_leg(ctx, fla, I, flush, steps):
             times.append(ea.elapsed_time(eb))
     batched = float(np.median(times))
     tun = b.tuning()
+    tun.update(b.mode())
+    # each window form timed the same way: one persistent kernel per window,
+    # and the launch per phase and group
+    forms = {}
+    for name, mode in (("persistent", fla.BATCH_PERSISTENT), ("launches", fla.BATCH_LAUNCHES)):
+        b.set_mode(mode)
+        with torch.cuda.stream(s):
+            b.reset(s)
+            b.run(windows, stream=s)
+            torch.cuda.synchronize()
+            ft = []
+            for _ in range(steps):
+                b.reset(s)
+                flush.add_(1.0)
+                ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ea.record(s)
+                b.run(windows, stream=s)
+                eb.record(s)
+                torch.cuda.synchronize()
+                ft.append(ea.elapsed_time(eb))
+        forms[name] = {"ms_per_run": round(float(np.median(ft)), 4),
+                       "launches_per_run": b.tuning()["launches_per_window"] * windows}
     del b
     torch.cuda.empty_cache()
     # the same clouds through the per-cloud calls
@@ -490,7 +512,7 @@ def batch_leg(ctx, fla, I, flush, steps):
             "cells": cells, "ms_per_run": round(batched, 4), "cells_per_s": cells * windows / (batched * 1e-3),
             "unbatched_ms_per_run": round(unbatched, 4), "speedup_vs_unbatched": round(unbatched / batched, 3),
             "launches_per_run": tun["launches_per_window"] * windows, "unbatched_launches_per_run": launches,
-            "tuning": tun}
+            "tuning": tun, "window_forms": forms}
 
 
 def run_ours(args):

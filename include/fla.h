@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define FLA_ABI_VERSION 7
+#define FLA_ABI_VERSION 8
 
 /* cudaStream_t without including the CUDA headers. */
 typedef struct CUstream_st* fla_stream_t;
@@ -453,6 +453,25 @@ int fla_batch_tuning(const fla_batch_plan* plan, int32_t* advance_threads, int32
  * order 0 natural / 1 interleaved) and skips the tuning. */
 int fla_batch_set_tuning(fla_batch_plan* plan, int32_t advance_threads, int32_t gather_ctas_per_sm,
                          int32_t tile_order);
+/* How a window runs.  FLA_BATCH_LAUNCHES: one kernel per phase and group
+ * (carrier, advance per dimension, binning, records and gather plan, items
+ * and combine per group, step), about 14 per window.  FLA_BATCH_PERSISTENT:
+ * one cooperative kernel per window (a memset of its barrier words before
+ * it) that runs the same phases, compiled from the same sources, separated
+ * by grid barriers; every CTA of the grid is resident, and a barrier wait
+ * gives up after about a second (FLA_STATUS_WAIT_TIMEOUT, fla_sync_status
+ * returns FLA_ERR_TIMEOUT, the window's outputs are then not valid).  Both
+ * give the same results bit for bit.  FLA_BATCH_AUTO (the default): the
+ * first fla_batch_run of at least five windows times its fourth window as
+ * the persistent kernel and its fifth as launches and keeps the faster
+ * (fewer windows: launches).  Changing the mode drops the plan's graph.
+ * FLA_ERR_UNSUPPORTED for FLA_BATCH_PERSISTENT where the kernel cannot run
+ * (no CTA of it fits an SM). */
+enum { FLA_BATCH_AUTO = 0, FLA_BATCH_LAUNCHES = 1, FLA_BATCH_PERSISTENT = 2 };
+int fla_batch_set_mode(fla_batch_plan* plan, int32_t mode);
+/* The mode in use (FLA_BATCH_AUTO until the first run has chosen) and the
+ * tuner's window times in ms (persistent, launches; 0 when not timed). */
+int fla_batch_mode(const fla_batch_plan* plan, int32_t* mode, float* persistent_ms, float* launches_ms);
 void fla_batch_destroy(fla_batch_plan* plan);
 
 /* Read the device status block (synchronises `stream`); reset != 0 zeroes it
@@ -501,13 +520,16 @@ const char* fla_phase_name(int32_t phase);
 
 /* Test hook for the bounded device-side waits (no paper passage: the waits
  * are this library's).  what = FLA_STALL_BINNING makes the next binning of this
- * context (fla_cell_bins, a deposit or a parcel deposit) leave one look-back
- * word of its first radix pass unpublished, so that the tiles after it wait
- * for it until their limit (about a second) runs out.  They then set the abort
- * word and FLA_STATUS_WAIT_TIMEOUT and return: the call's output is not valid,
- * fla_sync_status returns FLA_ERR_TIMEOUT, and the context stays usable.  The
- * hook acts once and clears itself.  FLA_ERR_ARG for unknown bits. */
+ * context (fla_cell_bins, a deposit or a parcel deposit) keep one CTA from
+ * arriving at its first grid barrier; FLA_STALL_BATCH_WINDOW does the same
+ * for the first barrier of the next persistent batch window issued on this
+ * context.  The other CTAs wait until their limit (about a second) runs out,
+ * then set the abort word and FLA_STATUS_WAIT_TIMEOUT and return, and so does
+ * the stalled CTA: the call's output is not valid, fla_sync_status returns
+ * FLA_ERR_TIMEOUT, and the context stays usable.  Each bit acts once and
+ * clears itself.  FLA_ERR_ARG for unknown bits. */
 #define FLA_STALL_BINNING 1u
+#define FLA_STALL_BATCH_WINDOW 2u
 int fla_test_stall(fla_ctx* ctx, uint32_t what);
 
 #ifdef __cplusplus

@@ -1,7 +1,8 @@
 """Build libfla.so in-tree with nvcc for sm_103a (GB300).
 
 Each translation unit is compiled in parallel, then linked into one shared
-library with the CUDA runtime linked statically.  ``records.cu`` is compiled
+library with the CUDA runtime linked statically (nvcc device-links the
+relocatable objects of the persistent window kernel).  ``records.cu`` is compiled
 without FMA contraction (its double-precision values decide the kernel's
 truncation test and are formed one rounding per operation).
 """
@@ -22,6 +23,12 @@ LIB = os.path.join(OUT_DIR, "libfla.so")
 SOURCES = ["api.cu", "carrier.cu", "advance.cu", "binning.cu", "records.cu", "deposit.cu", "gather2d.cu", "noalloc.cu",
            "mlp.cu", "learn.cu", "batch.cu"]
 NO_FMA = {"records.cu"}
+# The persistent window kernel (window.cu) calls phase functions that these
+# files define under FLA_WINDOW_PHASES: each is compiled a second time into
+# relocatable device code with the namespace renamed, so the phases keep their
+# file's flags and the kernels of the launch-per-phase path are unchanged.
+WINDOW_PHASES = ["carrier.cu", "advance.cu", "binning.cu", "records.cu", "deposit.cu"]
+WINDOW_FLAGS = ["-rdc=true", "-Dfla=fla_w", "-DFLA_WINDOW_PHASES", "-Xcompiler", "-fvisibility=hidden", "-maxrregcount=128"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -48,9 +55,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
               "-I", INCLUDE, "--expt-relaxed-constexpr"]
     procs = []
     objs = []
-    for src in SOURCES:
-        obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
-        cmd = [cc, *common, "-c", os.path.join(CSRC, src), "-o", obj]
+    units = [(src, src.replace(".cu", ".o"), []) for src in SOURCES]
+    units += [(src, src.replace(".cu", ".w.o"), WINDOW_FLAGS) for src in WINDOW_PHASES]
+    units.append(("window.cu", "window.o", WINDOW_FLAGS))
+    for src, oname, extra in units:
+        obj = os.path.join(OUT_DIR, oname)
+        cmd = [cc, *common, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if src in NO_FMA:
             cmd.insert(1, "-fmad=false")
         if verbose:

@@ -732,32 +732,38 @@ cudaError_t launch_x2(const AdvX2Args& b, cudaStream_t s)
 // group belongs to cloud k with pre[k] <= g < pre[k + 1] of the group's
 // prefix; the per-droplet work is that of k_advance.
 template <int D>
+__device__ __forceinline__ int batch_advance_droplet(const BatchDev& b, int first, int count, int64_t g, int nsteps,
+                                                     double dt, int reset, DevStatus* st)
+{
+    // droplets of the group's clouds are contiguous in the global droplet order
+    const int64_t base = b.drop_pre[first];
+    const int k = first + batch_find(b.drop_pre + first, count, base + g);
+    const BatchCloud& c = b.clouds[k];
+    AdvArgs a{};
+    a.state = c.state;
+    a.meta = c.meta;
+    a.batches = c.batches;
+    a.nodes = c.nodes;
+    a.n = c.n;
+    a.N = c.N;
+    a.step0 = *b.step;
+    a.nsteps = nsteps;
+    a.dt = dt;
+    a.delta = c.delta;
+    a.reset = reset;
+    a.status = st;
+    int nf = 0;
+    return advance_one<float, D, true, kPlain>(a, base + g - b.drop_pre[k], nf);
+}
+
+template <int D>
 __global__ void __launch_bounds__(256) k_batch_advance(BatchDev b, int first, int count, int64_t n_dim,
                                                        int nsteps, double dt, int reset, DevStatus* st)
 {
     pdl_entry();
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int n = 0, nf = 0;
-    if (g < n_dim) {
-        // droplets of the group's clouds are contiguous in the global droplet order
-        const int64_t base = b.drop_pre[first];
-        const int k = first + batch_find(b.drop_pre + first, count, base + g);
-        const BatchCloud& c = b.clouds[k];
-        AdvArgs a{};
-        a.state = c.state;
-        a.meta = c.meta;
-        a.batches = c.batches;
-        a.nodes = c.nodes;
-        a.n = c.n;
-        a.N = c.N;
-        a.step0 = *b.step;
-        a.nsteps = nsteps;
-        a.dt = dt;
-        a.delta = c.delta;
-        a.reset = reset;
-        a.status = st;
-        n = advance_one<float, D, true, kPlain>(a, base + g - b.drop_pre[k], nf);
-    }
+    int n = 0;
+    if (g < n_dim) n = batch_advance_droplet<D>(b, first, count, g, nsteps, dt, reset, st);
     __shared__ int s_sum[8];
     const int w = __reduce_add_sync(0xffffffffu, n);
     if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = w;
@@ -867,3 +873,24 @@ cudaError_t launch_batch_advance(const BatchDev& b, int dim, int64_t n_dim, int 
 }
 
 }  // namespace fla
+
+#ifdef FLA_WINDOW_PHASES
+// Phase of the persistent window kernel (window.cuh): the droplets of one
+// dimension's clouds, window sums reset.
+#include "window.cuh"
+namespace fla {
+
+__device__ int window_advance(const BatchDev& b, int dim, int64_t n_dim, int nsteps, double dt, DevStatus* st)
+{
+    if (n_dim == 0 || nsteps == 0) return 0;
+    const int g0 = batch_group(dim, 0);
+    const int first = b.group_first[g0], count = b.group_first[g0 + 2] - first;
+    int n = 0;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n_dim; g += (int64_t)gridDim.x * blockDim.x)
+        n += dim == 2 ? batch_advance_droplet<2>(b, first, count, g, nsteps, dt, 1, st)
+                      : batch_advance_droplet<3>(b, first, count, g, nsteps, dt, 1, st);
+    return n;
+}
+
+}  // namespace fla
+#endif

@@ -620,7 +620,7 @@ int psicell_deposit(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, 
 
 int fla_test_stall(fla_ctx* ctx, uint32_t what)
 {
-    if (!ctx || (what & ~FLA_STALL_BINNING)) return FLA_ERR_ARG;
+    if (!ctx || (what & ~(FLA_STALL_BINNING | FLA_STALL_BATCH_WINDOW))) return FLA_ERR_ARG;
     ctx->stall |= what;
     return FLA_OK;
 }

@@ -11,6 +11,12 @@
 
 using namespace fla;
 
+// The persistent window kernel (window.cu, its own compilation of the phases).
+extern "C" int fla_window_prepare(void);
+extern "C" int fla_window_issue(const void* batch_dev, const void* bin_work, uint32_t* bin_start, void* status,
+                                double dt, int window, int64_t n2, int64_t n3, int stall, uint32_t chunk,
+                                void* stream);
+
 struct fla_batch_plan {
     BatchDev dev;                       // device tables (pointers into the workspace)
     std::vector<BatchCloud> host;       // host copy of the cloud table
@@ -27,6 +33,10 @@ struct fla_batch_plan {
     int gather_ctas_per_sm = 2;
     int tile_order = 0;
     bool tuned = false;
+    int mode = FLA_BATCH_AUTO;          // requested window execution
+    int persistent = 0;                 // in use: one cooperative kernel per window
+    bool persistent_ok = false;         // the window kernel fits the device
+    float timed_ms[2] = {0.0f, 0.0f};   // the tuner's window: persistent, launches
     // graph of graph_windows windows
     cudaGraphExec_t exec = nullptr;
     int graph_windows = 0;
@@ -39,7 +49,8 @@ size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct BatchLayout {
     size_t clouds, drop_pre, node_pre, misc, ext, cargs, tiles[2][kBatchGroups], keys[2], vals[2], scratch,
-        bin_start, rec[kBatchGroups], tile_cand[kBatchGroups], tile_items[kBatchGroups], cloud_cand, item_temp, total;
+        bin_start, rec[kBatchGroups], tile_cand[kBatchGroups], tile_items[kBatchGroups], cloud_cand,
+        item_temp[kBatchGroups], total;
     int64_t n_total, cells_total, nodes_total, group_drops[kBatchGroups], group_items[kBatchGroups];
     int n_tiles[kBatchGroups];
 };
@@ -123,15 +134,17 @@ BatchLayout batch_layout(const fla_batch_item* items, int n)
         L.rec[g] = o;
         o += up256((size_t)L.group_drops[g] * rv * 4);
     }
-    size_t temp = 0;
     for (int g = 0; g < kBatchGroups; ++g) {
         L.tile_cand[g] = o; o += up256(4 * (size_t)L.n_tiles[g]);
         L.tile_items[g] = o; o += up256(4 * ((size_t)L.n_tiles[g] + 1));
-        const int dim = g < 2 ? 2 : 3;
-        temp = std::max(temp, (size_t)L.group_items[g] * (size_t)(dim + 2) * 256 * 4);
     }
     L.cloud_cand = o; o += up256(8 * (size_t)n);
-    L.item_temp = o; o += up256(temp);
+    // item partials, one region per group: the persistent window kernel runs
+    // the groups' work items in one phase
+    for (int g = 0; g < kBatchGroups; ++g) {
+        const int dim = g < 2 ? 2 : 3;
+        L.item_temp[g] = o; o += up256((size_t)L.group_items[g] * (size_t)(dim + 2) * 256 * 4);
+    }
     L.total = o;
     return L;
 }
@@ -184,8 +197,24 @@ int issue_gathers(fla_ctx* ctx, fla_batch_plan* p, int ctas_per_sm, int order, c
     return FLA_OK;
 }
 
+// One window as the persistent kernel (a memset of its barrier words, one
+// cooperative launch).
+int issue_persistent(fla_ctx* ctx, fla_batch_plan* p, cudaStream_t s)
+{
+    BatchDev& b = p->dev;
+    for (int g = 0; g < kBatchGroups; ++g) b.tiles[g] = p->tiles_order[p->tile_order][g];
+    b.perm = p->sort.vals[bin_sorted_buffer(p->bins)];
+    const int stall = (ctx->stall & FLA_STALL_BATCH_WINDOW) != 0;
+    ctx->stall &= ~FLA_STALL_BATCH_WINDOW;
+    return fla_window_issue(&b, &p->sort, p->bin_start, ctx->status_dev, p->dt, p->window, p->n_dim[0],
+                            p->n_dim[1], stall, nw_chunk(4), s) == (int)cudaSuccess
+               ? FLA_OK
+               : FLA_ERR_CUDA;
+}
+
 int issue_window(fla_ctx* ctx, fla_batch_plan* p, cudaStream_t s)
 {
+    if (p->persistent) return issue_persistent(ctx, p, s);
     int st = issue_advance(ctx, p, p->advance_threads, s);
     if (st == FLA_OK) st = issue_records(ctx, p, s);
     if (st == FLA_OK) st = issue_gathers(ctx, p, p->gather_ctas_per_sm, p->tile_order, s);
@@ -196,6 +225,7 @@ int issue_window(fla_ctx* ctx, fla_batch_plan* p, cudaStream_t s)
 // Kernel launches of one window (for the caller's launch accounting).
 int window_launches(const fla_batch_plan* p)
 {
+    if (p->persistent) return 1;
     int n = 2 + (p->n_dim[0] > 0) + (p->n_dim[1] > 0) + 1;   // carrier (2), advance, step
     if (p->dev.n_total > 0) n += 1;   // keys, sort and bin starts: one kernel
     for (int g = 0; g < kBatchGroups; ++g) {
@@ -261,6 +291,23 @@ int tune(fla_ctx* ctx, fla_batch_plan* p, int n_windows, cudaStream_t s)
         if (launch_batch_step(p->dev, p->window, s) != cudaSuccess) return -1;
         ++used;
     }
+    // then one whole window as the persistent kernel and one as launches
+    if (p->mode == FLA_BATCH_AUTO && p->persistent_ok && n_windows - used >= 2) {
+        float t[2];
+        for (int m = 0; m < 2; ++m) {
+            p->persistent = m == 0;
+            cudaEventRecord(ev.a, s);
+            if (issue_window(ctx, p, s) != FLA_OK) return -1;
+            cudaEventRecord(ev.b, s);
+            t[m] = ev.ms();
+            ++used;
+        }
+        p->persistent = t[0] < t[1];
+        p->timed_ms[0] = t[0];
+        p->timed_ms[1] = t[1];
+    } else {
+        p->persistent = p->mode == FLA_BATCH_PERSISTENT && p->persistent_ok;
+    }
     return used;
 }
 
@@ -290,6 +337,7 @@ extern "C" int fla_batch_create(fla_ctx* ctx, const fla_batch_item* items, int32
     if (!ws || ((uintptr_t)ws % 256) != 0 || ws_bytes < need) return FLA_ERR_WORKSPACE;
     const BatchLayout L = batch_layout(items, n_items);
     if (batch_prepare_gathers() != cudaSuccess || batch_prepare_advance() != cudaSuccess) return FLA_ERR_CUDA;
+    const bool persistent_ok = fla_window_prepare() > 0;
     fla_batch_plan* p = new (std::nothrow) fla_batch_plan();
     if (!p) return FLA_ERR_ARG;
     p->n_clouds = n_items;
@@ -400,7 +448,7 @@ extern "C" int fla_batch_create(fla_ctx* ctx, const fla_batch_item* items, int32
     b.tile_counter = at<unsigned int>(ws, L.misc + 16);
     b.plan_done = at<unsigned int>(ws, L.misc + 32);
     b.cloud_cand = at<unsigned long long>(ws, L.cloud_cand);
-    b.item_temp = at<void>(ws, L.item_temp);
+    for (int g = 0; g < kBatchGroups; ++g) b.item_temp[g] = at<void>(ws, L.item_temp[g]);
     b.ext_max = at<unsigned int>(ws, L.ext);
     b.cargs = at<void>(ws, L.cargs);
     for (int r = 0; r < 2; ++r)
@@ -419,6 +467,7 @@ extern "C" int fla_batch_create(fla_ctx* ctx, const fla_batch_item* items, int32
     p->bin_start = at<uint32_t>(ws, L.bin_start);
     b.bin_start = p->bin_start;
     p->bins = bin_plan(L.n_total, L.cells_total);
+    p->persistent_ok = persistent_ok;
     *out = p;
     return FLA_OK;
 }
@@ -467,6 +516,32 @@ extern "C" int fla_batch_set_tuning(fla_batch_plan* plan, int32_t advance_thread
         plan->exec = nullptr;
         plan->graph_windows = 0;
     }
+    return FLA_OK;
+}
+
+extern "C" int fla_batch_set_mode(fla_batch_plan* plan, int32_t mode)
+{
+    if (!plan || (mode != FLA_BATCH_AUTO && mode != FLA_BATCH_LAUNCHES && mode != FLA_BATCH_PERSISTENT))
+        return FLA_ERR_ARG;
+    if (mode == FLA_BATCH_PERSISTENT && !plan->persistent_ok) return FLA_ERR_UNSUPPORTED;
+    plan->mode = mode;
+    if (mode != FLA_BATCH_AUTO || plan->tuned) plan->persistent = mode == FLA_BATCH_PERSISTENT;
+    if (plan->exec) {   // the graph holds the other form
+        cudaGraphExecDestroy(plan->exec);
+        plan->exec = nullptr;
+        plan->graph_windows = 0;
+    }
+    return FLA_OK;
+}
+
+extern "C" int fla_batch_mode(const fla_batch_plan* plan, int32_t* mode, float* persistent_ms, float* launches_ms)
+{
+    if (!plan) return FLA_ERR_ARG;
+    if (mode) *mode = plan->tuned || plan->mode != FLA_BATCH_AUTO
+                          ? (plan->persistent ? FLA_BATCH_PERSISTENT : FLA_BATCH_LAUNCHES)
+                          : FLA_BATCH_AUTO;
+    if (persistent_ms) *persistent_ms = plan->timed_ms[0];
+    if (launches_ms) *launches_ms = plan->timed_ms[1];
     return FLA_OK;
 }
 

@@ -63,7 +63,7 @@ struct BatchDev {
     uint32_t* tile_items[kBatchGroups];      // per tile: first work item (n_tiles + 1)
     unsigned long long* cloud_cand;          // per cloud: candidates of its tiles (zero between plans)
     unsigned int* plan_done;                 // per group: plan CTAs finished
-    void* item_temp;                         // partial sums of the work items (shared by the groups)
+    void* item_temp[kBatchGroups];           // partial sums of each group's work items
 };
 
 // index k with pre[k] <= v < pre[k + 1] (pre ascending, n + 1 entries)

@@ -537,10 +537,13 @@ __device__ void scatter_pass(const BinArgs& a, int p, const ScatterSmem& sm, uin
     }
 }
 
+// The phases B, C, D and H over the calling CTA's tiles; gen is the barrier
+// generation (advanced by each barrier).  Returns false when a wait gave up.
+// stall_first: this CTA does not arrive at the first barrier (test hook).
 template <typename KF>
-__global__ void __launch_bounds__(RS_THREADS) k_binning(BinArgs a, KF kf)
+__device__ bool binning_phases(const BinArgs& a, const KF& kf, unsigned char* smem_raw, unsigned int& gen,
+                               bool stall_first)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem sm;
     sm.off = reinterpret_cast<uint32_t*>(smem_raw);
     sm.loc = sm.off + RS_MAX_DIGITS;
@@ -549,15 +552,13 @@ __global__ void __launch_bounds__(RS_THREADS) k_binning(BinArgs a, KF kf)
     sm.cnt = reinterpret_cast<uint16_t (*)[RS_MAX_DIGITS]>(sm.val + RS_MAX_DIGITS);
     __shared__ uint32_t s_warp[RS_WARPS];
     __shared__ uint32_t s_part[RS_WARPS][32];
-    __shared__ int s_last;
-    unsigned int gen = 0;
     bool ok = true;
 
     // B: keys, first-pass tile histograms, cell counts (bin_start starts at
-    // zero: cleared by the memset before the kernel)
+    // zero: cleared before the phase)
     if (blockIdx.x == 0 && (int)threadIdx.x < a.nzero) a.zero[threadIdx.x] = 0u;
     for (int64_t t = blockIdx.x; t < a.tiles; t += gridDim.x) key_tile(a, kf, t, sm.off);
-    ok = grid_barrier(a, ++gen, !(a.stall && blockIdx.x == 0));
+    ok = grid_barrier(a, ++gen, !stall_first);
     for (int p = 0; ok && p < a.passes; ++p) {
         if (p > 0) {
             // H: the pass's tile histograms of the previous pass's output
@@ -585,6 +586,16 @@ __global__ void __launch_bounds__(RS_THREADS) k_binning(BinArgs a, KF kf)
         if (p == 0) chunk_starts(a, s_warp);
         if (p + 1 < a.passes) ok = grid_barrier(a, ++gen);
     }
+    return ok;
+}
+
+template <typename KF>
+__global__ void __launch_bounds__(RS_THREADS) k_binning(BinArgs a, KF kf)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_last;
+    unsigned int gen = 0;
+    binning_phases(a, kf, smem_raw, gen, a.stall && blockIdx.x == 0);
 
     // After a wait gave up, the permutation and the bin starts may disagree:
     // the last CTA to finish then clears bin_start, so that every cell is
@@ -687,3 +698,41 @@ cudaError_t launch_batch_step(const BatchDev& b, int nsteps, cudaStream_t s)
 }
 
 }  // namespace fla
+
+#ifdef FLA_WINDOW_PHASES
+// Phase and barrier of the persistent window kernel (window.cuh).
+#include "window.cuh"
+namespace fla {
+
+static_assert(sizeof(BinArgs) <= sizeof(WindowBlob), "binning arguments fit the window's blob");
+
+__device__ bool window_binning(const WindowBlob& bin, const BatchDev& b, unsigned int& gen, unsigned char* smem)
+{
+    const BinArgs& a = *reinterpret_cast<const BinArgs*>(bin.b);
+    return binning_phases(a, BatchKeys{b}, smem, gen, false);
+}
+
+__device__ bool window_barrier(const WindowBlob& bin, unsigned int gen, bool arrive)
+{
+    return grid_barrier(*reinterpret_cast<const BinArgs*>(bin.b), gen, arrive);
+}
+
+// The binning's arguments for all clouds and the control words (barrier
+// arrivals, abort, done) that must be zero before the window kernel.
+size_t window_bin_blob(WindowBlob* out, const BatchDev& b, const BinWork& w, uint32_t* bin_start, DevStatus* st,
+                       void** clear, size_t* clear_bytes)
+{
+    const BinPlan p = bin_plan(b.n_total > 0 ? b.n_total : 1, b.cells_total);
+    BinArgs a = bin_args(p, w, bin_start, st, 0, nullptr, 0);
+    if (b.n_total == 0) a.n = 0;
+    memset(out, 0, sizeof(*out));
+    memcpy(out->b, &a, sizeof(a));
+    *clear = a.bar;
+    *clear_bytes = p.scratch_bytes - p.off_clear;
+    return sizeof(a);
+}
+
+size_t window_binning_smem() { return RS_SMEM; }
+
+}  // namespace fla
+#endif

@@ -356,29 +356,39 @@ __host__ __device__ inline CarrierArgs carrier_args(const fla_carrier_desc& c, i
 
 // Batched clouds: the carrier arguments of each cloud at the window's start
 // (and its largest support cleared for this window's records) ...
-__global__ void k_batch_carrier_args(BatchDev b, double dt)
+__device__ __forceinline__ void batch_carrier_args_of(const BatchDev& b, double dt, int k)
 {
-    pdl_entry();
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= b.n_clouds) return;
     b.ext_max[k] = 0u;
     const BatchCloud& c = b.clouds[k];
     const double t = __dmul_rn((double)*b.step, dt);
     reinterpret_cast<CarrierArgs*>(b.cargs)[k] = carrier_args(c.car, c.N, t);
 }
 
-// ... and every node of every cloud (single precision).
-__global__ void __launch_bounds__(256) k_batch_carrier_sample(BatchDev b)
+__global__ void k_batch_carrier_args(BatchDev b, double dt)
 {
     pdl_entry();
-    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= b.nodes_total) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= b.n_clouds) return;
+    batch_carrier_args_of(b, dt, k);
+}
+
+// ... and every node of every cloud (single precision).
+__device__ __forceinline__ void batch_carrier_node(const BatchDev& b, int64_t g)
+{
     const int k = batch_find(b.node_pre, b.n_clouds, g);
     const BatchCloud& c = b.clouds[k];
     const CarrierArgs& p = reinterpret_cast<const CarrierArgs*>(b.cargs)[k];
     const int64_t r = g - b.node_pre[k];
     if (c.dim == 2) sample_node<float, 2>(p, c.nodes, r);
     else sample_node<float, 3>(p, c.nodes, r);
+}
+
+__global__ void __launch_bounds__(256) k_batch_carrier_sample(BatchDev b)
+{
+    pdl_entry();
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= b.nodes_total) return;
+    batch_carrier_node(b, g);
 }
 
 }  // namespace
@@ -426,3 +436,24 @@ cudaError_t launch_batch_carrier(const BatchDev& b, double dt, cudaStream_t s)
 }
 
 }  // namespace fla
+
+#ifdef FLA_WINDOW_PHASES
+// Phases of the persistent window kernel (window.cuh).
+#include "window.cuh"
+namespace fla {
+
+__device__ void window_carrier_args(const BatchDev& b, double dt)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < b.n_clouds; k += gridDim.x * blockDim.x)
+        batch_carrier_args_of(b, dt, k);
+}
+
+__device__ void window_carrier_sample(const BatchDev& b)
+{
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < b.nodes_total;
+         g += (int64_t)gridDim.x * blockDim.x)
+        batch_carrier_node(b, g);
+}
+
+}  // namespace fla
+#endif

@@ -325,7 +325,7 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty
         const int last = (first + sq < N ? first + sq : N) - 1;
         s_slab[q][sl][end] = centre(end ? last : first);
     }
-    const float ext2max = __uint_as_float(__ldg(a.ext_max));
+    const float ext2max = __uint_as_float(ldro(a.ext_max));
     const int R = (int)floorf(sqrtf(ext2max) * (float)N + 0.5f) + 1;
 
     T sD = T(0), cD = T(0);
@@ -401,8 +401,8 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty
         if (r < nrows) {
             const int y = ylo + r % ny, z = zlo + r / ny;
             const int64_t rowbase = ((int64_t)z * N + y) * N;
-            beg = __ldg(a.bin_start + rowbase + xlo);
-            len = __ldg(a.bin_start + rowbase + xhi + 1) - beg;
+            beg = ldro(a.bin_start + rowbase + xlo);
+            len = ldro(a.bin_start + rowbase + xhi + 1) - beg;
         }
         uint32_t x = len;
 #pragma unroll
@@ -566,7 +566,7 @@ __device__ __forceinline__ TileRef tile_ref(const NwItems& a, int t)
 {
     TileRef r;
     r.g.rec = a.rec;
-    r.g.rec_base = a.rec_base_at ? (int64_t)__ldg(a.rec_base_at) : 0;
+    r.g.rec_base = a.rec_base_at ? (int64_t)ldro(a.rec_base_at) : 0;
     r.g.status = a.status;
     if (a.clouds) {
         const BatchTile bt = a.tiles[t];
@@ -598,14 +598,6 @@ __device__ __forceinline__ TileRef tile_ref(const NwItems& a, int t)
     return r;
 }
 
-// Candidates per work item: 4,096 in single precision; 64 in double
-// precision, whose candidates cost many times more, so that a small mesh
-// still spreads over many SMs (on a 64^2 Taylor-Green cloud the FP64 gather
-// took 27.3 / 11.5 / 7.5 / 4.8 / 3.6 / 3.5 ms per run at 2,048 / 512 / 256 /
-// 128 / 64 / 32 candidates).
-constexpr uint32_t kItemChunkF32 = 4096, kItemChunkF64 = 64;
-__host__ __device__ inline uint32_t nw_chunk(size_t elem) { return elem == 8 ? kItemChunkF64 : kItemChunkF32; }
-
 // Items beyond one per tile that a cloud may use: ceil(16 n / chunk) + 1, at
 // most 65,536 (the partials of a 3D double-precision item are 10 KB); a cloud
 // whose candidates need more widens its chunk instead.
@@ -615,48 +607,38 @@ __host__ __device__ inline int64_t nw_extra_items(int64_t n, uint32_t chunk)
     return e < 65536 ? e : 65536;
 }
 
-// Candidates of each tile (one warp per tile, lanes over the neighbourhood
-// rows); the last CTA to finish turns them into item counts and offsets.
+// Candidates of tile t (one warp; lanes over the neighbourhood rows).
 template <int D>
-__global__ void __launch_bounds__(256) k_nw_plan(NwItems a)
+__device__ __forceinline__ void nw_tile_cand(const NwItems& a, int t, int lane)
 {
-    pdl_entry();
-    const int lane = threadIdx.x & 31;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *a.counter = 0u;   // the items kernel's counter
-    const int t = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-    if (t < a.n_tiles) {
-        const TileRef tr = tile_ref<D>(a, t);
-        const int N = tr.g.N;
-        const float ext2max = __uint_as_float(__ldg(tr.g.ext_max));
-        const int R = (int)floorf(sqrtf(ext2max) * (float)N + 0.5f) + 1;
-        const int xlo = max(tr.o[0] - R, 0), xhi = min(tr.o[0] + Tile<D>::X - 1 + R, N - 1);
-        const int ylo = max(tr.o[1] - R, 0), yhi = min(tr.o[1] + Tile<D>::Y - 1 + R, N - 1);
-        const int zlo = D == 3 ? max(tr.o[2] - R, 0) : 0;
-        const int zhi = D == 3 ? min(tr.o[2] + Tile<D>::Z - 1 + R, N - 1) : 0;
-        const int ny = yhi - ylo + 1, nrows = ny * (zhi - zlo + 1);
-        uint32_t cand = 0;
-        for (int r = lane; r < nrows; r += 32) {
-            const int64_t rb = ((int64_t)(zlo + r / ny) * N + ylo + r % ny) * N;
-            cand += __ldg(tr.g.bin_start + rb + xhi + 1) - __ldg(tr.g.bin_start + rb + xlo);
-        }
-        cand = __reduce_add_sync(0xffffffffu, cand);
-        if (lane == 0) {
-            a.tile_cand[t] = cand;
-            if (cand) atomicAdd(a.cloud_cand + tr.cloud, (unsigned long long)cand);
-        }
+    const TileRef tr = tile_ref<D>(a, t);
+    const int N = tr.g.N;
+    const float ext2max = __uint_as_float(ldro(tr.g.ext_max));
+    const int R = (int)floorf(sqrtf(ext2max) * (float)N + 0.5f) + 1;
+    const int xlo = max(tr.o[0] - R, 0), xhi = min(tr.o[0] + Tile<D>::X - 1 + R, N - 1);
+    const int ylo = max(tr.o[1] - R, 0), yhi = min(tr.o[1] + Tile<D>::Y - 1 + R, N - 1);
+    const int zlo = D == 3 ? max(tr.o[2] - R, 0) : 0;
+    const int zhi = D == 3 ? min(tr.o[2] + Tile<D>::Z - 1 + R, N - 1) : 0;
+    const int ny = yhi - ylo + 1, nrows = ny * (zhi - zlo + 1);
+    uint32_t cand = 0;
+    for (int r = lane; r < nrows; r += 32) {
+        const int64_t rb = ((int64_t)(zlo + r / ny) * N + ylo + r % ny) * N;
+        cand += ldro(tr.g.bin_start + rb + xhi + 1) - ldro(tr.g.bin_start + rb + xlo);
     }
-    __shared__ bool s_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(a.done, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+    cand = __reduce_add_sync(0xffffffffu, cand);
+    if (lane == 0) {
+        a.tile_cand[t] = cand;
+        if (cand) atomicAdd(a.cloud_cand + tr.cloud, (unsigned long long)cand);
+    }
+}
 
-    // item counts: max(1, ceil(cand / chunk)), chunk = max(a.chunk,
-    // ceil(cloud candidates / extra items)); exclusive scan over the tiles
+// Item counts of every tile, max(1, ceil(cand / chunk)) with chunk =
+// max(a.chunk, ceil(cloud candidates / extra items)), and their exclusive
+// scan over the tiles (one CTA); the clouds' candidate totals are reset.
+__device__ __forceinline__ void nw_item_scan(const NwItems& a)
+{
     __shared__ uint32_t s_warp[32];
-    const int tid = threadIdx.x, w = tid >> 5, nw = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
     uint32_t running = 0;
     for (int base = 0; base < a.n_tiles; base += blockDim.x) {
         const int tt = base + tid;
@@ -700,13 +682,31 @@ __global__ void __launch_bounds__(256) k_nw_plan(NwItems a)
     for (int k = a.cloud_lo + tid; k < a.cloud_hi; k += blockDim.x) a.cloud_cand[k] = 0ull;
 }
 
-// Persistent CTAs: one work item at a time from the counter.
-template <typename T, int D, int KER>
-__global__ void __launch_bounds__(GT, sizeof(T) == 8 ? 1 : (D == 2 ? 3 : 2)) k_nw_items(NwItems a)
+// Candidates of each tile; the last CTA to finish turns them into item counts
+// and offsets.
+template <int D>
+__global__ void __launch_bounds__(256) k_nw_plan(NwItems a)
 {
     pdl_entry();
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.counter = 0u;   // the items kernel's counter
+    const int t = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (t < a.n_tiles) nw_tile_cand<D>(a, t, threadIdx.x & 31);
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(a.done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    nw_item_scan(a);
+}
+
+// Persistent CTAs: one work item at a time from the counter.
+template <typename T, int D, int KER>
+__device__ __forceinline__ void nw_items_loop(const NwItems& a)
+{
     __shared__ uint32_t s_item;
-    const uint32_t total = __ldg(a.tile_items + a.n_tiles);
+    const uint32_t total = __ldcg(a.tile_items + a.n_tiles);
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1u);
@@ -716,28 +716,35 @@ __global__ void __launch_bounds__(GT, sizeof(T) == 8 ? 1 : (D == 2 ? 3 : 2)) k_n
         int lo = 0, hi = a.n_tiles - 1;   // last tile with tile_items <= item
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(a.tile_items + mid) <= item) lo = mid;
+            if (__ldcg(a.tile_items + mid) <= item) lo = mid;
             else hi = mid - 1;
         }
         const int t = lo;
-        const uint32_t i0 = __ldg(a.tile_items + t), ni = __ldg(a.tile_items + t + 1) - i0;
-        const uint32_t cand = __ldg(a.tile_cand + t);
+        const uint32_t i0 = __ldcg(a.tile_items + t), ni = __ldcg(a.tile_items + t + 1) - i0;
+        const uint32_t cand = __ldcg(a.tile_cand + t);
         const uint32_t csize = (cand + ni - 1) / ni;
         const uint32_t c0 = (item - i0) * csize, c1 = min(c0 + csize, cand);
         const TileRef tr = tile_ref<D>(a, t);
         T* part = ni > 1 ? (T*)a.temp + (int64_t)item * (D + 2) * GT : nullptr;
         gather_tile<T, D, KER>(tr.g, tr.o[0], tr.o[1], tr.o[2], c0, c1, part);
     }
+    __syncthreads();   // s_item is read by every thread before the CTA moves on
+}
+
+template <typename T, int D, int KER>
+__global__ void __launch_bounds__(GT, sizeof(T) == 8 ? 1 : (D == 2 ? 3 : 2)) k_nw_items(NwItems a)
+{
+    pdl_entry();
+    nw_items_loop<T, D, KER>(a);
 }
 
 // Tiles of several items: the items' partials of each cell in item order.
 template <typename T, int D>
-__global__ void __launch_bounds__(GT) k_nw_combine(NwItems a)
+__device__ __forceinline__ void nw_combine_loop(const NwItems& a)
 {
-    pdl_entry();
     const int tid = threadIdx.x;
     for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
-        const uint32_t i0 = __ldg(a.tile_items + t), i1 = __ldg(a.tile_items + t + 1);
+        const uint32_t i0 = __ldcg(a.tile_items + t), i1 = __ldcg(a.tile_items + t + 1);
         if (i1 - i0 <= 1) continue;
         const TileRef tr = tile_ref<D>(a, t);
         int w0[3], cc[3];
@@ -750,13 +757,20 @@ __global__ void __launch_bounds__(GT) k_nw_combine(NwItems a)
         for (uint32_t it = i0; it < i1; ++it) {
             const T* p = (const T*)a.temp + (int64_t)it * (D + 2) * GT + tid;
 #pragma unroll
-            for (int q = 0; q < D + 2; ++q) neumaier(s[q], c[q], p[q * GT]);
+            for (int q = 0; q < D + 2; ++q) neumaier(s[q], c[q], __ldcg(p + q * GT));
         }
         T Nq[4];
 #pragma unroll
         for (int q = 0; q <= D; ++q) Nq[q] = s[1 + q] + c[1 + q];
         write_cell<T, D>(tr.g, cc, s[0] + c[0], Nq);
     }
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(GT) k_nw_combine(NwItems a)
+{
+    pdl_entry();
+    nw_combine_loop<T, D>(a);
 }
 
 template <typename T, int D, int KER>
@@ -1124,7 +1138,7 @@ cudaError_t launch_batch_gather_t(const BatchDev& b, int group, int ctas, DevSta
     a.cloud_cand = b.cloud_cand;
     a.done = b.plan_done + group;
     a.counter = b.tile_counter + group;
-    a.temp = b.item_temp;
+    a.temp = b.item_temp[group];
     a.status = st;
     a.chunk = nw_chunk(4);
     return launch_items_t<float, D, KER>(a, ctas, num_sms, s);
@@ -1152,3 +1166,85 @@ cudaError_t launch_batch_gather(const BatchDev& b, int group, int ctas, DevStatu
 }
 
 }  // namespace fla
+
+#ifdef FLA_WINDOW_PHASES
+// Gather phases of the persistent window kernel (window.cuh): the work-item
+// tile gather of one batch group, as launch_batch_gather runs it.
+#include <string.h>
+#include "window.cuh"
+namespace fla {
+
+static_assert(sizeof(NwItems) <= sizeof(WindowBlob), "gather arguments fit the window's blob");
+
+size_t window_gather_blob(WindowBlob* out, const BatchDev& b, int group, DevStatus* st, uint32_t chunk)
+{
+    NwItems a{};
+    a.tiles = b.tiles[group];
+    a.clouds = b.clouds;
+    a.bin_start = b.bin_start;
+    a.ext_max = b.ext_max;
+    a.rec = b.rec[group];
+    a.rec_base_at = b.bin_start + b.group_cells[group];
+    a.n_tiles = b.n_tiles[group];
+    a.cloud_lo = b.group_first[group];
+    a.cloud_hi = b.group_first[group + 1];
+    a.tile_cand = b.tile_cand[group];
+    a.tile_items = b.tile_items[group];
+    a.cloud_cand = b.cloud_cand;
+    a.done = b.plan_done + group;
+    a.counter = b.tile_counter + group;
+    a.temp = b.item_temp[group];
+    a.status = st;
+    a.chunk = chunk;
+    memset(out, 0, sizeof(*out));
+    memcpy(out->b, &a, sizeof(a));
+    return sizeof(a);
+}
+
+size_t window_items_smem()
+{
+    size_t m = items_smem<float, 2, FLA_KERNEL_ISO>();
+    m = items_smem<float, 2, FLA_KERNEL_ANISO>() > m ? items_smem<float, 2, FLA_KERNEL_ANISO>() : m;
+    m = items_smem<float, 3, FLA_KERNEL_ISO>() > m ? items_smem<float, 3, FLA_KERNEL_ISO>() : m;
+    m = items_smem<float, 3, FLA_KERNEL_ANISO>() > m ? items_smem<float, 3, FLA_KERNEL_ANISO>() : m;
+    return m;
+}
+
+__device__ void window_gather_cand(const WindowBlob& nw, int dim)
+{
+    const NwItems& a = *reinterpret_cast<const NwItems*>(nw.b);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.counter = 0u;   // the items phase's counter
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < a.n_tiles; t += warps) {
+        if (dim == 2) nw_tile_cand<2>(a, (int)t, lane);
+        else nw_tile_cand<3>(a, (int)t, lane);
+    }
+}
+
+__device__ void window_gather_plan(const WindowBlob& nw, int)
+{
+    nw_item_scan(*reinterpret_cast<const NwItems*>(nw.b));
+}
+
+__device__ void window_gather_items(const WindowBlob& nw, int dim, int kernel, unsigned char*)
+{
+    const NwItems& a = *reinterpret_cast<const NwItems*>(nw.b);
+    if (dim == 2) {
+        if (kernel == FLA_KERNEL_ISO) nw_items_loop<float, 2, FLA_KERNEL_ISO>(a);
+        else nw_items_loop<float, 2, FLA_KERNEL_ANISO>(a);
+    } else {
+        if (kernel == FLA_KERNEL_ISO) nw_items_loop<float, 3, FLA_KERNEL_ISO>(a);
+        else nw_items_loop<float, 3, FLA_KERNEL_ANISO>(a);
+    }
+}
+
+__device__ void window_gather_combine(const WindowBlob& nw, int dim)
+{
+    const NwItems& a = *reinterpret_cast<const NwItems*>(nw.b);
+    if (dim == 2) nw_combine_loop<float, 2>(a);
+    else nw_combine_loop<float, 3>(a);
+}
+
+}  // namespace fla
+#endif

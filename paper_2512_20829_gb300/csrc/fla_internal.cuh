@@ -69,19 +69,34 @@ template <> struct V4<double> {
     double2 a, b;
 };
 
+// Loads of a kernel's inputs (state, nodes, records, bin starts).  A kernel
+// of one phase reads them through the non-coherent read-only path; the
+// persistent window kernel (window.cuh), where an earlier phase of the same
+// launch wrote them, reads them with plain loads, which a grid barrier's
+// fences make coherent.
+template <typename T>
+__device__ __forceinline__ T ldro(const T* p)
+{
+#ifdef FLA_WINDOW_PHASES
+    return *p;
+#else
+    return __ldg(p);
+#endif
+}
+
 template <typename T>
 __device__ __forceinline__ void load4(const T* base, int64_t idx4, T out[4]);
 template <>
 __device__ __forceinline__ void load4<float>(const float* base, int64_t idx4, float out[4])
 {
-    float4 v = __ldg(reinterpret_cast<const float4*>(base) + idx4);
+    float4 v = ldro(reinterpret_cast<const float4*>(base) + idx4);
     out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
 }
 template <>
 __device__ __forceinline__ void load4<double>(const double* base, int64_t idx4, double out[4])
 {
     const double2* p = reinterpret_cast<const double2*>(base) + 2 * idx4;
-    double2 a = __ldg(p), b = __ldg(p + 1);
+    double2 a = ldro(p), b = ldro(p + 1);
     out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
 }
 template <typename T>
@@ -273,6 +288,14 @@ cudaError_t launch_records(const fla_cloud& cl, const fla_mesh& m, const fla_dep
 cudaError_t launch_learn_backward(const fla_cloud& cl, const fla_mesh& m, const fla_deposit_cfg& cfg,
                                   const uint32_t* perm, const uint32_t* bin_start, int64_t n_cells,
                                   const float* dldc, float* partial, int n_parts, DevStatus* st, cudaStream_t s);
+// Candidates per work item: 4,096 in single precision; 64 in double
+// precision, whose candidates cost many times more, so that a small mesh
+// still spreads over many SMs (on a 64^2 Taylor-Green cloud the FP64 gather
+// took 27.3 / 11.5 / 7.5 / 4.8 / 3.6 / 3.5 ms per run at 2,048 / 512 / 256 /
+// 128 / 64 / 32 candidates).
+constexpr uint32_t kItemChunkF32 = 4096, kItemChunkF64 = 64;
+__host__ __device__ inline uint32_t nw_chunk(size_t elem) { return elem == 8 ? kItemChunkF64 : kItemChunkF32; }
+
 // Work-item buffers of the tile gather (in the caller's workspace).
 struct NwWork {
     uint32_t* tile_cand;               // tiles

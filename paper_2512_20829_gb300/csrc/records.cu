@@ -646,14 +646,15 @@ __global__ void __launch_bounds__(kMlpRows, 1) k_learn_backward(RecArgs a, const
 
 // Batched clouds of one group (single precision): the sorted positions of the
 // group's cells, each record computed as k_records does for its cloud.
+// One block of 256 sorted positions from the group's first, block_base on
+// (every thread of the CTA takes part: it ends with a CTA barrier).
 template <int D, int KER>
-__global__ void __launch_bounds__(256) k_batch_records(BatchDev b, int group, DevStatus* st)
+__device__ __forceinline__ void batch_records_block(const BatchDev& b, int group, DevStatus* st, int64_t block_base)
 {
-    pdl_entry();
     constexpr int NP = state_planes(FLA_CLOUD_FLA, D);
     constexpr int RV = record_values(D, KER);
     const int64_t jb = b.bin_start[b.group_cells[group]], je = b.bin_start[b.group_cells[group + 1]];
-    const int64_t j = jb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t j = jb + block_base + threadIdx.x;
     float ext2 = 0.0f;
     bool bad = false;
     int k = -1;
@@ -709,6 +710,14 @@ __global__ void __launch_bounds__(256) k_batch_records(BatchDev b, int group, De
         if (tc) atomicAdd(&st->deposited, tc);
         if (tb) atomicAdd(&st->nonfinite, tb);
     }
+    __syncthreads();   // the counters are reused by the next block
+}
+
+template <int D, int KER>
+__global__ void __launch_bounds__(256) k_batch_records(BatchDev b, int group, DevStatus* st)
+{
+    pdl_entry();
+    batch_records_block<D, KER>(b, group, st, blockIdx.x * (int64_t)blockDim.x);
 }
 
 template <typename T, int D, int KER>
@@ -817,3 +826,32 @@ cudaError_t launch_batch_records(const BatchDev& b, int group, DevStatus* st, cu
 }
 
 }  // namespace fla
+
+#ifdef FLA_WINDOW_PHASES
+// Phase of the persistent window kernel (window.cuh): the records of one
+// group, blocks of 256 sorted positions in a grid-stride loop.
+#include "window.cuh"
+namespace fla {
+
+namespace {
+template <int D, int KER>
+__device__ void window_records_t(const BatchDev& b, int group, DevStatus* st)
+{
+    const int64_t n = b.group_drops[group];   // upper bound on the group's binned droplets
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x)
+        batch_records_block<D, KER>(b, group, st, base);
+}
+}  // namespace
+
+__device__ void window_records(const BatchDev& b, int group, DevStatus* st)
+{
+    switch (group) {
+    case 0: window_records_t<2, FLA_KERNEL_ISO>(b, group, st); break;
+    case 1: window_records_t<2, FLA_KERNEL_ANISO>(b, group, st); break;
+    case 2: window_records_t<3, FLA_KERNEL_ISO>(b, group, st); break;
+    default: window_records_t<3, FLA_KERNEL_ANISO>(b, group, st); break;
+    }
+}
+
+}  // namespace fla
+#endif

@@ -18,7 +18,7 @@ from . import inputs as I
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfla.so")
 
-ABI_VERSION = 7            # FLA_ABI_VERSION of include/fla.h that these structures mirror
+ABI_VERSION = 8            # FLA_ABI_VERSION of include/fla.h that these structures mirror
 F32, F64, F32X2 = 0, 1, 2  # F32X2: compensated single precision (hi planes, then lo planes)
 CLOUD_FLA, CLOUD_LPT = 0, 1
 KERNEL_ISO, KERNEL_ANISO = 0, 1
@@ -36,8 +36,11 @@ EXPORTED = ["fla_abi_version", "fla_status_string", "fla_create", "fla_destroy",
             "fla_profile_enable", "fla_profile_read", "fla_phase_name", "fla_fold_bytes", "fla_mlp_pack",
             "fla_mlp_forward", "fla_learn_workspace_size", "fla_learn_grad", "fla_adam_step",
             "fla_batch_workspace_size", "fla_batch_create", "fla_batch_run", "fla_batch_set_step",
-            "fla_batch_tuning", "fla_batch_set_tuning", "fla_batch_destroy", "fla_test_stall"]
-STALL_BINNING = 1           # fla_test_stall: one look-back word of the next binning stays unpublished
+            "fla_batch_tuning", "fla_batch_set_tuning", "fla_batch_set_mode", "fla_batch_mode",
+            "fla_batch_destroy", "fla_test_stall"]
+STALL_BINNING = 1           # fla_test_stall: one CTA of the next binning skips its first grid barrier
+STALL_BATCH_WINDOW = 2      # ... of the next persistent batch window
+BATCH_AUTO, BATCH_LAUNCHES, BATCH_PERSISTENT = 0, 1, 2
 STATUS_MLP_TIMEOUT, STATUS_WAIT_TIMEOUT = 1, 2   # fla_device_status.flags
 MLP_FEATURES, MLP_HIDDEN, MLP_PARAMS, MLP_PACKED_BYTES = 6, 64, 8833, 19472
 PREC_MIXED, PREC_PLAIN = 0, 1
@@ -145,6 +148,8 @@ def lib() -> C.CDLL:
         L.fla_batch_set_step.argtypes = [v, i32, v]
         L.fla_batch_tuning.argtypes = [v, P(i32), P(i32), P(i32), P(i32)]
         L.fla_batch_set_tuning.argtypes = [v, i32, i32, i32]
+        L.fla_batch_set_mode.argtypes = [v, i32]
+        L.fla_batch_mode.argtypes = [v, P(i32), P(C.c_float), P(C.c_float)]
         L.fla_batch_destroy.argtypes = [v]
         L.fla_batch_destroy.restype = None
         if L.fla_abi_version() != ABI_VERSION:
@@ -222,7 +227,8 @@ class Context:
         return st
 
     def test_stall(self, what: int) -> None:
-        """Test hook: the next binning leaves one look-back word unpublished."""
+        """Test hook (fla_test_stall): one CTA of the next binning (STALL_BINNING)
+        or persistent batch window (STALL_BATCH_WINDOW) skips its first grid barrier."""
         check(lib().fla_test_stall(self.handle, what), "fla_test_stall")
 
 
@@ -742,6 +748,15 @@ class Batch:
     def set_tuning(self, advance_threads: int, gather_ctas_per_sm: int, tile_order: int):
         check(lib().fla_batch_set_tuning(self.handle, int(advance_threads), int(gather_ctas_per_sm), int(tile_order)),
               "fla_batch_set_tuning")
+
+    def set_mode(self, mode: int):
+        check(lib().fla_batch_set_mode(self.handle, int(mode)), "fla_batch_set_mode")
+
+    def mode(self) -> dict:
+        m, tp, tl = C.c_int32(), C.c_float(), C.c_float()
+        check(lib().fla_batch_mode(self.handle, C.byref(m), C.byref(tp), C.byref(tl)), "fla_batch_mode")
+        return {"mode": ["auto", "launches", "persistent"][m.value], "persistent_ms": tp.value,
+                "launches_ms": tl.value}
 
     def close(self):
         if getattr(self, "handle", None):

@@ -140,3 +140,73 @@ def test_full_batch_of_64_clouds(ctx):
         tol = 0.0 if dim == 3 else 1e-5
         for g, r in zip(_fields(b.outs[k]), _fields(sim.out)):
             assert rel_l2(g, r) <= tol
+
+
+def _run_mode(ctx, wls, mode, windows, graph):
+    b = fla.Batch(ctx, wls)
+    b.set_tuning(128, 2, 1)
+    b.set_mode(mode)
+    if graph:
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            b.run(windows, stream=s)
+    else:
+        b.run(windows)
+    torch.cuda.synchronize()
+    return b
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_persistent_window_equals_launches(ctx, graph):
+    """One cooperative kernel per window runs the same phases as the launches:
+    states, meta words and sources bit for bit, on plain launches and in the
+    plan's graph."""
+    wls = _small_batch(seed=17, n=10)
+    ctx.sync_status(reset=True)
+    a = _run_mode(ctx, wls, fla.BATCH_LAUNCHES, 3, graph)
+    st_a = ctx.sync_status(reset=True)
+    b = _run_mode(ctx, wls, fla.BATCH_PERSISTENT, 3, graph)
+    st_b = ctx.sync_status(reset=True)
+    assert b.mode()["mode"] == "persistent" and b.tuning()["launches_per_window"] == 1
+    assert st_b.flags == 0 and st_b.nonfinite == 0
+    assert st_a.droplet_steps == st_b.droplet_steps and st_a.deposited == st_b.deposited
+    assert st_a.pairs == st_b.pairs
+    for ca, cb in zip(a.clouds, b.clouds):
+        assert torch.equal(ca.state, cb.state)
+        assert torch.equal(ca.meta, cb.meta)
+    for oa, ob in zip(a.outs, b.outs):
+        for x, y in zip(_fields(oa), _fields(ob)):
+            assert np.array_equal(x, y)
+
+
+def test_persistent_window_wait_times_out(ctx):
+    """A CTA held back from the window kernel's first grid barrier (test hook):
+    the others give up after about a second, the status reports the timeout,
+    nothing of the window is applied, and the next window runs correctly."""
+    import time
+    wls = _small_batch(seed=19, n=6)
+    ref = _run_mode(ctx, wls, fla.BATCH_LAUNCHES, 1, False)
+    ctx.sync_status(reset=True)
+    b = fla.Batch(ctx, wls)
+    b.set_tuning(128, 2, 1)
+    b.set_mode(fla.BATCH_PERSISTENT)
+    before = [c.state.clone() for c in b.clouds]
+    ctx.test_stall(fla.STALL_BATCH_WINDOW)
+    t0 = time.time()
+    b.run(1)
+    torch.cuda.synchronize()
+    dt = time.time() - t0
+    assert dt < 20.0
+    st = ctx.sync_status(reset=True, allow_timeout=True)
+    assert st.flags & fla.STATUS_WAIT_TIMEOUT
+    for c, x in zip(b.clouds, before):      # the first barrier precedes the advance
+        assert torch.equal(c.state, x)
+    b.run(1)                                # the step was not advanced: the same window again
+    torch.cuda.synchronize()
+    st = ctx.sync_status(reset=True)
+    assert st.flags == 0
+    for ca, cb in zip(ref.clouds, b.clouds):
+        assert torch.equal(ca.state, cb.state)
+    for oa, ob in zip(ref.outs, b.outs):
+        for x, y in zip(_fields(oa), _fields(ob)):
+            assert np.array_equal(x, y)
