@@ -426,7 +426,7 @@ typedef struct {
     int fp32_decision;   /* 1: the q <= 9 truncation is decided on single-precision operands */
     int plain;           /* with fp32_decision: det J decided in single precision throughout */
     const int* fold;     /* per droplet, or NULL: 1 = J is the fold guard's double-precision copy */
-    const float* mlp;    /* learned bandwidth correction (spherical kernel), or NULL */
+    const float* mlp;    /* learned bandwidth correction, or NULL */
 } ora_dep;
 
 /* learned bandwidth correction, defined at the end of this file */
@@ -446,7 +446,8 @@ typedef struct {
     float r2max_f;
     float Pf[9];
     double c;            /* learned correction g(f) (0 without the network) */
-    int dh_dc;           /* 1 when h moves with c: c inside (-2, 2) and h not clamped */
+    int dh_dc;           /* 1 when the bandwidth moves with c: c inside (-2, 2), away from folds, h not
+                            clamped (spherical) or the trace cap inactive (J-scaled) */
     double f[6];         /* the network's features */
 } ora_rec;
 
@@ -593,16 +594,32 @@ void ora_record(const ora_dep* D, const double* x, const double* J, const double
         if (hd > D->h_max) hd = D->h_max;
         r->r2max_f = (float)(9.0 * (double)(float)hd * (double)(float)hd);
     } else {
+        /* learned correction: the Lagrangian bandwidth h0 of the J-scaled kernel
+         * becomes h0 exp(clip(g(f), -2, 2)), off near folds as above */
+        double h0s = h0;
+        int moves = 0;
+        if (D->mlp) {
+            ora_mlp_features(d, J, n0, h0, 1.0 / D->N, r->f);
+            r->c = ora_mlp_forward(D->mlp, r->f, NULL, NULL, NULL, NULL);
+            double ad_fold = D->fp32_decision ? fabs(det_decision(d, J, D->plain, fold)) : adet;
+            if (ad_fold >= 1e-2) {
+                double ct = r->c < -2.0 ? -2.0 : (r->c > 2.0 ? 2.0 : r->c);
+                h0s = h0 * exp(ct);
+                moves = r->c > -2.0 && r->c < 2.0;
+            }
+        }
         double Sg[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         double tr0 = 0.0;
         for (int i = 0; i < d; ++i)
             for (int k = 0; k < d; ++k) {
                 double s = 0.0;
                 for (int j = 0; j < d; ++j) s += J[i * d + j] * J[k * d + j];
-                Sg[i * d + k] = h0 * h0 * s;
+                Sg[i * d + k] = h0s * h0s * s;
                 if (i == k) tr0 += Sg[i * d + k];
             }
         double room = D->h_max * D->h_max - d * D->h_min * D->h_min;
+        /* Sigma moves with c only while the trace cap is inactive */
+        r->dh_dc = moves && !(tr0 > room);
         if (tr0 > room) {
             double f = room / tr0;
             for (int q = 0; q < d * d; ++q) Sg[q] *= f;
@@ -614,7 +631,7 @@ void ora_record(const ora_dep* D, const double* x, const double* J, const double
         inv_sym(d, Sg, dS, r->P);
         r->pref = 1.0 / sqrt(dS);
         r->h = sqrt(tr);
-        aniso_decision(D, J, h0, r->Pf);
+        aniso_decision(D, J, h0s, r->Pf);
     }
 }
 
@@ -1362,23 +1379,46 @@ void ora_mlp_forward_batch(const float* P, int n, const double* F, const double*
 }
 
 /*
- * Training loss of the learned correction and its gradient (spherical kernel).
+ * Training loss of the learned correction and its gradient.
  * At the listed training cells c and for each source component k (mass, then
  * momentum):
  *   L = 1/(1+d) sum_k sum_c (S_kc - T_kc)^2 / sum_c T_kc^2,
- * S the Nadaraya-Watson sources of the cloud with the corrected h, T the
- * targets (n_train x (1+d)).  With w_ic = exp(-q/2)/h_i, q = r^2/h_i^2:
- *   dS_kc/dw_ic = -(a_ki + S_kc)/D_c,   dw_ic/dc_i = w_ic (q - 1) [dh_i/dc_i = h_i],
- * so dL/dc_i = -sum_c w_ic (q - 1) sum_k g_kc (a_ki + S_kc)/D_c with
+ * S the Nadaraya-Watson sources of the cloud with the corrected bandwidth, T
+ * the targets (n_train x (1+d)).  dS_kc/dw_ic = -(a_ki + S_kc)/D_c, and
+ *  - spherical kernel, w_ic = exp(-q/2)/h_i, q = r^2/h_i^2, dh_i/dc_i = h_i:
+ *      dw_ic/dc_i = w_ic (q - 1);
+ *  - J-scaled kernel, w_ic = det(Sigma_i)^(-1/2) exp(-q/2), q = r' P_i r,
+ *    P_i = Sigma_i^-1, Sigma_i = e^(2c_i) A_i + h_min^2 I (trace cap inactive),
+ *    so dSigma/dc = 2 (Sigma - h_min^2 I):
+ *      dq/dc = -r' P dSigma/dc P r = -2 (q - h_min^2 |P r|^2),
+ *      d log det(Sigma)^(-1/2)/dc = -tr(P (Sigma - h_min^2 I)) = -(d - h_min^2 tr P),
+ *      dw_ic/dc_i = w_ic ((q - h_min^2 |P r|^2) - (d - h_min^2 tr P));
+ * so dL/dc_i = -sum_c (dw_ic/dc_i) sum_k g_kc (a_ki + S_kc)/D_c with
  * g_kc = dL/dS_kc; the truncation edge is held fixed.  The gradient with
  * respect to the parameters follows by ora_mlp_backward.  grad may be NULL.
  */
+static double dw_dc(const ora_dep* D, const ora_rec* r, const double* xc, double q, double w)
+{
+    int d = D->dim;
+    if (D->kernel == 0) return w * (q - 1.0);
+    double rv[3], pr[3], pr2 = 0.0, trP = 0.0;
+    for (int a = 0; a < d; ++a) rv[a] = xc[a] - r->x[a];
+    for (int i = 0; i < d; ++i) {
+        pr[i] = 0.0;
+        for (int k = 0; k < d; ++k) pr[i] += r->P[i * d + k] * rv[k];
+        pr2 += pr[i] * pr[i];
+        trP += r->P[i * d + i];
+    }
+    double h2 = D->h_min * D->h_min;
+    return w * ((q - h2 * pr2) - (d - h2 * trP));
+}
+
 int ora_learn_loss_grad(const ora_dep* D, int n, const double* x, const double* J, const double* acc,
                         const int* status, const int* batch, const double* n0, const double* h0,
                         long n_train, const long* cells, const double* target, double* loss, double* grad)
 {
     int d = D->dim;
-    if (!D->mlp || D->kernel != 0) return -1;
+    if (!D->mlp) return -1;
     ora_rec* rec = (ora_rec*)malloc(sizeof(ora_rec) * (n > 0 ? n : 1));
     int* use = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
     for (int i = 0; i < n; ++i) {
@@ -1434,7 +1474,7 @@ int ora_learn_loss_grad(const ora_dep* D, int n, const double* x, const double* 
                     double g = 2.0 * (S[o * (1 + d) + a] - target[o * (1 + d) + a]) / (norm[a] * (1 + d));
                     acc_k += g * (rec[i].a[a] + S[o * (1 + d) + a]);
                 }
-                dLdc += -w * (q - 1.0) * acc_k / Dc[o];
+                dLdc += -dw_dc(D, &rec[i], xc, q, w) * acc_k / Dc[o];
             }
             if (dLdc != 0.0) ora_mlp_backward(D->mlp, rec[i].f, dLdc, grad);
         }

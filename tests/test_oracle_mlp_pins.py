@@ -127,32 +127,39 @@ def test_parameter_gradient_matches_central_differences():
             assert fd == pytest.approx(g[j], rel=1e-4, abs=1e-7), j
 
 
-def _tiny_cloud(seed, n=48, N=16):
+def _tiny_cloud(seed, n=48, N=16, dim=2, h0_cells=1.5):
     rng = np.random.default_rng(seed)
-    x = rng.uniform(0.15, 0.85, (n, 2))
-    J = np.eye(2)[None] + 0.3 * rng.standard_normal((n, 2, 2))
-    acc = np.empty((n, 3))
+    x = rng.uniform(0.15, 0.85, (n, dim))
+    J = np.eye(dim)[None] + 0.3 * rng.standard_normal((n, dim, dim))
+    acc = np.empty((n, 1 + dim))
     acc[:, 0] = -1e-3 * rng.uniform(0.5, 1.5, n)
-    acc[:, 1:] = 1e-2 * rng.standard_normal((n, 2))
+    acc[:, 1:] = 1e-2 * rng.standard_normal((n, dim))
     status = np.ones(n, np.int32)
     batch = np.zeros(n, np.int32)
-    return x, J, acc, status, batch, np.array([1.0]), np.array([1.5 / N])
+    return x, J, acc, status, batch, np.array([1.0]), np.array([h0_cells / N])
 
 
-def test_training_loss_gradient_matches_central_differences():
+# (dim, kernel, mesh, droplets, h0 and h_max in cells): the J-scaled cases keep
+# most supports below the trace cap, so that Sigma moves with c
+GRAD_CASES = [(2, 0, 16, 48, 1.5, 4.0), (2, 1, 16, 48, 1.5, 4.0), (3, 1, 8, 40, 0.8, 3.0)]
+
+
+@pytest.mark.parametrize("dim,kernel,N,n,h0c,hmaxc", GRAD_CASES)
+def test_training_loss_gradient_matches_central_differences(dim, kernel, N, n, h0c, hmaxc):
     """dL/dtheta through the Nadaraya-Watson ratio (exact network) against
-    central differences of the loss."""
-    N = 16
-    x, J, acc, status, batch, n0, h0 = _tiny_cloud(7, N=N)
+    central differences of the loss, for the spherical kernel (dh/dc = h) and
+    the J-scaled kernel (Sigma = e^2c A + h_min^2 I)."""
+    x, J, acc, status, batch, n0, h0 = _tiny_cloud(7, n=n, N=N, dim=dim, h0_cells=h0c)
     P = _random_params(8, scale=0.5)
     rng = np.random.default_rng(9)
-    cells = np.sort(rng.choice(N * N, 120, replace=False))
-    target = rng.standard_normal((cells.size, 3)) * np.array([0.05, 0.5, 0.5])
+    cells = np.sort(rng.choice(N ** dim, 120, replace=False))
+    target = rng.standard_normal((cells.size, 1 + dim)) * np.array([0.05] + [0.5] * dim)
+    kw = dict(dim=dim, N=N, kernel=kernel, h_min=0.5 / N, h_max=hmaxc / N, p=1.0, window_dt=0.01)
     with O.exact_mlp():
-        D = O.dep_struct(dim=2, N=N, kernel=0, h_min=0.5 / N, h_max=4.0 / N, p=1.0, window_dt=0.01, mlp=P)
+        D = O.dep_struct(**kw, mlp=P)
         L, g = O.learn_loss_grad(D, x, J, acc, status, batch, n0, h0, cells, target)
         _, act, _ = O.learn_records(D, x, J, acc, batch, n0, h0)
-        assert act.sum() > 20          # most droplets move h with c
+        assert act.sum() > 20          # most droplets move their bandwidth with c
         idx = np.concatenate([rng.choice(np.arange(OFF_W1, OFF_B1), 6), rng.choice(np.arange(OFF_W2, OFF_B2), 6),
                               rng.choice(np.arange(OFF_W3, OFF_B3), 6), rng.choice(np.arange(OFF_W4, OFF_B4), 6),
                               [OFF_B4]])
@@ -164,15 +171,40 @@ def test_training_loss_gradient_matches_central_differences():
             Pp, Pm = P.copy(), P.copy()
             Pp[j] = np.float32(P[j] + eps)
             Pm[j] = np.float32(P[j] - eps)
-            Dp = O.dep_struct(dim=2, N=N, kernel=0, h_min=0.5 / N, h_max=4.0 / N, p=1.0, window_dt=0.01, mlp=Pp)
-            Dm = O.dep_struct(dim=2, N=N, kernel=0, h_min=0.5 / N, h_max=4.0 / N, p=1.0, window_dt=0.01, mlp=Pm)
-            Lp, _ = O.learn_loss_grad(Dp, x, J, acc, status, batch, n0, h0, cells, target, with_grad=False)
-            Lm, _ = O.learn_loss_grad(Dm, x, J, acc, status, batch, n0, h0, cells, target, with_grad=False)
+            Lp, _ = O.learn_loss_grad(O.dep_struct(**kw, mlp=Pp), x, J, acc, status, batch, n0, h0, cells, target,
+                                      with_grad=False)
+            Lm, _ = O.learn_loss_grad(O.dep_struct(**kw, mlp=Pm), x, J, acc, status, batch, n0, h0, cells, target,
+                                      with_grad=False)
             fd = (Lp - Lm) / (float(Pp[j]) - float(Pm[j]))
             assert fd == pytest.approx(g[j], rel=1e-4, abs=1e-8 * max(1.0, abs(L))), (j, fd, g[j])
             checked += 1
         assert checked == idx.size
     assert np.abs(g).max() > 0
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_constant_correction_scales_the_lagrangian_bandwidth(dim):
+    """A network whose output is the constant c0 (W4 = 0, b4 = c0) gives the
+    J-scaled sources of the plain method with h0 replaced by h0 e^c0 (no droplet
+    near a fold, no support at the trace cap)."""
+    N = 16 if dim == 2 else 8
+    x, J, acc, status, batch, n0, h0 = _tiny_cloud(21, n=60, N=N, dim=dim, h0_cells=1.0)
+    dets = np.abs(np.linalg.det(J))
+    keep = dets > 0.05
+    x, J, acc, status, batch = x[keep], J[keep], acc[keep], status[keep], batch[keep]
+    c0 = 0.375
+    P = _random_params(22)
+    P[OFF_W4:OFF_B4] = 0.0
+    P[OFF_B4] = c0
+    kw = dict(dim=dim, N=N, kernel=1, h_min=0.5 / N, h_max=6.0 / N, p=1.0, window_dt=0.01)
+    with O.exact_mlp():
+        c, act, _ = O.learn_records(O.dep_struct(**kw, mlp=P), x, J, acc, batch, n0, h0)
+        assert np.all(c == c0) and np.all(act)
+        a = O.nw_deposit_celllist(O.dep_struct(**kw, mlp=P), x, J, acc, status, batch, n0, h0)
+    b = O.nw_deposit_celllist(O.dep_struct(**kw), x, J, acc, status, batch, n0, h0 * np.exp(c0))
+    for u, v in zip(a, b):
+        assert np.allclose(u, v, rtol=1e-12, atol=1e-300)
+    assert np.abs(a[2]).max() > 0
 
 
 def test_zero_network_is_the_plain_method():
