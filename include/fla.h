@@ -348,10 +348,12 @@ int cic_deposit(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, doub
 
 /* ------------------------------------------------------------------------
  * Learned bandwidth correction.  The paper has no counterpart: a small
- * network g corrects each droplet's smoothing length,
- *   h = clamp(h0 |det J|^p * exp(clip(g(f), -2, 2)), h_min, h_max),
- * for the spherical kernel (Eq. 14 with h of Eq. 15), except near fold
- * caustics: for droplets with |det J| < 1e-2 the plain kernel is the fallback
+ * network g corrects each droplet's bandwidth by the factor
+ * s = exp(clip(g(f), -2, 2)): for the spherical kernel (Eq. 14 with h of Eq. 15)
+ *   h = clamp(h0 |det J|^p * s, h_min, h_max),
+ * and for the J-scaled kernel its Lagrangian bandwidth h0 becomes h0 s in
+ *   Sigma = f (h0 s)^2 J J^T + h_min^2 I,  f = min(1, (h_max^2 - dim h_min^2) / tr((h0 s)^2 J J^T)),
+ * except near fold caustics: for droplets with |det J| < 1e-2 the plain kernel is the fallback
  * (g is evaluated but not applied), because n = n0/|det J| is singular there
  * and a bandwidth learned away from the folds does not transfer to them.  g is
  * 6 -> 64 -> 64 -> 64 -> 1 with SiLU after the hidden layers, evaluated on the
@@ -389,7 +391,8 @@ int fla_mlp_forward(fla_ctx* ctx, const void* packed_dev, const float* features_
  * to *loss_dev and dL/dtheta (the gradient with respect to the FP32 master
  * parameters, BF16 roundings treated as the identity, the truncation edge held
  * fixed) to grad_dev[FLA_MLP_PARAMS]; callers zero both to start a batch.
- * Single-precision clouds, FLA_KERNEL_ISO.  workspace: as for
+ * Single-precision clouds, either kernel (for the J-scaled one the bandwidth
+ * moves with g only below the trace cap, f = 1).  workspace: as for
  * fla_deposit_sources; learn_ws: fla_learn_workspace_size bytes, 256-byte
  * aligned.  The sums run in a fixed order: the result is deterministic. */
 int fla_learn_workspace_size(fla_ctx* ctx, const fla_mesh* mesh, int64_t n_droplets, size_t* bytes);

@@ -423,9 +423,9 @@ int deposit_impl(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, con
     if (cfg->kernel == FLA_KERNEL_ANISO && !(cfg->h_max * cfg->h_max > mesh->dim * cfg->h_min * cfg->h_min))
         return FLA_ERR_ARG;
     if (cfg->precision != FLA_PREC_MIXED && cfg->precision != FLA_PREC_PLAIN) return FLA_ERR_ARG;
-    if (cfg->mlp_dev) {   // learned correction: single precision, spherical kernel
+    if (cfg->mlp_dev) {   // learned correction: single precision
         if (!aligned(cfg->mlp_dev, 16) || (cfg->mlp_out_dev && !aligned(cfg->mlp_out_dev, 4))) return FLA_ERR_ARG;
-        if (cloud->dtype != FLA_F32 || cfg->kernel != FLA_KERNEL_ISO) return FLA_ERR_UNSUPPORTED;
+        if (cloud->dtype != FLA_F32) return FLA_ERR_UNSUPPORTED;
     }
     if (cfg->h_max * mesh->n > 64.0) return FLA_ERR_UNSUPPORTED;   // support wider than 192 cells
     if (!out->s_mass_dev || !out->s_mom_dev) return FLA_ERR_ARG;
@@ -525,7 +525,7 @@ int fla_learn_grad(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, c
 {
     if (!ctx || !cfg || !out || !cloud || !mesh) return FLA_ERR_ARG;
     if (!cfg->mlp_dev || !out->dsum_dev || !grad_dev || !loss_dev) return FLA_ERR_ARG;
-    if (cloud->dtype != FLA_F32 || cfg->kernel != FLA_KERNEL_ISO) return FLA_ERR_UNSUPPORTED;
+    if (cloud->dtype != FLA_F32) return FLA_ERR_UNSUPPORTED;
     if (n_train < 1 || n_train > 2147483647LL || !cells_dev || !targets_dev) return FLA_ERR_ARG;
     const LearnLayout LL = learn_layout(*mesh, cloud->n, ctx->num_sms);
     if (!lws || !aligned(lws, 256) || lws_bytes < LL.total) return FLA_ERR_WORKSPACE;
@@ -537,6 +537,8 @@ int fla_learn_grad(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, c
     LearnArgs a{};
     a.dim = mesh->dim;
     a.N = mesh->n;
+    a.kernel = cfg->kernel;
+    a.hmin2 = (float)(cfg->h_min * cfg->h_min);
     a.n_cells = cells_of(*mesh);
     a.s_mass = (const float*)out->s_mass_dev;
     a.s_mom = (const float*)out->s_mom_dev;

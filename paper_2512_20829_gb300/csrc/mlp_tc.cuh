@@ -379,6 +379,8 @@ __device__ __forceinline__ float img_weight(const unsigned char* img, int off, i
 // Arguments of the training kernels (learn.cu).
 struct LearnArgs {
     int dim, N;
+    int kernel;                 // FLA_KERNEL_ISO or FLA_KERNEL_ANISO
+    float hmin2;                // h_min^2 (J-scaled kernel)
     int64_t n_cells;
     const float* s_mass;        // deposit outputs of the learned forward
     const float* s_mom;
@@ -392,7 +394,7 @@ struct LearnArgs {
     float* loss;                // += loss
     const uint32_t* bin_start;  // cell list of the deposit
     const void* rec;            // records in sorted order
-    const float* aux;           // per sorted record: g(f), 1 if h moves with it
+    const float* aux;           // per sorted record: g(f), 1 if the bandwidth moves with it
     float* dldc;                // per sorted record: dL/dc
 };
 

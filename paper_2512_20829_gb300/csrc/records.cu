@@ -117,7 +117,7 @@ __device__ __forceinline__ void det_and_n(const RecArgs& a, const float* J, uint
 // Sigma and its inverse in single precision, in a fixed order (see file header).
 template <int D>
 __device__ __forceinline__ void sigma_inverse_f32(const float* j, float h0f, float room, float hmin2, float* P,
-                                                  float& dS, float& tr)
+                                                  float& dS, float& tr, bool* capped = nullptr)
 {
     float S[D * D];
     const float h02 = h0f * h0f;
@@ -137,6 +137,7 @@ __device__ __forceinline__ void sigma_inverse_f32(const float* j, float h0f, flo
 #pragma unroll
         for (int q = 0; q < D * D; ++q) S[q] = S[q] * f;
     }
+    if (capped) *capped = tr0 > room;
 #pragma unroll
     for (int i = 0; i < D; ++i) S[i * D + i] = S[i * D + i] + hmin2;
     tr = 0.0f;
@@ -193,8 +194,11 @@ __device__ __forceinline__ void record_f32(const RecArgs& a, const float* sv, do
         ext2 = r2max;
         bad = !isfinite(n) || !isfinite(hf);
     } else {
+        // learned correction: the Lagrangian bandwidth h0 scaled (corr = 1 without the network)
         float P[9], dS, tr;
-        sigma_inverse_f32<D>(J, (float)h0, a.room, a.hmin2, P, dS, tr);
+        bool capped = false;
+        sigma_inverse_f32<D>(J, (float)(h0 * corr), a.room, a.hmin2, P, dS, tr, &capped);
+        if (h_free) *h_free = !capped;   // Sigma moves with c only below the trace cap
         const float lpref = -0.5f * log2f(dS);
         const float e2 = 9.0f * tr;
         if (D == 2) {
@@ -395,17 +399,18 @@ __device__ __forceinline__ void mlp_features(const float* J, double adet, float 
     f[5] = fminf(ad, 4.0f) * 0.25f;
 }
 
-// Records with the learned correction (single precision, spherical kernel):
-// persistent CTAs take tiles of 128 sorted positions (the packed weights are
-// copied and the TMEM columns allocated once per CTA), the network on the
-// tensor cores.
-template <int D>
+// Records with the learned correction (single precision; the spherical
+// kernel's h or the J-scaled kernel's Lagrangian bandwidth h0 scaled by
+// exp(clip(g(f), -2, 2))): persistent CTAs take tiles of 128 sorted positions
+// (the packed weights are copied and the TMEM columns allocated once per CTA),
+// the network on the tensor cores.
+template <int D, int KER>
 __global__ void __launch_bounds__(kMlpRows) k_records_mlp(RecArgs a)
 {
     pdl_entry();
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int NP = state_planes(FLA_CLOUD_FLA, D);
-    constexpr int RV = record_values(D, FLA_KERNEL_ISO);
+    constexpr int RV = record_values(D, KER);
     const int64_t nvalid = a.bin_start[a.n_cells];
     const int64_t tiles = (nvalid + kMlpRows - 1) / kMlpRows;
     // the grid is sized for every droplet of the cloud; a CTA without a tile of
@@ -449,7 +454,7 @@ __global__ void __launch_bounds__(kMlpRows) k_records_mlp(RecArgs a)
             for (int q = 0; q < 16; ++q) r[q] = 0.0f;
             bool h_free = false, bad = false;
             float ext2 = 0.0f;
-            record_f32<D, FLA_KERNEL_ISO>(a, sv, adet, n, h0, exp((double)ct), r, ext2, bad, &h_free);
+            record_f32<D, KER>(a, sv, adet, n, h0, exp((double)ct), r, ext2, bad, &h_free);
 #pragma unroll
             for (int v = 0; v < RV / 4; ++v) store4<float>((float*)a.rec, j * (RV / 4) + v, r + 4 * v);
             if (ext2 >= 0.0f && isfinite(ext2)) ext_max = fmaxf(ext_max, ext2);
@@ -769,15 +774,21 @@ cudaError_t launch_records(const fla_cloud& cl, const fla_mesh& m, const fla_dep
     RecArgs a = make_rec_args(cl, m, cfg, perm, bin_start, n_cells, rec, ext_max, st);
     a.aux = aux;
     if (a.n == 0) return cudaSuccess;
-    if (a.mlp) {   // validated by the caller: single precision, spherical kernel
+    if (a.mlp) {   // validated by the caller: single precision
         // persistent: as many CTAs as fit at once (shared memory allows 6 per SM), at most one per tile
         int dev = 0, sms = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int64_t tiles = (a.n + kMlpRows - 1) / kMlpRows;
         const unsigned blocks = (unsigned)(tiles < 6LL * sms ? tiles : 6LL * sms);
-        if (m.dim == 2) launch_pdl(k_records_mlp<2>, dim3(blocks), dim3(kMlpRows), kMlpSmemBytes, s, a);
-        else launch_pdl(k_records_mlp<3>, dim3(blocks), dim3(kMlpRows), kMlpSmemBytes, s, a);
+        const bool iso = cfg.kernel == FLA_KERNEL_ISO;
+        if (m.dim == 2) {
+            if (iso) launch_pdl(k_records_mlp<2, FLA_KERNEL_ISO>, dim3(blocks), dim3(kMlpRows), kMlpSmemBytes, s, a);
+            else launch_pdl(k_records_mlp<2, FLA_KERNEL_ANISO>, dim3(blocks), dim3(kMlpRows), kMlpSmemBytes, s, a);
+        } else {
+            if (iso) launch_pdl(k_records_mlp<3, FLA_KERNEL_ISO>, dim3(blocks), dim3(kMlpRows), kMlpSmemBytes, s, a);
+            else launch_pdl(k_records_mlp<3, FLA_KERNEL_ANISO>, dim3(blocks), dim3(kMlpRows), kMlpSmemBytes, s, a);
+        }
         return cudaGetLastError();
     }
     const bool iso = cfg.kernel == FLA_KERNEL_ISO;

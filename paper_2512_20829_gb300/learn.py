@@ -76,7 +76,8 @@ def flow_pair(flow: str, flow_seed: int, seeding: int = 8, matched_scale: bool =
             times the seeds (2^24), 1,000 steps;
       cone: the 128^3 ABC + round-jet flow of the seed (amplitudes and radius
             drawn within 10 %), a 64^3 seed lattice (2^18) against a 256^3
-            one (2^24), spherical kernel, 500 steps.
+            one (2^24), J-scaled kernel (the correction scales its Lagrangian
+            bandwidth h0), 500 steps.
 
     The dense cloud keeps its own smoothing length (its seed spacing): the
     target resolves what 64 times the seeds resolve, and the correction learns
@@ -90,8 +91,8 @@ def flow_pair(flow: str, flow_seed: int, seeding: int = 8, matched_scale: bool =
         sp = I.jet_vortex_2d(scale=1, lpt_per_batch=0, flow_seed=flow_seed)
         de = I.jet_vortex_2d(scale=1, lpt_per_batch=0, flow_seed=flow_seed, seeding=seeding)
     elif flow == "cone":
-        sp = I.abc_jet_3d(seeds_side=64, flow_seed=flow_seed, kernel=I.KERNEL_ISO)
-        de = I.abc_jet_3d(seeds_side=256, flow_seed=flow_seed, kernel=I.KERNEL_ISO)
+        sp = I.abc_jet_3d(seeds_side=64, flow_seed=flow_seed, kernel=I.KERNEL_ANISO)
+        de = I.abc_jet_3d(seeds_side=256, flow_seed=flow_seed, kernel=I.KERNEL_ANISO)
     else:
         raise ValueError(flow)
     if matched_scale:
@@ -171,7 +172,7 @@ def train(ctx, samples: list[Sample], iters: int = 200, cells_per_sample: int = 
     for s in samples:
         cov = np.nonzero(s.covered)[0]
         cells = np.sort(rng.choice(cov, min(cells_per_sample, cov.size), replace=False))
-        bufs.append(fla.LearnBuffers(ctx, s.cloud, s.m, cells, s.target[cells]))
+        bufs.append(fla.LearnBuffers(ctx, s.cloud, s.m, cells, s.target[cells], kernel=s.wl.kernel))
     grad = torch.zeros(fla.MLP_PARAMS, dtype=torch.float32, device="cuda")
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     mom, var = torch.zeros_like(grad), torch.zeros_like(grad)

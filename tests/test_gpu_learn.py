@@ -21,36 +21,47 @@ def ctx():
     c.close()
 
 
-def _problem(dim, N, n, seed):
-    s = I.synthetic_state(dim, n, N, seed=seed, band=(0.15, 0.85), h0_cells=1.5, jac_spread=0.3)
+def _hmax(kernel, N):
+    return (4.0 if kernel == fla.KERNEL_ISO else 3.0) / N
+
+
+def _problem(dim, N, n, seed, kernel=0, h0_cells=1.5):
+    s = I.synthetic_state(dim, n, N, seed=seed, band=(0.15, 0.85), h0_cells=h0_cells, jac_spread=0.3)
     rng = np.random.default_rng(seed + 1)
     nc = N ** dim
     cells = np.sort(rng.choice(nc, min(nc, 600), replace=False))
     # targets: the plain method's sources at those cells, perturbed
-    D0 = O.dep_struct(dim=dim, N=N, kernel=0, h_min=0.5 / N, h_max=4.0 / N, p=1.0, window_dt=0.01)
+    D0 = O.dep_struct(dim=dim, N=N, kernel=kernel, h_min=0.5 / N, h_max=_hmax(kernel, N), p=1.0, window_dt=0.01)
     sm, sv, _ = O.nw_deposit_celllist(D0, s.x, s.J, s.acc, s.status, s.batch, s.n0, s.h0, cells=cells)
     T = np.concatenate([sm[:, None], sv], axis=1) * (1 + 0.2 * rng.standard_normal((cells.size, 1 + dim)))
     return s, cells, T
 
 
-@pytest.mark.parametrize("dim,N,n,seed", [(2, 32, 700, 3), (3, 12, 900, 4), (2, 48, 3000, 5)])
-def test_learn_grad_matches_oracle(ctx, dim, N, n, seed):
-    s, cells, T = _problem(dim, N, n, seed)
+@pytest.mark.parametrize("dim,N,n,seed,kernel,h0c", [(2, 32, 700, 3, 0, 1.5), (3, 12, 900, 4, 0, 1.5),
+                                                     (2, 48, 3000, 5, 0, 1.5), (2, 32, 900, 6, 1, 1.2),
+                                                     (3, 12, 1200, 7, 1, 0.8)])
+def test_learn_grad_matches_oracle(ctx, dim, N, n, seed, kernel, h0c):
+    """Spherical kernel (h scaled) and J-scaled kernel (its Lagrangian bandwidth
+    h0 scaled; h_max = 3 cells, so that most supports stay below the trace cap)."""
+    s, cells, T = _problem(dim, N, n, seed, kernel, h0c)
     P = fla.init_mlp_params(seed, 0.7)
     P[fla.MLP_PARAMS - 1] = 0.2
     net = fla.LearnedCorrection(ctx, P)
     cl = gpu_cloud_from_state(s, fla.F32)
     m = fla.mesh(dim, N)
-    b = fla.LearnBuffers(ctx, cl, m, cells, T)
-    cfg = fla.deposit_cfg(fla.KERNEL_ISO, 0.5 / N, 4.0 / N, 0.01, mlp=net)
+    b = fla.LearnBuffers(ctx, cl, m, cells, T, kernel=kernel)
+    cfg = fla.deposit_cfg(kernel, 0.5 / N, _hmax(kernel, N), 0.01, mlp=net)
     grad = torch.zeros(fla.MLP_PARAMS, dtype=torch.float32, device="cuda")
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     fla.learn_grad(ctx, b, cfg, grad, loss)
     torch.cuda.synchronize()
     assert ctx.sync_status(reset=True).flags == 0
-    D = O.dep_struct(dim=dim, N=N, kernel=0, h_min=0.5 / N, h_max=4.0 / N, p=1.0, window_dt=0.01,
+    D = O.dep_struct(dim=dim, N=N, kernel=kernel, h_min=0.5 / N, h_max=_hmax(kernel, N), p=1.0, window_dt=0.01,
                      fp32_decision=True, mlp=P)
     L_o, g_o = O.learn_loss_grad(D, s.x, s.J, s.acc, s.status, s.batch, s.n0, s.h0, cells, T)
+    if kernel == fla.KERNEL_ANISO:
+        _, act, _ = O.learn_records(D, s.x, s.J, s.acc, s.batch, s.n0, s.h0)
+        assert act.mean() > 0.3        # Sigma moves with c for a good share of the droplets
     g = grad.double().cpu().numpy()
     L = float(loss.item())
     cos = float(g @ g_o / (np.linalg.norm(g) * np.linalg.norm(g_o)))

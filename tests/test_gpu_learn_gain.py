@@ -12,11 +12,13 @@ printed beside).  The network is trained on the GPU by the library's own
 kernels; the test compares the learned and the plain method's error against
 the dense reference on the held-out flows, per flow family.
 
-Measured (GB300): the plain method's error away from caustics is 0.52 (jet)
-and 0.96 (cone); the learned correction takes the held-out jet to 0.44
-(-15 %) and the cone to 0.94 (-2 %).  Over all covered cells it is worse than
-the plain method (jet 1.2 -> 5.2): droplets just outside the fold band
-(|det J| of 1e-2..1e-1, n tens of times the cloud's) get narrower kernels.
+The cone is deposited with the J-scaled kernel, whose Lagrangian bandwidth h0
+the correction scales.  Measured (GB300): the plain method's error away from
+caustics is 0.52 (jet) and 0.96 (cone); the learned correction takes the
+held-out jet to 0.44 (-16 %) and leaves the cone at 0.96 (+0.2 %).  Over all
+covered cells it is worse than the plain method on the jet (1.2 -> 2.9):
+droplets just outside the fold band (|det J| of 1e-2..1e-1, n tens of times
+the cloud's) get narrower kernels.
 The test asserts what holds: both targets are within the plain method's
 reach, and the held-out jet gains.
 """
