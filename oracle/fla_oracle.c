@@ -233,6 +233,8 @@ typedef struct {
     const int* step_start;
     const int* step_dead;
     const double* St0;
+    const double* given_nodes;   /* non-NULL: these node values ((N+1)^d x (d + d*d)) instead of the
+                                    analytic carrier, e.g. a Navier-Stokes carrier's (two-way coupling) */
 } ora_setup;
 
 /* Steps at which a release stops: first step s >= s0 at which the closed-form
@@ -318,7 +320,9 @@ int ora_advance(const ora_setup* S, int step0, int nsteps, int n, double* y, dou
         /* carrier frozen over each carrier step, sampled at its start (reading: the
          * paper's carrier is a CFD solution updated once per carrier time step) */
         F.tc = (S->carrier_period > 0) ? (double)((s / S->carrier_period) * S->carrier_period) * S->dt : 0.0;
-        if (S->use_mesh) {
+        if (S->given_nodes) {
+            F.nodes = S->given_nodes;
+        } else if (S->use_mesh) {
             if (F.tc != nodes_t) { ora_carrier_nodes(S->car, F.tc, S->N, nodes); nodes_t = F.tc; }
             F.nodes = nodes;
         }

@@ -61,7 +61,7 @@ class _Setup(C.Structure):
                 ("delta", C.c_double), ("car", C.POINTER(_Carrier)), ("use_mesh", C.c_int),
                 ("carrier_period", C.c_int), ("n_batches", C.c_int),
                 ("step_start", C.POINTER(C.c_int)), ("step_dead", C.POINTER(C.c_int)),
-                ("St0", C.POINTER(C.c_double))]
+                ("St0", C.POINTER(C.c_double)), ("given_nodes", C.POINTER(C.c_double))]
 
 
 class _Dep(C.Structure):
@@ -236,10 +236,21 @@ class Advancer:
         S.St0 = self.St0.ctypes.data_as(C.POINTER(C.c_double))
         self.S = S
 
-    def advance(self, st: State, step0: int, nsteps: int, reset_acc: bool = False) -> State:
+    def advance(self, st: State, step0: int, nsteps: int, reset_acc: bool = False, nodes=None) -> State:
+        """nodes: carrier node values ((N+1)^d, d + d*d) to use instead of the
+        analytic carrier, e.g. the two-way carrier's (carrier_ns.carrier_nodes)."""
         assert st.y.flags.c_contiguous and st.acc.flags.c_contiguous
+        keep = None
+        if nodes is not None:
+            d = self.dim
+            keep = np.ascontiguousarray(np.asarray(nodes, np.float64)[:, :d + d * d])
+            self.S.given_nodes = keep.ctypes.data_as(C.POINTER(C.c_double))
+        else:
+            self.S.given_nodes = None
         lib().ora_advance(C.byref(self.S), int(step0), int(nsteps), st.y.shape[0], _p(st.y), _p(st.acc),
                           _p(st.status), _p(st.batch), 1 if reset_acc else 0)
+        self.S.given_nodes = None
+        del keep
         return st
 
 
