@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define FLA_ABI_VERSION 8
+#define FLA_ABI_VERSION 9
 
 /* cudaStream_t without including the CUDA headers. */
 typedef struct CUstream_st* fla_stream_t;
@@ -520,6 +520,53 @@ int fla_cell_bins_noalloc(const fla_cloud* cloud, const fla_mesh* mesh, uint32_t
 int fla_profile_enable(fla_ctx* ctx, int enable, int reset);
 int fla_profile_read(fla_ctx* ctx, int32_t n_phases, double* ms, int64_t* launches, int64_t* calls);
 const char* fla_phase_name(int32_t phase);
+
+/* ------------------------------------------------------------------------
+ * Two-way coupling: the carrier flow the droplets act on (App. B, carrier
+ * level: S_Mom added to Eq. 1, S_Mass to Eq. 2), on a periodic unit square of
+ * n x n cells, double precision.  Eq. 1 in vorticity-streamfunction form:
+ * omega at the mesh nodes (i h, j h), h = 1/n, psi from the 5-point
+ * Laplacian (solved in Fourier space), u = U_x + D_y psi, v = U_y - D_x psi
+ * by central differences, U the mean flow; a step of dt advances omega with
+ * explicit advection and source curl (from the cell-centred S_Mom) and
+ * implicit viscosity nu = 1/Re, and U by dt mean(S_Mom).  Eq. 2 at the cell
+ * centres: first-order upwind fluxes through faces whose velocities come from
+ * psi at their corner nodes (divergence-free cell by cell), explicit
+ * diffusion (read with the physical sign: Eq. 2 prints D grad^2 rho on the
+ * left), the mass source.  Node values for fla_advance: u, v and grad u at
+ * the (n+1)^2 mesh nodes (node n repeats node 0), grad u by central
+ * differences of the nodal velocity.  The state lives in the caller's
+ * workspace (fla_ns_workspace_size bytes, 256-byte aligned); all calls are
+ * asynchronous on stream except fla_ns_fields with mean_u.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t n;       /* cells (and nodes) per axis: a power of two, 8..1024 */
+    double nu;       /* kinematic viscosity 1/Re (Eq. 1), >= 0 */
+    double diff;     /* vapour diffusivity D (Eq. 2), >= 0, with diff dt n^2 <= 1/4 */
+    double dt;       /* carrier step */
+} fla_ns_cfg;
+
+/* Workspace bytes for cfg (0 when cfg is invalid). */
+size_t fla_ns_workspace_size(const fla_ns_cfg* cfg);
+/* Initial state: omega_dev the nodal vorticity (n*n doubles, x fastest; its
+ * mean is dropped), mean_u the mean velocity (host, 2 doubles), rho_dev the
+ * vapour at the cells (n*n doubles) or NULL for zero. */
+int fla_ns_init(fla_ctx* ctx, const fla_ns_cfg* cfg, const double* omega_dev, const double* mean_u,
+                const double* rho_dev, void* workspace_dev, size_t workspace_bytes, fla_stream_t stream);
+/* nsub steps of cfg->dt with the droplets' sources held fixed: s_mass_dev
+ * (n*n) and s_mom_dev (2 x n*n, component-major), per unit volume, as
+ * fla_deposit_sources writes them (src_dtype FLA_F32 or FLA_F64); either may
+ * be NULL (no source).  Stable while dt |u| < h (upwind vapour). */
+int fla_ns_step(fla_ctx* ctx, const fla_ns_cfg* cfg, const void* s_mass_dev, const void* s_mom_dev,
+                int32_t src_dtype, int32_t nsub, void* workspace_dev, size_t workspace_bytes, fla_stream_t stream);
+/* The carrier node array for fla_advance (fla_carrier_nodes_bytes of a 2D
+ * mesh of n cells; dtype FLA_F32 or FLA_F64, the cloud's). */
+int fla_ns_nodes(fla_ctx* ctx, const fla_ns_cfg* cfg, int32_t dtype, void* nodes_dev, void* workspace_dev,
+                 size_t workspace_bytes, fla_stream_t stream);
+/* Read back the nodal vorticity (-Lap_h psi), psi and the vapour (n*n doubles
+ * each, any may be NULL) and the mean velocity (host, synchronises stream). */
+int fla_ns_fields(fla_ctx* ctx, const fla_ns_cfg* cfg, double* omega_dev, double* psi_dev, double* rho_dev,
+                  double* mean_u, void* workspace_dev, size_t workspace_bytes, fla_stream_t stream);
 
 /* Test hook for the bounded device-side waits (no paper passage: the waits
  * are this library's).  what = FLA_STALL_BINNING makes the next binning of this

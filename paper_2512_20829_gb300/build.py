@@ -21,7 +21,7 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libfla.so")
 
 SOURCES = ["api.cu", "carrier.cu", "advance.cu", "binning.cu", "records.cu", "deposit.cu", "gather2d.cu", "noalloc.cu",
-           "mlp.cu", "learn.cu", "batch.cu"]
+           "mlp.cu", "learn.cu", "batch.cu", "ns.cu"]
 NO_FMA = {"records.cu"}
 # The persistent window kernel (window.cu) calls phase functions that these
 # files define under FLA_WINDOW_PHASES: each is compiled a second time into

@@ -18,7 +18,7 @@ from . import inputs as I
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfla.so")
 
-ABI_VERSION = 8            # FLA_ABI_VERSION of include/fla.h that these structures mirror
+ABI_VERSION = 9            # FLA_ABI_VERSION of include/fla.h that these structures mirror
 F32, F64, F32X2 = 0, 1, 2  # F32X2: compensated single precision (hi planes, then lo planes)
 CLOUD_FLA, CLOUD_LPT = 0, 1
 KERNEL_ISO, KERNEL_ANISO = 0, 1
@@ -37,7 +37,8 @@ EXPORTED = ["fla_abi_version", "fla_status_string", "fla_create", "fla_destroy",
             "fla_mlp_forward", "fla_learn_workspace_size", "fla_learn_grad", "fla_adam_step",
             "fla_batch_workspace_size", "fla_batch_create", "fla_batch_run", "fla_batch_set_step",
             "fla_batch_tuning", "fla_batch_set_tuning", "fla_batch_set_mode", "fla_batch_mode",
-            "fla_batch_destroy", "fla_test_stall"]
+            "fla_batch_destroy", "fla_test_stall", "fla_ns_workspace_size", "fla_ns_init", "fla_ns_step",
+            "fla_ns_nodes", "fla_ns_fields"]
 STALL_BINNING = 1           # fla_test_stall: one CTA of the next binning skips its first grid barrier
 STALL_BATCH_WINDOW = 2      # ... of the next persistent batch window
 BATCH_AUTO, BATCH_LAUNCHES, BATCH_PERSISTENT = 0, 1, 2
@@ -98,6 +99,11 @@ BATCH_DTYPE = np.dtype([("St0", "<f8"), ("n0", "<f8"), ("h0", "<f8"), ("step_sta
                         ("step_dead", "<i4")])
 assert BATCH_DTYPE.itemsize == 32
 
+class NSConfig(C.Structure):
+    """fla_ns_cfg: the two-way carrier on a periodic square of n x n cells."""
+    _fields_ = [("n", C.c_int32), ("nu", C.c_double), ("diff", C.c_double), ("dt", C.c_double)]
+
+
 _lib = None
 
 
@@ -152,6 +158,12 @@ def lib() -> C.CDLL:
         L.fla_batch_mode.argtypes = [v, P(i32), P(C.c_float), P(C.c_float)]
         L.fla_batch_destroy.argtypes = [v]
         L.fla_batch_destroy.restype = None
+        L.fla_ns_workspace_size.argtypes = [P(NSConfig)]
+        L.fla_ns_workspace_size.restype = C.c_size_t
+        L.fla_ns_init.argtypes = [v, P(NSConfig), v, P(d), v, v, C.c_size_t, v]
+        L.fla_ns_step.argtypes = [v, P(NSConfig), v, v, i32, i32, v, C.c_size_t, v]
+        L.fla_ns_nodes.argtypes = [v, P(NSConfig), i32, v, v, C.c_size_t, v]
+        L.fla_ns_fields.argtypes = [v, P(NSConfig), v, v, v, P(d), v, C.c_size_t, v]
         if L.fla_abi_version() != ABI_VERSION:
             raise FlaError(f"{LIB_PATH} has ABI version {L.fla_abi_version()}, the binding expects "
                            f"{ABI_VERSION}: rebuild it with __graft_entry__.build()")
@@ -768,3 +780,79 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class NavierStokes:
+    """The two-way carrier (fla_ns_*): its state in a device workspace."""
+
+    def __init__(self, ctx: "Context", n: int, nu: float, diff: float, dt: float, omega, mean_u=(0.0, 0.0),
+                 rho=None, device="cuda", stream=None):
+        torch = _torch()
+        self.ctx = ctx
+        self.cfg = NSConfig(int(n), float(nu), float(diff), float(dt))
+        nb = lib().fla_ns_workspace_size(C.byref(self.cfg))
+        if nb == 0:
+            raise FlaError("invalid two-way carrier configuration")
+        self.ws = aligned_ws(torch.empty(nb + 256, dtype=torch.uint8, device=device))
+        w = torch.as_tensor(np.ascontiguousarray(omega, np.float64).reshape(-1)).to(device)
+        r = None if rho is None else torch.as_tensor(np.ascontiguousarray(rho, np.float64).reshape(-1)).to(device)
+        U = (C.c_double * 2)(*[float(x) for x in mean_u])
+        check(lib().fla_ns_init(ctx.handle, C.byref(self.cfg), _ptr(w), U, _ptr(r) if r is not None else None,
+                                _ptr(self.ws), self.ws.numel(), _stream_ptr(stream)), "fla_ns_init")
+        self._keep = (w, r)
+
+    def step(self, nsub: int, sources: "SourceFields | None" = None, stream=None):
+        sm = sv = None
+        dt = F32
+        if sources is not None:
+            sm, sv = _ptr(sources.s_mass), _ptr(sources.s_mom)
+            dt = F64 if sources.s_mass.dtype == _torch().float64 else F32
+        check(lib().fla_ns_step(self.ctx.handle, C.byref(self.cfg), sm, sv, dt, int(nsub), _ptr(self.ws),
+                                self.ws.numel(), _stream_ptr(stream)), "fla_ns_step")
+
+    def nodes(self, dtype: int, out, stream=None):
+        check(lib().fla_ns_nodes(self.ctx.handle, C.byref(self.cfg), dtype, _ptr(out), _ptr(self.ws),
+                                 self.ws.numel(), _stream_ptr(stream)), "fla_ns_nodes")
+
+    def fields(self, stream=None) -> dict:
+        torch = _torch()
+        n = self.cfg.n
+        dev = self.ws.device
+        w, p, r = (torch.empty(n * n, dtype=torch.float64, device=dev) for _ in range(3))
+        U = (C.c_double * 2)()
+        check(lib().fla_ns_fields(self.ctx.handle, C.byref(self.cfg), _ptr(w), _ptr(p), _ptr(r), U, _ptr(self.ws),
+                                  self.ws.numel(), _stream_ptr(stream)), "fla_ns_fields")
+        return {"omega": w.cpu().numpy().reshape(n, n), "psi": p.cpu().numpy().reshape(n, n),
+                "rho": r.cpu().numpy().reshape(n, n), "U": np.array([U[0], U[1]])}
+
+
+class TwoWay:
+    """Two-way coupled run of a 2D workload on the periodic carrier (App. B):
+    per window the carrier's node values feed the droplet advance (frozen over
+    the window), the kernel-regression deposit gives S_Mass and S_Mom, and the
+    carrier takes the window's steps with those sources."""
+
+    def __init__(self, ctx: "Context", wl: I.Workload, ns: NavierStokes, dtype: int = F32, device="cuda",
+                 coupled: bool = True):
+        assert wl.dim == 2 and wl.n_cells_axis == ns.cfg.n
+        self.ctx, self.wl, self.ns, self.dtype, self.coupled = ctx, wl, ns, dtype, coupled
+        self.m = mesh(2, wl.n_cells_axis)
+        self.nodes = nodes_buffer(self.m, dtype, device)
+        self.fla = DeviceCloud.from_seeds(wl.fla, 2, wl.delta, wl.dt, dtype, device)
+        self.cfg = deposit_cfg(wl.kernel, wl.h_min, wl.h_max, wl.window * wl.dt, wl.p)
+        self.out = SourceFields(self.m, dtype, device)
+        self.ws = aligned_ws(workspace(self.m, dtype, wl.kernel, self.fla.n, device))
+        self.step = 0
+
+    def window(self, stream=None):
+        wl = self.wl
+        k = wl.window
+        self.ns.nodes(self.dtype, self.nodes, stream)
+        advance(self.ctx, self.fla, self.m, self.nodes, self.step, k, wl.dt, reset_acc=True, stream=stream)
+        deposit_sources(self.ctx, self.fla, self.m, self.cfg, self.out, self.ws, stream)
+        self.ns.step(k, self.out if self.coupled else None, stream)
+        self.step += k
+
+    def run(self, n_windows: int, stream=None):
+        for _ in range(n_windows):
+            self.window(stream)

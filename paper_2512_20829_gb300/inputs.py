@@ -143,6 +143,41 @@ def taylor_green_2d(scale: int = 1) -> Workload:
                     kernel=KERNEL_ISO, h_min=0.5 * dx, h_max=4.0 * dx)
 
 
+@dataclass
+class TwoWayCase:
+    """A two-way coupled workload: the droplet workload on a periodic carrier
+    (Eqs. 1-2) with its initial nodal vorticity and mean flow."""
+    wl: Workload
+    nu: float                  # 1/Re
+    diff: float                # vapour diffusivity
+    omega0: np.ndarray         # (N, N) nodal vorticity, x fastest
+    mean_u: tuple
+
+
+def two_way_taylor_green(scale: int = 1, nsteps: int = 200, n0: float = 1.0) -> TwoWayCase:
+    """128^2 periodic cells, Re = 1000, vapour diffusivity 1e-3; the carrier
+    starts as the Taylor-Green vortex of unit speed and period 1, stream
+    function sin(2 pi x) sin(2 pi y)/(2 pi), nodal vorticity
+    4 pi sin(2 pi x) sin(2 pi y).  A strip of FLA seeds (a 128 x 128 lattice in
+    y in [0.45, 0.55]) with St0 = 0.5 and delta = -0.2, number density n0,
+    spherical kernel, deposit every 10 steps; the carrier takes those 10 steps
+    with the window's sources.  ``scale`` divides the mesh and the lattice."""
+    N = 128 // scale
+    n_side = 128 // scale
+    x0 = _lattice_strip(n_side, n_side, 0.45, 0.55)
+    nf = x0.shape[0]
+    fla = Cloud(kind=CLOUD_FLA, x0=x0, batch=np.zeros(nf, np.int32),
+                step_start=np.zeros(1, np.int32), St0=np.array([0.5]),
+                n0=np.array([n0]), h0=np.array([1.0 / n_side]))
+    dx = 1.0 / N
+    wl = Workload(name=f"two_way_taylor_green_{N}x{N}_{nf}fla", dim=2, n_cells_axis=N, dt=1e-3,
+                  nsteps=nsteps, window=10, delta=-0.2, carrier=Carrier(kind=CARRIER_UNIFORM, dim=2),
+                  fla=fla, lpt=None, kernel=KERNEL_ISO, h_min=0.5 * dx, h_max=4.0 * dx)
+    g = np.arange(N) / N
+    omega0 = 4.0 * np.pi * np.sin(2 * np.pi * g)[None, :] * np.sin(2 * np.pi * g)[:, None]
+    return TwoWayCase(wl=wl, nu=1e-3, diff=1e-3, omega0=omega0, mean_u=(0.0, 0.0))
+
+
 def _jet_vortices(rng: np.random.Generator, n_vort: int, width: float) -> np.ndarray:
     x0 = rng.uniform(0.0, 1.0, n_vort)
     yc = rng.uniform(0.3, 0.7, n_vort)
