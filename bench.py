@@ -515,6 +515,51 @@ def batch_leg(ctx, fla, I, flush, steps):
             "tuning": tun, "window_forms": forms}
 
 
+def two_way_leg(ctx, fla, I, flush, steps):
+    """Two-way coupling (App. B) on the periodic Taylor-Green carrier: per
+    window the carrier's node values, the fused 10-step advance, the
+    kernel-regression deposit, and 10 carrier steps with the sources; one
+    graph per run (droplets in the mixed form, the carrier in double)."""
+    import torch
+    case = I.two_way_taylor_green()
+    wl = case.wl
+    n_windows = wl.nsteps // wl.window
+
+    class _Path:
+        def __init__(self, carrier_only=False):
+            self.ctx = ctx
+            self.ns = fla.NavierStokes(ctx, wl.n_cells_axis, case.nu, case.diff, wl.dt, case.omega0,
+                                       mean_u=case.mean_u)
+            self.tw = fla.TwoWay(ctx, wl, self.ns, dtype=fla.F32)
+            self.carrier_only = carrier_only
+
+        def reset(self):
+            self.tw.reset()
+
+        def issue(self):
+            if self.carrier_only:
+                for _ in range(n_windows):
+                    self.ns.nodes(fla.F32, self.tw.nodes)
+                    self.ns.step(wl.window, self.tw.out)
+            else:
+                self.tw.run(n_windows)
+
+    out = {}
+    for name, only in (("coupled", False), ("carrier", True)):
+        path = _Path(only)
+        g, launches = capture(path)
+        t = timed_replays(path, g, steps, flush)
+        out[name] = (float(np.median(t)), launches)
+        del g, path
+        torch.cuda.empty_cache()
+    ms = out["coupled"][0]
+    return {"workload": f"{wl.name}: periodic carrier Re = 1000, vapour D = 1e-3, {wl.nsteps} steps, "
+                        f"{n_windows} deposits, mixed-form droplets, double-precision carrier",
+            "ms_per_run": round(ms, 4), "carrier_ms_per_run": round(out["carrier"][0], 4),
+            "cells_per_s": wl.n_cells * n_windows / (ms * 1e-3),
+            "carrier_steps_per_s": wl.nsteps / (out["carrier"][0] * 1e-3)}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -673,6 +718,9 @@ def run_ours(args):
     batch = None
     if rank == 0 and not args.no_batch:
         batch = batch_leg(ctx, fla, I, flush, 3)
+    two_way = None
+    if rank == 0 and not args.no_secondary:
+        two_way = two_way_leg(ctx, fla, I, flush, 3)
 
     cpu, forms_error = None, None
     if rank == 0 and not args.no_cpu:
@@ -706,6 +754,7 @@ def run_ours(args):
             "forms": {"headline": form, "variants": variants, "rel_l2_all_cells": forms_error},
             "secondary": secondary,
             "batch": batch,
+            "two_way": two_way,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))

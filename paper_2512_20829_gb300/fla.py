@@ -797,9 +797,14 @@ class NavierStokes:
         w = torch.as_tensor(np.ascontiguousarray(omega, np.float64).reshape(-1)).to(device)
         r = None if rho is None else torch.as_tensor(np.ascontiguousarray(rho, np.float64).reshape(-1)).to(device)
         U = (C.c_double * 2)(*[float(x) for x in mean_u])
-        check(lib().fla_ns_init(ctx.handle, C.byref(self.cfg), _ptr(w), U, _ptr(r) if r is not None else None,
+        self._keep = (w, r, U)
+        self.reset(stream)
+
+    def reset(self, stream=None):
+        """Back to the initial state."""
+        w, r, U = self._keep
+        check(lib().fla_ns_init(self.ctx.handle, C.byref(self.cfg), _ptr(w), U, _ptr(r) if r is not None else None,
                                 _ptr(self.ws), self.ws.numel(), _stream_ptr(stream)), "fla_ns_init")
-        self._keep = (w, r)
 
     def step(self, nsub: int, sources: "SourceFields | None" = None, stream=None):
         sm = sv = None
@@ -842,6 +847,14 @@ class TwoWay:
         self.cfg = deposit_cfg(wl.kernel, wl.h_min, wl.h_max, wl.window * wl.dt, wl.p)
         self.out = SourceFields(self.m, dtype, device)
         self.ws = aligned_ws(workspace(self.m, dtype, wl.kernel, self.fla.n, device))
+        self.step = 0
+        self._seeds = (self.fla.state.clone(), self.fla.meta.clone())
+
+    def reset(self, stream=None):
+        """Droplets back to their seeds and the carrier to its initial state."""
+        self.fla.state.copy_(self._seeds[0])
+        self.fla.meta.copy_(self._seeds[1])
+        self.ns.reset(stream)
         self.step = 0
 
     def window(self, stream=None):
