@@ -128,6 +128,8 @@ def parse():
                     help="where the nvidia-smi clock samples of the timed region are written")
     ap.add_argument("--profile-batch", action="store_true",
                     help="one run of the 64-cloud batch with plain launches (no graph), for external profilers")
+    ap.add_argument("--batch-persistent", action="store_true",
+                    help="with --profile-batch: the windows as the persistent kernel")
     ap.add_argument("--profile-only", action="store_true",
                     help="one eager run of the whole path, nothing else (for external profilers)")
     return ap.parse_args()
@@ -584,6 +586,8 @@ def run_ours(args):
     if args.profile_batch:
         b = fla.Batch(ctx, I.batch_clouds())
         b.set_tuning(128, 4, 1)
+        if args.batch_persistent:
+            b.set_mode(fla.BATCH_PERSISTENT)
         b.run(b.workloads[0].nsteps // b.workloads[0].window)   # legacy stream: plain launches
         torch.cuda.synchronize()
         if rank == 0:
