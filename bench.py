@@ -688,7 +688,10 @@ def run_ours(args):
             w2 = make_workload(wname, with_lpt=(wname == "jet_vortex_2d" and not args.no_psicell))
             f2 = WORKLOADS[wname][1]
             leg = {"workload": WORKLOADS[wname][0], "forms": {}}
-            for name in ([f2, "mixed"] if f2 != "fp64" else [f2]):
+            names = [f2, "mixed"] if f2 != "fp64" else [f2]
+            if wname == "jet_vortex_2d":
+                names.append("learned")   # network with a zero last layer: the plain supports, the network's cost
+            for name in names:
                 p, ms, res = time_form(ctx, fla, w2, name, flush)
                 pr, sp = instrumented_run(p)
                 res.update(form=FORM_TEXT[name], cells_per_s=w2.n_cells * (w2.nsteps // w2.window) / (ms * 1e-3),
@@ -697,6 +700,15 @@ def run_ours(args):
                     res["rooflines"] = rooflines(pr, sp, w2, name, peaks, clocks)
                 leg["forms"][name] = res
                 del p
+                torch.cuda.empty_cache()
+            if wname == "jet_vortex_2d":
+                # the plain method at four times the seeds, the seeding whose error the
+                # learned form is compared with (tests/test_gpu_learn_gain.py)
+                w4 = I.jet_vortex_2d(seeding=2, lpt_per_batch=0)
+                p4, ms4, res4 = time_form(ctx, fla, w4, "mixed", flush, reps=2)
+                leg["mixed_4x_seeds"] = {"seeds": w4.fla.n, "ms_per_run": round(ms4, 4),
+                                         "cells_per_s": w4.n_cells * (w4.nsteps // w4.window) / (ms4 * 1e-3)}
+                del p4
                 torch.cuda.empty_cache()
             if w2.lpt is not None:
                 pp, pms, pres = time_form(ctx, fla, w2, "mixed", flush, reps=2, with_lpt=True, with_fla=False)

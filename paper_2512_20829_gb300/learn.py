@@ -67,7 +67,7 @@ def _fields(out: "fla.SourceFields") -> np.ndarray:
     return np.concatenate([out.s_mass.double().cpu().numpy()[:, None], out.s_mom.double().cpu().numpy().T], axis=1)
 
 
-def flow_pair(flow: str, flow_seed: int, seeding: int = 8, matched_scale: bool = False):
+def flow_pair(flow: str, flow_seed: int, seeding: int = 8, matched_scale: bool = False, sparse_seeding: int = 1):
     """The sparse workload of a flow and its dense counterpart (seeding^2 = 64
     times the seeds in 2D, seeding^3 / 8 = 64 times in 3D: 2^24 droplets each).
 
@@ -86,9 +86,11 @@ def flow_pair(flow: str, flow_seed: int, seeding: int = 8, matched_scale: bool =
     method's own estimate without its sampling noise); against that target no
     bandwidth change improves on the plain method (measured: constant factors
     e^c, c in [-0.7, 1.1], and supports up to 3 h_max all leave the error at or
-    above the plain one on the jet), so it is not used for training."""
+    above the plain one on the jet), so it is not used for training.
+    sparse_seeding (jet only) multiplies the sparse cloud's seeds by its square,
+    as ``seeding`` does the dense one's: the plain method at a denser seeding."""
     if flow == "jet":
-        sp = I.jet_vortex_2d(scale=1, lpt_per_batch=0, flow_seed=flow_seed)
+        sp = I.jet_vortex_2d(scale=1, lpt_per_batch=0, flow_seed=flow_seed, seeding=sparse_seeding)
         de = I.jet_vortex_2d(scale=1, lpt_per_batch=0, flow_seed=flow_seed, seeding=seeding)
     elif flow == "cone":
         sp = I.abc_jet_3d(seeds_side=64, flow_seed=flow_seed, kernel=I.KERNEL_ANISO)
@@ -100,13 +102,14 @@ def flow_pair(flow: str, flow_seed: int, seeding: int = 8, matched_scale: bool =
     return sp, de
 
 
-def make_samples(ctx: "fla.Context", flow: str, flow_seeds, windows, matched_scale: bool = False) -> list[Sample]:
+def make_samples(ctx: "fla.Context", flow: str, flow_seeds, windows, matched_scale: bool = False,
+                 sparse_seeding: int = 1) -> list[Sample]:
     """Runs the sparse and the dense cloud of each flow (see flow_pair) and
     keeps a sample at the end of each listed window."""
     import torch
     samples = []
     for fs in flow_seeds:
-        wl_s, wl_d = flow_pair(flow, fs, matched_scale=matched_scale)
+        wl_s, wl_d = flow_pair(flow, fs, matched_scale=matched_scale, sparse_seeding=sparse_seeding)
         sims = fla.Simulation(ctx, wl_s), fla.Simulation(ctx, wl_d)
         keep = set(windows)
         w = 0

@@ -70,3 +70,10 @@ def test_trained_correction_beats_the_plain_method_on_held_out_flows(ctx):
         assert e_plain < 1.0          # the target is one the plain method can approach
         if name == "jet":
             assert e_learn < 0.95 * e_plain
+            # the plain method at four times the seeds (release count and seeds
+            # per release each doubled) against the same dense targets: the error
+            # the learned form reaches with the base seeding costs the plain
+            # method this much more seeding (the bench's jet leg times both runs)
+            denser = LRN.make_samples(ctx, "jet", range(20, 25), JET_WINDOWS, sparse_seeding=2)
+            e_plain4 = LRN.evaluate(ctx, denser)
+            print(f"jet held-out, plain with 4x seeds: {e_plain4:.4f} (plain {e_plain:.4f}, learned {e_learn:.4f})")
