@@ -23,6 +23,12 @@ Discretisation (plain, second order in space, first order in time):
   anti-diffusion): rho <- rho + dt (-div_h F + D Lap_h rho + S_mass), F the
   first-order upwind fluxes with face velocities from psi at the face's two
   corner nodes (exactly divergence-free cell by cell).
+* An immersed cylinder (optional, Body): the momentum equation gains the
+  volume-penalisation force -chi u / eta (its curl in the vorticity equation,
+  by central differences of the nodal products), a fringe strip relaxes the
+  vorticity to zero, and the mean flow is either held (constant inflow) or
+  decelerated by the mean penalisation force.  The force on the body is the
+  sum of chi u / eta h^2 over the nodes.
 * For the droplets: u, v and grad u at the (N+1)^2 mesh nodes (the periodic
   node N repeats node 0), grad u by central differences of the nodal
   velocity (trace-free exactly), in the node layout of the analytic carriers
@@ -36,6 +42,24 @@ import numpy as np
 
 
 @dataclass
+class Body:
+    """An immersed cylinder by volume penalisation (Brinkman): the momentum
+    equation gains -chi u / eta, chi = (1 - tanh((r - R)/h))/2 at the nodes,
+    r the distance to the centre; and a fringe strip x0 <= x <= x1 where the
+    vorticity relaxes to zero at the rate sigma_max sin^2(pi (x - x0)/(x1 - x0)),
+    so the periodic wake does not re-enter.  hold_mean_flow keeps U fixed (a
+    mean pressure gradient balances the mean forcing: a constant inflow)."""
+    xc: float
+    yc: float
+    R: float
+    eta: float
+    x0: float = 0.0
+    x1: float = 0.0
+    sigma_max: float = 0.0
+    hold_mean_flow: bool = True
+
+
+@dataclass
 class NSState:
     N: int
     nu: float             # 1/Re
@@ -44,6 +68,7 @@ class NSState:
     U: np.ndarray          # (2,) mean velocity
     rho: np.ndarray        # (N, N) vapour at the cells
     t: float = 0.0
+    body: Body | None = None
 
 
 def laplacian_eigenvalues(N: int) -> np.ndarray:
@@ -66,12 +91,37 @@ def lap5(f, h):
     return (np.roll(f, 1, 0) + np.roll(f, -1, 0) + np.roll(f, 1, 1) + np.roll(f, -1, 1) - 4.0 * f) / (h * h)
 
 
-def init(N: int, nu: float, D: float, omega: np.ndarray, U=(0.0, 0.0), rho=None) -> NSState:
+def init(N: int, nu: float, D: float, omega: np.ndarray, U=(0.0, 0.0), rho=None, body: Body | None = None) -> NSState:
     """State from a nodal vorticity field (its mean is removed)."""
     oh = np.fft.fft2(np.asarray(omega, np.float64))
     oh[0, 0] = 0.0
     r = np.zeros((N, N)) if rho is None else np.array(rho, np.float64)
-    return NSState(N=N, nu=float(nu), D=float(D), omega_hat=oh, U=np.array(U, np.float64), rho=r)
+    return NSState(N=N, nu=float(nu), D=float(D), omega_hat=oh, U=np.array(U, np.float64), rho=r, body=body)
+
+
+def body_mask(N: int, b: Body) -> np.ndarray:
+    """chi at the nodes (i h, j h), [j, i]."""
+    x = np.arange(N) / N
+    r = np.hypot(x[None, :] - b.xc, x[:, None] - b.yc)
+    return 0.5 * (1.0 - np.tanh((r - b.R) * N))
+
+
+def fringe(N: int, b: Body) -> np.ndarray:
+    """sigma(x) at the nodes, [j, i]."""
+    x = np.arange(N) / N
+    s = np.zeros(N)
+    if b.x1 > b.x0 and b.sigma_max > 0:
+        inside = (x >= b.x0) & (x <= b.x1)
+        s[inside] = b.sigma_max * np.sin(np.pi * (x[inside] - b.x0) / (b.x1 - b.x0)) ** 2
+    return np.broadcast_to(s[None, :], (N, N)).copy()
+
+
+def body_force(st: NSState) -> np.ndarray:
+    """Force of the fluid on the body: sum over the nodes of chi u / eta h^2."""
+    b = st.body
+    u, v = velocity(st)
+    chi = body_mask(st.N, b) / b.eta
+    return np.array([(chi * u).sum(), (chi * v).sum()]) / (st.N * st.N)
 
 
 def streamfunction(st: NSState) -> np.ndarray:
@@ -124,11 +174,19 @@ def step(st: NSState, dt: float, S_mass=None, Sx=None, Sy=None, nsub: int = 1) -
     Sy = z if Sy is None else np.asarray(Sy, np.float64).reshape(N, N)
     curl = curl_cells(Sx, Sy, h)
     mean_S = np.array([Sx.mean(), Sy.mean()])
+    b = st.body
+    if b is not None:
+        chi = body_mask(N, b) / b.eta
+        sig = fringe(N, b)
+        if b.hold_mean_flow:
+            mean_S = np.zeros(2)
     for _ in range(nsub):
         psi = streamfunction(st)
         u, v = velocity(st, psi)
         w = omega(st)
         R = -(u * _dx(w, h) + v * _dy(w, h)) + curl
+        if b is not None:   # curl of -chi u / eta, and the fringe's relaxation
+            R += -(_dx(chi * v, h) - _dy(chi * u, h)) - sig * w
         # vapour: upwind fluxes on the faces, diffusion, source
         ux, vy = face_velocities(st, psi)
         rho = st.rho
@@ -139,7 +197,10 @@ def step(st: NSState, dt: float, S_mass=None, Sx=None, Sy=None, nsub: int = 1) -
         oh = (st.omega_hat + dt * np.fft.fft2(R)) / (1.0 - dt * st.nu * lam)
         oh[0, 0] = 0.0
         st.omega_hat = oh
-        st.U = st.U + dt * mean_S
+        if b is not None and not b.hold_mean_flow:   # the mean of the penalisation force
+            st.U = st.U + dt * (mean_S - np.array([(chi * u).mean(), (chi * v).mean()]))
+        else:
+            st.U = st.U + dt * mean_S
         st.t += dt
     return st
 

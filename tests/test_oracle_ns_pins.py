@@ -192,3 +192,57 @@ def test_advance_with_given_nodes_equals_the_sampled_carrier():
     adv.advance(a, 0, 30, reset_acc=True)
     adv.advance(b, 0, 30, reset_acc=True, nodes=nodes)
     assert np.array_equal(a.y, b.y) and np.array_equal(a.acc, b.acc) and np.array_equal(a.status, b.status)
+
+
+# ----------------------------------------------------------------- immersed cylinder
+
+def test_cylinder_mask_area_converges_at_second_order():
+    b = NS.Body(xc=0.41, yc=0.47, R=0.13, eta=1e-3)
+    errs = [abs(NS.body_mask(N, b).sum() / N ** 2 - np.pi * b.R ** 2) for N in (64, 128, 256)]
+    assert errs[0] / errs[1] == pytest.approx(4.0, rel=0.25)
+    assert errs[1] / errs[2] == pytest.approx(4.0, rel=0.25)
+
+
+def test_uniform_penalisation_damps_each_mode_in_closed_form():
+    """chi = 1 everywhere: a single Fourier mode (no self-advection) is multiplied
+    each step by (1 - dt g / eta)/(1 - dt nu lambda), g = (sin^2 2 pi k_x h +
+    sin^2 2 pi k_y h) / (4 (sin^2 pi k_x h + sin^2 pi k_y h)) -- the wide-stencil
+    curl of the velocity over the compact Laplacian -- and the force on the body
+    is U / eta with the mean flow decelerating at the same rate."""
+    N, kx, ky, nu, dt, eta, n = 32, 2, 3, 1e-3, 1e-3, 5e-3, 10
+    x = np.arange(N) / N
+    w0 = np.cos(2 * np.pi * (kx * x[None, :] + ky * x[:, None]))
+    b = NS.Body(xc=0.5, yc=0.5, R=10.0, eta=eta, hold_mean_flow=False)
+    assert np.all(NS.body_mask(N, b) == 1.0)
+    st = NS.init(N, nu, 0.0, w0, U=(0.3, 0.0), body=b)
+    F0 = NS.body_force(st)
+    assert np.allclose(F0, [0.3 / eta, 0.0], rtol=1e-12, atol=1e-9)
+    NS.step(st, dt, nsub=n)
+    h = 1.0 / N
+    g = (np.sin(2 * np.pi * kx * h) ** 2 + np.sin(2 * np.pi * ky * h) ** 2) / (
+        4 * (np.sin(np.pi * kx * h) ** 2 + np.sin(np.pi * ky * h) ** 2))
+    lam = NS.laplacian_eigenvalues(N)[ky, kx]
+    # the mean-flow advection of a single mode rotates its phase; compare amplitudes
+    amp = np.abs(np.fft.fft2(NS.omega(st))[ky, kx]) / (N * N / 2)
+    assert amp == pytest.approx(((1 - dt * g / eta) / (1 - dt * nu * lam)) ** n, rel=1e-3)
+    assert st.U[0] == pytest.approx(0.3 * (1 - dt / eta) ** n, rel=1e-12)
+
+
+def test_fringe_relaxes_vorticity_in_its_strip_only():
+    """omega = cos(2 pi k x) (velocity along y: no self-advection), nu = 0, U = 0:
+    each step multiplies omega by 1 - dt sigma(x) at each node, then removes the
+    mean; outside the strip only the mean removal acts."""
+    N, k, dt, n = 32, 2, 1e-3, 8
+    x = np.arange(N) / N
+    w = np.cos(2 * np.pi * k * x)[None, :] * np.ones((N, 1))
+    b = NS.Body(xc=-5.0, yc=-5.0, R=0.01, eta=1.0, x0=0.6, x1=0.9, sigma_max=40.0)
+    assert NS.body_mask(N, b).max() < 1e-300
+    sig = NS.fringe(N, b)
+    assert sig[:, x < 0.6].max() == 0.0 and sig[:, x > 0.9].max() == 0.0
+    assert sig.max() == pytest.approx(40.0 * np.sin(np.pi * (np.round(0.75 * N) / N - 0.6) / 0.3) ** 2)
+    st = NS.init(N, 0.0, 0.0, w, body=b)
+    for _ in range(n):
+        w = w * (1 - dt * sig)
+        w = w - w.mean()
+    NS.step(st, dt, nsub=n)
+    assert np.abs(NS.omega(st) - w).max() <= 1e-12
