@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define FLA_ABI_VERSION 9
+#define FLA_ABI_VERSION 10
 
 /* cudaStream_t without including the CUDA headers. */
 typedef struct CUstream_st* fla_stream_t;
@@ -544,6 +544,17 @@ typedef struct {
     double nu;       /* kinematic viscosity 1/Re (Eq. 1), >= 0 */
     double diff;     /* vapour diffusivity D (Eq. 2), >= 0, with diff dt n^2 <= 1/4 */
     double dt;       /* carrier step */
+    /* Optional immersed cylinder (the paper's test case, Sec. 5) by volume
+     * penalisation: the momentum equation gains -chi u / eta with
+     * chi = (1 - tanh((r - R) n))/2 at the nodes, r the distance to (xc, yc);
+     * a fringe strip fringe_x0 <= x <= fringe_x1 relaxes the vorticity at the
+     * rate fringe_sigma sin^2(pi (x - x0)/(x1 - x0)), so the periodic wake does
+     * not re-enter; hold_mean_flow != 0 keeps the mean flow fixed (a constant
+     * inflow), else the mean penalisation force decelerates it.  body = 0: none. */
+    int32_t body;
+    int32_t hold_mean_flow;
+    double body_xc, body_yc, body_r, body_eta;   /* eta > 0, dt / eta <= 1 */
+    double fringe_x0, fringe_x1, fringe_sigma;   /* sigma dt <= 1 */
 } fla_ns_cfg;
 
 /* Workspace bytes for cfg (0 when cfg is invalid). */
@@ -563,6 +574,10 @@ int fla_ns_step(fla_ctx* ctx, const fla_ns_cfg* cfg, const void* s_mass_dev, con
  * mesh of n cells; dtype FLA_F32 or FLA_F64, the cloud's). */
 int fla_ns_nodes(fla_ctx* ctx, const fla_ns_cfg* cfg, int32_t dtype, void* nodes_dev, void* workspace_dev,
                  size_t workspace_bytes, fla_stream_t stream);
+/* The force of the fluid on the cylinder, sum over the nodes of chi u / eta h^2
+ * (host, 2 doubles; synchronises stream).  FLA_ERR_ARG without a body. */
+int fla_ns_body_force(fla_ctx* ctx, const fla_ns_cfg* cfg, double* force, void* workspace_dev,
+                      size_t workspace_bytes, fla_stream_t stream);
 /* Read back the nodal vorticity (-Lap_h psi), psi and the vapour (n*n doubles
  * each, any may be NULL) and the mean velocity (host, synchronises stream). */
 int fla_ns_fields(fla_ctx* ctx, const fla_ns_cfg* cfg, double* omega_dev, double* psi_dev, double* rho_dev,

@@ -30,7 +30,7 @@ constexpr int kNsThreads = 256;
 
 // Workspace layout (bytes), each array on a 256-byte boundary.
 struct NsLayout {
-    size_t omega_hat, a, b, c, psi, omega, rho, rho2, twiddle, scal, partial, total;
+    size_t omega_hat, a, b, c, psi, omega, u, v, chi, rho, rho2, twiddle, scal, partial, total;
 };
 
 inline size_t ns_up(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -46,10 +46,13 @@ inline NsLayout ns_layout(int n)
     L.c = o; o += ns_up(c);
     L.psi = o; o += ns_up(r);
     L.omega = o; o += ns_up(r);
+    L.u = o; o += ns_up(r);
+    L.v = o; o += ns_up(r);
+    L.chi = o; o += ns_up(r);
     L.rho = o; o += ns_up(r);
     L.rho2 = o; o += ns_up(r);
     L.twiddle = o; o += ns_up((size_t)(n / 2) * sizeof(double2));
-    L.scal = o; o += 256;                                  // U[2], mean S[2]
+    L.scal = o; o += 256;                                  // U[2], mean S[2], mean chi u[2]
     L.partial = o; o += ns_up((size_t)2 * kNsThreads * sizeof(double));
     L.total = o;
     return L;
@@ -64,10 +67,15 @@ struct NsArgs {
     double2* c;
     double* psi;          // nodes [j][i]
     double* omega;
+    double* u;            // nodal velocity
+    double* v;
+    double* chi;          // penalisation mask over eta (body)
+    int body, hold;
+    double fx0, fx1, fsig; // fringe
     double* rho;          // cells [j][i]
     double* rho2;
     const double2* twiddle;   // exp(-2 pi i t / n), t < n/2
-    double* scal;         // U[2], mean S[2]
+    double* scal;         // U[2], mean S[2], mean chi u[2]
     double* partial;
 };
 
@@ -91,6 +99,14 @@ NsArgs ns_args(const fla_ns_cfg& cfg, void* ws)
     a.c = reinterpret_cast<double2*>(w + L.c);
     a.psi = reinterpret_cast<double*>(w + L.psi);
     a.omega = reinterpret_cast<double*>(w + L.omega);
+    a.u = reinterpret_cast<double*>(w + L.u);
+    a.v = reinterpret_cast<double*>(w + L.v);
+    a.chi = reinterpret_cast<double*>(w + L.chi);
+    a.body = cfg.body != 0;
+    a.hold = cfg.hold_mean_flow != 0;
+    a.fx0 = cfg.fringe_x0;
+    a.fx1 = cfg.fringe_x1;
+    a.fsig = cfg.fringe_sigma;
     a.rho = reinterpret_cast<double*>(w + L.rho);
     a.rho2 = reinterpret_cast<double*>(w + L.rho2);
     a.twiddle = reinterpret_cast<const double2*>(w + L.twiddle);
@@ -176,6 +192,9 @@ __global__ void __launch_bounds__(kNsThreads) k_ns_vort(NsArgs a, const double2*
                      phys[(int64_t)wrap(j + 1, n) * n + i].x + phys[(int64_t)wrap(j - 1, n) * n + i].x;
     a.psi[k] = c;
     a.omega[k] = -(s - 4.0 * c) * (a.inv_h * a.inv_h);
+    const double h2 = 0.5 * a.inv_h;
+    a.u[k] = a.scal[0] + (phys[(int64_t)wrap(j + 1, n) * n + i].x - phys[(int64_t)wrap(j - 1, n) * n + i].x) * h2;
+    a.v[k] = a.scal[1] - (phys[(int64_t)j * n + wrap(i + 1, n)].x - phys[(int64_t)j * n + wrap(i - 1, n)].x) * h2;
 }
 
 template <typename S>
@@ -193,10 +212,8 @@ __global__ void __launch_bounds__(kNsThreads) k_ns_rhs(NsArgs a, const S* __rest
     const int i = (int)(k & (n - 1)), j = (int)(k >> a.logn);
     const int ip = wrap(i + 1, n), im = wrap(i - 1, n), jp = wrap(j + 1, n), jm = wrap(j - 1, n);
     const double h2 = 0.5 * a.inv_h;
-    const double* P = a.psi;
     const double* W = a.omega;
-    const double u = a.scal[0] + (P[(int64_t)jp * n + i] - P[(int64_t)jm * n + i]) * h2;
-    const double v = a.scal[1] - (P[(int64_t)j * n + ip] - P[(int64_t)j * n + im]) * h2;
+    const double u = a.u[k], v = a.v[k];
     const double wx = (W[(int64_t)j * n + ip] - W[(int64_t)j * n + im]) * h2;
     const double wy = (W[(int64_t)jp * n + i] - W[(int64_t)jm * n + i]) * h2;
     double curl = 0.0;
@@ -207,7 +224,21 @@ __global__ void __launch_bounds__(kNsThreads) k_ns_rhs(NsArgs a, const S* __rest
         const double sxb = src_at(sx, (int64_t)jm * n + i) + src_at(sx, (int64_t)jm * n + im);
         curl = (syr - syl) * h2 - (sxt - sxb) * h2;
     }
-    out[k] = make_double2(-(u * wx + v * wy) + curl, 0.0);
+    double r = -(u * wx + v * wy) + curl;
+    if (a.body) {
+        // curl of -chi u / eta (central differences of the nodal products), the fringe
+        const int64_t kp = (int64_t)j * n + ip, km = (int64_t)j * n + im;
+        const int64_t kt = (int64_t)jp * n + i, kb = (int64_t)jm * n + i;
+        const double dcv = (a.chi[kp] * a.v[kp] - a.chi[km] * a.v[km]) * h2;
+        const double dcu = (a.chi[kt] * a.u[kt] - a.chi[kb] * a.u[kb]) * h2;
+        r += -(dcv - dcu);
+        const double x = (double)i * a.h;
+        if (a.fsig > 0.0 && a.fx1 > a.fx0 && x >= a.fx0 && x <= a.fx1) {
+            const double sn = sin(M_PI * (x - a.fx0) / (a.fx1 - a.fx0));
+            r -= a.fsig * sn * sn * W[k];
+        }
+    }
+    out[k] = make_double2(r, 0.0);
 }
 
 // Per cell: the vapour step (upwind fluxes through divergence-free faces,
@@ -247,8 +278,13 @@ __global__ void __launch_bounds__(kNsThreads) k_ns_spectral(NsArgs a, double2* _
     const int n = a.n;
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k == 0 && update) {
-        a.scal[0] += a.dt * a.scal[2];
-        a.scal[1] += a.dt * a.scal[3];
+        if (!a.body) {
+            a.scal[0] += a.dt * a.scal[2];
+            a.scal[1] += a.dt * a.scal[3];
+        } else if (!a.hold) {   // the mean of the penalisation force decelerates the flow
+            a.scal[0] += a.dt * (a.scal[2] - a.scal[4]);
+            a.scal[1] += a.dt * (a.scal[3] - a.scal[5]);
+        }
     }
     if (k >= (int64_t)n * n) return;
     const int kx = (int)(k >> a.logn), ky = (int)(k & (n - 1));
@@ -352,6 +388,44 @@ cudaError_t fft2(const NsArgs& a, const double2* in, double2* tmp, double2* out,
     return cudaGetLastError();
 }
 
+// The penalisation mask over eta at the nodes: (1 - tanh((r - R) n))/2 / eta.
+__global__ void __launch_bounds__(kNsThreads) k_ns_mask(NsArgs a, double xc, double yc, double R, double eta)
+{
+    const int n = a.n;
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= (int64_t)n * n) return;
+    const int i = (int)(k & (n - 1)), j = (int)(k >> a.logn);
+    const double r = hypot((double)i * a.h - xc, (double)j * a.h - yc);
+    a.chi[k] = 0.5 * (1.0 - tanh((r - R) * (double)n)) / eta;
+}
+
+// mean(chi u), mean(chi v) over the nodes into scal[4], scal[5]: one CTA, a
+// fixed order (deterministic).
+__global__ void __launch_bounds__(kNsThreads) k_ns_body_mean(NsArgs a)
+{
+    __shared__ double s_x[kNsThreads], s_y[kNsThreads];
+    const int64_t nc = (int64_t)a.n * a.n;
+    double px = 0.0, py = 0.0;
+    for (int64_t c = threadIdx.x; c < nc; c += kNsThreads) {
+        px += a.chi[c] * a.u[c];
+        py += a.chi[c] * a.v[c];
+    }
+    s_x[threadIdx.x] = px;
+    s_y[threadIdx.x] = py;
+    __syncthreads();
+    for (int w = kNsThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            s_x[threadIdx.x] += s_x[threadIdx.x + w];
+            s_y[threadIdx.x] += s_y[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        a.scal[4] = s_x[0] / (double)nc;
+        a.scal[5] = s_y[0] / (double)nc;
+    }
+}
+
 }  // namespace
 }  // namespace fla
 
@@ -365,7 +439,17 @@ bool ns_cfg_ok(const fla_ns_cfg* c)
     if (!c || c->n < 8 || c->n > 1024 || (c->n & (c->n - 1)) != 0) return false;
     if (!(c->nu >= 0.0) || !isfinite(c->nu) || !(c->diff >= 0.0) || !isfinite(c->diff)) return false;
     if (!(c->dt > 0.0) || !isfinite(c->dt)) return false;
-    return c->diff * c->dt * (double)c->n * (double)c->n <= 0.25;   // explicit diffusion stays stable
+    if (!(c->diff * c->dt * (double)c->n * (double)c->n <= 0.25)) return false;   // explicit diffusion stays stable
+    if (c->body) {
+        const double vals[7] = {c->body_xc, c->body_yc, c->body_r, c->body_eta, c->fringe_x0, c->fringe_x1,
+                                c->fringe_sigma};
+        for (double x : vals)
+            if (!isfinite(x)) return false;
+        if (!(c->body_r > 0.0) || !(c->body_eta > 0.0) || c->dt > c->body_eta) return false;   // explicit penalisation
+        if (c->fringe_sigma < 0.0 || c->fringe_sigma * c->dt > 1.0) return false;
+        if (c->fringe_sigma > 0.0 && !(c->fringe_x1 > c->fringe_x0)) return false;
+    }
+    return true;
 }
 
 bool ws_ok(const fla_ns_cfg* c, const void* ws, size_t bytes)
@@ -392,6 +476,7 @@ cudaError_t ns_steps(const NsArgs& a, const S* sm, const S* sx, const S* sy, int
     for (int q = 0; q < nsub; ++q) {
         cudaError_t e = ns_physical(a, s);
         if (e != cudaSuccess) return e;
+        if (a.body && !a.hold) k_ns_body_mean<<<1, kNsThreads, 0, s>>>(a);
         k_ns_rhs<S><<<ns_blocks(nc), kNsThreads, 0, s>>>(a, sx, sy, a.c);
         k_ns_vapour<S><<<ns_blocks(nc), kNsThreads, 0, s>>>(a, sm);
         e = fft2(a, a.c, a.b, a.a, false, s);
@@ -419,6 +504,7 @@ extern "C" int fla_ns_init(fla_ctx* ctx, const fla_ns_cfg* cfg, const double* om
     const int64_t nc = (int64_t)a.n * a.n;
     k_ns_twiddle<<<(unsigned)((a.n / 2 + 255) / 256), 256, 0, s>>>(const_cast<double2*>(a.twiddle), a.n);
     k_ns_load<<<ns_blocks(nc), kNsThreads, 0, s>>>(a, omega_dev, rho_dev, mean_u[0], mean_u[1]);
+    if (a.body) k_ns_mask<<<ns_blocks(nc), kNsThreads, 0, s>>>(a, cfg->body_xc, cfg->body_yc, cfg->body_r, cfg->body_eta);
     cudaError_t e = fft2(a, a.b, a.c, a.omega_hat, false, s);
     if (e != cudaSuccess) return FLA_ERR_CUDA;
     k_ns_spectral<<<ns_blocks(nc), kNsThreads, 0, s>>>(a, a.a, 0);
@@ -475,5 +561,19 @@ extern "C" int fla_ns_fields(fla_ctx* ctx, const fla_ns_cfg* cfg, double* omega_
         e = cudaMemcpyAsync(mean_u, a.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }
+    return ns_status(e);
+}
+
+extern "C" int fla_ns_body_force(fla_ctx* ctx, const fla_ns_cfg* cfg, double* force, void* ws, size_t ws_bytes,
+                                 fla_stream_t stream)
+{
+    if (!ctx || !ns_cfg_ok(cfg) || !cfg->body || !force) return FLA_ERR_ARG;
+    if (!ws_ok(cfg, ws, ws_bytes)) return FLA_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const NsArgs a = ns_args(*cfg, ws);
+    if (ns_physical(a, s) != cudaSuccess) return FLA_ERR_CUDA;
+    k_ns_body_mean<<<1, kNsThreads, 0, s>>>(a);
+    cudaError_t e = cudaMemcpyAsync(force, a.scal + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return ns_status(e);
 }

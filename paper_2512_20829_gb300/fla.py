@@ -18,7 +18,7 @@ from . import inputs as I
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfla.so")
 
-ABI_VERSION = 9            # FLA_ABI_VERSION of include/fla.h that these structures mirror
+ABI_VERSION = 10            # FLA_ABI_VERSION of include/fla.h that these structures mirror
 F32, F64, F32X2 = 0, 1, 2  # F32X2: compensated single precision (hi planes, then lo planes)
 CLOUD_FLA, CLOUD_LPT = 0, 1
 KERNEL_ISO, KERNEL_ANISO = 0, 1
@@ -38,7 +38,7 @@ EXPORTED = ["fla_abi_version", "fla_status_string", "fla_create", "fla_destroy",
             "fla_batch_workspace_size", "fla_batch_create", "fla_batch_run", "fla_batch_set_step",
             "fla_batch_tuning", "fla_batch_set_tuning", "fla_batch_set_mode", "fla_batch_mode",
             "fla_batch_destroy", "fla_test_stall", "fla_ns_workspace_size", "fla_ns_init", "fla_ns_step",
-            "fla_ns_nodes", "fla_ns_fields"]
+            "fla_ns_nodes", "fla_ns_fields", "fla_ns_body_force"]
 STALL_BINNING = 1           # fla_test_stall: one CTA of the next binning skips its first grid barrier
 STALL_BATCH_WINDOW = 2      # ... of the next persistent batch window
 BATCH_AUTO, BATCH_LAUNCHES, BATCH_PERSISTENT = 0, 1, 2
@@ -101,7 +101,10 @@ assert BATCH_DTYPE.itemsize == 32
 
 class NSConfig(C.Structure):
     """fla_ns_cfg: the two-way carrier on a periodic square of n x n cells."""
-    _fields_ = [("n", C.c_int32), ("nu", C.c_double), ("diff", C.c_double), ("dt", C.c_double)]
+    _fields_ = [("n", C.c_int32), ("nu", C.c_double), ("diff", C.c_double), ("dt", C.c_double),
+                ("body", C.c_int32), ("hold_mean_flow", C.c_int32), ("body_xc", C.c_double),
+                ("body_yc", C.c_double), ("body_r", C.c_double), ("body_eta", C.c_double),
+                ("fringe_x0", C.c_double), ("fringe_x1", C.c_double), ("fringe_sigma", C.c_double)]
 
 
 _lib = None
@@ -164,6 +167,7 @@ def lib() -> C.CDLL:
         L.fla_ns_step.argtypes = [v, P(NSConfig), v, v, i32, i32, v, C.c_size_t, v]
         L.fla_ns_nodes.argtypes = [v, P(NSConfig), i32, v, v, C.c_size_t, v]
         L.fla_ns_fields.argtypes = [v, P(NSConfig), v, v, v, P(d), v, C.c_size_t, v]
+        L.fla_ns_body_force.argtypes = [v, P(NSConfig), P(d), v, C.c_size_t, v]
         if L.fla_abi_version() != ABI_VERSION:
             raise FlaError(f"{LIB_PATH} has ABI version {L.fla_abi_version()}, the binding expects "
                            f"{ABI_VERSION}: rebuild it with __graft_entry__.build()")
@@ -786,10 +790,21 @@ class NavierStokes:
     """The two-way carrier (fla_ns_*): its state in a device workspace."""
 
     def __init__(self, ctx: "Context", n: int, nu: float, diff: float, dt: float, omega, mean_u=(0.0, 0.0),
-                 rho=None, device="cuda", stream=None):
+                 rho=None, device="cuda", stream=None, body=None):
+        """body: None, or a mapping with xc, yc, r, eta and optionally fringe_x0,
+        fringe_x1, fringe_sigma, hold_mean_flow (default True): an immersed
+        cylinder by volume penalisation (fla_ns_cfg)."""
         torch = _torch()
         self.ctx = ctx
         self.cfg = NSConfig(int(n), float(nu), float(diff), float(dt))
+        if body is not None:
+            self.cfg.body = 1
+            self.cfg.hold_mean_flow = 1 if body.get("hold_mean_flow", True) else 0
+            self.cfg.body_xc, self.cfg.body_yc = float(body["xc"]), float(body["yc"])
+            self.cfg.body_r, self.cfg.body_eta = float(body["r"]), float(body["eta"])
+            self.cfg.fringe_x0 = float(body.get("fringe_x0", 0.0))
+            self.cfg.fringe_x1 = float(body.get("fringe_x1", 0.0))
+            self.cfg.fringe_sigma = float(body.get("fringe_sigma", 0.0))
         nb = lib().fla_ns_workspace_size(C.byref(self.cfg))
         if nb == 0:
             raise FlaError("invalid two-way carrier configuration")
@@ -818,6 +833,13 @@ class NavierStokes:
     def nodes(self, dtype: int, out, stream=None):
         check(lib().fla_ns_nodes(self.ctx.handle, C.byref(self.cfg), dtype, _ptr(out), _ptr(self.ws),
                                  self.ws.numel(), _stream_ptr(stream)), "fla_ns_nodes")
+
+    def body_force(self, stream=None) -> np.ndarray:
+        """Force of the fluid on the cylinder (2 values)."""
+        F = (C.c_double * 2)()
+        check(lib().fla_ns_body_force(self.ctx.handle, C.byref(self.cfg), F, _ptr(self.ws), self.ws.numel(),
+                                      _stream_ptr(stream)), "fla_ns_body_force")
+        return np.array([F[0], F[1]])
 
     def fields(self, stream=None) -> dict:
         torch = _torch()

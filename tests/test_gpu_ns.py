@@ -147,3 +147,29 @@ def test_two_way_single_precision_droplets_follow_double(ctx):
     e_psi, e_rho = rel_l2(res[1]["psi"], res[0]["psi"]), rel_l2(res[1]["rho"], res[0]["rho"])
     print(f"\nsingle vs double droplets, 64^2, 100 steps: psi {e_psi:.2e}, rho {e_rho:.2e}")
     assert e_psi <= 1e-4 and e_rho <= 1e-3
+
+
+@pytest.mark.parametrize("hold", [True, False])
+def test_carrier_with_cylinder_matches_oracle(ctx, hold):
+    """The immersed cylinder (penalisation, fringe strip, held or decelerated
+    mean flow): fields, mean flow and the force on the body against the oracle."""
+    N, nu, D, dt, nsub = 64, 5e-3, 1e-3, 1e-3, 30
+    body = dict(xc=0.3, yc=0.52, r=0.06, eta=2e-3, fringe_x0=0.8, fringe_x1=0.98, fringe_sigma=200.0,
+                hold_mean_flow=hold)
+    w0 = 5.0 * _random_field(N, 7)
+    ns = fla.NavierStokes(ctx, N, nu, D, dt, w0, mean_u=(1.0, 0.0), body=body)
+    ob = NS.Body(xc=0.3, yc=0.52, R=0.06, eta=2e-3, x0=0.8, x1=0.98, sigma_max=200.0, hold_mean_flow=hold)
+    st = NS.init(N, nu, D, w0, U=(1.0, 0.0), body=ob)
+    F0 = ns.body_force()
+    assert np.allclose(F0, NS.body_force(st), rtol=1e-11, atol=1e-9)
+    ns.step(nsub)
+    NS.step(st, dt, nsub=nsub)
+    g = ns.fields()
+    psi = NS.streamfunction(st)
+    print(f"\nhold {hold}: psi rel-L2 {rel_l2(g['psi'], psi):.2e}, U {g['U']} vs {st.U}, "
+          f"force {ns.body_force()} vs {NS.body_force(st)}")
+    assert rel_l2(g["psi"], psi) <= 1e-10
+    assert np.allclose(g["U"], st.U, rtol=1e-11, atol=1e-14)
+    assert np.allclose(ns.body_force(), NS.body_force(st), rtol=1e-9, atol=1e-9)
+    if hold:
+        assert np.array_equal(g["U"], [1.0, 0.0])
