@@ -178,6 +178,72 @@ def two_way_taylor_green(scale: int = 1, nsteps: int = 200, n0: float = 1.0) -> 
     return TwoWayCase(wl=wl, nu=1e-3, diff=1e-3, omega0=omega0, mean_u=(0.0, 0.0))
 
 
+@dataclass
+class CylinderCase:
+    """Flow past a cylinder with droplets injected upstream (the paper's test
+    case, Sec. 5) on the periodic two-way carrier: the droplet workload (FLA
+    seeds and PSI-CELL parcels), the carrier's viscosity and vapour
+    diffusivity, the cylinder (volume penalisation) and fringe, the inflow and
+    the carrier steps run before the first release."""
+    wl: Workload
+    nu: float
+    diff: float
+    body: dict
+    mean_u: tuple
+    warm_steps: int
+    R: float
+    xc: float
+
+
+def cylinder_flow(re: float = 20.0, evaporating: bool = False, scale: int = 1, nsteps: int = 2000,
+                  warm_steps: int = 1000, lpt: bool = True) -> CylinderCase:
+    """Cylinder of radius R = 0.05 at (0.3, 0.5) in a periodic unit square of
+    256^2 cells (R = 12.8 cells), inflow U = (1, 0) held fixed, Re = 2 U R / nu
+    (20: steady wake; 100: shedding), vapour diffusivity nu (Schmidt number 1),
+    a fringe strip 0.92 <= x <= 1 absorbing the wake.  Droplets enter at
+    x/R = -5 (x = 0.05) across 0.3 <= y <= 0.7: FLA releases of 100 seeds every
+    5 steps, PSI-CELL releases of 2,000 parcels every step (100 times the droplets
+    per unit time, as in the paper), n0 = 1, St = tau U / 2R of 0.1 (0.5 for the
+    evaporating Re = 100 case, as Table 1), delta = -0.2 when evaporating.
+    The carrier runs warm_steps steps before the first release.  ``scale``
+    divides the mesh (the droplet counts stay)."""
+    N = 256 // scale
+    R, xc, yc, U = 0.05, 0.3, 0.5, 1.0
+    dt = 1e-3
+    nu = 2.0 * U * R / re
+    st = 0.5 if (evaporating and re >= 100) else 0.1
+    St0 = st * 2.0 * R / U
+    delta = -0.2 if evaporating else 0.0
+    y_lo, y_hi, x_inj = 0.3, 0.7, xc - 5.0 * R
+    # FLA: 100 seeds per release every 5 steps
+    every, per = 5, 100
+    n_rel = nsteps // every
+    ys = y_lo + (np.arange(per) + 0.5) * (y_hi - y_lo) / per
+    x0 = np.stack([np.full(n_rel * per, x_inj), np.tile(ys, n_rel)], axis=1)
+    batch = np.repeat(np.arange(n_rel, dtype=np.int32), per)
+    step_start = (np.arange(n_rel) * every).astype(np.int32)
+    tau = every * dt
+    h0 = max((y_hi - y_lo) / per, U * tau)
+    fla = Cloud(kind=CLOUD_FLA, x0=x0, batch=batch, step_start=step_start, St0=np.full(n_rel, St0),
+                n0=np.ones(n_rel), h0=np.full(n_rel, h0))
+    lp = None
+    if lpt:
+        m_b = 2000
+        rng = np.random.default_rng(5)
+        xl = np.stack([np.full(nsteps * m_b, x_inj), rng.uniform(y_lo, y_hi, nsteps * m_b)], axis=1)
+        V_inj = (y_hi - y_lo) * U * dt          # swept by the inlet per release
+        lp = Cloud(kind=CLOUD_LPT, x0=xl, batch=np.repeat(np.arange(nsteps, dtype=np.int32), m_b),
+                   step_start=np.arange(nsteps, dtype=np.int32), St0=np.full(nsteps, St0),
+                   n0=np.full(nsteps, V_inj / m_b), h0=np.zeros(nsteps))
+    dx = 1.0 / N
+    wl = Workload(name=f"cylinder_re{int(re)}{'_evap' if evaporating else ''}_{N}x{N}", dim=2, n_cells_axis=N, dt=dt,
+                  nsteps=nsteps, window=10, delta=delta, carrier=Carrier(kind=CARRIER_UNIFORM, dim=2),
+                  fla=fla, lpt=lp, kernel=KERNEL_ISO, h_min=0.5 * dx, h_max=4.0 * dx)
+    body = dict(xc=xc, yc=yc + 0.25 * dx, r=R, eta=2.0 * dt, fringe_x0=0.92, fringe_x1=1.0, fringe_sigma=200.0,
+                hold_mean_flow=True)   # off the node lattice's symmetry line by a quarter cell: shedding can start
+    return CylinderCase(wl=wl, nu=nu, diff=nu, body=body, mean_u=(U, 0.0), warm_steps=warm_steps, R=R, xc=xc)
+
+
 def _jet_vortices(rng: np.random.Generator, n_vort: int, width: float) -> np.ndarray:
     x0 = rng.uniform(0.0, 1.0, n_vort)
     yc = rng.uniform(0.3, 0.7, n_vort)
