@@ -199,7 +199,8 @@ def cylinder_flow(re: float = 20.0, evaporating: bool = False, scale: int = 1, n
                   warm_steps: int = 1000, lpt: bool = True) -> CylinderCase:
     """Cylinder of radius R = 0.05 at (0.3, 0.5) in a periodic unit square of
     256^2 cells (R = 12.8 cells), inflow U = (1, 0) held fixed, Re = 2 U R / nu
-    (20: steady wake; 100: shedding), vapour diffusivity nu (Schmidt number 1),
+    (20: steady wake; 100: shedding), vapour diffusivity nu/2 (Schmidt number 2,
+    within the explicit diffusion's limit at 256^2),
     a fringe strip 0.92 <= x <= 1 absorbing the wake.  Droplets enter at
     x/R = -5 (x = 0.05) across 0.3 <= y <= 0.7: FLA releases of 100 seeds every
     5 steps, PSI-CELL releases of 2,000 parcels every step (100 times the droplets
@@ -241,7 +242,7 @@ def cylinder_flow(re: float = 20.0, evaporating: bool = False, scale: int = 1, n
                   fla=fla, lpt=lp, kernel=KERNEL_ISO, h_min=0.5 * dx, h_max=4.0 * dx)
     body = dict(xc=xc, yc=yc + 0.25 * dx, r=R, eta=2.0 * dt, fringe_x0=0.92, fringe_x1=1.0, fringe_sigma=200.0,
                 hold_mean_flow=True)   # off the node lattice's symmetry line by a quarter cell: shedding can start
-    return CylinderCase(wl=wl, nu=nu, diff=nu, body=body, mean_u=(U, 0.0), warm_steps=warm_steps, R=R, xc=xc)
+    return CylinderCase(wl=wl, nu=nu, diff=0.5 * nu, body=body, mean_u=(U, 0.0), warm_steps=warm_steps, R=R, xc=xc)
 
 
 def _jet_vortices(rng: np.random.Generator, n_vort: int, width: float) -> np.ndarray:
