@@ -189,8 +189,9 @@ class ClockSampler:
 class RunPath:
     """Device buffers and the issue order of one whole run of a workload."""
 
-    def __init__(self, ctx, wl, fla, form, with_fla=True, with_lpt=False, parcel_deposit="psicell"):
+    def __init__(self, ctx, wl, fla, form, with_fla=True, with_lpt=False, parcel_deposit="psicell", ordered=True):
         dname, pname, fold_guard, learned = FORMS[form]
+        self.ordered = ordered
         self.parcel_deposit = fla.psicell if parcel_deposit == "psicell" else fla.cic
         self.fla, self.ctx, self.wl, self.form = fla, ctx, wl, form
         self.dtype = getattr(fla, dname)
@@ -224,6 +225,11 @@ class RunPath:
     def issue(self):
         """Enqueue the whole run on the current stream (capturable)."""
         fla, wl, m = self.fla, self.wl, self.m
+        binned = None   # the cloud whose cell-sorted order the workspace holds
+
+        def order(c):
+            return fla.workspace_order(self.ws, m, c.n) if self.ordered and binned is c else None
+
         for s in range(0, wl.nsteps, wl.window):
             if s == 0 or not wl.carrier.steady:   # a steady carrier is sampled once per run
                 t = 0.0 if wl.carrier.steady else s * wl.dt
@@ -233,14 +239,17 @@ class RunPath:
                     ln = self.lnodes if self.lnodes is not None else self.nodes
                     fla.carrier_sample(self.ctx, self.desc, m, t, self.lpt.dtype, ln)
             if self.cloud is not None:
-                fla.advance(self.ctx, self.cloud, m, self.nodes, s, wl.window, wl.dt, reset_acc=True)
+                fla.advance(self.ctx, self.cloud, m, self.nodes, s, wl.window, wl.dt, reset_acc=True,
+                            order=order(self.cloud))
             if self.lpt is not None:
                 ln = self.lnodes if self.lnodes is not None else self.nodes
-                fla.advance(self.ctx, self.lpt, m, ln, s, wl.window, wl.dt, reset_acc=True)
+                fla.advance(self.ctx, self.lpt, m, ln, s, wl.window, wl.dt, reset_acc=True, order=order(self.lpt))
             if self.cloud is not None:
                 fla.deposit_sources(self.ctx, self.cloud, m, self.cfg, self.out, self.ws)
+                binned = self.cloud
             if self.lpt is not None:
                 self.parcel_deposit(self.ctx, self.lpt, m, wl.window * wl.dt, self.psi, self.ws)
+                binned = self.lpt
 
 
 def capture(path):

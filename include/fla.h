@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define FLA_ABI_VERSION 10
+#define FLA_ABI_VERSION 11
 
 /* cudaStream_t without including the CUDA headers. */
 typedef struct CUstream_st* fla_stream_t;
@@ -286,11 +286,33 @@ int fla_batch_deadline(double St0, double delta, double dt, int32_t step_start, 
 int fla_advance(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, const void* nodes_dev,
                 int32_t step0, int32_t nsteps, double dt, uint32_t flags, fla_stream_t stream);
 
+/* fla_advance with a processing order: thread t of the launch advances
+ * droplet order_dev[t] (device, n words, 4-byte aligned, caller-owned, read
+ * only).  Each droplet's arithmetic does not depend on the order, so the
+ * results are bit for bit those of fla_advance; the order only decides which
+ * droplets share a warp.  With the cell-sorted permutation of the cloud's last
+ * binning (fla_workspace_order) the droplets of a warp lie in neighbouring
+ * cells and read the same carrier nodes, and the active ones are packed
+ * together.  order_dev must be a permutation of [0, n): entries >= n are
+ * skipped (those threads advance nothing), repeated entries race.  NULL
+ * gives fla_advance. */
+int fla_advance_ordered(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, const void* nodes_dev,
+                        const uint32_t* order_dev, int32_t step0, int32_t nsteps, double dt, uint32_t flags,
+                        fla_stream_t stream);
+
 /* Workspace bytes needed by fla_cell_bins, fla_deposit_sources and
  * psicell_deposit for a cloud of n_droplets on this mesh (the maximum over the
  * three, for the given dtype and kernel).  The workspace must be 256-byte
  * aligned. */
 int fla_workspace_size(const fla_mesh* mesh, int32_t dtype, int32_t kernel, int64_t n_droplets, size_t* bytes);
+
+/* Byte offset, within a deposit workspace, of the sorted permutation (n
+ * uint32 words: the droplet index at each position of the stable sort by cell
+ * key, inactive droplets last) that fla_cell_bins, fla_deposit_sources,
+ * psicell_deposit, cic_deposit and fla_learn_grad leave there for a cloud of
+ * n_droplets (>= 1) on this mesh.  It stays valid until the workspace serves
+ * another cloud; it is the processing order fla_advance_ordered wants. */
+int fla_workspace_order(const fla_mesh* mesh, int64_t n_droplets, size_t* offset);
 
 /* Cell binning of a cloud: key_i = linear index of the cell holding x_i
  * (floor(x N) per axis in the cloud's precision, clamped to N-1 so x = 1 is in

@@ -51,9 +51,23 @@ struct AdvArgs {
     uint32_t* fold_list; // droplets handed from the screening pass to the guarded pass
     unsigned int* fold_count;
     float tau_fold;
+    const uint32_t* order; // thread t advances droplet order[t] (null: droplet t)
 };
 
 enum { kPlain = 0, kScreen = 1, kGuarded = 2 };
+
+// The droplet of thread t: order[t] when an order is given (a permutation of
+// [0, n), e.g. the cell-sorted one of the last binning, so that the droplets
+// of a warp share carrier nodes), else t.  Entries out of range map to n (no
+// droplet): a wrong order leaves droplets unadvanced but never reads or writes
+// outside the cloud.
+__device__ __forceinline__ int64_t droplet_of(const uint32_t* order, int64_t t, int64_t n)
+{
+    if (t >= n) return n;
+    if (!order) return t;
+    const int64_t i = (int64_t)__ldg(order + t);
+    return i < n ? i : n;
+}
 
 // Double-precision J, W of one droplet in the fold guard, and its RK4 stage
 // accumulators.
@@ -409,7 +423,7 @@ __global__ void __launch_bounds__(128) k_advance(AdvArgs a)
     constexpr bool FOLD = MODE == kGuarded;
     int nf = 0, n = 0;
     if (MODE != kGuarded) {
-        const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        const int64_t i = droplet_of(a.order, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, a.n);
         n = i < a.n ? advance_one<T, D, FLA, MODE>(a, i, nf) : 0;
     } else {   // the listed droplets, grid-stride
         const unsigned cnt = *a.fold_count;
@@ -448,6 +462,7 @@ struct AdvX2Args {
     df dt, half, sixth, delta;
     int reset;
     DevStatus* status;
+    const uint32_t* order; // as AdvArgs::order
 };
 
 // Bi/trilinear interpolation of the double-float node values at the
@@ -705,7 +720,7 @@ __global__ void __launch_bounds__(kAdvX2Threads, x2_min_blocks<D, FLA>()) k_adva
 {
     pdl_entry();
     constexpr int NY = FLA ? 2 * D + 2 * D * D : 2 * D;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = droplet_of(a.order, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, a.n);
     int n = 0;
     if (i < a.n) {
         RegVec<NY> y, ks;
@@ -796,9 +811,10 @@ cudaError_t launch_t(const AdvArgs& a, cudaStream_t s, int guarded_blocks = 0)
 }  // namespace
 
 cudaError_t launch_advance(const fla_cloud& cl, const fla_mesh& m, const void* nodes, int step0, int nsteps,
-                           double dt, bool reset, DevStatus* st, int num_sms, cudaStream_t s)
+                           double dt, bool reset, DevStatus* st, int num_sms, cudaStream_t s, const uint32_t* order)
 {
     AdvArgs a{};
+    a.order = order;
     a.status = st;
     a.state = cl.state_dev;
     a.meta = cl.meta_dev;
@@ -833,6 +849,7 @@ cudaError_t launch_advance(const fla_cloud& cl, const fla_mesh& m, const void* n
         b.delta = df_host(cl.delta);
         b.reset = reset ? 1 : 0;
         b.status = st;
+        b.order = order;
         if (cl.dim == 2) return fla ? launch_x2<2, true>(b, s) : launch_x2<2, false>(b, s);
         return fla ? launch_x2<3, true>(b, s) : launch_x2<3, false>(b, s);
     }

@@ -99,6 +99,9 @@ WsLayout layout(const fla_mesh& m, int dtype, int kernel, int64_t n)
     return L;
 }
 
+// Which of the sort's ping-pong buffers holds the sorted order of a cloud of n.
+int sorted_buffer(const fla_mesh& m, int64_t n) { return bin_sorted_buffer(bin_plan(n, cells_of(m))); }
+
 template <typename P>
 P* at(void* base, size_t off) { return reinterpret_cast<P*>(static_cast<char*>(base) + off); }
 
@@ -351,7 +354,15 @@ int fla_batch_deadline(double St0, double delta, double dt, int32_t step_start, 
 int fla_advance(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, const void* nodes_dev, int32_t step0,
                 int32_t nsteps, double dt, uint32_t flags, fla_stream_t stream)
 {
+    return fla_advance_ordered(ctx, cloud, mesh, nodes_dev, nullptr, step0, nsteps, dt, flags, stream);
+}
+
+int fla_advance_ordered(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, const void* nodes_dev,
+                        const uint32_t* order_dev, int32_t step0, int32_t nsteps, double dt, uint32_t flags,
+                        fla_stream_t stream)
+{
     if (!ctx) return FLA_ERR_ARG;
+    if (order_dev && !aligned(order_dev, 4)) return FLA_ERR_ARG;
     int st = cloud_ok(cloud, mesh);
     if (st != FLA_OK) return st;
     if (nsteps < 0 || step0 < 0 || (int64_t)step0 + nsteps > 2147483647LL || !(dt > 0) || !isfinite(dt))
@@ -363,7 +374,15 @@ int fla_advance(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, cons
     PhaseScope ps(ctx, FLA_PHASE_ADVANCE, (cudaStream_t)stream, guarded ? 2 : 1);
     return cuda_status(launch_advance(*cloud, *mesh, nodes_dev, step0, nsteps, dt,
                                       (flags & FLA_ADVANCE_RESET_ACC) != 0, (DevStatus*)ctx->status_dev,
-                                      ctx->num_sms, (cudaStream_t)stream));
+                                      ctx->num_sms, (cudaStream_t)stream, order_dev));
+}
+
+int fla_workspace_order(const fla_mesh* mesh, int64_t n_droplets, size_t* offset)
+{
+    if (!offset || !mesh_ok(mesh) || n_droplets < 1 || n_droplets >= 2147483647LL) return FLA_ERR_ARG;
+    // keys and values lead the layout and depend on n alone
+    *offset = layout(*mesh, FLA_F32, FLA_KERNEL_ISO, n_droplets).vals[sorted_buffer(*mesh, n_droplets)];
+    return FLA_OK;
 }
 
 size_t fla_fold_bytes(int32_t dim, int64_t n)
@@ -474,9 +493,6 @@ int deposit_impl(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, con
     return cuda_status(launch_nw_gather(*cloud, *mesh, *cfg, at<void>(ws, L.rec), bins, ext, w, *out,
                                         (DevStatus*)ctx->status_dev, ctx->num_sms, s));
 }
-
-// Which of the sort's ping-pong buffers holds the sorted order of a cloud of n.
-int sorted_buffer(const fla_mesh& m, int64_t n) { return bin_sorted_buffer(bin_plan(n, cells_of(m))); }
 
 struct LearnLayout {
     size_t q, aux, dldc, partial, scal, total;

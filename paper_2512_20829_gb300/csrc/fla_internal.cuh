@@ -272,7 +272,8 @@ int cloud_valid(const fla_cloud* c, const fla_mesh* m);
 cudaError_t launch_carrier_sample(const fla_carrier_desc& c, const fla_mesh& m, double t, int dtype, void* nodes,
                                   cudaStream_t s);
 cudaError_t launch_advance(const fla_cloud& cl, const fla_mesh& m, const void* nodes, int step0, int nsteps,
-                           double dt, bool reset, DevStatus* st, int num_sms, cudaStream_t s);
+                           double dt, bool reset, DevStatus* st, int num_sms, cudaStream_t s,
+                           const uint32_t* order = nullptr);
 // Binning of one cloud with n > 0 (one memset, one kernel): cell keys, the
 // stable sort of (key, index) and bin_start (n_cells + 1 words).  The sorted
 // keys and permutation end in buffer bin_sorted_buffer(plan).  zero[0, nzero)

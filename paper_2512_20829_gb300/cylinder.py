@@ -49,7 +49,8 @@ def run(ctx, case: I.CylinderCase, method: str = "fla", dtype: int = fla.F32, co
     for w in range(n_windows):
         step = w * wl.window
         ns.nodes(dtype, nodes)
-        fla.advance(ctx, cloud, m, nodes, step, wl.window, wl.dt, reset_acc=True)
+        order = fla.workspace_order(ws, m, cloud.n) if w > 0 else None   # cell-sorted by the last deposit
+        fla.advance(ctx, cloud, m, nodes, step, wl.window, wl.dt, reset_acc=True, order=order)
         if method == "fla":
             fla.deposit_sources(ctx, cloud, m, cfg, out, ws)
         else:

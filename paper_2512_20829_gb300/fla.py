@@ -18,7 +18,7 @@ from . import inputs as I
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfla.so")
 
-ABI_VERSION = 10            # FLA_ABI_VERSION of include/fla.h that these structures mirror
+ABI_VERSION = 11            # FLA_ABI_VERSION of include/fla.h that these structures mirror
 F32, F64, F32X2 = 0, 1, 2  # F32X2: compensated single precision (hi planes, then lo planes)
 CLOUD_FLA, CLOUD_LPT = 0, 1
 KERNEL_ISO, KERNEL_ANISO = 0, 1
@@ -31,7 +31,7 @@ MAX_VORTICES = 16
 
 EXPORTED = ["fla_abi_version", "fla_status_string", "fla_create", "fla_destroy", "fla_state_layout",
             "fla_carrier_nodes_bytes", "fla_carrier_sample", "fla_batch_deadline", "fla_advance",
-            "fla_workspace_size", "fla_cell_bins", "fla_deposit_sources", "psicell_deposit", "cic_deposit",
+            "fla_advance_ordered", "fla_workspace_size", "fla_workspace_order", "fla_cell_bins", "fla_deposit_sources", "psicell_deposit", "cic_deposit",
             "fla_sync_status",
             "fla_profile_enable", "fla_profile_read", "fla_phase_name", "fla_fold_bytes", "fla_mlp_pack",
             "fla_mlp_forward", "fla_learn_workspace_size", "fla_learn_grad", "fla_adam_step",
@@ -132,6 +132,8 @@ def lib() -> C.CDLL:
         L.fla_carrier_sample.argtypes = [v, P(CarrierDesc), P(Mesh), d, i32, v, v]
         L.fla_batch_deadline.argtypes = [d, d, d, i32, P(i32)]
         L.fla_advance.argtypes = [v, P(Cloud), P(Mesh), v, i32, i32, d, u32, v]
+        L.fla_advance_ordered.argtypes = [v, P(Cloud), P(Mesh), v, v, i32, i32, d, u32, v]
+        L.fla_workspace_order.argtypes = [P(Mesh), i64, P(C.c_size_t)]
         L.fla_workspace_size.argtypes = [P(Mesh), i32, i32, i64, P(C.c_size_t)]
         L.fla_cell_bins.argtypes = [v, P(Cloud), P(Mesh), v, v, v, v, C.c_size_t, v]
         L.fla_deposit_sources.argtypes = [v, P(Cloud), P(Mesh), P(DepositCfg), P(Sources), v, C.c_size_t, v]
@@ -449,10 +451,27 @@ def carrier_sample(ctx: Context, desc: CarrierDesc, m: Mesh, t: float, dtype: in
 
 
 def advance(ctx: Context, cloud: DeviceCloud, m: Mesh, nodes, step0: int, nsteps: int, dt: float,
-            reset_acc: bool = False, stream=None):
+            reset_acc: bool = False, stream=None, order=None):
+    """fla_advance; with order (n int32 words on the device, a permutation of
+    the droplets, e.g. workspace_order) fla_advance_ordered: same results, the
+    droplets processed in that order."""
     cs = cloud.struct()
-    check(lib().fla_advance(ctx.handle, C.byref(cs), C.byref(m), _ptr(nodes), int(step0), int(nsteps), float(dt),
-                            ADVANCE_RESET_ACC if reset_acc else 0, _stream_ptr(stream)), "fla_advance")
+    flags = ADVANCE_RESET_ACC if reset_acc else 0
+    if order is None:
+        check(lib().fla_advance(ctx.handle, C.byref(cs), C.byref(m), _ptr(nodes), int(step0), int(nsteps),
+                                float(dt), flags, _stream_ptr(stream)), "fla_advance")
+    else:
+        check(lib().fla_advance_ordered(ctx.handle, C.byref(cs), C.byref(m), _ptr(nodes), _ptr(order), int(step0),
+                                        int(nsteps), float(dt), flags, _stream_ptr(stream)), "fla_advance_ordered")
+
+
+def workspace_order(ws, m: Mesh, n: int):
+    """The cell-sorted permutation that the last binning of a cloud of n
+    droplets left in the (aligned) workspace ws, as an int32 view."""
+    torch = _torch()
+    off = C.c_size_t()
+    check(lib().fla_workspace_order(C.byref(m), int(n), C.byref(off)), "fla_workspace_order")
+    return ws[off.value:off.value + 4 * int(n)].view(torch.int32)
 
 
 def workspace_size(m: Mesh, dtype: int, kernel: int, n: int) -> int:
@@ -660,6 +679,10 @@ class Simulation:
         self.ws = aligned_ws(workspace(self.m, dtype, wl.kernel, n_ws, device))
         self.step = 0
         self._sampled_t = None
+        self._binned = None   # the cloud whose cell-sorted order self.ws holds
+
+    def _order(self, c):
+        return workspace_order(self.ws, self.m, c.n) if self._binned is c else None
 
     def reset(self):
         """Back to the seeds (device-side copies only re-upload the initial planes)."""
@@ -669,6 +692,7 @@ class Simulation:
             self.lpt = DeviceCloud.from_seeds(wl.lpt, wl.dim, wl.delta, wl.dt, self.dtype, self.lpt.state.device)
         self.step = 0
         self._sampled_t = None
+        self._binned = None
 
     def _fla_cloud(self, device):
         wl = self.wl
@@ -684,14 +708,18 @@ class Simulation:
         if self._sampled_t != t_c:
             carrier_sample(self.ctx, self.desc, self.m, t_c, self.dtype, self.nodes, stream)
             self._sampled_t = t_c
-        advance(self.ctx, self.fla, self.m, self.nodes, self.step, k, wl.dt, reset_acc=True, stream=stream)
+        advance(self.ctx, self.fla, self.m, self.nodes, self.step, k, wl.dt, reset_acc=True, stream=stream,
+                order=self._order(self.fla))
         if self.lpt is not None:
-            advance(self.ctx, self.lpt, self.m, self.nodes, self.step, k, wl.dt, reset_acc=True, stream=stream)
+            advance(self.ctx, self.lpt, self.m, self.nodes, self.step, k, wl.dt, reset_acc=True, stream=stream,
+                    order=self._order(self.lpt))
         self.step += k
         if deposit:
             deposit_sources(self.ctx, self.fla, self.m, self.cfg, self.out, self.ws, stream)
+            self._binned = self.fla
         if with_psicell and self.lpt is not None:
             psicell(self.ctx, self.lpt, self.m, wl.window * wl.dt, self.psi, self.ws, stream=stream)
+            self._binned = self.lpt
 
     def run(self, nsteps: int | None = None, deposit_every: bool = True, stream=None):
         total = self.wl.nsteps if nsteps is None else nsteps
@@ -883,7 +911,10 @@ class TwoWay:
         wl = self.wl
         k = wl.window
         self.ns.nodes(self.dtype, self.nodes, stream)
-        advance(self.ctx, self.fla, self.m, self.nodes, self.step, k, wl.dt, reset_acc=True, stream=stream)
+        # after the first window the workspace holds the droplets' cell-sorted order
+        order = workspace_order(self.ws, self.m, self.fla.n) if self.step > 0 else None
+        advance(self.ctx, self.fla, self.m, self.nodes, self.step, k, wl.dt, reset_acc=True, stream=stream,
+                order=order)
         deposit_sources(self.ctx, self.fla, self.m, self.cfg, self.out, self.ws, stream)
         self.ns.step(k, self.out if self.coupled else None, stream)
         self.step += k

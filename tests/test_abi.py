@@ -95,6 +95,14 @@ def test_sizes(lib):
     out = C.c_size_t()
     assert lib.fla_workspace_size(C.byref(fla.mesh(4, 16)), 0, 0, 10, C.byref(out)) == -1
     assert lib.fla_workspace_size(C.byref(m), 0, 0, -1, C.byref(out)) == -1
+    # the sorted permutation sits in one of the two value buffers, after the two key buffers
+    for n in (1, 1000, 100000):
+        assert lib.fla_workspace_order(C.byref(m), n, C.byref(out)) == 0
+        u = (4 * n + 255) // 256 * 256
+        assert out.value in (2 * u, 3 * u)
+        assert out.value + 4 * n <= fla.workspace_size(m, fla.F32, fla.KERNEL_ISO, n)
+    assert lib.fla_workspace_order(C.byref(m), 0, C.byref(out)) == -1
+    assert lib.fla_workspace_order(C.byref(fla.mesh(4, 16)), 10, C.byref(out)) == -1
 
 
 def test_batch_deadline_agrees_with_oracle(lib):
@@ -127,6 +135,9 @@ def test_entry_points_reject_bad_arguments_before_launching(lib):
     assert lib.fla_advance(null, C.byref(cl), C.byref(m), null, 0, 1, 1e-3, 0, null) == -1
     fake_ctx = C.c_void_p(1)   # never dereferenced: validation fails first
     assert lib.fla_advance(fake_ctx, C.byref(cl), C.byref(m), null, 0, 1, 1e-3, 0, null) == -1
+    # a processing order that is not 4-byte aligned
+    assert lib.fla_advance_ordered(fake_ctx, C.byref(cl), C.byref(m), C.c_void_p(256), C.c_void_p(258), 0, 1, 1e-3,
+                                   0, null) == -1
     cl.dim = 3
     assert lib.fla_advance(fake_ctx, C.byref(cl), C.byref(m), null, 0, 1, 1e-3, 0, null) == -1
     cfg = fla.deposit_cfg(0, 0.0, 0.1, 0.01)
