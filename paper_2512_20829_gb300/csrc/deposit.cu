@@ -52,15 +52,24 @@ struct GatherArgs {
     DevStatus* status;
 };
 
-// CTA tile of cells and the per-warp sub-tile (32 cells, one per lane).
+// CTA tile of cells and the per-warp sub-tile (32 cells, one per lane).  A
+// tile's candidates arrive in mesh-row order (x rows, y inner, z outer), so a
+// staged chunk holds records of a few neighbouring rows: it spans the tile in
+// x but only part of it in y and z.  The sub-tiles therefore split the tile
+// four ways in x, two in y and not in z (3D: 2 x 4 x 4 cells), so that every
+// warp finds records of its own in most chunks; with 4 x 4 x 2 sub-tiles
+// (two per axis) the warps whose z half the chunk missed idled at the chunk's
+// barrier.  A support reaches as many sub-tiles either way.
 template <int D> struct Tile;
 template <> struct Tile<2> {
-    static constexpr int X = 16, Y = 16, Z = 1;      // 8 warps of 8 x 4 cells
-    static constexpr int SX = 8, SY = 4, SZ = 1;
+    static constexpr int X = 16, Y = 16, Z = 1;      // 8 warps of 4 x 8 cells
+    static constexpr int SX = 4, SY = 8, SZ = 1;
+    static constexpr int NSX = 4, NSY = 2, NSZ = 1;
 };
 template <> struct Tile<3> {
-    static constexpr int X = 8, Y = 8, Z = 4;        // 8 warps of 4 x 4 x 2 cells
-    static constexpr int SX = 4, SY = 4, SZ = 2;
+    static constexpr int X = 8, Y = 8, Z = 4;        // 8 warps of 2 x 4 x 4 cells
+    static constexpr int SX = 2, SY = 4, SZ = 4;
+    static constexpr int NSX = 4, NSY = 2, NSZ = 1;
 };
 
 constexpr int GT = 256;            // threads per CTA = cells per tile
@@ -194,35 +203,34 @@ __device__ __forceinline__ void support_box(const T* r, T W2[3])
 // the record's support sphere (radius^2 in slot EXT, with the 2^-10 margin of
 // the tile test) reaches sub-tile w's box of cell centres and, for the J-scaled
 // kernel, its support box overlaps that box too.  slab[q][s] = {lo, hi} of the
-// s-th slab of sub-tiles along axis q (2D: 2 in x, 4 in y; 3D: 2 per axis).
+// s-th slab of sub-tiles along axis q (Tile<D>::NSX, NSY, NSZ of them).
 template <typename T, int D, int KER>
 __device__ __forceinline__ unsigned subtile_mask(const T* rv, const T (*slab)[4][2])
 {
-    constexpr int NS1 = D == 2 ? 4 : 2;
-    constexpr int NS2 = D == 2 ? 1 : 2;
+    constexpr int NSX = Tile<D>::NSX, NSY = Tile<D>::NSY, NSZ = Tile<D>::NSZ;
     T W2[3];
     support_box<T, D, KER>(rv, W2);
     const T e2m = rv[ExtSlot<D, KER>::v] * T(1.0009765625);
-    T d2a[2], d2b[4], d2c[2];
-    bool ba[2], bb[4], bc[2];
+    T d2a[NSX], d2b[NSY], d2c[NSZ];
+    bool ba[NSX], bb[NSY], bc[NSZ];
     auto dist2 = [&](int q, int sl) {
         const T dl = slab[q][sl][0] - rv[q], dh = rv[q] - slab[q][sl][1];
         const T dd = dl > T(0) ? dl : (dh > T(0) ? dh : T(0));
         return dd * dd;
     };
 #pragma unroll
-    for (int sl = 0; sl < 2; ++sl) { d2a[sl] = dist2(0, sl); ba[sl] = d2a[sl] <= W2[0]; }
+    for (int sl = 0; sl < NSX; ++sl) { d2a[sl] = dist2(0, sl); ba[sl] = d2a[sl] <= W2[0]; }
 #pragma unroll
-    for (int sl = 0; sl < NS1; ++sl) { d2b[sl] = dist2(1, sl); bb[sl] = d2b[sl] <= W2[1]; }
+    for (int sl = 0; sl < NSY; ++sl) { d2b[sl] = dist2(1, sl); bb[sl] = d2b[sl] <= W2[1]; }
 #pragma unroll
-    for (int sl = 0; sl < NS2; ++sl) {
+    for (int sl = 0; sl < NSZ; ++sl) {
         d2c[sl] = D == 3 ? dist2(2, sl) : T(0);
         bc[sl] = D == 3 ? d2c[sl] <= W2[2] : true;
     }
     unsigned m = 0;
 #pragma unroll
     for (int w = 0; w < GT / 32; ++w) {
-        const int sx = w & 1, sy = D == 2 ? (w >> 1) : ((w >> 1) & 1), sz = D == 2 ? 0 : (w >> 2);
+        const int sx = w % NSX, sy = (w / NSX) % NSY, sz = w / (NSX * NSY);
         T d2 = T(0);
         d2 += d2a[sx];
         d2 += d2b[sy];
@@ -238,13 +246,15 @@ __device__ __forceinline__ void tile_cell(int tid, const int t0[3], int w0[3], i
 {
     const int lane = tid & 31, warp = tid >> 5;
     constexpr int SX = Tile<D>::SX, SY = Tile<D>::SY, SZ = Tile<D>::SZ;
-    if (D == 2) {
-        w0[0] = t0[0] + (warp & 1) * SX; w0[1] = t0[1] + (warp >> 1) * SY; w0[2] = 0;
-        cc[0] = w0[0] + (lane & 7); cc[1] = w0[1] + (lane >> 3); cc[2] = 0;
-    } else {
-        w0[0] = t0[0] + (warp & 1) * SX; w0[1] = t0[1] + ((warp >> 1) & 1) * SY; w0[2] = t0[2] + (warp >> 2) * SZ;
-        cc[0] = w0[0] + (lane & 3); cc[1] = w0[1] + ((lane >> 2) & 3); cc[2] = w0[2] + (lane >> 4);
-    }
+    constexpr int NSX = Tile<D>::NSX, NSY = Tile<D>::NSY;
+    static_assert(SX * SY * SZ == 32 && Tile<D>::NSX * Tile<D>::NSY * Tile<D>::NSZ == GT / 32, "sub-tiles");
+    static_assert(NSX <= 4 && NSY <= 4 && Tile<D>::NSZ <= 4, "at most 4 slabs per axis");
+    w0[0] = t0[0] + (warp % NSX) * SX;
+    w0[1] = t0[1] + ((warp / NSX) % NSY) * SY;
+    w0[2] = D == 3 ? t0[2] + (warp / (NSX * NSY)) * SZ : 0;
+    cc[0] = w0[0] + lane % SX;
+    cc[1] = w0[1] + (lane / SX) % SY;
+    cc[2] = D == 3 ? w0[2] + lane / (SX * SY) : 0;
 }
 
 // Source terms of one cell from its weight sum Dt and weighted sums Nq (Eq. 13).
