@@ -160,82 +160,111 @@ __device__ __forceinline__ T weight_of(const T* r, const float* xcf, const T* xc
     }
 }
 
-// Squared half-widths per axis of the axis-aligned box that holds a J-scaled
-// record's truncated support {d : d' P d <= 9}: 9 (P^-1)_qq, from the
-// cofactors of P.  The margin covers the rounding of the single- or double-
-// precision evaluation and of this bound; it grows with a bound on the
-// condition number of Sigma, kappa <= tr(Sigma)^D det(P).  Where that bound is
-// large or P is not positive definite, no box is used (+inf) and the sphere
-// test alone decides.  The spherical kernel needs no box: its sphere test is exact.
+// Bounds of a J-scaled record's truncated support {d : d' P d <= 9} (P = Sigma^-1):
+//  * W2: squared half-widths per axis of the axis-aligned box that holds it,
+//    9 Sigma_qq = 9 C_qq / det P (C the cofactors of P);
+//  * a separating axis against a box: with b the offset from the record to the
+//    box's nearest point, every point p of the box has (p - x).b >= |b|^2 (the
+//    box is convex), while the support reaches 3 sqrt(b' Sigma b) / |b| along b
+//    at most; so it misses the box when |b|^4 > 9 b' Sigma b = grow' b' C b.
+//    The support's longest axis is often a third of the sphere of radius
+//    3 sqrt(tr Sigma) that bounds it, which this test cuts down to the
+//    ellipsoid's own extent towards the box.
+// The margin in grow covers the rounding of the single- or double-precision
+// evaluation and of these bounds; it grows with a bound on the condition
+// number of Sigma, kappa <= tr(Sigma)^D det(P).  Where that bound is large or
+// P is not positive definite, neither bound is used (valid = false) and the
+// sphere test alone decides.  The spherical kernel needs neither: its sphere
+// test is exact.
+template <typename T>
+struct SupportBounds {
+    T W2[3];
+    T C[6];        // cofactors c00, c11, c22, c01, c02, c12 (2D: c00, c11, c01 in slots 0, 1, 3)
+    T grow;        // 9 (1 + margin) / det P
+    bool valid;
+};
+
 template <typename T, int D, int KER>
-__device__ __forceinline__ void support_box(const T* r, T W2[3])
+__device__ __forceinline__ SupportBounds<T> support_bounds(const T* r)
 {
-    W2[0] = W2[1] = W2[2] = T(INFINITY);
-    if (KER == FLA_KERNEL_ISO) return;
+    SupportBounds<T> s;
+    s.W2[0] = s.W2[1] = s.W2[2] = T(INFINITY);
+    s.valid = false;
+    if (KER == FLA_KERNEL_ISO) return s;
     const T eps = sizeof(T) == 4 ? T(5.9604644775390625e-8) : T(1.1102230246251565e-16);
-    T diag[3] = {T(0), T(0), T(0)}, det;
+    T det;
     if (D == 2) {
         const T a = r[4], b = r[5], c = r[6];
         det = a * c - b * b;
-        diag[0] = c;
-        diag[1] = a;
+        s.C[0] = c;
+        s.C[1] = a;
+        s.C[2] = T(0);
+        s.C[3] = -b;
+        s.C[4] = s.C[5] = T(0);
     } else {
         const T p00 = r[4], p01 = r[5], p02 = r[6], p11 = r[7], p12 = r[8], p22 = r[9];
         const T c00 = p11 * p22 - p12 * p12, c11 = p00 * p22 - p02 * p02, c22 = p00 * p11 - p01 * p01;
-        const T c01 = p12 * p02 - p01 * p22, c02 = p01 * p12 - p11 * p02;
+        const T c01 = p12 * p02 - p01 * p22, c02 = p01 * p12 - p11 * p02, c12 = p01 * p02 - p00 * p12;
         det = p00 * c00 + p01 * c01 + p02 * c02;
-        diag[0] = c00;
-        diag[1] = c11;
-        diag[2] = c22;
+        s.C[0] = c00;
+        s.C[1] = c11;
+        s.C[2] = c22;
+        s.C[3] = c01;
+        s.C[4] = c02;
+        s.C[5] = c12;
     }
     const T tr = r[ExtSlot<D, KER>::v] * T(1.0 / 9.0);
     const T kb = (D == 2 ? tr * tr : tr * tr * tr) * det;
-    if (!(det > T(0)) || !(kb <= T(1e4))) return;
-    const T grow = T(9) * (T(1) + T(0.0009765625) + T(64) * kb * eps) / det;
+    if (!(det > T(0)) || !(kb <= T(1e4))) return s;
+    s.grow = T(9) * (T(1) + T(0.0009765625) + T(64) * kb * eps) / det;
+    if (!(s.grow < T(INFINITY))) return s;
+    s.valid = true;
 #pragma unroll
     for (int q = 0; q < D; ++q) {
-        const T w2 = diag[q] * grow;
-        if (w2 >= T(0) && w2 < T(INFINITY)) W2[q] = w2;
+        const T w2 = s.C[q] * s.grow;
+        if (w2 >= T(0) && w2 < T(INFINITY)) s.W2[q] = w2;
     }
+    return s;
 }
 
 // The warp sub-tiles of a tile that a staged record can reach: bit w set when
 // the record's support sphere (radius^2 in slot EXT, with the 2^-10 margin of
 // the tile test) reaches sub-tile w's box of cell centres and, for the J-scaled
-// kernel, its support box overlaps that box too.  slab[q][s] = {lo, hi} of the
-// s-th slab of sub-tiles along axis q (Tile<D>::NSX, NSY, NSZ of them).
+// kernel, its support box overlaps that box and no separating axis (above)
+// splits them.  slab[q][s] = {lo, hi} of the s-th slab of sub-tiles along
+// axis q (Tile<D>::NSX, NSY, NSZ of them).
 template <typename T, int D, int KER>
 __device__ __forceinline__ unsigned subtile_mask(const T* rv, const T (*slab)[4][2])
 {
     constexpr int NSX = Tile<D>::NSX, NSY = Tile<D>::NSY, NSZ = Tile<D>::NSZ;
-    T W2[3];
-    support_box<T, D, KER>(rv, W2);
+    const SupportBounds<T> sb = support_bounds<T, D, KER>(rv);
     const T e2m = rv[ExtSlot<D, KER>::v] * T(1.0009765625);
-    T d2a[NSX], d2b[NSY], d2c[NSZ];
-    bool ba[NSX], bb[NSY], bc[NSZ];
-    auto dist2 = [&](int q, int sl) {
+    T ba_[NSX], bb_[NSY], bc_[NSZ];   // signed offsets to the nearest point of each slab
+    auto off = [&](int q, int sl) {
         const T dl = slab[q][sl][0] - rv[q], dh = rv[q] - slab[q][sl][1];
-        const T dd = dl > T(0) ? dl : (dh > T(0) ? dh : T(0));
-        return dd * dd;
+        return dl > T(0) ? dl : (dh > T(0) ? -dh : T(0));
     };
 #pragma unroll
-    for (int sl = 0; sl < NSX; ++sl) { d2a[sl] = dist2(0, sl); ba[sl] = d2a[sl] <= W2[0]; }
+    for (int sl = 0; sl < NSX; ++sl) ba_[sl] = off(0, sl);
 #pragma unroll
-    for (int sl = 0; sl < NSY; ++sl) { d2b[sl] = dist2(1, sl); bb[sl] = d2b[sl] <= W2[1]; }
+    for (int sl = 0; sl < NSY; ++sl) bb_[sl] = off(1, sl);
 #pragma unroll
-    for (int sl = 0; sl < NSZ; ++sl) {
-        d2c[sl] = D == 3 ? dist2(2, sl) : T(0);
-        bc[sl] = D == 3 ? d2c[sl] <= W2[2] : true;
-    }
+    for (int sl = 0; sl < NSZ; ++sl) bc_[sl] = D == 3 ? off(2, sl) : T(0);
     unsigned m = 0;
 #pragma unroll
     for (int w = 0; w < GT / 32; ++w) {
         const int sx = w % NSX, sy = (w / NSX) % NSY, sz = w / (NSX * NSY);
-        T d2 = T(0);
-        d2 += d2a[sx];
-        d2 += d2b[sy];
-        if (D == 3) d2 += d2c[sz];
-        if (d2 <= e2m && ba[sx] && bb[sy] && bc[sz]) m |= 1u << w;
+        const T bx = ba_[sx], by = bb_[sy], bz = bc_[sz];
+        const T xx = bx * bx, yy = by * by, zz = bz * bz;
+        const T d2 = D == 3 ? xx + yy + zz : xx + yy;
+        bool hit = d2 <= e2m;
+        if (KER != FLA_KERNEL_ISO && sb.valid) {
+            hit = hit && xx <= sb.W2[0] && yy <= sb.W2[1] && (D == 2 || zz <= sb.W2[2]);
+            T qf = sb.C[0] * xx + sb.C[1] * yy + T(2) * sb.C[3] * (bx * by);
+            if (D == 3) qf += sb.C[2] * zz + T(2) * (sb.C[4] * (bx * bz) + sb.C[5] * (by * bz));
+            hit = hit && d2 * d2 <= sb.grow * qf;
+        }
+        if (hit) m |= 1u << w;
     }
     return m;
 }
