@@ -406,6 +406,23 @@ class DeviceCloud:
             c.fold[: planes_f.size].copy_(torch.from_numpy(planes_f.ravel()))
         return c
 
+    def snapshot(self) -> dict:
+        """Copies of the device buffers a run changes (state planes, meta words,
+        fold planes): the cloud's part of a checkpoint at a window boundary."""
+        snap = {"state": self.state.clone(), "meta": self.meta.clone()}
+        if self.fold is not None:
+            snap["fold"] = self.fold.clone()
+        return snap
+
+    def restore(self, snap: dict):
+        """Back to a snapshot of this cloud (or of one with the same seeds)."""
+        if snap["state"].shape != self.state.shape or ("fold" in snap) != (self.fold is not None):
+            raise FlaError("checkpoint does not match this cloud")
+        self.state.copy_(snap["state"])
+        self.meta.copy_(snap["meta"])
+        if self.fold is not None:
+            self.fold.copy_(snap["fold"])
+
     def struct(self) -> Cloud:
         c = Cloud()
         c.kind, c.dim, c.dtype, c.n_batches = self.kind, self.dim, self.dtype, self.n_batches
@@ -472,6 +489,15 @@ def workspace_order(ws, m: Mesh, n: int):
     off = C.c_size_t()
     check(lib().fla_workspace_order(C.byref(m), int(n), C.byref(off)), "fla_workspace_order")
     return ws[off.value:off.value + 4 * int(n)].view(torch.int32)
+
+
+def save_checkpoint(path, ck: dict) -> None:
+    """Write a checkpoint (Simulation / TwoWay / Batch .checkpoint()) to a file."""
+    _torch().save(ck, path)
+
+
+def load_checkpoint(path, device="cuda") -> dict:
+    return _torch().load(path, map_location=device)
 
 
 def workspace_size(m: Mesh, dtype: int, kernel: int, n: int) -> int:
@@ -694,6 +720,24 @@ class Simulation:
         self._sampled_t = None
         self._binned = None
 
+    def checkpoint(self) -> dict:
+        """The run at a window boundary: its step and copies of its clouds' device
+        buffers (torch.save-able).  restore() on a Simulation of the same workload
+        and form continues it with results bit for bit those of the uninterrupted
+        run: the advance and the deposit read nothing else that carries over."""
+        ck = {"step": self.step, "fla": self.fla.snapshot()}
+        if self.lpt is not None:
+            ck["lpt"] = self.lpt.snapshot()
+        return ck
+
+    def restore(self, ck: dict):
+        self.fla.restore(ck["fla"])
+        if self.lpt is not None:
+            self.lpt.restore(ck["lpt"])
+        self.step = int(ck["step"])
+        self._sampled_t = None
+        self._binned = None   # the workspace's order belongs to no restored cloud
+
     def _fla_cloud(self, device):
         wl = self.wl
         c = DeviceCloud.from_seeds(wl.fla, wl.dim, wl.delta, wl.dt, self.dtype, device)
@@ -767,14 +811,17 @@ class Batch:
         check(lib().fla_batch_create(ctx.handle, items, len(self.workloads), float(self.dt), int(self.window),
                                      int(step0), _ptr(self.ws), self.ws.numel(), C.byref(h)), "fla_batch_create")
         self.handle = h
+        self.step = int(step0)
         self.n_droplets = sum(c.n for c in self.clouds)
         self.n_cells = sum(m.n ** m.dim for m in self.meshes)
 
     def run(self, n_windows: int, stream=None):
         check(lib().fla_batch_run(self.ctx.handle, self.handle, int(n_windows), _stream_ptr(stream)), "fla_batch_run")
+        self.step += int(n_windows) * self.window
 
     def set_step(self, step: int, stream=None):
         check(lib().fla_batch_set_step(self.handle, int(step), _stream_ptr(stream)), "fla_batch_set_step")
+        self.step = int(step)
 
     def reset(self, stream=None):
         """Seeds back in place and the device step at 0."""
@@ -782,6 +829,18 @@ class Batch:
             c.state.copy_(st)
             c.meta.copy_(me)
         self.set_step(0, stream)
+
+    def checkpoint(self) -> dict:
+        """Every cloud's device buffers and the step of the next window (the
+        run's host-side count of the windows issued through run())."""
+        return {"step": self.step, "clouds": [c.snapshot() for c in self.clouds]}
+
+    def restore(self, ck: dict, stream=None):
+        if len(ck["clouds"]) != len(self.clouds):
+            raise FlaError("checkpoint does not match this batch")
+        for c, snap in zip(self.clouds, ck["clouds"]):
+            c.restore(snap)
+        self.set_step(int(ck["step"]), stream)
 
     def tuning(self) -> dict:
         a, g, o, n = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
@@ -843,6 +902,16 @@ class NavierStokes:
         self._keep = (w, r, U)
         self.reset(stream)
 
+    def snapshot(self) -> dict:
+        """A copy of the carrier's workspace (its fields and mean flow, stored at
+        offsets, so any workspace of the same configuration can take it back)."""
+        return {"ws": self.ws.clone()}
+
+    def restore(self, snap: dict):
+        if snap["ws"].numel() != self.ws.numel():
+            raise FlaError("checkpoint does not match this carrier")
+        self.ws.copy_(snap["ws"])
+
     def reset(self, stream=None):
         """Back to the initial state."""
         w, r, U = self._keep
@@ -898,6 +967,7 @@ class TwoWay:
         self.out = SourceFields(self.m, dtype, device)
         self.ws = aligned_ws(workspace(self.m, dtype, wl.kernel, self.fla.n, device))
         self.step = 0
+        self._restored = False
         self._seeds = (self.fla.state.clone(), self.fla.meta.clone())
 
     def reset(self, stream=None):
@@ -907,12 +977,28 @@ class TwoWay:
         self.ns.reset(stream)
         self.step = 0
 
+    def checkpoint(self) -> dict:
+        """Droplets, carrier and step at a window boundary (torch.save-able)."""
+        return {"step": self.step, "fla": self.fla.snapshot(), "ns": self.ns.snapshot(),
+                "sources": (self.out.s_mass.clone(), self.out.s_mom.clone())}
+
+    def restore(self, ck: dict):
+        self.fla.restore(ck["fla"])
+        self.ns.restore(ck["ns"])
+        self.out.s_mass.copy_(ck["sources"][0])
+        self.out.s_mom.copy_(ck["sources"][1])
+        # the next window's order comes from a deposit into this object's
+        # workspace, which a restored run has not made yet
+        self.step = int(ck["step"])
+        self._restored = True
+
     def window(self, stream=None):
         wl = self.wl
         k = wl.window
         self.ns.nodes(self.dtype, self.nodes, stream)
         # after the first window the workspace holds the droplets' cell-sorted order
-        order = workspace_order(self.ws, self.m, self.fla.n) if self.step > 0 else None
+        order = workspace_order(self.ws, self.m, self.fla.n) if self.step > 0 and not self._restored else None
+        self._restored = False
         advance(self.ctx, self.fla, self.m, self.nodes, self.step, k, wl.dt, reset_acc=True, stream=stream,
                 order=order)
         deposit_sources(self.ctx, self.fla, self.m, self.cfg, self.out, self.ws, stream)
