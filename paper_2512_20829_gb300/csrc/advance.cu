@@ -501,27 +501,45 @@ __device__ __forceinline__ void interp_x2(const AdvX2Args& a, const df* x, df* u
     float sa[NV], sb[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) sa[q] = sb[q] = 0.0f;
+    // Corner weights w = prod_q (f_q or g_q), corners in the order of their
+    // bits (x, then y, then z): the factors of the lower axes once per stage,
+    // then one product with the last axis's factor per corner.  The products
+    // are left unrenormalised (hi + lo, |lo| a few ulp(hi) at most): they only
+    // feed the split w = w1 + w2, which needs w to about 2^-36.
+    constexpr int NC = 1 << (D - 1);
+    df wl[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        wl[c] = (c & 1) ? f[0] : g[0];
+        if (D == 3) wl[c] = mul_unnorm(wl[c], ((c >> 1) & 1) ? f[1] : g[1]);
+    }
     // two corners per iteration: fully unrolled, the node loads of all corners
     // compete for registers and spill (3D cone: 380.8 ms per run fully
     // unrolled, 391.7 ms rolled, 374.8 ms two at a time)
 #pragma unroll 2
     for (int cnr = 0; cnr < (1 << D); ++cnr) {
-        df w = (cnr & 1) ? f[0] : g[0];
+        const int c = cnr & (NC - 1);
+        df wlo;   // selected, not indexed: an indexed wl would live in local memory
+        if (D == 3) {
+            const bool hy = (c >> 1) & 1;
+            wlo = (c & 1) ? (hy ? wl[NC - 1] : wl[1]) : (hy ? wl[NC - 2] : wl[0]);
+        } else {
+            wlo = (c & 1) ? wl[NC - 1] : wl[0];
+        }
+        const df w = mul_unnorm(wlo, (cnr >> (D - 1)) ? f[D - 1] : g[D - 1]);
         int64_t idx = base + (cnr & 1), m2 = nn;
 #pragma unroll
         for (int q = 1; q < D; ++q) {
-            const int bit = (cnr >> q) & 1;
-            w = w * (bit ? f[q] : g[q]);
-            idx += bit * m2;
+            idx += ((cnr >> q) & 1) * m2;
             m2 *= nn;
         }
         const float w1 = __fmul_rn(rintf(__fmul_rn(w.hi, 1024.0f)), 1.0f / 1024.0f);
         const float w2 = __fadd_rn(__fsub_rn(w.hi, w1), w.lo);   // w.hi - w1 is exact
         float va[S], vb[S];
 #pragma unroll
-        for (int c = 0; c < S / 4; ++c) {
-            load4<float>(a.nodes, idx * (S / 4) + c, va + 4 * c);
-            load4<float>(a.nodes + a.n_nodes * S, idx * (S / 4) + c, vb + 4 * c);
+        for (int k = 0; k < S / 4; ++k) {
+            load4<float>(a.nodes, idx * (S / 4) + k, va + 4 * k);
+            load4<float>(a.nodes + a.n_nodes * S, idx * (S / 4) + k, vb + 4 * k);
         }
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
@@ -535,14 +553,16 @@ __device__ __forceinline__ void interp_x2(const AdvX2Args& a, const df* x, df* u
     for (int q = 0; q < D * D; ++q) G[q] = two_sum(sa[D + q], sb[D + q]);
 }
 
-// Right-hand side of Eqs. 3 and 8 in double-float.
+// Right-hand side of Eqs. 3 and 8 in double-float.  The slopes are left
+// unrenormalised (hi + lo with |lo| a few ulp(hi)): they only enter the
+// stage states and the slope sum, whose operations take any such pair.
 template <int D, bool FLA>
 __device__ __forceinline__ void rhs_x2(const df* y, const df* u, const df* G, df invSt, df* f)
 {
 #pragma unroll
     for (int q = 0; q < D; ++q) {
         f[q] = y[D + q];
-        f[D + q] = (u[q] - y[D + q]) * invSt;
+        f[D + q] = mul_unnorm(add_unnorm(u[q], -y[D + q]), invSt);
     }
     if (FLA) {
         const df* J = y + 2 * D;
@@ -557,7 +577,7 @@ __device__ __forceinline__ void rhs_x2(const df* y, const df* u, const df* G, df
                 for (int j = 1; j < D; ++j) gj = dot_add(gj, G[i * D + j], J[j * D + k]);
                 gj = dot_add(gj, -W[i * D + k]);
                 f[2 * D + i * D + k] = W[i * D + k];
-                f[2 * D + D * D + i * D + k] = dot_value(gj) * invSt;
+                f[2 * D + D * D + i * D + k] = mul_unnorm(dot_unnorm(gj), invSt);
             }
     }
 }
@@ -666,12 +686,14 @@ __device__ __forceinline__ int advance_x2_one(const AdvX2Args& a, int64_t i, Vec
             // state y + c k (c = dt/2, dt/2, dt)
             const float wk = (stage == 1 || stage == 2) ? 2.0f : 1.0f;
             const df c = stage == 2 ? a.dt : a.half;
+            // the running slope sum and the stage states stay unrenormalised; the
+            // step's final axpy renormalises the new state
 #pragma unroll
             for (int q = 0; q < NY; ++q)
-                ks.set(q, stage == 0 ? k[q] : ks.get(q) + df{k[q].hi * wk, k[q].lo * wk});
+                ks.set(q, stage == 0 ? k[q] : add_unnorm(ks.get(q), df{k[q].hi * wk, k[q].lo * wk}));
             if (stage < 3) {
 #pragma unroll
-                for (int q = 0; q < NY; ++q) ys[q] = df_axpy(c, k[q], y.get(q));
+                for (int q = 0; q < NY; ++q) ys[q] = axpy_unnorm(c, k[q], y.get(q));
             }
         }
 #pragma unroll

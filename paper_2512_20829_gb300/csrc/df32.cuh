@@ -80,6 +80,14 @@ __device__ __forceinline__ df operator+(df a, float b)
     return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
 }
 
+// a + b without the final renormalisation (|lo| up to a few ulp(hi)): for
+// running sums whose value is renormalised once at the end.
+__device__ __forceinline__ df add_unnorm(df a, df b)
+{
+    const df s = two_sum(a.hi, b.hi);
+    return {s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo))};
+}
+
 // y + c k in one pass: the exact product of the high parts and the cross terms
 // added to the exact sum's error, one renormalisation.
 __device__ __forceinline__ df df_axpy(df c, df k, df y)
@@ -89,6 +97,16 @@ __device__ __forceinline__ df df_axpy(df c, df k, df y)
     float e = __fadd_rn(s.lo, __fadd_rn(y.lo, p.lo));
     e = __fmaf_rn(c.hi, k.lo, __fmaf_rn(c.lo, k.hi, e));
     return fast_two_sum(s.hi, e);
+}
+
+// df_axpy without the final renormalisation (|lo| up to a few ulp(hi)).
+__device__ __forceinline__ df axpy_unnorm(df c, df k, df y)
+{
+    const df p = two_prod(c.hi, k.hi);
+    const df s = two_sum(y.hi, p.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(y.lo, p.lo));
+    e = __fmaf_rn(c.hi, k.lo, __fmaf_rn(c.lo, k.hi, e));
+    return {s.hi, e};
 }
 
 // Compensated dot product (Ogita, Rump and Oishi 2005, "Dot2"): the running
@@ -124,6 +142,9 @@ __device__ __forceinline__ DotAcc dot_add(DotAcc acc, df b)
 
 __device__ __forceinline__ df dot_value(DotAcc acc) { return fast_two_sum(acc.s, acc.e); }
 
+// The sum as an unrenormalised pair (s, e): |e| can reach a few ulp(s).
+__device__ __forceinline__ df dot_unnorm(DotAcc acc) { return {acc.s, acc.e}; }
+
 __device__ __forceinline__ df operator-(df a, float b) { return a + (-b); }
 
 // a b: the exact product of the high parts plus the two cross terms (the
@@ -133,6 +154,16 @@ __device__ __forceinline__ df operator*(df a, df b)
     const df p = two_prod(a.hi, b.hi);
     const float e = __fmaf_rn(a.lo, b.hi, __fmaf_rn(a.hi, b.lo, p.lo));
     return fast_two_sum(p.hi, e);
+}
+
+// a b without the final renormalisation: hi is the rounded product of the
+// high parts and lo collects its rounding error and the cross terms, so
+// |lo| can reach a few ulp(hi); the pair still represents a b to about u^2.
+// For products that feed further products or a final split, not comparisons.
+__device__ __forceinline__ df mul_unnorm(df a, df b)
+{
+    const df p = two_prod(a.hi, b.hi);
+    return {p.hi, __fmaf_rn(a.lo, b.hi, __fmaf_rn(a.hi, b.lo, p.lo))};
 }
 
 __device__ __forceinline__ df operator*(df a, float b)
