@@ -771,14 +771,17 @@ cudaError_t launch_x2(const AdvX2Args& b, cudaStream_t s)
 // Batched clouds of one dimension (single precision, FLA): droplet g of the
 // group belongs to cloud k with pre[k] <= g < pre[k + 1] of the group's
 // prefix; the per-droplet work is that of k_advance.
+// skip_active: leave droplets that are active now to the cell-sorted part of
+// an ordered launch (below).
 template <int D>
 __device__ __forceinline__ int batch_advance_droplet(const BatchDev& b, int first, int count, int64_t g, int nsteps,
-                                                     double dt, int reset, DevStatus* st)
+                                                     double dt, int reset, DevStatus* st, bool skip_active = false)
 {
     // droplets of the group's clouds are contiguous in the global droplet order
     const int64_t base = b.drop_pre[first];
     const int k = first + batch_find(b.drop_pre + first, count, base + g);
     const BatchCloud& c = b.clouds[k];
+    if (skip_active && (c.meta[base + g - b.drop_pre[k]] & FLA_META_ACTIVE)) return 0;
     AdvArgs a{};
     a.state = c.state;
     a.meta = c.meta;
@@ -796,14 +799,37 @@ __device__ __forceinline__ int batch_advance_droplet(const BatchDev& b, int firs
     return advance_one<float, D, true, kPlain>(a, base + g - b.drop_pre[k], nf);
 }
 
+// The launch covers 2 n_dim threads.  Once a window of this run has binned
+// the clouds (step[1] set), the droplets that were active then -- the sorted
+// positions [s0, s1) of this dimension's cells, s1 - s0 = A of them -- are
+// taken in that cell-sorted order by threads [0, A), so that the droplets of a
+// warp read the same carrier nodes; threads [A, A + n_dim) then run through
+// the dimension's droplets in seed order and take those that are not active
+// (pending releases; dead ones return at once).  The two sets are disjoint:
+// between the binning and this launch no kernel changes a meta word, and a
+// droplet that the sorted part ends stays out of the second set.  Each
+// droplet's arithmetic is the same whichever thread runs it.
 template <int D>
 __global__ void __launch_bounds__(256) k_batch_advance(BatchDev b, int first, int count, int64_t n_dim,
                                                        int nsteps, double dt, int reset, DevStatus* st)
 {
     pdl_entry();
-    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int n = 0;
-    if (g < n_dim) n = batch_advance_droplet<D>(b, first, count, g, nsteps, dt, reset, st);
+    if (b.step[1] == 0) {
+        if (t < n_dim) n = batch_advance_droplet<D>(b, first, count, t, nsteps, dt, reset, st);
+    } else {
+        const int g0 = batch_group(D, 0);
+        const uint32_t s0 = __ldg(b.bin_start + b.group_cells[g0]);
+        const uint32_t s1 = __ldg(b.bin_start + b.group_cells[g0 + 2]);
+        const int64_t A = s1 > s0 ? (int64_t)(s1 - s0) : 0;
+        if (t < A) {
+            const int64_t g = (int64_t)__ldg(b.perm + s0 + t) - b.drop_pre[first];
+            if (g >= 0 && g < n_dim) n = batch_advance_droplet<D>(b, first, count, g, nsteps, dt, reset, st);
+        } else if (t - A < n_dim) {
+            n = batch_advance_droplet<D>(b, first, count, t - A, nsteps, dt, reset, st, true);
+        }
+    }
     __shared__ int s_sum[8];
     const int w = __reduce_add_sync(0xffffffffu, n);
     if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = w;
@@ -908,7 +934,7 @@ cudaError_t launch_batch_advance(const BatchDev& b, int dim, int64_t n_dim, int 
     if (n_dim == 0 || nsteps == 0) return cudaSuccess;
     const int g0 = batch_group(dim, 0);
     const int first = b.group_first[g0], count = b.group_first[g0 + 2] - first;
-    const unsigned blocks = (unsigned)((n_dim + threads - 1) / threads);
+    const unsigned blocks = (unsigned)((2 * n_dim + threads - 1) / threads);   // see k_batch_advance
     if (dim == 2) launch_pdl(k_batch_advance<2>, dim3(blocks), dim3(threads), 0, s, b, first, count, n_dim, nsteps, dt, reset ? 1 : 0, st);
     else launch_pdl(k_batch_advance<3>, dim3(blocks), dim3(threads), 0, s, b, first, count, n_dim, nsteps, dt, reset ? 1 : 0, st);
     return cudaGetLastError();

@@ -467,6 +467,7 @@ extern "C" int fla_batch_create(fla_ctx* ctx, const fla_batch_item* items, int32
     p->bin_start = at<uint32_t>(ws, L.bin_start);
     b.bin_start = p->bin_start;
     p->bins = bin_plan(L.n_total, L.cells_total);
+    b.perm = p->sort.vals[bin_sorted_buffer(p->bins)];   // the same buffer every window
     p->persistent_ok = persistent_ok;
     *out = p;
     return FLA_OK;
@@ -482,9 +483,13 @@ extern "C" void fla_batch_destroy(fla_batch_plan* plan)
 extern "C" int fla_batch_set_step(fla_batch_plan* plan, int32_t step, fla_stream_t stream)
 {
     if (!plan || step < 0) return FLA_ERR_ARG;
-    static thread_local int host_step;   // pageable source: the copy is staged at the call
-    host_step = step;
-    return cudaMemcpyAsync(plan->dev.step, &host_step, sizeof(int), cudaMemcpyHostToDevice, (cudaStream_t)stream) ==
+    // step[1] = 0: the workspace's binning is not this run's (the next window
+    // advances in seed order)
+    static thread_local int host_step[2];   // pageable source: the copy is staged at the call
+    host_step[0] = step;
+    host_step[1] = 0;
+    return cudaMemcpyAsync(plan->dev.step, host_step, sizeof(host_step), cudaMemcpyHostToDevice,
+                           (cudaStream_t)stream) ==
                    cudaSuccess
                ? FLA_OK
                : FLA_ERR_CUDA;

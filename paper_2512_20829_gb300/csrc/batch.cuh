@@ -47,7 +47,8 @@ struct BatchDev {
     int64_t nodes_total;
     const int64_t* drop_pre;      // n_clouds + 1 droplet offsets
     const int64_t* node_pre;      // n_clouds + 1 node offsets
-    int* step;                    // first step of the next window
+    int* step;                    // [0] first step of the next window; [1] 1 when perm and
+                                  // bin_start hold the binning of the window before it
     unsigned int* ext_max;        // per cloud: max squared support radius (float bits)
     unsigned int* tile_counter;   // per group
     void* cargs;                  // per cloud carrier arguments of the current window

@@ -659,7 +659,10 @@ cudaError_t launch_coop(const BinPlan& p, const BinArgs& a, const KF& kf, cudaSt
 __global__ void k_batch_step(int* step, int nsteps)
 {
     pdl_entry();
-    if (threadIdx.x == 0 && blockIdx.x == 0) *step += nsteps;
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        step[0] += nsteps;
+        step[1] = 1;   // this window's binning orders the next window's advance
+    }
 }
 
 }  // namespace

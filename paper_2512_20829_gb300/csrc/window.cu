@@ -92,7 +92,10 @@ __global__ void __launch_bounds__(kWinThreads, 1) k_batch_window(const __grid_co
     ok = ok && window_barrier(w.bin, ++gen, true);
 
     // the next window's start step (every CTA has read this one's)
-    if (ok && blockIdx.x == 0 && threadIdx.x == 0) *w.b.step += w.window;
+    if (ok && blockIdx.x == 0 && threadIdx.x == 0) {
+        w.b.step[0] += w.window;
+        w.b.step[1] = 1;   // this window's binning orders the next launched advance
+    }
 }
 
 size_t window_smem()
