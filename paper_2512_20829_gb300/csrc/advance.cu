@@ -513,10 +513,10 @@ __device__ __forceinline__ void interp_x2(const AdvX2Args& a, const df* x, df* u
         wl[c] = (c & 1) ? f[0] : g[0];
         if (D == 3) wl[c] = mul_unnorm(wl[c], ((c >> 1) & 1) ? f[1] : g[1]);
     }
-    // two corners per iteration: fully unrolled, the node loads of all corners
-    // compete for registers and spill (3D cone: 380.8 ms per run fully
-    // unrolled, 391.7 ms rolled, 374.8 ms two at a time)
-#pragma unroll 2
+    // four corners per iteration (3D cone, advance ms per run: 236.5 four at a
+    // time, 250.1 two at a time, 251.8 fully unrolled, where the node loads of
+    // all corners compete for the registers)
+#pragma unroll 4
     for (int cnr = 0; cnr < (1 << D); ++cnr) {
         const int c = cnr & (NC - 1);
         df wlo;   // selected, not indexed: an indexed wl would live in local memory
@@ -732,10 +732,11 @@ __device__ __forceinline__ int advance_x2_one(const AdvX2Args& a, int64_t i, Vec
 
 constexpr int kAdvX2Threads = 128;
 
-// The 2D step fits in 128 registers (4 blocks per SM; uncapped it takes 187 and
-// runs 8 % slower); the 3D step keeps its 255.
+// The 2D step runs 3 blocks per SM in 168 registers (13.8 ms per jet run,
+// against 14.5 ms at 4 blocks in 128 registers with spills; uncapped it takes
+// 187); the 3D step keeps its 255.
 template <int D, bool FLA>
-constexpr int x2_min_blocks() { return D == 2 && FLA ? 4 : 1; }
+constexpr int x2_min_blocks() { return D == 2 && FLA ? 3 : 1; }
 
 template <int D, bool FLA>
 __global__ void __launch_bounds__(kAdvX2Threads, x2_min_blocks<D, FLA>()) k_advance_x2(AdvX2Args a)
