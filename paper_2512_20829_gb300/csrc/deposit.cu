@@ -75,6 +75,35 @@ template <> struct Tile<3> {
 constexpr int GT = 256;            // threads per CTA = cells per tile
 constexpr int CAP = 4 * GT;        // staged records (1,024: 4-5 % faster than 512 on the ABC cone)
 
+// The x cells of mesh row (y, z) whose records can reach the tile with origin
+// t0: a record in a cell dq cells away from the tile's cells along axis q lies
+// at least (dq - 1/2) cells from the box of their centres (0 for dq = 0), and
+// a record reaches the tile only within its support radius of that box (the
+// staging test: d^2 <= ext (1 + 2^-10)).  rr2 = (largest such radius in cells)^2
+// with that margin.  Returns false for a row no record of which can reach it.
+template <int D>
+__device__ __forceinline__ bool row_xrange(int N, const int t0[3], int y, int z, float rr2, int& xlo, int& xhi)
+{
+    constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
+    const int dy = max(max(t0[1] - y, y - (t0[1] + TY - 1)), 0);
+    const int dz = D == 3 ? max(max(t0[2] - z, z - (t0[2] + TZ - 1)), 0) : 0;
+    const float ey = dy > 0 ? (float)dy - 0.5f : 0.0f, ez = dz > 0 ? (float)dz - 0.5f : 0.0f;
+    const float rem = rr2 - ey * ey - ez * ez;
+    if (!(rem >= 0.0f)) return false;
+    // dx - 1/2 <= sqrt(rem), with a little slack over the float rounding
+    const int xr = (int)floorf(sqrtf(rem) * 1.0001f + 0.5f + 1e-3f);
+    xlo = max(t0[0] - xr, 0);
+    xhi = min(t0[0] + TX - 1 + xr, N - 1);
+    return xlo <= xhi;
+}
+
+// (largest support radius in cells)^2 with the staging test's margin, from the
+// cloud's largest squared support radius ext2max
+__device__ __forceinline__ float row_radius2(float ext2max, int N)
+{
+    return ext2max * 1.0009765625f * (float)N * (float)N * 1.0001f;
+}
+
 // position of the squared support radius inside a record
 template <int D, int KER> struct ExtSlot { static constexpr int v = (KER == FLA_KERNEL_ISO) ? (D == 2 ? 7 : 3) : (D == 2 ? 3 : 10); };
 
@@ -366,6 +395,7 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty
     }
     const float ext2max = __uint_as_float(ldro(a.ext_max));
     const int R = (int)floorf(sqrtf(ext2max) * (float)N + 0.5f) + 1;
+    const float rr2 = row_radius2(ext2max, N);
 
     T sD = T(0), cD = T(0);
     T sN[4] = {T(0), T(0), T(0), T(0)}, cN[4] = {T(0), T(0), T(0), T(0)};
@@ -373,8 +403,6 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty
     int count = 0;      // staged records (the same in every thread)
     int wbuf = 0;       // s_wcount buffer of the current chunk
 
-    const int xlo = t0[0] - R < 0 ? 0 : t0[0] - R;
-    const int xhi = t0[0] + TX - 1 + R > N - 1 ? N - 1 : t0[0] + TX - 1 + R;
     const int ylo = t0[1] - R < 0 ? 0 : t0[1] - R;
     const int yhi = t0[1] + TY - 1 + R > N - 1 ? N - 1 : t0[1] + TY - 1 + R;
     int zlo = 0, zhi = 0;
@@ -437,11 +465,12 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty
     for (int rb = 0; rb < nrows && off < c1; rb += GT) {
         const int r = rb + tid;
         uint32_t beg = 0, len = 0;
-        if (r < nrows) {
+        int rxlo, rxhi;
+        if (r < nrows && row_xrange<D>(N, t0, ylo + r % ny, zlo + r / ny, rr2, rxlo, rxhi)) {
             const int y = ylo + r % ny, z = zlo + r / ny;
             const int64_t rowbase = ((int64_t)z * N + y) * N;
-            beg = ldro(a.bin_start + rowbase + xlo);
-            len = ldro(a.bin_start + rowbase + xhi + 1) - beg;
+            beg = ldro(a.bin_start + rowbase + rxlo);
+            len = ldro(a.bin_start + rowbase + rxhi + 1) - beg;
         }
         uint32_t x = len;
 #pragma unroll
@@ -654,13 +683,16 @@ __device__ __forceinline__ void nw_tile_cand(const NwItems& a, int t, int lane)
     const int N = tr.g.N;
     const float ext2max = __uint_as_float(ldro(tr.g.ext_max));
     const int R = (int)floorf(sqrtf(ext2max) * (float)N + 0.5f) + 1;
-    const int xlo = max(tr.o[0] - R, 0), xhi = min(tr.o[0] + Tile<D>::X - 1 + R, N - 1);
+    const float rr2 = row_radius2(ext2max, N);
+    const int t0[3] = {tr.o[0], tr.o[1], tr.o[2]};
     const int ylo = max(tr.o[1] - R, 0), yhi = min(tr.o[1] + Tile<D>::Y - 1 + R, N - 1);
     const int zlo = D == 3 ? max(tr.o[2] - R, 0) : 0;
     const int zhi = D == 3 ? min(tr.o[2] + Tile<D>::Z - 1 + R, N - 1) : 0;
     const int ny = yhi - ylo + 1, nrows = ny * (zhi - zlo + 1);
     uint32_t cand = 0;
     for (int r = lane; r < nrows; r += 32) {
+        int xlo, xhi;
+        if (!row_xrange<D>(N, t0, ylo + r % ny, zlo + r / ny, rr2, xlo, xhi)) continue;
         const int64_t rb = ((int64_t)(zlo + r / ny) * N + ylo + r % ny) * N;
         cand += ldro(tr.g.bin_start + rb + xhi + 1) - ldro(tr.g.bin_start + rb + xlo);
     }
