@@ -81,6 +81,9 @@ constexpr int CAP = 4 * GT;        // staged records (1,024: 4-5 % faster than 5
 // a record reaches the tile only within its support radius of that box (the
 // staging test: d^2 <= ext (1 + 2^-10)).  rr2 = (largest such radius in cells)^2
 // with that margin.  Returns false for a row no record of which can reach it.
+// The plan and the gather both call this and must agree on every row to the
+// bit, so each operation is rounded explicitly (no contraction that could
+// differ between the two call sites).
 template <int D>
 __device__ __forceinline__ bool row_xrange(int N, const int t0[3], int y, int z, float rr2, int& xlo, int& xhi)
 {
@@ -88,10 +91,10 @@ __device__ __forceinline__ bool row_xrange(int N, const int t0[3], int y, int z,
     const int dy = max(max(t0[1] - y, y - (t0[1] + TY - 1)), 0);
     const int dz = D == 3 ? max(max(t0[2] - z, z - (t0[2] + TZ - 1)), 0) : 0;
     const float ey = dy > 0 ? (float)dy - 0.5f : 0.0f, ez = dz > 0 ? (float)dz - 0.5f : 0.0f;
-    const float rem = rr2 - ey * ey - ez * ez;
+    const float rem = __fsub_rn(__fsub_rn(rr2, __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
     if (!(rem >= 0.0f)) return false;
     // dx - 1/2 <= sqrt(rem), with a little slack over the float rounding
-    const int xr = (int)floorf(sqrtf(rem) * 1.0001f + 0.5f + 1e-3f);
+    const int xr = (int)floorf(__fadd_rn(__fmul_rn(__fsqrt_rn(rem), 1.0001f), 0.501f));
     xlo = max(t0[0] - xr, 0);
     xhi = min(t0[0] + TX - 1 + xr, N - 1);
     return xlo <= xhi;
@@ -101,7 +104,15 @@ __device__ __forceinline__ bool row_xrange(int N, const int t0[3], int y, int z,
 // cloud's largest squared support radius ext2max
 __device__ __forceinline__ float row_radius2(float ext2max, int N)
 {
-    return ext2max * 1.0009765625f * (float)N * (float)N * 1.0001f;
+    const float n = (float)N;
+    return __fmul_rn(__fmul_rn(__fmul_rn(__fmul_rn(ext2max, 1.0009765625f), n), n), 1.0001f);
+}
+
+// Rows of a tile's neighbourhood on each side: the largest support radius in
+// cells, rounded up with a cell to spare (rounded explicitly, as row_xrange).
+__device__ __forceinline__ int support_rows(float ext2max, int N)
+{
+    return (int)floorf(__fadd_rn(__fmul_rn(__fsqrt_rn(ext2max), (float)N), 0.5f)) + 1;
 }
 
 // position of the squared support radius inside a record
@@ -394,7 +405,7 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& a, int tx0, int ty
         s_slab[q][sl][end] = centre(end ? last : first);
     }
     const float ext2max = __uint_as_float(ldro(a.ext_max));
-    const int R = (int)floorf(sqrtf(ext2max) * (float)N + 0.5f) + 1;
+    const int R = support_rows(ext2max, N);
     const float rr2 = row_radius2(ext2max, N);
 
     T sD = T(0), cD = T(0);
@@ -682,7 +693,7 @@ __device__ __forceinline__ void nw_tile_cand(const NwItems& a, int t, int lane)
     const TileRef tr = tile_ref<D>(a, t);
     const int N = tr.g.N;
     const float ext2max = __uint_as_float(ldro(tr.g.ext_max));
-    const int R = (int)floorf(sqrtf(ext2max) * (float)N + 0.5f) + 1;
+    const int R = support_rows(ext2max, N);
     const float rr2 = row_radius2(ext2max, N);
     const int t0[3] = {tr.o[0], tr.o[1], tr.o[2]};
     const int ylo = max(tr.o[1] - R, 0), yhi = min(tr.o[1] + Tile<D>::Y - 1 + R, N - 1);

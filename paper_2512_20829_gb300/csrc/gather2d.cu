@@ -46,7 +46,8 @@ __device__ __forceinline__ float ex2_approx(float x)
 __device__ __forceinline__ int support_cells(const unsigned int* ext_max, int N)
 {
     const float ext2max = __uint_as_float(__ldg(ext_max));
-    return (int)floorf(sqrtf(ext2max) * (float)N + 0.5f) + 1;
+    // rounded explicitly: the plan and the gather must agree on R to the bit
+    return (int)floorf(__fadd_rn(__fmul_rn(__fsqrt_rn(ext2max), (float)N), 0.5f)) + 1;
 }
 
 struct PlanArgs {
