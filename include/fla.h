@@ -286,9 +286,9 @@ int fla_batch_deadline(double St0, double delta, double dt, int32_t step_start, 
 int fla_advance(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* mesh, const void* nodes_dev,
                 int32_t step0, int32_t nsteps, double dt, uint32_t flags, fla_stream_t stream);
 
-/* fla_advance with a processing order: thread t of the launch advances
- * droplet order_dev[t] (device, n words, 4-byte aligned, caller-owned, read
- * only).  Each droplet's arithmetic does not depend on the order, so the
+/* fla_advance (the RK4 step of Eqs. 3-5 and 8, §2) with a processing order:
+ * thread t of the launch advances droplet order_dev[t] (device, n words,
+ * 4-byte aligned, caller-owned, read only).  Each droplet's arithmetic does not depend on the order, so the
  * results are bit for bit those of fla_advance; the order only decides which
  * droplets share a warp.  With the cell-sorted permutation of the cloud's last
  * binning (fla_workspace_order) the droplets of a warp lie in neighbouring
@@ -306,7 +306,8 @@ int fla_advance_ordered(fla_ctx* ctx, const fla_cloud* cloud, const fla_mesh* me
  * aligned. */
 int fla_workspace_size(const fla_mesh* mesh, int32_t dtype, int32_t kernel, int64_t n_droplets, size_t* bytes);
 
-/* Byte offset, within a deposit workspace, of the sorted permutation (n
+/* (No counterpart in the paper: the cell list is this library's.)  Byte
+ * offset, within a deposit workspace, of the sorted permutation (n
  * uint32 words: the droplet index at each position of the stable sort by cell
  * key, inactive droplets last) that fla_cell_bins, fla_deposit_sources,
  * psicell_deposit, cic_deposit and fla_learn_grad leave there for a cloud of
